@@ -1,0 +1,304 @@
+#!/usr/bin/env python
+"""Voxelwise ABC throughput on B300: voxels/s to posterior (and voxel-draw pairs/s).
+
+One step = the whole hot path over one synthetic volume: prior draws and
+simulated TACs for every candidate model, tensor-core discrepancy + top-k,
+posterior model probabilities and posterior summaries.  Default workload:
+the brain lp-ntPET/MRTM model-selection volume (250,000 voxels, 60 one-minute
+frames, 1,000,000 draws per model, k = 500), BF16 discrepancy with exact FP32
+re-scoring.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision bf16r|fp32] [--workload NAME]
+
+Multi-GPU (torchrun): every rank runs its own voxel shard against the same
+seeded draws (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "raclopride_lpntpet": "brain lp-ntPET vs MRTM: {J} voxels x ({n} MRTM + {n} lp-ntPET draws), 60 x 1-min frames, k={k}",
+    "totalbody_fdg": "total-body FDG 2TCM irr vs rev: {J} voxels x ({n} + {n} draws), 29 frames, k={k}",
+    "brain_fdg_2tcm": "2TCM-irr: {J} voxels x {n} draws, 22 frames, k={k}",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16r", choices=["bf16r", "fp32"])
+    ap.add_argument("--workload", default="raclopride_lpntpet", choices=sorted(WORKLOADS))
+    ap.add_argument("--voxels", type=int, default=None, help="override J (smaller runs)")
+    ap.add_argument("--draws", type=int, default=None, help="override draws per model")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def cpu_baseline(W, seconds_budget=20.0):
+    """The FP64 oracle as it stands, timed on this host on a bounded sample of the
+    workload and scaled to voxels/s of the full volume."""
+    import oracle
+    from paper_2603_14859_b300 import synth as S
+    oracle.build()
+    cores = oracle.num_threads()
+    L = W.L
+    # 1. simulation cost per draw, per model (sample of draws)
+    t_sim = 0.0
+    xs = []
+    sim_desc = []
+    for model, n in zip(W.models, W.n_per_model):
+        lo, hi = W.priors(model)
+        ns = 2000 if model != S.LPNTPET else 2000
+        ns = min(ns, n)
+        th = oracle.sample_prior(W.prior_seed, model, lo, hi, ns)
+        t0 = time.perf_counter()
+        x = oracle.simulate(model, W.ts, W.te, W.inp, th)
+        dt = time.perf_counter() - t0
+        t_sim += dt / ns * n
+        xs.append(x)
+        sim_desc.append(f"{ns} {S.MODEL_NAMES[model]} draws")
+    xs = np.concatenate(xs)
+    # 2. distance + full sort per voxel: sample of voxels against the sampled draws
+    rng = np.random.default_rng(0)
+    y = (xs[rng.integers(0, len(xs), 64)] * (1 + 0.1 * rng.standard_normal((64, L)))).astype(np.float32)
+    k = min(W.k, len(xs))
+    t0 = time.perf_counter()
+    oracle.topk(y, xs, W.weights, k)
+    dt = time.perf_counter() - t0
+    per_pair = dt / (64 * len(xs))
+    t_topk = per_pair * W.J * W.N * math.log(W.N) / math.log(len(xs))   # n log n sort
+    total = t_sim + t_topk
+    return {"value": W.J / total, "unit": "voxels/s", "cores": cores, "kind": "oracle",
+            "sample": (f"simulation timed on {', '.join(sim_desc)}; distance+sort timed on 64 voxels x "
+                       f"{len(xs)} draws; scaled to {W.J} voxels x {W.N} draws (sort as n log n)"),
+            "pairs_per_s": W.J * W.N / total}
+
+
+# ------------------------------------------------------------------ main
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2603_14859_b300 import synth as S
+
+    def make_workload(r):
+        W = S.workload(args.workload, seed=None, J=args.voxels, N_per_model=args.draws)
+        if r:   # another voxel shard of the volume, same seeded draws
+            W2 = S.workload(args.workload, seed=5000 + r, J=args.voxels, N_per_model=args.draws)
+            W2.prior_seed = W.prior_seed
+            W2.inp = W.inp
+            W = W2
+        return W
+
+    W = make_workload(rank)
+    cfg = {"workload": WORKLOADS[args.workload].format(J=W.J, n=W.n_per_model[0], k=W.k),
+           "voxels_per_gpu": W.J, "draws": W.N, "frames": W.L, "k": W.k,
+           "precision": args.precision, "l2": "inputs larger than L2 (draw operands + candidate lists > 126 MB)",
+           "parallelism": f"voxel shards x{args.gpus}" if args.gpus > 1 else "single GPU"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # the reference arm is the FP64 oracle on the host cores
+        vals = []
+        cb = None
+        for _ in range(args.warmup + args.steps):
+            cb = cpu_baseline(W)
+            vals.append(cb["value"])
+        v = statistics.median(vals[args.warmup:]) if args.steps else vals[-1]
+        cb["value"] = v
+        print(json.dumps({"impl": "reference", "metric": "voxels/s to posterior", "value": v, "unit": "voxels/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1000.0 * W.J / v, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+                          "cpu_baseline": cb, "e2e": {"value": v, "unit": "voxels/s", "h2d_bytes_per_step": 0,
+                                                      "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    from paper_2603_14859_b300 import _lib, api, pipeline
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    prec = _lib.ABC_FP32 if args.precision == "fp32" else _lib.ABC_BF16_RESCORE
+    run = pipeline.AbcPipeline(W, prec)
+    y = pipeline.make_y_gpu(W)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        run.step(y)
+    torch.cuda.synchronize()
+    st = api.topk_status(run.ws)
+    # timed region (device time on the launching stream)
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    for i in range(K):
+        api.profile_events(*ev[i])
+        run.step(y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    api.profile_events(None, None)
+    barrier()
+    ms = e0.elapsed_time(e1) / K
+    tc_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    clk = clocks.stop()
+    t = torch.tensor([ms, tc_ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, tc_ms = float(t[0]), float(t[1])
+
+    # end to end through the public API with host buffers
+    y_host = y.cpu().pin_memory()
+    outs_host = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in [run.prob, run.pref] + run.summ]
+    y_dev = torch.empty_like(y)
+    h2d = y_host.numel() * y_host.element_size()
+    d2h = sum(o.numel() * o.element_size() for o in outs_host)
+    Ke = max(1, min(K, 3))
+    barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(Ke):
+        y_dev.copy_(y_host, non_blocking=True)
+        out = run.step(y_dev)
+        for h, d in zip(outs_host, [out.prob, out.pref, out.mean, out.sd, out.lo, out.hi]):
+            h.copy_(d, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / Ke
+    t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(t[0])
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    n_gpu = world
+    voxels = W.J * n_gpu
+    value = voxels / (ms / 1000.0)
+    flops = 2.0 * W.L * W.J * W.N
+    achieved = flops / (tc_ms / 1000.0) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        src = open(os.path.join(ROOT, "paper_2603_14859_b300", "csrc", "topk.cu"), "rb").read()
+        h = hashlib.sha1(src).hexdigest()[:12]
+        rec = json.load(open(tp)).get(f"{args.workload}/{args.precision}")
+        if rec and rec.get("source_sha1") == h:
+            traffic = rec["bytes_per_launch"]
+    launches_per_step = 2 * len(W.models) + 7
+    line = {
+        "metric": "voxels/s to posterior", "value": value, "unit": "voxels/s", "n_gpus": n_gpu, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if prec == _lib.ABC_BF16_RESCORE else "bf16x3-split (fp32-exact)",
+        "data": "synthetic", "config": cfg,
+        "pairs_per_s": W.J * W.N * n_gpu / (ms / 1000.0),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_tc_topk (fused discrepancy + top-k filter)", "kernel_ms": tc_ms,
+                     "algorithmic_flops_per_launch": flops, "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"},
+        "e2e": {"value": voxels / (e2e_ms / 1000.0), "unit": "voxels/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * K,
+        "clocks": clk,
+        "topk_status": list(st),
+    }
+    if n_gpu == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(W)
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * vpetabc — voxelwise ABC rejection for dynamic PET kinetic modelling on one
+ * NVIDIA B300 (sm_103a).  C ABI of libvpetabc.so.
+ *
+ * The library runs the data-parallel hot path of vPET-ABC (Algorithm 1 of the
+ * paper): prior draws -> simulated frame-mean TACs -> frame-weighted squared
+ * Euclidean discrepancy to every voxel TAC -> the k nearest draws per voxel ->
+ * posterior model probabilities and posterior summaries.
+ *
+ * Conventions shared by every entry point
+ *  - Time is in minutes, rate constants in 1/min.
+ *  - `_dev` pointers are CUDA device memory owned by the caller; `_host`
+ *    pointers (and structs) are host memory read before the call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is enqueued on it asynchronously; host pointers are not
+ *    retained after return.
+ *  - Matrices are row-major with an explicit leading dimension (elements).
+ *  - Return value: ABC_OK (0) or a negative ABC_ERR_* code.  On error nothing
+ *    is enqueued, and abc_last_error() (thread-local) describes the cause.
+ *  - The library never allocates device memory on these paths: scratch comes
+ *    from the caller's `workspace`.
+ */
+#ifndef VPETABC_H
+#define VPETABC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ABC_OK 0
+#define ABC_ERR_ARG (-1)         /* invalid argument (null, size, alignment, range) */
+#define ABC_ERR_CUDA (-2)        /* a CUDA runtime/driver call failed */
+#define ABC_ERR_WORKSPACE (-3)   /* workspace too small or misaligned */
+#define ABC_ERR_TIMEOUT (-4)     /* a bounded device wait ran out (reported by abc_topk_status) */
+#define ABC_ERR_UNSUPPORTED (-5) /* shape outside what the kernels support (e.g. L > 61) */
+
+/* Kinetic models (Sec. II-A).  Parameter order of a draw row (theta):
+ *  ABC_2TCM_IRR: K1, k2, k3, Vb            (Eq. 1-2 with k4 = 0)
+ *  ABC_2TCM_REV: K1, k2, k3, k4, Vb        (Eq. 1-2)
+ *  ABC_MRTM:     R1, k2, BPnd              (Eq. 3 with gamma = 0; k2a = k2/(1+BPnd))
+ *  ABC_LPNTPET:  R1, k2, BPnd, gamma, tD, tP - tD, alpha   (Eq. 3-4)
+ * 2TCM models take the plasma input C_p (= C_wb for FDG, Sec. II-A); MRTM and
+ * lp-ntPET take the reference-region TAC C_r. */
+#define ABC_2TCM_IRR 0
+#define ABC_2TCM_REV 1
+#define ABC_MRTM 2
+#define ABC_LPNTPET 3
+
+/* Precision of the tensor-core discrepancy (Sec. II-C distance, Alg. 1 step 4).
+ *  ABC_FP32:         operands split into bf16 hi+lo pairs (three bf16 products
+ *                    per term, fp32 accumulate) with a rigorous error margin,
+ *                    then every surviving candidate re-scored exactly in fp32.
+ *                    The accepted set is the exact fp32 top-k.
+ *  ABC_BF16_RESCORE: one bf16 product per term; each voxel keeps its 4k
+ *                    nearest by the bf16 distance, which are re-scored exactly
+ *                    in fp32 before the final k are chosen. */
+#define ABC_FP32 0
+#define ABC_BF16_RESCORE 1
+
+/* Contiguous or gapped frame schedule: frame l spans [t_start[l], t_end[l]). */
+typedef struct {
+    int32_t L;
+    const double* t_start;
+    const double* t_end;
+} abc_frames;
+
+/* Input function sum_i (a0[i] + a1[i] t + a2[i] t^2) exp(-c[i] t), c[i] >= 0. */
+typedef struct {
+    int32_t n_terms;       /* 1 .. 16 */
+    const double* c;
+    const double* a0;
+    const double* a1;
+    const double* a2;
+} abc_polyexp;
+
+/* Feng's three-exponential plasma input (Sec. III-A):
+ * C_a(t) = (beta1 t - beta2 - beta3) e^{-kappa1 t} + beta2 e^{-kappa2 t} + beta3 e^{-kappa3 t},
+ * written into three poly-exponential terms (c, a0, a1, a2 each of length 3). */
+int abc_feng_input(const double beta[3], const double kappa[3], double c[3], double a0[3], double a1[3],
+                   double a2[3]);
+
+/* Prior draws (Algorithm 1, steps 1-2; uniform priors of Sec. III-A).
+ * Writes theta_dev[n * ldtheta + p] for n in [0, N), p in [0, P) with
+ * theta = fl32(lo[p] + (hi[p] - lo[p]) * u) evaluated in fp64, where u is the
+ * top 24 bits of word (p % 4) of Philox4x32-10 at counter
+ * (first_index + n [lo 32, hi 32 bits], model, p / 4) and key (seed lo, seed hi).
+ * The stream is reproducible from (seed, model, global draw index).
+ * lo/hi: host, P entries, lo <= hi.  P in 1..8, ldtheta >= P. */
+int abc_sample_prior(uint64_t seed, int32_t model, const double* lo_host, const double* hi_host, int32_t P,
+                     int64_t N, int64_t first_index, float* theta_dev, int32_t ldtheta, void* stream);
+
+/* Simulated frame-mean TACs (Algorithm 1, step 3):
+ * x_dev[n * ldx + l] = (1 / dt_l) * integral over frame l of C_t(t) for draw n,
+ * C_t from Eq. 1-2 (2TCM, closed-form convolution with `input` = C_p),
+ * Eq. 3 with gamma = 0 (MRTM, closed form, `input` = C_r), or Eq. 3-4
+ * (lp-ntPET: closed form up to t_D, exponential integrator after it).
+ * Columns l >= L of each row are left untouched.
+ * theta_dev: N x ldtheta fp32 (layout above).  L in 1..64, ldx >= L. */
+int abc_simulate(int32_t model, const abc_frames* frames_host, const abc_polyexp* input_host,
+                 const float* theta_dev, int64_t N, int32_t ldtheta, float* x_dev, int32_t ldx, void* stream);
+
+/* Bytes of device workspace abc_discrepancy_topk needs for these sizes. */
+size_t abc_workspace_size(int64_t J, int64_t N, int32_t L, int32_t k, int32_t precision);
+
+/* Discrepancy and top-k (Algorithm 1, steps 4-5; fixed-budget rejection,
+ * Sec. II-C).  For every voxel j in [0, J) finds the k draws n in [0, N)
+ * with the smallest d_jn = sum_l w_l (y_jl - x_nl)^2 and writes them sorted
+ * ascending by (d, n):
+ *   idx_dev[j * k + r]  = n       (global draw index, int32)
+ *   dist_dev[j * k + r] = d_jn    (fp32, computed directly from y and x)
+ * y_dev: J x ldy fp32 voxel TACs; x_dev: N x ldx fp32 simulated TACs;
+ * w_host: L frame weights >= 0 (not all zero); 1 <= k <= min(N, 2048);
+ * 1 <= L <= 61; N < 2^31.  ldx and ldy are multiples of 4 and the pointers
+ * 16-byte aligned.  workspace: >= abc_workspace_size(...) bytes, 256-byte
+ * aligned, device memory; its contents on entry do not matter.
+ * The voxel-by-draw distance matrix is never formed in memory. */
+int abc_discrepancy_topk(const float* y_dev, int64_t J, int32_t ldy, const float* x_dev, int64_t N, int32_t ldx,
+                         int32_t L, const float* w_host, int32_t k, int32_t precision, void* workspace,
+                         size_t ws_bytes, int32_t* idx_dev, float* dist_dev, void* stream);
+
+/* Status of the last abc_discrepancy_topk that used this workspace.  Blocks
+ * on `stream`.  Writes status[0] = ABC_OK or ABC_ERR_TIMEOUT, status[1] = the
+ * number of voxels whose candidate buffer hit its capacity (for ABC_FP32 the
+ * exactness guarantee then does not hold for those voxels). */
+int abc_topk_status(const void* workspace, int32_t status_host[2], void* stream);
+
+/* Timing hook: when both are non-NULL (cudaEvent_t passed as void*), every
+ * later abc_discrepancy_topk records `start_event` on its stream right before
+ * the fused tensor-core kernel and `stop_event` right after it, so a caller can
+ * time that kernel alone with cudaEventElapsedTime.  NULL, NULL turns it off.
+ * Process-wide setting; the events stay owned by the caller. */
+int abc_profile_events(void* start_event, void* stop_event);
+
+/* Test hook: the raw tensor-core ranking keys d' = ||yh||^2-free part of the
+ * distance (||xh_n||^2 - 2 yh_j . xh_n, yh = sqrt(w)(y - mu), xh = sqrt(w)(x - mu),
+ * mu the voxel-mean TAC held in the workspace at byte offset 256) for every
+ * pair, written to dump_dev (row stride ld_dump >= N rounded up to 128; J
+ * rounded up to 128 rows), without the top-k.  Same argument rules as
+ * abc_discrepancy_topk with k = 1. */
+int abc_debug_gemm_keys(const float* y_dev, int64_t J, int32_t ldy, const float* x_dev, int64_t N, int32_t ldx,
+                        int32_t L, const float* w_host, int32_t precision, void* workspace, size_t ws_bytes,
+                        float* dump_dev, int64_t ld_dump, void* stream);
+
+/* Posterior model probabilities (Sec. II-B Eq. 6; Sec. III-B).  Draws of model
+ * m are the global indices [offsets[m], offsets[m+1]).  prob_dev[j*M + m] =
+ * (# of the k accepted draws of voxel j from model m) / k; preferred_dev[j] =
+ * the model with most accepted draws, ties to the lower model position (with
+ * M = 2 a model is preferred with more than 50 % of the draws; an even split
+ * goes to the first-listed model).  M in 1..16. */
+int abc_model_select(const int32_t* idx_dev, int64_t J, int32_t k, const int64_t* model_offsets_host, int32_t M,
+                     float* prob_dev, int8_t* preferred_dev, void* stream);
+
+/* Posterior summaries (Sec. II-D point estimate = posterior mean; 95 %
+ * credible intervals; Sec. III-B K_i = K1 k3/(k2 + k3) per accepted sample).
+ * For voxel j the summarised set is the accepted draws of model
+ * preferred_dev[j] (or all k accepted draws when preferred_dev is NULL, using
+ * the parameters common to all models).  Output rows have ncols = Pmax + 1
+ * columns, Pmax = max(nparams): columns 0..P_m-1 hold the model's parameters,
+ * columns P_m..Pmax-1 are NaN, and column Pmax holds K_i when has_ki[m] (K1,
+ * k2, k3 read from theta columns ki_cols[0..2]) else NaN.
+ *   mean: arithmetic mean;  sd: standard deviation with ddof = 1 (0 for one
+ *   sample), accumulated in fp64;  lo / hi: the 0.025 / 0.975 quantiles by
+ *   linear interpolation between order statistics (type 7).
+ * Each output is J x ncols fp32, row-major. */
+int abc_summarize(const float* theta_dev, int32_t ldtheta, const int64_t* model_offsets_host, int32_t M,
+                  const int32_t* nparams_host, const int32_t* has_ki_host, const int32_t* ki_cols_host,
+                  const int32_t* idx_dev, int64_t J, int32_t k, const int8_t* preferred_dev, int32_t ncols,
+                  float* mean_dev, float* sd_dev, float* lo_dev, float* hi_dev, void* stream);
+
+/* Description of the last error on this thread ("" if none). */
+const char* abc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VPETABC_H */

@@ -1,0 +1,79 @@
+"""ctypes loader for libvpetabc.so (the C ABI in include/vpetabc.h).
+
+The shared library is built in-tree by `paper_2603_14859_b300.csrc.build`.
+There is no fallback: if the library is missing or a call fails, an
+exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "libvpetabc.so")
+
+ABC_OK = 0
+ABC_ERR_ARG = -1
+ABC_ERR_CUDA = -2
+ABC_ERR_WORKSPACE = -3
+ABC_ERR_TIMEOUT = -4
+ABC_ERR_UNSUPPORTED = -5
+ABC_2TCM_IRR, ABC_2TCM_REV, ABC_MRTM, ABC_LPNTPET = 0, 1, 2, 3
+ABC_FP32, ABC_BF16_RESCORE = 0, 1
+
+# every symbol the public header declares
+EXPORTS = [
+    "abc_feng_input", "abc_sample_prior", "abc_simulate", "abc_workspace_size", "abc_discrepancy_topk",
+    "abc_topk_status", "abc_model_select", "abc_summarize", "abc_last_error", "abc_profile_events",
+    "abc_debug_gemm_keys",
+]
+
+
+class Frames(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("t_start", ctypes.c_void_p), ("t_end", ctypes.c_void_p)]
+
+
+class PolyExp(ctypes.Structure):
+    _fields_ = [("n_terms", ctypes.c_int32), ("c", ctypes.c_void_p), ("a0", ctypes.c_void_p),
+                ("a1", ctypes.c_void_p), ("a2", ctypes.c_void_p)]
+
+
+class AbcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(SO_PATH):
+        raise RuntimeError(f"{SO_PATH} is not built; run `python -m paper_2603_14859_b300.csrc.build`")
+    L = ctypes.CDLL(SO_PATH)
+    P, i32, i64, u64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+    L.abc_feng_input.argtypes = [P, P, P, P, P, P]
+    L.abc_sample_prior.argtypes = [u64, i32, P, P, i32, i64, i64, P, i32, P]
+    L.abc_simulate.argtypes = [i32, ctypes.POINTER(Frames), ctypes.POINTER(PolyExp), P, i64, i32, P, i32, P]
+    L.abc_workspace_size.argtypes = [i64, i64, i32, i32, i32]
+    L.abc_workspace_size.restype = sz
+    L.abc_discrepancy_topk.argtypes = [P, i64, i32, P, i64, i32, i32, P, i32, i32, P, sz, P, P, P]
+    L.abc_topk_status.argtypes = [P, P, P]
+    L.abc_model_select.argtypes = [P, i64, i32, P, i32, P, P, P]
+    L.abc_summarize.argtypes = [P, i32, P, i32, P, P, P, P, i64, i32, P, i32, P, P, P, P, P]
+    L.abc_last_error.restype = ctypes.c_char_p
+    L.abc_profile_events.argtypes = [P, P]
+    L.abc_debug_gemm_keys.argtypes = [P, i64, i32, P, i64, i32, i32, P, i32, P, sz, P, i64, P]
+    for fn in ["abc_feng_input", "abc_sample_prior", "abc_simulate", "abc_discrepancy_topk", "abc_topk_status",
+               "abc_model_select", "abc_summarize", "abc_debug_gemm_keys", "abc_profile_events"]:
+        getattr(L, fn).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def check(rc: int):
+    if rc != ABC_OK:
+        raise AbcError(rc, lib().abc_last_error().decode())

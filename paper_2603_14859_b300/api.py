@@ -1,0 +1,159 @@
+"""Thin PyTorch-facing wrappers over the C ABI (argument marshalling only).
+
+Device tensors are torch CUDA tensors; every call is enqueued on the current
+torch CUDA stream unless `stream` is given.  All arithmetic runs in the CUDA
+library; nothing here computes on the host beyond packing arguments.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, lib
+
+PARAM_COUNT = {_lib.ABC_2TCM_IRR: 4, _lib.ABC_2TCM_REV: 5, _lib.ABC_MRTM: 3, _lib.ABC_LPNTPET: 7}
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def feng_input(beta, kappa):
+    """Feng's three-exponential plasma input as poly-exponential arrays (c, a0, a1, a2)."""
+    b = _np(beta, np.float64)
+    k = _np(kappa, np.float64)
+    outs = [np.zeros(3) for _ in range(4)]
+    check(lib().abc_feng_input(*(o.ctypes.data_as(ctypes.c_void_p) for o in [b, k] + outs)))
+    return outs
+
+
+def sample_prior(seed, model, lo, hi, N, first_index=0, ldtheta=8, out=None, stream=None):
+    lo = _np(lo, np.float64)
+    hi = _np(hi, np.float64)
+    P = len(lo)
+    if out is None:
+        out = torch.zeros((N, ldtheta), dtype=torch.float32, device="cuda")
+    assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.shape[0] >= N
+    check(lib().abc_sample_prior(seed, model, lo.ctypes.data_as(ctypes.c_void_p), hi.ctypes.data_as(ctypes.c_void_p),
+                                 P, N, first_index, _ptr(out), out.shape[1], _stream(stream)))
+    return out
+
+
+class _HostArgs:
+    """Keeps the host arrays of a frames / input struct alive for one call."""
+
+    def __init__(self, ts, te, inp):
+        self.ts = _np(ts, np.float64)
+        self.te = _np(te, np.float64)
+        self.arr = [_np(a, np.float64) for a in (inp.c, inp.a0, inp.a1, inp.a2)]
+        self.frames = _lib.Frames(len(self.ts), self.ts.ctypes.data, self.te.ctypes.data)
+        self.inp = _lib.PolyExp(len(self.arr[0]), *[a.ctypes.data for a in self.arr])
+
+
+def simulate(model, ts, te, inp, theta, N=None, ldx=None, out=None, stream=None):
+    """Frame-mean TACs for the first N rows of theta (N x ldtheta fp32, CUDA)."""
+    N = theta.shape[0] if N is None else N
+    L = len(ts)
+    ldx = ldx or ((L + 3) // 4) * 4
+    if out is None:
+        out = torch.zeros((N, ldx), dtype=torch.float32, device="cuda")
+    h = _HostArgs(ts, te, inp)
+    check(lib().abc_simulate(model, ctypes.byref(h.frames), ctypes.byref(h.inp), _ptr(theta), N, theta.shape[1],
+                             _ptr(out), out.shape[1], _stream(stream)))
+    return out
+
+
+def workspace_size(J, N, L, k, precision):
+    n = lib().abc_workspace_size(J, N, L, k, precision)
+    if n == 0:
+        raise ValueError("abc_workspace_size: unsupported sizes")
+    return n
+
+
+def alloc_workspace(J, N, L, k, precision):
+    n = workspace_size(J, N, L, k, precision)
+    return torch.empty(n, dtype=torch.uint8, device="cuda")
+
+
+def discrepancy_topk(y, x, L, w, k, precision=_lib.ABC_FP32, workspace=None, idx=None, dist=None, stream=None):
+    """k nearest draws per voxel: returns (idx int32 J x k, dist fp32 J x k)."""
+    J, N = y.shape[0], x.shape[0]
+    w = _np(w, np.float32)
+    if workspace is None:
+        workspace = alloc_workspace(J, N, L, k, precision)
+    if idx is None:
+        idx = torch.empty((J, k), dtype=torch.int32, device="cuda")
+    if dist is None:
+        dist = torch.empty((J, k), dtype=torch.float32, device="cuda")
+    check(lib().abc_discrepancy_topk(_ptr(y), J, y.shape[1], _ptr(x), N, x.shape[1], L,
+                                     w.ctypes.data_as(ctypes.c_void_p), k, precision, _ptr(workspace),
+                                     workspace.numel(), _ptr(idx), _ptr(dist), _stream(stream)))
+    return idx, dist
+
+
+def topk_status(workspace, stream=None):
+    st = np.zeros(2, np.int32)
+    check(lib().abc_topk_status(_ptr(workspace), st.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return int(st[0]), int(st[1])
+
+
+def debug_gemm_keys(y, x, L, w, precision, stream=None):
+    """Raw tensor-core ranking keys d' = ||xh||^2 - 2 yh.xh for all pairs (test hook)."""
+    J, N = y.shape[0], x.shape[0]
+    w = _np(w, np.float32)
+    ws = alloc_workspace(J, N, L, 1, precision)
+    Jp, Np = -(-J // 128) * 128, -(-N // 128) * 128
+    dump = torch.full((Jp, Np), float("nan"), dtype=torch.float32, device="cuda")
+    check(lib().abc_debug_gemm_keys(_ptr(y), J, y.shape[1], _ptr(x), N, x.shape[1], L,
+                                    w.ctypes.data_as(ctypes.c_void_p), precision, _ptr(ws), ws.numel(), _ptr(dump),
+                                    Np, _stream(stream)))
+    return dump[:J, :N], ws
+
+
+def model_select(idx, offsets, prob=None, pref=None, stream=None):
+    J, k = idx.shape
+    off = _np(offsets, np.int64)
+    M = len(off) - 1
+    if prob is None:
+        prob = torch.empty((J, M), dtype=torch.float32, device="cuda")
+    if pref is None:
+        pref = torch.empty(J, dtype=torch.int8, device="cuda")
+    check(lib().abc_model_select(_ptr(idx), J, k, off.ctypes.data_as(ctypes.c_void_p), M, _ptr(prob), _ptr(pref),
+                                 _stream(stream)))
+    return prob, pref
+
+
+def summarize(theta, offsets, nparams, has_ki, ki_cols, idx, pref=None, out=None, stream=None):
+    """Posterior summaries -> (mean, sd, lo, hi), each J x (max(nparams) + 1) fp32."""
+    J, k = idx.shape
+    off = _np(offsets, np.int64)
+    npar = _np(nparams, np.int32)
+    hk = _np(has_ki, np.int32)
+    kc = _np(ki_cols, np.int32)
+    nc = int(npar.max()) + 1
+    if out is None:
+        out = [torch.empty((J, nc), dtype=torch.float32, device="cuda") for _ in range(4)]
+    check(lib().abc_summarize(_ptr(theta), theta.shape[1], off.ctypes.data_as(ctypes.c_void_p), len(off) - 1,
+                              npar.ctypes.data_as(ctypes.c_void_p), hk.ctypes.data_as(ctypes.c_void_p),
+                              kc.ctypes.data_as(ctypes.c_void_p), _ptr(idx), J, k, _ptr(pref), nc,
+                              *[_ptr(o) for o in out], _stream(stream)))
+    return tuple(out)
+
+
+def profile_events(start=None, stop=None):
+    """Record torch.cuda.Event pair around the fused tensor-core kernel (None, None = off)."""
+    a = ctypes.c_void_p(start.cuda_event) if start is not None else None
+    b = ctypes.c_void_p(stop.cuda_event) if stop is not None else None
+    check(lib().abc_profile_events(a, b))

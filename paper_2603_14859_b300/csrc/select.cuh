@@ -1,0 +1,121 @@
+// Warp-cooperative selection on per-voxel candidate lists (Algorithm 1, step 5:
+// keep the smallest distances).  Candidates live in global memory as parallel
+// arrays of fp32 keys and int32 draw indices; one warp works on one list.
+#pragma once
+#include <stdint.h>
+
+namespace vpet {
+
+// Order-preserving map of fp32 onto uint32 (negative values flipped).
+__device__ __forceinline__ uint32_t f2key(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// Radix select over keys[0..cnt): returns a key value T with
+//   #{i : key(keys[i]) <= T} >= rank + 1,
+// resolved to the top `levels` x 8 bits (the returned T is the largest key of
+// the bucket holding the element of that rank; levels = 4 gives the exact key).
+// hist: 256 words of this warp's shared memory.  All lanes get the result.
+__device__ __forceinline__ uint32_t warp_select(const float* keys, int cnt, int rank, int levels, uint32_t* hist,
+                                                int lane) {
+    uint32_t prefix = 0;
+    int r = rank;
+    for (int lv = 0; lv < levels; ++lv) {
+        const int shift = 24 - 8 * lv;
+        const uint32_t mask = lv == 0 ? 0u : (0xFFFFFFFFu << (shift + 8));
+#pragma unroll
+        for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0;
+        __syncwarp();
+        int i = lane;
+        for (; i + 96 < cnt; i += 128) {
+            const uint32_t k0 = f2key(keys[i]), k1 = f2key(keys[i + 32]), k2 = f2key(keys[i + 64]),
+                           k3 = f2key(keys[i + 96]);
+            if ((k0 & mask) == prefix) atomicAdd(&hist[(k0 >> shift) & 255u], 1u);
+            if ((k1 & mask) == prefix) atomicAdd(&hist[(k1 >> shift) & 255u], 1u);
+            if ((k2 & mask) == prefix) atomicAdd(&hist[(k2 >> shift) & 255u], 1u);
+            if ((k3 & mask) == prefix) atomicAdd(&hist[(k3 >> shift) & 255u], 1u);
+        }
+        for (; i < cnt; i += 32) {
+            const uint32_t k0 = f2key(keys[i]);
+            if ((k0 & mask) == prefix) atomicAdd(&hist[(k0 >> shift) & 255u], 1u);
+        }
+        __syncwarp();
+        uint32_t loc[8], sum = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) { loc[b] = hist[lane * 8 + b]; sum += loc[b]; }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        uint32_t c = incl - sum;
+        int found = -1, newr = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            if (found < 0 && c + loc[b] > (uint32_t)r) { found = lane * 8 + b; newr = r - (int)c; }
+            c += loc[b];
+        }
+        const uint32_t who = __ballot_sync(0xFFFFFFFFu, found >= 0);
+        const int src = who ? __ffs(who) - 1 : 31;
+        const int bin = __shfl_sync(0xFFFFFFFFu, found, src);
+        r = __shfl_sync(0xFFFFFFFFu, newr, src);
+        prefix |= (uint32_t)(bin < 0 ? 255 : bin) << shift;
+        __syncwarp();
+    }
+    const int low_bits = 32 - 8 * levels;
+    return low_bits > 0 ? (prefix | ((1u << low_bits) - 1u)) : prefix;
+}
+
+// In-place stable compaction of (keys, idx)[0..cnt) to the entries with key <= T.
+// At most `cap` entries are written; returns the number that qualified (which
+// may exceed cap).
+__device__ __forceinline__ int warp_compact(float* keys, int32_t* idx, int cnt, uint32_t T, int cap, int lane) {
+    int out = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        float k = 0.0f;
+        int32_t id = 0;
+        bool keep = false;
+        if (i < cnt) {
+            k = keys[i];
+            id = idx[i];
+            keep = f2key(k) <= T;
+        }
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+        const int pos = out + __popc(bal & ((1u << lane) - 1u));
+        if (keep && pos < cap) {
+            keys[pos] = k;
+            idx[pos] = id;
+        }
+        out += __popc(bal);
+    }
+    __syncwarp();
+    return out;
+}
+
+// Ascending bitonic sort of n (a power of two) 64-bit keys in this warp's shared memory.
+__device__ __forceinline__ void warp_bitonic_sort(unsigned long long* s, int n, int lane) {
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncwarp();
+            for (int t = lane; t < (n >> 1); t += 32) {
+                const int lo = 2 * t - (t & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = ((lo & size) == 0);
+                const unsigned long long a = s[lo], b = s[hi];
+                if ((a > b) == up) {
+                    s[lo] = b;
+                    s[hi] = a;
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+}  // namespace vpet

@@ -1,0 +1,233 @@
+// Posterior model probabilities and posterior summaries over each voxel's
+// accepted draws (Sec. II-B Eq. 6, Sec. II-D, Sec. III-B).  One warp per voxel;
+// fp64 accumulation for means and variances; credible intervals from sorted
+// order statistics (type-7 interpolation).
+#include <string.h>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int MAXM = 16;
+
+struct Segs {
+    int M;
+    int64_t off[MAXM + 1];
+};
+
+__device__ __forceinline__ int model_of(int64_t i, const Segs& s) {
+    int m = 0;
+    while (m < s.M && i >= s.off[m + 1]) ++m;
+    return (i >= s.off[0] && m < s.M) ? m : -1;
+}
+
+__global__ void k_model_select(const int32_t* __restrict__ idx, int64_t J, int k, Segs S, float* __restrict__ prob,
+                               int8_t* __restrict__ pref) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= J) return;
+    int cnt[MAXM];
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) cnt[m] = 0;
+    for (int r = lane; r < k; r += 32) {
+        const int m = model_of(idx[j * k + r], S);
+#pragma unroll
+        for (int q = 0; q < MAXM; ++q) cnt[q] += (q == m);
+    }
+    int best = 0, bestc = -1;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+        int c = cnt[m];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        if (m < S.M) {
+            if (lane == 0) prob[j * S.M + m] = (float)c / (float)k;
+            if (c > bestc) { bestc = c; best = m; }
+        }
+    }
+    if (lane == 0) pref[j] = (int8_t)best;
+}
+
+struct SumParams {
+    Segs S;
+    int nparams[MAXM];
+    int has_ki[MAXM];
+    int ki[3];
+    int Pmax, ncols, k, p2, ldt;
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__device__ void bitonic_f(float* s, int n, int lane) {
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncwarp();
+            for (int t = lane; t < (n >> 1); t += 32) {
+                const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const float a = s[lo], b = s[hi];
+                if ((a > b) == up) { s[lo] = b; s[hi] = a; }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+__global__ void k_summarize(const float* __restrict__ theta, const int32_t* __restrict__ idx, int64_t J,
+                            const int8_t* __restrict__ pref, SumParams Q, float* __restrict__ mean,
+                            float* __restrict__ sd, float* __restrict__ lo, float* __restrict__ hi) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t* sel = (int32_t*)sm + (size_t)wid * Q.p2;
+    float* vals = (float*)(sm + (size_t)warps * Q.p2 * 4) + (size_t)wid * Q.p2;
+    const int64_t j = (int64_t)blockIdx.x * warps + wid;
+    if (j >= J) return;
+    const int pm = pref ? (int)pref[j] : -1;
+    int P = pm >= 0 ? Q.nparams[pm] : Q.Pmax;
+    int ki = pm >= 0 ? Q.has_ki[pm] : 1;
+    if (pm < 0)
+        for (int m = 0; m < Q.S.M; ++m) {
+            if (Q.nparams[m] < P) P = Q.nparams[m];
+            if (!Q.has_ki[m]) ki = 0;
+        }
+    // accepted draws of the summarised model, in accepted order
+    int n = 0;
+    for (int base = 0; base < Q.k; base += 32) {
+        const int r = base + lane;
+        int32_t id = 0;
+        bool take = false;
+        if (r < Q.k) {
+            id = idx[j * Q.k + r];
+            take = id >= 0 && (pm < 0 || model_of(id, Q.S) == pm);
+        }
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, take);
+        if (take) sel[n + __popc(b & ((1u << lane) - 1u))] = id;
+        n += __popc(b);
+    }
+    __syncwarp();
+    const float qnan = __int_as_float(0x7FC00000);
+    for (int col = 0; col < Q.ncols; ++col) {
+        const bool isk = col == Q.Pmax;
+        float o0 = qnan, o1 = qnan, o2 = qnan, o3 = qnan;
+        if (n > 0 && ((isk && ki) || (!isk && col < P))) {
+            double s = 0.0;
+            for (int i = lane; i < n; i += 32) {
+                const float* th = theta + (int64_t)sel[i] * Q.ldt;
+                float v;
+                if (isk) {
+                    const double K1 = th[Q.ki[0]], k2 = th[Q.ki[1]], k3 = th[Q.ki[2]];
+                    v = (float)(K1 * k3 / (k2 + k3));
+                } else {
+                    v = th[col];
+                }
+                vals[i] = v;
+                s += v;
+            }
+            s = warp_sum_d(s);
+            const double mu = s / n;
+            double ss = 0.0;
+            __syncwarp();
+            for (int i = lane; i < n; i += 32) {
+                const double e = (double)vals[i] - mu;
+                ss += e * e;
+            }
+            ss = warp_sum_d(ss);
+            int n2 = 1;
+            while (n2 < n) n2 <<= 1;
+            for (int i = n + lane; i < n2; i += 32) vals[i] = __int_as_float(0x7F800000);
+            bitonic_f(vals, n2, lane);
+            double qv[2];
+            const double qs[2] = {0.025, 0.975};
+            for (int t = 0; t < 2; ++t) {
+                const double h = (n - 1) * qs[t];
+                const int a = (int)floor(h);
+                const int b = a + 1 < n ? a + 1 : n - 1;
+                qv[t] = (double)vals[a] + (h - a) * ((double)vals[b] - (double)vals[a]);
+            }
+            o0 = (float)mu;
+            o1 = n > 1 ? (float)sqrt(ss / (n - 1)) : 0.0f;
+            o2 = (float)qv[0];
+            o3 = (float)qv[1];
+            __syncwarp();
+        }
+        if (lane == 0) {
+            mean[j * Q.ncols + col] = o0;
+            sd[j * Q.ncols + col] = o1;
+            lo[j * Q.ncols + col] = o2;
+            hi[j * Q.ncols + col] = o3;
+        }
+    }
+}
+
+int fill_segs(const int64_t* off, int M, Segs* s) {
+    VPET_ARG(off, "model offsets: null pointer");
+    VPET_ARG(M >= 1 && M <= MAXM, "model count must be in 1..%d", MAXM);
+    s->M = M;
+    for (int m = 0; m <= M; ++m) {
+        s->off[m] = off[m];
+        if (m > 0) VPET_ARG(off[m] >= off[m - 1], "model offsets must be non-decreasing");
+    }
+    return ABC_OK;
+}
+
+}  // namespace
+
+extern "C" int abc_model_select(const int32_t* idx_dev, int64_t J, int32_t k, const int64_t* model_offsets_host,
+                                int32_t M, float* prob_dev, int8_t* preferred_dev, void* stream) {
+    vpet::clear_error();
+    Segs S;
+    int rc = fill_segs(model_offsets_host, M, &S);
+    if (rc) return rc;
+    VPET_ARG(J >= 0 && k >= 1, "abc_model_select: need J >= 0, k >= 1");
+    if (J == 0) return ABC_OK;
+    VPET_ARG(idx_dev && prob_dev && preferred_dev, "abc_model_select: null pointer");
+    k_model_select<<<(unsigned)vpet_ceil_div(J, 8), 256, 0, (cudaStream_t)stream>>>(idx_dev, J, k, S, prob_dev,
+                                                                                   preferred_dev);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}
+
+extern "C" int abc_summarize(const float* theta_dev, int32_t ldtheta, const int64_t* model_offsets_host, int32_t M,
+                             const int32_t* nparams_host, const int32_t* has_ki_host, const int32_t* ki_cols_host,
+                             const int32_t* idx_dev, int64_t J, int32_t k, const int8_t* preferred_dev, int32_t ncols,
+                             float* mean_dev, float* sd_dev, float* lo_dev, float* hi_dev, void* stream) {
+    vpet::clear_error();
+    SumParams Q;
+    memset(&Q, 0, sizeof Q);
+    int rc = fill_segs(model_offsets_host, M, &Q.S);
+    if (rc) return rc;
+    VPET_ARG(nparams_host && has_ki_host && ki_cols_host, "abc_summarize: null host array");
+    VPET_ARG(k >= 1 && k <= 2048, "abc_summarize: k must be in 1..2048");
+    VPET_ARG(J >= 0, "abc_summarize: negative J");
+    Q.Pmax = 0;
+    for (int m = 0; m < M; ++m) {
+        VPET_ARG(nparams_host[m] >= 1 && nparams_host[m] <= ldtheta, "abc_summarize: nparams out of range");
+        Q.nparams[m] = nparams_host[m];
+        Q.has_ki[m] = has_ki_host[m] != 0;
+        if (nparams_host[m] > Q.Pmax) Q.Pmax = nparams_host[m];
+        if (Q.has_ki[m])
+            for (int c = 0; c < 3; ++c)
+                VPET_ARG(ki_cols_host[c] >= 0 && ki_cols_host[c] < nparams_host[m], "abc_summarize: bad ki_cols");
+    }
+    for (int c = 0; c < 3; ++c) Q.ki[c] = ki_cols_host[c] < 0 ? 0 : ki_cols_host[c];
+    VPET_ARG(ncols == Q.Pmax + 1, "abc_summarize: ncols must be max(nparams) + 1 = %d", Q.Pmax + 1);
+    Q.ncols = ncols;
+    Q.k = k;
+    Q.ldt = ldtheta;
+    int p2 = 32;
+    while (p2 < k) p2 <<= 1;
+    Q.p2 = p2;
+    if (J == 0) return ABC_OK;
+    VPET_ARG(theta_dev && idx_dev && mean_dev && sd_dev && lo_dev && hi_dev, "abc_summarize: null pointer");
+    int warps = 8;
+    while (warps > 1 && (size_t)warps * p2 * 8 > 48 * 1024) warps >>= 1;
+    const size_t smem = (size_t)warps * p2 * 8;
+    k_summarize<<<(unsigned)vpet_ceil_div(J, warps), warps * 32, smem, (cudaStream_t)stream>>>(
+        theta_dev, idx_dev, J, preferred_dev, Q, mean_dev, sd_dev, lo_dev, hi_dev);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}

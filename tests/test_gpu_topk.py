@@ -1,0 +1,135 @@
+"""Fused discrepancy + top-k (Algorithm 1 steps 4-5) against the FP64 oracle.
+
+Stage parity: the oracle ranks the GPU's own simulated TACs, so any difference
+is the discrepancy/top-k path alone.  Accepted sets must be identical except
+for draws inside the near-tie band tau * d_(k), tau = 16 L eps32; returned
+distances are the exact fp32 re-score (relative error <= 4 L eps32 vs fp64)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2603_14859_b300 import synth as S
+from parity import check_topk_sets
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_case(name, J, n, orc):
+    from paper_2603_14859_b300 import api
+    W = S.workload(name, J=J, N_per_model=n)
+    # measured TACs from the oracle's simulator (no CUDA in the inputs)
+    L = W.L
+    xc = np.zeros((W.J, L))
+    for th, rows in zip(W.truth, W.truth_rows):
+        if len(rows):
+            xc[rows] = orc.simulate(int(W.truth_model[rows[0]]), W.ts, W.te, W.inp, th)
+    y = S.add_noise(xc, W.ts, W.te, W.half_life, W.q, W.z)
+    ld = (L + 3) // 4 * 4
+    yp = np.zeros((W.J, ld), np.float32)
+    yp[:, :L] = y
+    off = W.model_offsets()
+    theta = torch.zeros((W.N, 8), device="cuda")
+    x = torch.zeros((W.N, ld), device="cuda")
+    for m, model in enumerate(W.models):
+        lo, hi = W.priors(model)
+        api.sample_prior(W.prior_seed, model, lo, hi, off[m + 1] - off[m], out=theta[off[m]:off[m + 1]])
+        api.simulate(model, W.ts, W.te, W.inp, theta[off[m]:off[m + 1]], out=x[off[m]:off[m + 1]])
+    return W, torch.from_numpy(yp).cuda(), x
+
+
+def _compare(orc, W, y, x, k, prec, tau_extra=0.0):
+    from paper_2603_14859_b300 import api
+    L = W.L
+    w = W.weights.astype(np.float32)
+    ws = api.alloc_workspace(W.J, x.shape[0], L, k, prec)
+    idx, dist = api.discrepancy_topk(y, x, L, w, k, prec, ws)
+    st = api.topk_status(ws)
+    idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
+    yn, xn = y.cpu().numpy()[:, :L], x.cpu().numpy()[:, :L].astype(np.float64)
+    oi, od = orc.topk(yn, xn, w.astype(np.float64), k)
+    swaps, worst = check_topk_sets(idx, oi, od, lambda vj, dn: orc.pair_dist(yn, xn, w, vj, dn), L, tau_extra)
+    # returned distances: exact fp32 re-score of the returned draws
+    J = W.J
+    ref = orc.pair_dist(yn, xn, w, np.repeat(np.arange(J), k), idx.reshape(-1)).reshape(J, k)
+    assert np.all(np.abs(dist - ref) <= 4 * L * 2.0**-24 * ref + 1e-30)
+    # sorted ascending by (distance, index)
+    assert np.all((np.diff(dist, axis=1) > 0) | ((np.diff(dist, axis=1) == 0) & (np.diff(idx, axis=1) > 0)))
+    assert st == (0, 0), f"status {st}"
+    return swaps, worst
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_topk_brain_2tcm_small(orc, prec):
+    W, y, x = _gpu_case("brain_fdg_2tcm", 300, 5000, orc)          # 3 voxel tiles (ragged), 40 draw tiles (ragged)
+    swaps, worst = _compare(orc, W, y, x, 100, prec)
+    assert swaps <= 3
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_topk_raclopride_two_models(orc, prec):
+    W, y, x = _gpu_case("raclopride_lpntpet", 260, 3000, orc)     # 60 frames, FP32 K = 192 (3 K-blocks)
+    _compare(orc, W, y, x, 50, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_topk_totalbody_rev_irr(orc, prec):
+    W, y, x = _gpu_case("totalbody_fdg", 129, 20000, orc)          # 29 frames, K = 128 (2 K-blocks)
+    _compare(orc, W, y, x, 200, prec)
+
+
+def test_topk_many_compactions(orc):
+    """k small against a long draw stream: the candidate lists are compacted many times."""
+    W, y, x = _gpu_case("brain_fdg_2tcm", 64, 60000, orc)
+    _compare(orc, W, y, x, 5, 0)
+
+
+@pytest.mark.parametrize("k", [1, 7])
+def test_topk_tiny_and_k_edges(orc, k):
+    W, y, x = _gpu_case("brain_fdg_2tcm", 5, 9, orc)               # N = 9 < one tile
+    _compare(orc, W, y, x, k, 0)
+    _compare(orc, W, y, x, 9, 0)                                   # k = N
+
+
+def test_noise_free_recovery():
+    """A voxel whose TAC is exactly draw i*'s TAC gets i* first with distance 0."""
+    from paper_2603_14859_b300 import api
+    W = S.workload("brain_fdg_2tcm", J=4, N_per_model=4)
+    lo, hi = S.PRIORS[S.TCM2_IRR]
+    N = 7000
+    th = api.sample_prior(3, S.TCM2_IRR, lo, hi, N)
+    x = api.simulate(S.TCM2_IRR, W.ts, W.te, W.inp, th)
+    stars = [0, 4095, 6999, 1234, 5000]
+    y = x[stars].clone()
+    for prec in (0, 1):
+        idx, dist = api.discrepancy_topk(y, x, W.L, W.weights.astype(np.float32), 10, prec)
+        assert idx[:, 0].cpu().tolist() == stars
+        assert torch.all(dist[:, 0] == 0)
+
+
+def test_ties_resolved_by_index():
+    from paper_2603_14859_b300 import api
+    W = S.workload("brain_fdg_2tcm", J=4, N_per_model=4)
+    lo, hi = S.PRIORS[S.TCM2_IRR]
+    th = api.sample_prior(3, S.TCM2_IRR, lo, hi, 500)
+    x = api.simulate(S.TCM2_IRR, W.ts, W.te, W.inp, th)
+    x[300] = x[17]
+    x[450] = x[17]
+    y = x[17:18].clone()
+    idx, dist = api.discrepancy_topk(y, x, W.L, W.weights.astype(np.float32), 3, 0)
+    assert idx[0].cpu().tolist() == [17, 300, 450]
+
+
+def test_argument_errors():
+    from paper_2603_14859_b300 import api
+    from paper_2603_14859_b300._lib import AbcError
+    y = torch.zeros((4, 24), device="cuda")
+    x = torch.zeros((10, 24), device="cuda")
+    w = np.ones(22, np.float32)
+    with pytest.raises(AbcError):
+        api.discrepancy_topk(y, x, 22, w, 11, 0)          # k > N
+    with pytest.raises(AbcError):
+        api.discrepancy_topk(y, x, 22, -w, 3, 0)          # negative weights
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(AbcError) as e:
+        api.discrepancy_topk(y, x, 22, w, 3, 0, workspace=ws)
+    assert e.value.code == -3
