@@ -213,6 +213,10 @@ def main():
     K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for a, b in ev:             # torch creates the CUDA event objects on first record
+        a.record(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     barrier()
     torch.cuda.synchronize()
@@ -291,7 +295,7 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * K,
         "clocks": clk,
-        "topk_status": list(st),
+        "topk_status": {"error": st[0], "exact_scan_voxels": st[1], "tie_overflow_voxels": st[2], "uncertified_voxels": st[3]},
     }
     if n_gpu == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)

@@ -51,12 +51,16 @@ extern "C" {
 
 /* Precision of the tensor-core discrepancy (Sec. II-C distance, Alg. 1 step 4).
  *  ABC_FP32:         operands split into bf16 hi+lo pairs (three bf16 products
- *                    per term, fp32 accumulate) with a rigorous error margin,
- *                    then every surviving candidate re-scored exactly in fp32.
- *                    The accepted set is the exact fp32 top-k.
+ *                    per term, fp32 accumulate); each voxel keeps its 2k
+ *                    nearest by that distance, re-scores them exactly in fp32,
+ *                    and certifies from the product error bound that no other
+ *                    draw can be nearer than the k-th; a voxel that cannot be
+ *                    certified is resolved by an exact fp32 scan.  The accepted
+ *                    set is the exact fp32 top-k.
  *  ABC_BF16_RESCORE: one bf16 product per term; each voxel keeps its 4k
  *                    nearest by the bf16 distance, which are re-scored exactly
- *                    in fp32 before the final k are chosen. */
+ *                    in fp32 before the final k are chosen (certification is
+ *                    reported, not enforced). */
 #define ABC_FP32 0
 #define ABC_BF16_RESCORE 1
 
@@ -122,10 +126,19 @@ int abc_discrepancy_topk(const float* y_dev, int64_t J, int32_t ldy, const float
                          size_t ws_bytes, int32_t* idx_dev, float* dist_dev, void* stream);
 
 /* Status of the last abc_discrepancy_topk that used this workspace.  Blocks
- * on `stream`.  Writes status[0] = ABC_OK or ABC_ERR_TIMEOUT, status[1] = the
- * number of voxels whose candidate buffer hit its capacity (for ABC_FP32 the
- * exactness guarantee then does not hold for those voxels). */
-int abc_topk_status(const void* workspace, int32_t status_host[2], void* stream);
+ * on `stream`.  Writes
+ *   status[0] = ABC_OK or ABC_ERR_TIMEOUT (a bounded device wait ran out; the
+ *               outputs are then not valid);
+ *   status[1] = number of voxels resolved by an exact fp32 scan of all draws
+ *               (ABC_FP32 voxels whose tensor-core result could not be
+ *               certified, or whose candidate list overflowed; exact results);
+ *   status[2] = number of voxels with more candidates tied at the k-th
+ *               distance than the final sort holds (those ties are cut in
+ *               list order rather than by index);
+ *   status[3] = ABC_BF16_RESCORE voxels whose accepted set could not be
+ *               certified exact from the bf16 error bound (the 4k net may
+ *               have missed a member of the exact top-k). */
+int abc_topk_status(const void* workspace, int32_t status_host[4], void* stream);
 
 /* Timing hook: when both are non-NULL (cudaEvent_t passed as void*), every
  * later abc_discrepancy_topk records `start_event` on its stream right before

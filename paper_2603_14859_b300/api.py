@@ -104,9 +104,9 @@ def discrepancy_topk(y, x, L, w, k, precision=_lib.ABC_FP32, workspace=None, idx
 
 
 def topk_status(workspace, stream=None):
-    st = np.zeros(2, np.int32)
+    st = np.zeros(4, np.int32)
     check(lib().abc_topk_status(_ptr(workspace), st.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
-    return int(st[0]), int(st[1])
+    return tuple(int(v) for v in st)
 
 
 def debug_gemm_keys(y, x, L, w, precision, stream=None):

@@ -30,18 +30,22 @@ __device__ __forceinline__ uint32_t warp_select(const float* keys, int cnt, int 
 #pragma unroll
         for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0;
         __syncwarp();
-        int i = lane;
-        for (; i + 96 < cnt; i += 128) {
-            const uint32_t k0 = f2key(keys[i]), k1 = f2key(keys[i + 32]), k2 = f2key(keys[i + 64]),
-                           k3 = f2key(keys[i + 96]);
-            if ((k0 & mask) == prefix) atomicAdd(&hist[(k0 >> shift) & 255u], 1u);
-            if ((k1 & mask) == prefix) atomicAdd(&hist[(k1 >> shift) & 255u], 1u);
-            if ((k2 & mask) == prefix) atomicAdd(&hist[(k2 >> shift) & 255u], 1u);
-            if ((k3 & mask) == prefix) atomicAdd(&hist[(k3 >> shift) & 255u], 1u);
-        }
-        for (; i < cnt; i += 32) {
-            const uint32_t k0 = f2key(keys[i]);
-            if ((k0 & mask) == prefix) atomicAdd(&hist[(k0 >> shift) & 255u], 1u);
+        // lanes holding the same bin are merged with match.any, so a bin that most
+        // keys share costs one shared-memory atomic per 32 keys, not 32
+        for (int base = 0; base < cnt; base += 128) {
+            uint32_t kk[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = base + 32 * u + lane;
+                kk[u] = i < cnt ? f2key(keys[i]) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool in = base + 32 * u + lane < cnt && (kk[u] & mask) == prefix;
+                const uint32_t bin = (kk[u] >> shift) & 255u;
+                const uint32_t peers = __match_any_sync(0xFFFFFFFFu, in ? bin : (0x100u | (uint32_t)lane));
+                if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+            }
         }
         __syncwarp();
         uint32_t loc[8], sum = 0;

@@ -16,17 +16,30 @@
 // Warp roles: 0 = TMA producer, 1 = TMEM allocator + MMA issuer (one thread),
 // 2..5 = epilogue (thread <-> voxel).  Accumulators are double-buffered in TMEM
 // (2 x 128 fp32 columns) so MMA of tile t+1 overlaps the epilogue of tile t.
-// The epilogue reads 32 columns at a time, takes their minimum, and only if it
-// is below the voxel's running threshold appends the passing (key, index)
-// pairs to the voxel's candidate list in global memory.  When a list could
-// overflow, the warp compacts it cooperatively (radix select of the k-th key,
-// then in-place filtering) and tightens the threshold:
-//   ABC_FP32: keep key <= T_k + 2E, T_k >= the k-th smallest key seen, which
-//             provably keeps every member of the exact top-k;
-//   ABC_BF16_RESCORE: keep the 4k smallest keys.
-// Kernel `k_finalize` (one warp per voxel) re-scores the surviving candidates
-// exactly as sum_l w_l (y_l - x_l)^2 in fp32, then selects and sorts the k
-// smallest by (distance, index).
+// The epilogue reads 32 columns at a time and takes their minimum; a thread
+// whose minimum is within its voxel's running threshold stages the 32 keys in
+// shared memory, and the warp then appends each such voxel's passing
+// (key, draw index) pairs to that voxel's candidate list in global memory with
+// one coalesced store.  When a list could overflow, the warp compacts it
+// (radix select of the kt-th key, in-place filtering) and tightens the
+// threshold, so each list always holds every draw whose key is at most the
+// kt-th smallest seen (the "net": kt = 2k for ABC_FP32, 4k for ABC_BF16_RESCORE).
+//
+// A pilot pass of the same kernel over every 16th draw (a strided TMA tensor
+// map) first finds each voxel's r-th smallest key, r = 1.5 kt / 16; as draws are
+// i.i.d. within each model, about 1.5 kt of all N draws fall below it, so the
+// main pass starts from that threshold, appends ~1.5 kt candidates per voxel and
+// normally never compacts.  Nothing relies on the prediction for correctness:
+// the list always holds every draw below its voxel's threshold.
+//
+// Kernel `k_finalize` (one warp per voxel) re-scores the net exactly as
+// sum_l w_l (y_l - x_l)^2 in fp32, selects the exact k-th distance d_k, and
+// certifies the result: with E bounding |computed d' - exact d'| for any draw
+// that could beat d_k (its ||xh|| <= ||yh|| + sqrt(d_k)), every draw outside
+// the net has computed key > T_out, so none can beat d_k when
+// T_out >= d_k - ||yh||^2 + E.  ABC_FP32 resolves an uncertified voxel by an
+// exact fp32 scan of all draws, which makes its accepted set the exact fp32
+// top-k; ABC_BF16_RESCORE counts uncertified voxels (abc_topk_status).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -47,6 +60,7 @@ constexpr int KBLK_BYTES = BM * KBLK * 2;   // 16 KB (BM == BN)
 constexpr int TC_THREADS = 192;
 constexpr uint64_t WAIT_NS = 2000000000ull; // 2 s bound on any barrier wait
 constexpr int MAXL = 64;
+constexpr int PILOT_STRIDE = 16;
 
 struct Weights {
     float w[MAXL];
@@ -55,10 +69,12 @@ struct Weights {
 
 struct Layout {
     int mode;          // ABC_FP32 / ABC_BF16_RESCORE
-    int L, k, Kp, nkb, C, kt, cap, sortcap;
+    int L, k, Kp, nkb, C, kt, cap, sortcap, r;
+    int64_t Ns;
+    bool pilot;
     int64_t J, N, Jp, Np;
     int npart;
-    size_t off_mu, off_part, off_ynorm, off_a, off_b, off_keys, off_idx, off_cnt, off_status, total;
+    size_t off_mu, off_part, off_ynorm, off_a, off_b, off_keys, off_idx, off_cnt, off_thr, off_thr0, off_status, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -80,9 +96,15 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode) {
     const int kcols = mode == ABC_FP32 ? 3 * L + 3 : L + 3;
     s.Kp = (int)vpet_round_up(kcols, KBLK);
     s.nkb = s.Kp / KBLK;
-    s.kt = mode == ABC_FP32 ? k : (int)((int64_t)4 * k < N ? 4 * k : N);
+    const int64_t net = (int64_t)(mode == ABC_FP32 ? 2 : 4) * k;
+    s.kt = (int)(net < N ? net : N);
     s.cap = s.kt + (s.kt / 4 > 64 ? s.kt / 4 : 64);
-    s.C = (int)vpet_round_up((int64_t)s.cap + (s.cap > 512 ? s.cap : 512), 32);
+    // pilot: the r-th smallest key over every 16th draw predicts the 1.5 kt-th
+    // smallest over all draws (draws are i.i.d. within each model)
+    s.r = (int)((3 * (int64_t)s.kt + 31) / 32);
+    s.Ns = N / PILOT_STRIDE;
+    s.pilot = s.Ns >= 8 * (int64_t)s.r && s.Ns >= 4 * BN;
+    s.C = (int)vpet_round_up(3 * (int64_t)s.kt + 2 * BN, 32);
     s.sortcap = next_pow2(2 * k);
     if (s.sortcap < 64) s.sortcap = 64;
     s.Jp = vpet_round_up(J > 0 ? J : 1, BM);
@@ -99,6 +121,8 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode) {
     s.off_keys = o; o = align256(o + (size_t)J * s.C * sizeof(float));
     s.off_idx = o; o = align256(o + (size_t)J * s.C * sizeof(int32_t));
     s.off_cnt = o; o = align256(o + (size_t)s.Jp * sizeof(int32_t));
+    s.off_thr = o; o = align256(o + (size_t)s.Jp * sizeof(float));
+    s.off_thr0 = o; o = align256(o + (size_t)s.Jp * sizeof(float));
     s.total = o;
     return s;
 }
@@ -220,41 +244,33 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
 // ------------------------------------------------------------------ fused GEMM + filter
 struct TcParams {
     int64_t J, N;
-    int ntiles, C, kt, cap, mode;
-    float cE;                    // error-bound coefficient (ABC_FP32)
-    const float* ynorm;
+    int ntiles, C, kt, cap;
+    int lim;                     // a list is compacted once it could exceed lim entries (lim <= C)
     float* keys;
     int32_t* idx;
     int32_t* cnt;
+    float* thr;                  // final running threshold per voxel
+    const float* thr0;           // initial threshold per voxel (pilot), or null = +huge
     int32_t* status;
     float* dump;                 // debug probe: raw keys, Jp x Np (nullptr in production)
     int64_t ld_dump;
 };
 
-// Bound on |computed d' - exact d'| for draws that can still be in the top-k,
-// given the current k-th key tk (d' units) and ||yh||^2.
-__device__ __forceinline__ float margin(float tk, float yn, float cE) {
-    const float dk = fmaxf(tk + yn, 0.0f) * 1.001f;
-    const float ry = sqrtf(yn);
-    const float R = ry + sqrtf(dk) + 1e-30f;
-    return cE * (2.0f * ry * R + R * R);
-}
+constexpr int STAGE_LD = 36;     // floats per staged row (16-byte aligned, conflict-free)
 
-// Tightens voxel j's candidate list; returns the new threshold, updates cnt.
-__device__ __forceinline__ float compact_list(const TcParams& P, int64_t j, int& cnt, float yn, uint32_t* hist,
-                                              int lane) {
+// Bound on |computed d' - exact d'| for any draw with ||xh|| <= R.
+__device__ __forceinline__ float err_bound(float cE, float ry, float R) { return cE * (2.0f * ry * R + R * R); }
+
+// Tightens voxel j's candidate list to the keys <= its kt-th key; returns the new
+// threshold and updates cnt.
+__device__ __forceinline__ float compact_list(const TcParams& P, int64_t j, int& cnt, uint32_t* hist, int lane) {
     float* kj = P.keys + j * P.C;
     int32_t* ij = P.idx + j * P.C;
     const uint32_t T = warp_select(kj, cnt, P.kt - 1, 3, hist, lane);
-    uint32_t Tk = T;
-    if (P.mode == ABC_FP32) {
-        const float tf = key2f(T);
-        Tk = f2key(tf + 2.0f * margin(tf, yn, P.cE));
-    }
-    const int q = warp_compact(kj, ij, cnt, Tk, P.cap, lane);
+    const int q = warp_compact(kj, ij, cnt, T, P.cap, lane);
     cnt = q < P.cap ? q : P.cap;
-    if (q > P.cap && lane == 0) atomicOr(&P.cnt[j], 0x40000000);   // overflow flag for this voxel
-    return key2f(Tk);
+    if (q > P.cap && lane == 0) atomicOr(&P.cnt[j], 0x40000000);   // overflow: resolved by an exact scan
+    return key2f(T);
 }
 
 __device__ __forceinline__ float min32(const float (&v)[32]) {
@@ -270,6 +286,42 @@ __device__ __forceinline__ float min32(const float (&v)[32]) {
     return fminf(fminf(b, c), d);
 }
 
+// One 32-column chunk of the epilogue: filter, then warp-cooperative appends.
+__device__ __forceinline__ void epilogue_chunk(const TcParams& P, float (&v)[32], int64_t n0, int64_t jbase,
+                                               float thr, int& cnt, float* stage, int lane) {
+    if (n0 + 32 > P.N) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (n0 + i >= P.N) v[i] = __int_as_float(0x7F800000);   // +inf: never kept
+    }
+    const bool slow = min32(v) <= thr;
+    uint32_t bal = __ballot_sync(0xFFFFFFFFu, slow);
+    if (!bal) return;
+    if (slow) {
+        float4* dst = (float4*)(stage + lane * STAGE_LD);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+    __syncwarp();
+    const uint32_t lt = (1u << lane) - 1u;
+    while (bal) {
+        const int s = __ffs(bal) - 1;
+        bal &= bal - 1;
+        const float val = stage[s * STAGE_LD + lane];
+        const float ts = __shfl_sync(0xFFFFFFFFu, thr, s);
+        const int cs = __shfl_sync(0xFFFFFFFFu, cnt, s);
+        const bool pass = val <= ts;
+        const uint32_t pb = __ballot_sync(0xFFFFFFFFu, pass);
+        if (pass) {
+            const int64_t at = (jbase + s) * (int64_t)P.C + cs + __popc(pb & lt);
+            P.keys[at] = val;
+            P.idx[at] = (int32_t)(n0 + lane);
+        }
+        if (lane == s) cnt += __popc(pb);
+    }
+    __syncwarp();
+}
+
 template <int NKB, int STAGES, bool DUMP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams P) {
@@ -277,7 +329,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;                                        // NKB x 16 KB
     uint8_t* sB = smem + NKB * KBLK_BYTES;                     // STAGES x NKB x 16 KB
-    uint64_t* bars = (uint64_t*)(sB + STAGES * NKB * KBLK_BYTES);
+    float* sStage = (float*)(sB + STAGES * NKB * KBLK_BYTES);  // 4 warps x 32 x STAGE_LD
+    uint32_t* hist = (uint32_t*)(sStage + 4 * 32 * STAGE_LD);  // 4 warps x 256
+    uint64_t* bars = (uint64_t*)(hist + 4 * 256);
     uint64_t* full = bars;                  // [STAGES]
     uint64_t* empty = bars + STAGES;        // [STAGES]
     uint64_t* tfull = bars + 2 * STAGES;    // [2]
@@ -285,7 +339,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint64_t* afull = bars + 2 * STAGES + 4;
     uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 5);
     volatile int* s_err = (volatile int*)(tmem_holder + 1);
-    uint32_t* hist = (uint32_t*)(bars + 2 * STAGES + 8);      // 4 warps x 256
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t m0 = (int64_t)blockIdx.x * BM;
@@ -371,14 +424,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- epilogue: warps 2..5, thread <-> voxel
         const int q = warp & 3;                          // TMEM lane quadrant of this warp
         const int row = q * 32 + lane;
-        const int64_t j = m0 + row;
+        const int64_t jbase = m0 + q * 32;
+        const int64_t j = jbase + lane;
         const bool valid = j < P.J;
         uint32_t* whist = hist + (warp - 2) * 256;
-        float thr = valid ? 3.0e38f : -3.0e38f;
+        float* stage = sStage + (warp - 2) * 32 * STAGE_LD;
+        float thr = valid ? (P.thr0 ? P.thr0[j] : 3.0e38f) : -3.0e38f;
         int cnt = 0;
-        const float yn = valid ? P.ynorm[j] : 0.0f;
-        float* kj = P.keys + (valid ? j : 0) * (int64_t)P.C;
-        int32_t* ij = P.idx + (valid ? j : 0) * (int64_t)P.C;
         for (int t = 0; t < ntiles; ++t) {
             const int acc = t & 1;
             const uint32_t aph = (uint32_t)(t >> 1) & 1u;
@@ -387,49 +439,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ptx::tc_fence_after();
             const int64_t nbase = (int64_t)t * BN;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                float v[32];
-                ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32), v);
-                const int64_t n0 = nbase + c * 32;
+            for (int h = 0; h < BN / 64; ++h) {
+                uint32_t r0[32], r1[32];
+                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + h * 64);
+                ptx::tmem_ld32_async(ta, r0);
+                ptx::tmem_ld32_async(ta + 32, r1);
+                ptx::tmem_wait_ld();
+                ptx::tmem_fence_regs(r0);
+                ptx::tmem_fence_regs(r1);
+                float v0[32], v1[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) { v0[i] = __uint_as_float(r0[i]); v1[i] = __uint_as_float(r1[i]); }
                 if (DUMP) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) P.dump[(m0 + row) * P.ld_dump + n0 + i] = v[i];
+                    for (int i = 0; i < 32; ++i) {
+                        P.dump[(m0 + row) * P.ld_dump + nbase + h * 64 + i] = v0[i];
+                        P.dump[(m0 + row) * P.ld_dump + nbase + h * 64 + 32 + i] = v1[i];
+                    }
                     continue;
                 }
-                if (n0 + 32 > P.N) {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (n0 + i >= P.N) v[i] = __int_as_float(0x7F800000);   // +inf: never kept
-                }
-                if (min32(v) <= thr) {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        if (v[i] <= thr) {
-                            kj[cnt] = v[i];
-                            ij[cnt] = (int32_t)(n0 + i);
-                            ++cnt;
-                        }
-                    }
-                }
+                epilogue_chunk(P, v0, nbase + h * 64, jbase, thr, cnt, stage, lane);
+                epilogue_chunk(P, v1, nbase + h * 64 + 32, jbase, thr, cnt, stage, lane);
             }
             ptx::tc_fence_before();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&tempty[acc]));
+            if (DUMP) continue;
             // compaction of lists that might not fit the next tile
-            uint32_t need = __ballot_sync(0xFFFFFFFFu, valid && cnt > P.C - BN);
+            uint32_t need = __ballot_sync(0xFFFFFFFFu, valid && cnt > P.lim - BN);
             while (need) {
                 const int src = __ffs(need) - 1;
                 need &= need - 1;
                 int c2 = __shfl_sync(0xFFFFFFFFu, cnt, src);
-                const float yn2 = __shfl_sync(0xFFFFFFFFu, yn, src);
-                const float nt = compact_list(P, m0 + q * 32 + src, c2, yn2, whist, lane);
+                const float nt = compact_list(P, jbase + src, c2, whist, lane);
                 if (lane == src) {
                     cnt = c2;
                     thr = nt;
                 }
             }
         }
-        if (valid && !DUMP) atomicOr(&P.cnt[j], cnt);   // cnt[] was zeroed; keeps the overflow bit
+        if (valid && !DUMP) {
+            atomicOr(&P.cnt[j], cnt);      // cnt[] was zeroed; keeps the overflow bit
+            P.thr[j] = thr;
+        }
     }
 
     ptx::tc_fence_before();
@@ -441,9 +493,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (threadIdx.x == 0 && *s_err) atomicExch(&P.status[0], ABC_ERR_TIMEOUT);
 }
 
+// Pilot threshold: the r-th smallest key of each voxel's pilot list, then the
+// list is emptied for the main pass.
+__global__ void k_pilot_threshold(float* keys, int32_t* cnt, int C, int r, int64_t J, float* thr0) {
+    __shared__ uint32_t hist[8][256];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * 8 + wid;
+    if (j >= J) return;
+    const int c = cnt[j] & 0x3FFFFFFF;
+    float t = 3.0e38f;
+    if (!(cnt[j] & 0x40000000) && c >= r) t = key2f(warp_select(keys + j * C, c, r - 1, 3, hist[wid], lane));
+    if (lane == 0) {
+        thr0[j] = t;
+        cnt[j] = 0;
+    }
+}
+
 // ------------------------------------------------------------------ finalize
 struct FinParams {
-    int64_t J;
+    int64_t J, N;
     int L, k, C, kt, mode, sortcap;
     float cE;
     const float* y;
@@ -454,11 +522,33 @@ struct FinParams {
     float* keys;
     int32_t* idx;
     int32_t* cnt;
+    const float* thr;
     int32_t* status;
     int32_t* out_idx;
     float* out_dist;
 };
 
+// Exact fp32 distance sum_l w_l (y_l - x_l)^2 in a fixed order (y in shared memory).
+__device__ __forceinline__ float exact_dist(const float* ys, const float* x, int L, const Weights& W) {
+    const float4* xr = (const float4*)x;
+    float d = 0.0f;
+    int l = 0;
+    for (; l + 4 <= L; l += 4) {
+        const float4 xv = __ldg(xr + (l >> 2));
+        const float e0 = ys[l] - xv.x, e1 = ys[l + 1] - xv.y, e2 = ys[l + 2] - xv.z, e3 = ys[l + 3] - xv.w;
+        d = fmaf(W.w[l] * e0, e0, d);
+        d = fmaf(W.w[l + 1] * e1, e1, d);
+        d = fmaf(W.w[l + 2] * e2, e2, d);
+        d = fmaf(W.w[l + 3] * e3, e3, d);
+    }
+    for (; l < L; ++l) {
+        const float e = ys[l] - x[l];
+        d = fmaf(W.w[l] * e, e, d);
+    }
+    return d;
+}
+
+// status[1]: voxels resolved by the exact scan; [2]: tie overflow; [3]: uncertified (bf16 mode)
 __global__ void k_finalize(FinParams P, Weights W) {
     extern __shared__ __align__(16) uint8_t fsm[];
     const int warps = blockDim.x >> 5;
@@ -472,47 +562,72 @@ __global__ void k_finalize(FinParams P, Weights W) {
     int32_t* ij = P.idx + j * P.C;
     const int raw = P.cnt[j];
     int cnt = raw & 0x3FFFFFFF;
-    if ((raw & 0x40000000) && lane == 0) atomicAdd(&P.status[1], 1);
-    // 1. the candidate net: approximate keys up to the kt-th (+ margin)
-    if (cnt > P.kt) {
-        const uint32_t T = warp_select(kj, cnt, P.kt - 1, 3, hist, lane);
-        uint32_t Tk = T;
-        if (P.mode == ABC_FP32) {
-            const float tf = key2f(T);
-            Tk = f2key(tf + 2.0f * margin(tf, P.ynorm[j], P.cE));
-        }
-        cnt = warp_compact(kj, ij, cnt, Tk, P.C, lane);
-    }
-    // 2. exact fp32 re-score: sum_l w_l (y_l - x_l)^2
     for (int l = lane; l < P.L; l += 32) ys[l] = P.y[j * P.ldy + l];
     __syncwarp();
-    for (int i = lane; i < cnt; i += 32) {
-        const float4* xr = (const float4*)(P.x + (int64_t)ij[i] * P.ldx);
-        float d = 0.0f;
-        int l = 0;
-        for (; l + 4 <= P.L; l += 4) {
-            const float4 xv = __ldg(xr + (l >> 2));
-            const float e0 = ys[l] - xv.x, e1 = ys[l + 1] - xv.y, e2 = ys[l + 2] - xv.z, e3 = ys[l + 3] - xv.w;
-            d = fmaf(W.w[l] * e0, e0, d);
-            d = fmaf(W.w[l + 1] * e1, e1, d);
-            d = fmaf(W.w[l + 2] * e2, e2, d);
-            d = fmaf(W.w[l + 3] * e3, e3, d);
+    bool scan = (raw & 0x40000000) != 0;
+    uint32_t K = 0;
+    if (!scan) {
+        // 1. the net: every draw outside it has computed key > T_out
+        float T_out = P.thr[j];
+        if (P.mode != ABC_FP32 && cnt > P.kt) {
+            const uint32_t T = warp_select(kj, cnt, P.kt - 1, 3, hist, lane);
+            cnt = warp_compact(kj, ij, cnt, T, P.C, lane);
+            T_out = key2f(T);
         }
-        for (; l < P.L; ++l) {
-            const float e = ys[l] - P.x[(int64_t)ij[i] * P.ldx + l];
-            d = fmaf(W.w[l] * e, e, d);
+        // 2. exact fp32 re-score of the net
+        for (int i = lane; i < cnt; i += 32) kj[i] = exact_dist(ys, P.x + (int64_t)ij[i] * P.ldx, P.L, W);
+        __syncwarp();
+        // 3. exact k-th distance and the certificate
+        bool cert = false;
+        if (cnt >= P.k) {
+            K = warp_select(kj, cnt, P.k - 1, 4, hist, lane);
+            const float dk = key2f(K);
+            const float yn = P.ynorm[j];
+            const float slack = 4.0f * (float)P.L * 0x1p-24f;
+            const float ry = sqrtf(yn);
+            const float R = ry + sqrtf(dk * (1.0f + slack)) + 1e-30f;
+            const float need = dk * (1.0f + slack) - yn * (1.0f - slack) + err_bound(P.cE, ry, R);
+            cert = T_out >= 2.9e38f || T_out >= need;
         }
-        kj[i] = d;
+        if (!cert) {
+            if (P.mode == ABC_FP32) scan = true;
+            else if (lane == 0) atomicAdd(&P.status[3], 1);
+        }
+        if (!scan && cnt < P.k) K = 0xFFFFFFFFu;
     }
-    __syncwarp();
-    // 3. exact k-th distance, keep everything at or below it (ties resolved by index below)
+    if (scan) {
+        // exact fp32 scan of every draw (candidate list rebuilt with exact keys)
+        if (lane == 0) atomicAdd(&P.status[1], 1);
+        cnt = 0;
+        float thr = __int_as_float(0x7F800000);
+        for (int64_t base = 0; base < P.N; base += 32) {
+            const int64_t n = base + lane;
+            const float d = n < P.N ? exact_dist(ys, P.x + n * P.ldx, P.L, W) : __int_as_float(0x7F800000);
+            const bool take = n < P.N && d <= thr;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
+            if (take) {
+                const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+                kj[pos] = d;
+                ij[pos] = (int32_t)n;
+            }
+            cnt += __popc(bal);
+            if (cnt > P.C - 32) {
+                __syncwarp();
+                const uint32_t T = warp_select(kj, cnt, P.k - 1, 4, hist, lane);
+                const int q = warp_compact(kj, ij, cnt, T, P.C - 64, lane);
+                cnt = q < P.C - 64 ? q : P.C - 64;
+                thr = key2f(T);
+            }
+        }
+        __syncwarp();
+        K = cnt >= P.k ? warp_select(kj, cnt, P.k - 1, 4, hist, lane) : 0xFFFFFFFFu;
+    }
+    // 4. keep everything at or below the exact k-th distance, sort by (distance, index)
     if (cnt > P.k) {
-        const uint32_t K = warp_select(kj, cnt, P.k - 1, 4, hist, lane);
         const int g = warp_compact(kj, ij, cnt, K, P.sortcap, lane);
-        if (g > P.sortcap && lane == 0) atomicAdd(&P.status[1], 1);
+        if (g > P.sortcap && lane == 0) atomicAdd(&P.status[2], 1);
         cnt = g < P.sortcap ? g : P.sortcap;
     }
-    // 4. sort (distance, index) and emit the first k
     int n2 = 32;
     while (n2 < cnt) n2 <<= 1;
     for (int i = lane; i < n2; i += 32)
@@ -542,9 +657,9 @@ int get_encoder() {
     return ABC_OK;
 }
 
-int make_tmap(CUtensorMap* m, void* base, int64_t rows, int Kp) {
+int make_tmap(CUtensorMap* m, void* base, int64_t rows, int Kp, int row_step = 1) {
     const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2 * row_step};
     const cuuint32_t box[2] = {(cuuint32_t)KBLK, (cuuint32_t)BM};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
@@ -558,11 +673,12 @@ int make_tmap(CUtensorMap* m, void* base, int64_t rows, int Kp) {
 }
 
 template <int NKB>
-constexpr int stages_for() { return NKB == 1 ? 5 : (NKB == 2 ? 4 : 3); }
+constexpr int stages_for() { return NKB == 1 ? 4 : (NKB == 2 ? 4 : 3); }
 
 template <int NKB>
 size_t tc_smem_bytes() {
-    return 1024 + (size_t)NKB * KBLK_BYTES * (1 + stages_for<NKB>()) + (2 * stages_for<NKB>() + 8) * 8 + 4 * 256 * 4;
+    return 1024 + (size_t)NKB * KBLK_BYTES * (1 + stages_for<NKB>()) + 4 * 32 * STAGE_LD * 4 + 4 * 256 * 4 +
+           (2 * stages_for<NKB>() + 8) * 8;
 }
 
 template <int NKB, bool DUMP>
@@ -593,10 +709,14 @@ int dispatch_tc(int nkb, const CUtensorMap& ta, const CUtensorMap& tb, const TcP
 }
 
 float error_coef(const Layout& lay) {
-    // |d' error| <= cE (2 ||yh|| R + R^2): split representation 3 * 2^-16 per
-    // product (bf16 hi + lo of each operand), fp32 accumulation over the
-    // 3 Kp products and the fp32 norm, doubled for safety.
-    return 2.0f * (3.0f * 0x1p-16f + (float)(3 * lay.Kp + lay.L + 16) * 0x1p-24f);
+    // |d' error| <= cE (2 ||yh|| R + R^2) for a draw with ||xh|| <= R.
+    //  ABC_FP32: bf16 hi + lo of each operand leaves |a - a_hi - a_lo| <= 2^-16 |a|,
+    //   |a_lo| <= 2^-8 |a|, so the three products miss at most 3 * 2^-16 |a b|;
+    //  ABC_BF16_RESCORE: one rounding of each operand and of the norm, 2^-8 each.
+    // Both add fp32 accumulation over Kp terms, the fp32 norm and the fp32
+    // centring / scaling of the operands.
+    const float split = lay.mode == ABC_FP32 ? 3.0f * 0x1p-16f : 3.0f * 0x1p-8f;
+    return split + (float)(3 * lay.Kp + lay.L + 16) * 0x1p-24f;
 }
 
 int validate(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w, int k,
@@ -662,31 +782,48 @@ int run_topk(const float* y, int64_t J, int ldy, const float* x, int64_t N, int 
     P.N = N;
     P.ntiles = (int)(lay.Np / BN);
     P.C = lay.C;
+    P.lim = lay.C;
     P.kt = lay.kt;
     P.cap = lay.cap;
-    P.mode = mode;
-    P.cE = error_coef(lay);
-    P.ynorm = ynorm;
     P.keys = (float*)(base + lay.off_keys);
     P.idx = (int32_t*)(base + lay.off_idx);
     P.cnt = cnt;
+    P.thr = (float*)(base + lay.off_thr);
     P.status = status;
     P.dump = dump;
     P.ld_dump = ld_dump;
     const int64_t grid = lay.Jp / BM;
     if (dump) return dispatch_tc<true>(lay.nkb, ta, tb, P, grid, s);
+    P.thr0 = nullptr;
+    if (lay.pilot) {
+        // pilot pass over every 16th draw (strided tensor map, no copy)
+        CUtensorMap tp;
+        if ((rc = make_tmap(&tp, B, lay.Ns, lay.Kp, PILOT_STRIDE))) return rc;
+        TcParams Q = P;
+        Q.N = lay.Ns;
+        Q.ntiles = (int)vpet_ceil_div(lay.Ns, BN);
+        Q.kt = lay.r;
+        Q.cap = lay.r + (lay.r / 4 > 64 ? lay.r / 4 : 64);
+        Q.lim = (int)(4 * (int64_t)lay.r + 2 * BN < lay.C ? 4 * (int64_t)lay.r + 2 * BN : lay.C);
+        if ((rc = dispatch_tc<false>(lay.nkb, ta, tp, Q, grid, s))) return rc;
+        float* thr0 = (float*)(base + lay.off_thr0);
+        k_pilot_threshold<<<(unsigned)vpet_ceil_div(J, 8), 256, 0, s>>>(P.keys, cnt, lay.C, lay.r, J, thr0);
+        VPET_LAUNCH_CHECK();
+        P.thr0 = thr0;
+    }
     if (g_prof_start) VPET_CUDA(cudaEventRecord(g_prof_start, s));
     if ((rc = dispatch_tc<false>(lay.nkb, ta, tb, P, grid, s))) return rc;
     if (g_prof_stop) VPET_CUDA(cudaEventRecord(g_prof_stop, s));
     FinParams F;
     F.J = J;
+    F.N = N;
     F.L = L;
     F.k = k;
     F.C = lay.C;
     F.kt = lay.kt;
     F.mode = mode;
     F.sortcap = lay.sortcap;
-    F.cE = P.cE;
+    F.cE = error_coef(lay);
     F.y = y;
     F.ldy = ldy;
     F.x = x;
@@ -695,6 +832,7 @@ int run_topk(const float* y, int64_t J, int ldy, const float* x, int64_t N, int 
     F.keys = P.keys;
     F.idx = P.idx;
     F.cnt = cnt;
+    F.thr = P.thr;
     F.status = status;
     F.out_idx = out_idx;
     F.out_dist = out_dist;
@@ -737,14 +875,16 @@ extern "C" int abc_profile_events(void* start_event, void* stop_event) {
     return ABC_OK;
 }
 
-extern "C" int abc_topk_status(const void* workspace, int32_t status_host[2], void* stream) {
+extern "C" int abc_topk_status(const void* workspace, int32_t status_host[4], void* stream) {
     vpet::clear_error();
     VPET_ARG(workspace && status_host, "abc_topk_status: null pointer");
-    int32_t st[2];
+    int32_t st[4];
     VPET_CUDA(cudaMemcpyAsync(st, workspace, sizeof st, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     VPET_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     status_host[0] = st[0];
     status_host[1] = st[1];
+    status_host[2] = st[2];
+    status_host[3] = st[3];
     return ABC_OK;
 }
 

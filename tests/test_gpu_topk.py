@@ -44,6 +44,7 @@ def _compare(orc, W, y, x, k, prec, tau_extra=0.0):
     ws = api.alloc_workspace(W.J, x.shape[0], L, k, prec)
     idx, dist = api.discrepancy_topk(y, x, L, w, k, prec, ws)
     st = api.topk_status(ws)
+    assert st[0] == 0 and st[2] == 0, f"status {st}"
     idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
     yn, xn = y.cpu().numpy()[:, :L], x.cpu().numpy()[:, :L].astype(np.float64)
     oi, od = orc.topk(yn, xn, w.astype(np.float64), k)
@@ -54,14 +55,13 @@ def _compare(orc, W, y, x, k, prec, tau_extra=0.0):
     assert np.all(np.abs(dist - ref) <= 4 * L * 2.0**-24 * ref + 1e-30)
     # sorted ascending by (distance, index)
     assert np.all((np.diff(dist, axis=1) > 0) | ((np.diff(dist, axis=1) == 0) & (np.diff(idx, axis=1) > 0)))
-    assert st == (0, 0), f"status {st}"
-    return swaps, worst
+    return swaps, worst, st[1]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_topk_brain_2tcm_small(orc, prec):
     W, y, x = _gpu_case("brain_fdg_2tcm", 300, 5000, orc)          # 3 voxel tiles (ragged), 40 draw tiles (ragged)
-    swaps, worst = _compare(orc, W, y, x, 100, prec)
+    swaps, worst, fallback = _compare(orc, W, y, x, 100, prec)
     assert swaps <= 3
 
 
@@ -125,10 +125,11 @@ def test_argument_errors():
     y = torch.zeros((4, 24), device="cuda")
     x = torch.zeros((10, 24), device="cuda")
     w = np.ones(22, np.float32)
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
     with pytest.raises(AbcError):
-        api.discrepancy_topk(y, x, 22, w, 11, 0)          # k > N
+        api.discrepancy_topk(y, x, 22, w, 11, 0, workspace=ws)          # k > N
     with pytest.raises(AbcError):
-        api.discrepancy_topk(y, x, 22, -w, 3, 0)          # negative weights
+        api.discrepancy_topk(y, x, 22, -w, 3, 0, workspace=ws)          # negative weights
     ws = torch.empty(16, dtype=torch.uint8, device="cuda")
     with pytest.raises(AbcError) as e:
         api.discrepancy_topk(y, x, 22, w, 3, 0, workspace=ws)
