@@ -125,6 +125,28 @@ int abc_discrepancy_topk(const float* y_dev, int64_t J, int32_t ldy, const float
                          int32_t L, const float* w_host, int32_t k, int32_t precision, void* workspace,
                          size_t ws_bytes, int32_t* idx_dev, float* dist_dev, void* stream);
 
+/* Allocation-free variant of abc_discrepancy_topk.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory themselves (a host framework that owns the whole device-memory
+ * budget, a real-time pipeline that forbids allocation once running, a plugin
+ * handed only its input and output buffers).  Same computation, arguments and
+ * outputs as abc_discrepancy_topk, but the scratch memory is a fixed 64 MiB
+ * device array inside this library (held on every GPU that loads the library
+ * until the process exits); the call allocates nothing.
+ *  - Sizes whose abc_workspace_size() exceeds 64 MiB are rejected with
+ *    ABC_ERR_UNSUPPORTED (e.g. 2,048 voxels x 50,000 draws x 22 frames, k = 100,
+ *    fits in either precision).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array, which keeps the previous call's contents
+ *    (the call clears what must start at zero).  Calls that overlap on the GPU
+ *    (concurrent streams, or several host threads) race on it: serialise them.
+ *  - abc_topk_status is not available for this variant. */
+int abc_discrepancy_topk_noalloc(const float* y_dev, int64_t J, int32_t ldy, const float* x_dev, int64_t N,
+                                 int32_t ldx, int32_t L, const float* w_host, int32_t k, int32_t precision,
+                                 int32_t* idx_dev, float* dist_dev, void* stream);
+
 /* Status of the last abc_discrepancy_topk that used this workspace.  Blocks
  * on `stream`.  Writes
  *   status[0] = ABC_OK or ABC_ERR_TIMEOUT (a bounded device wait ran out; the

@@ -25,7 +25,7 @@ ABC_FP32, ABC_BF16_RESCORE = 0, 1
 EXPORTS = [
     "abc_feng_input", "abc_sample_prior", "abc_simulate", "abc_workspace_size", "abc_discrepancy_topk",
     "abc_topk_status", "abc_model_select", "abc_summarize", "abc_last_error", "abc_profile_events",
-    "abc_debug_gemm_keys",
+    "abc_debug_gemm_keys", "abc_discrepancy_topk_noalloc",
 ]
 
 
@@ -66,9 +66,11 @@ def lib():
     L.abc_summarize.argtypes = [P, i32, P, i32, P, P, P, P, i64, i32, P, i32, P, P, P, P, P]
     L.abc_last_error.restype = ctypes.c_char_p
     L.abc_profile_events.argtypes = [P, P]
+    L.abc_discrepancy_topk_noalloc.argtypes = [P, i64, i32, P, i64, i32, i32, P, i32, i32, P, P, P]
     L.abc_debug_gemm_keys.argtypes = [P, i64, i32, P, i64, i32, i32, P, i32, P, sz, P, i64, P]
     for fn in ["abc_feng_input", "abc_sample_prior", "abc_simulate", "abc_discrepancy_topk", "abc_topk_status",
-               "abc_model_select", "abc_summarize", "abc_debug_gemm_keys", "abc_profile_events"]:
+               "abc_model_select", "abc_summarize", "abc_debug_gemm_keys", "abc_profile_events",
+               "abc_discrepancy_topk_noalloc"]:
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L

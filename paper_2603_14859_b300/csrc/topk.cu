@@ -851,6 +851,21 @@ int run_topk(const float* y, int64_t J, int ldy, const float* x, int64_t N, int 
 
 }  // namespace
 
+namespace vpet {
+
+size_t topk_workspace_bytes(int64_t J, int64_t N, int L, int k, int precision) {
+    return make_layout(J, N, L, k, precision).total;
+}
+
+int topk_on_workspace(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w,
+                      int k, int precision, void* ws, size_t ws_bytes, int32_t* idx, float* dist, cudaStream_t s) {
+    const int rc = validate(y, J, ldy, x, N, ldx, L, w, k, precision);
+    if (rc) return rc;
+    return run_topk(y, J, ldy, x, N, ldx, L, w, k, precision, ws, ws_bytes, idx, dist, nullptr, 0, s);
+}
+
+}  // namespace vpet
+
 extern "C" size_t abc_workspace_size(int64_t J, int64_t N, int32_t L, int32_t k, int32_t precision) {
     if (J < 1 || N < 1 || L < 1 || L > 61 || k < 1 || k > N || k > 2048) return 0;
     if (precision != ABC_FP32 && precision != ABC_BF16_RESCORE) return 0;
