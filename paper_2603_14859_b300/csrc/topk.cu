@@ -25,12 +25,14 @@
 // threshold, so each list always holds every draw whose key is at most the
 // kt-th smallest seen (the "net": kt = 2k for ABC_FP32, 4k for ABC_BF16_RESCORE).
 //
-// A pilot pass of the same kernel over every 16th draw (a strided TMA tensor
-// map) first finds each voxel's r-th smallest key, r = 1.5 kt / 16; as draws are
-// i.i.d. within each model, about 1.5 kt of all N draws fall below it, so the
-// main pass starts from that threshold, appends ~1.5 kt candidates per voxel and
-// normally never compacts.  Nothing relies on the prediction for correctness:
-// the list always holds every draw below its voxel's threshold.
+// Pilot passes of the same kernel over every 16th (then 256th, ...) draw (a
+// strided TMA tensor map) first find each voxel's r-th smallest key,
+// r = 1.5 kt / 16; as draws are i.i.d. within each model, about 1.5 kt of all N
+// draws fall below it, so the main pass starts from that threshold, appends
+// ~1.5 kt candidates per voxel and normally never compacts.  Each pilot starts
+// from the next coarser pilot's threshold in the same way.  Nothing relies on
+// the prediction for correctness: a list always holds every draw below its
+// voxel's threshold.
 //
 // Kernel `k_finalize` (one warp per voxel) re-scores the net exactly as
 // sum_l w_l (y_l - x_l)^2 in fp32, selects the exact k-th distance d_k, and
@@ -61,6 +63,7 @@ constexpr int TC_THREADS = 192;
 constexpr uint64_t WAIT_NS = 2000000000ull; // 2 s bound on any barrier wait
 constexpr int MAXL = 64;
 constexpr int PILOT_STRIDE = 16;
+constexpr int MAX_PILOT_LEVELS = 4;
 
 struct Weights {
     float w[MAXL];
@@ -69,9 +72,10 @@ struct Weights {
 
 struct Layout {
     int mode;          // ABC_FP32 / ABC_BF16_RESCORE
-    int L, k, Kp, nkb, C, kt, cap, sortcap, r;
-    int64_t Ns;
-    bool pilot;
+    int L, k, Kp, nkb, C, kt, cap, sortcap;
+    int nlev;                          // pilot levels (finest first)
+    int lev_rank[4];
+    int64_t lev_stride[4];
     int64_t J, N, Jp, Np;
     int npart;
     size_t off_mu, off_part, off_ynorm, off_a, off_b, off_keys, off_idx, off_cnt, off_thr, off_thr0, off_status, total;
@@ -101,11 +105,31 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode) {
     s.cap = s.kt + (s.kt / 4 > 64 ? s.kt / 4 : 64);
     // pilot: the r-th smallest key over every 16th draw predicts the 1.5 kt-th
     // smallest over all draws (draws are i.i.d. within each model)
-    s.r = (int)((3 * (int64_t)s.kt + 31) / 32);
-    s.Ns = N / PILOT_STRIDE;
-    s.pilot = s.Ns >= 8 * (int64_t)s.r && s.Ns >= 4 * BN;
+    // Levels of pilots: level i uses every 16^i-th draw and a target rank
+    // r_i = ceil(f r_{i-1} / 16), r_0 = kt; each starts from the next coarser
+    // level's threshold.  f = 1.5 predicts 1.5 r_{i-1} draws below the
+    // threshold at the finer level; for a small r_i the rank statistic is noisy
+    // (relative sd ~ 1 / sqrt(r_i)), so f grows until an under-prediction is
+    // more than ~4 sd away.
+    s.nlev = 0;
+    int64_t rr = s.kt, stride = 1;
+    while (s.nlev < MAX_PILOT_LEVELS) {
+        int64_t r_next = (3 * rr + 31) / 32;
+        for (int it = 0; it < 8; ++it) {
+            const double f = (double)r_next * PILOT_STRIDE / (double)rr;       // predicted count / needed
+            if (1.0 - 1.0 / f >= 4.0 / sqrt((double)r_next)) break;
+            r_next = r_next + r_next / 2 + 1;
+        }
+        const int64_t n_next = N / (stride * PILOT_STRIDE);
+        if (n_next < 8 * r_next || n_next < 4 * BN) break;
+        stride *= PILOT_STRIDE;
+        rr = r_next;
+        s.lev_rank[s.nlev] = (int)rr;
+        s.lev_stride[s.nlev] = stride;
+        s.nlev++;
+    }
     s.C = (int)vpet_round_up(3 * (int64_t)s.kt + 2 * BN, 32);
-    s.sortcap = next_pow2(2 * k);
+    s.sortcap = next_pow2(k + 8);     // k plus a few ties at the k-th distance
     if (s.sortcap < 64) s.sortcap = 64;
     s.Jp = vpet_round_up(J > 0 ? J : 1, BM);
     s.Np = vpet_round_up(N > 0 ? N : 1, BN);
@@ -548,6 +572,43 @@ __device__ __forceinline__ float exact_dist(const float* ys, const float* x, int
     return d;
 }
 
+// exact_dist for two rows at once (same operation order), loads interleaved.
+__device__ __forceinline__ void exact_dist2(const float* ys, const float* xa, const float* xb, int L, const Weights& W,
+                                            float& da, float& db) {
+    const float4* ra = (const float4*)xa;
+    const float4* rb = (const float4*)xb;
+    float a = 0.0f, b = 0.0f;
+    int l = 0;
+    for (; l + 4 <= L; l += 4) {
+        const float4 va = __ldg(ra + (l >> 2));
+        const float4 vb = __ldg(rb + (l >> 2));
+        float e = ys[l] - va.x;
+        a = fmaf(W.w[l] * e, e, a);
+        e = ys[l + 1] - va.y;
+        a = fmaf(W.w[l + 1] * e, e, a);
+        e = ys[l + 2] - va.z;
+        a = fmaf(W.w[l + 2] * e, e, a);
+        e = ys[l + 3] - va.w;
+        a = fmaf(W.w[l + 3] * e, e, a);
+        e = ys[l] - vb.x;
+        b = fmaf(W.w[l] * e, e, b);
+        e = ys[l + 1] - vb.y;
+        b = fmaf(W.w[l + 1] * e, e, b);
+        e = ys[l + 2] - vb.z;
+        b = fmaf(W.w[l + 2] * e, e, b);
+        e = ys[l + 3] - vb.w;
+        b = fmaf(W.w[l + 3] * e, e, b);
+    }
+    for (; l < L; ++l) {
+        float e = ys[l] - xa[l];
+        a = fmaf(W.w[l] * e, e, a);
+        e = ys[l] - xb[l];
+        b = fmaf(W.w[l] * e, e, b);
+    }
+    da = a;
+    db = b;
+}
+
 // status[1]: voxels resolved by the exact scan; [2]: tie overflow; [3]: uncertified (bf16 mode)
 __global__ void k_finalize(FinParams P, Weights W) {
     extern __shared__ __align__(16) uint8_t fsm[];
@@ -574,8 +635,16 @@ __global__ void k_finalize(FinParams P, Weights W) {
             cnt = warp_compact(kj, ij, cnt, T, P.C, lane);
             T_out = key2f(T);
         }
-        // 2. exact fp32 re-score of the net
-        for (int i = lane; i < cnt; i += 32) kj[i] = exact_dist(ys, P.x + (int64_t)ij[i] * P.ldx, P.L, W);
+        // 2. exact fp32 re-score of the net (two candidates per lane in flight)
+        int i = lane;
+        for (; i + 32 < cnt; i += 64) {
+            const int32_t n0 = ij[i], n1 = ij[i + 32];
+            float d0, d1;
+            exact_dist2(ys, P.x + (int64_t)n0 * P.ldx, P.x + (int64_t)n1 * P.ldx, P.L, W, d0, d1);
+            kj[i] = d0;
+            kj[i + 32] = d1;
+        }
+        if (i < cnt) kj[i] = exact_dist(ys, P.x + (int64_t)ij[i] * P.ldx, P.L, W);
         __syncwarp();
         // 3. exact k-th distance and the certificate
         bool cert = false;
@@ -795,19 +864,22 @@ int run_topk(const float* y, int64_t J, int ldy, const float* x, int64_t N, int 
     const int64_t grid = lay.Jp / BM;
     if (dump) return dispatch_tc<true>(lay.nkb, ta, tb, P, grid, s);
     P.thr0 = nullptr;
-    if (lay.pilot) {
-        // pilot pass over every 16th draw (strided tensor map, no copy)
+    float* thr0 = (float*)(base + lay.off_thr0);
+    for (int lv = lay.nlev - 1; lv >= 0; --lv) {
+        // pilot pass over every lev_stride-th draw (strided tensor map, no copy)
+        const int64_t st = lay.lev_stride[lv];
+        const int64_t Ns = N / st;
+        const int r = lay.lev_rank[lv];
         CUtensorMap tp;
-        if ((rc = make_tmap(&tp, B, lay.Ns, lay.Kp, PILOT_STRIDE))) return rc;
+        if ((rc = make_tmap(&tp, B, Ns, lay.Kp, (int)st))) return rc;
         TcParams Q = P;
-        Q.N = lay.Ns;
-        Q.ntiles = (int)vpet_ceil_div(lay.Ns, BN);
-        Q.kt = lay.r;
-        Q.cap = lay.r + (lay.r / 4 > 64 ? lay.r / 4 : 64);
-        Q.lim = (int)(4 * (int64_t)lay.r + 2 * BN < lay.C ? 4 * (int64_t)lay.r + 2 * BN : lay.C);
+        Q.N = Ns;
+        Q.ntiles = (int)vpet_ceil_div(Ns, BN);
+        Q.kt = r;
+        Q.cap = r + (r / 4 > 64 ? r / 4 : 64);
+        Q.lim = (int)(4 * (int64_t)r + 2 * BN < lay.C ? 4 * (int64_t)r + 2 * BN : lay.C);
         if ((rc = dispatch_tc<false>(lay.nkb, ta, tp, Q, grid, s))) return rc;
-        float* thr0 = (float*)(base + lay.off_thr0);
-        k_pilot_threshold<<<(unsigned)vpet_ceil_div(J, 8), 256, 0, s>>>(P.keys, cnt, lay.C, lay.r, J, thr0);
+        k_pilot_threshold<<<(unsigned)vpet_ceil_div(J, 8), 256, 0, s>>>(P.keys, cnt, lay.C, r, J, thr0);
         VPET_LAUNCH_CHECK();
         P.thr0 = thr0;
     }
