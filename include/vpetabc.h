@@ -125,6 +125,62 @@ int abc_discrepancy_topk(const float* y_dev, int64_t J, int32_t ldy, const float
                          int32_t L, const float* w_host, int32_t k, int32_t precision, void* workspace,
                          size_t ws_bytes, int32_t* idx_dev, float* dist_dev, void* stream);
 
+/* Launch choices of the fused tensor-core kernel (picked by the project's
+ * autotuner; abc_default_tuning gives the values used when none is passed).
+ *  bn:           draws per tile and TMEM accumulator width, 64 or 128;
+ *  ctas_per_sm:  persistent CTAs launched per SM (1..4, capped by occupancy);
+ *  pilot_stride: draw stride between pilot levels, 8, 16 or 32;
+ *  pilot_factor: candidates a pilot threshold aims to admit, as a multiple of
+ *                the net size at the next finer level (1.25 .. 4). */
+typedef struct {
+    int32_t bn;
+    int32_t ctas_per_sm;
+    int32_t pilot_stride;
+    float pilot_factor;
+} abc_tuning;
+
+/* The tuning used for `precision` when none is passed: the built-in choice
+ * (64-draw tiles, 3 CTAs/SM for ABC_BF16_RESCORE; 128-draw tiles for ABC_FP32)
+ * unless abc_set_default_tuning replaced it. */
+int abc_default_tuning(int32_t precision, abc_tuning* out);
+
+/* Replaces the process-wide default tuning for both precisions (NULL restores
+ * the built-in ones).  Results never depend on the tuning; only speed does. */
+int abc_set_default_tuning(const abc_tuning* tuning);
+
+/* One scan (volume or ROI set) of a batch: its own voxel TACs, simulated
+ * draws, frame count and weights, k and outputs; arguments as in
+ * abc_discrepancy_topk. */
+typedef struct {
+    const float* y_dev;
+    int64_t J;
+    int32_t ldy;
+    const float* x_dev;
+    int64_t N;
+    int32_t ldx;
+    int32_t L;
+    const float* w_host;
+    int32_t k;
+    int32_t* idx_dev;
+    float* dist_dev;
+} abc_scan;
+
+/* Bytes of workspace abc_batch_discrepancy_topk needs (0 for invalid sizes). */
+size_t abc_batch_workspace_size(const abc_scan* scans, int32_t n_scans, int32_t precision);
+
+/* Batched discrepancy + top-k (Alg. 1 steps 4-5 for many scans at once): up to
+ * 64 scans with uneven voxel counts, frame schedules and draw counts, each with
+ * the same result as its own abc_discrepancy_topk.  All scans share one
+ * persistent launch of the fused kernel per pass (pilot levels, main pass),
+ * whose CTAs take (scan, 128-voxel tile) work items costliest-scan first; one
+ * launch re-scores and sorts every voxel of every scan.  Everything is enqueued
+ * on `stream` with no host-to-device copies, so the call can be captured in a
+ * CUDA graph and replayed while the buffers stay in place.  tuning may be NULL
+ * (default tuning).  Status as for abc_discrepancy_topk (abc_topk_status on
+ * this workspace covers the whole batch). */
+int abc_batch_discrepancy_topk(const abc_scan* scans, int32_t n_scans, int32_t precision, const abc_tuning* tuning,
+                               void* workspace, size_t ws_bytes, void* stream);
+
 /* Allocation-free variant of abc_discrepancy_topk.  The paper has no
  * counterpart: this entry point exists for callers that must not allocate
  * device memory themselves (a host framework that owns the whole device-memory
@@ -168,6 +224,11 @@ int abc_topk_status(const void* workspace, int32_t status_host[4], void* stream)
  * time that kernel alone with cudaEventElapsedTime.  NULL, NULL turns it off.
  * Process-wide setting; the events stay owned by the caller. */
 int abc_profile_events(void* start_event, void* stop_event);
+
+/* Diagnostics: grid size of the last fused-kernel launch of this process and
+ * the CTAs per SM its variant can keep resident (shared memory, registers and
+ * TMEM columns). */
+int abc_launch_info(int64_t* grid, int32_t* resident_per_sm);
 
 /* Test hook: the raw tensor-core ranking keys d' = ||yh||^2-free part of the
  * distance (||xh_n||^2 - 2 yh_j . xh_n, yh = sqrt(w)(y - mu), xh = sqrt(w)(x - mu),

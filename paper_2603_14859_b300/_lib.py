@@ -25,7 +25,8 @@ ABC_FP32, ABC_BF16_RESCORE = 0, 1
 EXPORTS = [
     "abc_feng_input", "abc_sample_prior", "abc_simulate", "abc_workspace_size", "abc_discrepancy_topk",
     "abc_topk_status", "abc_model_select", "abc_summarize", "abc_last_error", "abc_profile_events",
-    "abc_debug_gemm_keys", "abc_discrepancy_topk_noalloc",
+    "abc_debug_gemm_keys", "abc_discrepancy_topk_noalloc", "abc_default_tuning", "abc_set_default_tuning",
+    "abc_batch_workspace_size", "abc_batch_discrepancy_topk", "abc_launch_info",
 ]
 
 
@@ -36,6 +37,17 @@ class Frames(ctypes.Structure):
 class PolyExp(ctypes.Structure):
     _fields_ = [("n_terms", ctypes.c_int32), ("c", ctypes.c_void_p), ("a0", ctypes.c_void_p),
                 ("a1", ctypes.c_void_p), ("a2", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("bn", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("pilot_stride", ctypes.c_int32),
+                ("pilot_factor", ctypes.c_float)]
+
+
+class Scan(ctypes.Structure):
+    _fields_ = [("y_dev", ctypes.c_void_p), ("J", ctypes.c_int64), ("ldy", ctypes.c_int32), ("x_dev", ctypes.c_void_p),
+                ("N", ctypes.c_int64), ("ldx", ctypes.c_int32), ("L", ctypes.c_int32), ("w_host", ctypes.c_void_p),
+                ("k", ctypes.c_int32), ("idx_dev", ctypes.c_void_p), ("dist_dev", ctypes.c_void_p)]
 
 
 class AbcError(RuntimeError):
@@ -67,10 +79,17 @@ def lib():
     L.abc_last_error.restype = ctypes.c_char_p
     L.abc_profile_events.argtypes = [P, P]
     L.abc_discrepancy_topk_noalloc.argtypes = [P, i64, i32, P, i64, i32, i32, P, i32, i32, P, P, P]
+    L.abc_default_tuning.argtypes = [i32, ctypes.POINTER(Tuning)]
+    L.abc_set_default_tuning.argtypes = [ctypes.POINTER(Tuning)]
+    L.abc_launch_info.argtypes = [P, P]
+    L.abc_batch_workspace_size.argtypes = [ctypes.POINTER(Scan), i32, i32]
+    L.abc_batch_workspace_size.restype = sz
+    L.abc_batch_discrepancy_topk.argtypes = [ctypes.POINTER(Scan), i32, i32, ctypes.POINTER(Tuning), P, sz, P]
     L.abc_debug_gemm_keys.argtypes = [P, i64, i32, P, i64, i32, i32, P, i32, P, sz, P, i64, P]
     for fn in ["abc_feng_input", "abc_sample_prior", "abc_simulate", "abc_discrepancy_topk", "abc_topk_status",
                "abc_model_select", "abc_summarize", "abc_debug_gemm_keys", "abc_profile_events",
-               "abc_discrepancy_topk_noalloc"]:
+               "abc_discrepancy_topk_noalloc", "abc_default_tuning", "abc_set_default_tuning",
+               "abc_batch_discrepancy_topk", "abc_launch_info"]:
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L

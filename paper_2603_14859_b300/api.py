@@ -157,3 +157,26 @@ def profile_events(start=None, stop=None):
     a = ctypes.c_void_p(start.cuda_event) if start is not None else None
     b = ctypes.c_void_p(stop.cuda_event) if stop is not None else None
     check(lib().abc_profile_events(a, b))
+
+
+def launch_info():
+    """(grid, resident CTAs per SM) of the last fused-kernel launch."""
+    g = ctypes.c_int64(0)
+    r = ctypes.c_int32(0)
+    check(lib().abc_launch_info(ctypes.byref(g), ctypes.byref(r)))
+    return g.value, r.value
+
+
+def set_default_tuning(bn=None, ctas_per_sm=2, pilot_stride=16, pilot_factor=1.5):
+    """Process-wide default tuning; bn=None restores the built-in per-precision defaults."""
+    if bn is None:
+        check(lib().abc_set_default_tuning(None))
+        return
+    t = _lib.Tuning(bn, ctas_per_sm, pilot_stride, pilot_factor)
+    check(lib().abc_set_default_tuning(ctypes.byref(t)))
+
+
+def default_tuning(precision=_lib.ABC_BF16_RESCORE):
+    t = _lib.Tuning()
+    check(lib().abc_default_tuning(precision, ctypes.byref(t)))
+    return dict(bn=t.bn, ctas_per_sm=t.ctas_per_sm, pilot_stride=t.pilot_stride, pilot_factor=t.pilot_factor)

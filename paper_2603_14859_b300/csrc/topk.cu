@@ -55,30 +55,45 @@ using namespace vpet;
 
 namespace {
 
-constexpr int BM = 128;          // voxels per CTA = TMEM lanes
-constexpr int BN = 128;          // draws per tile = accumulator columns
-constexpr int KBLK = 64;         // bf16 per K-block (128-byte rows)
-constexpr int KBLK_BYTES = BM * KBLK * 2;   // 16 KB (BM == BN)
+constexpr int BM = 128;                       // voxels per CTA tile = TMEM lanes
+constexpr int KBLK = 64;                      // bf16 per K-block (128-byte rows)
+constexpr int A_KBLK_BYTES = BM * KBLK * 2;   // 16 KB
 constexpr int TC_THREADS = 192;
-constexpr uint64_t WAIT_NS = 2000000000ull; // 2 s bound on any barrier wait
+constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any barrier wait
 constexpr int MAXL = 64;
-constexpr int PILOT_STRIDE = 16;
 constexpr int MAX_PILOT_LEVELS = 4;
+constexpr int MAX_ITEMS = 64;                 // scans per batched launch
+constexpr int STAGE_LD = 36;                  // floats per staged row (16-byte aligned, conflict-free)
 
 struct Weights {
     float w[MAXL];
     float sw[MAXL];   // sqrt(w)
 };
 
+// Launch choices the autotuner varies (abc_tuning in the C ABI).
+struct Tuning {
+    int bn;               // draws per tile: 64 or 128
+    int ctas_per_sm;      // persistent CTAs per SM (capped by occupancy)
+    int pilot_stride;     // draw stride of each pilot level: 8, 16 or 32
+    float pilot_factor;   // predicted candidates / net size at the next finer level (>= 1.25)
+};
+
+// Built-in defaults (measured on B300 for the brain lp-ntPET workload): bf16
+// operands fit three 64-draw CTAs per SM; the fp32-split operands (3 K-blocks)
+// fit one CTA per SM, where 128-draw tiles are faster.
+Tuning default_tuning(int mode) {
+    return mode == ABC_FP32 ? Tuning{128, 2, 16, 1.5f} : Tuning{64, 3, 16, 1.5f};
+}
+
 struct Layout {
     int mode;          // ABC_FP32 / ABC_BF16_RESCORE
     int L, k, Kp, nkb, C, kt, cap, sortcap;
     int nlev;                          // pilot levels (finest first)
-    int lev_rank[4];
-    int64_t lev_stride[4];
+    int lev_rank[MAX_PILOT_LEVELS];
+    int64_t lev_stride[MAX_PILOT_LEVELS];
     int64_t J, N, Jp, Np;
     int npart;
-    size_t off_mu, off_part, off_ynorm, off_a, off_b, off_keys, off_idx, off_cnt, off_thr, off_thr0, off_status, total;
+    size_t off_mu, off_part, off_ynorm, off_a, off_b, off_keys, off_idx, off_cnt, off_thr, off_thr0, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -89,7 +104,7 @@ int next_pow2(int x) {
     return p;
 }
 
-Layout make_layout(int64_t J, int64_t N, int L, int k, int mode) {
+Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& tu) {
     Layout s;
     memset(&s, 0, sizeof s);
     s.mode = mode;
@@ -103,40 +118,37 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode) {
     const int64_t net = (int64_t)(mode == ABC_FP32 ? 2 : 4) * k;
     s.kt = (int)(net < N ? net : N);
     s.cap = s.kt + (s.kt / 4 > 64 ? s.kt / 4 : 64);
-    // pilot: the r-th smallest key over every 16th draw predicts the 1.5 kt-th
-    // smallest over all draws (draws are i.i.d. within each model)
-    // Levels of pilots: level i uses every 16^i-th draw and a target rank
-    // r_i = ceil(f r_{i-1} / 16), r_0 = kt; each starts from the next coarser
-    // level's threshold.  f = 1.5 predicts 1.5 r_{i-1} draws below the
-    // threshold at the finer level; for a small r_i the rank statistic is noisy
-    // (relative sd ~ 1 / sqrt(r_i)), so f grows until an under-prediction is
-    // more than ~4 sd away.
+    // Pilot levels: level i uses every stride^i-th draw and a target rank
+    // r_i = ceil(f r_{i-1} / stride), r_0 = kt, so that about f r_{i-1} draws of
+    // the next finer level fall below its threshold.  For a small r_i the rank
+    // statistic is noisy (relative sd ~ 1 / sqrt(r_i)), so r_i grows until an
+    // under-prediction is more than ~4 sd away.
     s.nlev = 0;
     int64_t rr = s.kt, stride = 1;
+    const double f0 = tu.pilot_factor;
     while (s.nlev < MAX_PILOT_LEVELS) {
-        int64_t r_next = (3 * rr + 31) / 32;
+        int64_t r_next = (int64_t)ceil(f0 * (double)rr / tu.pilot_stride);
         for (int it = 0; it < 8; ++it) {
-            const double f = (double)r_next * PILOT_STRIDE / (double)rr;       // predicted count / needed
+            const double f = (double)r_next * tu.pilot_stride / (double)rr;   // predicted count / needed
             if (1.0 - 1.0 / f >= 4.0 / sqrt((double)r_next)) break;
             r_next = r_next + r_next / 2 + 1;
         }
-        const int64_t n_next = N / (stride * PILOT_STRIDE);
-        if (n_next < 8 * r_next || n_next < 4 * BN) break;
-        stride *= PILOT_STRIDE;
+        const int64_t n_next = N / (stride * tu.pilot_stride);
+        if (n_next < 8 * r_next || n_next < 512) break;
+        stride *= tu.pilot_stride;
         rr = r_next;
         s.lev_rank[s.nlev] = (int)rr;
         s.lev_stride[s.nlev] = stride;
         s.nlev++;
     }
-    s.C = (int)vpet_round_up(3 * (int64_t)s.kt + 2 * BN, 32);
+    s.C = (int)vpet_round_up(3 * (int64_t)s.kt + 256, 32);
     s.sortcap = next_pow2(k + 8);     // k plus a few ties at the k-th distance
     if (s.sortcap < 64) s.sortcap = 64;
     s.Jp = vpet_round_up(J > 0 ? J : 1, BM);
-    s.Np = vpet_round_up(N > 0 ? N : 1, BN);
+    s.Np = vpet_round_up(N > 0 ? N : 1, 128);
     s.npart = (int)(vpet_ceil_div(J, 256) < 1024 ? vpet_ceil_div(J, 256) : 1024);
     if (s.npart < 1) s.npart = 1;
     size_t o = 0;
-    s.off_status = o; o = align256(o + 64 * sizeof(int32_t));
     s.off_mu = o; o = align256(o + MAXL * sizeof(float));
     s.off_part = o; o = align256(o + (size_t)s.npart * MAXL * sizeof(float));
     s.off_ynorm = o; o = align256(o + (size_t)s.Jp * sizeof(float));
@@ -266,34 +278,48 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
 }
 
 // ------------------------------------------------------------------ fused GEMM + filter
-struct TcParams {
-    int64_t J, N;
-    int ntiles, C, kt, cap;
-    int lim;                     // a list is compacted once it could exceed lim entries (lim <= C)
-    float* keys;
+// One scan of a batch, as the fused kernel sees it (kernel parameter space).
+struct __align__(64) ItemTc {
+    CUtensorMap tmA;             // packed voxel operand, box {64, 128}
+    CUtensorMap tmB;             // packed draw operand (strided for a pilot), box {64, BN}
+    int64_t J, N;                // voxels; draws in this pass
+    float* keys;                 // candidate lists, J x C
     int32_t* idx;
     int32_t* cnt;
     float* thr;                  // final running threshold per voxel
     const float* thr0;           // initial threshold per voxel (pilot), or null = +huge
+    int ntiles, C, kt, cap;
+    int lim;                     // a list is compacted once it could exceed lim entries (lim <= C)
+};
+
+struct BatchTc {
+    ItemTc item[MAX_ITEMS];
+    int64_t vt_prefix[MAX_ITEMS + 1];   // voxel tiles before each item (work index space)
+    int n_items;
+    unsigned long long* counter;        // next work index (zeroed before the launch)
     int32_t* status;
-    float* dump;                 // debug probe: raw keys, Jp x Np (nullptr in production)
+    float* dump;                 // debug probe: raw keys, Jp x Np (null in production)
     int64_t ld_dump;
 };
 
-constexpr int STAGE_LD = 36;     // floats per staged row (16-byte aligned, conflict-free)
+__device__ __forceinline__ int item_of(const BatchTc& P, int64_t w) {
+    int it = 0;
+    while (it + 1 < P.n_items && w >= P.vt_prefix[it + 1]) ++it;
+    return it;
+}
 
 // Bound on |computed d' - exact d'| for any draw with ||xh|| <= R.
 __device__ __forceinline__ float err_bound(float cE, float ry, float R) { return cE * (2.0f * ry * R + R * R); }
 
 // Tightens voxel j's candidate list to the keys <= its kt-th key; returns the new
 // threshold and updates cnt.
-__device__ __forceinline__ float compact_list(const TcParams& P, int64_t j, int& cnt, uint32_t* hist, int lane) {
-    float* kj = P.keys + j * P.C;
-    int32_t* ij = P.idx + j * P.C;
-    const uint32_t T = warp_select(kj, cnt, P.kt - 1, 3, hist, lane);
-    const int q = warp_compact(kj, ij, cnt, T, P.cap, lane);
-    cnt = q < P.cap ? q : P.cap;
-    if (q > P.cap && lane == 0) atomicOr(&P.cnt[j], 0x40000000);   // overflow: resolved by an exact scan
+__device__ __forceinline__ float compact_list(const ItemTc& I, int64_t j, int& cnt, uint32_t* hist, int lane) {
+    float* kj = I.keys + j * I.C;
+    int32_t* ij = I.idx + j * I.C;
+    const uint32_t T = warp_select(kj, cnt, I.kt - 1, 3, hist, lane);
+    const int q = warp_compact(kj, ij, cnt, T, I.cap, lane);
+    cnt = q < I.cap ? q : I.cap;
+    if (q > I.cap && lane == 0) atomicOr(&I.cnt[j], 0x40000000);   // overflow: resolved by an exact scan
     return key2f(T);
 }
 
@@ -310,13 +336,21 @@ __device__ __forceinline__ float min32(const float (&v)[32]) {
     return fminf(fminf(b, c), d);
 }
 
+// The fields of an item the epilogue touches per chunk, held in registers.
+struct ItemRegs {
+    int64_t N;
+    float* keys;
+    int32_t* idx;
+    int C;
+};
+
 // One 32-column chunk of the epilogue: filter, then warp-cooperative appends.
-__device__ __forceinline__ void epilogue_chunk(const TcParams& P, float (&v)[32], int64_t n0, int64_t jbase,
+__device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32], int64_t n0, int64_t jbase,
                                                float thr, int& cnt, float* stage, int lane) {
-    if (n0 + 32 > P.N) {
+    if (n0 + 32 > I.N) {
 #pragma unroll
         for (int i = 0; i < 32; ++i)
-            if (n0 + i >= P.N) v[i] = __int_as_float(0x7F800000);   // +inf: never kept
+            if (n0 + i >= I.N) v[i] = __int_as_float(0x7F800000);   // +inf: never kept
     }
     const bool slow = min32(v) <= thr;
     uint32_t bal = __ballot_sync(0xFFFFFFFFu, slow);
@@ -337,35 +371,43 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& P, float (&v)[32]
         const bool pass = val <= ts;
         const uint32_t pb = __ballot_sync(0xFFFFFFFFu, pass);
         if (pass) {
-            const int64_t at = (jbase + s) * (int64_t)P.C + cs + __popc(pb & lt);
-            P.keys[at] = val;
-            P.idx[at] = (int32_t)(n0 + lane);
+            const int64_t at = (jbase + s) * (int64_t)I.C + cs + __popc(pb & lt);
+            I.keys[at] = val;
+            I.idx[at] = (int32_t)(n0 + lane);
         }
         if (lane == s) cnt += __popc(pb);
     }
     __syncwarp();
 }
 
-template <int NKB, int STAGES, bool DUMP>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams P) {
+// Persistent fused kernel over the (scan, 128-voxel tile) work items of a batch,
+// handed out round-robin in the order of the work index space (costliest
+// scans first).  All roles walk the same sequence; the shared-memory ring and
+// the TMEM accumulators keep their phases across items.
+template <int NKB, int STAGES, int BN, bool DUMP>
+__global__ void __launch_bounds__(TC_THREADS) k_tc_topk(const __grid_constant__ BatchTc P) {
+    constexpr int B_KBLK_BYTES = BN * KBLK * 2;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* sA = smem;                                        // NKB x 16 KB
-    uint8_t* sB = smem + NKB * KBLK_BYTES;                     // STAGES x NKB x 16 KB
-    float* sStage = (float*)(sB + STAGES * NKB * KBLK_BYTES);  // 4 warps x 32 x STAGE_LD
-    uint32_t* hist = (uint32_t*)(sStage + 4 * 32 * STAGE_LD);  // 4 warps x 256
+    uint8_t* sA = smem;                                          // NKB x 16 KB
+    uint8_t* sB = smem + NKB * A_KBLK_BYTES;                     // STAGES x NKB x BN rows
+    float* sStage = (float*)(sB + STAGES * NKB * B_KBLK_BYTES);  // 4 warps x 32 x STAGE_LD
+    uint32_t* hist = (uint32_t*)(sStage + 4 * 32 * STAGE_LD);    // 4 warps x 256
     uint64_t* bars = (uint64_t*)(hist + 4 * 256);
     uint64_t* full = bars;                  // [STAGES]
     uint64_t* empty = bars + STAGES;        // [STAGES]
     uint64_t* tfull = bars + 2 * STAGES;    // [2]
     uint64_t* tempty = bars + 2 * STAGES + 2;
     uint64_t* afull = bars + 2 * STAGES + 4;
-    uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 5);
+    uint64_t* aempty = bars + 2 * STAGES + 5;
+    uint64_t* ifull = bars + 2 * STAGES + 6;    // [2] work-item mailbox
+    uint64_t* iempty = bars + 2 * STAGES + 8;   // [2]
+    volatile long long* slot = (volatile long long*)(bars + 2 * STAGES + 10);   // [2]
+    uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 12);
     volatile int* s_err = (volatile int*)(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int64_t total = P.vt_prefix[P.n_items];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -377,6 +419,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ptx::mbar_init(ptx::smem_u32(&tempty[a]), 4);
         }
         ptx::mbar_init(ptx::smem_u32(afull), 1);
+        ptx::mbar_init(ptx::smem_u32(aempty), 1);
+        for (int a = 0; a < 2; ++a) {
+            ptx::mbar_init(ptx::smem_u32(&ifull[a]), 1);
+            ptx::mbar_init(ptx::smem_u32(&iempty[a]), 5);   // MMA thread + 4 epilogue warps
+        }
         *s_err = 0;
         ptx::fence_mbar_init();
     }
@@ -388,123 +435,179 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_holder;
-    const int ntiles = P.ntiles;
 
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
-            ptx::tma_prefetch_desc(&tmA);
-            ptx::tma_prefetch_desc(&tmB);
-            const uint32_t ab = ptx::smem_u32(afull);
-            ptx::mbar_arrive_expect_tx(ab, NKB * KBLK_BYTES);
-            for (int kb = 0; kb < NKB; ++kb)
-                ptx::tma_load_2d(ptx::smem_u32(sA + kb * KBLK_BYTES), &tmA, ab, kb * KBLK, (int32_t)m0);
-            for (int t = 0; t < ntiles; ++t) {
-                const int s = t % STAGES;
-                const uint32_t ph = (uint32_t)(t / STAGES) & 1u;
-                if (!ptx::mbar_wait(ptx::smem_u32(&empty[s]), ph ^ 1u, WAIT_NS)) { *s_err = 1; break; }
-                if (*s_err) break;
-                const uint32_t fb = ptx::smem_u32(&full[s]);
-                ptx::mbar_arrive_expect_tx(fb, NKB * KBLK_BYTES);
+            uint32_t gt = 0;
+            for (uint32_t ic = 0;; ++ic) {
+                // take the next work item and post it to the other roles
+                long long w = (long long)atomicAdd(P.counter, 1ull);
+                if (w >= total || *s_err) w = -1;
+                const uint32_t sl = ic & 1u;
+                if (!ptx::mbar_wait(ptx::smem_u32(&iempty[sl]), ((ic >> 1) & 1u) ^ 1u, WAIT_NS)) { *s_err = 1; w = -1; }
+                slot[sl] = w;
+                ptx::mbar_arrive(ptx::smem_u32(&ifull[sl]));
+                if (w < 0) break;
+                const int it = item_of(P, w);
+                const ItemTc& I = P.item[it];
+                const int64_t m0 = (w - P.vt_prefix[it]) * BM;
+                const int ntiles = I.ntiles;
+                ptx::tma_prefetch_desc(&I.tmA);
+                ptx::tma_prefetch_desc(&I.tmB);
+                // the previous item's MMAs must be done with the A tile
+                if (!ptx::mbar_wait(ptx::smem_u32(aempty), (ic & 1u) ^ 1u, WAIT_NS)) { *s_err = 1; break; }
+                const uint32_t ab = ptx::smem_u32(afull);
+                ptx::mbar_arrive_expect_tx(ab, NKB * A_KBLK_BYTES);
                 for (int kb = 0; kb < NKB; ++kb)
-                    ptx::tma_load_2d(ptx::smem_u32(sB + (s * NKB + kb) * KBLK_BYTES), &tmB, fb, kb * KBLK, t * BN);
+                    ptx::tma_load_2d(ptx::smem_u32(sA + kb * A_KBLK_BYTES), &I.tmA, ab, kb * KBLK, (int32_t)m0);
+                for (int t = 0; t < ntiles; ++t, ++gt) {
+                    const uint32_t s = gt % STAGES;
+                    const uint32_t ph = (gt / STAGES) & 1u;
+                    if (!ptx::mbar_wait(ptx::smem_u32(&empty[s]), ph ^ 1u, WAIT_NS)) { *s_err = 1; break; }
+                    if (*s_err) break;
+                    const uint32_t fb = ptx::smem_u32(&full[s]);
+                    ptx::mbar_arrive_expect_tx(fb, NKB * B_KBLK_BYTES);
+                    for (int kb = 0; kb < NKB; ++kb)
+                        ptx::tma_load_2d(ptx::smem_u32(sB + (s * NKB + kb) * B_KBLK_BYTES), &I.tmB, fb, kb * KBLK,
+                                         t * BN);
+                }
             }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer (single thread)
         if (lane == 0) {
             constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
-            bool ok = ptx::mbar_wait(ptx::smem_u32(afull), 0, WAIT_NS);
-            if (!ok) *s_err = 1;
             const uint32_t a_base = ptx::smem_u32(sA);
-            for (int t = 0; ok && t < ntiles; ++t) {
-                const int s = t % STAGES;
-                const uint32_t ph = (uint32_t)(t / STAGES) & 1u;
-                const int acc = t & 1;
-                const uint32_t aph = (uint32_t)(t >> 1) & 1u;
-                if (!ptx::mbar_wait(ptx::smem_u32(&tempty[acc]), aph ^ 1u, WAIT_NS) ||
-                    !ptx::mbar_wait(ptx::smem_u32(&full[s]), ph, WAIT_NS)) {
-                    *s_err = 1;
-                    break;
-                }
-                if (*s_err) break;
-                ptx::tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
-                const uint32_t b_base = ptx::smem_u32(sB + s * NKB * KBLK_BYTES);
-#pragma unroll
-                for (int kb = 0; kb < NKB; ++kb) {
-#pragma unroll
-                    for (int kk = 0; kk < KBLK / 16; ++kk) {
-                        const uint64_t ad = ptx::desc_sw128(a_base + kb * KBLK_BYTES + kk * 32);
-                        const uint64_t bd = ptx::desc_sw128(b_base + kb * KBLK_BYTES + kk * 32);
-                        ptx::mma_bf16(d_tmem, ad, bd, idesc, (kb | kk) ? 1u : 0u);
+            uint32_t gt = 0;
+            for (uint32_t ic = 0;; ++ic) {
+                const uint32_t sl = ic & 1u;
+                long long w = -1;
+                if (ptx::mbar_wait(ptx::smem_u32(&ifull[sl]), (ic >> 1) & 1u, WAIT_NS)) w = slot[sl];
+                else *s_err = 1;
+                ptx::mbar_arrive(ptx::smem_u32(&iempty[sl]));
+                if (w < 0) break;
+                const int ntiles = P.item[item_of(P, w)].ntiles;
+                if (!ptx::mbar_wait(ptx::smem_u32(afull), ic & 1u, WAIT_NS)) { *s_err = 1; break; }
+                for (int t = 0; t < ntiles; ++t, ++gt) {
+                    const uint32_t s = gt % STAGES;
+                    const uint32_t ph = (gt / STAGES) & 1u;
+                    const uint32_t acc = gt & 1u;
+                    const uint32_t aph = (gt >> 1) & 1u;
+                    if (!ptx::mbar_wait(ptx::smem_u32(&tempty[acc]), aph ^ 1u, WAIT_NS) ||
+                        !ptx::mbar_wait(ptx::smem_u32(&full[s]), ph, WAIT_NS)) {
+                        *s_err = 1;
+                        break;
                     }
+                    if (*s_err) break;
+                    ptx::tc_fence_after();
+                    const uint32_t d_tmem = tmem + acc * BN;
+                    const uint32_t b_base = ptx::smem_u32(sB + s * NKB * B_KBLK_BYTES);
+#pragma unroll
+                    for (int kb = 0; kb < NKB; ++kb) {
+#pragma unroll
+                        for (int kk = 0; kk < KBLK / 16; ++kk) {
+                            const uint64_t ad = ptx::desc_sw128(a_base + kb * A_KBLK_BYTES + kk * 32);
+                            const uint64_t bd = ptx::desc_sw128(b_base + kb * B_KBLK_BYTES + kk * 32);
+                            ptx::mma_bf16(d_tmem, ad, bd, idesc, (kb | kk) ? 1u : 0u);
+                        }
+                    }
+                    ptx::mma_commit(ptx::smem_u32(&empty[s]));
+                    ptx::mma_commit(ptx::smem_u32(&tfull[acc]));
                 }
-                ptx::mma_commit(ptx::smem_u32(&empty[s]));
-                ptx::mma_commit(ptx::smem_u32(&tfull[acc]));
+                ptx::mma_commit(ptx::smem_u32(aempty));   // A tile free once these MMAs complete
             }
         }
     } else {
         // ---------------- epilogue: warps 2..5, thread <-> voxel
         const int q = warp & 3;                          // TMEM lane quadrant of this warp
         const int row = q * 32 + lane;
-        const int64_t jbase = m0 + q * 32;
-        const int64_t j = jbase + lane;
-        const bool valid = j < P.J;
         uint32_t* whist = hist + (warp - 2) * 256;
         float* stage = sStage + (warp - 2) * 32 * STAGE_LD;
-        float thr = valid ? (P.thr0 ? P.thr0[j] : 3.0e38f) : -3.0e38f;
-        int cnt = 0;
-        for (int t = 0; t < ntiles; ++t) {
-            const int acc = t & 1;
-            const uint32_t aph = (uint32_t)(t >> 1) & 1u;
-            if (!ptx::mbar_wait(ptx::smem_u32(&tfull[acc]), aph, WAIT_NS)) { *s_err = 1; }
-            if (__any_sync(0xFFFFFFFFu, *s_err != 0)) break;
-            ptx::tc_fence_after();
-            const int64_t nbase = (int64_t)t * BN;
-#pragma unroll 1
-            for (int h = 0; h < BN / 64; ++h) {
-                uint32_t r0[32], r1[32];
-                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + h * 64);
-                ptx::tmem_ld32_async(ta, r0);
-                ptx::tmem_ld32_async(ta + 32, r1);
-                ptx::tmem_wait_ld();
-                ptx::tmem_fence_regs(r0);
-                ptx::tmem_fence_regs(r1);
-                float v0[32], v1[32];
-#pragma unroll
-                for (int i = 0; i < 32; ++i) { v0[i] = __uint_as_float(r0[i]); v1[i] = __uint_as_float(r1[i]); }
-                if (DUMP) {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        P.dump[(m0 + row) * P.ld_dump + nbase + h * 64 + i] = v0[i];
-                        P.dump[(m0 + row) * P.ld_dump + nbase + h * 64 + 32 + i] = v1[i];
-                    }
-                    continue;
-                }
-                epilogue_chunk(P, v0, nbase + h * 64, jbase, thr, cnt, stage, lane);
-                epilogue_chunk(P, v1, nbase + h * 64 + 32, jbase, thr, cnt, stage, lane);
-            }
-            ptx::tc_fence_before();
+        uint32_t gt = 0;
+        bool stop = false;
+        for (uint32_t ic = 0; !stop; ++ic) {
+            const uint32_t sl = ic & 1u;
+            long long w = -1;
+            if (ptx::mbar_wait(ptx::smem_u32(&ifull[sl]), (ic >> 1) & 1u, WAIT_NS)) w = slot[sl];
+            else *s_err = 1;
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&tempty[acc]));
-            if (DUMP) continue;
-            // compaction of lists that might not fit the next tile
-            uint32_t need = __ballot_sync(0xFFFFFFFFu, valid && cnt > P.lim - BN);
-            while (need) {
-                const int src = __ffs(need) - 1;
-                need &= need - 1;
-                int c2 = __shfl_sync(0xFFFFFFFFu, cnt, src);
-                const float nt = compact_list(P, jbase + src, c2, whist, lane);
-                if (lane == src) {
-                    cnt = c2;
-                    thr = nt;
+            if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&iempty[sl]));
+            if (w < 0) break;
+            const int it = item_of(P, w);
+            const ItemTc& I = P.item[it];
+            const ItemRegs R{I.N, I.keys, I.idx, I.C};
+            const int ntiles = I.ntiles, lim = I.lim;
+            const int64_t m0 = (w - P.vt_prefix[it]) * BM;
+            const int64_t jbase = m0 + q * 32;
+            const int64_t j = jbase + lane;
+            const bool valid = j < I.J;
+            float thr = valid ? (I.thr0 ? I.thr0[j] : 3.0e38f) : -3.0e38f;
+            int cnt = 0;
+            for (int t = 0; t < ntiles; ++t, ++gt) {
+                const uint32_t acc = gt & 1u;
+                const uint32_t aph = (gt >> 1) & 1u;
+                if (!ptx::mbar_wait(ptx::smem_u32(&tfull[acc]), aph, WAIT_NS)) { *s_err = 1; }
+                if (__any_sync(0xFFFFFFFFu, *s_err != 0)) { stop = true; break; }
+                ptx::tc_fence_after();
+                const int64_t nbase = (int64_t)t * BN;
+                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
+                if (DUMP) {
+                    for (int c = 0; c < BN / 32; ++c) {
+                        uint32_t r[32];
+                        ptx::tmem_ld32_async(ta + c * 32, r);
+                        ptx::tmem_wait_ld();
+                        ptx::tmem_fence_regs(r);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            P.dump[(m0 + row) * P.ld_dump + nbase + c * 32 + i] = __uint_as_float(r[i]);
+                    }
+                } else {
+                    // software pipeline: the load of chunk c+1 is in flight while chunk c is filtered
+                    uint32_t ra[32], rb[32];
+                    ptx::tmem_ld32_async(ta, ra);
+                    ptx::tmem_wait_ld();
+                    ptx::tmem_fence_regs(ra);
+#pragma unroll
+                    for (int c = 0; c < BN / 32; c += 2) {
+                        float v[32];
+                        ptx::tmem_ld32_async(ta + (c + 1) * 32, rb);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(ra[i]);
+                        epilogue_chunk(R, v, nbase + c * 32, jbase, thr, cnt, stage, lane);
+                        ptx::tmem_wait_ld();
+                        ptx::tmem_fence_regs(rb);
+                        if (c + 2 < BN / 32) ptx::tmem_ld32_async(ta + (c + 2) * 32, ra);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(rb[i]);
+                        epilogue_chunk(R, v, nbase + (c + 1) * 32, jbase, thr, cnt, stage, lane);
+                        if (c + 2 < BN / 32) {
+                            ptx::tmem_wait_ld();
+                            ptx::tmem_fence_regs(ra);
+                        }
+                    }
+                }
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&tempty[acc]));
+                if (DUMP) continue;
+                // compaction of lists that might not fit the next tile
+                uint32_t need = __ballot_sync(0xFFFFFFFFu, valid && cnt > lim - BN);
+                while (need) {
+                    const int src = __ffs(need) - 1;
+                    need &= need - 1;
+                    int c2 = __shfl_sync(0xFFFFFFFFu, cnt, src);
+                    const float nt = compact_list(I, jbase + src, c2, whist, lane);
+                    if (lane == src) {
+                        cnt = c2;
+                        thr = nt;
+                    }
                 }
             }
-        }
-        if (valid && !DUMP) {
-            atomicOr(&P.cnt[j], cnt);      // cnt[] was zeroed; keeps the overflow bit
-            P.thr[j] = thr;
+            if (valid && !DUMP && !stop) {
+                atomicOr(&I.cnt[j], cnt);      // cnt[] was zeroed; keeps the overflow bit
+                I.thr[j] = thr;
+            }
         }
     }
 
@@ -518,62 +621,88 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // Pilot threshold: the r-th smallest key of each voxel's pilot list, then the
-// list is emptied for the main pass.
-__global__ void k_pilot_threshold(float* keys, int32_t* cnt, int C, int r, int64_t J, float* thr0) {
+// list is emptied for the next pass.
+struct PilotItem {
+    float* keys;
+    int32_t* cnt;
+    float* thr0;
+    int64_t J;
+    int C, r;
+};
+
+struct BatchPilot {
+    PilotItem item[MAX_ITEMS];
+    int64_t v_prefix[MAX_ITEMS + 1];
+    int n_items;
+};
+
+__global__ void k_pilot_threshold(const __grid_constant__ BatchPilot B) {
     __shared__ uint32_t hist[8][256];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t j = (int64_t)blockIdx.x * 8 + wid;
-    if (j >= J) return;
-    const int c = cnt[j] & 0x3FFFFFFF;
+    const int64_t g = (int64_t)blockIdx.x * 8 + wid;
+    if (g >= B.v_prefix[B.n_items]) return;
+    int it = 0;
+    while (it + 1 < B.n_items && g >= B.v_prefix[it + 1]) ++it;
+    const PilotItem& I = B.item[it];
+    const int64_t j = g - B.v_prefix[it];
+    const int raw = I.cnt[j];
+    const int c = raw & 0x3FFFFFFF;
     float t = 3.0e38f;
-    if (!(cnt[j] & 0x40000000) && c >= r) t = key2f(warp_select(keys + j * C, c, r - 1, 3, hist[wid], lane));
+    if (!(raw & 0x40000000) && c >= I.r) t = key2f(warp_select(I.keys + j * I.C, c, I.r - 1, 3, hist[wid], lane));
     if (lane == 0) {
-        thr0[j] = t;
-        cnt[j] = 0;
+        I.thr0[j] = t;
+        I.cnt[j] = 0;
     }
 }
 
 // ------------------------------------------------------------------ finalize
-struct FinParams {
+struct FinItem {
     int64_t J, N;
     int L, k, C, kt, mode, sortcap;
     float cE;
+    int ldy, ldx;
     const float* y;
-    int ldy;
     const float* x;
-    int ldx;
     const float* ynorm;
     float* keys;
     int32_t* idx;
     int32_t* cnt;
     const float* thr;
-    int32_t* status;
     int32_t* out_idx;
     float* out_dist;
+    float w[MAXL];
+};
+
+struct BatchFin {
+    FinItem item[MAX_ITEMS];
+    int64_t v_prefix[MAX_ITEMS + 1];
+    int n_items;
+    int sortcap;                 // largest sortcap of the batch (shared-memory sizing)
+    int32_t* status;
 };
 
 // Exact fp32 distance sum_l w_l (y_l - x_l)^2 in a fixed order (y in shared memory).
-__device__ __forceinline__ float exact_dist(const float* ys, const float* x, int L, const Weights& W) {
+__device__ __forceinline__ float exact_dist(const float* ys, const float* x, int L, const float* w) {
     const float4* xr = (const float4*)x;
     float d = 0.0f;
     int l = 0;
     for (; l + 4 <= L; l += 4) {
         const float4 xv = __ldg(xr + (l >> 2));
         const float e0 = ys[l] - xv.x, e1 = ys[l + 1] - xv.y, e2 = ys[l + 2] - xv.z, e3 = ys[l + 3] - xv.w;
-        d = fmaf(W.w[l] * e0, e0, d);
-        d = fmaf(W.w[l + 1] * e1, e1, d);
-        d = fmaf(W.w[l + 2] * e2, e2, d);
-        d = fmaf(W.w[l + 3] * e3, e3, d);
+        d = fmaf(w[l] * e0, e0, d);
+        d = fmaf(w[l + 1] * e1, e1, d);
+        d = fmaf(w[l + 2] * e2, e2, d);
+        d = fmaf(w[l + 3] * e3, e3, d);
     }
     for (; l < L; ++l) {
         const float e = ys[l] - x[l];
-        d = fmaf(W.w[l] * e, e, d);
+        d = fmaf(w[l] * e, e, d);
     }
     return d;
 }
 
 // exact_dist for two rows at once (same operation order), loads interleaved.
-__device__ __forceinline__ void exact_dist2(const float* ys, const float* xa, const float* xb, int L, const Weights& W,
+__device__ __forceinline__ void exact_dist2(const float* ys, const float* xa, const float* xb, int L, const float* w,
                                             float& da, float& db) {
     const float4* ra = (const float4*)xa;
     const float4* rb = (const float4*)xb;
@@ -583,42 +712,46 @@ __device__ __forceinline__ void exact_dist2(const float* ys, const float* xa, co
         const float4 va = __ldg(ra + (l >> 2));
         const float4 vb = __ldg(rb + (l >> 2));
         float e = ys[l] - va.x;
-        a = fmaf(W.w[l] * e, e, a);
+        a = fmaf(w[l] * e, e, a);
         e = ys[l + 1] - va.y;
-        a = fmaf(W.w[l + 1] * e, e, a);
+        a = fmaf(w[l + 1] * e, e, a);
         e = ys[l + 2] - va.z;
-        a = fmaf(W.w[l + 2] * e, e, a);
+        a = fmaf(w[l + 2] * e, e, a);
         e = ys[l + 3] - va.w;
-        a = fmaf(W.w[l + 3] * e, e, a);
+        a = fmaf(w[l + 3] * e, e, a);
         e = ys[l] - vb.x;
-        b = fmaf(W.w[l] * e, e, b);
+        b = fmaf(w[l] * e, e, b);
         e = ys[l + 1] - vb.y;
-        b = fmaf(W.w[l + 1] * e, e, b);
+        b = fmaf(w[l + 1] * e, e, b);
         e = ys[l + 2] - vb.z;
-        b = fmaf(W.w[l + 2] * e, e, b);
+        b = fmaf(w[l + 2] * e, e, b);
         e = ys[l + 3] - vb.w;
-        b = fmaf(W.w[l + 3] * e, e, b);
+        b = fmaf(w[l + 3] * e, e, b);
     }
     for (; l < L; ++l) {
         float e = ys[l] - xa[l];
-        a = fmaf(W.w[l] * e, e, a);
+        a = fmaf(w[l] * e, e, a);
         e = ys[l] - xb[l];
-        b = fmaf(W.w[l] * e, e, b);
+        b = fmaf(w[l] * e, e, b);
     }
     da = a;
     db = b;
 }
 
 // status[1]: voxels resolved by the exact scan; [2]: tie overflow; [3]: uncertified (bf16 mode)
-__global__ void k_finalize(FinParams P, Weights W) {
+__global__ void k_finalize(const __grid_constant__ BatchFin B) {
     extern __shared__ __align__(16) uint8_t fsm[];
     const int warps = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t* hist = (uint32_t*)fsm + wid * 256;
     float* ys = (float*)(fsm + warps * 1024) + wid * MAXL;
-    unsigned long long* sbuf = (unsigned long long*)(fsm + warps * 1024 + warps * MAXL * 4) + (size_t)wid * P.sortcap;
-    const int64_t j = (int64_t)blockIdx.x * warps + wid;
-    if (j >= P.J) return;
+    unsigned long long* sbuf = (unsigned long long*)(fsm + warps * 1024 + warps * MAXL * 4) + (size_t)wid * B.sortcap;
+    const int64_t g = (int64_t)blockIdx.x * warps + wid;
+    if (g >= B.v_prefix[B.n_items]) return;
+    int it = 0;
+    while (it + 1 < B.n_items && g >= B.v_prefix[it + 1]) ++it;
+    const FinItem& P = B.item[it];
+    const int64_t j = g - B.v_prefix[it];
     float* kj = P.keys + j * P.C;
     int32_t* ij = P.idx + j * P.C;
     const int raw = P.cnt[j];
@@ -640,11 +773,11 @@ __global__ void k_finalize(FinParams P, Weights W) {
         for (; i + 32 < cnt; i += 64) {
             const int32_t n0 = ij[i], n1 = ij[i + 32];
             float d0, d1;
-            exact_dist2(ys, P.x + (int64_t)n0 * P.ldx, P.x + (int64_t)n1 * P.ldx, P.L, W, d0, d1);
+            exact_dist2(ys, P.x + (int64_t)n0 * P.ldx, P.x + (int64_t)n1 * P.ldx, P.L, P.w, d0, d1);
             kj[i] = d0;
             kj[i + 32] = d1;
         }
-        if (i < cnt) kj[i] = exact_dist(ys, P.x + (int64_t)ij[i] * P.ldx, P.L, W);
+        if (i < cnt) kj[i] = exact_dist(ys, P.x + (int64_t)ij[i] * P.ldx, P.L, P.w);
         __syncwarp();
         // 3. exact k-th distance and the certificate
         bool cert = false;
@@ -659,19 +792,18 @@ __global__ void k_finalize(FinParams P, Weights W) {
             cert = T_out >= 2.9e38f || T_out >= need;
         }
         if (!cert) {
-            if (P.mode == ABC_FP32) scan = true;
-            else if (lane == 0) atomicAdd(&P.status[3], 1);
+            if (P.mode == ABC_FP32 || cnt < P.k) scan = true;
+            else if (lane == 0) atomicAdd(&B.status[3], 1);
         }
-        if (!scan && cnt < P.k) K = 0xFFFFFFFFu;
     }
     if (scan) {
         // exact fp32 scan of every draw (candidate list rebuilt with exact keys)
-        if (lane == 0) atomicAdd(&P.status[1], 1);
+        if (lane == 0) atomicAdd(&B.status[1], 1);
         cnt = 0;
         float thr = __int_as_float(0x7F800000);
         for (int64_t base = 0; base < P.N; base += 32) {
             const int64_t n = base + lane;
-            const float d = n < P.N ? exact_dist(ys, P.x + n * P.ldx, P.L, W) : __int_as_float(0x7F800000);
+            const float d = n < P.N ? exact_dist(ys, P.x + n * P.ldx, P.L, P.w) : __int_as_float(0x7F800000);
             const bool take = n < P.N && d <= thr;
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
             if (take) {
@@ -693,9 +825,9 @@ __global__ void k_finalize(FinParams P, Weights W) {
     }
     // 4. keep everything at or below the exact k-th distance, sort by (distance, index)
     if (cnt > P.k) {
-        const int g = warp_compact(kj, ij, cnt, K, P.sortcap, lane);
-        if (g > P.sortcap && lane == 0) atomicAdd(&P.status[2], 1);
-        cnt = g < P.sortcap ? g : P.sortcap;
+        const int gq = warp_compact(kj, ij, cnt, K, P.sortcap, lane);
+        if (gq > P.sortcap && lane == 0) atomicAdd(&B.status[2], 1);
+        cnt = gq < P.sortcap ? gq : P.sortcap;
     }
     int n2 = 32;
     while (n2 < cnt) n2 <<= 1;
@@ -709,9 +841,16 @@ __global__ void k_finalize(FinParams P, Weights W) {
     }
 }
 
+// Kernel parameter blocks must fit the 32 KB parameter space.
+static_assert(sizeof(BatchTc) <= 32000, "BatchTc exceeds the kernel parameter space");
+static_assert(sizeof(BatchFin) <= 32000, "BatchFin exceeds the kernel parameter space");
+static_assert(sizeof(BatchPilot) <= 32000, "BatchPilot exceeds the kernel parameter space");
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
+int g_last_resident = 0;     // residency of the last configured fused-kernel variant
+int64_t g_last_grid = 0;     // grid of the last fused-kernel launch
 
 int get_encoder() {
     if (g_encode) return ABC_OK;
@@ -726,10 +865,12 @@ int get_encoder() {
     return ABC_OK;
 }
 
-int make_tmap(CUtensorMap* m, void* base, int64_t rows, int Kp, int row_step = 1) {
+// Rows of Kp bf16 (128-byte swizzle), box {64, box_rows}; row_step > 1 gives a
+// view of every row_step-th row (pilot passes).
+int make_tmap(CUtensorMap* m, void* base, int64_t rows, int Kp, int box_rows, int64_t row_step) {
     const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2 * row_step};
-    const cuuint32_t box[2] = {(cuuint32_t)KBLK, (cuuint32_t)BM};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2 * (cuuint64_t)row_step};
+    const cuuint32_t box[2] = {(cuuint32_t)KBLK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -741,40 +882,85 @@ int make_tmap(CUtensorMap* m, void* base, int64_t rows, int Kp, int row_step = 1
     return ABC_OK;
 }
 
-template <int NKB>
-constexpr int stages_for() { return NKB == 1 ? 4 : (NKB == 2 ? 4 : 3); }
-
-template <int NKB>
-size_t tc_smem_bytes() {
-    return 1024 + (size_t)NKB * KBLK_BYTES * (1 + stages_for<NKB>()) + 4 * 32 * STAGE_LD * 4 + 4 * 256 * 4 +
-           (2 * stages_for<NKB>() + 8) * 8;
+constexpr int stages_for(int nkb, int bn) {
+    return nkb == 1 ? 4 : (nkb == 2 ? (bn == 128 ? 4 : 3) : (bn == 128 ? 3 : 4));
 }
 
-template <int NKB, bool DUMP>
-int launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const TcParams& P, int64_t grid, cudaStream_t s) {
-    constexpr int S = stages_for<NKB>();
-    const size_t smem = tc_smem_bytes<NKB>();
+size_t tc_smem_bytes(int nkb, int bn) {
+    const int S = stages_for(nkb, bn);
+    return 1024 + (size_t)nkb * A_KBLK_BYTES + (size_t)S * nkb * bn * KBLK * 2 + 4 * 32 * STAGE_LD * 4 + 4 * 256 * 4 +
+           (2 * S + 14) * 8;
+}
+
+int num_sms() {
+    static int sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!sms[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        sms[dev] = v;
+    }
+    return sms[dev];
+}
+
+template <int NKB, int BN, bool DUMP>
+int launch_tc(const BatchTc& P, int ctas_per_sm, cudaStream_t s) {
+    constexpr int S = stages_for(NKB, BN);
+    const size_t smem = tc_smem_bytes(NKB, BN);
     static bool configured = false;
+    static int max_resident = 1;
     if (!configured) {
-        VPET_CUDA(cudaFuncSetAttribute(k_tc_topk<NKB, S, DUMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        VPET_CUDA(cudaFuncSetAttribute(k_tc_topk<NKB, S, BN, DUMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // all of the unified L1 / shared storage as shared memory, so that the
+        // residency the tuning asks for is actually available
+        VPET_CUDA(cudaFuncSetAttribute(k_tc_topk<NKB, S, BN, DUMP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared));
+        // residency from the limits that apply: shared memory, registers, TMEM columns
+        cudaFuncAttributes fa;
+        VPET_CUDA(cudaFuncGetAttributes(&fa, k_tc_topk<NKB, S, BN, DUMP>));
+        int dev = 0, smem_sm = 0, resv = 0;
+        VPET_CUDA(cudaGetDevice(&dev));
+        VPET_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        VPET_CUDA(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+        const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + resv);
+        const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+        const int by_regs = 65536 / (regs_warp * (TC_THREADS / 32));
+        const int by_tmem = 512 / (2 * BN);
+        max_resident = by_smem < by_regs ? by_smem : by_regs;
+        if (max_resident > by_tmem) max_resident = by_tmem;
+        if (max_resident < 1) max_resident = 1;
+        g_last_resident = max_resident;
         configured = true;
     }
-    k_tc_topk<NKB, S, DUMP><<<(unsigned)grid, TC_THREADS, smem, s>>>(ta, tb, P);
+    const int per_sm = ctas_per_sm < max_resident ? ctas_per_sm : max_resident;
+    const int64_t total = P.vt_prefix[P.n_items];
+    int64_t grid = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+    if (grid > total) grid = total;
+    if (grid < 1) return ABC_OK;
+    g_last_grid = grid;
+    k_tc_topk<NKB, S, BN, DUMP><<<(unsigned)grid, TC_THREADS, smem, s>>>(P);
     VPET_LAUNCH_CHECK();
     return ABC_OK;
 }
 
 template <bool DUMP>
-int dispatch_tc(int nkb, const CUtensorMap& ta, const CUtensorMap& tb, const TcParams& P, int64_t grid,
-                cudaStream_t s) {
-    switch (nkb) {
-        case 1: return launch_tc<1, DUMP>(ta, tb, P, grid, s);
-        case 2: return launch_tc<2, DUMP>(ta, tb, P, grid, s);
-        case 3: return launch_tc<3, DUMP>(ta, tb, P, grid, s);
-        default:
-            vpet::set_error("unsupported K-block count %d", nkb);
-            return ABC_ERR_UNSUPPORTED;
+int dispatch_tc(int nkb, int bn, const BatchTc& P, int ctas_per_sm, cudaStream_t s) {
+    if (bn == 128) {
+        switch (nkb) {
+            case 1: return launch_tc<1, 128, DUMP>(P, ctas_per_sm, s);
+            case 2: return launch_tc<2, 128, DUMP>(P, ctas_per_sm, s);
+            case 3: return launch_tc<3, 128, DUMP>(P, ctas_per_sm, s);
+        }
+    } else if (!DUMP && bn == 64) {
+        switch (nkb) {
+            case 1: return launch_tc<1, 64, false>(P, ctas_per_sm, s);
+            case 2: return launch_tc<2, 64, false>(P, ctas_per_sm, s);
+            case 3: return launch_tc<3, 64, false>(P, ctas_per_sm, s);
+        }
     }
+    vpet::set_error("unsupported tile shape (K-blocks %d, BN %d)", nkb, bn);
+    return ABC_ERR_UNSUPPORTED;
 }
 
 float error_coef(const Layout& lay) {
@@ -788,136 +974,303 @@ float error_coef(const Layout& lay) {
     return split + (float)(3 * lay.Kp + lay.L + 16) * 0x1p-24f;
 }
 
-int validate(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w, int k,
-             int mode) {
-    VPET_ARG(J >= 1 && N >= 1, "abc_discrepancy_topk: J and N must be >= 1");
-    VPET_ARG(N < ((int64_t)1 << 31), "abc_discrepancy_topk: N must be < 2^31");
-    VPET_ARG(L >= 1 && L <= 61, "abc_discrepancy_topk: L must be in 1..61 (got %d)", L);
-    VPET_ARG(k >= 1 && k <= 2048 && k <= N, "abc_discrepancy_topk: need 1 <= k <= min(N, 2048)");
-    VPET_ARG(mode == ABC_FP32 || mode == ABC_BF16_RESCORE, "abc_discrepancy_topk: unknown precision %d", mode);
-    VPET_ARG(y && x && w, "abc_discrepancy_topk: null pointer");
-    VPET_ARG(ldy >= L && ldx >= L && ldx % 4 == 0 && ldy % 4 == 0,
-             "abc_discrepancy_topk: ldy, ldx must be >= L and multiples of 4");
-    VPET_ARG(((uintptr_t)y & 15) == 0 && ((uintptr_t)x & 15) == 0, "abc_discrepancy_topk: y, x must be 16-byte aligned");
+// One scan of a batch as the host sees it.
+struct ScanSpec {
+    const float* y;
+    int64_t J;
+    int ldy;
+    const float* x;
+    int64_t N;
+    int ldx;
+    int L;
+    const float* w;
+    int k;
+    int32_t* idx;
+    float* dist;
+};
+
+int validate(const ScanSpec& c, int mode) {
+    VPET_ARG(c.J >= 1 && c.N >= 1, "discrepancy/top-k: J and N must be >= 1");
+    VPET_ARG(c.N < ((int64_t)1 << 31), "discrepancy/top-k: N must be < 2^31");
+    VPET_ARG(c.L >= 1 && c.L <= 61, "discrepancy/top-k: L must be in 1..61 (got %d)", c.L);
+    VPET_ARG(c.k >= 1 && c.k <= 2048 && c.k <= c.N, "discrepancy/top-k: need 1 <= k <= min(N, 2048)");
+    VPET_ARG(mode == ABC_FP32 || mode == ABC_BF16_RESCORE, "discrepancy/top-k: unknown precision %d", mode);
+    VPET_ARG(c.y && c.x && c.w, "discrepancy/top-k: null pointer");
+    VPET_ARG(c.ldy >= c.L && c.ldx >= c.L && c.ldx % 4 == 0 && c.ldy % 4 == 0,
+             "discrepancy/top-k: ldy, ldx must be >= L and multiples of 4");
+    VPET_ARG(((uintptr_t)c.y & 15) == 0 && ((uintptr_t)c.x & 15) == 0, "discrepancy/top-k: y, x must be 16-byte aligned");
     bool any = false;
-    for (int l = 0; l < L; ++l) {
-        VPET_ARG(w[l] >= 0.0f && w[l] == w[l], "abc_discrepancy_topk: weights must be >= 0");
-        any |= w[l] > 0.0f;
+    for (int l = 0; l < c.L; ++l) {
+        VPET_ARG(c.w[l] >= 0.0f && c.w[l] == c.w[l], "discrepancy/top-k: weights must be >= 0");
+        any |= c.w[l] > 0.0f;
     }
-    VPET_ARG(any, "abc_discrepancy_topk: all weights are zero");
+    VPET_ARG(any, "discrepancy/top-k: all weights are zero");
     return ABC_OK;
 }
 
-int run_topk(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w, int k,
-             int mode, void* ws, size_t ws_bytes, int32_t* out_idx, float* out_dist, float* dump, int64_t ld_dump,
-             cudaStream_t s) {
-    const Layout lay = make_layout(J, N, L, k, mode);
-    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < lay.total) {
-        vpet::set_error("abc_discrepancy_topk: workspace needs %zu bytes, 256-aligned (got %zu)", lay.total, ws_bytes);
+int check_tuning(const Tuning& t) {
+    VPET_ARG(t.bn == 64 || t.bn == 128, "tuning: bn must be 64 or 128");
+    VPET_ARG(t.ctas_per_sm >= 1 && t.ctas_per_sm <= 4, "tuning: ctas_per_sm must be in 1..4");
+    VPET_ARG(t.pilot_stride == 8 || t.pilot_stride == 16 || t.pilot_stride == 32, "tuning: pilot_stride must be 8, 16 or 32");
+    VPET_ARG(t.pilot_factor >= 1.25f && t.pilot_factor <= 4.0f, "tuning: pilot_factor must be in [1.25, 4]");
+    return ABC_OK;
+}
+
+// Workspace of a batch: a 256-byte status block, then one section per scan.
+struct BatchLayout {
+    int n;
+    Layout lay[MAX_ITEMS];
+    size_t off[MAX_ITEMS];
+    size_t total;
+};
+
+void make_batch_layout(const ScanSpec* sc, int n, int mode, const Tuning& tu, BatchLayout* B) {
+    B->n = n;
+    int kp = 0;
+    for (int i = 0; i < n; ++i) {
+        B->lay[i] = make_layout(sc[i].J, sc[i].N, sc[i].L, sc[i].k, mode, tu);
+        if (B->lay[i].Kp > kp) kp = B->lay[i].Kp;
+    }
+    size_t o = 256;
+    for (int i = 0; i < n; ++i) {
+        // one K-width per launch: pad every scan to the widest
+        if (B->lay[i].Kp != kp) {
+            Layout& L = B->lay[i];
+            const int64_t Jp = L.Jp, Np = L.Np;
+            const size_t grow_a = (size_t)Jp * (kp - L.Kp) * 2, grow_b = (size_t)Np * (kp - L.Kp) * 2;
+            L.Kp = kp;
+            L.nkb = kp / KBLK;
+            L.off_b += align256(grow_a);
+            L.off_keys += align256(grow_a) + align256(grow_b);
+            L.off_idx += align256(grow_a) + align256(grow_b);
+            L.off_cnt += align256(grow_a) + align256(grow_b);
+            L.off_thr += align256(grow_a) + align256(grow_b);
+            L.off_thr0 += align256(grow_a) + align256(grow_b);
+            L.total += align256(grow_a) + align256(grow_b);
+        }
+        B->off[i] = o;
+        o = align256(o + B->lay[i].total);
+    }
+    B->total = o;
+}
+
+int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws, size_t ws_bytes, float* dump,
+              int64_t ld_dump, cudaStream_t s) {
+    VPET_ARG(n >= 1 && n <= MAX_ITEMS, "batch: 1..%d scans per call (got %d)", MAX_ITEMS, n);
+    Tuning tu = tu_in;
+    if (dump) tu.bn = 128;       // the key dump is only instantiated for 128-draw tiles
+    int rc = check_tuning(tu);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i)
+        if ((rc = validate(sc[i], mode))) return rc;
+    BatchLayout BL;
+    make_batch_layout(sc, n, mode, tu, &BL);
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < BL.total) {
+        vpet::set_error("discrepancy/top-k: workspace needs %zu bytes, 256-aligned (got %zu)", BL.total, ws_bytes);
         return ABC_ERR_WORKSPACE;
     }
-    if (!dump) VPET_ARG(out_idx && out_dist, "abc_discrepancy_topk: null output");
-    int rc = get_encoder();
-    if (rc) return rc;
-    uint8_t* base = (uint8_t*)ws;
-    float* mu = (float*)(base + lay.off_mu);
-    float* part = (float*)(base + lay.off_part);
-    float* ynorm = (float*)(base + lay.off_ynorm);
-    __nv_bfloat16* A = (__nv_bfloat16*)(base + lay.off_a);
-    __nv_bfloat16* B = (__nv_bfloat16*)(base + lay.off_b);
-    int32_t* status = (int32_t*)(base + lay.off_status);
-    int32_t* cnt = (int32_t*)(base + lay.off_cnt);
-    Weights W;
-    memset(&W, 0, sizeof W);
-    for (int l = 0; l < L; ++l) {
-        W.w[l] = w[l];
-        W.sw[l] = sqrtf(w[l]);
-    }
-    VPET_CUDA(cudaMemsetAsync(status, 0, 64 * sizeof(int32_t), s));
-    VPET_CUDA(cudaMemsetAsync(cnt, 0, (size_t)lay.Jp * sizeof(int32_t), s));
-    k_colmean_part<<<lay.npart, 256, 0, s>>>(y, J, ldy, L, part, lay.npart);
-    VPET_LAUNCH_CHECK();
-    k_colmean_final<<<1, MAXL, 0, s>>>(part, lay.npart, J, mu);
-    VPET_LAUNCH_CHECK();
-    k_pack_y<<<(unsigned)vpet_ceil_div(lay.Jp, 8), 256, 0, s>>>(y, J, lay.Jp, ldy, L, lay.Kp, mode, W, mu, A, ynorm);
-    VPET_LAUNCH_CHECK();
-    k_pack_x<<<(unsigned)vpet_ceil_div(lay.Np, 8), 256, 0, s>>>(x, N, lay.Np, ldx, L, lay.Kp, mode, W, mu, B);
-    VPET_LAUNCH_CHECK();
-    CUtensorMap ta, tb;
-    if ((rc = make_tmap(&ta, A, lay.Jp, lay.Kp))) return rc;
-    if ((rc = make_tmap(&tb, B, lay.Np, lay.Kp))) return rc;
-    TcParams P;
-    P.J = J;
-    P.N = N;
-    P.ntiles = (int)(lay.Np / BN);
-    P.C = lay.C;
-    P.lim = lay.C;
-    P.kt = lay.kt;
-    P.cap = lay.cap;
-    P.keys = (float*)(base + lay.off_keys);
-    P.idx = (int32_t*)(base + lay.off_idx);
-    P.cnt = cnt;
-    P.thr = (float*)(base + lay.off_thr);
-    P.status = status;
-    P.dump = dump;
-    P.ld_dump = ld_dump;
-    const int64_t grid = lay.Jp / BM;
-    if (dump) return dispatch_tc<true>(lay.nkb, ta, tb, P, grid, s);
-    P.thr0 = nullptr;
-    float* thr0 = (float*)(base + lay.off_thr0);
-    for (int lv = lay.nlev - 1; lv >= 0; --lv) {
-        // pilot pass over every lev_stride-th draw (strided tensor map, no copy)
-        const int64_t st = lay.lev_stride[lv];
-        const int64_t Ns = N / st;
-        const int r = lay.lev_rank[lv];
-        CUtensorMap tp;
-        if ((rc = make_tmap(&tp, B, Ns, lay.Kp, (int)st))) return rc;
-        TcParams Q = P;
-        Q.N = Ns;
-        Q.ntiles = (int)vpet_ceil_div(Ns, BN);
-        Q.kt = r;
-        Q.cap = r + (r / 4 > 64 ? r / 4 : 64);
-        Q.lim = (int)(4 * (int64_t)r + 2 * BN < lay.C ? 4 * (int64_t)r + 2 * BN : lay.C);
-        if ((rc = dispatch_tc<false>(lay.nkb, ta, tp, Q, grid, s))) return rc;
-        k_pilot_threshold<<<(unsigned)vpet_ceil_div(J, 8), 256, 0, s>>>(P.keys, cnt, lay.C, r, J, thr0);
+    if (!dump)
+        for (int i = 0; i < n; ++i) VPET_ARG(sc[i].idx && sc[i].dist, "discrepancy/top-k: null output");
+    if ((rc = get_encoder())) return rc;
+    uint8_t* wsb = (uint8_t*)ws;
+    int32_t* status = (int32_t*)wsb;
+    unsigned long long* counters = (unsigned long long*)(wsb + 64);   // one work counter per fused launch
+    VPET_CUDA(cudaMemsetAsync(status, 0, 256, s));
+    const int nkb = BL.lay[0].nkb;
+
+    // per scan: centring, packing, tensor maps
+    BatchTc T;                 // kernel parameter blocks (copied into each launch)
+    BatchPilot PB;
+    BatchFin F;
+    struct Ptrs {
+        float *mu, *part, *ynorm, *keys, *thr, *thr0;
+        __nv_bfloat16 *A, *B;
+        int32_t *idx, *cnt;
+    } ptr[MAX_ITEMS];
+    for (int i = 0; i < n; ++i) {
+        const Layout& L = BL.lay[i];
+        uint8_t* base = wsb + BL.off[i];
+        Ptrs& p = ptr[i];
+        p.mu = (float*)(base + L.off_mu);
+        p.part = (float*)(base + L.off_part);
+        p.ynorm = (float*)(base + L.off_ynorm);
+        p.A = (__nv_bfloat16*)(base + L.off_a);
+        p.B = (__nv_bfloat16*)(base + L.off_b);
+        p.keys = (float*)(base + L.off_keys);
+        p.idx = (int32_t*)(base + L.off_idx);
+        p.cnt = (int32_t*)(base + L.off_cnt);
+        p.thr = (float*)(base + L.off_thr);
+        p.thr0 = (float*)(base + L.off_thr0);
+        Weights W;
+        memset(&W, 0, sizeof W);
+        for (int l = 0; l < L.L; ++l) {
+            W.w[l] = sc[i].w[l];
+            W.sw[l] = sqrtf(sc[i].w[l]);
+        }
+        VPET_CUDA(cudaMemsetAsync(p.cnt, 0, (size_t)L.Jp * sizeof(int32_t), s));
+        k_colmean_part<<<L.npart, 256, 0, s>>>(sc[i].y, L.J, sc[i].ldy, L.L, p.part, L.npart);
         VPET_LAUNCH_CHECK();
-        P.thr0 = thr0;
+        k_colmean_final<<<1, MAXL, 0, s>>>(p.part, L.npart, L.J, p.mu);
+        VPET_LAUNCH_CHECK();
+        k_pack_y<<<(unsigned)vpet_ceil_div(L.Jp, 8), 256, 0, s>>>(sc[i].y, L.J, L.Jp, sc[i].ldy, L.L, L.Kp, mode, W,
+                                                                  p.mu, p.A, p.ynorm);
+        VPET_LAUNCH_CHECK();
+        k_pack_x<<<(unsigned)vpet_ceil_div(L.Np, 8), 256, 0, s>>>(sc[i].x, L.N, L.Np, sc[i].ldx, L.L, L.Kp, mode, W,
+                                                                  p.mu, p.B);
+        VPET_LAUNCH_CHECK();
     }
+    // work order: costliest scans first (longest-processing-time round robin)
+    int order[MAX_ITEMS];
+    for (int i = 0; i < n; ++i) order[i] = i;
+    for (int a = 1; a < n; ++a) {
+        const int v = order[a];
+        const double cv = (double)BL.lay[v].Jp * (double)BL.lay[v].N;
+        int b = a;
+        while (b > 0 && (double)BL.lay[order[b - 1]].Jp * (double)BL.lay[order[b - 1]].N < cv) {
+            order[b] = order[b - 1];
+            --b;
+        }
+        order[b] = v;
+    }
+    auto fill_item = [&](ItemTc& I, int i, int64_t stride, int kt, int lim, const float* thr0) -> int {
+        const Layout& L = BL.lay[i];
+        const Ptrs& p = ptr[i];
+        int r;
+        if ((r = make_tmap(&I.tmA, p.A, L.Jp, L.Kp, BM, 1))) return r;
+        const int64_t Nn = L.N / stride;
+        if ((r = make_tmap(&I.tmB, p.B, stride == 1 ? L.Np : Nn, L.Kp, tu.bn, stride))) return r;
+        I.J = L.J;
+        I.N = stride == 1 ? L.N : Nn;
+        I.keys = p.keys;
+        I.idx = p.idx;
+        I.cnt = p.cnt;
+        I.thr = p.thr;
+        I.thr0 = thr0;
+        I.ntiles = (int)vpet_ceil_div(I.N, tu.bn);
+        I.C = L.C;
+        I.kt = kt;
+        I.cap = kt + (kt / 4 > 64 ? kt / 4 : 64);
+        I.lim = lim;
+        return ABC_OK;
+    };
+    int maxlev = 0;
+    for (int i = 0; i < n; ++i) maxlev = BL.lay[i].nlev > maxlev ? BL.lay[i].nlev : maxlev;
+    if (dump) maxlev = 0;
+    // pilot passes, coarsest level first
+    for (int lv = maxlev - 1; lv >= 0; --lv) {
+        memset(&T, 0, sizeof T);
+        memset(&PB, 0, sizeof PB);
+        int m = 0;
+        for (int oi = 0; oi < n; ++oi) {
+            const int i = order[oi];
+            const Layout& L = BL.lay[i];
+            if (L.nlev <= lv) continue;
+            const int r = L.lev_rank[lv];
+            const int lim = (int)(4 * (int64_t)r + 256 < L.C ? 4 * (int64_t)r + 256 : L.C);
+            if ((rc = fill_item(T.item[m], i, L.lev_stride[lv], r, lim, lv + 1 < L.nlev ? ptr[i].thr0 : nullptr)))
+                return rc;
+            T.vt_prefix[m + 1] = T.vt_prefix[m] + L.Jp / BM;
+            PB.item[m] = PilotItem{ptr[i].keys, ptr[i].cnt, ptr[i].thr0, L.J, L.C, r};
+            PB.v_prefix[m + 1] = PB.v_prefix[m] + L.J;
+            ++m;
+        }
+        T.n_items = m;
+        T.status = status;
+        T.counter = counters + (lv + 1);
+        PB.n_items = m;
+        if ((rc = dispatch_tc<false>(nkb, tu.bn, T, tu.ctas_per_sm, s))) return rc;
+        k_pilot_threshold<<<(unsigned)vpet_ceil_div(PB.v_prefix[m], 8), 256, 0, s>>>(PB);
+        VPET_LAUNCH_CHECK();
+    }
+    // main pass
+    memset(&T, 0, sizeof T);
+    for (int oi = 0; oi < n; ++oi) {
+        const int i = order[oi];
+        const Layout& L = BL.lay[i];
+        if ((rc = fill_item(T.item[oi], i, 1, L.kt, L.C, L.nlev > 0 ? ptr[i].thr0 : nullptr))) return rc;
+        T.vt_prefix[oi + 1] = T.vt_prefix[oi] + L.Jp / BM;
+    }
+    T.n_items = n;
+    T.status = status;
+    T.counter = counters;
+    T.dump = dump;
+    T.ld_dump = ld_dump;
+    if (dump) return dispatch_tc<true>(nkb, 128, T, tu.ctas_per_sm, s);
     if (g_prof_start) VPET_CUDA(cudaEventRecord(g_prof_start, s));
-    if ((rc = dispatch_tc<false>(lay.nkb, ta, tb, P, grid, s))) return rc;
+    if ((rc = dispatch_tc<false>(nkb, tu.bn, T, tu.ctas_per_sm, s))) return rc;
     if (g_prof_stop) VPET_CUDA(cudaEventRecord(g_prof_stop, s));
-    FinParams F;
-    F.J = J;
-    F.N = N;
-    F.L = L;
-    F.k = k;
-    F.C = lay.C;
-    F.kt = lay.kt;
-    F.mode = mode;
-    F.sortcap = lay.sortcap;
-    F.cE = error_coef(lay);
-    F.y = y;
-    F.ldy = ldy;
-    F.x = x;
-    F.ldx = ldx;
-    F.ynorm = ynorm;
-    F.keys = P.keys;
-    F.idx = P.idx;
-    F.cnt = cnt;
-    F.thr = P.thr;
+    // finalize
+    memset(&F, 0, sizeof F);
+    int sortcap = 64;
+    for (int i = 0; i < n; ++i) {
+        const Layout& L = BL.lay[i];
+        FinItem& f = F.item[i];
+        f.J = L.J;
+        f.N = L.N;
+        f.L = L.L;
+        f.k = L.k;
+        f.C = L.C;
+        f.kt = L.kt;
+        f.mode = mode;
+        f.sortcap = L.sortcap;
+        f.cE = error_coef(L);
+        f.y = sc[i].y;
+        f.ldy = sc[i].ldy;
+        f.x = sc[i].x;
+        f.ldx = sc[i].ldx;
+        f.ynorm = ptr[i].ynorm;
+        f.keys = ptr[i].keys;
+        f.idx = ptr[i].idx;
+        f.cnt = ptr[i].cnt;
+        f.thr = ptr[i].thr;
+        f.out_idx = sc[i].idx;
+        f.out_dist = sc[i].dist;
+        for (int l = 0; l < L.L; ++l) f.w[l] = sc[i].w[l];
+        F.v_prefix[i + 1] = F.v_prefix[i] + L.J;
+        if (L.sortcap > sortcap) sortcap = L.sortcap;
+    }
+    F.n_items = n;
+    F.sortcap = sortcap;
     F.status = status;
-    F.out_idx = out_idx;
-    F.out_dist = out_dist;
     int warps = 8;
-    while (warps > 1 && (size_t)warps * lay.sortcap * 8 > 64 * 1024) warps >>= 1;
-    const size_t fsmem = (size_t)warps * (1024 + MAXL * 4 + (size_t)lay.sortcap * 8);
+    while (warps > 1 && (size_t)warps * sortcap * 8 > 64 * 1024) warps >>= 1;
+    const size_t fsmem = (size_t)warps * (1024 + MAXL * 4 + (size_t)sortcap * 8);
     static size_t fin_configured = 0;
     if (fsmem > 48 * 1024 && fsmem > fin_configured) {
         VPET_CUDA(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
         fin_configured = fsmem;
     }
-    k_finalize<<<(unsigned)vpet_ceil_div(J, warps), warps * 32, fsmem, s>>>(F, W);
+    k_finalize<<<(unsigned)vpet_ceil_div(F.v_prefix[n], warps), warps * 32, fsmem, s>>>(F);
     VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}
+
+bool g_has_default = false;   // abc_set_default_tuning was called
+Tuning g_default_tuning = default_tuning(ABC_BF16_RESCORE);
+
+Tuning tuning_for(int mode) { return g_has_default ? g_default_tuning : default_tuning(mode); }
+
+ScanSpec single(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w, int k,
+                int32_t* idx, float* dist) {
+    return ScanSpec{y, J, ldy, x, N, ldx, L, w, k, idx, dist};
+}
+
+int to_tuning(const abc_tuning* t, int mode, Tuning* out) {
+    if (!t) {
+        *out = tuning_for(mode);
+        return ABC_OK;
+    }
+    *out = Tuning{t->bn, t->ctas_per_sm, t->pilot_stride, t->pilot_factor};
+    return check_tuning(*out);
+}
+
+int gather_scans(const abc_scan* scans, int n, ScanSpec* out) {
+    VPET_ARG(scans, "batch: null scan array");
+    VPET_ARG(n >= 1 && n <= MAX_ITEMS, "batch: 1..%d scans per call (got %d)", MAX_ITEMS, n);
+    for (int i = 0; i < n; ++i) {
+        const abc_scan& c = scans[i];
+        out[i] = ScanSpec{c.y_dev, c.J, c.ldy, c.x_dev, c.N, c.ldx, c.L, c.w_host, c.k, c.idx_dev, c.dist_dev};
+    }
     return ABC_OK;
 }
 
@@ -926,14 +1279,18 @@ int run_topk(const float* y, int64_t J, int ldy, const float* x, int64_t N, int 
 namespace vpet {
 
 size_t topk_workspace_bytes(int64_t J, int64_t N, int L, int k, int precision) {
-    return make_layout(J, N, L, k, precision).total;
+    ScanSpec c = single(nullptr, J, L, nullptr, N, L, L, nullptr, k, nullptr, nullptr);
+    BatchLayout* B = new BatchLayout;
+    make_batch_layout(&c, 1, precision, tuning_for(precision), B);
+    const size_t t = B->total;
+    delete B;
+    return t;
 }
 
 int topk_on_workspace(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w,
                       int k, int precision, void* ws, size_t ws_bytes, int32_t* idx, float* dist, cudaStream_t s) {
-    const int rc = validate(y, J, ldy, x, N, ldx, L, w, k, precision);
-    if (rc) return rc;
-    return run_topk(y, J, ldy, x, N, ldx, L, w, k, precision, ws, ws_bytes, idx, dist, nullptr, 0, s);
+    const ScanSpec c = single(y, J, ldy, x, N, ldx, L, w, k, idx, dist);
+    return run_batch(&c, 1, precision, g_default_tuning, ws, ws_bytes, nullptr, 0, s);
 }
 
 }  // namespace vpet
@@ -941,17 +1298,64 @@ int topk_on_workspace(const float* y, int64_t J, int ldy, const float* x, int64_
 extern "C" size_t abc_workspace_size(int64_t J, int64_t N, int32_t L, int32_t k, int32_t precision) {
     if (J < 1 || N < 1 || L < 1 || L > 61 || k < 1 || k > N || k > 2048) return 0;
     if (precision != ABC_FP32 && precision != ABC_BF16_RESCORE) return 0;
-    return make_layout(J, N, L, k, precision).total;
+    return vpet::topk_workspace_bytes(J, N, L, k, precision);
 }
 
 extern "C" int abc_discrepancy_topk(const float* y_dev, int64_t J, int32_t ldy, const float* x_dev, int64_t N,
                                     int32_t ldx, int32_t L, const float* w_host, int32_t k, int32_t precision,
                                     void* workspace, size_t ws_bytes, int32_t* idx_dev, float* dist_dev, void* stream) {
     vpet::clear_error();
-    const int rc = validate(y_dev, J, ldy, x_dev, N, ldx, L, w_host, k, precision);
+    return vpet::topk_on_workspace(y_dev, J, ldy, x_dev, N, ldx, L, w_host, k, precision, workspace, ws_bytes, idx_dev,
+                                   dist_dev, (cudaStream_t)stream);
+}
+
+extern "C" int abc_default_tuning(int32_t precision, abc_tuning* out) {
+    vpet::clear_error();
+    VPET_ARG(out, "abc_default_tuning: null pointer");
+    VPET_ARG(precision == ABC_FP32 || precision == ABC_BF16_RESCORE, "abc_default_tuning: unknown precision");
+    const Tuning t = tuning_for(precision);
+    out->bn = t.bn;
+    out->ctas_per_sm = t.ctas_per_sm;
+    out->pilot_stride = t.pilot_stride;
+    out->pilot_factor = t.pilot_factor;
+    return ABC_OK;
+}
+
+extern "C" int abc_set_default_tuning(const abc_tuning* t) {
+    vpet::clear_error();
+    Tuning tu;
+    const int rc = to_tuning(t, ABC_BF16_RESCORE, &tu);
     if (rc) return rc;
-    return run_topk(y_dev, J, ldy, x_dev, N, ldx, L, w_host, k, precision, workspace, ws_bytes, idx_dev, dist_dev,
-                    nullptr, 0, (cudaStream_t)stream);
+    g_has_default = t != nullptr;
+    if (t) g_default_tuning = tu;
+    return ABC_OK;
+}
+
+extern "C" size_t abc_batch_workspace_size(const abc_scan* scans, int32_t n_scans, int32_t precision) {
+    ScanSpec sp[MAX_ITEMS];
+    if (!scans || n_scans < 1 || n_scans > MAX_ITEMS) return 0;
+    if (precision != ABC_FP32 && precision != ABC_BF16_RESCORE) return 0;
+    for (int i = 0; i < n_scans; ++i) {
+        const abc_scan& c = scans[i];
+        if (c.J < 1 || c.N < 1 || c.L < 1 || c.L > 61 || c.k < 1 || c.k > c.N || c.k > 2048) return 0;
+        sp[i] = ScanSpec{c.y_dev, c.J, c.ldy, c.x_dev, c.N, c.ldx, c.L, c.w_host, c.k, c.idx_dev, c.dist_dev};
+    }
+    BatchLayout* B = new BatchLayout;
+    make_batch_layout(sp, n_scans, precision, tuning_for(precision), B);
+    const size_t t = B->total;
+    delete B;
+    return t;
+}
+
+extern "C" int abc_batch_discrepancy_topk(const abc_scan* scans, int32_t n_scans, int32_t precision,
+                                          const abc_tuning* tuning, void* workspace, size_t ws_bytes, void* stream) {
+    vpet::clear_error();
+    ScanSpec sp[MAX_ITEMS];
+    int rc = gather_scans(scans, n_scans, sp);
+    if (rc) return rc;
+    Tuning tu;
+    if ((rc = to_tuning(tuning, precision, &tu))) return rc;
+    return run_batch(sp, n_scans, precision, tu, workspace, ws_bytes, nullptr, 0, (cudaStream_t)stream);
 }
 
 extern "C" int abc_profile_events(void* start_event, void* stop_event) {
@@ -968,10 +1372,7 @@ extern "C" int abc_topk_status(const void* workspace, int32_t status_host[4], vo
     int32_t st[4];
     VPET_CUDA(cudaMemcpyAsync(st, workspace, sizeof st, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     VPET_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-    status_host[0] = st[0];
-    status_host[1] = st[1];
-    status_host[2] = st[2];
-    status_host[3] = st[3];
+    for (int i = 0; i < 4; ++i) status_host[i] = st[i];
     return ABC_OK;
 }
 
@@ -981,9 +1382,16 @@ extern "C" int abc_debug_gemm_keys(const float* y_dev, int64_t J, int32_t ldy, c
                                    int32_t ldx, int32_t L, const float* w_host, int32_t precision, void* workspace,
                                    size_t ws_bytes, float* dump_dev, int64_t ld_dump, void* stream) {
     vpet::clear_error();
-    const int rc = validate(y_dev, J, ldy, x_dev, N, ldx, L, w_host, 1, precision);
-    if (rc) return rc;
-    VPET_ARG(dump_dev && ld_dump >= vpet_round_up(N, BN), "abc_debug_gemm_keys: dump too small");
-    return run_topk(y_dev, J, ldy, x_dev, N, ldx, L, w_host, 1, precision, workspace, ws_bytes, nullptr, nullptr,
-                    dump_dev, ld_dump, (cudaStream_t)stream);
+    VPET_ARG(dump_dev && ld_dump >= vpet_round_up(N, 128), "abc_debug_gemm_keys: dump too small");
+    const ScanSpec c = single(y_dev, J, ldy, x_dev, N, ldx, L, w_host, 1, nullptr, nullptr);
+    return run_batch(&c, 1, precision, tuning_for(precision), workspace, ws_bytes, dump_dev, ld_dump,
+                     (cudaStream_t)stream);
+}
+
+extern "C" int abc_launch_info(int64_t* grid, int32_t* resident_per_sm) {
+    vpet::clear_error();
+    VPET_ARG(grid && resident_per_sm, "abc_launch_info: null pointer");
+    *grid = g_last_grid;
+    *resident_per_sm = g_last_resident;
+    return ABC_OK;
 }
