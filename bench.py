@@ -36,6 +36,8 @@ WORKLOADS = {
     "raclopride_lpntpet": "brain lp-ntPET vs MRTM: {J} voxels x ({n} MRTM + {n} lp-ntPET draws), 60 x 1-min frames, k={k}",
     "totalbody_fdg": "total-body FDG 2TCM irr vs rev: {J} voxels x ({n} + {n} draws), 29 frames, k={k}",
     "brain_fdg_2tcm": "2TCM-irr: {J} voxels x {n} draws, 22 frames, k={k}",
+    "batched": "{n} uneven scans: {J} voxels in total (log-uniform 1,000-500,000 per scan), 22-60 frames, 1-3 of "
+               "{{2TCM-irr, 2TCM-rev, MRTM}} per scan, 200,000-1,000,000 draws per model, k={k}; one CUDA graph",
 }
 
 
@@ -50,6 +52,9 @@ def parse():
     ap.add_argument("--voxels", type=int, default=None, help="override J (smaller runs)")
     ap.add_argument("--draws", type=int, default=None, help="override draws per model")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--voxel-scale", type=float, default=1.0, help="batched workload: scale voxel counts")
+    ap.add_argument("--draw-scale", type=float, default=1.0, help="batched workload: scale draw counts")
+    ap.add_argument("--scans", type=int, default=64, help="batched workload: number of scans")
     return ap.parse_args()
 
 
@@ -144,6 +149,124 @@ def cpu_baseline(W, seconds_budget=20.0):
             "pairs_per_s": W.J * W.N / total}
 
 
+# ------------------------------------------------------------------ batched uneven scans
+def run_batched(args, world, rank, local):
+    """Many scans per step: prior draws and simulation per scan, one batched
+    discrepancy + top-k (persistent fused kernel, autotuned launch), model
+    selection and summaries per scan, the whole step replayed from a CUDA graph."""
+    import torch
+    from paper_2603_14859_b300 import _lib, api, autotune, pipeline
+    from paper_2603_14859_b300 import synth as S
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    prec = _lib.ABC_FP32 if args.precision == "fp32" else _lib.ABC_BF16_RESCORE
+    plan = S.scan_plan(seed=1004 + 1000 * rank, n_scans=args.scans, voxel_scale=args.voxel_scale,
+                       draw_scale=args.draw_scale)
+    scans = [S.scan_workload(p) for p in plan]
+    bp = pipeline.BatchPipeline(scans, prec)
+    ys = [pipeline.make_y_gpu(W) for W in scans]
+    bp.set_inputs(ys)
+    for r in bp.runs:
+        r.simulate_draws()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bp.tuning = autotune.tune(bp)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    prof = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    for e in prof:
+        e.record(stream)
+    torch.cuda.synchronize()
+    api.profile_events(*prof)
+    l0 = api.launch_info()[2]
+    bp.capture()                                   # one eager warm-up step, then the captured step
+    launches_per_step = (api.launch_info()[2] - l0) // 2
+    for _ in range(args.warmup):
+        bp.replay()
+    torch.cuda.synchronize()
+    st = api.topk_status(bp.ws)
+    K = args.steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    tc = []
+    for _ in range(K):
+        bp.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tc.append(prof[0].elapsed_time(prof[1]))
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / K
+    api.profile_events(None, None)
+    # end to end: pinned host TACs in, model probabilities and summaries out, around each replay
+    y_host = [y.cpu().pin_memory() for y in ys]
+    outs = [(r.prob, r.pref, *r.summ) for r in bp.runs]
+    outs_host = [[torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in grp] for grp in outs]
+    h2d = sum(y.numel() * y.element_size() for y in y_host)
+    d2h = sum(o.numel() * o.element_size() for grp in outs_host for o in grp)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Ke = max(1, min(K, 3))
+    f0.record(stream)
+    for _ in range(Ke):
+        for yd, yh in zip(ys, y_host):
+            yd.copy_(yh, non_blocking=True)
+        bp.replay()
+        for grp_h, grp_d in zip(outs_host, outs):
+            for h, d in zip(grp_h, grp_d):
+                h.copy_(d, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / Ke
+    t = torch.tensor([ms, statistics.mean(tc), e2e_ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, tc_ms, e2e_ms = (float(v) for v in t)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    J = sum(W.J for W in scans)
+    pairs = sum(W.J * W.N for W in scans)
+    flops = sum(2.0 * W.L * W.J * W.N for W in scans)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    achieved = flops / (tc_ms / 1000.0) / 1e12
+    cfg = {"workload": WORKLOADS["batched"].format(n=len(scans), J=J, k=scans[0].k), "scans": len(scans),
+           "voxels_per_gpu": J, "pairs_per_gpu": pairs, "voxel_scale": args.voxel_scale,
+           "draw_scale": args.draw_scale, "precision": args.precision, "tuning": bp.tuning,
+           "autotune_s": tune_s, "l2": "inputs larger than L2",
+           "parallelism": f"voxel shards x{args.gpus}" if args.gpus > 1 else "single GPU"}
+    line = {
+        "metric": "voxels/s to posterior", "value": J * world / (ms / 1000.0), "unit": "voxels/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if prec == _lib.ABC_BF16_RESCORE else "bf16x3-split (fp32-exact)",
+        "data": "synthetic", "config": cfg, "pairs_per_s": pairs * world / (ms / 1000.0),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_tc_topk main pass (all scans, one persistent launch)",
+                     "kernel_ms": tc_ms, "algorithmic_flops_per_launch": flops,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"},
+        "e2e": {"value": J * world / (e2e_ms / 1000.0), "unit": "voxels/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * K,
+        "clocks": clk,
+        "topk_status": {"error": st[0], "exact_scan_voxels": st[1], "tie_overflow_voxels": st[2],
+                        "uncertified_voxels": st[3],
+                        "diagnostics": list(st[4:8])},
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------------ main
 def main():
     args = parse()
@@ -161,6 +284,8 @@ def main():
             W = W2
         return W
 
+    if args.workload == "batched":
+        return run_batched(args, world, rank, local)
     W = make_workload(rank)
     cfg = {"workload": WORKLOADS[args.workload].format(J=W.J, n=W.n_per_model[0], k=W.k),
            "voxels_per_gpu": W.J, "draws": W.N, "frames": W.L, "k": W.k,
@@ -209,6 +334,7 @@ def main():
         run.step(y)
     torch.cuda.synchronize()
     st = api.topk_status(run.ws)
+    launches0 = api.launch_info()[2]
     # timed region (device time on the launching stream)
     K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -228,6 +354,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     api.profile_events(None, None)
+    launches = api.launch_info()[2] - launches0
     barrier()
     ms = e0.elapsed_time(e1) / K
     tc_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
@@ -280,7 +407,6 @@ def main():
         rec = json.load(open(tp)).get(f"{args.workload}/{args.precision}")
         if rec and rec.get("source_sha1") == h:
             traffic = rec["bytes_per_launch"]
-    launches_per_step = 2 * len(W.models) + 7
     line = {
         "metric": "voxels/s to posterior", "value": value, "unit": "voxels/s", "n_gpus": n_gpu, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -293,9 +419,10 @@ def main():
                      "algorithmic_flops_per_launch": flops, "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"},
         "e2e": {"value": voxels / (e2e_ms / 1000.0), "unit": "voxels/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_step * K,
+        "gpu_launches": launches,
         "clocks": clk,
-        "topk_status": {"error": st[0], "exact_scan_voxels": st[1], "tie_overflow_voxels": st[2], "uncertified_voxels": st[3]},
+        "topk_status": {"error": st[0], "exact_scan_voxels": st[1], "tie_overflow_voxels": st[2], "uncertified_voxels": st[3],
+                        "diagnostics": list(st[4:8])},
     }
     if n_gpu == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)

@@ -215,8 +215,11 @@ int abc_discrepancy_topk_noalloc(const float* y_dev, int64_t J, int32_t ldy, con
  *               list order rather than by index);
  *   status[3] = ABC_BF16_RESCORE voxels whose accepted set could not be
  *               certified exact from the bf16 error bound (the 4k net may
- *               have missed a member of the exact top-k). */
-int abc_topk_status(const void* workspace, int32_t status_host[4], void* stream);
+ *               have missed a member of the exact top-k);
+ *   status[4..7] = diagnostics: voxels whose candidate list overflowed, voxels
+ *               left with fewer than k / fewer than the net size of candidates,
+ *               and (voxel, pilot level) pairs left without a pilot threshold. */
+int abc_topk_status(const void* workspace, int32_t status_host[8], void* stream);
 
 /* Timing hook: when both are non-NULL (cudaEvent_t passed as void*), every
  * later abc_discrepancy_topk records `start_event` on its stream right before
@@ -225,10 +228,11 @@ int abc_topk_status(const void* workspace, int32_t status_host[4], void* stream)
  * Process-wide setting; the events stay owned by the caller. */
 int abc_profile_events(void* start_event, void* stop_event);
 
-/* Diagnostics: grid size of the last fused-kernel launch of this process and
- * the CTAs per SM its variant can keep resident (shared memory, registers and
- * TMEM columns). */
-int abc_launch_info(int64_t* grid, int32_t* resident_per_sm);
+/* Diagnostics: grid size of the last fused-kernel launch of this process, the
+ * CTAs per SM its variant can keep resident (shared memory, registers and TMEM
+ * columns), and how many kernels this library has launched in this process
+ * (replays of a captured CUDA graph are not counted). */
+int abc_launch_info(int64_t* grid, int32_t* resident_per_sm, int64_t* kernel_launches);
 
 /* Test hook: the raw tensor-core ranking keys d' = ||yh||^2-free part of the
  * distance (||xh_n||^2 - 2 yh_j . xh_n, yh = sqrt(w)(y - mu), xh = sqrt(w)(x - mu),

@@ -81,7 +81,7 @@ def lib():
     L.abc_discrepancy_topk_noalloc.argtypes = [P, i64, i32, P, i64, i32, i32, P, i32, i32, P, P, P]
     L.abc_default_tuning.argtypes = [i32, ctypes.POINTER(Tuning)]
     L.abc_set_default_tuning.argtypes = [ctypes.POINTER(Tuning)]
-    L.abc_launch_info.argtypes = [P, P]
+    L.abc_launch_info.argtypes = [P, P, P]
     L.abc_batch_workspace_size.argtypes = [ctypes.POINTER(Scan), i32, i32]
     L.abc_batch_workspace_size.restype = sz
     L.abc_batch_discrepancy_topk.argtypes = [ctypes.POINTER(Scan), i32, i32, ctypes.POINTER(Tuning), P, sz, P]

@@ -104,7 +104,7 @@ def discrepancy_topk(y, x, L, w, k, precision=_lib.ABC_FP32, workspace=None, idx
 
 
 def topk_status(workspace, stream=None):
-    st = np.zeros(4, np.int32)
+    st = np.zeros(8, np.int32)
     check(lib().abc_topk_status(_ptr(workspace), st.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
     return tuple(int(v) for v in st)
 
@@ -160,11 +160,12 @@ def profile_events(start=None, stop=None):
 
 
 def launch_info():
-    """(grid, resident CTAs per SM) of the last fused-kernel launch."""
+    """(grid, resident CTAs per SM) of the last fused-kernel launch, and the library's kernel-launch count."""
     g = ctypes.c_int64(0)
     r = ctypes.c_int32(0)
-    check(lib().abc_launch_info(ctypes.byref(g), ctypes.byref(r)))
-    return g.value, r.value
+    n = ctypes.c_int64(0)
+    check(lib().abc_launch_info(ctypes.byref(g), ctypes.byref(r), ctypes.byref(n)))
+    return g.value, r.value, n.value
 
 
 def set_default_tuning(bn=None, ctas_per_sm=2, pilot_stride=16, pilot_factor=1.5):

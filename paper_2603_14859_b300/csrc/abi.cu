@@ -1,10 +1,13 @@
 // Error reporting for the C ABI (thread-local last-error text).
 #include <stdarg.h>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace {
 thread_local char g_err[512] = {0};
+std::atomic<long long> g_launches{0};
 }
 
 namespace vpet {
@@ -17,6 +20,10 @@ void set_error(const char* fmt, ...) {
 }
 
 void clear_error() { g_err[0] = 0; }
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
 }  // namespace vpet
 

@@ -12,6 +12,9 @@ namespace vpet {
 void set_error(const char* fmt, ...);
 void clear_error();
 
+// Process-wide count of kernels this library has launched (abc_launch_info).
+void count_launch();
+
 }  // namespace vpet
 
 #define VPET_CUDA(call)                                                                  \
@@ -33,6 +36,7 @@ void clear_error();
 
 #define VPET_LAUNCH_CHECK()                                                              \
     do {                                                                                 \
+        vpet::count_launch();                                                            \
         cudaError_t e_ = cudaGetLastError();                                             \
         if (e_ != cudaSuccess) {                                                         \
             vpet::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \

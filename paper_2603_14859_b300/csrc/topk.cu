@@ -316,7 +316,7 @@ __device__ __forceinline__ float err_bound(float cE, float ry, float R) { return
 __device__ __forceinline__ float compact_list(const ItemTc& I, int64_t j, int& cnt, uint32_t* hist, int lane) {
     float* kj = I.keys + j * I.C;
     int32_t* ij = I.idx + j * I.C;
-    const uint32_t T = warp_select(kj, cnt, I.kt - 1, 3, hist, lane);
+    const uint32_t T = warp_select(kj, cnt, I.kt - 1, 4, hist, lane);   // exact kt-th key
     const int q = warp_compact(kj, ij, cnt, T, I.cap, lane);
     cnt = q < I.cap ? q : I.cap;
     if (q > I.cap && lane == 0) atomicOr(&I.cnt[j], 0x40000000);   // overflow: resolved by an exact scan
@@ -634,6 +634,7 @@ struct BatchPilot {
     PilotItem item[MAX_ITEMS];
     int64_t v_prefix[MAX_ITEMS + 1];
     int n_items;
+    int32_t* status;
 };
 
 __global__ void k_pilot_threshold(const __grid_constant__ BatchPilot B) {
@@ -652,6 +653,7 @@ __global__ void k_pilot_threshold(const __grid_constant__ BatchPilot B) {
     if (lane == 0) {
         I.thr0[j] = t;
         I.cnt[j] = 0;
+        if (t >= 3.0e38f) atomicAdd(&B.status[7], 1);     // diagnostics: pilot level without a threshold
     }
 }
 
@@ -759,6 +761,11 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
     for (int l = lane; l < P.L; l += 32) ys[l] = P.y[j * P.ldy + l];
     __syncwarp();
     bool scan = (raw & 0x40000000) != 0;
+    if (lane == 0) {                       // diagnostics: overflowed lists, short lists
+        if (scan) atomicAdd(&B.status[4], 1);
+        else if (cnt < P.k) atomicAdd(&B.status[5], 1);
+        else if (cnt < P.kt) atomicAdd(&B.status[6], 1);
+    }
     uint32_t K = 0;
     if (!scan) {
         // 1. the net: every draw outside it has computed key > T_out
@@ -851,6 +858,16 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
 int g_last_resident = 0;     // residency of the last configured fused-kernel variant
 int64_t g_last_grid = 0;     // grid of the last fused-kernel launch
+
+// Records a timing event on s; inside a stream capture it becomes a record node
+// of the graph (an ordinary record there would only express a dependency).
+cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t r = cudaStreamIsCapturing(s, &cs);
+    if (r != cudaSuccess) return r;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, s);
+}
 
 int get_encoder() {
     if (g_encode) return ABC_OK;
@@ -1178,6 +1195,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         T.status = status;
         T.counter = counters + (lv + 1);
         PB.n_items = m;
+        PB.status = status;
         if ((rc = dispatch_tc<false>(nkb, tu.bn, T, tu.ctas_per_sm, s))) return rc;
         k_pilot_threshold<<<(unsigned)vpet_ceil_div(PB.v_prefix[m], 8), 256, 0, s>>>(PB);
         VPET_LAUNCH_CHECK();
@@ -1196,9 +1214,9 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     T.dump = dump;
     T.ld_dump = ld_dump;
     if (dump) return dispatch_tc<true>(nkb, 128, T, tu.ctas_per_sm, s);
-    if (g_prof_start) VPET_CUDA(cudaEventRecord(g_prof_start, s));
+    if (g_prof_start) VPET_CUDA(record_event(g_prof_start, s));
     if ((rc = dispatch_tc<false>(nkb, tu.bn, T, tu.ctas_per_sm, s))) return rc;
-    if (g_prof_stop) VPET_CUDA(cudaEventRecord(g_prof_stop, s));
+    if (g_prof_stop) VPET_CUDA(record_event(g_prof_stop, s));
     // finalize
     memset(&F, 0, sizeof F);
     int sortcap = 64;
@@ -1366,13 +1384,13 @@ extern "C" int abc_profile_events(void* start_event, void* stop_event) {
     return ABC_OK;
 }
 
-extern "C" int abc_topk_status(const void* workspace, int32_t status_host[4], void* stream) {
+extern "C" int abc_topk_status(const void* workspace, int32_t status_host[8], void* stream) {
     vpet::clear_error();
     VPET_ARG(workspace && status_host, "abc_topk_status: null pointer");
-    int32_t st[4];
+    int32_t st[8];
     VPET_CUDA(cudaMemcpyAsync(st, workspace, sizeof st, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     VPET_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-    for (int i = 0; i < 4; ++i) status_host[i] = st[i];
+    for (int i = 0; i < 8; ++i) status_host[i] = st[i];
     return ABC_OK;
 }
 
@@ -1388,10 +1406,15 @@ extern "C" int abc_debug_gemm_keys(const float* y_dev, int64_t J, int32_t ldy, c
                      (cudaStream_t)stream);
 }
 
-extern "C" int abc_launch_info(int64_t* grid, int32_t* resident_per_sm) {
+namespace vpet {
+long long launches();
+}
+
+extern "C" int abc_launch_info(int64_t* grid, int32_t* resident_per_sm, int64_t* kernel_launches) {
     vpet::clear_error();
-    VPET_ARG(grid && resident_per_sm, "abc_launch_info: null pointer");
+    VPET_ARG(grid && resident_per_sm && kernel_launches, "abc_launch_info: null pointer");
     *grid = g_last_grid;
     *resident_per_sm = g_last_resident;
+    *kernel_launches = vpet::launches();
     return ABC_OK;
 }

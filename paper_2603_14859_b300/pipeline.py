@@ -8,6 +8,7 @@ device memory and sequences the calls on one stream.
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
 
 import numpy as np
@@ -32,7 +33,7 @@ class StepOutput:
 
 
 class AbcPipeline:
-    def __init__(self, W: S.Workload, precision: int | None = None, ldtheta: int = 8):
+    def __init__(self, W: S.Workload, precision: int | None = None, ldtheta: int = 8, own_workspace: bool = True):
         self.W = W
         self.precision = (_lib.ABC_FP32 if W.precision == "fp32" else _lib.ABC_BF16_RESCORE) if precision is None \
             else precision
@@ -47,7 +48,7 @@ class AbcPipeline:
         dev = "cuda"
         self.theta = torch.zeros((self.N, ldtheta), dtype=torch.float32, device=dev)
         self.x = torch.zeros((self.N, self.ldx), dtype=torch.float32, device=dev)
-        self.ws = api.alloc_workspace(self.J, self.N, self.L, self.k, self.precision)
+        self.ws = api.alloc_workspace(self.J, self.N, self.L, self.k, self.precision) if own_workspace else None
         self.idx = torch.empty((self.J, self.k), dtype=torch.int32, device=dev)
         self.dist = torch.empty((self.J, self.k), dtype=torch.float32, device=dev)
         M = len(W.models)
@@ -64,7 +65,7 @@ class AbcPipeline:
             a, b = self.offsets[m], self.offsets[m + 1]
             lo, hi = W.priors(model)
             api.sample_prior(W.prior_seed, model, lo, hi, b - a, 0, out=self.theta[a:b], stream=stream)
-            api.simulate(model, W.ts, W.te, W.inp, self.theta[a:b], out=self.x[a:b], stream=stream)
+            api.simulate(model, W.ts, W.te, W.input_for(model), self.theta[a:b], out=self.x[a:b], stream=stream)
 
     def select(self, y, stream=None):
         """Algorithm 1, steps 4-5 plus model probabilities and summaries."""
@@ -94,9 +95,86 @@ def make_y_gpu(W: S.Workload, stream=None) -> torch.Tensor:
     ldy = ((L + 3) // 4) * 4
     x_clean = np.zeros((W.J, L), np.float64)
     for model, rows, th in truth_groups(W):
-        xc = api.simulate(model, W.ts, W.te, W.inp, torch.from_numpy(np.ascontiguousarray(th)).cuda(), stream=stream)
+        xc = api.simulate(model, W.ts, W.te, W.input_for(model), torch.from_numpy(np.ascontiguousarray(th)).cuda(),
+                          stream=stream)
         x_clean[rows] = xc[:, :L].cpu().numpy()
     y = S.add_noise(x_clean, W.ts, W.te, W.half_life, W.q, W.z)
     out = torch.zeros((W.J, ldy), dtype=torch.float32)
     out[:, :L] = torch.from_numpy(y)
     return out.cuda()
+
+
+class BatchPipeline:
+    """Many scans in one pass: per-scan prior draws and simulations, one
+    batched discrepancy + top-k call for all scans (persistent fused kernel),
+    then per-scan model selection and summaries.  `capture()` records the
+    whole step into a CUDA graph; `replay()` runs it."""
+
+    def __init__(self, scans: list, precision: int = _lib.ABC_BF16_RESCORE, tuning: dict | None = None):
+        self.scans = scans
+        self.precision = precision
+        self.runs = [AbcPipeline(W, precision, own_workspace=False) for W in scans]   # one batch workspace
+        self.ys = [None] * len(scans)
+        self.tuning = tuning
+        self.graph = None
+        self._scan_structs = None
+        self.ws = None
+
+    def set_inputs(self, ys):
+        self.ys = list(ys)
+        self._build_structs()
+
+    def _build_structs(self):
+        S_ = _lib.Scan * len(self.scans)
+        arr = S_()
+        self._w = []
+        for i, (r, y) in enumerate(zip(self.runs, self.ys)):
+            w = np.ascontiguousarray(r.weights, np.float32)
+            self._w.append(w)
+            arr[i] = _lib.Scan(y.data_ptr(), r.J, y.shape[1], r.x.data_ptr(), r.N, r.x.shape[1], r.L,
+                               w.ctypes.data, r.k, r.idx.data_ptr(), r.dist.data_ptr())
+        self._scan_structs = arr
+        n = _lib.lib().abc_batch_workspace_size(arr, len(self.scans), self.precision)
+        if n == 0:
+            raise ValueError("abc_batch_workspace_size: unsupported batch")
+        if self.ws is None or self.ws.numel() < n:
+            self.ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+
+    def _tuning_ptr(self):
+        if self.tuning is None:
+            return None
+        t = self.tuning
+        self._t = _lib.Tuning(t["bn"], t["ctas_per_sm"], t["pilot_stride"], t["pilot_factor"])
+        return ctypes.byref(self._t)
+
+    def topk(self, stream=None):
+        s = torch.cuda.current_stream() if stream is None else stream
+        _lib.check(_lib.lib().abc_batch_discrepancy_topk(self._scan_structs, len(self.scans), self.precision,
+                                                         self._tuning_ptr(), ctypes.c_void_p(self.ws.data_ptr()),
+                                                         self.ws.numel(), ctypes.c_void_p(s.cuda_stream)))
+
+    def step(self, stream=None):
+        for r in self.runs:
+            r.simulate_draws(stream)
+        self.topk(stream)
+        for r in self.runs:
+            api.model_select(r.idx, r.offsets, r.prob, r.pref, stream=stream)
+            pref = r.pref if len(r.W.models) > 1 else None
+            api.summarize(r.theta, r.offsets, r.nparams, r.has_ki, [0, 1, 2], r.idx, pref, out=r.summ,
+                          stream=stream)
+
+    def capture(self):
+        """Record one step into a CUDA graph (after one eager warm-up step)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step()
+        torch.cuda.synchronize()
+
+    def replay(self):
+        self.graph.replay()

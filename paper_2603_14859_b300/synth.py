@@ -244,6 +244,12 @@ class Workload:
     z: np.ndarray           # (J, L) standard normals
     prior_seed: int
     precision: str = "fp32"
+    model_inp: dict | None = None  # per-model input when the models need different ones
+
+    def input_for(self, model):
+        if self.model_inp and model in self.model_inp:
+            return self.model_inp[model]
+        return self.inp
 
     @property
     def L(self):
@@ -334,3 +340,34 @@ def scan_plan(seed: int = 1004, n_scans: int = 64, voxel_scale: float = 1.0, dra
         n = [int(round(rng.uniform(200_000, 1_000_000) * draw_scale)) for _ in models]
         plan.append(dict(scan=s, J=max(J, 1), F=F, models=models, n_per_model=n, seed=seed * 1000 + s))
     return plan
+
+
+def scan_workload(item: dict, k: int = 100) -> Workload:
+    """One scan of the batched uneven workload (an entry of `scan_plan`).
+
+    Frames: `frames_uneven(F)`.  Inputs: a seeded Feng C_p for the 2TCM
+    models and the 1-tissue reference C_r built from it for MRTM.  Truth: each
+    voxel follows one of the scan's candidate models (uniformly), parameters
+    uniform over that model's prior box; noise level q = 0.10."""
+    seed = item["seed"]
+    J = item["J"]
+    ts, te = frames_uneven(item["F"])
+    beta, kap = draw_feng(seed, avoid=[REF_K2])
+    cp = feng_polyexp(beta, kap)
+    cr = reference_tissue_polyexp(cp)
+    models = list(item["models"])
+    inputs = {m: (cr if m == MRTM else cp) for m in models}
+    rng = _rng(seed, 81)
+    pick = rng.integers(0, len(models), J)
+    tm = np.asarray(models)[pick].astype(np.int32)
+    truth, rows = [], []
+    for m in models:
+        r = np.nonzero(tm == m)[0]
+        rows.append(r)
+        truth.append(uniform_truth(seed, m, len(r)))
+    n = [int(v) for v in item["n_per_model"]]
+    kk = min(k, sum(n))
+    half = HALF_LIFE_C11 if models == [MRTM] else HALF_LIFE_F18
+    return Workload(f"scan{item['scan']}", ts, te, models, n, kk, cp, half, tm, truth, rows,
+                    noise_levels(seed, J, 0.10, 0.10), standard_normals(seed, J, len(ts)), seed + 7, "bf16r",
+                    model_inp=inputs)

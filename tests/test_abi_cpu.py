@@ -88,3 +88,25 @@ def test_simulate_rejects_bad_schedules(lib):
     pe = _lib.PolyExp(1, c.ctypes.data, c.ctypes.data, z.ctypes.data, z.ctypes.data)
     rc = lib.abc_simulate(0, ctypes.byref(fr), ctypes.byref(pe), P(256), 10, 4, P(256), 4, None)
     assert rc == _lib.ABC_ERR_ARG and b"overlap" in lib.abc_last_error()
+
+
+def test_batch_and_tuning_validation_without_gpu(lib):
+    from paper_2603_14859_b300 import _lib
+    P = ctypes.c_void_p
+    w = np.ones(22, np.float32)
+    scans = (_lib.Scan * 2)()
+    for i in range(2):
+        scans[i] = _lib.Scan(256, 10, 24, 256, 50, 24, 22, w.ctypes.data, 5, 256, 256)
+    assert lib.abc_batch_workspace_size(scans, 2, 1) > lib.abc_workspace_size(10, 50, 22, 5, 1)
+    assert lib.abc_batch_workspace_size(scans, 0, 1) == 0
+    assert lib.abc_batch_workspace_size(scans, 65, 1) == 0
+    bad = _lib.Tuning(96, 2, 16, 1.5)
+    rc = lib.abc_batch_discrepancy_topk(scans, 2, 1, ctypes.byref(bad), P(256), 1 << 30, None)
+    assert rc == _lib.ABC_ERR_ARG and b"bn" in lib.abc_last_error()
+    bad = _lib.Tuning(64, 2, 12, 1.5)
+    assert lib.abc_set_default_tuning(ctypes.byref(bad)) == _lib.ABC_ERR_ARG
+    t = _lib.Tuning()
+    assert lib.abc_default_tuning(1, ctypes.byref(t)) == 0 and t.bn in (64, 128)
+    scans[1].k = 51                                   # k > N in the second scan
+    rc = lib.abc_batch_discrepancy_topk(scans, 2, 1, None, P(256), 1 << 30, None)
+    assert rc == _lib.ABC_ERR_ARG
