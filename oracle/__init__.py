@@ -54,6 +54,19 @@ def lib():
         L.orc_summarize.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, P, P, P, i64, ctypes.c_int, P,
                                     ctypes.c_int, P, P, P, P]
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_Phi.argtypes = [f64]
+        L.orc_Phi.restype = f64
+        L.orc_Phi_inv.argtypes = [f64]
+        L.orc_Phi_inv.restype = f64
+        L.orc_truncnorm01.argtypes = [f64, f64, f64]
+        L.orc_truncnorm01.restype = f64
+        L.orc_truncnorm01_logpdf.argtypes = [f64, f64, f64]
+        L.orc_truncnorm01_logpdf.restype = f64
+        L.orc_mlp_forward.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P, P]
+        L.orc_mlp_loss_grad.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P]
+        L.orc_mlp_loss_grad.restype = f64
+        L.orc_local_abc.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P, ctypes.c_int, P, P,
+                                    ctypes.c_int, P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -181,3 +194,64 @@ def summarize(theta, offsets, nparams, has_ki, ki_cols, idx, pref=None):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+# ---------------------------------------------------------------- learned proposal (build extra)
+def Phi(z):
+    return lib().orc_Phi(float(z))
+
+
+def Phi_inv(p):
+    return lib().orc_Phi_inv(float(p))
+
+
+def truncnorm01(mu, sigma, u):
+    return lib().orc_truncnorm01(float(mu), float(sigma), float(u))
+
+
+def truncnorm01_logpdf(mu, sigma, t):
+    return lib().orc_truncnorm01_logpdf(float(mu), float(sigma), float(t))
+
+
+def mlp_param_count(D, H, O):
+    return H * D + H + H * H + H + O * H + O
+
+
+def mlp_forward(params, D, H, O, X):
+    prm = _c(params, np.float64)
+    X = _c(X, np.float64)
+    B = X.shape[0]
+    out = np.zeros((B, O))
+    z1 = np.zeros((B, H))
+    z2 = np.zeros((B, H))
+    lib().orc_mlp_forward(_p(prm), D, H, O, _p(X), B, _p(out), _p(z1), _p(z2))
+    return out
+
+
+def mlp_loss_grad(params, D, H, P, X, T):
+    prm = _c(params, np.float64)
+    X = _c(X, np.float64)
+    T = _c(T, np.float64)
+    g = np.zeros_like(prm)
+    loss = lib().orc_mlp_loss_grad(_p(prm), D, H, P, _p(X), _p(T), X.shape[0], _p(g))
+    return loss, g
+
+
+def local_abc(u, mu, sigma, x, y, w, k, lo, hi, ki=True):
+    """Importance-weighted local ABC for one voxel; returns dict of outputs."""
+    u = _c(u, np.float64)
+    M, P = u.shape
+    x = _c(x, np.float64)
+    y = _c(y, np.float32)
+    w = _c(w, np.float64)
+    mu = _c(mu, np.float64)
+    sigma = _c(sigma, np.float64)
+    lo = _c(lo, np.float64)
+    hi = _c(hi, np.float64)
+    nc = P + (1 if ki else 0)
+    idx = np.zeros(k, np.int32)
+    outs = [np.zeros(nc) for _ in range(4)]
+    ess = np.zeros(1)
+    lib().orc_local_abc(_p(u), _p(mu), _p(sigma), P, M, _p(x), x.shape[1], _p(y), _p(w), k, _p(lo), _p(hi),
+                        1 if ki else 0, _p(idx), *[_p(o) for o in outs], _p(ess))
+    return dict(idx=idx, mean=outs[0], sd=outs[1], lo=outs[2], hi=outs[3], ess=float(ess[0]))

@@ -568,3 +568,209 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------ learned proposal (build extra) */
+/* Standard normal density, CDF (via erfc) and quantile (Newton iterations on
+ * the CDF to full double precision; no tables).  Pinned against scipy's ndtr /
+ * ndtri in tests/test_oracle_learned.py. */
+static double nphi(double z) { return exp(-0.5 * z * z) / sqrt(2.0 * M_PI); }
+double orc_Phi(double z) { return 0.5 * erfc(-z / sqrt(2.0)); }
+/* Lower-half quantile (p <= 0.5), where Phi(x) - p keeps full relative precision. */
+static double phi_inv_lower(double p) {
+    double x = log(p / (1.0 - p)) * 0.6266570686577501;   /* logistic start, sqrt(pi/8) */
+    for (int it = 0; it < 200; ++it) {
+        const double f = orc_Phi(x) - p;
+        const double d = nphi(x);
+        double step = d > 1e-300 ? f / d : (f > 0 ? 0.5 : -0.5);
+        if (step > 1.0) step = 1.0;
+        if (step < -1.0) step = -1.0;
+        x -= step;
+        if (fabs(step) < 1e-15 * (1.0 + fabs(x))) break;
+    }
+    return x;
+}
+
+double orc_Phi_inv(double p) {
+    if (p <= 0.0) return -INFINITY;
+    if (p >= 1.0) return INFINITY;
+    return p <= 0.5 ? phi_inv_lower(p) : -phi_inv_lower(1.0 - p);   /* 1 - p is exact for p >= 0.5 */
+}
+
+/* Truncated normal N(mu, sigma^2) on [0, 1] by inverse CDF of a uniform u in (0,1):
+ * t = mu + sigma Phi^-1(Phi(a) + u (Phi(b) - Phi(a))), a = -mu/sigma, b = (1-mu)/sigma. */
+double orc_truncnorm01(double mu, double sigma, double u) {
+    const double a = -mu / sigma, b = (1.0 - mu) / sigma;
+    const double Pa = orc_Phi(a), Pb = orc_Phi(b);
+    double t = mu + sigma * orc_Phi_inv(Pa + u * (Pb - Pa));
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    return t;
+}
+
+/* log density of that truncated normal at t in [0, 1]. */
+double orc_truncnorm01_logpdf(double mu, double sigma, double t) {
+    const double a = -mu / sigma, b = (1.0 - mu) / sigma, z = (t - mu) / sigma;
+    return -0.5 * z * z - 0.5 * log(2.0 * M_PI) - log(sigma) - log(orc_Phi(b) - orc_Phi(a));
+}
+
+static double gelu(double z) { return 0.5 * z * (1.0 + erf(z / sqrt(2.0))); }
+static double gelu_d(double z) { return orc_Phi(z) + z * nphi(z); }
+
+/* MLP proposal network, FP64.  params layout: W1 (H x D), b1 (H), W2 (H x H), b2 (H),
+ * W3 (O x H), b3 (O), row-major; weights are used rounded to bf16 (the caller
+ * passes them already rounded).  out: B x O.  z1, z2 (B x H) hold pre-activations. */
+void orc_mlp_forward(const double* prm, int D, int H, int O, const double* X, int B, double* out, double* z1,
+                     double* z2) {
+    const double *W1 = prm, *b1 = W1 + (size_t)H * D, *W2 = b1 + H, *b2 = W2 + (size_t)H * H, *W3 = b2 + H,
+                 *b3 = W3 + (size_t)O * H;
+    double* h1 = (double*)malloc(sizeof(double) * H);
+    double* h2 = (double*)malloc(sizeof(double) * H);
+    for (int n = 0; n < B; ++n) {
+        const double* x = X + (size_t)n * D;
+        for (int o = 0; o < H; ++o) {
+            double s = b1[o];
+            for (int i = 0; i < D; ++i) s += W1[(size_t)o * D + i] * x[i];
+            z1[(size_t)n * H + o] = s;
+            h1[o] = gelu(s);
+        }
+        for (int o = 0; o < H; ++o) {
+            double s = b2[o];
+            for (int i = 0; i < H; ++i) s += W2[(size_t)o * H + i] * h1[i];
+            z2[(size_t)n * H + o] = s;
+            h2[o] = gelu(s);
+        }
+        for (int o = 0; o < O; ++o) {
+            double s = b3[o];
+            for (int i = 0; i < H; ++i) s += W3[(size_t)o * H + i] * h2[i];
+            out[(size_t)n * O + o] = s;
+        }
+    }
+    free(h1);
+    free(h2);
+}
+
+/* Mean truncated-normal negative log likelihood of targets T (B x P, in [0,1])
+ * under the network outputs (mu_p, log sigma_p) = (out[2p], out[2p+1]), with
+ * mu clamped to [-3, 4] and log sigma to [-7, 2] (zero gradient outside), and
+ * the analytic gradient of that mean w.r.t. every parameter (grad, same layout). */
+double orc_mlp_loss_grad(const double* prm, int D, int H, int P, const double* X, const double* T, int B,
+                         double* grad) {
+    const int O = 2 * P;
+    const double *W1 = prm, *W2 = prm + (size_t)H * D + H, *W3 = W2 + (size_t)H * H + H;
+    double* out = (double*)malloc(sizeof(double) * (size_t)B * O);
+    double* z1 = (double*)malloc(sizeof(double) * (size_t)B * H);
+    double* z2 = (double*)malloc(sizeof(double) * (size_t)B * H);
+    orc_mlp_forward(prm, D, H, O, X, B, out, z1, z2);
+    const size_t np = (size_t)H * D + H + (size_t)H * H + H + (size_t)O * H + O;
+    memset(grad, 0, sizeof(double) * np);
+    double *gW1 = grad, *gb1 = gW1 + (size_t)H * D, *gW2 = gb1 + H, *gb2 = gW2 + (size_t)H * H, *gW3 = gb2 + H,
+           *gb3 = gW3 + (size_t)O * H;
+    double loss = 0.0;
+    double* dout = (double*)malloc(sizeof(double) * O);
+    double* dh2 = (double*)malloc(sizeof(double) * H);
+    double* dh1 = (double*)malloc(sizeof(double) * H);
+    for (int n = 0; n < B; ++n) {
+        for (int p = 0; p < P; ++p) {
+            double mu = out[(size_t)n * O + 2 * p], s = out[(size_t)n * O + 2 * p + 1];
+            const int mu_in = mu >= -3.0 && mu <= 4.0, s_in = s >= -7.0 && s <= 2.0;
+            mu = mu < -3.0 ? -3.0 : (mu > 4.0 ? 4.0 : mu);
+            s = s < -7.0 ? -7.0 : (s > 2.0 ? 2.0 : s);
+            const double sg = exp(s), t = T[(size_t)n * P + p];
+            const double z = (t - mu) / sg, a = -mu / sg, b = (1.0 - mu) / sg;
+            const double Z = orc_Phi(b) - orc_Phi(a);
+            loss += s + 0.5 * z * z + log(Z) + 0.5 * log(2.0 * M_PI);
+            const double dmu = -z / sg + (nphi(a) - nphi(b)) / (sg * Z);
+            const double ds = 1.0 - z * z + (a * nphi(a) - b * nphi(b)) / Z;
+            dout[2 * p] = mu_in ? dmu / B : 0.0;
+            dout[2 * p + 1] = s_in ? ds / B : 0.0;
+        }
+        const double* x = X + (size_t)n * D;
+        /* layer 3 */
+        for (int i = 0; i < H; ++i) dh2[i] = 0.0;
+        for (int o = 0; o < O; ++o) {
+            gb3[o] += dout[o];
+            for (int i = 0; i < H; ++i) {
+                const double h2 = gelu(z2[(size_t)n * H + i]);
+                gW3[(size_t)o * H + i] += dout[o] * h2;
+                dh2[i] += dout[o] * W3[(size_t)o * H + i];
+            }
+        }
+        /* layer 2 */
+        for (int i = 0; i < H; ++i) dh1[i] = 0.0;
+        for (int o = 0; o < H; ++o) {
+            const double dz = dh2[o] * gelu_d(z2[(size_t)n * H + o]);
+            gb2[o] += dz;
+            for (int i = 0; i < H; ++i) {
+                gW2[(size_t)o * H + i] += dz * gelu(z1[(size_t)n * H + i]);
+                dh1[i] += dz * W2[(size_t)o * H + i];
+            }
+        }
+        /* layer 1 */
+        for (int o = 0; o < H; ++o) {
+            const double dz = dh1[o] * gelu_d(z1[(size_t)n * H + o]);
+            gb1[o] += dz;
+            for (int i = 0; i < D; ++i) gW1[(size_t)o * D + i] += dz * x[i];
+        }
+    }
+    free(out); free(z1); free(z2); free(dout); free(dh2); free(dh1);
+    return loss / B;
+}
+
+/* Importance-weighted local ABC for one voxel (build extra): proposals u (M x P in
+ * [0,1]) with their truncated-normal parameters (mu, sigma per p), simulated TACs
+ * x (M x L), the voxel TAC y, weights w; the k nearest proposals by (d, index)
+ * are accepted, weighted by prior/proposal = 1/q(u) (uniform prior on the box),
+ * normalised over the accepted set.  theta = lo + (hi - lo) u.  Outputs per
+ * column (P parameters, then K_i if ki): weighted mean, weighted SD (sum W (t-m)^2
+ * with W normalised), and weighted 2.5 / 97.5 % quantiles (smallest value whose
+ * cumulative weight reaches q); ess = 1 / sum W^2; idx = accepted proposals. */
+void orc_local_abc(const double* u, const double* mu, const double* sigma, int P, int M, const double* x, int L,
+                   const float* y, const double* w, int k, const double* lo, const double* hi, int ki,
+                   int32_t* idx, double* mean, double* sd, double* qlo, double* qhi, double* ess) {
+    di_pair* buf = (di_pair*)malloc(sizeof(di_pair) * (size_t)M);
+    for (int i = 0; i < M; ++i) { buf[i].d = wdist(y, x + (size_t)i * L, w, L); buf[i].i = i; }
+    qsort(buf, (size_t)M, sizeof(di_pair), di_cmp);
+    double* lw = (double*)malloc(sizeof(double) * k);
+    double mx = -INFINITY;
+    for (int r = 0; r < k; ++r) {
+        const int i = (int)buf[r].i;
+        idx[r] = i;
+        double l = 0.0;
+        for (int p = 0; p < P; ++p) l -= orc_truncnorm01_logpdf(mu[p], sigma[p], u[(size_t)i * P + p]);
+        lw[r] = l;
+        if (l > mx) mx = l;
+    }
+    double sw = 0.0, sw2 = 0.0;
+    for (int r = 0; r < k; ++r) { lw[r] = exp(lw[r] - mx); sw += lw[r]; }
+    for (int r = 0; r < k; ++r) { lw[r] /= sw; sw2 += lw[r] * lw[r]; }
+    *ess = 1.0 / sw2;
+    const int nc = P + (ki ? 1 : 0);
+    double* v = (double*)malloc(sizeof(double) * k);
+    di_pair* srt = (di_pair*)malloc(sizeof(di_pair) * (size_t)k);
+    for (int c = 0; c < nc; ++c) {
+        double m = 0.0;
+        for (int r = 0; r < k; ++r) {
+            const double* uu = u + (size_t)idx[r] * P;
+            if (c < P) v[r] = lo[c] + (hi[c] - lo[c]) * uu[c];
+            else {
+                const double K1 = lo[0] + (hi[0] - lo[0]) * uu[0], k2 = lo[1] + (hi[1] - lo[1]) * uu[1],
+                             k3 = lo[2] + (hi[2] - lo[2]) * uu[2];
+                v[r] = K1 * k3 / (k2 + k3);
+            }
+            m += lw[r] * v[r];
+        }
+        double var = 0.0;
+        for (int r = 0; r < k; ++r) var += lw[r] * (v[r] - m) * (v[r] - m);
+        for (int r = 0; r < k; ++r) { srt[r].d = v[r]; srt[r].i = r; }
+        qsort(srt, (size_t)k, sizeof(di_pair), di_cmp);
+        double cum = 0.0, ql = srt[k - 1].d, qh = srt[k - 1].d;
+        int got_l = 0, got_h = 0;
+        for (int r = 0; r < k; ++r) {
+            cum += lw[srt[r].i];
+            if (!got_l && cum >= 0.025) { ql = srt[r].d; got_l = 1; }
+            if (!got_h && cum >= 0.975) { qh = srt[r].d; got_h = 1; }
+        }
+        mean[c] = m; sd[c] = sqrt(var); qlo[c] = ql; qhi[c] = qh;
+    }
+    free(buf); free(lw); free(v); free(srt);
+}
