@@ -36,6 +36,9 @@ WORKLOADS = {
     "raclopride_lpntpet": "brain lp-ntPET vs MRTM: {J} voxels x ({n} MRTM + {n} lp-ntPET draws), 60 x 1-min frames, k={k}",
     "totalbody_fdg": "total-body FDG 2TCM irr vs rev: {J} voxels x ({n} + {n} draws), 29 frames, k={k}",
     "brain_fdg_2tcm": "2TCM-irr: {J} voxels x {n} draws, 22 frames, k={k}",
+    "learned": "learned proposal + local importance-weighted ABC, 2TCM-irr on the total-body FDG volume: {J} voxels x "
+               "{M} proposals, 29 frames, k={k}; network trained on {P} simulated pairs; fallback to the global path "
+               "({n} 2TCM-irr draws)",
     "batched": "{n} uneven scans: {J} voxels in total (log-uniform 1,000-500,000 per scan), 22-60 frames, 1-3 of "
                "{{2TCM-irr, 2TCM-rev, MRTM}} per scan, 200,000-1,000,000 draws per model, k={k}; one CUDA graph",
 }
@@ -55,6 +58,9 @@ def parse():
     ap.add_argument("--voxel-scale", type=float, default=1.0, help="batched workload: scale voxel counts")
     ap.add_argument("--draw-scale", type=float, default=1.0, help="batched workload: scale draw counts")
     ap.add_argument("--scans", type=int, default=64, help="batched workload: number of scans")
+    ap.add_argument("--proposals", type=int, default=10_000, help="learned workload: proposals per voxel")
+    ap.add_argument("--train-pairs", type=int, default=10_000_000, help="learned workload: training pairs")
+    ap.add_argument("--sigma-scale", type=float, default=1.0, help="learned workload: proposal widening")
     return ap.parse_args()
 
 
@@ -267,6 +273,183 @@ def run_batched(args, world, rank, local):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ learned proposal + local ABC
+LOCAL_FLOPS_PER_FRAME = 18   # cubic interpolation 8, model combination 6, residual and weighted square 4
+
+
+def cpu_baseline_learned(W, M, k, model_params, D, H, seconds_budget=20.0):
+    """The FP64 oracle as it stands on a bounded sample of the learned workload:
+    network forward, truncated-normal proposals, simulation of every proposal and
+    the importance-weighted local ABC, for a few voxels; scaled to the volume."""
+    import oracle
+    from paper_2603_14859_b300 import synth as S
+    oracle.build()
+    cores = oracle.num_threads()
+    lo, hi = (np.asarray(a, np.float64) for a in S.PRIORS[S.TCM2_IRR])
+    w = W.weights.astype(np.float64)
+    rng = np.random.default_rng(0)
+    ys = []
+    for th, rows in zip(W.truth, W.truth_rows):
+        if W.truth_model[rows[0]] == S.TCM2_IRR:
+            x = oracle.simulate(S.TCM2_IRR, W.ts, W.te, W.input_for(S.TCM2_IRR), th[:2])
+            ys = (x * (1 + 0.1 * rng.standard_normal(x.shape))).astype(np.float32)
+    prm = np.asarray(model_params, np.float64)
+    t0 = time.perf_counter()
+    nv = 0
+    for yv in ys:
+        s = math.sqrt(float((w * yv.astype(np.float64) ** 2).sum()))
+        feat = np.concatenate([yv / s, [math.log(s) / 10]])[None, :]
+        out = oracle.mlp_forward(prm, D, H, 8, feat)[0]
+        mu = np.clip(out[0::2], -3, 4)
+        sg = np.exp(np.clip(out[1::2], -7, 2))
+        uni = rng.random((M, 4))
+        u = np.array([[oracle.truncnorm01(mu[p], sg[p], uni[i, p]) for p in range(4)] for i in range(M)])
+        th = (lo + (hi - lo) * u).astype(np.float32)
+        x = oracle.simulate(S.TCM2_IRR, W.ts, W.te, W.input_for(S.TCM2_IRR), th)
+        oracle.local_abc(u, mu, sg, x, yv, w, k, lo, hi)
+        nv += 1
+        if time.perf_counter() - t0 > seconds_budget:
+            break
+    dt = (time.perf_counter() - t0) / nv
+    return {"value": 1.0 / dt, "unit": "voxels/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nv} voxels end to end (FP64 network, {M} truncated-normal proposals, FP64 simulation of "
+                      f"each, weighted local ABC); scaled per voxel (fallback voxels not included)"}
+
+
+def run_learned_bench(args, world, rank, local):
+    """One step = network features + forward over every voxel, local ABC with M
+    proposals per voxel, and the global path for the voxels that fall back."""
+    import torch
+    from paper_2603_14859_b300 import api, learned
+    from paper_2603_14859_b300 import pipeline
+    from paper_2603_14859_b300 import synth as S
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    W = S.workload("totalbody_fdg", seed=None if rank == 0 else 5000 + rank, J=args.voxels)
+    M, k = args.proposals, W.k
+    model = learned.LearnedLocalAbc(W.ts, W.te, W.input_for(S.TCM2_IRR), W.half_life)
+    tl = model.train(n_pairs=args.train_pairs)
+    n_glob = args.draws or 1_000_000
+    g = learned.GlobalIrr(model, N=n_glob, k=k)
+    y = pipeline.make_y_gpu(W)
+    rel = g.calibrate(y[:2048].contiguous())
+    g.reserve(W.J)
+    stream = torch.cuda.current_stream()
+    J = W.J
+    outs = dict(mean=torch.empty((J, 5), device="cuda"), sd=torch.empty((J, 5), device="cuda"),
+                lo=torch.empty((J, 5), device="cuda"), hi=torch.empty((J, 5), device="cuda"),
+                ess=torch.empty(J, device="cuda"), dmed=torch.empty(J, device="cuda"),
+                ynorm=torch.empty(J, device="cuda"))
+    prop = torch.empty((J, 8), device="cuda")
+    ev_local = []
+
+    def step(yd, rec=None):
+        model.propose(yd, out=prop)
+        if rec is not None:
+            rec[0].record(stream)
+        model.local(yd, prop, M=M, k=k, sigma_scale=args.sigma_scale, out=outs)
+        if rec is not None:
+            rec[1].record(stream)
+        bad = (outs["ess"] < k / 4.0) | (outs["dmed"] > rel * outs["ynorm"])
+        fb = torch.nonzero(bad).flatten()
+        if fb.numel():
+            r = g.run(yd.index_select(0, fb).contiguous())
+            for key in ("mean", "sd", "lo", "hi"):
+                outs[key].index_copy_(0, fb, r[key])
+        return fb.numel()
+
+    for _ in range(args.warmup):
+        step(y)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in ev:
+        a.record(stream)
+        b.record(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    l0 = api.launch_info()[2]
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    nfb = [step(y, ev[i]) for i in range(K)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = api.launch_info()[2] - l0
+    ms = e0.elapsed_time(e1) / K
+    local_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    # end to end: pinned host TACs in, posterior summaries out
+    y_host = y.cpu().pin_memory()
+    y_dev = torch.empty_like(y)
+    outs_host = [torch.empty(outs[key].shape).pin_memory() for key in ("mean", "sd", "lo", "hi")]
+    Ke = max(1, min(K, 3))
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(Ke):
+        y_dev.copy_(y_host, non_blocking=True)
+        step(y_dev)
+        for h, key in zip(outs_host, ("mean", "sd", "lo", "hi")):
+            h.copy_(outs[key], non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / Ke
+    # accuracy against the global path on a voxel sample (outside the timed region)
+    sub = y[:4096].contiguous()
+    ref = g.run(sub)["mean"].cpu().numpy()
+    got = outs["mean"][:4096].cpu().numpy()
+    g2 = learned.GlobalIrr(model, N=n_glob, k=k, seed=4321)
+    ref2 = g2.run(sub)["mean"].cpu().numpy()
+    rel_l2 = lambda a, b: [float(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c])) for c in range(5)]
+    t = torch.tensor([ms, local_ms, e2e_ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, local_ms, e2e_ms = (float(v) for v in t)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    flops = float(LOCAL_FLOPS_PER_FRAME) * W.L * J * M
+    achieved = flops / (local_ms / 1000.0) / 1e12
+    sm_mhz = clk["sm_mhz"] if clk else 2032.0
+    peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    cfg = {"workload": WORKLOADS["learned"].format(J=J, M=M, k=k, P=tl.pairs, n=n_glob), "voxels_per_gpu": J,
+           "proposals_per_voxel": M, "frames": W.L, "k": k, "sigma_scale": args.sigma_scale,
+           "training": {"pairs": tl.pairs, "steps": tl.steps, "seconds": tl.seconds,
+                        "pairs_per_s": tl.pairs / tl.seconds, "final_loss": tl.losses[-1][1]},
+           "fallback": {"rule": "ESS < k/4 or median accepted distance > calibrated relative threshold",
+                        "rel_threshold": rel, "voxels_per_step": statistics.mean(nfb)},
+           "accuracy_vs_global": {"columns": ["K1", "k2", "k3", "Vb", "Ki"], "sample_voxels": 4096,
+                                  "rel_l2_learned": rel_l2(got, ref), "rel_l2_global_reseeded": rel_l2(ref2, ref)},
+           "l2": "inputs larger than L2", "parallelism": f"voxel shards x{args.gpus}" if args.gpus > 1 else "single GPU"}
+    line = {
+        "metric": "voxels/s to posterior", "value": J * world / (ms / 1000.0), "unit": "voxels/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (network weights bf16)", "data": "synthetic", "config": cfg,
+        "pairs_per_s": J * M * world / (ms / 1000.0),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_local_abc (proposals, TACs, distances, selection, summaries)",
+                     "kernel_ms": local_ms, "algorithmic_flops_per_launch": flops,
+                     "peak_source": "FP32 lanes: 148 SMs x 128 x 2 flops x median SM clock under load"},
+        "e2e": {"value": J * world / (e2e_ms / 1000.0), "unit": "voxels/s",
+                "h2d_bytes_per_step": y_host.numel() * 4, "d2h_bytes_per_step": sum(o.numel() * 4 for o in outs_host)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_learned(W, M, k, model.params.cpu().numpy(), model.D, model.H)
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------------ main
 def main():
     args = parse()
@@ -286,6 +469,31 @@ def main():
 
     if args.workload == "batched":
         return run_batched(args, world, rank, local)
+    if args.workload == "learned":
+        if args.impl == "ours":
+            return run_learned_bench(args, world, rank, local)
+        if rank != 0:
+            return
+        # reference arm: the FP64 oracle's learned path on the host cores (network parameters
+        # drawn at random: the oracle's cost does not depend on their values)
+        W = S.workload("totalbody_fdg", J=args.voxels)
+        D, H = W.L + 1, 256
+        prm = np.random.default_rng(0).normal(0.0, 0.05, H * D + H + H * H + H + 8 * H + 8)
+        vals, cb = [], None
+        for _ in range(args.warmup + args.steps):
+            cb = cpu_baseline_learned(W, args.proposals, W.k, prm, D, H, seconds_budget=10.0)
+            vals.append(cb["value"])
+        v = statistics.median(vals[args.warmup:]) if args.steps else vals[-1]
+        cb["value"] = v
+        cfg = {"workload": WORKLOADS["learned"].format(J=W.J, M=args.proposals, k=W.k, P=args.train_pairs,
+                                                       n=args.draws or 1_000_000), "voxels_per_gpu": W.J}
+        print(json.dumps({"impl": "reference", "metric": "voxels/s to posterior", "value": v, "unit": "voxels/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1000.0 * W.J / v, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+                          "cpu_baseline": cb, "e2e": {"value": v, "unit": "voxels/s", "h2d_bytes_per_step": 0,
+                                                      "d2h_bytes_per_step": 0}}))
+        return
     W = make_workload(rank)
     cfg = {"workload": WORKLOADS[args.workload].format(J=W.J, n=W.n_per_model[0], k=W.k),
            "voxels_per_gpu": W.J, "draws": W.N, "frames": W.L, "k": W.k,

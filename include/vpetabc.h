@@ -270,6 +270,110 @@ int abc_summarize(const float* theta_dev, int32_t ldtheta, const int64_t* model_
                   const int32_t* idx_dev, int64_t J, int32_t k, const int8_t* preferred_dev, int32_t ncols,
                   float* mean_dev, float* sd_dev, float* lo_dev, float* hi_dev, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned proposal and importance-weighted local ABC.  A build extra: the paper
+ * has no counterpart; it replaces the global scan of Algorithm 1 for the
+ * irreversible 2TCM (Eq. 1-2 with k4 = 0) by a few thousand proposals per
+ * voxel drawn from a per-voxel truncated Gaussian that a small network
+ * predicts from the voxel's TAC.
+ *
+ * Network: D = L + 1 features -> H -> H -> O = 2P outputs, GELU (exact, erf
+ * form) after the two hidden layers.  Parameters are one fp32 array in the
+ * order W1 (H x D), b1 (H), W2 (H x H), b2 (H), W3 (O x H), b3 (O), row-major;
+ * every weight matrix is used rounded to bf16 (round to nearest even), biases
+ * and accumulation are fp32.  Output p pairs (out[2p], out[2p+1]) =
+ * (mu_p, log sigma_p) of a normal truncated to [0, 1] over the unit-box
+ * coordinate u_p = (theta_p - lo_p) / (hi_p - lo_p); mu is clamped to [-3, 4]
+ * and log sigma to [-7, 2] wherever they are used.  All buffers are device
+ * memory owned by the caller; calls are asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+
+/* Number of fp32 parameters of a D -> H -> H -> O network (0 on bad sizes). */
+size_t abc_mlp_param_count(int32_t D, int32_t H, int32_t O);
+
+/* Bytes of device workspace abc_mlp_forward / abc_mlp_loss_grad need for a
+ * batch of B rows (0 on bad sizes). */
+size_t abc_mlp_workspace_size(int32_t D, int32_t H, int32_t O, int64_t B);
+
+/* Weights uniform in +-1/sqrt(fan_in) from Philox4x32-10 (counter = parameter
+ * index, key = seed), biases zero.  D, H in 1..4096, O in 1..64. */
+int abc_mlp_init(uint64_t seed, int32_t D, int32_t H, int32_t O, float* params_dev, void* stream);
+
+/* Network input of each voxel TAC: feat[j*(L+1) + l] = y_jl / s_j for l < L and
+ * feat[j*(L+1) + L] = ln(s_j) / 10, s_j = sqrt(sum_l w_l y_jl^2) (the frame
+ * weights of Sec. II-C).  y_dev J x ldy; w_host L weights; L in 1..64. */
+int abc_mlp_features(const float* y_dev, int64_t J, int32_t ldy, int32_t L, const float* w_host, float* feat_dev,
+                     void* stream);
+
+/* out_dev (B x O) = the network applied to the rows of X_dev (B x D).
+ * work_dev: >= abc_mlp_workspace_size(D, H, O, B) bytes (its first 2 B H
+ * floats are left holding the two hidden pre-activations). */
+int abc_mlp_forward(const float* params_dev, int32_t D, int32_t H, int32_t O, const float* X_dev, int64_t B,
+                    float* out_dev, void* work_dev, size_t work_bytes, void* stream);
+
+/* Training loss and gradient: *loss_dev = (1/B) sum_n sum_p -log TN(T_np; mu_np,
+ * sigma_np, [0, 1]) for targets T_dev (B x P, unit-box coordinates in [0, 1])
+ * with O = 2P outputs, and grad_dev (abc_mlp_param_count entries) = its
+ * gradient with respect to the parameters (the bf16-rounded weights are
+ * differentiated as if they were the fp32 ones; a clamped output passes no
+ * gradient).  P in 1..32. */
+int abc_mlp_loss_grad(const float* params_dev, int32_t D, int32_t H, int32_t P, const float* X_dev,
+                      const float* T_dev, int64_t B, void* work_dev, size_t work_bytes, float* grad_dev,
+                      float* loss_dev, void* stream);
+
+/* Training targets: t_dev[n*P + p] = (theta_np - lo_p) / (hi_p - lo_p) clamped to
+ * [0, 1], theta_dev N x ldtheta (the layout of abc_sample_prior); P in 1..8. */
+int abc_unit_box(const float* theta_dev, int64_t N, int32_t ldtheta, int32_t P, const double* lo_host,
+                 const double* hi_host, float* t_dev, void* stream);
+
+/* One Adam step (Kingma and Ba, 2015) with bias correction at step t >= 1:
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps); n entries each. */
+int abc_adam_update(float* params_dev, const float* grad_dev, float* m_dev, float* v_dev, int64_t n, float lr,
+                    float beta1, float beta2, float eps, int32_t t, void* stream);
+
+/* Gaussian decay-weighted noise of Sec. III-A on N simulated TACs:
+ * y_nl = x_nl + l_n sigma_nl z_nl, sigma_nl = sqrt(max(x_nl, 0) exp(lambda t_l) / dt_l)
+ * (t_l the frame mid-time, lambda = ln 2 / half_life), l_n = q_n ||x_n|| / ||sigma_n||,
+ * q_n ~ U(q_lo, q_hi), z ~ N(0, 1) by Box-Muller; the uniforms come from
+ * Philox4x32-10 keyed by seed at counters tied to the global row
+ * first_index + n, so a chunked run reproduces a single call.  L in 1..64. */
+int abc_add_noise(const float* x_dev, int64_t N, int32_t ldx, const abc_frames* frames, double half_life, double q_lo,
+                  double q_hi, uint64_t seed, int64_t first_index, float* y_dev, int32_t ldy, void* stream);
+
+/* Shared memory abc_local_abc needs per block (it must stay <= 227 KB). */
+size_t abc_local_abc_smem_bytes(int32_t T, int32_t L, int32_t M);
+
+/* Importance-weighted local ABC for the irreversible 2TCM, P = 4 parameters
+ * (K1, k2, k3, Vb) on the prior box [lo, hi] (host, 4 entries each, lo >= 0).
+ * For each voxel j: M proposals u_i ~ TN(mu_jp, sigma_jp) on [0, 1] per
+ * parameter, mu and sigma = sigma_scale * exp(log sigma) from prop_dev (J x 8
+ * network outputs, clamped as above; sigma_scale in (0, 100] widens the
+ * proposal), drawn by inverse CDF of the
+ * uniforms ((r_p >> 9) + 1/2) 2^-23, r = Philox4x32-10 at counter
+ * (i, j lo, j hi, 0x4C4F43) and key (seed lo, seed hi); theta = lo + (hi - lo) u; the TAC
+ * of each proposal from
+ *   x_l = Vb cp_l + (1 - Vb) K1 / a (k3 G_l(0) + k2 G_l(a)),  a = k2 + k3,
+ * where table_dev (T x L) holds G(a_i) = frame means of e^{-a_i t} (*) C_p at
+ * a_i = a_max (i / (T - 1))^2 (row 0 = frame means of 1 (*) C_p) and
+ * cp_frames_dev the L frame means of C_p, read by cubic Lagrange interpolation
+ * in i; d_ji = sum_l w_l (y_jl - x_l)^2; the k nearest kept (ties to the lower
+ * proposal index); weights W = (1/q(u)) normalised over the accepted set
+ * (uniform prior).  Outputs (J x 5, columns K1, k2, k3, Vb, K_i = K1 k3/(k2+k3)):
+ * weighted mean, weighted SD sqrt(sum W (v - m)^2), and weighted 2.5 / 97.5 %
+ * quantiles (the smallest accepted value whose cumulative weight reaches the
+ * level); per voxel ess = 1 / sum W^2, dmed = the ((k-1)/2)-th smallest
+ * distance, ynorm = sum_l w_l y_jl^2.  u_dump_dev (J x M x 4) and d_dump_dev
+ * (J x M) receive every proposal and distance when non-NULL.
+ * 1 <= k <= 256, k <= M; T >= 8; lo[1] + lo[2] > 0 and hi[1] + hi[2] <= a_max;
+ * abc_local_abc_smem_bytes(T, L, M) <= 227 KB. */
+int abc_local_abc(const float* y_dev, int64_t J, int32_t ldy, int32_t L, const float* w_host, const float* prop_dev,
+                  const float* table_dev, int32_t T, double a_max, const float* cp_frames_dev, const double* lo_host,
+                  const double* hi_host, int32_t M, int32_t k, float sigma_scale, uint64_t seed, float* mean_dev,
+                  float* sd_dev,
+                  float* qlo_dev, float* qhi_dev, float* ess_dev, float* dmed_dev, float* ynorm_dev,
+                  float* u_dump_dev, float* d_dump_dev, void* stream);
+
 /* Description of the last error on this thread ("" if none). */
 const char* abc_last_error(void);
 

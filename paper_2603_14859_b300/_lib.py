@@ -27,6 +27,9 @@ EXPORTS = [
     "abc_topk_status", "abc_model_select", "abc_summarize", "abc_last_error", "abc_profile_events",
     "abc_debug_gemm_keys", "abc_discrepancy_topk_noalloc", "abc_default_tuning", "abc_set_default_tuning",
     "abc_batch_workspace_size", "abc_batch_discrepancy_topk", "abc_launch_info",
+    "abc_mlp_param_count", "abc_mlp_workspace_size", "abc_mlp_init", "abc_mlp_features", "abc_mlp_forward",
+    "abc_mlp_loss_grad", "abc_adam_update", "abc_add_noise", "abc_local_abc_smem_bytes", "abc_local_abc",
+    "abc_unit_box",
 ]
 
 
@@ -86,10 +89,28 @@ def lib():
     L.abc_batch_workspace_size.restype = sz
     L.abc_batch_discrepancy_topk.argtypes = [ctypes.POINTER(Scan), i32, i32, ctypes.POINTER(Tuning), P, sz, P]
     L.abc_debug_gemm_keys.argtypes = [P, i64, i32, P, i64, i32, i32, P, i32, P, sz, P, i64, P]
+    f32 = ctypes.c_float
+    f64 = ctypes.c_double
+    L.abc_mlp_param_count.argtypes = [i32, i32, i32]
+    L.abc_mlp_param_count.restype = sz
+    L.abc_mlp_workspace_size.argtypes = [i32, i32, i32, i64]
+    L.abc_mlp_workspace_size.restype = sz
+    L.abc_mlp_init.argtypes = [u64, i32, i32, i32, P, P]
+    L.abc_mlp_features.argtypes = [P, i64, i32, i32, P, P, P]
+    L.abc_mlp_forward.argtypes = [P, i32, i32, i32, P, i64, P, P, sz, P]
+    L.abc_mlp_loss_grad.argtypes = [P, i32, i32, i32, P, P, i64, P, sz, P, P, P]
+    L.abc_adam_update.argtypes = [P, P, P, P, i64, f32, f32, f32, f32, i32, P]
+    L.abc_add_noise.argtypes = [P, i64, i32, ctypes.POINTER(Frames), f64, f64, f64, u64, i64, P, i32, P]
+    L.abc_unit_box.argtypes = [P, i64, i32, i32, P, P, P, P]
+    L.abc_local_abc_smem_bytes.argtypes = [i32, i32, i32]
+    L.abc_local_abc_smem_bytes.restype = sz
+    L.abc_local_abc.argtypes = [P, i64, i32, i32, P, P, P, i32, f64, P, P, P, i32, i32, f32, u64,
+                                P, P, P, P, P, P, P, P, P, P]
     for fn in ["abc_feng_input", "abc_sample_prior", "abc_simulate", "abc_discrepancy_topk", "abc_topk_status",
                "abc_model_select", "abc_summarize", "abc_debug_gemm_keys", "abc_profile_events",
                "abc_discrepancy_topk_noalloc", "abc_default_tuning", "abc_set_default_tuning",
-               "abc_batch_discrepancy_topk", "abc_launch_info"]:
+               "abc_batch_discrepancy_topk", "abc_launch_info", "abc_mlp_init", "abc_mlp_features",
+               "abc_mlp_forward", "abc_mlp_loss_grad", "abc_adam_update", "abc_add_noise", "abc_local_abc", "abc_unit_box"]:
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L

@@ -181,3 +181,117 @@ def default_tuning(precision=_lib.ABC_BF16_RESCORE):
     t = _lib.Tuning()
     check(lib().abc_default_tuning(precision, ctypes.byref(t)))
     return dict(bn=t.bn, ctas_per_sm=t.ctas_per_sm, pilot_stride=t.pilot_stride, pilot_factor=t.pilot_factor)
+
+
+# ---------------------------------------------------------------- learned proposal + local ABC
+def _vp(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def mlp_param_count(D, H, O):
+    n = lib().abc_mlp_param_count(D, H, O)
+    if n == 0:
+        raise ValueError("abc_mlp_param_count: bad sizes")
+    return n
+
+
+def mlp_workspace_size(D, H, O, B):
+    n = lib().abc_mlp_workspace_size(D, H, O, B)
+    if n == 0:
+        raise ValueError("abc_mlp_workspace_size: bad sizes")
+    return n
+
+
+def mlp_init(seed, D, H, O, out=None, stream=None):
+    if out is None:
+        out = torch.empty(mlp_param_count(D, H, O), dtype=torch.float32, device="cuda")
+    check(lib().abc_mlp_init(seed, D, H, O, _ptr(out), _stream(stream)))
+    return out
+
+
+def mlp_features(y, L, w, out=None, stream=None):
+    """Network inputs (J x (L+1)) of the voxel TACs y (J x ldy)."""
+    J = y.shape[0]
+    w = _np(w, np.float32)
+    if out is None:
+        out = torch.empty((J, L + 1), dtype=torch.float32, device="cuda")
+    check(lib().abc_mlp_features(_ptr(y), J, y.shape[1], L, _vp(w), _ptr(out), _stream(stream)))
+    return out
+
+
+def mlp_forward(params, D, H, O, X, out=None, work=None, stream=None):
+    B = X.shape[0]
+    if out is None:
+        out = torch.empty((B, O), dtype=torch.float32, device="cuda")
+    if work is None:
+        work = torch.empty(mlp_workspace_size(D, H, O, B), dtype=torch.uint8, device="cuda")
+    check(lib().abc_mlp_forward(_ptr(params), D, H, O, _ptr(X), B, _ptr(out), _ptr(work), work.numel(),
+                                _stream(stream)))
+    return out
+
+
+def mlp_loss_grad(params, D, H, P, X, T, grad=None, loss=None, work=None, stream=None):
+    """(loss tensor [1], grad tensor) of the mean truncated-normal NLL."""
+    B = X.shape[0]
+    if grad is None:
+        grad = torch.empty_like(params)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    if work is None:
+        work = torch.empty(mlp_workspace_size(D, H, 2 * P, B), dtype=torch.uint8, device="cuda")
+    check(lib().abc_mlp_loss_grad(_ptr(params), D, H, P, _ptr(X), _ptr(T), B, _ptr(work), work.numel(), _ptr(grad),
+                                  _ptr(loss), _stream(stream)))
+    return loss, grad
+
+
+def adam_update(params, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    check(lib().abc_adam_update(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), lr, beta1, beta2, eps,
+                                t, _stream(stream)))
+
+
+def unit_box(theta, N, P, lo, hi, out=None, stream=None):
+    lo = _np(lo, np.float64)
+    hi = _np(hi, np.float64)
+    if out is None:
+        out = torch.empty((N, P), dtype=torch.float32, device="cuda")
+    check(lib().abc_unit_box(_ptr(theta), N, theta.shape[1], P, _vp(lo), _vp(hi), _ptr(out), _stream(stream)))
+    return out
+
+
+def add_noise(x, ts, te, half_life, q_lo, q_hi, seed, first_index=0, N=None, out=None, stream=None):
+    N = x.shape[0] if N is None else N
+    ts = _np(ts, np.float64)
+    te = _np(te, np.float64)
+    fr = _lib.Frames(len(ts), ts.ctypes.data, te.ctypes.data)
+    if out is None:
+        out = torch.empty_like(x)
+    check(lib().abc_add_noise(_ptr(x), N, x.shape[1], ctypes.byref(fr), half_life, q_lo, q_hi, seed, first_index,
+                              _ptr(out), out.shape[1], _stream(stream)))
+    return out
+
+
+def local_abc_smem_bytes(T, L, M):
+    return lib().abc_local_abc_smem_bytes(T, L, M)
+
+
+def local_abc(y, L, w, prop, table, a_max, cp_frames, lo, hi, M, k, seed, sigma_scale=1.0, dump=False, out=None,
+              stream=None):
+    """Importance-weighted local ABC (2TCM-irr) -> dict of device tensors."""
+    J = y.shape[0]
+    T = table.shape[0]
+    w = _np(w, np.float32)
+    lo = _np(lo, np.float64)
+    hi = _np(hi, np.float64)
+    dev = dict(device="cuda", dtype=torch.float32)
+    if out is None:
+        out = dict(mean=torch.empty((J, 5), **dev), sd=torch.empty((J, 5), **dev), lo=torch.empty((J, 5), **dev),
+                   hi=torch.empty((J, 5), **dev), ess=torch.empty(J, **dev), dmed=torch.empty(J, **dev),
+                   ynorm=torch.empty(J, **dev))
+    if dump:
+        out["u"] = torch.empty((J, M, 4), **dev)
+        out["d"] = torch.empty((J, M), **dev)
+    check(lib().abc_local_abc(_ptr(y), J, y.shape[1], L, _vp(w), _ptr(prop), _ptr(table), T, a_max, _ptr(cp_frames),
+                              _vp(lo), _vp(hi), M, k, sigma_scale, seed, _ptr(out["mean"]), _ptr(out["sd"]), _ptr(out["lo"]),
+                              _ptr(out["hi"]), _ptr(out["ess"]), _ptr(out["dmed"]), _ptr(out["ynorm"]),
+                              _ptr(out.get("u")), _ptr(out.get("d")), _stream(stream)))
+    return out

@@ -1,0 +1,949 @@
+// Learned proposal for local ABC (a build extra; the paper has no counterpart):
+// a small MLP maps a voxel TAC to a truncated-Gaussian proposal over the
+// 2TCM-irr parameters, and importance-weighted local ABC then draws a few
+// thousand proposals per voxel instead of scanning a million prior draws.
+//
+//  * Network: features (L + 1) -> H -> H -> 2P with GELU, fp32 master weights
+//    used rounded to bf16, fp32 accumulation.  Outputs (mu_p, log sigma_p) in
+//    unit-box coordinates u = (theta - lo) / (hi - lo).
+//  * Loss: mean truncated-normal negative log likelihood of the true u
+//    (mu clamped to [-3, 4], log sigma to [-7, 2]); analytic backward; Adam.
+//  * Training pairs: prior draws -> simulated TACs -> the Gaussian
+//    decay-weighted noise model of Sec. III-A (abc_add_noise), all on the GPU.
+//  * Local ABC: per voxel M proposals u ~ TN(mu, sigma) on [0, 1] by inverse
+//    CDF, their TACs, the k nearest kept, weights prior / proposal = 1 / q(u)
+//    normalised over the accepted set, weighted summaries.  The irreversible
+//    2TCM (Eq. 1-2 with k4 = 0) has
+//      C_t = Vb C_p + (1 - Vb) K1 / a [k3 (1 (*) C_p) + k2 (e^{-a t} (*) C_p)],
+//    a = k2 + k3, so every frame mean is a fixed combination of G(0), G(a) and
+//    the frame mean of C_p, G(a) = frame mean of e^{-a t} (*) C_p.  G is
+//    tabulated once per scan (with abc_simulate) on a_i = a_max (i / (T-1))^2
+//    and read back by the cubic Lagrange interpolant through four nodes.
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "select.cuh"
+
+using namespace vpet;
+
+namespace {
+
+constexpr int MAXL = 64;
+constexpr int GT = 64;          // GEMM tile (M and N)
+constexpr int GK = 16;          // GEMM K step
+constexpr int LA_THREADS = 512;
+constexpr int LA_P = 4;         // K1, k2, k3, Vb
+constexpr int LA_C = LA_P + 1;  // ... and K_i
+constexpr int LA_KMAX = 256;
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float nphi(float z) { return 0.39894228040143268f * expf(-0.5f * z * z); }
+
+// P(a < Z < b), a < b, without cancellation in either tail.
+__device__ __forceinline__ float norm_mass(float a, float b) {
+    constexpr float r2 = 0.70710678118654752f;
+    if (a > 0.0f) return 0.5f * (erfcf(a * r2) - erfcf(b * r2));
+    if (b < 0.0f) return 0.5f * (erfcf(-b * r2) - erfcf(-a * r2));
+    return 1.0f - 0.5f * (erfcf(-a * r2) + erfcf(b * r2));
+}
+
+// ------------------------------------------------------------------ features
+struct FrameW {
+    float w[MAXL];
+};
+
+// f_l = y_l / s (l < L), f_L = log(s) / 10, s = sqrt(sum_l w_l y_l^2) + 1e-30; one warp per voxel
+__global__ void k_features(const float* __restrict__ y, int64_t J, int ldy, int L, FrameW W, float* __restrict__ f) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= J) return;
+    const float* yr = y + j * ldy;
+    float ss = 0.0f;
+    for (int l = lane; l < L; l += 32) ss = fmaf(W.w[l] * yr[l], yr[l], ss);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+    const float s = sqrtf(ss) + 1e-30f;
+    float* fr = f + j * (L + 1);
+    for (int l = lane; l < L; l += 32) fr[l] = yr[l] / s;
+    if (lane == 0) fr[L] = logf(s) * 0.1f;
+}
+
+// ------------------------------------------------------------------ GEMM
+// C[m, n] = sum_k A(m, k) B(k, n) (+ bias[n]), A(m, k) = gelu?(A[m sam + k sak]),
+// B(k, n) = gelu?/bf16?(B[k sbk + n sbn]).  64 x 64 tiles, 256 threads, 4 x 4
+// outputs per thread.  With split-K (gridDim.z > 1) each z-slice adds its
+// partial sum atomically into a zeroed C.
+struct GemmArgs {
+    const float* A;
+    int64_t sam, sak;
+    const float* B;
+    int64_t sbk, sbn;
+    float* C;
+    int64_t ldc;
+    const float* bias;
+    int M, N, K;
+    int actA;    // 1 = GELU of the loaded A value
+    int actB;    // 1 = GELU of the loaded B value
+    int roundB;  // 1 = B rounded to bf16 (weights)
+};
+
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int kchunk) {
+    __shared__ float sa[GK][GT + 4];
+    __shared__ float sb[GK][GT + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+    const int kbeg = blockIdx.z * kchunk, kend = min(g.K, kbeg + kchunk);
+    float acc[4][4] = {};
+    for (int k0 = kbeg; k0 < kend; k0 += GK) {
+        for (int e = threadIdx.x; e < GK * GT; e += 256) {
+            // consecutive threads walk the unit-stride dimension of the operand
+            int kk, mm;
+            if (g.sak == 1) { kk = e % GK; mm = e / GK; } else { kk = e / GT; mm = e % GT; }
+            const int m = m0 + mm, k = k0 + kk;
+            float a = 0.0f;
+            if (m < g.M && k < kend) {
+                a = g.A[m * g.sam + k * g.sak];
+                if (g.actA) a = gelu(a);
+            }
+            sa[kk][mm] = a;
+        }
+        for (int e = threadIdx.x; e < GK * GT; e += 256) {
+            int kk, nn;
+            if (g.sbk == 1) { kk = e % GK; nn = e / GK; } else { kk = e / GT; nn = e % GT; }
+            const int n = n0 + nn, k = k0 + kk;
+            float b = 0.0f;
+            if (n < g.N && k < kend) {
+                b = g.B[k * g.sbk + n * g.sbn];
+                if (g.actB) b = gelu(b);
+                if (g.roundB) b = bf16r(b);
+            }
+            sb[kk][nn] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { av[i] = sa[kk][ty * 4 + i]; bv[i] = sb[kk][tx * 4 + i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(av[i], bv[q], acc[i][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty * 4 + i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int n = n0 + tx * 4 + q;
+            if (n >= g.N) continue;
+            float v = acc[i][q];
+            if (g.bias && blockIdx.z == 0) v += g.bias[n];
+            float* c = g.C + (int64_t)m * g.ldc + n;
+            if (gridDim.z > 1) atomicAdd(c, v);
+            else *c = v;
+        }
+    }
+}
+
+int g_sms = 0;
+
+int gemm(const GemmArgs& a, cudaStream_t s) {
+    if (g_sms == 0) {
+        int dev = 0;
+        VPET_CUDA(cudaGetDevice(&dev));
+        VPET_CUDA(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int64_t tiles = vpet_ceil_div(a.N, GT) * vpet_ceil_div(a.M, GT);
+    // split K when the output has too few tiles to fill the GPU (weight gradients)
+    int64_t split = 1;
+    if (tiles < g_sms && a.K >= 8 * GK) {
+        split = vpet_ceil_div(2 * g_sms, tiles);
+        const int64_t maxsplit = a.K / (4 * GK);
+        if (split > maxsplit) split = maxsplit;
+        if (split < 1) split = 1;
+    }
+    const int kchunk = (int)vpet_round_up(vpet_ceil_div(a.K, split), GK);
+    split = vpet_ceil_div(a.K, kchunk);
+    if (split > 1) {
+        VPET_ARG(a.ldc == a.N, "gemm: split-K needs a contiguous output");
+        VPET_CUDA(cudaMemsetAsync(a.C, 0, sizeof(float) * (size_t)a.M * a.N, s));
+    }
+    const dim3 grid((unsigned)vpet_ceil_div(a.N, GT), (unsigned)vpet_ceil_div(a.M, GT), (unsigned)split);
+    k_gemm<<<grid, 256, 0, s>>>(a, kchunk);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}
+
+// dZ = dH * gelu'(Z)
+__global__ void k_gelu_back(const float* __restrict__ dh, const float* __restrict__ z, float* __restrict__ dz,
+                            int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dz[i] = dh[i] * gelu_d(z[i]);
+}
+
+// out[n] = sum_b X[b, n]: a block per 32 columns, rows split over its 8 warps
+__global__ void k_colsum(const float* __restrict__ x, int B, int N, float* __restrict__ out) {
+    __shared__ float part[8][33];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + lane;
+    float s = 0.0f;
+    if (n < N)
+        for (int b = wp; b < B; b += 8) s += x[(int64_t)b * N + n];
+    part[wp][lane] = s;
+    __syncthreads();
+    if (wp == 0 && n < N) {
+        float t = 0.0f;
+        for (int q = 0; q < 8; ++q) t += part[q][lane];
+        out[n] = t;
+    }
+}
+
+// truncated-normal NLL of targets T (B x P) under out (B x 2P); dout = d(mean NLL) / d(out)
+__global__ void k_trunc_nll(const float* __restrict__ out, const float* __restrict__ T, int B, int P,
+                            float* __restrict__ dout, float* __restrict__ loss) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (e < (int64_t)B * P) {
+        const int64_t n = e / P;
+        const int p = (int)(e - n * P);
+        float mu = out[n * 2 * P + 2 * p], s = out[n * 2 * P + 2 * p + 1];
+        const bool mu_in = mu >= -3.0f && mu <= 4.0f, s_in = s >= -7.0f && s <= 2.0f;
+        mu = fminf(fmaxf(mu, -3.0f), 4.0f);
+        s = fminf(fmaxf(s, -7.0f), 2.0f);
+        const float sg = expf(s), t = T[e];
+        const float z = (t - mu) / sg, a = -mu / sg, b = (1.0f - mu) / sg;
+        const float Z = fmaxf(norm_mass(a, b), 1e-30f);
+        l = s + 0.5f * z * z + logf(Z) + 0.91893853320467274f;
+        const float dmu = -z / sg + (nphi(a) - nphi(b)) / (sg * Z);
+        const float ds = 1.0f - z * z + (a * nphi(a) - b * nphi(b)) / Z;
+        dout[n * 2 * P + 2 * p] = mu_in ? dmu / B : 0.0f;
+        dout[n * 2 * P + 2 * p + 1] = s_in ? ds / B : 0.0f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, l / B);
+}
+
+// t[n, p] = (theta[n, p] - lo_p) / (hi_p - lo_p), clamped to [0, 1]
+struct Box {
+    float lo[8], inv[8];
+};
+__global__ void k_unit_box(const float* __restrict__ th, int64_t N, int ldt, int P, Box b, float* __restrict__ t) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * P) return;
+    const int64_t n = e / P;
+    const int p = (int)(e - n * P);
+    t[e] = fminf(fmaxf((th[n * ldt + p] - b.lo[p]) * b.inv[p], 0.0f), 1.0f);
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ------------------------------------------------------------------ Philox4x32-10 (Salmon et al., SC'11)
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+// uniform in (0, 1) from the top 23 bits: ((r >> 9) + 1/2) 2^-23, exact in fp32
+__device__ __forceinline__ float u01(uint32_t r) { return ((float)(r >> 9) + 0.5f) * 1.1920928955078125e-7f; }
+
+// weights W ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)), zero biases
+__global__ void k_mlp_init(float* p, int D, int H, int O, uint64_t seed) {
+    const int64_t n1 = (int64_t)H * D, n2 = n1 + H, n3 = n2 + (int64_t)H * H, n4 = n3 + H, n5 = n4 + (int64_t)O * H,
+                  n6 = n5 + O;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n6) return;
+    float fan = 0.0f;
+    if (i < n1) fan = (float)D;
+    else if (i >= n2 && i < n3) fan = (float)H;
+    else if (i >= n4 && i < n5) fan = (float)H;
+    if (fan == 0.0f) { p[i] = 0.0f; return; }
+    const uint4 r = philox(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0x6D6C70u, 0u), (uint32_t)seed,
+                           (uint32_t)(seed >> 32));
+    p[i] = (2.0f * u01(r.x) - 1.0f) * rsqrtf(fan);
+}
+
+// Gaussian decay-weighted noise (Sec. III-A): y = x + l_n sigma z with
+// sigma_l = sqrt(max(x_l, 0) exp(lambda t_mid,l) / dt_l), l_n = q ||x|| / ||sigma||,
+// q ~ U(q_lo, q_hi), z ~ N(0, 1) by Box-Muller on Philox uniforms; one warp per row.
+struct NoiseFrames {
+    int L;
+    float tmid[MAXL];
+    float dt[MAXL];
+};
+
+__global__ void k_add_noise(const float* __restrict__ x, int64_t N, int ldx, NoiseFrames F, float lambda, float q_lo,
+                            float q_hi, uint64_t seed, int64_t first, float* __restrict__ y, int ldy) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (n >= N) return;
+    const uint64_t g = (uint64_t)(first + n);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const float* xr = x + n * ldx;
+    float sx = 0.0f, ss = 0.0f, sig[2] = {0.0f, 0.0f}, z[2] = {0.0f, 0.0f}, xv[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int l = lane + 32 * h;
+        if (l >= F.L) continue;
+        xv[h] = xr[l];
+        const float s = sqrtf(fmaxf(xv[h], 0.0f) * expf(lambda * F.tmid[l]) / F.dt[l]);
+        sig[h] = s;
+        sx = fmaf(xv[h], xv[h], sx);
+        ss = fmaf(s, s, ss);
+        const uint4 r = philox(make_uint4((uint32_t)g, (uint32_t)(g >> 32), 0x4E4F49u, (uint32_t)l), k0, k1);
+        z[h] = sqrtf(-2.0f * logf(u01(r.x))) * cospif(2.0f * u01(r.y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xFFFFFFFFu, sx, o);
+        ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+    }
+    const uint4 rq = philox(make_uint4((uint32_t)g, (uint32_t)(g >> 32), 0x515556u, 0u), k0, k1);
+    const float q = q_lo + (q_hi - q_lo) * u01(rq.x);
+    const float ln = ss > 0.0f ? q * sqrtf(sx) / sqrtf(ss) : 0.0f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int l = lane + 32 * h;
+        if (l < F.L) y[n * ldy + l] = xv[h] + ln * sig[h] * z[h];
+    }
+}
+
+// ------------------------------------------------------------------ local importance-weighted ABC
+struct LocalArgs {
+    const float* y;
+    int64_t J;
+    int ldy, L;
+    float w[MAXL];
+    const float* prop;     // J x 2P network outputs (mu, log sigma) per parameter
+    const float* table;    // T x L: row i = G(a_i); row 0 = G(0) = frame means of 1 (*) C_p
+    const float* cpf;      // L frame means of C_p
+    int T, ldt;            // ldt: table row stride in shared memory (odd)
+    float a_max;
+    float lo[LA_P], hi[LA_P];
+    int M, k;
+    float sigma_scale;     // proposal widening: sigma = sigma_scale exp(clamped log sigma)
+    uint64_t seed;
+    float* mean;           // J x 5: K1, k2, k3, Vb, K_i
+    float* sd;
+    float* qlo;
+    float* qhi;
+    float* ess;            // J
+    float* dmed;           // J: median accepted distance
+    float* ynorm;          // J: sum_l w_l y_l^2
+    float* u_dump;         // optional J x M x P proposals (tests)
+    float* d_dump;         // optional J x M distances (tests)
+};
+
+struct TnParams {         // truncated normal on [0, 1], per voxel and parameter
+    float mu, sg, lnorm;  // lnorm = log sigma + log Z + log sqrt(2 pi)
+    float pa, pb;         // CDF at the bounds, taken in the tail where it is accurate
+    int upper;            // pa, pb are upper-tail probabilities
+};
+
+__device__ __forceinline__ TnParams tn_params(float mu_raw, float s_raw, float sigma_scale) {
+    TnParams t;
+    t.mu = fminf(fmaxf(mu_raw, -3.0f), 4.0f);
+    const float s = fminf(fmaxf(s_raw, -7.0f), 2.0f) + logf(sigma_scale);
+    t.sg = expf(s);
+    const float a = -t.mu / t.sg, b = (1.0f - t.mu) / t.sg;
+    t.lnorm = s + logf(fmaxf(norm_mass(a, b), 1e-30f)) + 0.91893853320467274f;
+    t.upper = a + b > 0.0f;
+    if (t.upper) { t.pa = normcdff(-a); t.pb = normcdff(-b); }
+    else { t.pa = normcdff(a); t.pb = normcdff(b); }
+    return t;
+}
+
+// inverse-CDF draw: u uniform in (0, 1) -> t in [0, 1]
+__device__ __forceinline__ float tn_draw(const TnParams& t, float u) {
+    // pa (1 - u) + pb u: two non-negative terms (1 - u is exact for these uniforms), no cancellation
+    const float p = fminf(fmaxf(fmaf(t.pa, 1.0f - u, u * t.pb), 1e-30f), 1.0f - 6e-8f);
+    const float zq = normcdfinvf(p);
+    const float v = t.mu + t.sg * (t.upper ? -zq : zq);
+    return fminf(fmaxf(v, 0.0f), 1.0f);
+}
+
+__device__ __forceinline__ float tn_logpdf(const TnParams& t, float v) {
+    const float z = (v - t.mu) / t.sg;
+    return -0.5f * z * z - t.lnorm;
+}
+
+// the P proposal coordinates of proposal i of voxel j
+__device__ __forceinline__ void draw_u(const LocalArgs& A, const TnParams* tp, int64_t j, int i, float* u) {
+    const uint4 r = philox(make_uint4((uint32_t)i, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), 0x4C4F43u),
+                           (uint32_t)A.seed, (uint32_t)(A.seed >> 32));
+    u[0] = tn_draw(tp[0], u01(r.x));
+    u[1] = tn_draw(tp[1], u01(r.y));
+    u[2] = tn_draw(tp[2], u01(r.z));
+    u[3] = tn_draw(tp[3], u01(r.w));
+}
+
+// Block-wide radix select over n fp32 keys in shared memory: the exact key of
+// the given rank (0-based), returned to all threads.
+__device__ uint32_t block_select(const float* keys, int n, int rank, uint32_t* hist, int* sh) {
+    uint32_t prefix = 0;
+    int r = rank;
+    for (int lv = 0; lv < 4; ++lv) {
+        const int shift = 24 - 8 * lv;
+        const uint32_t mask = lv == 0 ? 0u : (0xFFFFFFFFu << (shift + 8));
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t k = f2key(keys[i]);
+            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            uint32_t loc[8], sum = 0;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) { loc[b] = hist[lane * 8 + b]; sum += loc[b]; }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            uint32_t c = incl - sum;
+            int found = -1, newr = 0;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                if (found < 0 && c + loc[b] > (uint32_t)r) { found = lane * 8 + b; newr = r - (int)c; }
+                c += loc[b];
+            }
+            const uint32_t who = __ballot_sync(0xFFFFFFFFu, found >= 0);
+            const int src = who ? __ffs(who) - 1 : 31;
+            const int bin = __shfl_sync(0xFFFFFFFFu, found, src);
+            const int nr = __shfl_sync(0xFFFFFFFFu, newr, src);
+            if (lane == 0) { sh[0] = bin < 0 ? 255 : bin; sh[1] = nr; }
+        }
+        __syncthreads();
+        prefix |= (uint32_t)sh[0] << shift;
+        r = sh[1];
+        __syncthreads();
+    }
+    return prefix;
+}
+
+__device__ __forceinline__ float block_sum(float v, float* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.0f;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    return t;
+}
+
+__device__ __forceinline__ float block_max(float v, float* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = -3.0e38f;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = fmaxf(t, red[q]);
+    return t;
+}
+
+// Persistent blocks over voxels; the G table stays in shared memory for the
+// block's lifetime.  Per voxel: M proposals and distances, exact k-th distance
+// by radix select, ordered compaction of the accepted set (ties at the k-th
+// distance to the lower proposal index), weights, bitonic sort of the accepted
+// values of all five columns, weighted quantiles.
+__global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    float* tab = (float*)sm;                              // T x ldt
+    float* cps = tab + (size_t)A.T * A.ldt;               // MAXL
+    float* ys = cps + MAXL;                               // MAXL
+    float* keys = ys + MAXL;                              // M
+    int32_t* acc = (int32_t*)(keys + A.M);                // LA_KMAX accepted proposal indices
+    float* wacc = (float*)(acc + LA_KMAX);                // LA_KMAX normalised weights
+    float* sv = wacc + LA_KMAX;                           // LA_C x LA_KMAX values (sorted in place)
+    float* sw = sv + LA_C * LA_KMAX;                      // LA_C x LA_KMAX weights (permuted alongside)
+    float* red = sw + LA_C * LA_KMAX;                     // 64
+    uint32_t* hist = (uint32_t*)(red + 64);               // 256
+    int* sh = (int*)(hist + 256);                         // 8
+    int* wcnt = sh + 8;                                   // 2 x 16 warp counts
+    __shared__ TnParams tp[LA_P];
+
+    for (int e = threadIdx.x; e < A.T * A.L; e += blockDim.x) tab[(e / A.L) * A.ldt + e % A.L] = A.table[e];
+    for (int l = threadIdx.x; l < A.L; l += blockDim.x) cps[l] = A.cpf[l];
+    const float scale = (float)(A.T - 1) * rsqrtf(A.a_max);
+    const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+
+    for (int64_t j = blockIdx.x; j < A.J; j += gridDim.x) {
+        __syncthreads();
+        for (int l = threadIdx.x; l < A.L; l += blockDim.x) ys[l] = A.y[j * A.ldy + l];
+        if (threadIdx.x < LA_P)
+            tp[threadIdx.x] = tn_params(A.prop[j * 2 * LA_P + 2 * threadIdx.x],
+                                        A.prop[j * 2 * LA_P + 2 * threadIdx.x + 1], A.sigma_scale);
+        __syncthreads();
+
+        // proposals, their TACs and distances
+        for (int i = threadIdx.x; i < A.M; i += blockDim.x) {
+            float u[LA_P];
+            draw_u(A, tp, j, i, u);
+            const float K1 = A.lo[0] + (A.hi[0] - A.lo[0]) * u[0];
+            const float k2 = A.lo[1] + (A.hi[1] - A.lo[1]) * u[1];
+            const float k3 = A.lo[2] + (A.hi[2] - A.lo[2]) * u[2];
+            const float Vb = A.lo[3] + (A.hi[3] - A.lo[3]) * u[3];
+            const float a = k2 + k3;
+            const float pos = scale * sqrtf(fminf(fmaxf(a, 0.0f), A.a_max));
+            const int i0 = max(1, min((int)pos, A.T - 3));
+            const float t = pos - (float)i0;
+            // Lagrange basis on the nodes i0-1, i0, i0+1, i0+2
+            const float tm = t - 1.0f, tp1 = t + 1.0f, t2 = t - 2.0f;
+            const float c0 = -t * tm * t2 * (1.0f / 6.0f), c1 = 0.5f * tp1 * tm * t2, c2 = -0.5f * tp1 * t * t2,
+                        c3 = tp1 * t * tm * (1.0f / 6.0f);
+            const float ca = (1.0f - Vb) * K1 / a;
+            const float* r0 = tab + (size_t)(i0 - 1) * A.ldt;
+            float d = 0.0f;
+            for (int l = 0; l < A.L; ++l) {
+                const float g =
+                    fmaf(c0, r0[l], fmaf(c1, r0[A.ldt + l], fmaf(c2, r0[2 * A.ldt + l], c3 * r0[3 * A.ldt + l])));
+                const float x = fmaf(ca, fmaf(k3, tab[l], k2 * g), Vb * cps[l]);
+                const float e = ys[l] - x;
+                d = fmaf(A.w[l] * e, e, d);
+            }
+            keys[i] = d;
+            if (A.u_dump) {
+#pragma unroll
+                for (int p = 0; p < LA_P; ++p) A.u_dump[((size_t)j * A.M + i) * LA_P + p] = u[p];
+            }
+            if (A.d_dump) A.d_dump[(size_t)j * A.M + i] = d;
+        }
+        __syncthreads();
+
+        // accepted set: every key below the k-th, then the lowest-index keys equal to it
+        const uint32_t K = block_select(keys, A.M, A.k - 1, hist, sh);
+        int nless = 0;
+        for (int i = threadIdx.x; i < A.M; i += blockDim.x) nless += f2key(keys[i]) < K;
+        const int n_less = (int)(block_sum((float)nless, red) + 0.5f);
+        const int need_ties = A.k - n_less;
+        int base_less = 0, base_tie = 0;
+        for (int c0 = 0; c0 < A.M; c0 += blockDim.x) {
+            const int i = c0 + threadIdx.x;
+            const uint32_t kk = i < A.M ? f2key(keys[i]) : 0xFFFFFFFFu;
+            const bool isl = i < A.M && kk < K, ist = i < A.M && kk == K;
+            const uint32_t bl = __ballot_sync(0xFFFFFFFFu, isl), bt = __ballot_sync(0xFFFFFFFFu, ist);
+            __syncthreads();
+            if (lane == 0) { wcnt[wp] = __popc(bl); wcnt[16 + wp] = __popc(bt); }
+            __syncthreads();
+            int pl = base_less, pt = base_tie, tl = 0, tt = 0;
+            for (int q = 0; q < nw; ++q) {
+                if (q < wp) { pl += wcnt[q]; pt += wcnt[16 + q]; }
+                tl += wcnt[q];
+                tt += wcnt[16 + q];
+            }
+            const uint32_t below = (1u << lane) - 1u;
+            pl += __popc(bl & below);
+            pt += __popc(bt & below);
+            if (isl) acc[pl + min(pt, need_ties)] = i;
+            else if (ist && pt < need_ties) acc[pl + pt] = i;
+            base_less += tl;
+            base_tie += tt;
+        }
+        __syncthreads();
+
+        // weights 1/q, normalised over the accepted set; accepted values
+        float lw = -3.0e38f;
+        float vals[LA_C] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (threadIdx.x < A.k) {
+            float u[LA_P];
+            draw_u(A, tp, j, acc[threadIdx.x], u);
+            lw = 0.0f;
+#pragma unroll
+            for (int p = 0; p < LA_P; ++p) {
+                lw -= tn_logpdf(tp[p], u[p]);
+                vals[p] = A.lo[p] + (A.hi[p] - A.lo[p]) * u[p];
+            }
+            vals[4] = vals[0] * vals[2] / (vals[1] + vals[2]);
+        }
+        const float lmax = block_max(lw, red);
+        const float wu = threadIdx.x < A.k ? expf(lw - lmax) : 0.0f;
+        const float wsum = block_sum(wu, red);
+        const float W = wu / wsum;
+        const float s2 = block_sum(W * W, red);
+        if (threadIdx.x < LA_KMAX) {
+            wacc[threadIdx.x] = W;
+#pragma unroll
+            for (int c = 0; c < LA_C; ++c) {
+                sv[c * LA_KMAX + threadIdx.x] = threadIdx.x < A.k ? vals[c] : __int_as_float(0x7F800000);
+                sw[c * LA_KMAX + threadIdx.x] = W;
+            }
+        }
+        // weighted mean and SD per column (fp64 sums over the k accepted)
+        __syncthreads();
+        if (wp < LA_C) {
+            const int c = wp;
+            double m = 0.0;
+            for (int r = lane; r < A.k; r += 32) m += (double)wacc[r] * sv[c * LA_KMAX + r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xFFFFFFFFu, m, o);
+            double v2 = 0.0;
+            for (int r = lane; r < A.k; r += 32) {
+                const double e = (double)sv[c * LA_KMAX + r] - m;
+                v2 += (double)wacc[r] * e * e;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xFFFFFFFFu, v2, o);
+            if (lane == 0) {
+                A.mean[j * LA_C + c] = (float)m;
+                A.sd[j * LA_C + c] = (float)sqrt(v2);
+            }
+        }
+        if (threadIdx.x == 0) {
+            A.ess[j] = 1.0f / s2;
+            float yn = 0.0f;
+            for (int l = 0; l < A.L; ++l) yn = fmaf(A.w[l] * ys[l], ys[l], yn);
+            A.ynorm[j] = yn;
+        }
+        // bitonic sort of the five 256-entry columns by value, weights alongside
+        for (int size = 2; size <= LA_KMAX; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                __syncthreads();
+                for (int e = threadIdx.x; e < LA_C * (LA_KMAX / 2); e += blockDim.x) {
+                    const int c = e / (LA_KMAX / 2), q = e % (LA_KMAX / 2);
+                    const int i = 2 * q - (q & (stride - 1));
+                    const int pi = i + stride;
+                    const bool asc = (i & size) == 0;
+                    float* v = sv + c * LA_KMAX;
+                    float* ww = sw + c * LA_KMAX;
+                    const float a = v[i], b = v[pi];
+                    if ((a > b) == asc) {
+                        v[i] = b;
+                        v[pi] = a;
+                        const float t = ww[i];
+                        ww[i] = ww[pi];
+                        ww[pi] = t;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // weighted 2.5 / 97.5 % quantiles: smallest value whose cumulative weight reaches q
+        if (wp < LA_C) {
+            const int c = wp;
+            const float* v = sv + c * LA_KMAX;
+            const float* ww = sw + c * LA_KMAX;
+            constexpr int PER = LA_KMAX / 32;
+            float loc[PER], s = 0.0f;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) { s += ww[lane * PER + q]; loc[q] = s; }
+            float incl = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const float excl = incl - s;
+            int fl = LA_KMAX, fh = LA_KMAX;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int r = lane * PER + q;
+                if (r < A.k) {
+                    if (fl == LA_KMAX && excl + loc[q] >= 0.025f) fl = r;
+                    if (fh == LA_KMAX && excl + loc[q] >= 0.975f) fh = r;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                fl = min(fl, __shfl_xor_sync(0xFFFFFFFFu, fl, o));
+                fh = min(fh, __shfl_xor_sync(0xFFFFFFFFu, fh, o));
+            }
+            if (lane == 0) {
+                A.qlo[j * LA_C + c] = v[min(fl, A.k - 1)];
+                A.qhi[j * LA_C + c] = v[min(fh, A.k - 1)];
+            }
+        }
+        // median accepted distance: the ((k - 1) / 2)-th smallest key
+        const uint32_t Km = block_select(keys, A.M, (A.k - 1) / 2, hist, sh);
+        if (threadIdx.x == 0) A.dmed[j] = key2f(Km);
+    }
+}
+
+int mlp_dims_ok(int D, int H, int O) {
+    VPET_ARG(D >= 1 && D <= 4096 && H >= 1 && H <= 4096 && O >= 1 && O <= 64, "mlp: dimensions out of range");
+    return ABC_OK;
+}
+
+size_t mlp_params(int D, int H, int O) { return (size_t)H * D + H + (size_t)H * H + H + (size_t)O * H + O; }
+
+// forward pass: z1 = X bf16(W1)^T + b1, z2 = gelu(z1) bf16(W2)^T + b2, out = gelu(z2) bf16(W3)^T + b3
+int mlp_forward(const float* prm, int D, int H, int O, const float* X, int64_t B, float* out, float* z1, float* z2,
+                cudaStream_t s) {
+    const float* W1 = prm;
+    const float* b1 = W1 + (size_t)H * D;
+    const float* W2 = b1 + H;
+    const float* b2 = W2 + (size_t)H * H;
+    const float* W3 = b2 + H;
+    const float* b3 = W3 + (size_t)O * H;
+    const int Bi = (int)B;
+    int rc;
+    if ((rc = gemm(GemmArgs{X, D, 1, W1, 1, D, z1, H, b1, Bi, H, D, 0, 0, 1}, s))) return rc;
+    if ((rc = gemm(GemmArgs{z1, H, 1, W2, 1, H, z2, H, b2, Bi, H, H, 1, 0, 1}, s))) return rc;
+    return gemm(GemmArgs{z2, H, 1, W3, 1, H, out, O, b3, Bi, O, H, 1, 0, 1}, s);
+}
+
+}  // namespace
+
+extern "C" size_t abc_mlp_param_count(int32_t D, int32_t H, int32_t O) {
+    if (D < 1 || H < 1 || O < 1) return 0;
+    return mlp_params(D, H, O);
+}
+
+extern "C" size_t abc_mlp_workspace_size(int32_t D, int32_t H, int32_t O, int64_t B) {
+    if (D < 1 || H < 1 || O < 1 || B < 1) return 0;
+    // z1, z2, dh, dz (B x H each), out, dout (B x O each)
+    return sizeof(float) * ((size_t)B * H * 4 + (size_t)B * O * 2) + 256;
+}
+
+extern "C" int abc_mlp_init(uint64_t seed, int32_t D, int32_t H, int32_t O, float* params_dev, void* stream) {
+    vpet::clear_error();
+    int rc = mlp_dims_ok(D, H, O);
+    if (rc) return rc;
+    VPET_ARG(params_dev, "abc_mlp_init: null pointer");
+    const int64_t n = (int64_t)mlp_params(D, H, O);
+    k_mlp_init<<<(unsigned)vpet_ceil_div(n, 256), 256, 0, (cudaStream_t)stream>>>(params_dev, D, H, O, seed);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}
+
+extern "C" int abc_mlp_features(const float* y_dev, int64_t J, int32_t ldy, int32_t L, const float* w_host,
+                                float* feat_dev, void* stream) {
+    vpet::clear_error();
+    VPET_ARG(w_host, "abc_mlp_features: null weights");
+    VPET_ARG(L >= 1 && L <= MAXL && ldy >= L && J >= 0, "abc_mlp_features: bad sizes");
+    VPET_ARG(J == 0 || (y_dev && feat_dev), "abc_mlp_features: null pointer");
+    if (J == 0) return ABC_OK;
+    FrameW W;
+    memset(&W, 0, sizeof W);
+    for (int l = 0; l < L; ++l) W.w[l] = w_host[l];
+    k_features<<<(unsigned)vpet_ceil_div(J, 8), 256, 0, (cudaStream_t)stream>>>(y_dev, J, ldy, L, W, feat_dev);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}
+
+extern "C" int abc_mlp_forward(const float* params_dev, int32_t D, int32_t H, int32_t O, const float* X_dev,
+                               int64_t B, float* out_dev, void* work_dev, size_t work_bytes, void* stream) {
+    vpet::clear_error();
+    int rc = mlp_dims_ok(D, H, O);
+    if (rc) return rc;
+    VPET_ARG(B >= 1 && B < (1 << 30), "abc_mlp_forward: batch must be in [1, 2^30)");
+    VPET_ARG(params_dev && X_dev && out_dev && work_dev, "abc_mlp_forward: null pointer");
+    if (work_bytes < abc_mlp_workspace_size(D, H, O, B)) {
+        vpet::set_error("abc_mlp_forward: workspace too small");
+        return ABC_ERR_WORKSPACE;
+    }
+    float* z1 = (float*)work_dev;
+    float* z2 = z1 + (size_t)B * H;
+    return mlp_forward(params_dev, D, H, O, X_dev, B, out_dev, z1, z2, (cudaStream_t)stream);
+}
+
+extern "C" int abc_mlp_loss_grad(const float* params_dev, int32_t D, int32_t H, int32_t P, const float* X_dev,
+                                 const float* T_dev, int64_t B, void* work_dev, size_t work_bytes, float* grad_dev,
+                                 float* loss_dev, void* stream) {
+    vpet::clear_error();
+    VPET_ARG(P >= 1 && P <= 32, "abc_mlp_loss_grad: P must be in [1, 32]");
+    const int O = 2 * P;
+    int rc = mlp_dims_ok(D, H, O);
+    if (rc) return rc;
+    VPET_ARG(B >= 1 && B < (1 << 30), "abc_mlp_loss_grad: batch must be in [1, 2^30)");
+    VPET_ARG(params_dev && X_dev && T_dev && grad_dev && loss_dev && work_dev, "abc_mlp_loss_grad: null pointer");
+    if (work_bytes < abc_mlp_workspace_size(D, H, O, B)) {
+        vpet::set_error("abc_mlp_loss_grad: workspace too small");
+        return ABC_ERR_WORKSPACE;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float* z1 = (float*)work_dev;
+    float* z2 = z1 + (size_t)B * H;
+    float* dh = z2 + (size_t)B * H;
+    float* dz = dh + (size_t)B * H;
+    float* out = dz + (size_t)B * H;
+    float* dout = out + (size_t)B * O;
+    if ((rc = mlp_forward(params_dev, D, H, O, X_dev, B, out, z1, z2, s))) return rc;
+    VPET_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), s));
+    k_trunc_nll<<<(unsigned)vpet_ceil_div(B * P, 256), 256, 0, s>>>(out, T_dev, (int)B, P, dout, loss_dev);
+    VPET_LAUNCH_CHECK();
+    const float* W2 = params_dev + (size_t)H * D + H;
+    const float* W3 = W2 + (size_t)H * H + H;
+    float* gW1 = grad_dev;
+    float* gb1 = gW1 + (size_t)H * D;
+    float* gW2 = gb1 + H;
+    float* gb2 = gW2 + (size_t)H * H;
+    float* gW3 = gb2 + H;
+    float* gb3 = gW3 + (size_t)O * H;
+    const int Bi = (int)B;
+    // layer 3: gW3 = dout^T gelu(z2), gb3 = colsum(dout), dh = dout bf16(W3)
+    if ((rc = gemm(GemmArgs{dout, 1, O, z2, H, 1, gW3, H, nullptr, O, H, Bi, 0, 1, 0}, s))) return rc;
+    k_colsum<<<(unsigned)vpet_ceil_div(O, 32), 256, 0, s>>>(dout, Bi, O, gb3);
+    VPET_LAUNCH_CHECK();
+    if ((rc = gemm(GemmArgs{dout, O, 1, W3, H, 1, dh, H, nullptr, Bi, H, O, 0, 0, 1}, s))) return rc;
+    // layer 2: dz = dh gelu'(z2), gW2 = dz^T gelu(z1), gb2 = colsum(dz), dh = dz bf16(W2)
+    k_gelu_back<<<(unsigned)vpet_ceil_div(B * H, 256), 256, 0, s>>>(dh, z2, dz, B * H);
+    VPET_LAUNCH_CHECK();
+    if ((rc = gemm(GemmArgs{dz, 1, H, z1, H, 1, gW2, H, nullptr, H, H, Bi, 0, 1, 0}, s))) return rc;
+    k_colsum<<<(unsigned)vpet_ceil_div(H, 32), 256, 0, s>>>(dz, Bi, H, gb2);
+    VPET_LAUNCH_CHECK();
+    if ((rc = gemm(GemmArgs{dz, H, 1, W2, H, 1, dh, H, nullptr, Bi, H, H, 0, 0, 1}, s))) return rc;
+    // layer 1: dz = dh gelu'(z1), gW1 = dz^T X, gb1 = colsum(dz)
+    k_gelu_back<<<(unsigned)vpet_ceil_div(B * H, 256), 256, 0, s>>>(dh, z1, dz, B * H);
+    VPET_LAUNCH_CHECK();
+    if ((rc = gemm(GemmArgs{dz, 1, H, X_dev, D, 1, gW1, D, nullptr, H, D, Bi, 0, 0, 0}, s))) return rc;
+    k_colsum<<<(unsigned)vpet_ceil_div(H, 32), 256, 0, s>>>(dz, Bi, H, gb1);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}
+
+extern "C" int abc_unit_box(const float* theta_dev, int64_t N, int32_t ldtheta, int32_t P, const double* lo_host,
+                            const double* hi_host, float* t_dev, void* stream) {
+    vpet::clear_error();
+    VPET_ARG(lo_host && hi_host, "abc_unit_box: null bounds");
+    VPET_ARG(P >= 1 && P <= 8 && ldtheta >= P && N >= 0, "abc_unit_box: bad sizes");
+    VPET_ARG(N == 0 || (theta_dev && t_dev), "abc_unit_box: null pointer");
+    Box b;
+    memset(&b, 0, sizeof b);
+    for (int p = 0; p < P; ++p) {
+        VPET_ARG(hi_host[p] > lo_host[p], "abc_unit_box: need lo < hi");
+        b.lo[p] = (float)lo_host[p];
+        b.inv[p] = (float)(1.0 / (hi_host[p] - lo_host[p]));
+    }
+    if (N == 0) return ABC_OK;
+    k_unit_box<<<(unsigned)vpet_ceil_div(N * P, 256), 256, 0, (cudaStream_t)stream>>>(theta_dev, N, ldtheta, P, b,
+                                                                                     t_dev);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}
+
+extern "C" int abc_adam_update(float* params_dev, const float* grad_dev, float* m_dev, float* v_dev, int64_t n,
+                               float lr, float beta1, float beta2, float eps, int32_t t, void* stream) {
+    vpet::clear_error();
+    VPET_ARG(params_dev && grad_dev && m_dev && v_dev, "abc_adam_update: null pointer");
+    VPET_ARG(n >= 1 && t >= 1 && beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps > 0.0f,
+             "abc_adam_update: bad arguments");
+    const float c1 = 1.0f - powf(beta1, (float)t), c2 = 1.0f - powf(beta2, (float)t);
+    k_adam<<<(unsigned)vpet_ceil_div(n, 256), 256, 0, (cudaStream_t)stream>>>(params_dev, grad_dev, m_dev, v_dev, n,
+                                                                              lr, beta1, beta2, eps, c1, c2);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}
+
+extern "C" int abc_add_noise(const float* x_dev, int64_t N, int32_t ldx, const abc_frames* frames, double half_life,
+                             double q_lo, double q_hi, uint64_t seed, int64_t first_index, float* y_dev, int32_t ldy,
+                             void* stream) {
+    vpet::clear_error();
+    VPET_ARG(frames && frames->t_start && frames->t_end, "abc_add_noise: null frames");
+    VPET_ARG(frames->L >= 1 && frames->L <= MAXL && ldx >= frames->L && ldy >= frames->L, "abc_add_noise: bad sizes");
+    VPET_ARG(half_life > 0 && q_lo >= 0 && q_hi >= q_lo, "abc_add_noise: bad noise parameters");
+    VPET_ARG(N >= 0 && (N == 0 || (x_dev && y_dev)), "abc_add_noise: null pointer");
+    NoiseFrames F;
+    memset(&F, 0, sizeof F);
+    F.L = frames->L;
+    for (int l = 0; l < F.L; ++l) {
+        F.tmid[l] = (float)(0.5 * (frames->t_start[l] + frames->t_end[l]));
+        F.dt[l] = (float)(frames->t_end[l] - frames->t_start[l]);
+        VPET_ARG(F.dt[l] > 0.0f, "abc_add_noise: empty frame");
+    }
+    if (N == 0) return ABC_OK;
+    k_add_noise<<<(unsigned)vpet_ceil_div(N, 8), 256, 0, (cudaStream_t)stream>>>(
+        x_dev, N, ldx, F, (float)(0.69314718055994531 / half_life), (float)q_lo, (float)q_hi, seed, first_index,
+        y_dev, ldy);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}
+
+extern "C" size_t abc_local_abc_smem_bytes(int32_t T, int32_t L, int32_t M) {
+    if (T < 1 || L < 1 || M < 1) return 0;
+    const size_t ldt = (size_t)(L | 1);
+    return sizeof(float) * ((size_t)T * ldt + 2 * MAXL + (size_t)M + 2 * LA_KMAX + 2 * LA_C * LA_KMAX + 64 + 256 +
+                            8 + 32);
+}
+
+extern "C" int abc_local_abc(const float* y_dev, int64_t J, int32_t ldy, int32_t L, const float* w_host,
+                             const float* prop_dev, const float* table_dev, int32_t T, double a_max,
+                             const float* cp_frames_dev, const double* lo_host, const double* hi_host, int32_t M,
+                             int32_t k, float sigma_scale, uint64_t seed, float* mean_dev, float* sd_dev, float* qlo_dev, float* qhi_dev,
+                             float* ess_dev, float* dmed_dev, float* ynorm_dev, float* u_dump_dev, float* d_dump_dev,
+                             void* stream) {
+    vpet::clear_error();
+    VPET_ARG(w_host && lo_host && hi_host, "abc_local_abc: null host pointer");
+    VPET_ARG(L >= 1 && L <= MAXL && ldy >= L && J >= 0 && T >= 8 && a_max > 0, "abc_local_abc: bad sizes");
+    VPET_ARG(k >= 1 && k <= LA_KMAX && M >= k && M <= (1 << 20), "abc_local_abc: need 1 <= k <= 256 and k <= M");
+    VPET_ARG(sigma_scale > 0.0f && sigma_scale <= 100.0f, "abc_local_abc: sigma_scale must be in (0, 100]");
+    for (int p = 0; p < LA_P; ++p)
+        VPET_ARG(lo_host[p] <= hi_host[p] && lo_host[p] >= 0.0, "abc_local_abc: prior box must satisfy 0 <= lo <= hi");
+    VPET_ARG(lo_host[1] + lo_host[2] > 0.0 && hi_host[1] + hi_host[2] <= a_max,
+             "abc_local_abc: k2 + k3 must stay in (0, a_max]");
+    const size_t smem = abc_local_abc_smem_bytes(T, L, M);
+    VPET_ARG(smem <= 227 * 1024, "abc_local_abc: table (T x L) and M distances exceed 227 KB of shared memory");
+    if (J == 0) return ABC_OK;
+    VPET_ARG(y_dev && prop_dev && table_dev && cp_frames_dev, "abc_local_abc: null device input");
+    VPET_ARG(mean_dev && sd_dev && qlo_dev && qhi_dev && ess_dev && dmed_dev && ynorm_dev,
+             "abc_local_abc: null output");
+    LocalArgs A;
+    memset(&A, 0, sizeof A);
+    A.y = y_dev;
+    A.J = J;
+    A.ldy = ldy;
+    A.L = L;
+    for (int l = 0; l < L; ++l) A.w[l] = w_host[l];
+    A.prop = prop_dev;
+    A.table = table_dev;
+    A.cpf = cp_frames_dev;
+    A.T = T;
+    A.ldt = L | 1;
+    A.a_max = (float)a_max;
+    for (int p = 0; p < LA_P; ++p) {
+        A.lo[p] = (float)lo_host[p];
+        A.hi[p] = (float)hi_host[p];
+    }
+    A.M = M;
+    A.k = k;
+    A.sigma_scale = sigma_scale;
+    A.seed = seed;
+    A.mean = mean_dev;
+    A.sd = sd_dev;
+    A.qlo = qlo_dev;
+    A.qhi = qhi_dev;
+    A.ess = ess_dev;
+    A.dmed = dmed_dev;
+    A.ynorm = ynorm_dev;
+    A.u_dump = u_dump_dev;
+    A.d_dump = d_dump_dev;
+    VPET_CUDA(cudaFuncSetAttribute(k_local_abc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    VPET_CUDA(cudaGetDevice(&dev));
+    VPET_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    VPET_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_abc, LA_THREADS, smem));
+    VPET_ARG(per_sm >= 1, "abc_local_abc: kernel does not fit on an SM with this shared memory");
+    int64_t grid = (int64_t)sms * per_sm;
+    if (grid > J) grid = J;
+    k_local_abc<<<(unsigned)grid, LA_THREADS, smem, (cudaStream_t)stream>>>(A);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}

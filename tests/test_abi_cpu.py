@@ -110,3 +110,40 @@ def test_batch_and_tuning_validation_without_gpu(lib):
     scans[1].k = 51                                   # k > N in the second scan
     rc = lib.abc_batch_discrepancy_topk(scans, 2, 1, None, P(256), 1 << 30, None)
     assert rc == _lib.ABC_ERR_ARG
+
+
+def test_learned_sizes_and_validation_without_gpu(lib):
+    """Learned-proposal entry points: sizes and host-side argument checks (nothing enqueued)."""
+    from paper_2603_14859_b300 import _lib
+    P = ctypes.c_void_p
+    assert lib.abc_mlp_param_count(30, 256, 8) == 256 * 30 + 256 + 256 * 256 + 256 + 8 * 256 + 8
+    assert lib.abc_mlp_param_count(0, 256, 8) == 0
+    assert lib.abc_mlp_workspace_size(30, 256, 8, 100) >= 4 * (100 * 256 * 4 + 100 * 8 * 2)
+    assert lib.abc_mlp_workspace_size(30, 256, 8, 0) == 0
+    assert lib.abc_mlp_init(1, 0, 256, 8, P(16), None) == _lib.ABC_ERR_ARG
+    assert lib.abc_mlp_init(1, 30, 256, 8, None, None) == _lib.ABC_ERR_ARG
+    assert lib.abc_mlp_forward(P(16), 30, 256, 8, P(16), 0, P(16), P(16), 1 << 30, None) == _lib.ABC_ERR_ARG
+    assert lib.abc_mlp_forward(P(16), 30, 256, 8, P(16), 100, P(16), P(16), 16, None) == _lib.ABC_ERR_WORKSPACE
+    assert lib.abc_mlp_loss_grad(P(16), 30, 256, 0, P(16), P(16), 10, P(16), 1 << 30, P(16), P(16),
+                                 None) == _lib.ABC_ERR_ARG
+    assert lib.abc_adam_update(P(16), P(16), P(16), P(16), 10, 1e-3, 1.0, 0.999, 1e-8, 1, None) == _lib.ABC_ERR_ARG
+    assert lib.abc_adam_update(P(16), P(16), P(16), P(16), 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == _lib.ABC_ERR_ARG
+    lo = np.array([0.0, 1.0]), np.array([1.0, 1.0])
+    assert lib.abc_unit_box(P(16), 4, 8, 2, lo[0].ctypes.data, lo[1].ctypes.data, P(16), None) == _lib.ABC_ERR_ARG
+    ts = np.array([0.0, 1.0]); te = np.array([1.0, 1.0])
+    fr = _lib.Frames(2, ts.ctypes.data, te.ctypes.data)
+    assert lib.abc_add_noise(P(16), 4, 4, ctypes.byref(fr), 109.8, 0.1, 0.1, 1, 0, P(16), 4,
+                             None) == _lib.ABC_ERR_ARG       # empty frame
+    assert "empty frame" in lib.abc_last_error().decode()
+    w = np.ones(29, np.float32)
+    lo4 = np.array([0.001, 0.001, 0.001, 0.03]); hi4 = np.array([1.0, 2.0, 0.5, 0.2])
+    args = lambda k, M, T, amax: (P(16), 10, 32, 29, w.ctypes.data, P(16), P(16), T, amax, P(16),
+                                  lo4.ctypes.data, hi4.ctypes.data, M, k, 1.0, 1, P(16), P(16), P(16), P(16), P(16),
+                                  P(16), P(16), None, None, None)
+    assert lib.abc_local_abc(*args(0, 100, 512, 2.5)) == _lib.ABC_ERR_ARG          # k = 0
+    assert lib.abc_local_abc(*args(300, 1000, 512, 2.5)) == _lib.ABC_ERR_ARG       # k > 256
+    assert lib.abc_local_abc(*args(100, 50, 512, 2.5)) == _lib.ABC_ERR_ARG         # M < k
+    assert lib.abc_local_abc(*args(100, 1000, 512, 2.0)) == _lib.ABC_ERR_ARG       # k2 + k3 beyond the table
+    assert lib.abc_local_abc(*args(100, 60000, 1024, 2.5)) == _lib.ABC_ERR_ARG     # shared memory
+    assert "shared memory" in lib.abc_last_error().decode()
+    assert lib.abc_local_abc_smem_bytes(512, 29, 10000) <= 227 * 1024
