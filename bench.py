@@ -9,7 +9,7 @@ frames, 1,000,000 draws per model, k = 500), BF16 discrepancy with exact FP32
 re-scoring.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision bf16r|fp32] [--workload NAME]
+                    [--precision bf16r|fp32|split] [--workload NAME]
 
 Multi-GPU (torchrun): every rank runs its own voxel shard against the same
 seeded draws (weak scaling, no collective on the data path).
@@ -44,13 +44,22 @@ WORKLOADS = {
 }
 
 
+def _precisions():
+    from paper_2603_14859_b300 import _lib
+    return {"bf16r": _lib.ABC_BF16_RESCORE, "fp32": _lib.ABC_FP32, "split": _lib.ABC_SPLIT_DRAWS}
+
+
+PRECISIONS = _precisions()
+DTYPES = {"bf16r": "bf16", "fp32": "bf16x3-split (fp32-exact)", "split": "bf16x2 (draws split; fp32-exact)"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16r", choices=["bf16r", "fp32"])
+    ap.add_argument("--precision", default="bf16r", choices=["bf16r", "fp32", "split"])
     ap.add_argument("--workload", default="raclopride_lpntpet", choices=sorted(WORKLOADS))
     ap.add_argument("--voxels", type=int, default=None, help="override J (smaller runs)")
     ap.add_argument("--draws", type=int, default=None, help="override draws per model")
@@ -170,7 +179,7 @@ def run_batched(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     else:
         torch.cuda.set_device(0)
-    prec = _lib.ABC_FP32 if args.precision == "fp32" else _lib.ABC_BF16_RESCORE
+    prec = PRECISIONS[args.precision]
     plan = S.scan_plan(seed=1004 + 1000 * rank, n_scans=args.scans, voxel_scale=args.voxel_scale,
                        draw_scale=args.draw_scale)
     scans = [S.scan_workload(p) for p in plan]
@@ -254,7 +263,7 @@ def run_batched(args, world, rank, local):
     line = {
         "metric": "voxels/s to posterior", "value": J * world / (ms / 1000.0), "unit": "voxels/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if prec == _lib.ABC_BF16_RESCORE else "bf16x3-split (fp32-exact)",
+        "vs_baseline": None, "dtype": DTYPES[args.precision],
         "data": "synthetic", "config": cfg, "pairs_per_s": pairs * world / (ms / 1000.0),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "k_tc_topk main pass (all scans, one persistent launch)",
@@ -528,7 +537,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     else:
         torch.cuda.set_device(0)
-    prec = _lib.ABC_FP32 if args.precision == "fp32" else _lib.ABC_BF16_RESCORE
+    prec = PRECISIONS[args.precision]
     run = pipeline.AbcPipeline(W, prec)
     y = pipeline.make_y_gpu(W)
     stream = torch.cuda.current_stream()
@@ -618,7 +627,7 @@ def main():
     line = {
         "metric": "voxels/s to posterior", "value": value, "unit": "voxels/s", "n_gpus": n_gpu, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if prec == _lib.ABC_BF16_RESCORE else "bf16x3-split (fp32-exact)",
+        "dtype": DTYPES[args.precision],
         "data": "synthetic", "config": cfg,
         "pairs_per_s": W.J * W.N * n_gpu / (ms / 1000.0),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

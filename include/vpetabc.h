@@ -60,9 +60,19 @@ extern "C" {
  *  ABC_BF16_RESCORE: one bf16 product per term; each voxel keeps its 4k
  *                    nearest by the bf16 distance, which are re-scored exactly
  *                    in fp32 before the final k are chosen (certification is
- *                    reported, not enforced). */
+ *                    reported, not enforced).
+ *  ABC_SPLIT_DRAWS:  the draw operand split into bf16 hi + lo, the voxel
+ *                    operand rounded once (two bf16 products per term, fp32
+ *                    accumulate); each voxel keeps its 2k nearest, re-scores
+ *                    them exactly in fp32, and certifies the result with a bound
+ *                    that tracks the voxel row's rounding exactly (its common
+ *                    part shifts every key of the voxel alike; the rest is at
+ *                    most 2 ||delta|| sqrt(d)); an uncertified voxel is resolved
+ *                    by an exact fp32 scan.  Like ABC_FP32, the accepted set is
+ *                    the exact fp32 top-k. */
 #define ABC_FP32 0
 #define ABC_BF16_RESCORE 1
+#define ABC_SPLIT_DRAWS 2
 
 /* Contiguous or gapped frame schedule: frame l spans [t_start[l], t_end[l]). */
 typedef struct {

@@ -19,7 +19,7 @@ ABC_ERR_WORKSPACE = -3
 ABC_ERR_TIMEOUT = -4
 ABC_ERR_UNSUPPORTED = -5
 ABC_2TCM_IRR, ABC_2TCM_REV, ABC_MRTM, ABC_LPNTPET = 0, 1, 2, 3
-ABC_FP32, ABC_BF16_RESCORE = 0, 1
+ABC_FP32, ABC_BF16_RESCORE, ABC_SPLIT_DRAWS = 0, 1, 2
 
 # every symbol the public header declares
 EXPORTS = [

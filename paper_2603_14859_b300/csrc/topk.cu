@@ -10,6 +10,11 @@
 //              B = [-2xh_hi, -2xh_lo, -2xh_hi, n_hi, n_mid, n_lo]: three bf16
 //              products per term, |error| <= E(voxel) (bound below).
 //   ABC_BF16_RESCORE: one bf16 product per term.
+//   ABC_SPLIT_DRAWS: only xh split; A = [yh_bf, yh_bf, 1,1,1], B = [-2xh_hi,
+//              -2xh_lo, n_hi, n_mid, n_lo]: two products per term.  The key is
+//              then exact up to the voxel row's own rounding delta, whose
+//              effect c0 - 2 delta . (xh - yh) is a per-voxel constant plus a
+//              term bounded by 2 ||delta|| sqrt(d), which the certificate uses.
 //
 // Kernel `k_tc_topk`: one CTA owns 128 voxels (one TMEM lane each) and streams
 // every draw tile of 128 rows through shared memory (TMA, 128-byte swizzle).
@@ -23,7 +28,7 @@
 // one coalesced store.  When a list could overflow, the warp compacts it
 // (radix select of the kt-th key, in-place filtering) and tightens the
 // threshold, so each list always holds every draw whose key is at most the
-// kt-th smallest seen (the "net": kt = 2k for ABC_FP32, 4k for ABC_BF16_RESCORE).
+// kt-th smallest seen (the "net": kt = 4k for ABC_BF16_RESCORE, else 2k).
 //
 // Pilot passes of the same kernel over every 16th (then 256th, ...) draw (a
 // strided TMA tensor map) first find each voxel's r-th smallest key,
@@ -39,9 +44,10 @@
 // certifies the result: with E bounding |computed d' - exact d'| for any draw
 // that could beat d_k (its ||xh|| <= ||yh|| + sqrt(d_k)), every draw outside
 // the net has computed key > T_out, so none can beat d_k when
-// T_out >= d_k - ||yh||^2 + E.  ABC_FP32 resolves an uncertified voxel by an
-// exact fp32 scan of all draws, which makes its accepted set the exact fp32
-// top-k; ABC_BF16_RESCORE counts uncertified voxels (abc_topk_status).
+// T_out >= d_k - ||yh||^2 + E (for ABC_SPLIT_DRAWS: + c0 + 2 ||delta|| sqrt(d_k)).
+// ABC_FP32 and ABC_SPLIT_DRAWS resolve an uncertified voxel by an exact fp32
+// scan of all draws, which makes their accepted sets the exact fp32 top-k;
+// ABC_BF16_RESCORE counts uncertified voxels (abc_topk_status).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -85,15 +91,19 @@ Tuning default_tuning(int mode) {
     return mode == ABC_FP32 ? Tuning{128, 2, 16, 1.5f} : Tuning{64, 3, 16, 1.5f};
 }
 
+// bf16 columns of the packed operands per frame: products per term of the key.
+__host__ __device__ inline int cols_per_frame(int mode) { return mode == ABC_FP32 ? 3 : (mode == ABC_SPLIT_DRAWS ? 2 : 1); }
+
 struct Layout {
-    int mode;          // ABC_FP32 / ABC_BF16_RESCORE
+    int mode;          // ABC_FP32 / ABC_BF16_RESCORE / ABC_SPLIT_DRAWS
     int L, k, Kp, nkb, C, kt, cap, sortcap;
     int nlev;                          // pilot levels (finest first)
     int lev_rank[MAX_PILOT_LEVELS];
     int64_t lev_stride[MAX_PILOT_LEVELS];
     int64_t J, N, Jp, Np;
     int npart;
-    size_t off_mu, off_part, off_ynorm, off_a, off_b, off_keys, off_idx, off_cnt, off_thr, off_thr0, total;
+    size_t off_mu, off_part, off_ynorm, off_c0, off_dn, off_a, off_b, off_keys, off_idx, off_cnt, off_thr, off_thr0,
+        total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -112,10 +122,10 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.k = k;
     s.J = J;
     s.N = N;
-    const int kcols = mode == ABC_FP32 ? 3 * L + 3 : L + 3;
+    const int kcols = cols_per_frame(mode) * L + 3;
     s.Kp = (int)vpet_round_up(kcols, KBLK);
     s.nkb = s.Kp / KBLK;
-    const int64_t net = (int64_t)(mode == ABC_FP32 ? 2 : 4) * k;
+    const int64_t net = (int64_t)(mode == ABC_BF16_RESCORE ? 4 : 2) * k;
     s.kt = (int)(net < N ? net : N);
     s.cap = s.kt + (s.kt / 4 > 64 ? s.kt / 4 : 64);
     // Pilot levels: level i uses every stride^i-th draw and a target rank
@@ -152,6 +162,8 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.off_mu = o; o = align256(o + MAXL * sizeof(float));
     s.off_part = o; o = align256(o + (size_t)s.npart * MAXL * sizeof(float));
     s.off_ynorm = o; o = align256(o + (size_t)s.Jp * sizeof(float));
+    s.off_c0 = o; o = align256(o + (size_t)s.Jp * sizeof(float));
+    s.off_dn = o; o = align256(o + (size_t)s.Jp * sizeof(float));
     s.off_a = o; o = align256(o + (size_t)s.Jp * s.Kp * 2);
     s.off_b = o; o = align256(o + (size_t)s.Np * s.Kp * 2);
     s.off_keys = o; o = align256(o + (size_t)J * s.C * sizeof(float));
@@ -195,26 +207,41 @@ __device__ __forceinline__ float warp_sum(float v) {
 __device__ __forceinline__ __nv_bfloat16 bf(float v) { return __float2bfloat16_rn(v); }
 
 // One warp per voxel row: A row of the GEMM and ||yh||^2.
+// ABC_SPLIT_DRAWS also records, per voxel, the rounding of its bf16 row,
+// delta = bf16(yh) - yh: c0 = -2 delta . yh and dn = ||delta|| (certificate).
 __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int ldy, int L, int Kp, int mode,
                          Weights W, const float* __restrict__ mu, __nv_bfloat16* __restrict__ A,
-                         float* __restrict__ ynorm) {
+                         float* __restrict__ ynorm, float* __restrict__ c0, float* __restrict__ dn) {
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= Jp) return;
     __nv_bfloat16* row = A + j * Kp;
     if (j >= J) {
         for (int e = lane; e < Kp; e += 32) row[e] = bf(0.0f);
-        if (lane == 0) ynorm[j] = 0.0f;
+        if (lane == 0) {
+            ynorm[j] = 0.0f;
+            c0[j] = 0.0f;
+            dn[j] = 0.0f;
+        }
         return;
     }
     const float* yr = y + j * ldy;
-    float ss = 0.0f;
+    float ss = 0.0f, sc = 0.0f, sd = 0.0f;
     for (int l = lane; l < L; l += 32) {
         const float v = W.sw[l] * (yr[l] - mu[l]);
         ss = fmaf(v, v, ss);
+        const float dl = __bfloat162float(bf(v)) - v;       // exact in fp32
+        sc = fmaf(dl, v, sc);
+        sd = fmaf(dl, dl, sd);
     }
     ss = warp_sum(ss);
-    if (lane == 0) ynorm[j] = ss;
+    sc = warp_sum(sc);
+    sd = warp_sum(sd);
+    if (lane == 0) {
+        ynorm[j] = ss;
+        c0[j] = -2.0f * sc;
+        dn[j] = sqrtf(sd);
+    }
     for (int e = lane; e < Kp; e += 32) {
         float out = 0.0f;
         if (mode == ABC_FP32) {
@@ -224,6 +251,13 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
                 const float hi = __bfloat162float(bf(v));
                 out = e < 2 * L ? hi : v - hi;
             } else if (e < 3 * L + 3) {
+                out = 1.0f;
+            }
+        } else if (mode == ABC_SPLIT_DRAWS) {
+            if (e < 2 * L) {
+                const int l = e % L;
+                out = W.sw[l] * (yr[l] - mu[l]);                // the same bf16 row against x_hi and x_lo
+            } else if (e < 2 * L + 3) {
                 out = 1.0f;
             }
         } else {
@@ -249,7 +283,7 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
     float ss = 0.0f;
     for (int l = lane; l < L; l += 32) {
         float v = W.sw[l] * (xr[l] - mu[l]);
-        if (mode != ABC_FP32) v = __bfloat162float(bf(v));   // norm of the rounded vector
+        if (mode == ABC_BF16_RESCORE) v = __bfloat162float(bf(v));   // norm of the rounded vector
         ss = fmaf(v, v, ss);
     }
     ss = warp_sum(ss);
@@ -257,7 +291,7 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
     const float r1 = ss - n1;
     const float n2 = __bfloat162float(bf(r1));
     const float n3 = r1 - n2;
-    const int aug = mode == ABC_FP32 ? 3 * L : L;
+    const int aug = cols_per_frame(mode) * L;
     for (int e = lane; e < Kp; e += 32) {
         float out = 0.0f;
         if (e < aug) {
@@ -265,6 +299,7 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
             const float v = W.sw[l] * (xr[l] - mu[l]);
             const float hi = __bfloat162float(bf(v));
             if (mode == ABC_FP32) out = -2.0f * ((e >= L && e < 2 * L) ? (v - hi) : hi);
+            else if (mode == ABC_SPLIT_DRAWS) out = -2.0f * (e >= L ? (v - hi) : hi);
             else out = -2.0f * hi;
         } else if (e == aug) {
             out = n1;
@@ -666,6 +701,8 @@ struct FinItem {
     const float* y;
     const float* x;
     const float* ynorm;
+    const float* c0;             // ABC_SPLIT_DRAWS: -2 delta . yh per voxel
+    const float* dn;             // ABC_SPLIT_DRAWS: ||delta|| per voxel
     float* keys;
     int32_t* idx;
     int32_t* cnt;
@@ -683,71 +720,76 @@ struct BatchFin {
     int32_t* status;
 };
 
-// Exact fp32 distance sum_l w_l (y_l - x_l)^2 in a fixed order (y in shared memory).
-__device__ __forceinline__ float exact_dist(const float* ys, const float* x, int L, const float* w) {
-    const float4* xr = (const float4*)x;
-    float d = 0.0f;
-    int l = 0;
-    for (; l + 4 <= L; l += 4) {
-        const float4 xv = __ldg(xr + (l >> 2));
-        const float e0 = ys[l] - xv.x, e1 = ys[l + 1] - xv.y, e2 = ys[l + 2] - xv.z, e3 = ys[l + 3] - xv.w;
-        d = fmaf(w[l] * e0, e0, d);
-        d = fmaf(w[l + 1] * e1, e1, d);
-        d = fmaf(w[l + 2] * e2, e2, d);
-        d = fmaf(w[l + 3] * e3, e3, d);
+// Exact fp32 distance sum_l w_l (y_l - x_l)^2 of a draw row in one fixed
+// order: 4-frame partial sums p_h (frames 4h..4h+3 in order), combined by the
+// pairing tree p_h + p_{h+o}, o = G/2 .. 1 (G = the power of two covering L
+// in 4-frame pieces).  group_dist2 evaluates it with G lanes per row (one
+// 16-byte load per lane, a butterfly over the group), lane_dist with one lane
+// per row; both give the same value for a (voxel, draw) pair.  y and w live in
+// shared memory.
+__device__ __forceinline__ float lane_dist(const float* ys, const float* ws, const float* xrow, int L, int G) {
+    float p[16];
+    const float4* xr = (const float4*)xrow;
+#pragma unroll
+    for (int h = 0; h < 16; ++h) {
+        p[h] = 0.0f;
+        const int l = 4 * h;
+        if (h < G && l < L) {
+            const float4 v = __ldg(xr + h);
+            const float xv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (l + q < L) {
+                    const float e = ys[l + q] - xv[q];
+                    p[h] = fmaf(ws[l + q] * e, e, p[h]);
+                }
+        }
     }
-    for (; l < L; ++l) {
-        const float e = ys[l] - x[l];
-        d = fmaf(w[l] * e, e, d);
-    }
-    return d;
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1)
+        if (o < G) {
+#pragma unroll
+            for (int h = 0; h < o; ++h) p[h] += p[h + o];
+        }
+    return p[0];
 }
 
-// exact_dist for two rows at once (same operation order), loads interleaved.
-__device__ __forceinline__ void exact_dist2(const float* ys, const float* xa, const float* xb, int L, const float* w,
-                                            float& da, float& db) {
-    const float4* ra = (const float4*)xa;
-    const float4* rb = (const float4*)xb;
+// Two rows per group of G lanes, both loads issued before the arithmetic;
+// every lane of the warp must call it (full-warp shuffles).
+__device__ __forceinline__ void group_dist2(const float* ys, const float* ws, const float* xa, const float* xb, int L,
+                                            int h, int G, float& da, float& db) {
     float a = 0.0f, b = 0.0f;
-    int l = 0;
-    for (; l + 4 <= L; l += 4) {
-        const float4 va = __ldg(ra + (l >> 2));
-        const float4 vb = __ldg(rb + (l >> 2));
-        float e = ys[l] - va.x;
-        a = fmaf(w[l] * e, e, a);
-        e = ys[l + 1] - va.y;
-        a = fmaf(w[l + 1] * e, e, a);
-        e = ys[l + 2] - va.z;
-        a = fmaf(w[l + 2] * e, e, a);
-        e = ys[l + 3] - va.w;
-        a = fmaf(w[l + 3] * e, e, a);
-        e = ys[l] - vb.x;
-        b = fmaf(w[l] * e, e, b);
-        e = ys[l + 1] - vb.y;
-        b = fmaf(w[l + 1] * e, e, b);
-        e = ys[l + 2] - vb.z;
-        b = fmaf(w[l + 2] * e, e, b);
-        e = ys[l + 3] - vb.w;
-        b = fmaf(w[l + 3] * e, e, b);
+    const int l = 4 * h;
+    if (l < L) {
+        const float4 va = __ldg((const float4*)xa + h);
+        const float4 vb = __ldg((const float4*)xb + h);
+        const float xva[4] = {va.x, va.y, va.z, va.w};
+        const float xvb[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (l + q < L) {
+                const float e = ys[l + q] - xva[q];
+                a = fmaf(ws[l + q] * e, e, a);
+                const float f = ys[l + q] - xvb[q];
+                b = fmaf(ws[l + q] * f, f, b);
+            }
     }
-    for (; l < L; ++l) {
-        float e = ys[l] - xa[l];
-        a = fmaf(w[l] * e, e, a);
-        e = ys[l] - xb[l];
-        b = fmaf(w[l] * e, e, b);
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
     }
     da = a;
     db = b;
 }
 
-// status[1]: voxels resolved by the exact scan; [2]: tie overflow; [3]: uncertified (bf16 mode)
 __global__ void k_finalize(const __grid_constant__ BatchFin B) {
     extern __shared__ __align__(16) uint8_t fsm[];
     const int warps = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t* hist = (uint32_t*)fsm + wid * 256;
-    float* ys = (float*)(fsm + warps * 1024) + wid * MAXL;
-    unsigned long long* sbuf = (unsigned long long*)(fsm + warps * 1024 + warps * MAXL * 4) + (size_t)wid * B.sortcap;
+    float* ys = (float*)(fsm + warps * 1024) + wid * 2 * MAXL;
+    float* ws = ys + MAXL;
+    unsigned long long* sbuf = (unsigned long long*)(fsm + warps * 1024 + warps * 2 * MAXL * 4) + (size_t)wid * B.sortcap;
     const int64_t g = (int64_t)blockIdx.x * warps + wid;
     if (g >= B.v_prefix[B.n_items]) return;
     int it = 0;
@@ -758,8 +800,14 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
     int32_t* ij = P.idx + j * P.C;
     const int raw = P.cnt[j];
     int cnt = raw & 0x3FFFFFFF;
-    for (int l = lane; l < P.L; l += 32) ys[l] = P.y[j * P.ldy + l];
+    for (int l = lane; l < P.L; l += 32) {
+        ys[l] = P.y[j * P.ldy + l];
+        ws[l] = P.w[l];
+    }
     __syncwarp();
+    int G = 1;
+    while (4 * G < P.L) G <<= 1;
+    const int R = 32 / G, grp = lane / G, h = lane % G;
     bool scan = (raw & 0x40000000) != 0;
     if (lane == 0) {                       // diagnostics: overflowed lists, short lists
         if (scan) atomicAdd(&B.status[4], 1);
@@ -775,16 +823,18 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
             cnt = warp_compact(kj, ij, cnt, T, P.C, lane);
             T_out = key2f(T);
         }
-        // 2. exact fp32 re-score of the net (two candidates per lane in flight)
-        int i = lane;
-        for (; i + 32 < cnt; i += 64) {
-            const int32_t n0 = ij[i], n1 = ij[i + 32];
-            float d0, d1;
-            exact_dist2(ys, P.x + (int64_t)n0 * P.ldx, P.x + (int64_t)n1 * P.ldx, P.L, P.w, d0, d1);
-            kj[i] = d0;
-            kj[i + 32] = d1;
+        // 2. exact fp32 re-score of the net: G lanes per row, two rows per group in flight
+        for (int i0 = 0; i0 < cnt; i0 += 2 * R) {
+            const int ia = i0 + grp, ib = i0 + R + grp;
+            const int32_t na = ij[ia < cnt ? ia : cnt - 1], nb = ij[ib < cnt ? ib : cnt - 1];
+            float da, db;
+            group_dist2(ys, ws, P.x + (int64_t)na * P.ldx, P.x + (int64_t)nb * P.ldx, P.L, h, G, da, db);
+            __syncwarp();
+            if (h == 0) {
+                if (ia < cnt) kj[ia] = da;
+                if (ib < cnt) kj[ib] = db;
+            }
         }
-        if (i < cnt) kj[i] = exact_dist(ys, P.x + (int64_t)ij[i] * P.ldx, P.L, P.w);
         __syncwarp();
         // 3. exact k-th distance and the certificate
         bool cert = false;
@@ -795,11 +845,17 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
             const float slack = 4.0f * (float)P.L * 0x1p-24f;
             const float ry = sqrtf(yn);
             const float R = ry + sqrtf(dk * (1.0f + slack)) + 1e-30f;
-            const float need = dk * (1.0f + slack) - yn * (1.0f - slack) + err_bound(P.cE, ry, R);
+            float need = dk * (1.0f + slack) - yn * (1.0f - slack) + err_bound(P.cE, ry, R);
+            if (P.mode == ABC_SPLIT_DRAWS) {
+                // the voxel row was rounded once: key - d' = c0 - 2 delta . (xh - yh) + (bounded above),
+                // |2 delta . (xh - yh)| <= 2 ||delta|| sqrt(d) <= 2 ||delta|| sqrt(d_k) for the k nearest
+                const float c0 = P.c0[j], dd = P.dn[j] * (1.0f + 0x1p-10f);
+                need += c0 + 2.0f * dd * sqrtf(dk * (1.0f + slack)) + fabsf(c0) * 0x1p-16f;
+            }
             cert = T_out >= 2.9e38f || T_out >= need;
         }
         if (!cert) {
-            if (P.mode == ABC_FP32 || cnt < P.k) scan = true;
+            if (P.mode != ABC_BF16_RESCORE || cnt < P.k) scan = true;
             else if (lane == 0) atomicAdd(&B.status[3], 1);
         }
     }
@@ -810,7 +866,7 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
         float thr = __int_as_float(0x7F800000);
         for (int64_t base = 0; base < P.N; base += 32) {
             const int64_t n = base + lane;
-            const float d = n < P.N ? exact_dist(ys, P.x + n * P.ldx, P.L, P.w) : __int_as_float(0x7F800000);
+            const float d = n < P.N ? lane_dist(ys, ws, P.x + n * P.ldx, P.L, G) : __int_as_float(0x7F800000);
             const bool take = n < P.N && d <= thr;
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
             if (take) {
@@ -987,7 +1043,10 @@ float error_coef(const Layout& lay) {
     //  ABC_BF16_RESCORE: one rounding of each operand and of the norm, 2^-8 each.
     // Both add fp32 accumulation over Kp terms, the fp32 norm and the fp32
     // centring / scaling of the operands.
-    const float split = lay.mode == ABC_FP32 ? 3.0f * 0x1p-16f : 3.0f * 0x1p-8f;
+    //  ABC_SPLIT_DRAWS: the draw operand as hi + lo (2^-16 |x| left); the voxel
+    //   row's single rounding is handled exactly by the certificate (c0, dn).
+    const float split = lay.mode == ABC_FP32 ? 3.0f * 0x1p-16f
+                                            : (lay.mode == ABC_SPLIT_DRAWS ? 3.0f * 0x1p-16f : 3.0f * 0x1p-8f);
     return split + (float)(3 * lay.Kp + lay.L + 16) * 0x1p-24f;
 }
 
@@ -1011,7 +1070,8 @@ int validate(const ScanSpec& c, int mode) {
     VPET_ARG(c.N < ((int64_t)1 << 31), "discrepancy/top-k: N must be < 2^31");
     VPET_ARG(c.L >= 1 && c.L <= 61, "discrepancy/top-k: L must be in 1..61 (got %d)", c.L);
     VPET_ARG(c.k >= 1 && c.k <= 2048 && c.k <= c.N, "discrepancy/top-k: need 1 <= k <= min(N, 2048)");
-    VPET_ARG(mode == ABC_FP32 || mode == ABC_BF16_RESCORE, "discrepancy/top-k: unknown precision %d", mode);
+    VPET_ARG(mode == ABC_FP32 || mode == ABC_BF16_RESCORE || mode == ABC_SPLIT_DRAWS,
+             "discrepancy/top-k: unknown precision %d", mode);
     VPET_ARG(c.y && c.x && c.w, "discrepancy/top-k: null pointer");
     VPET_ARG(c.ldy >= c.L && c.ldx >= c.L && c.ldx % 4 == 0 && c.ldy % 4 == 0,
              "discrepancy/top-k: ldy, ldx must be >= L and multiples of 4");
@@ -1100,7 +1160,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     BatchPilot PB;
     BatchFin F;
     struct Ptrs {
-        float *mu, *part, *ynorm, *keys, *thr, *thr0;
+        float *mu, *part, *ynorm, *c0, *dn, *keys, *thr, *thr0;
         __nv_bfloat16 *A, *B;
         int32_t *idx, *cnt;
     } ptr[MAX_ITEMS];
@@ -1111,6 +1171,8 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         p.mu = (float*)(base + L.off_mu);
         p.part = (float*)(base + L.off_part);
         p.ynorm = (float*)(base + L.off_ynorm);
+        p.c0 = (float*)(base + L.off_c0);
+        p.dn = (float*)(base + L.off_dn);
         p.A = (__nv_bfloat16*)(base + L.off_a);
         p.B = (__nv_bfloat16*)(base + L.off_b);
         p.keys = (float*)(base + L.off_keys);
@@ -1130,7 +1192,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         k_colmean_final<<<1, MAXL, 0, s>>>(p.part, L.npart, L.J, p.mu);
         VPET_LAUNCH_CHECK();
         k_pack_y<<<(unsigned)vpet_ceil_div(L.Jp, 8), 256, 0, s>>>(sc[i].y, L.J, L.Jp, sc[i].ldy, L.L, L.Kp, mode, W,
-                                                                  p.mu, p.A, p.ynorm);
+                                                                  p.mu, p.A, p.ynorm, p.c0, p.dn);
         VPET_LAUNCH_CHECK();
         k_pack_x<<<(unsigned)vpet_ceil_div(L.Np, 8), 256, 0, s>>>(sc[i].x, L.N, L.Np, sc[i].ldx, L.L, L.Kp, mode, W,
                                                                   p.mu, p.B);
@@ -1237,6 +1299,8 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         f.x = sc[i].x;
         f.ldx = sc[i].ldx;
         f.ynorm = ptr[i].ynorm;
+        f.c0 = ptr[i].c0;
+        f.dn = ptr[i].dn;
         f.keys = ptr[i].keys;
         f.idx = ptr[i].idx;
         f.cnt = ptr[i].cnt;
@@ -1252,7 +1316,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     F.status = status;
     int warps = 8;
     while (warps > 1 && (size_t)warps * sortcap * 8 > 64 * 1024) warps >>= 1;
-    const size_t fsmem = (size_t)warps * (1024 + MAXL * 4 + (size_t)sortcap * 8);
+    const size_t fsmem = (size_t)warps * (1024 + 2 * MAXL * 4 + (size_t)sortcap * 8);
     static size_t fin_configured = 0;
     if (fsmem > 48 * 1024 && fsmem > fin_configured) {
         VPET_CUDA(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
@@ -1315,7 +1379,7 @@ int topk_on_workspace(const float* y, int64_t J, int ldy, const float* x, int64_
 
 extern "C" size_t abc_workspace_size(int64_t J, int64_t N, int32_t L, int32_t k, int32_t precision) {
     if (J < 1 || N < 1 || L < 1 || L > 61 || k < 1 || k > N || k > 2048) return 0;
-    if (precision != ABC_FP32 && precision != ABC_BF16_RESCORE) return 0;
+    if (precision != ABC_FP32 && precision != ABC_BF16_RESCORE && precision != ABC_SPLIT_DRAWS) return 0;
     return vpet::topk_workspace_bytes(J, N, L, k, precision);
 }
 
@@ -1330,7 +1394,8 @@ extern "C" int abc_discrepancy_topk(const float* y_dev, int64_t J, int32_t ldy, 
 extern "C" int abc_default_tuning(int32_t precision, abc_tuning* out) {
     vpet::clear_error();
     VPET_ARG(out, "abc_default_tuning: null pointer");
-    VPET_ARG(precision == ABC_FP32 || precision == ABC_BF16_RESCORE, "abc_default_tuning: unknown precision");
+    VPET_ARG(precision == ABC_FP32 || precision == ABC_BF16_RESCORE || precision == ABC_SPLIT_DRAWS,
+             "abc_default_tuning: unknown precision");
     const Tuning t = tuning_for(precision);
     out->bn = t.bn;
     out->ctas_per_sm = t.ctas_per_sm;
@@ -1352,7 +1417,7 @@ extern "C" int abc_set_default_tuning(const abc_tuning* t) {
 extern "C" size_t abc_batch_workspace_size(const abc_scan* scans, int32_t n_scans, int32_t precision) {
     ScanSpec sp[MAX_ITEMS];
     if (!scans || n_scans < 1 || n_scans > MAX_ITEMS) return 0;
-    if (precision != ABC_FP32 && precision != ABC_BF16_RESCORE) return 0;
+    if (precision != ABC_FP32 && precision != ABC_BF16_RESCORE && precision != ABC_SPLIT_DRAWS) return 0;
     for (int i = 0; i < n_scans; ++i) {
         const abc_scan& c = scans[i];
         if (c.J < 1 || c.N < 1 || c.L < 1 || c.L > 61 || c.k < 1 || c.k > c.N || c.k > 2048) return 0;

@@ -39,7 +39,7 @@ def batch(orc):
     return scans, ys
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_batch_equals_single_scan_calls(batch, prec):
     from paper_2603_14859_b300 import api, pipeline
     scans, ys = batch
@@ -57,10 +57,11 @@ def test_batch_equals_single_scan_calls(batch, prec):
         assert torch.equal(dist, r.dist)
 
 
-def test_batch_oracle_parity(batch, orc):
+@pytest.mark.parametrize("prec", [0, 2])
+def test_batch_oracle_parity(batch, orc, prec):
     from paper_2603_14859_b300 import pipeline
     scans, ys = batch
-    bp = pipeline.BatchPipeline(scans, 0)
+    bp = pipeline.BatchPipeline(scans, prec)
     for r in bp.runs:
         r.simulate_draws()
     bp.set_inputs(ys)

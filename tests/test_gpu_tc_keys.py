@@ -24,7 +24,7 @@ def _pad(a):
     return torch.from_numpy(out).cuda()
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("J,N,L", [(128, 128, 22), (200, 300, 22), (77, 1000, 60), (300, 129, 29)])
 def test_gemm_keys_against_fp64(prec, J, N, L):
     from paper_2603_14859_b300 import api
@@ -45,8 +45,23 @@ def test_gemm_keys_against_fp64(prec, J, N, L):
         Kp = ((3 * L + 3 + 63) // 64) * 64
         cE = 3 * 2.0**-16 + (3 * Kp + L + 16) * 2.0**-24      # the kernel uses twice this
         bound = cE * (2 * ry * R + R * R)
-    else:
+    elif prec == 1:
         bound = 2.0**-6 * (2 * ry * R + R * R)
+    if prec == 2:
+        # the voxel row is rounded once, as the kernel rounds it (fp32 centring and scaling, bf16 round to nearest)
+        mu32 = mu.astype(np.float32)
+        v32 = np.sqrt(w).astype(np.float32) * (y - mu32)
+        yb = torch.from_numpy(v32).to(torch.bfloat16).to(torch.float32).numpy()
+        delta = yb.astype(np.float64) - v32
+        c0 = -2.0 * (delta * v32).sum(1)[:, None]
+        dn = np.sqrt((delta**2).sum(1))[:, None]
+        Kp = ((2 * L + 3 + 63) // 64) * 64
+        cE = 3 * 2.0**-16 + (3 * Kp + L + 16) * 2.0**-24
+        err = np.abs(d_gpu - d_exact - c0)
+        bound = 2 * dn * np.sqrt(d_exact) + cE * (2 * ry * R + R * R) + np.abs(c0) * 2.0**-16
+        assert np.isfinite(keys).all()
+        assert (err <= bound).all(), f"max err/bound = {(err / bound).max()}"
+        return
     err = np.abs(d_gpu - d_exact)
     assert np.isfinite(keys).all()
     assert (err <= bound).all(), f"max err/bound = {(err / bound).max()}"

@@ -58,36 +58,38 @@ def _compare(orc, W, y, x, k, prec, tau_extra=0.0):
     return swaps, worst, st[1]
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_topk_brain_2tcm_small(orc, prec):
     W, y, x = _gpu_case("brain_fdg_2tcm", 300, 5000, orc)          # 3 voxel tiles (ragged), 40 draw tiles (ragged)
     swaps, worst, fallback = _compare(orc, W, y, x, 100, prec)
     assert swaps <= 3
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_topk_raclopride_two_models(orc, prec):
     W, y, x = _gpu_case("raclopride_lpntpet", 260, 3000, orc)     # 60 frames, FP32 K = 192 (3 K-blocks)
     _compare(orc, W, y, x, 50, prec)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_topk_totalbody_rev_irr(orc, prec):
     W, y, x = _gpu_case("totalbody_fdg", 129, 20000, orc)          # 29 frames, K = 128 (2 K-blocks)
     _compare(orc, W, y, x, 200, prec)
 
 
-def test_topk_many_compactions(orc):
+@pytest.mark.parametrize("prec", [0, 2])
+def test_topk_many_compactions(orc, prec):
     """k small against a long draw stream: the candidate lists are compacted many times."""
     W, y, x = _gpu_case("brain_fdg_2tcm", 64, 60000, orc)
-    _compare(orc, W, y, x, 5, 0)
+    _compare(orc, W, y, x, 5, prec)
 
 
 @pytest.mark.parametrize("k", [1, 7])
 def test_topk_tiny_and_k_edges(orc, k):
     W, y, x = _gpu_case("brain_fdg_2tcm", 5, 9, orc)               # N = 9 < one tile
-    _compare(orc, W, y, x, k, 0)
-    _compare(orc, W, y, x, 9, 0)                                   # k = N
+    for prec in (0, 2):
+        _compare(orc, W, y, x, k, prec)
+        _compare(orc, W, y, x, 9, prec)                            # k = N
 
 
 def test_noise_free_recovery():
@@ -100,7 +102,7 @@ def test_noise_free_recovery():
     x = api.simulate(S.TCM2_IRR, W.ts, W.te, W.inp, th)
     stars = [0, 4095, 6999, 1234, 5000]
     y = x[stars].clone()
-    for prec in (0, 1):
+    for prec in (0, 1, 2):
         idx, dist = api.discrepancy_topk(y, x, W.L, W.weights.astype(np.float32), 10, prec)
         assert idx[:, 0].cpu().tolist() == stars
         assert torch.all(dist[:, 0] == 0)
@@ -115,8 +117,9 @@ def test_ties_resolved_by_index():
     x[300] = x[17]
     x[450] = x[17]
     y = x[17:18].clone()
-    idx, dist = api.discrepancy_topk(y, x, W.L, W.weights.astype(np.float32), 3, 0)
-    assert idx[0].cpu().tolist() == [17, 300, 450]
+    for prec in (0, 2):
+        idx, dist = api.discrepancy_topk(y, x, W.L, W.weights.astype(np.float32), 3, prec)
+        assert idx[0].cpu().tolist() == [17, 300, 450]
 
 
 def test_argument_errors():

@@ -41,7 +41,7 @@ def _noalloc(y, x, L, w, k, prec):
     return idx, dist
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_noalloc_matches_workspace_entry_point_twice(prec):
     from paper_2603_14859_b300 import api
     L, k = 22, 100
