@@ -69,7 +69,6 @@ constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any barrier wait
 constexpr int MAXL = 64;
 constexpr int MAX_PILOT_LEVELS = 4;
 constexpr int MAX_ITEMS = 64;                 // scans per batched launch
-constexpr int STAGE_LD = 36;                  // floats per staged row (16-byte aligned, conflict-free)
 
 struct Weights {
     float w[MAXL];
@@ -358,6 +357,14 @@ __device__ __forceinline__ float compact_list(const ItemTc& I, int64_t j, int& c
     return key2f(T);
 }
 
+// The fields of an item the epilogue touches per chunk, held in registers.
+struct ItemRegs {
+    int64_t N;
+    float* keys;
+    int32_t* idx;
+    int C;
+};
+
 __device__ __forceinline__ float min32(const float (&v)[32]) {
     float m[11];
 #pragma unroll
@@ -371,48 +378,40 @@ __device__ __forceinline__ float min32(const float (&v)[32]) {
     return fminf(fminf(b, c), d);
 }
 
-// The fields of an item the epilogue touches per chunk, held in registers.
-struct ItemRegs {
-    int64_t N;
-    float* keys;
-    int32_t* idx;
-    int C;
-};
-
-// One 32-column chunk of the epilogue: filter, then warp-cooperative appends.
-__device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32], int64_t n0, int64_t jbase,
-                                               float thr, int& cnt, float* stage, int lane) {
+// One 32-column chunk of the epilogue, per thread (= voxel j): the minimum of
+// the 32 keys against the voxel's threshold; a thread whose minimum passes
+// builds the 32-bit mask of passing keys and appends each one, picked out of
+// its registers by a 5-level select tree on the bit position, to the voxel's
+// list.  About 0.1 % of the pairs pass, so few threads enter the append path,
+// and threads never wait for one another.
+__device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32], int64_t n0, int64_t j, float thr,
+                                               int& cnt) {
     if (n0 + 32 > I.N) {
 #pragma unroll
         for (int i = 0; i < 32; ++i)
             if (n0 + i >= I.N) v[i] = __int_as_float(0x7F800000);   // +inf: never kept
     }
-    const bool slow = min32(v) <= thr;
-    uint32_t bal = __ballot_sync(0xFFFFFFFFu, slow);
-    if (!bal) return;
-    if (slow) {
-        float4* dst = (float4*)(stage + lane * STAGE_LD);
+    if (min32(v) > thr) return;
+    uint32_t m = 0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    for (int i = 0; i < 32; ++i) m |= (v[i] <= thr ? 1u : 0u) << i;
+    const int64_t row = j * (int64_t)I.C;
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        float t16[16], t8[8], t4[4], t2[2];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) t16[i] = (b & 1) ? v[2 * i + 1] : v[2 * i];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t8[i] = (b & 2) ? t16[2 * i + 1] : t16[2 * i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) t4[i] = (b & 4) ? t8[2 * i + 1] : t8[2 * i];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) t2[i] = (b & 8) ? t4[2 * i + 1] : t4[2 * i];
+        I.keys[row + cnt] = (b & 16) ? t2[1] : t2[0];
+        I.idx[row + cnt] = (int32_t)(n0 + b);
+        ++cnt;
     }
-    __syncwarp();
-    const uint32_t lt = (1u << lane) - 1u;
-    while (bal) {
-        const int s = __ffs(bal) - 1;
-        bal &= bal - 1;
-        const float val = stage[s * STAGE_LD + lane];
-        const float ts = __shfl_sync(0xFFFFFFFFu, thr, s);
-        const int cs = __shfl_sync(0xFFFFFFFFu, cnt, s);
-        const bool pass = val <= ts;
-        const uint32_t pb = __ballot_sync(0xFFFFFFFFu, pass);
-        if (pass) {
-            const int64_t at = (jbase + s) * (int64_t)I.C + cs + __popc(pb & lt);
-            I.keys[at] = val;
-            I.idx[at] = (int32_t)(n0 + lane);
-        }
-        if (lane == s) cnt += __popc(pb);
-    }
-    __syncwarp();
 }
 
 // Persistent fused kernel over the (scan, 128-voxel tile) work items of a batch,
@@ -420,14 +419,13 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
 // scans first).  All roles walk the same sequence; the shared-memory ring and
 // the TMEM accumulators keep their phases across items.
 template <int NKB, int STAGES, int BN, bool DUMP>
-__global__ void __launch_bounds__(TC_THREADS) k_tc_topk(const __grid_constant__ BatchTc P) {
+__global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant__ BatchTc P) {
     constexpr int B_KBLK_BYTES = BN * KBLK * 2;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;                                          // NKB x 16 KB
     uint8_t* sB = smem + NKB * A_KBLK_BYTES;                     // STAGES x NKB x BN rows
-    float* sStage = (float*)(sB + STAGES * NKB * B_KBLK_BYTES);  // 4 warps x 32 x STAGE_LD
-    uint32_t* hist = (uint32_t*)(sStage + 4 * 32 * STAGE_LD);    // 4 warps x 256
+    uint32_t* hist = (uint32_t*)(sB + STAGES * NKB * B_KBLK_BYTES);   // 4 warps x 256
     uint64_t* bars = (uint64_t*)(hist + 4 * 256);
     uint64_t* full = bars;                  // [STAGES]
     uint64_t* empty = bars + STAGES;        // [STAGES]
@@ -558,7 +556,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_topk(const __grid_constant__ 
         const int q = warp & 3;                          // TMEM lane quadrant of this warp
         const int row = q * 32 + lane;
         uint32_t* whist = hist + (warp - 2) * 256;
-        float* stage = sStage + (warp - 2) * 32 * STAGE_LD;
         uint32_t gt = 0;
         bool stop = false;
         for (uint32_t ic = 0; !stop; ++ic) {
@@ -609,13 +606,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_topk(const __grid_constant__ 
                         ptx::tmem_ld32_async(ta + (c + 1) * 32, rb);
 #pragma unroll
                         for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(ra[i]);
-                        epilogue_chunk(R, v, nbase + c * 32, jbase, thr, cnt, stage, lane);
+                        epilogue_chunk(R, v, nbase + c * 32, j, thr, cnt);
                         ptx::tmem_wait_ld();
                         ptx::tmem_fence_regs(rb);
                         if (c + 2 < BN / 32) ptx::tmem_ld32_async(ta + (c + 2) * 32, ra);
 #pragma unroll
                         for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(rb[i]);
-                        epilogue_chunk(R, v, nbase + (c + 1) * 32, jbase, thr, cnt, stage, lane);
+                        epilogue_chunk(R, v, nbase + (c + 1) * 32, j, thr, cnt);
                         if (c + 2 < BN / 32) {
                             ptx::tmem_wait_ld();
                             ptx::tmem_fence_regs(ra);
@@ -961,7 +958,7 @@ constexpr int stages_for(int nkb, int bn) {
 
 size_t tc_smem_bytes(int nkb, int bn) {
     const int S = stages_for(nkb, bn);
-    return 1024 + (size_t)nkb * A_KBLK_BYTES + (size_t)S * nkb * bn * KBLK * 2 + 4 * 32 * STAGE_LD * 4 + 4 * 256 * 4 +
+    return 1024 + (size_t)nkb * A_KBLK_BYTES + (size_t)S * nkb * bn * KBLK * 2 + 4 * 256 * 4 +
            (2 * S + 14) * 8;
 }
 
