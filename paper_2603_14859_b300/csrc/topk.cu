@@ -365,24 +365,28 @@ struct ItemRegs {
     int C;
 };
 
-__device__ __forceinline__ float min32(const float (&v)[32]) {
-    float m[11];
-#pragma unroll
-    for (int i = 0; i < 10; ++i) asm("min.f32 %0, %1, %2, %3;" : "=f"(m[i]) : "f"(v[3 * i]), "f"(v[3 * i + 1]), "f"(v[3 * i + 2]));
-    m[10] = fminf(v[30], v[31]);
-    float a, b, c, d;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(a) : "f"(m[0]), "f"(m[1]), "f"(m[2]));
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(b) : "f"(m[3]), "f"(m[4]), "f"(m[5]));
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(c) : "f"(m[6]), "f"(m[7]), "f"(m[8]));
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(m[9]), "f"(m[10]), "f"(a));
-    return fminf(fminf(b, c), d);
+// Minimum of the 8 keys v[o .. o+7] (three-input min instructions).
+__device__ __forceinline__ float min8(const float (&v)[32], int o) {
+    float a, b;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(a) : "f"(v[o]), "f"(v[o + 1]), "f"(v[o + 2]));
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(b) : "f"(v[o + 3]), "f"(v[o + 4]), "f"(v[o + 5]));
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(a) : "f"(a), "f"(b), "f"(v[o + 6]));
+    return fminf(a, v[o + 7]);
 }
 
-// One 32-column chunk of the epilogue, per thread (= voxel j): the minimum of
-// the 32 keys against the voxel's threshold; a thread whose minimum passes
-// builds the 32-bit mask of passing keys and appends each one, picked out of
-// its registers by a 5-level select tree on the bit position, to the voxel's
-// list.  About 0.1 % of the pairs pass, so few threads enter the append path,
+// Bits i - o of the keys v[o .. o+7] that are <= thr.
+__device__ __forceinline__ uint32_t mask8(const float (&v)[32], int o, float thr) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) m |= (v[o + i] <= thr ? 1u : 0u) << i;
+    return m;
+}
+
+// One 32-column chunk of the epilogue, per thread (= voxel j): the minima of
+// the four 8-key groups against the voxel's threshold; a thread with a passing
+// group builds the mask of passing keys (passing groups only) and appends each
+// one, picked out of its registers by a 5-level select tree on the bit
+// position, to the voxel's list.  About 0.1 % of the pairs pass, so few threads enter the append path,
 // and threads never wait for one another.
 __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32], int64_t n0, int64_t j, float thr,
                                                int& cnt) {
@@ -391,10 +395,16 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
         for (int i = 0; i < 32; ++i)
             if (n0 + i >= I.N) v[i] = __int_as_float(0x7F800000);   // +inf: never kept
     }
-    if (min32(v) > thr) return;
+    const float g0 = min8(v, 0), g1 = min8(v, 8), g2 = min8(v, 16), g3 = min8(v, 24);
+    float gm;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(gm) : "f"(g0), "f"(g1), "f"(g2));
+    if (fminf(gm, g3) > thr) return;
+    // only the 8-key groups whose minimum passes are examined key by key
     uint32_t m = 0;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) m |= (v[i] <= thr ? 1u : 0u) << i;
+    if (g0 <= thr) m |= mask8(v, 0, thr);
+    if (g1 <= thr) m |= mask8(v, 8, thr) << 8;
+    if (g2 <= thr) m |= mask8(v, 16, thr) << 16;
+    if (g3 <= thr) m |= mask8(v, 24, thr) << 24;
     const int64_t row = j * (int64_t)I.C;
     while (m) {
         const int b = __ffs(m) - 1;
