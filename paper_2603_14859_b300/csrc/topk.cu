@@ -605,28 +605,18 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                             P.dump[(m0 + row) * P.ld_dump + nbase + c * 32 + i] = __uint_as_float(r[i]);
                     }
                 } else {
-                    // software pipeline: the load of chunk c+1 is in flight while chunk c is filtered
-                    uint32_t ra[32], rb[32];
-                    ptx::tmem_ld32_async(ta, ra);
-                    ptx::tmem_wait_ld();
-                    ptx::tmem_fence_regs(ra);
-#pragma unroll
-                    for (int c = 0; c < BN / 32; c += 2) {
-                        float v[32];
-                        ptx::tmem_ld32_async(ta + (c + 1) * 32, rb);
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(ra[i]);
-                        epilogue_chunk(R, v, nbase + c * 32, j, thr, cnt);
+                    // one 32-column load at a time (fewer live registers than overlapping two
+                    // loads, which measured slower)
+#pragma unroll 1
+                    for (int c = 0; c < BN / 32; ++c) {
+                        uint32_t r[32];
+                        ptx::tmem_ld32_async(ta + c * 32, r);
                         ptx::tmem_wait_ld();
-                        ptx::tmem_fence_regs(rb);
-                        if (c + 2 < BN / 32) ptx::tmem_ld32_async(ta + (c + 2) * 32, ra);
+                        ptx::tmem_fence_regs(r);
+                        float v[32];
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(rb[i]);
-                        epilogue_chunk(R, v, nbase + (c + 1) * 32, j, thr, cnt);
-                        if (c + 2 < BN / 32) {
-                            ptx::tmem_wait_ld();
-                            ptx::tmem_fence_regs(ra);
-                        }
+                        for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+                        epilogue_chunk(R, v, nbase + c * 32, j, thr, cnt);
                     }
                 }
                 ptx::tc_fence_before();
