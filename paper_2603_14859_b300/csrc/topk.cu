@@ -720,7 +720,7 @@ struct BatchFin {
 // Exact fp32 distance sum_l w_l (y_l - x_l)^2 of a draw row in one fixed
 // order: 4-frame partial sums p_h (frames 4h..4h+3 in order), combined by the
 // pairing tree p_h + p_{h+o}, o = G/2 .. 1 (G = the power of two covering L
-// in 4-frame pieces).  group_dist2 evaluates it with G lanes per row (one
+// in 4-frame pieces).  group_dist_n evaluates it with G lanes per row (one
 // 16-byte load per lane, a butterfly over the group), lane_dist with one lane
 // per row; both give the same value for a (voxel, draw) pair.  y and w live in
 // shared memory.
@@ -751,32 +751,34 @@ __device__ __forceinline__ float lane_dist(const float* ys, const float* ws, con
     return p[0];
 }
 
-// Two rows per group of G lanes, both loads issued before the arithmetic;
+// NR rows per group of G lanes, all loads issued before the arithmetic;
 // every lane of the warp must call it (full-warp shuffles).
-__device__ __forceinline__ void group_dist2(const float* ys, const float* ws, const float* xa, const float* xb, int L,
-                                            int h, int G, float& da, float& db) {
-    float a = 0.0f, b = 0.0f;
+template <int NR>
+__device__ __forceinline__ void group_dist_n(const float* ys, const float* ws, const float* const (&xr)[NR], int L,
+                                             int h, int G, float (&d)[NR]) {
     const int l = 4 * h;
-    if (l < L) {
-        const float4 va = __ldg((const float4*)xa + h);
-        const float4 vb = __ldg((const float4*)xb + h);
-        const float xva[4] = {va.x, va.y, va.z, va.w};
-        const float xvb[4] = {vb.x, vb.y, vb.z, vb.w};
+    float4 v[NR];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (l + q < L) {
-                const float e = ys[l + q] - xva[q];
-                a = fmaf(ws[l + q] * e, e, a);
-                const float f = ys[l + q] - xvb[q];
-                b = fmaf(ws[l + q] * f, f, b);
-            }
+    for (int r = 0; r < NR; ++r) {
+        d[r] = 0.0f;
+        if (l < L) v[r] = __ldg((const float4*)xr[r] + h);
+    }
+    if (l < L) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const float xv[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (l + q < L) {
+                    const float e = ys[l + q] - xv[q];
+                    d[r] = fmaf(ws[l + q] * e, e, d[r]);
+                }
+        }
     }
     for (int o = G >> 1; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-        b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) d[r] += __shfl_xor_sync(0xFFFFFFFFu, d[r], o);
     }
-    da = a;
-    db = b;
 }
 
 __global__ void k_finalize(const __grid_constant__ BatchFin B) {
@@ -820,16 +822,24 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
             cnt = warp_compact(kj, ij, cnt, T, P.C, lane);
             T_out = key2f(T);
         }
-        // 2. exact fp32 re-score of the net: G lanes per row, two rows per group in flight
-        for (int i0 = 0; i0 < cnt; i0 += 2 * R) {
-            const int ia = i0 + grp, ib = i0 + R + grp;
-            const int32_t na = ij[ia < cnt ? ia : cnt - 1], nb = ij[ib < cnt ? ib : cnt - 1];
-            float da, db;
-            group_dist2(ys, ws, P.x + (int64_t)na * P.ldx, P.x + (int64_t)nb * P.ldx, P.L, h, G, da, db);
+        // 2. exact fp32 re-score of the net: G lanes per row, four rows per group in flight
+        constexpr int NR = 4;
+        for (int i0 = 0; i0 < cnt; i0 += NR * R) {
+            const float* xr[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int i = i0 + r * R + grp;
+                xr[r] = P.x + (int64_t)ij[i < cnt ? i : cnt - 1] * P.ldx;
+            }
+            float d[NR];
+            group_dist_n<NR>(ys, ws, xr, P.L, h, G, d);
             __syncwarp();
             if (h == 0) {
-                if (ia < cnt) kj[ia] = da;
-                if (ib < cnt) kj[ib] = db;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const int i = i0 + r * R + grp;
+                    if (i < cnt) kj[i] = d[r];
+                }
             }
         }
         __syncwarp();
