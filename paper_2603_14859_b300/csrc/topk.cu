@@ -67,6 +67,8 @@ constexpr int A_KBLK_BYTES = BM * KBLK * 2;   // 16 KB
 constexpr int TC_THREADS = 192;
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any barrier wait
 constexpr int MAXL = 64;
+constexpr int ORDER_BITS = 10;                 // bits per ordering feature (30-bit Morton key)
+constexpr int ORDER_BUCKETS = 1 << 16;         // counting-sort buckets (top 16 key bits)
 constexpr int MAX_PILOT_LEVELS = 4;
 constexpr int MAX_ITEMS = 64;                 // scans per batched launch
 
@@ -102,7 +104,7 @@ struct Layout {
     int64_t J, N, Jp, Np;
     int npart;
     size_t off_mu, off_part, off_ynorm, off_c0, off_dn, off_a, off_b, off_keys, off_idx, off_cnt, off_thr, off_thr0,
-        total;
+        off_perm, off_feat, off_hist, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -113,7 +115,8 @@ int next_pow2(int x) {
     return p;
 }
 
-Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& tu) {
+// kp_min: the packed K width is at least this (a batch pads every scan to its widest).
+Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& tu, int kp_min = 0) {
     Layout s;
     memset(&s, 0, sizeof s);
     s.mode = mode;
@@ -123,6 +126,7 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.N = N;
     const int kcols = cols_per_frame(mode) * L + 3;
     s.Kp = (int)vpet_round_up(kcols, KBLK);
+    if (s.Kp < kp_min) s.Kp = kp_min;
     s.nkb = s.Kp / KBLK;
     const int64_t net = (int64_t)(mode == ABC_BF16_RESCORE ? 4 : 2) * k;
     s.kt = (int)(net < N ? net : N);
@@ -170,6 +174,9 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.off_cnt = o; o = align256(o + (size_t)s.Jp * sizeof(int32_t));
     s.off_thr = o; o = align256(o + (size_t)s.Jp * sizeof(float));
     s.off_thr0 = o; o = align256(o + (size_t)s.Jp * sizeof(float));
+    s.off_perm = o; o = align256(o + (size_t)s.Jp * sizeof(int32_t));
+    s.off_feat = o; o = align256(o + (size_t)3 * s.Jp * sizeof(float) + 8 * sizeof(uint32_t));
+    s.off_hist = o; o = align256(o + (size_t)ORDER_BUCKETS * sizeof(uint32_t));
     s.total = o;
     return s;
 }
@@ -206,11 +213,118 @@ __device__ __forceinline__ float warp_sum(float v) {
 __device__ __forceinline__ __nv_bfloat16 bf(float v) { return __float2bfloat16_rn(v); }
 
 // One warp per voxel row: A row of the GEMM and ||yh||^2.
+// ------------------------------------------------------------------ voxel order
+// Voxels whose TACs are alike share their nearest draws, so the rare keys that
+// pass the epilogue's threshold fall into the same columns for all of them.
+// The fused kernel therefore processes voxels in an order that keeps such
+// voxels in the same warp: a Morton key over three features (log of the
+// weighted early, middle and late thirds of the TAC), counting-sorted on its
+// top 16 bits.  Only the processing order changes; every voxel's result is
+// computed exactly as before.
+__device__ __forceinline__ uint32_t ord_f2u(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord_u2f(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// mm = {min, max} x 3 features as ordered integers; hist = 0
+__global__ void k_order_init(uint32_t* __restrict__ mm, uint32_t* __restrict__ hist) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 6) mm[i] = (i & 1) ? 0u : 0xFFFFFFFFu;
+    if (i < ORDER_BUCKETS) hist[i] = 0u;
+}
+
+// feat[3 j + c] = log of the weighted sum of third c of voxel j's TAC
+__global__ void k_order_features(const float* __restrict__ y, int64_t J, int ldy, int L, Weights W,
+                                 float* __restrict__ feat, uint32_t* __restrict__ mm) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    const float* yr = y + j * ldy;
+    float f[3] = {0.0f, 0.0f, 0.0f};
+    for (int l = 0; l < L; ++l) {
+        const int c = (3 * l) / L;
+        f[c] = fmaf(W.w[l], yr[l], f[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float v = logf(fmaxf(f[c], 1e-30f));
+        feat[3 * j + c] = v;
+        atomicMin(&mm[2 * c], ord_f2u(v));
+        atomicMax(&mm[2 * c + 1], ord_f2u(v));
+    }
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t x) {     // bit i -> bit 3i (10 bits)
+    x &= 0x3FFu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t order_key(const float* feat, const uint32_t* mm, int64_t j) {
+    uint32_t q[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float lo = ord_u2f(mm[2 * c]), hi = ord_u2f(mm[2 * c + 1]);
+        const float t = hi > lo ? (feat[3 * j + c] - lo) / (hi - lo) : 0.0f;
+        q[c] = (uint32_t)fminf(fmaxf(t * (float)((1 << ORDER_BITS) - 1), 0.0f), (float)((1 << ORDER_BITS) - 1));
+    }
+    return spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+}
+
+__global__ void k_order_hist(const float* __restrict__ feat, const uint32_t* __restrict__ mm, int64_t J,
+                             uint32_t* __restrict__ hist) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < J) atomicAdd(&hist[order_key(feat, mm, j) >> (3 * ORDER_BITS - 16)], 1u);
+}
+
+// exclusive scan of the ORDER_BUCKETS counts, in place (one block of 1024 threads)
+__global__ void __launch_bounds__(1024) k_order_scan(uint32_t* __restrict__ hist) {
+    __shared__ uint32_t part[1024];
+    constexpr int PER = ORDER_BUCKETS / 1024;
+    const int t = threadIdx.x;
+    uint32_t loc[PER], s = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        loc[i] = hist[t * PER + i];
+        s += loc[i];
+    }
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const uint32_t v = t >= o ? part[t - o] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[t] - s;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        hist[t * PER + i] = run;
+        run += loc[i];
+    }
+}
+
+// perm[position] = voxel; voxels of one bucket land in arrival order
+__global__ void k_order_scatter(const float* __restrict__ feat, const uint32_t* __restrict__ mm, int64_t J,
+                                uint32_t* __restrict__ hist, int32_t* __restrict__ perm) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    const uint32_t pos = atomicAdd(&hist[order_key(feat, mm, j) >> (3 * ORDER_BITS - 16)], 1u);
+    perm[pos] = (int32_t)j;
+}
+
 // ABC_SPLIT_DRAWS also records, per voxel, the rounding of its bf16 row,
 // delta = bf16(yh) - yh: c0 = -2 delta . yh and dn = ||delta|| (certificate).
+// Row j of A is voxel perm[j] (perm = null: voxel j).
 __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int ldy, int L, int Kp, int mode,
-                         Weights W, const float* __restrict__ mu, __nv_bfloat16* __restrict__ A,
-                         float* __restrict__ ynorm, float* __restrict__ c0, float* __restrict__ dn) {
+                         Weights W, const float* __restrict__ mu, const int32_t* __restrict__ perm,
+                         __nv_bfloat16* __restrict__ A, float* __restrict__ ynorm, float* __restrict__ c0,
+                         float* __restrict__ dn) {
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= Jp) return;
@@ -224,7 +338,7 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
         }
         return;
     }
-    const float* yr = y + j * ldy;
+    const float* yr = y + (perm ? (int64_t)perm[j] : j) * ldy;
     float ss = 0.0f, sc = 0.0f, sd = 0.0f;
     for (int l = lane; l < L; l += 32) {
         const float v = W.sw[l] * (yr[l] - mu[l]);
@@ -700,6 +814,7 @@ struct FinItem {
     const float* ynorm;
     const float* c0;             // ABC_SPLIT_DRAWS: -2 delta . yh per voxel
     const float* dn;             // ABC_SPLIT_DRAWS: ||delta|| per voxel
+    const int32_t* perm;         // list row -> voxel (null: identity)
     float* keys;
     int32_t* idx;
     int32_t* cnt;
@@ -794,13 +909,14 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
     int it = 0;
     while (it + 1 < B.n_items && g >= B.v_prefix[it + 1]) ++it;
     const FinItem& P = B.item[it];
-    const int64_t j = g - B.v_prefix[it];
+    const int64_t j = g - B.v_prefix[it];                  // list row
+    const int64_t vox = P.perm ? (int64_t)P.perm[j] : j;   // voxel of that row
     float* kj = P.keys + j * P.C;
     int32_t* ij = P.idx + j * P.C;
     const int raw = P.cnt[j];
     int cnt = raw & 0x3FFFFFFF;
     for (int l = lane; l < P.L; l += 32) {
-        ys[l] = P.y[j * P.ldy + l];
+        ys[l] = P.y[vox * P.ldy + l];
         ws[l] = P.w[l];
     }
     __syncwarp();
@@ -906,8 +1022,8 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
     warp_bitonic_sort(sbuf, n2, lane);
     for (int r = lane; r < P.k; r += 32) {
         const unsigned long long e = r < cnt ? sbuf[r] : ~0ull;
-        P.out_idx[j * P.k + r] = r < cnt ? (int32_t)(uint32_t)e : -1;
-        P.out_dist[j * P.k + r] = r < cnt ? key2f((uint32_t)(e >> 32)) : __int_as_float(0x7F800000);
+        P.out_idx[vox * P.k + r] = r < cnt ? (int32_t)(uint32_t)e : -1;
+        P.out_dist[vox * P.k + r] = r < cnt ? key2f((uint32_t)(e >> 32)) : __int_as_float(0x7F800000);
     }
 }
 
@@ -1112,30 +1228,33 @@ void make_batch_layout(const ScanSpec* sc, int n, int mode, const Tuning& tu, Ba
     B->n = n;
     int kp = 0;
     for (int i = 0; i < n; ++i) {
-        B->lay[i] = make_layout(sc[i].J, sc[i].N, sc[i].L, sc[i].k, mode, tu);
-        if (B->lay[i].Kp > kp) kp = B->lay[i].Kp;
+        const int w = make_layout(sc[i].J, sc[i].N, sc[i].L, sc[i].k, mode, tu).Kp;
+        if (w > kp) kp = w;
     }
+    // one K-width per launch: every scan is laid out at the widest
     size_t o = 256;
     for (int i = 0; i < n; ++i) {
-        // one K-width per launch: pad every scan to the widest
-        if (B->lay[i].Kp != kp) {
-            Layout& L = B->lay[i];
-            const int64_t Jp = L.Jp, Np = L.Np;
-            const size_t grow_a = (size_t)Jp * (kp - L.Kp) * 2, grow_b = (size_t)Np * (kp - L.Kp) * 2;
-            L.Kp = kp;
-            L.nkb = kp / KBLK;
-            L.off_b += align256(grow_a);
-            L.off_keys += align256(grow_a) + align256(grow_b);
-            L.off_idx += align256(grow_a) + align256(grow_b);
-            L.off_cnt += align256(grow_a) + align256(grow_b);
-            L.off_thr += align256(grow_a) + align256(grow_b);
-            L.off_thr0 += align256(grow_a) + align256(grow_b);
-            L.total += align256(grow_a) + align256(grow_b);
-        }
+        B->lay[i] = make_layout(sc[i].J, sc[i].N, sc[i].L, sc[i].k, mode, tu, kp);
         B->off[i] = o;
         o = align256(o + B->lay[i].total);
     }
     B->total = o;
+}
+
+// Every section of a scan's layout lies after the previous one and inside the scan's total.
+bool layout_consistent(const Layout& L) {
+    const size_t off[] = {L.off_mu, L.off_part, L.off_ynorm, L.off_c0, L.off_dn, L.off_a, L.off_b, L.off_keys,
+                          L.off_idx, L.off_cnt, L.off_thr, L.off_thr0, L.off_perm, L.off_feat, L.off_hist};
+    const size_t len[] = {MAXL * 4, (size_t)L.npart * MAXL * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
+                          (size_t)L.Jp * L.Kp * 2, (size_t)L.Np * L.Kp * 2, (size_t)L.J * L.C * 4,
+                          (size_t)L.J * L.C * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
+                          (size_t)L.Jp * 4, (size_t)3 * L.Jp * 4 + 32, (size_t)ORDER_BUCKETS * 4};
+    const int n = (int)(sizeof off / sizeof off[0]);
+    for (int i = 0; i < n; ++i) {
+        if (off[i] + len[i] > (i + 1 < n ? off[i + 1] : L.total)) return false;
+        if (i > 0 && off[i] < off[i - 1]) return false;
+    }
+    return true;
 }
 
 int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws, size_t ws_bytes, float* dump,
@@ -1149,6 +1268,11 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         if ((rc = validate(sc[i], mode))) return rc;
     BatchLayout BL;
     make_batch_layout(sc, n, mode, tu, &BL);
+    for (int i = 0; i < n; ++i)
+        if (!layout_consistent(BL.lay[i])) {
+            vpet::set_error("discrepancy/top-k: internal workspace layout error (scan %d)", i);
+            return ABC_ERR_WORKSPACE;
+        }
     if (!ws || ((uintptr_t)ws & 255) || ws_bytes < BL.total) {
         vpet::set_error("discrepancy/top-k: workspace needs %zu bytes, 256-aligned (got %zu)", BL.total, ws_bytes);
         return ABC_ERR_WORKSPACE;
@@ -1167,7 +1291,9 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     BatchPilot PB;
     BatchFin F;
     struct Ptrs {
-        float *mu, *part, *ynorm, *c0, *dn, *keys, *thr, *thr0;
+        float *mu, *part, *ynorm, *c0, *dn, *keys, *thr, *thr0, *feat;
+        int32_t* perm;
+        uint32_t *mm, *hist;
         __nv_bfloat16 *A, *B;
         int32_t *idx, *cnt;
     } ptr[MAX_ITEMS];
@@ -1187,6 +1313,10 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         p.cnt = (int32_t*)(base + L.off_cnt);
         p.thr = (float*)(base + L.off_thr);
         p.thr0 = (float*)(base + L.off_thr0);
+        p.perm = (int32_t*)(base + L.off_perm);
+        p.feat = (float*)(base + L.off_feat);
+        p.mm = (uint32_t*)(p.feat + 3 * L.Jp);
+        p.hist = (uint32_t*)(base + L.off_hist);
         Weights W;
         memset(&W, 0, sizeof W);
         for (int l = 0; l < L.L; ++l) {
@@ -1198,8 +1328,23 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         VPET_LAUNCH_CHECK();
         k_colmean_final<<<1, MAXL, 0, s>>>(p.part, L.npart, L.J, p.mu);
         VPET_LAUNCH_CHECK();
+        const bool order = dump == nullptr && L.J > 1;   // the debug dump keeps voxel order
+        if (order) {
+            k_order_init<<<(unsigned)vpet_ceil_div(ORDER_BUCKETS, 256), 256, 0, s>>>(p.mm, p.hist);
+            VPET_LAUNCH_CHECK();
+            const unsigned gb = (unsigned)vpet_ceil_div(L.J, 256);
+            k_order_features<<<gb, 256, 0, s>>>(sc[i].y, L.J, sc[i].ldy, L.L, W, p.feat, p.mm);
+            VPET_LAUNCH_CHECK();
+            k_order_hist<<<gb, 256, 0, s>>>(p.feat, p.mm, L.J, p.hist);
+            VPET_LAUNCH_CHECK();
+            k_order_scan<<<1, 1024, 0, s>>>(p.hist);
+            VPET_LAUNCH_CHECK();
+            k_order_scatter<<<gb, 256, 0, s>>>(p.feat, p.mm, L.J, p.hist, p.perm);
+            VPET_LAUNCH_CHECK();
+        }
         k_pack_y<<<(unsigned)vpet_ceil_div(L.Jp, 8), 256, 0, s>>>(sc[i].y, L.J, L.Jp, sc[i].ldy, L.L, L.Kp, mode, W,
-                                                                  p.mu, p.A, p.ynorm, p.c0, p.dn);
+                                                                  p.mu, order ? p.perm : nullptr, p.A, p.ynorm, p.c0,
+                                                                  p.dn);
         VPET_LAUNCH_CHECK();
         k_pack_x<<<(unsigned)vpet_ceil_div(L.Np, 8), 256, 0, s>>>(sc[i].x, L.N, L.Np, sc[i].ldx, L.L, L.Kp, mode, W,
                                                                   p.mu, p.B);
@@ -1308,6 +1453,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         f.ynorm = ptr[i].ynorm;
         f.c0 = ptr[i].c0;
         f.dn = ptr[i].dn;
+        f.perm = (dump == nullptr && L.J > 1) ? ptr[i].perm : nullptr;
         f.keys = ptr[i].keys;
         f.idx = ptr[i].idx;
         f.cnt = ptr[i].cnt;

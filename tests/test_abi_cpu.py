@@ -147,3 +147,22 @@ def test_learned_sizes_and_validation_without_gpu(lib):
     assert lib.abc_local_abc(*args(100, 60000, 1024, 2.5)) == _lib.ABC_ERR_ARG     # shared memory
     assert "shared memory" in lib.abc_last_error().decode()
     assert lib.abc_local_abc_smem_bytes(512, 29, 10000) <= 227 * 1024
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_batch_layout_of_mixed_widths_without_gpu(lib, prec):
+    """A batch whose scans pack to different K widths is laid out at the widest: the
+    host-side layout check passes (the call then stops at the workspace-size check),
+    and the batch needs more than the sum of the narrower single-scan layouts."""
+    from paper_2603_14859_b300 import _lib
+    P = ctypes.c_void_p
+    w = np.ones(61, np.float32)
+    shapes = [(1000, 50000, 22, 50), (3000, 200000, 60, 100), (10, 5000, 29, 5), (1, 300, 61, 1)]
+    scans = (_lib.Scan * len(shapes))()
+    for i, (J, N, L, k) in enumerate(shapes):
+        scans[i] = _lib.Scan(256, J, 64, 256, N, 64, L, w.ctypes.data, k, 256, 256)
+    need = lib.abc_batch_workspace_size(scans, len(shapes), prec)
+    assert need > sum(lib.abc_workspace_size(J, N, L, k, prec) for J, N, L, k in shapes) - 4 * 4096
+    rc = lib.abc_batch_discrepancy_topk(scans, len(shapes), prec, None, P(256), need - 256, None)
+    assert rc == _lib.ABC_ERR_WORKSPACE
+    assert b"workspace needs" in lib.abc_last_error()
