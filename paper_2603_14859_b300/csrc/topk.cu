@@ -104,7 +104,10 @@ struct Layout {
     int64_t J, N, Jp, Np;
     int npart;
     size_t off_mu, off_part, off_ynorm, off_c0, off_dn, off_a, off_b, off_keys, off_idx, off_cnt, off_thr, off_thr0,
-        off_perm, off_feat, off_hist, total;
+        off_perm, off_feat, off_hist, off_xperm, off_xfeat, off_xhist, off_fy, off_fx, off_tbox, off_ktile,
+        off_kcount, total;
+    int64_t nt64;                      // 64-draw tiles of the draw operand
+    int64_t nvt;                       // 128-voxel tiles
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -177,6 +180,16 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.off_perm = o; o = align256(o + (size_t)s.Jp * sizeof(int32_t));
     s.off_feat = o; o = align256(o + (size_t)3 * s.Jp * sizeof(float) + 8 * sizeof(uint32_t));
     s.off_hist = o; o = align256(o + (size_t)ORDER_BUCKETS * sizeof(uint32_t));
+    s.nt64 = s.Np / 64;
+    s.nvt = s.Jp / BM;
+    s.off_xperm = o; o = align256(o + (size_t)s.Np * sizeof(int32_t));
+    s.off_xfeat = o; o = align256(o + (size_t)3 * s.Np * sizeof(float) + 8 * sizeof(uint32_t));
+    s.off_xhist = o; o = align256(o + (size_t)ORDER_BUCKETS * sizeof(uint32_t));
+    s.off_fy = o; o = align256(o + (size_t)3 * s.Jp * sizeof(float));
+    s.off_fx = o; o = align256(o + (size_t)3 * s.Np * sizeof(float));
+    s.off_tbox = o; o = align256(o + (size_t)6 * s.nt64 * sizeof(float));
+    s.off_ktile = o; o = align256(o + (size_t)s.nvt * s.nt64 * sizeof(int32_t));
+    s.off_kcount = o; o = align256(o + (size_t)s.nvt * sizeof(int32_t));
     s.total = o;
     return s;
 }
@@ -320,11 +333,27 @@ __global__ void k_order_scatter(const float* __restrict__ feat, const uint32_t* 
 
 // ABC_SPLIT_DRAWS also records, per voxel, the rounding of its bf16 row,
 // delta = bf16(yh) - yh: c0 = -2 delta . yh and dn = ||delta|| (certificate).
-// Row j of A is voxel perm[j] (perm = null: voxel j).
+// Weighted sums of the three consecutive thirds of a TAC (the features of the
+// tile bound), computed by a warp; every lane gets them.
+__device__ __forceinline__ void seg_features(const float* r, int L, const Weights& W, int lane, float (&f)[3]) {
+    f[0] = f[1] = f[2] = 0.0f;
+    for (int l = lane; l < L; l += 32) {
+        const int c = (3 * l) / L;
+        const float v = W.w[l] * r[l];
+        f[0] += c == 0 ? v : 0.0f;
+        f[1] += c == 1 ? v : 0.0f;
+        f[2] += c == 2 ? v : 0.0f;
+    }
+    f[0] = warp_sum(f[0]);
+    f[1] = warp_sum(f[1]);
+    f[2] = warp_sum(f[2]);
+}
+
+// Row j of A is voxel perm[j] (perm = null: voxel j); fy[3 j + c] = its segment features.
 __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int ldy, int L, int Kp, int mode,
                          Weights W, const float* __restrict__ mu, const int32_t* __restrict__ perm,
                          __nv_bfloat16* __restrict__ A, float* __restrict__ ynorm, float* __restrict__ c0,
-                         float* __restrict__ dn) {
+                         float* __restrict__ dn, float* __restrict__ fy) {
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= Jp) return;
@@ -350,10 +379,15 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
     ss = warp_sum(ss);
     sc = warp_sum(sc);
     sd = warp_sum(sd);
+    float f[3];
+    seg_features(yr, L, W, lane, f);
     if (lane == 0) {
         ynorm[j] = ss;
         c0[j] = -2.0f * sc;
         dn[j] = sqrtf(sd);
+        fy[3 * j] = f[0];
+        fy[3 * j + 1] = f[1];
+        fy[3 * j + 2] = f[2];
     }
     for (int e = lane; e < Kp; e += 32) {
         float out = 0.0f;
@@ -382,8 +416,10 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
 }
 
 // One warp per draw row: B row of the GEMM.
+// Row n of B is draw xperm[n] (xperm = null: draw n); fx[3 n + c] = its segment features.
 __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int ldx, int L, int Kp, int mode,
-                         Weights W, const float* __restrict__ mu, __nv_bfloat16* __restrict__ B) {
+                         Weights W, const float* __restrict__ mu, const int32_t* __restrict__ xperm,
+                         __nv_bfloat16* __restrict__ B, float* __restrict__ fx) {
     const int lane = threadIdx.x & 31;
     const int64_t n = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (n >= Np) return;
@@ -392,7 +428,16 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
         for (int e = lane; e < Kp; e += 32) row[e] = bf(0.0f);
         return;
     }
-    const float* xr = x + n * ldx;
+    const float* xr = x + (xperm ? (int64_t)xperm[n] : n) * ldx;
+    {
+        float f[3];
+        seg_features(xr, L, W, lane, f);
+        if (lane == 0) {
+            fx[3 * n] = f[0];
+            fx[3 * n + 1] = f[1];
+            fx[3 * n + 2] = f[2];
+        }
+    }
     float ss = 0.0f;
     for (int l = lane; l < L; l += 32) {
         float v = W.sw[l] * (xr[l] - mu[l]);
@@ -425,6 +470,148 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
     }
 }
 
+// ------------------------------------------------------------------ tile bound
+// For the weighted sums F_c(v) = sum_{l in third c} w_l v_l of the three thirds of
+// the frames, Cauchy-Schwarz gives (F_c(y) - F_c(x))^2 <= W_c sum_{l in c} w_l (y_l - x_l)^2
+// with W_c = sum_{l in c} w_l, so d(y, x) >= sum_c (F_c(y) - F_c(x))^2 / W_c.  With
+// boxes [lo_c, hi_c] of the features over a 128-voxel tile and over a draw tile,
+// the squared gaps between the boxes bound every pair of the two tiles from below.
+// A draw tile whose bound exceeds the largest distance threshold of the voxel
+// tile holds no draw that any of its voxels would keep, so the main pass skips it.
+
+// tbox[6 t + 2 c], tbox[6 t + 2 c + 1] = min, max of feature c over the draws of 64-draw tile t
+__global__ void k_tile_boxes(const float* __restrict__ fx, int64_t N, int64_t nt64, float* __restrict__ tbox) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= nt64) return;
+    float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t n = t * 64 + h * 32 + lane;
+        if (n < N) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = fminf(lo[c], fx[3 * n + c]);
+                hi[c] = fmaxf(hi[c], fx[3 * n + c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xFFFFFFFFu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xFFFFFFFFu, hi[c], o));
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            tbox[6 * t + 2 * c] = lo[c];
+            tbox[6 * t + 2 * c + 1] = hi[c];
+        }
+}
+
+struct KeepArgs {
+    const float* fy;             // packed voxel rows x 3
+    const float* thr0;           // key threshold per packed row
+    const float* ynorm;          // ||yh||^2 per packed row
+    const float* tbox;           // 64-draw tile boxes
+    int32_t* ktile;              // kept tile indices, nvt x nt64 (row stride nt64)
+    int32_t* kcount;             // kept tiles per voxel tile
+    unsigned long long* tally;   // [0] += kept, [1] += all (diagnostics)
+    int64_t J, N, nt64;
+    float Wc[3];                 // segment weight sums
+    float cE;                    // error coefficient of the keys (0: the key threshold is used as is)
+    int bn;                      // draw-tile width of the pass, 64 or 128
+};
+
+// One block (256 threads) per 128-voxel tile: the voxel tile's feature box and
+// largest distance threshold, then the ordered list of draw tiles that cannot
+// be skipped.
+__global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ KeepArgs K) {
+    __shared__ uint32_t box[7];                 // ordered-int min/max x 3, max threshold
+    __shared__ int wcount[8];
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    const int64_t vt = blockIdx.x;
+    if (tid < 7) box[tid] = (tid < 6 && (tid & 1) == 0) ? 0xFFFFFFFFu : 0u;
+    __syncthreads();
+    if (tid < BM) {
+        const int64_t j = vt * BM + tid;
+        if (j < K.J) {
+            const float t = K.thr0[j];
+            const float yn = K.ynorm[j];
+            float td = t + yn;
+            if (K.cE > 0.0f && td < 1.0e30f) {
+                const float ry = sqrtf(fmaxf(yn, 0.0f));
+                const float R = ry + sqrtf(fmaxf(td, 0.0f));
+                td += K.cE * (2.0f * ry * R + R * R);
+            }
+            td = td >= 1.0e30f ? 3.0e38f : td * (1.0f + 0x1p-10f) + 1e-30f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                atomicMin(&box[2 * c], ord_f2u(K.fy[3 * j + c]));
+                atomicMax(&box[2 * c + 1], ord_f2u(K.fy[3 * j + c]));
+            }
+            atomicMax(&box[6], ord_f2u(td));
+        }
+    }
+    __syncthreads();
+    float ylo[3], yhi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ylo[c] = ord_u2f(box[2 * c]);
+        yhi[c] = ord_u2f(box[2 * c + 1]);
+    }
+    const float tmax = ord_u2f(box[6]);
+    const bool all = !(tmax < 1.0e30f);
+    const int per = K.bn / 64;
+    const int64_t ntiles = (K.N + K.bn - 1) / K.bn;
+    int base = 0;
+    for (int64_t t0 = 0; t0 < ntiles; t0 += 256) {
+        const int64_t t = t0 + tid;
+        bool keep = false;
+        if (t < ntiles) {
+            keep = all;
+            if (!keep) {
+                float lb = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float xl = 3.0e38f, xh = -3.0e38f;
+                    for (int q = 0; q < per; ++q) {
+                        const int64_t u = t * per + q;
+                        if (u < K.nt64) {
+                            xl = fminf(xl, K.tbox[6 * u + 2 * c]);
+                            xh = fmaxf(xh, K.tbox[6 * u + 2 * c + 1]);
+                        }
+                    }
+                    // a gap smaller than the features' rounding is treated as none
+                    const float slack = 0x1p-18f * (fabsf(xl) + fabsf(xh) + fabsf(ylo[c]) + fabsf(yhi[c]));
+                    const float gap = fmaxf(fmaxf(xl - yhi[c], ylo[c] - xh) - slack, 0.0f);
+                    if (K.Wc[c] > 0.0f) lb += gap * gap / K.Wc[c];
+                }
+                keep = lb * (1.0f - 0x1p-10f) <= tmax;
+            }
+        }
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+        if (lane == 0) wcount[wp] = __popc(bal);
+        __syncthreads();
+        int pos = base, tot = 0;
+        for (int q = 0; q < 8; ++q) {
+            if (q < wp) pos += wcount[q];
+            tot += wcount[q];
+        }
+        pos += __popc(bal & ((1u << lane) - 1u));
+        if (keep) K.ktile[vt * K.nt64 + pos] = (int32_t)t;
+        base += tot;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        K.kcount[vt] = base;
+        atomicAdd(&K.tally[0], (unsigned long long)base);
+        atomicAdd(&K.tally[1], (unsigned long long)ntiles);
+    }
+}
+
 // ------------------------------------------------------------------ fused GEMM + filter
 // One scan of a batch, as the fused kernel sees it (kernel parameter space).
 struct __align__(64) ItemTc {
@@ -438,6 +625,9 @@ struct __align__(64) ItemTc {
     const float* thr0;           // initial threshold per voxel (pilot), or null = +huge
     int ntiles, C, kt, cap;
     int lim;                     // a list is compacted once it could exceed lim entries (lim <= C)
+    const int32_t* ktile;        // kept draw tiles per voxel tile (null: every tile)
+    const int32_t* kcount;
+    int64_t kstride;
 };
 
 struct BatchTc {
@@ -608,8 +798,10 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                 if (w < 0) break;
                 const int it = item_of(P, w);
                 const ItemTc& I = P.item[it];
-                const int64_t m0 = (w - P.vt_prefix[it]) * BM;
-                const int ntiles = I.ntiles;
+                const int64_t vt = w - P.vt_prefix[it];
+                const int64_t m0 = vt * BM;
+                const int ntiles = I.ktile ? I.kcount[vt] : I.ntiles;
+                const int32_t* kt_list = I.ktile ? I.ktile + vt * I.kstride : nullptr;
                 ptx::tma_prefetch_desc(&I.tmA);
                 ptx::tma_prefetch_desc(&I.tmB);
                 // the previous item's MMAs must be done with the A tile
@@ -627,7 +819,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                     ptx::mbar_arrive_expect_tx(fb, NKB * B_KBLK_BYTES);
                     for (int kb = 0; kb < NKB; ++kb)
                         ptx::tma_load_2d(ptx::smem_u32(sB + (s * NKB + kb) * B_KBLK_BYTES), &I.tmB, fb, kb * KBLK,
-                                         t * BN);
+                                         (kt_list ? kt_list[t] : t) * BN);
                 }
             }
         }
@@ -644,7 +836,9 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                 else *s_err = 1;
                 ptx::mbar_arrive(ptx::smem_u32(&iempty[sl]));
                 if (w < 0) break;
-                const int ntiles = P.item[item_of(P, w)].ntiles;
+                const int itm = item_of(P, w);
+                const ItemTc& IM = P.item[itm];
+                const int ntiles = IM.ktile ? IM.kcount[w - P.vt_prefix[itm]] : IM.ntiles;
                 if (!ptx::mbar_wait(ptx::smem_u32(afull), ic & 1u, WAIT_NS)) { *s_err = 1; break; }
                 for (int t = 0; t < ntiles; ++t, ++gt) {
                     const uint32_t s = gt % STAGES;
@@ -693,8 +887,10 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
             const int it = item_of(P, w);
             const ItemTc& I = P.item[it];
             const ItemRegs R{I.N, I.keys, I.idx, I.C};
-            const int ntiles = I.ntiles, lim = I.lim;
-            const int64_t m0 = (w - P.vt_prefix[it]) * BM;
+            const int64_t vt = w - P.vt_prefix[it];
+            const int ntiles = I.ktile ? I.kcount[vt] : I.ntiles, lim = I.lim;
+            const int32_t* kt_list = I.ktile ? I.ktile + vt * I.kstride : nullptr;
+            const int64_t m0 = vt * BM;
             const int64_t jbase = m0 + q * 32;
             const int64_t j = jbase + lane;
             const bool valid = j < I.J;
@@ -706,7 +902,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                 if (!ptx::mbar_wait(ptx::smem_u32(&tfull[acc]), aph, WAIT_NS)) { *s_err = 1; }
                 if (__any_sync(0xFFFFFFFFu, *s_err != 0)) { stop = true; break; }
                 ptx::tc_fence_after();
-                const int64_t nbase = (int64_t)t * BN;
+                const int64_t nbase = (int64_t)(kt_list ? kt_list[t] : t) * BN;
                 const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
                 if (DUMP) {
                     for (int c = 0; c < BN / 32; ++c) {
@@ -815,6 +1011,7 @@ struct FinItem {
     const float* c0;             // ABC_SPLIT_DRAWS: -2 delta . yh per voxel
     const float* dn;             // ABC_SPLIT_DRAWS: ||delta|| per voxel
     const int32_t* perm;         // list row -> voxel (null: identity)
+    const int32_t* xperm;        // packed draw row -> draw (null: identity)
     float* keys;
     int32_t* idx;
     int32_t* cnt;
@@ -937,6 +1134,11 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
             const uint32_t T = warp_select(kj, cnt, P.kt - 1, 3, hist, lane);
             cnt = warp_compact(kj, ij, cnt, T, P.C, lane);
             T_out = key2f(T);
+        }
+        // list entries are packed draw rows: back to global draw indices
+        if (P.xperm) {
+            for (int i = lane; i < cnt; i += 32) ij[i] = P.xperm[ij[i]];
+            __syncwarp();
         }
         // 2. exact fp32 re-score of the net: G lanes per row, four rows per group in flight
         constexpr int NR = 4;
@@ -1244,11 +1446,16 @@ void make_batch_layout(const ScanSpec* sc, int n, int mode, const Tuning& tu, Ba
 // Every section of a scan's layout lies after the previous one and inside the scan's total.
 bool layout_consistent(const Layout& L) {
     const size_t off[] = {L.off_mu, L.off_part, L.off_ynorm, L.off_c0, L.off_dn, L.off_a, L.off_b, L.off_keys,
-                          L.off_idx, L.off_cnt, L.off_thr, L.off_thr0, L.off_perm, L.off_feat, L.off_hist};
+                          L.off_idx, L.off_cnt, L.off_thr, L.off_thr0, L.off_perm, L.off_feat, L.off_hist,
+                          L.off_xperm, L.off_xfeat, L.off_xhist, L.off_fy, L.off_fx, L.off_tbox, L.off_ktile,
+                          L.off_kcount};
     const size_t len[] = {MAXL * 4, (size_t)L.npart * MAXL * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
                           (size_t)L.Jp * L.Kp * 2, (size_t)L.Np * L.Kp * 2, (size_t)L.J * L.C * 4,
                           (size_t)L.J * L.C * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
-                          (size_t)L.Jp * 4, (size_t)3 * L.Jp * 4 + 32, (size_t)ORDER_BUCKETS * 4};
+                          (size_t)L.Jp * 4, (size_t)3 * L.Jp * 4 + 32, (size_t)ORDER_BUCKETS * 4,
+                          (size_t)L.Np * 4, (size_t)3 * L.Np * 4 + 32, (size_t)ORDER_BUCKETS * 4,
+                          (size_t)3 * L.Jp * 4, (size_t)3 * L.Np * 4, (size_t)6 * L.nt64 * 4,
+                          (size_t)L.nvt * L.nt64 * 4, (size_t)L.nvt * 4};
     const int n = (int)(sizeof off / sizeof off[0]);
     for (int i = 0; i < n; ++i) {
         if (off[i] + len[i] > (i + 1 < n ? off[i + 1] : L.total)) return false;
@@ -1291,9 +1498,9 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     BatchPilot PB;
     BatchFin F;
     struct Ptrs {
-        float *mu, *part, *ynorm, *c0, *dn, *keys, *thr, *thr0, *feat;
-        int32_t* perm;
-        uint32_t *mm, *hist;
+        float *mu, *part, *ynorm, *c0, *dn, *keys, *thr, *thr0, *feat, *xfeat, *fy, *fx, *tbox;
+        int32_t *perm, *xperm, *ktile, *kcount;
+        uint32_t *mm, *hist, *xmm, *xhist;
         __nv_bfloat16 *A, *B;
         int32_t *idx, *cnt;
     } ptr[MAX_ITEMS];
@@ -1317,6 +1524,15 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         p.feat = (float*)(base + L.off_feat);
         p.mm = (uint32_t*)(p.feat + 3 * L.Jp);
         p.hist = (uint32_t*)(base + L.off_hist);
+        p.xperm = (int32_t*)(base + L.off_xperm);
+        p.xfeat = (float*)(base + L.off_xfeat);
+        p.xmm = (uint32_t*)(p.xfeat + 3 * L.Np);
+        p.xhist = (uint32_t*)(base + L.off_xhist);
+        p.fy = (float*)(base + L.off_fy);
+        p.fx = (float*)(base + L.off_fx);
+        p.tbox = (float*)(base + L.off_tbox);
+        p.ktile = (int32_t*)(base + L.off_ktile);
+        p.kcount = (int32_t*)(base + L.off_kcount);
         Weights W;
         memset(&W, 0, sizeof W);
         for (int l = 0; l < L.L; ++l) {
@@ -1344,11 +1560,30 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         }
         k_pack_y<<<(unsigned)vpet_ceil_div(L.Jp, 8), 256, 0, s>>>(sc[i].y, L.J, L.Jp, sc[i].ldy, L.L, L.Kp, mode, W,
                                                                   p.mu, order ? p.perm : nullptr, p.A, p.ynorm, p.c0,
-                                                                  p.dn);
+                                                                  p.dn, p.fy);
         VPET_LAUNCH_CHECK();
+        // draws in the same kind of order (alike draws in the same tiles, so that tile boxes are tight)
+        const bool xorder = dump == nullptr && L.N > 1;
+        if (xorder) {
+            k_order_init<<<(unsigned)vpet_ceil_div(ORDER_BUCKETS, 256), 256, 0, s>>>(p.xmm, p.xhist);
+            VPET_LAUNCH_CHECK();
+            const unsigned gb = (unsigned)vpet_ceil_div(L.N, 256);
+            k_order_features<<<gb, 256, 0, s>>>(sc[i].x, L.N, sc[i].ldx, L.L, W, p.xfeat, p.xmm);
+            VPET_LAUNCH_CHECK();
+            k_order_hist<<<gb, 256, 0, s>>>(p.xfeat, p.xmm, L.N, p.xhist);
+            VPET_LAUNCH_CHECK();
+            k_order_scan<<<1, 1024, 0, s>>>(p.xhist);
+            VPET_LAUNCH_CHECK();
+            k_order_scatter<<<gb, 256, 0, s>>>(p.xfeat, p.xmm, L.N, p.xhist, p.xperm);
+            VPET_LAUNCH_CHECK();
+        }
         k_pack_x<<<(unsigned)vpet_ceil_div(L.Np, 8), 256, 0, s>>>(sc[i].x, L.N, L.Np, sc[i].ldx, L.L, L.Kp, mode, W,
-                                                                  p.mu, p.B);
+                                                                  p.mu, xorder ? p.xperm : nullptr, p.B, p.fx);
         VPET_LAUNCH_CHECK();
+        if (xorder) {
+            k_tile_boxes<<<(unsigned)vpet_ceil_div(L.nt64, 8), 256, 0, s>>>(p.fx, L.N, L.nt64, p.tbox);
+            VPET_LAUNCH_CHECK();
+        }
     }
     // work order: costliest scans first (longest-processing-time round robin)
     int order[MAX_ITEMS];
@@ -1414,12 +1649,42 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         k_pilot_threshold<<<(unsigned)vpet_ceil_div(PB.v_prefix[m], 8), 256, 0, s>>>(PB);
         VPET_LAUNCH_CHECK();
     }
+    // draw tiles the main pass can skip (needs the pilot thresholds and the ordered draws)
+    unsigned long long* tally = (unsigned long long*)(wsb + 192);
+    bool skip[MAX_ITEMS];
+    for (int i = 0; i < n; ++i) {
+        const Layout& L = BL.lay[i];
+        skip[i] = dump == nullptr && L.nlev > 0 && L.N > 1;
+        if (!skip[i]) continue;
+        KeepArgs K;
+        memset(&K, 0, sizeof K);
+        K.fy = ptr[i].fy;
+        K.thr0 = ptr[i].thr0;
+        K.ynorm = ptr[i].ynorm;
+        K.tbox = ptr[i].tbox;
+        K.ktile = ptr[i].ktile;
+        K.kcount = ptr[i].kcount;
+        K.tally = tally;
+        K.J = L.J;
+        K.N = L.N;
+        K.nt64 = L.nt64;
+        for (int l = 0; l < L.L; ++l) K.Wc[(3 * l) / L.L] += sc[i].w[l];
+        K.cE = mode == ABC_BF16_RESCORE ? 0.0f : error_coef(L);
+        K.bn = tu.bn;
+        k_keep_tiles<<<(unsigned)L.nvt, 256, 0, s>>>(K);
+        VPET_LAUNCH_CHECK();
+    }
     // main pass
     memset(&T, 0, sizeof T);
     for (int oi = 0; oi < n; ++oi) {
         const int i = order[oi];
         const Layout& L = BL.lay[i];
         if ((rc = fill_item(T.item[oi], i, 1, L.kt, L.C, L.nlev > 0 ? ptr[i].thr0 : nullptr))) return rc;
+        if (skip[i]) {
+            T.item[oi].ktile = ptr[i].ktile;
+            T.item[oi].kcount = ptr[i].kcount;
+            T.item[oi].kstride = L.nt64;
+        }
         T.vt_prefix[oi + 1] = T.vt_prefix[oi] + L.Jp / BM;
     }
     T.n_items = n;
@@ -1454,6 +1719,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         f.c0 = ptr[i].c0;
         f.dn = ptr[i].dn;
         f.perm = (dump == nullptr && L.J > 1) ? ptr[i].perm : nullptr;
+        f.xperm = (dump == nullptr && L.N > 1) ? ptr[i].xperm : nullptr;
         f.keys = ptr[i].keys;
         f.idx = ptr[i].idx;
         f.cnt = ptr[i].cnt;
