@@ -231,6 +231,16 @@ int abc_discrepancy_topk_noalloc(const float* y_dev, int64_t J, int32_t ldy, con
  *               and (voxel, pilot level) pairs left without a pilot threshold. */
 int abc_topk_status(const void* workspace, int32_t status_host[8], void* stream);
 
+/* Work done by the last main pass on this workspace: out_host[0] = draw tiles it
+ * processed, out_host[1] = draw tiles a pass without skipping would process,
+ * summed over voxel tiles (both 0 when no tile was skipped).  The main pass
+ * skips a draw tile when a lower bound on every voxel-draw distance of the two
+ * tiles, (F_c(y) - F_c(x))^2 / W_c summed over the three consecutive thirds c
+ * of the frames (F_c = sum over the third of w_l v_l, W_c = sum of its w_l; a
+ * Cauchy-Schwarz bound on Sec. II-C's distance), exceeds the voxel tile's
+ * largest threshold.  Synchronises `stream`. */
+int abc_topk_work(const void* workspace, int64_t out_host[2], void* stream);
+
 /* Timing hook: when both are non-NULL (cudaEvent_t passed as void*), every
  * later abc_discrepancy_topk records `start_event` on its stream right before
  * the fused tensor-core kernel and `stop_event` right after it, so a caller can

@@ -109,6 +109,13 @@ def topk_status(workspace, stream=None):
     return tuple(int(v) for v in st)
 
 
+def topk_work(workspace, stream=None):
+    """(draw tiles processed, draw tiles without skipping) of the last main pass."""
+    out = np.zeros(2, np.int64)
+    check(lib().abc_topk_work(_ptr(workspace), out.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return int(out[0]), int(out[1])
+
+
 def debug_gemm_keys(y, x, L, w, precision, stream=None):
     """Raw tensor-core ranking keys d' = ||xh||^2 - 2 yh.xh for all pairs (test hook)."""
     J, N = y.shape[0], x.shape[0]

@@ -68,7 +68,8 @@ constexpr int TC_THREADS = 192;
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any barrier wait
 constexpr int MAXL = 64;
 constexpr int ORDER_BITS = 10;                 // bits per ordering feature (30-bit Morton key)
-constexpr int ORDER_BUCKETS = 1 << 16;         // counting-sort buckets (top 16 key bits)
+constexpr int ORDER_BUCKET_BITS = 18;
+constexpr int ORDER_BUCKETS = 1 << ORDER_BUCKET_BITS;   // counting-sort buckets
 constexpr int MAX_PILOT_LEVELS = 4;
 constexpr int MAX_ITEMS = 64;                 // scans per batched launch
 
@@ -289,10 +290,29 @@ __device__ __forceinline__ uint32_t order_key(const float* feat, const uint32_t*
     return spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
 }
 
-__global__ void k_order_hist(const float* __restrict__ feat, const uint32_t* __restrict__ mm, int64_t J,
-                             uint32_t* __restrict__ hist) {
+// Counting-sort bucket of row j.  Draws (nlev > 0) are grouped first by the
+// pilot samples they belong to: the draws j with j % s1^nlev == 0 (the coarsest
+// pilot) come first, then those of the next finer pilot, and so on, so every
+// pilot pass reads a contiguous leading block of the packed draws; within a
+// group (but the coarsest) the Morton key orders them.  Voxels (nlev = 0):
+// Morton key only.
+__device__ __forceinline__ uint32_t order_bucket(const float* feat, const uint32_t* mm, int64_t j, int nlev,
+                                                 int64_t s1) {
+    const uint32_t key = order_key(feat, mm, j);
+    if (nlev <= 0) return key >> (3 * ORDER_BITS - ORDER_BUCKET_BITS);
+    int g = 0;
+    int64_t sl = s1;
+    for (int l = 1; l <= nlev; ++l, sl *= s1) g += (j % sl) == 0;
+    // the coarsest pilot starts without a threshold and converges fastest on
+    // draws in arbitrary order: its group is one bucket
+    if (g == nlev) return 0u;
+    return ((uint32_t)(nlev - g) << (ORDER_BUCKET_BITS - 3)) | (key >> (3 * ORDER_BITS - (ORDER_BUCKET_BITS - 3)));
+}
+
+__global__ void k_order_hist(const float* __restrict__ feat, const uint32_t* __restrict__ mm, int64_t J, int nlev,
+                             int64_t s1, uint32_t* __restrict__ hist) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < J) atomicAdd(&hist[order_key(feat, mm, j) >> (3 * ORDER_BITS - 16)], 1u);
+    if (j < J) atomicAdd(&hist[order_bucket(feat, mm, j, nlev, s1)], 1u);
 }
 
 // exclusive scan of the ORDER_BUCKETS counts, in place (one block of 1024 threads)
@@ -300,12 +320,8 @@ __global__ void __launch_bounds__(1024) k_order_scan(uint32_t* __restrict__ hist
     __shared__ uint32_t part[1024];
     constexpr int PER = ORDER_BUCKETS / 1024;
     const int t = threadIdx.x;
-    uint32_t loc[PER], s = 0;
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        loc[i] = hist[t * PER + i];
-        s += loc[i];
-    }
+    uint32_t s = 0;
+    for (int i = 0; i < PER; ++i) s += hist[t * PER + i];
     part[t] = s;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {
@@ -315,19 +331,19 @@ __global__ void __launch_bounds__(1024) k_order_scan(uint32_t* __restrict__ hist
         __syncthreads();
     }
     uint32_t run = part[t] - s;
-#pragma unroll
     for (int i = 0; i < PER; ++i) {
+        const uint32_t c = hist[t * PER + i];
         hist[t * PER + i] = run;
-        run += loc[i];
+        run += c;
     }
 }
 
 // perm[position] = voxel; voxels of one bucket land in arrival order
 __global__ void k_order_scatter(const float* __restrict__ feat, const uint32_t* __restrict__ mm, int64_t J,
-                                uint32_t* __restrict__ hist, int32_t* __restrict__ perm) {
+                                int nlev, int64_t s1, uint32_t* __restrict__ hist, int32_t* __restrict__ perm) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= J) return;
-    const uint32_t pos = atomicAdd(&hist[order_key(feat, mm, j) >> (3 * ORDER_BITS - 16)], 1u);
+    const uint32_t pos = atomicAdd(&hist[order_bucket(feat, mm, j, nlev, s1)], 1u);
     perm[pos] = (int32_t)j;
 }
 
@@ -607,8 +623,10 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
     }
     if (tid == 0) {
         K.kcount[vt] = base;
-        atomicAdd(&K.tally[0], (unsigned long long)base);
-        atomicAdd(&K.tally[1], (unsigned long long)ntiles);
+        if (K.tally) {
+            atomicAdd(&K.tally[0], (unsigned long long)base);
+            atomicAdd(&K.tally[1], (unsigned long long)ntiles);
+        }
     }
 }
 
@@ -1551,11 +1569,11 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             const unsigned gb = (unsigned)vpet_ceil_div(L.J, 256);
             k_order_features<<<gb, 256, 0, s>>>(sc[i].y, L.J, sc[i].ldy, L.L, W, p.feat, p.mm);
             VPET_LAUNCH_CHECK();
-            k_order_hist<<<gb, 256, 0, s>>>(p.feat, p.mm, L.J, p.hist);
+            k_order_hist<<<gb, 256, 0, s>>>(p.feat, p.mm, L.J, 0, 1, p.hist);
             VPET_LAUNCH_CHECK();
             k_order_scan<<<1, 1024, 0, s>>>(p.hist);
             VPET_LAUNCH_CHECK();
-            k_order_scatter<<<gb, 256, 0, s>>>(p.feat, p.mm, L.J, p.hist, p.perm);
+            k_order_scatter<<<gb, 256, 0, s>>>(p.feat, p.mm, L.J, 0, 1, p.hist, p.perm);
             VPET_LAUNCH_CHECK();
         }
         k_pack_y<<<(unsigned)vpet_ceil_div(L.Jp, 8), 256, 0, s>>>(sc[i].y, L.J, L.Jp, sc[i].ldy, L.L, L.Kp, mode, W,
@@ -1570,11 +1588,11 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             const unsigned gb = (unsigned)vpet_ceil_div(L.N, 256);
             k_order_features<<<gb, 256, 0, s>>>(sc[i].x, L.N, sc[i].ldx, L.L, W, p.xfeat, p.xmm);
             VPET_LAUNCH_CHECK();
-            k_order_hist<<<gb, 256, 0, s>>>(p.xfeat, p.xmm, L.N, p.xhist);
+            k_order_hist<<<gb, 256, 0, s>>>(p.xfeat, p.xmm, L.N, L.nlev, tu.pilot_stride, p.xhist);
             VPET_LAUNCH_CHECK();
             k_order_scan<<<1, 1024, 0, s>>>(p.xhist);
             VPET_LAUNCH_CHECK();
-            k_order_scatter<<<gb, 256, 0, s>>>(p.xfeat, p.xmm, L.N, p.xhist, p.xperm);
+            k_order_scatter<<<gb, 256, 0, s>>>(p.xfeat, p.xmm, L.N, L.nlev, tu.pilot_stride, p.xhist, p.xperm);
             VPET_LAUNCH_CHECK();
         }
         k_pack_x<<<(unsigned)vpet_ceil_div(L.Np, 8), 256, 0, s>>>(sc[i].x, L.N, L.Np, sc[i].ldx, L.L, L.Kp, mode, W,
@@ -1622,7 +1640,30 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     int maxlev = 0;
     for (int i = 0; i < n; ++i) maxlev = BL.lay[i].nlev > maxlev ? BL.lay[i].nlev : maxlev;
     if (dump) maxlev = 0;
-    // pilot passes, coarsest level first
+    // draw tiles a pass can skip, from the thresholds in thr0 (needs the ordered draws)
+    auto keep_tiles = [&](int i, int64_t npass, unsigned long long* tally) -> int {
+        const Layout& L = BL.lay[i];
+        KeepArgs K;
+        memset(&K, 0, sizeof K);
+        K.fy = ptr[i].fy;
+        K.thr0 = ptr[i].thr0;
+        K.ynorm = ptr[i].ynorm;
+        K.tbox = ptr[i].tbox;
+        K.ktile = ptr[i].ktile;
+        K.kcount = ptr[i].kcount;
+        K.tally = tally;
+        K.J = L.J;
+        K.N = npass;
+        K.nt64 = L.nt64;
+        for (int l = 0; l < L.L; ++l) K.Wc[(3 * l) / L.L] += sc[i].w[l];
+        K.cE = mode == ABC_BF16_RESCORE ? 0.0f : error_coef(L);
+        K.bn = tu.bn;
+        k_keep_tiles<<<(unsigned)L.nvt, 256, 0, s>>>(K);
+        VPET_LAUNCH_CHECK();
+        return ABC_OK;
+    };
+    // pilot passes, coarsest level first; pilot level lv reads the leading
+    // ceil(N / stride) packed draws (the draws j with j % stride == 0)
     for (int lv = maxlev - 1; lv >= 0; --lv) {
         memset(&T, 0, sizeof T);
         memset(&PB, 0, sizeof PB);
@@ -1633,8 +1674,17 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             if (L.nlev <= lv) continue;
             const int r = L.lev_rank[lv];
             const int lim = (int)(4 * (int64_t)r + 256 < L.C ? 4 * (int64_t)r + 256 : L.C);
-            if ((rc = fill_item(T.item[m], i, L.lev_stride[lv], r, lim, lv + 1 < L.nlev ? ptr[i].thr0 : nullptr)))
-                return rc;
+            const bool has_thr = lv + 1 < L.nlev;
+            if ((rc = fill_item(T.item[m], i, 1, r, lim, has_thr ? ptr[i].thr0 : nullptr))) return rc;
+            const int64_t npass = vpet_ceil_div(L.N, L.lev_stride[lv]);
+            T.item[m].N = npass;
+            T.item[m].ntiles = (int)vpet_ceil_div(npass, tu.bn);
+            if (has_thr) {
+                if ((rc = keep_tiles(i, npass, nullptr))) return rc;
+                T.item[m].ktile = ptr[i].ktile;
+                T.item[m].kcount = ptr[i].kcount;
+                T.item[m].kstride = L.nt64;
+            }
             T.vt_prefix[m + 1] = T.vt_prefix[m] + L.Jp / BM;
             PB.item[m] = PilotItem{ptr[i].keys, ptr[i].cnt, ptr[i].thr0, L.J, L.C, r};
             PB.v_prefix[m + 1] = PB.v_prefix[m] + L.J;
@@ -1655,24 +1705,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     for (int i = 0; i < n; ++i) {
         const Layout& L = BL.lay[i];
         skip[i] = dump == nullptr && L.nlev > 0 && L.N > 1;
-        if (!skip[i]) continue;
-        KeepArgs K;
-        memset(&K, 0, sizeof K);
-        K.fy = ptr[i].fy;
-        K.thr0 = ptr[i].thr0;
-        K.ynorm = ptr[i].ynorm;
-        K.tbox = ptr[i].tbox;
-        K.ktile = ptr[i].ktile;
-        K.kcount = ptr[i].kcount;
-        K.tally = tally;
-        K.J = L.J;
-        K.N = L.N;
-        K.nt64 = L.nt64;
-        for (int l = 0; l < L.L; ++l) K.Wc[(3 * l) / L.L] += sc[i].w[l];
-        K.cE = mode == ABC_BF16_RESCORE ? 0.0f : error_coef(L);
-        K.bn = tu.bn;
-        k_keep_tiles<<<(unsigned)L.nvt, 256, 0, s>>>(K);
-        VPET_LAUNCH_CHECK();
+        if (skip[i] && (rc = keep_tiles(i, L.N, tally))) return rc;
     }
     // main pass
     memset(&T, 0, sizeof T);
@@ -1808,6 +1841,18 @@ extern "C" int abc_discrepancy_topk(const float* y_dev, int64_t J, int32_t ldy, 
     vpet::clear_error();
     return vpet::topk_on_workspace(y_dev, J, ldy, x_dev, N, ldx, L, w_host, k, precision, workspace, ws_bytes, idx_dev,
                                    dist_dev, (cudaStream_t)stream);
+}
+
+extern "C" int abc_topk_work(const void* workspace, int64_t out_host[2], void* stream) {
+    vpet::clear_error();
+    VPET_ARG(workspace && out_host, "abc_topk_work: null pointer");
+    unsigned long long t[2];
+    VPET_CUDA(cudaMemcpyAsync(t, (const uint8_t*)workspace + 192, sizeof t, cudaMemcpyDeviceToHost,
+                              (cudaStream_t)stream));
+    VPET_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    out_host[0] = (int64_t)t[0];
+    out_host[1] = (int64_t)t[1];
+    return ABC_OK;
 }
 
 extern "C" int abc_default_tuning(int32_t precision, abc_tuning* out) {
