@@ -106,7 +106,8 @@ struct Layout {
     int npart;
     size_t off_mu, off_part, off_ynorm, off_c0, off_dn, off_a, off_b, off_keys, off_idx, off_cnt, off_thr, off_thr0,
         off_perm, off_feat, off_hist, off_xperm, off_xfeat, off_xhist, off_fy, off_fx, off_tbox, off_ktile,
-        off_kcount, total;
+        off_kcount, off_xs, total;
+    int ldxs;                          // row stride (floats) of the packed fp32 draw copy
     int64_t nt64;                      // 64-draw tiles of the draw operand
     int64_t nvt;                       // 128-voxel tiles
 };
@@ -191,6 +192,8 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.off_tbox = o; o = align256(o + (size_t)6 * s.nt64 * sizeof(float));
     s.off_ktile = o; o = align256(o + (size_t)s.nvt * s.nt64 * sizeof(int32_t));
     s.off_kcount = o; o = align256(o + (size_t)s.nvt * sizeof(int32_t));
+    s.ldxs = (int)vpet_round_up(L, 4);
+    s.off_xs = o; o = align256(o + (size_t)s.Np * s.ldxs * sizeof(float));
     s.total = o;
     return s;
 }
@@ -432,10 +435,13 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
 }
 
 // One warp per draw row: B row of the GEMM.
-// Row n of B is draw xperm[n] (xperm = null: draw n); fx[3 n + c] = its segment features.
+// Row n of B is draw xperm[n] (xperm = null: draw n); fx[3 n + c] = its segment
+// features; xs row n (stride ldxs, zero-padded) = that draw's fp32 TAC, so that
+// the exact re-score reads the draws in packed order.
 __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int ldx, int L, int Kp, int mode,
                          Weights W, const float* __restrict__ mu, const int32_t* __restrict__ xperm,
-                         __nv_bfloat16* __restrict__ B, float* __restrict__ fx) {
+                         __nv_bfloat16* __restrict__ B, float* __restrict__ fx, float* __restrict__ xs,
+                         int ldxs) {
     const int lane = threadIdx.x & 31;
     const int64_t n = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (n >= Np) return;
@@ -445,6 +451,7 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
         return;
     }
     const float* xr = x + (xperm ? (int64_t)xperm[n] : n) * ldx;
+    for (int l = lane; l < ldxs; l += 32) xs[n * ldxs + l] = l < L ? xr[l] : 0.0f;
     {
         float f[3];
         seg_features(xr, L, W, lane, f);
@@ -1030,6 +1037,8 @@ struct FinItem {
     const float* dn;             // ABC_SPLIT_DRAWS: ||delta|| per voxel
     const int32_t* perm;         // list row -> voxel (null: identity)
     const int32_t* xperm;        // packed draw row -> draw (null: identity)
+    const float* xs;             // draws in packed order, fp32 (row stride ldxs)
+    int ldxs;
     float* keys;
     int32_t* idx;
     int32_t* cnt;
@@ -1153,19 +1162,15 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
             cnt = warp_compact(kj, ij, cnt, T, P.C, lane);
             T_out = key2f(T);
         }
-        // list entries are packed draw rows: back to global draw indices
-        if (P.xperm) {
-            for (int i = lane; i < cnt; i += 32) ij[i] = P.xperm[ij[i]];
-            __syncwarp();
-        }
-        // 2. exact fp32 re-score of the net: G lanes per row, four rows per group in flight
+        // 2. exact fp32 re-score of the net (list entries are packed draw rows, read from the
+        // packed fp32 copy): G lanes per row, four rows per group in flight
         constexpr int NR = 4;
         for (int i0 = 0; i0 < cnt; i0 += NR * R) {
             const float* xr[NR];
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 const int i = i0 + r * R + grp;
-                xr[r] = P.x + (int64_t)ij[i < cnt ? i : cnt - 1] * P.ldx;
+                xr[r] = P.xs + (int64_t)ij[i < cnt ? i : cnt - 1] * P.ldxs;
             }
             float d[NR];
             group_dist_n<NR>(ys, ws, xr, P.L, h, G, d);
@@ -1179,6 +1184,11 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
             }
         }
         __syncwarp();
+        // back to global draw indices (ties break by them)
+        if (P.xperm) {
+            for (int i = lane; i < cnt; i += 32) ij[i] = P.xperm[ij[i]];
+            __syncwarp();
+        }
         // 3. exact k-th distance and the certificate
         bool cert = false;
         if (cnt >= P.k) {
@@ -1466,14 +1476,14 @@ bool layout_consistent(const Layout& L) {
     const size_t off[] = {L.off_mu, L.off_part, L.off_ynorm, L.off_c0, L.off_dn, L.off_a, L.off_b, L.off_keys,
                           L.off_idx, L.off_cnt, L.off_thr, L.off_thr0, L.off_perm, L.off_feat, L.off_hist,
                           L.off_xperm, L.off_xfeat, L.off_xhist, L.off_fy, L.off_fx, L.off_tbox, L.off_ktile,
-                          L.off_kcount};
+                          L.off_kcount, L.off_xs};
     const size_t len[] = {MAXL * 4, (size_t)L.npart * MAXL * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
                           (size_t)L.Jp * L.Kp * 2, (size_t)L.Np * L.Kp * 2, (size_t)L.J * L.C * 4,
                           (size_t)L.J * L.C * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
                           (size_t)L.Jp * 4, (size_t)3 * L.Jp * 4 + 32, (size_t)ORDER_BUCKETS * 4,
                           (size_t)L.Np * 4, (size_t)3 * L.Np * 4 + 32, (size_t)ORDER_BUCKETS * 4,
                           (size_t)3 * L.Jp * 4, (size_t)3 * L.Np * 4, (size_t)6 * L.nt64 * 4,
-                          (size_t)L.nvt * L.nt64 * 4, (size_t)L.nvt * 4};
+                          (size_t)L.nvt * L.nt64 * 4, (size_t)L.nvt * 4, (size_t)L.Np * L.ldxs * 4};
     const int n = (int)(sizeof off / sizeof off[0]);
     for (int i = 0; i < n; ++i) {
         if (off[i] + len[i] > (i + 1 < n ? off[i + 1] : L.total)) return false;
@@ -1518,6 +1528,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     struct Ptrs {
         float *mu, *part, *ynorm, *c0, *dn, *keys, *thr, *thr0, *feat, *xfeat, *fy, *fx, *tbox;
         int32_t *perm, *xperm, *ktile, *kcount;
+        float* xs;
         uint32_t *mm, *hist, *xmm, *xhist;
         __nv_bfloat16 *A, *B;
         int32_t *idx, *cnt;
@@ -1551,6 +1562,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         p.tbox = (float*)(base + L.off_tbox);
         p.ktile = (int32_t*)(base + L.off_ktile);
         p.kcount = (int32_t*)(base + L.off_kcount);
+        p.xs = (float*)(base + L.off_xs);
         Weights W;
         memset(&W, 0, sizeof W);
         for (int l = 0; l < L.L; ++l) {
@@ -1596,7 +1608,8 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             VPET_LAUNCH_CHECK();
         }
         k_pack_x<<<(unsigned)vpet_ceil_div(L.Np, 8), 256, 0, s>>>(sc[i].x, L.N, L.Np, sc[i].ldx, L.L, L.Kp, mode, W,
-                                                                  p.mu, xorder ? p.xperm : nullptr, p.B, p.fx);
+                                                                  p.mu, xorder ? p.xperm : nullptr, p.B, p.fx, p.xs,
+                                                                  L.ldxs);
         VPET_LAUNCH_CHECK();
         if (xorder) {
             k_tile_boxes<<<(unsigned)vpet_ceil_div(L.nt64, 8), 256, 0, s>>>(p.fx, L.N, L.nt64, p.tbox);
@@ -1753,6 +1766,8 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         f.dn = ptr[i].dn;
         f.perm = (dump == nullptr && L.J > 1) ? ptr[i].perm : nullptr;
         f.xperm = (dump == nullptr && L.N > 1) ? ptr[i].xperm : nullptr;
+        f.xs = ptr[i].xs;
+        f.ldxs = L.ldxs;
         f.keys = ptr[i].keys;
         f.idx = ptr[i].idx;
         f.cnt = ptr[i].cnt;
