@@ -1039,6 +1039,10 @@ struct FinItem {
     const int32_t* xperm;        // packed draw row -> draw (null: identity)
     const float* xs;             // draws in packed order, fp32 (row stride ldxs)
     int ldxs;
+    const float* tbox;           // 64-draw tile feature boxes (null: draws not ordered)
+    const float* fy;             // voxel segment features per list row
+    int64_t nt64;
+    float Wc[3];
     float* keys;
     int32_t* idx;
     int32_t* cnt;
@@ -1154,6 +1158,7 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
         else if (cnt < P.kt) atomicAdd(&B.status[6], 1);
     }
     uint32_t K = 0;
+    float dbound = __int_as_float(0x7F800000);   // exact k-th distance of the net: bounds the true one
     if (!scan) {
         // 1. the net: every draw outside it has computed key > T_out
         float T_out = P.thr[j];
@@ -1194,6 +1199,7 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
         if (cnt >= P.k) {
             K = warp_select(kj, cnt, P.k - 1, 4, hist, lane);
             const float dk = key2f(K);
+            dbound = dk;
             const float yn = P.ynorm[j];
             const float slack = 4.0f * (float)P.L * 0x1p-24f;
             const float ry = sqrtf(yn);
@@ -1213,19 +1219,20 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
         }
     }
     if (scan) {
-        // exact fp32 scan of every draw (candidate list rebuilt with exact keys)
+        // exact fp32 scan (candidate list rebuilt with exact keys) of every draw that can
+        // be within the net's exact k-th distance: with ordered draws, only the 64-draw
+        // tiles whose segment-feature bound does not exceed it
         if (lane == 0) atomicAdd(&B.status[1], 1);
         cnt = 0;
-        float thr = __int_as_float(0x7F800000);
-        for (int64_t base = 0; base < P.N; base += 32) {
-            const int64_t n = base + lane;
-            const float d = n < P.N ? lane_dist(ys, ws, P.x + n * P.ldx, P.L, G) : __int_as_float(0x7F800000);
+        float thr = dbound;
+        auto take_row = [&](int64_t n, const float* xrow, int32_t gidx) {
+            const float d = n < P.N ? lane_dist(ys, ws, xrow, P.L, G) : __int_as_float(0x7F800000);
             const bool take = n < P.N && d <= thr;
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
             if (take) {
                 const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
                 kj[pos] = d;
-                ij[pos] = (int32_t)n;
+                ij[pos] = gidx;
             }
             cnt += __popc(bal);
             if (cnt > P.C - 32) {
@@ -1234,6 +1241,42 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
                 const int q = warp_compact(kj, ij, cnt, T, P.C - 64, lane);
                 cnt = q < P.C - 64 ? q : P.C - 64;
                 thr = key2f(T);
+            }
+        };
+        if (P.tbox) {
+            const float db = dbound < 3.0e38f ? dbound * (1.0f + 0x1p-10f) : 3.0e38f;
+            const float f0 = P.fy[3 * j], f1 = P.fy[3 * j + 1], f2 = P.fy[3 * j + 2];
+            for (int64_t t0 = 0; t0 < P.nt64; t0 += 32) {
+                const int64_t t = t0 + lane;
+                bool keep = false;
+                if (t < P.nt64 && t * 64 < P.N) {
+                    float lb = 0.0f;
+                    const float fv[3] = {f0, f1, f2};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float xl = P.tbox[6 * t + 2 * c], xh = P.tbox[6 * t + 2 * c + 1];
+                        const float slack = 0x1p-18f * (fabsf(xl) + fabsf(xh) + 2.0f * fabsf(fv[c]));
+                        const float gap = fmaxf(fmaxf(xl - fv[c], fv[c] - xh) - slack, 0.0f);
+                        if (P.Wc[c] > 0.0f) lb += gap * gap / P.Wc[c];
+                    }
+                    keep = lb * (1.0f - 0x1p-10f) <= db;
+                }
+                uint32_t km = __ballot_sync(0xFFFFFFFFu, keep);
+                while (km) {
+                    const int b = __ffs(km) - 1;
+                    km &= km - 1;
+#pragma unroll 1
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int64_t n = (t0 + b) * 64 + hh * 32 + lane;      // packed draw row
+                        const int64_t nn = n < P.N ? n : 0;
+                        take_row(n, P.xs + nn * P.ldxs, P.xperm ? P.xperm[nn] : (int32_t)nn);
+                    }
+                }
+            }
+        } else {
+            for (int64_t base = 0; base < P.N; base += 32) {
+                const int64_t n = base + lane;
+                take_row(n, P.x + (n < P.N ? n : 0) * P.ldx, (int32_t)n);
             }
         }
         __syncwarp();
@@ -1768,6 +1811,10 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         f.xperm = (dump == nullptr && L.N > 1) ? ptr[i].xperm : nullptr;
         f.xs = ptr[i].xs;
         f.ldxs = L.ldxs;
+        f.tbox = (dump == nullptr && L.N > 1) ? ptr[i].tbox : nullptr;
+        f.fy = ptr[i].fy;
+        f.nt64 = L.nt64;
+        for (int l = 0; l < L.L; ++l) f.Wc[(3 * l) / L.L] += sc[i].w[l];
         f.keys = ptr[i].keys;
         f.idx = ptr[i].idx;
         f.cnt = ptr[i].cnt;

@@ -137,3 +137,14 @@ def test_argument_errors():
     with pytest.raises(AbcError) as e:
         api.discrepancy_topk(y, x, 22, w, 3, 0, workspace=ws)
     assert e.value.code == -3
+
+
+def test_exact_scan_path_matches_oracle(orc):
+    """The split-draws form cannot certify many voxels of this case; they go through the
+    exact scan over the tiles whose segment-feature bound admits the net's k-th distance.
+    The accepted sets still match the oracle's."""
+    from paper_2603_14859_b300 import api
+    W, y, x = _gpu_case("raclopride_lpntpet", 512, 20000, orc)
+    swaps, worst, scanned = _compare(orc, W, y, x, 50, 2)
+    assert scanned > 0
+    assert swaps == 0
