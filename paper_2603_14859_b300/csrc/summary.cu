@@ -1,7 +1,7 @@
 // Posterior model probabilities and posterior summaries over each voxel's
 // accepted draws (Sec. II-B Eq. 6, Sec. II-D, Sec. III-B).  One warp per voxel;
-// fp64 accumulation for means and variances; credible intervals from sorted
-// order statistics (type-7 interpolation).
+// fp64 accumulation for means and variances; credible intervals from exact
+// order statistics (radix selection, type-7 interpolation).
 #include <string.h>
 
 #include "common.cuh"
@@ -62,19 +62,74 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-__device__ void bitonic_f(float* s, int n, int lane) {
-    for (int size = 2; size <= n; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            __syncwarp();
-            for (int t = lane; t < (n >> 1); t += 32) {
-                const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const float a = s[lo], b = s[hi];
-                if ((a > b) == up) { s[lo] = b; s[hi] = a; }
-            }
+__device__ __forceinline__ uint32_t f2o(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(uint32_t k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k); }
+
+// The r-th smallest (0-based) of the n floats in s (shared memory), exactly: a
+// 4-level radix select on the order-preserving integer image, 8 bits per level;
+// hist is 256 words of this warp's shared memory.
+__device__ float warp_kth(const float* s, int n, int r, uint32_t* hist, int lane) {
+    uint32_t prefix = 0;
+    for (int lv = 0; lv < 4; ++lv) {
+        const int shift = 24 - 8 * lv;
+        const uint32_t mask = lv == 0 ? 0u : (0xFFFFFFFFu << (shift + 8));
+        for (int b = lane; b < 256; b += 32) hist[b] = 0;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const uint32_t k = f2o(s[i]);
+            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
         }
+        __syncwarp();
+        uint32_t loc[8], sum = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) { loc[b] = hist[lane * 8 + b]; sum += loc[b]; }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        uint32_t c = incl - sum;
+        int found = -1, nr = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            if (found < 0 && c + loc[b] > (uint32_t)r) { found = lane * 8 + b; nr = r - (int)c; }
+            c += loc[b];
+        }
+        const uint32_t who = __ballot_sync(0xFFFFFFFFu, found >= 0);
+        const int src = __ffs(who) - 1;
+        const int bin = __shfl_sync(0xFFFFFFFFu, found, src);
+        r = __shfl_sync(0xFFFFFFFFu, nr, src);
+        prefix |= (uint32_t)bin << shift;
+        __syncwarp();
     }
-    __syncwarp();
+    return o2f(prefix);
+}
+
+// Order statistics a and a + 1 (clamped to n - 1) of the n floats in s.
+__device__ void warp_pair(const float* s, int n, int a, uint32_t* hist, int lane, float& va, float& vb) {
+    va = warp_kth(s, n, a, hist, lane);
+    if (a + 1 >= n) {
+        vb = va;
+        return;
+    }
+    // the next order statistic: va again if more than a + 1 values are <= va, else the smallest above it
+    int le = 0;
+    float up = __int_as_float(0x7F800000);
+    for (int i = lane; i < n; i += 32) {
+        const float v = s[i];
+        le += v <= va;
+        if (v > va) up = fminf(up, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        le += __shfl_xor_sync(0xFFFFFFFFu, le, o);
+        up = fminf(up, __shfl_xor_sync(0xFFFFFFFFu, up, o));
+    }
+    vb = le > a + 1 ? va : up;
 }
 
 __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __restrict__ idx, int64_t J,
@@ -84,6 +139,7 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
     const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t* sel = (int32_t*)sm + (size_t)wid * Q.p2;
     float* vals = (float*)(sm + (size_t)warps * Q.p2 * 4) + (size_t)wid * Q.p2;
+    uint32_t* hist = (uint32_t*)(sm + (size_t)warps * Q.p2 * 8) + (size_t)wid * 256;
     const int64_t j = (int64_t)blockIdx.x * warps + wid;
     if (j >= J) return;
     const int pm = pref ? (int)pref[j] : -1;
@@ -136,17 +192,15 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
                 ss += e * e;
             }
             ss = warp_sum_d(ss);
-            int n2 = 1;
-            while (n2 < n) n2 <<= 1;
-            for (int i = n + lane; i < n2; i += 32) vals[i] = __int_as_float(0x7F800000);
-            bitonic_f(vals, n2, lane);
+            // type-7 quantiles from the two order statistics around each level
             double qv[2];
             const double qs[2] = {0.025, 0.975};
             for (int t = 0; t < 2; ++t) {
                 const double h = (n - 1) * qs[t];
                 const int a = (int)floor(h);
-                const int b = a + 1 < n ? a + 1 : n - 1;
-                qv[t] = (double)vals[a] + (h - a) * ((double)vals[b] - (double)vals[a]);
+                float va, vb;
+                warp_pair(vals, n, a, hist, lane, va, vb);
+                qv[t] = (double)va + (h - a) * ((double)vb - (double)va);
             }
             o0 = (float)mu;
             o1 = n > 1 ? (float)sqrt(ss / (n - 1)) : 0.0f;
@@ -224,8 +278,8 @@ extern "C" int abc_summarize(const float* theta_dev, int32_t ldtheta, const int6
     if (J == 0) return ABC_OK;
     VPET_ARG(theta_dev && idx_dev && mean_dev && sd_dev && lo_dev && hi_dev, "abc_summarize: null pointer");
     int warps = 8;
-    while (warps > 1 && (size_t)warps * p2 * 8 > 48 * 1024) warps >>= 1;
-    const size_t smem = (size_t)warps * p2 * 8;
+    while (warps > 1 && (size_t)warps * (p2 * 8 + 1024) > 48 * 1024) warps >>= 1;
+    const size_t smem = (size_t)warps * (p2 * 8 + 1024);
     k_summarize<<<(unsigned)vpet_ceil_div(J, warps), warps * 32, smem, (cudaStream_t)stream>>>(
         theta_dev, idx_dev, J, preferred_dev, Q, mean_dev, sd_dev, lo_dev, hi_dev);
     VPET_LAUNCH_CHECK();
