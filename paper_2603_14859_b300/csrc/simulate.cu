@@ -419,7 +419,7 @@ static int build_sim_params(int32_t model, const abc_frames* fr, const abc_polye
         p.a[i][1] = (float)in->a1[i];
         p.a[i][2] = (float)(2.0 * in->a2[i]);
     }
-    p.lp_h = 1.0f / 32.0f;
+    p.lp_h = 1.0f / 16.0f;
     return ABC_OK;
 }
 

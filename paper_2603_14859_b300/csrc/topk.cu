@@ -650,6 +650,7 @@ struct __align__(64) ItemTc {
     const float* thr0;           // initial threshold per voxel (pilot), or null = +huge
     int ntiles, C, kt, cap;
     int lim;                     // a list is compacted once it could exceed lim entries (lim <= C)
+    int lim0;                    // ... or lim0 entries while its voxel has no finite threshold yet
     const int32_t* ktile;        // kept draw tiles per voxel tile (null: every tile)
     const int32_t* kcount;
     int64_t kstride;
@@ -913,7 +914,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
             const ItemTc& I = P.item[it];
             const ItemRegs R{I.N, I.keys, I.idx, I.C};
             const int64_t vt = w - P.vt_prefix[it];
-            const int ntiles = I.ktile ? I.kcount[vt] : I.ntiles, lim = I.lim;
+            const int ntiles = I.ktile ? I.kcount[vt] : I.ntiles, lim = I.lim, lim0 = I.lim0;
             const int32_t* kt_list = I.ktile ? I.ktile + vt * I.kstride : nullptr;
             const int64_t m0 = vt * BM;
             const int64_t jbase = m0 + q * 32;
@@ -959,7 +960,9 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                 if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&tempty[acc]));
                 if (DUMP) continue;
                 // compaction of lists that might not fit the next tile
-                uint32_t need = __ballot_sync(0xFFFFFFFFu, valid && cnt > lim - BN);
+                // a list without a threshold yet (the coarsest pilot) is first cut early, at
+                // lim0: from then on far fewer keys pass than the everything of a +inf start
+                uint32_t need = __ballot_sync(0xFFFFFFFFu, valid && cnt > (thr >= 3.0e38f ? lim0 : lim) - BN);
                 while (need) {
                     const int src = __ffs(need) - 1;
                     need &= need - 1;
@@ -1691,6 +1694,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         I.kt = kt;
         I.cap = kt + (kt / 4 > 64 ? kt / 4 : 64);
         I.lim = lim;
+        I.lim0 = 2 * kt + tu.bn < lim ? 2 * kt + tu.bn : lim;
         return ABC_OK;
     };
     int maxlev = 0;
