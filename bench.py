@@ -475,14 +475,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     from paper_2603_14859_b300 import synth as S
 
+    from paper_2603_14859_b300 import sharding
+
     def make_workload(r):
-        W = S.workload(args.workload, seed=None, J=args.voxels, N_per_model=args.draws)
-        if r:   # another voxel shard of the volume, same seeded draws
-            W2 = S.workload(args.workload, seed=5000 + r, J=args.voxels, N_per_model=args.draws)
-            W2.prior_seed = W.prior_seed
-            W2.inp = W.inp
-            W = W2
-        return W
+        return sharding.rank_workload(args.workload, r, J=args.voxels, N_per_model=args.draws)
 
     if args.workload == "batched":
         return run_batched(args, world, rank, local)
@@ -584,10 +580,7 @@ def main():
     ms = e0.elapsed_time(e1) / K
     tc_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     clk = clocks.stop()
-    t = torch.tensor([ms, tc_ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms, tc_ms = float(t[0]), float(t[1])
+    ms, tc_ms = sharding.max_over_ranks([ms, tc_ms], dist, device="cuda")
 
     # end to end through the public API with host buffers
     y_host = y.cpu().pin_memory()
@@ -608,10 +601,7 @@ def main():
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / Ke
-    t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t[0])
+    e2e_ms = sharding.max_over_ranks([e2e_ms], dist, device="cuda")[0]
 
     if rank != 0:
         dist.destroy_process_group()
