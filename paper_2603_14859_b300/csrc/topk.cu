@@ -71,6 +71,7 @@ constexpr int ORDER_BITS = 10;                 // bits per ordering feature (30-
 constexpr int ORDER_BUCKET_BITS = 18;
 constexpr int ORDER_BUCKETS = 1 << ORDER_BUCKET_BITS;   // counting-sort buckets
 constexpr int MAX_PILOT_LEVELS = 4;
+constexpr int ROW_LD = 36;                     // floats per epilogue thread's key row (16-byte rows, conflict-free)
 constexpr int MAX_ITEMS = 64;                 // scans per batched launch
 
 struct Weights {
@@ -714,12 +715,11 @@ __device__ __forceinline__ uint32_t mask8(const float (&v)[32], int o, float thr
 
 // One 32-column chunk of the epilogue, per thread (= voxel j): the minima of
 // the four 8-key groups against the voxel's threshold; a thread with a passing
-// group builds the mask of passing keys (passing groups only) and appends each
-// one, picked out of its registers by a 5-level select tree on the bit
-// position, to the voxel's list.  About 0.1 % of the pairs pass, so few threads enter the append path,
-// and threads never wait for one another.
+// group builds the mask of passing keys (passing groups only), copies its 32
+// keys to its own row of shared memory (row_s) and appends each passing key,
+// read back by position, to the voxel's list.  Threads never wait for one another.
 __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32], int64_t n0, int64_t j, float thr,
-                                               int& cnt) {
+                                               int& cnt, float* row_s) {
     if (n0 + 32 > I.N) {
 #pragma unroll
         for (int i = 0; i < 32; ++i)
@@ -735,20 +735,15 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
     if (g1 <= thr) m |= mask8(v, 8, thr) << 8;
     if (g2 <= thr) m |= mask8(v, 16, thr) << 16;
     if (g3 <= thr) m |= mask8(v, 24, thr) << 24;
+    // the passing keys are read back by position from this thread's own row of shared memory
+    float4* dst = (float4*)row_s;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     const int64_t row = j * (int64_t)I.C;
     while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
-        float t16[16], t8[8], t4[4], t2[2];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) t16[i] = (b & 1) ? v[2 * i + 1] : v[2 * i];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) t8[i] = (b & 2) ? t16[2 * i + 1] : t16[2 * i];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) t4[i] = (b & 4) ? t8[2 * i + 1] : t8[2 * i];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) t2[i] = (b & 8) ? t4[2 * i + 1] : t4[2 * i];
-        I.keys[row + cnt] = (b & 16) ? t2[1] : t2[0];
+        I.keys[row + cnt] = row_s[b];
         I.idx[row + cnt] = (int32_t)(n0 + b);
         ++cnt;
     }
@@ -765,7 +760,8 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;                                          // NKB x 16 KB
     uint8_t* sB = smem + NKB * A_KBLK_BYTES;                     // STAGES x NKB x BN rows
-    uint32_t* hist = (uint32_t*)(sB + STAGES * NKB * B_KBLK_BYTES);   // 4 warps x 256
+    float* sRow = (float*)(sB + STAGES * NKB * B_KBLK_BYTES);         // 128 threads x ROW_LD
+    uint32_t* hist = (uint32_t*)(sRow + 128 * ROW_LD);                  // 4 warps x 256
     uint64_t* bars = (uint64_t*)(hist + 4 * 256);
     uint64_t* full = bars;                  // [STAGES]
     uint64_t* empty = bars + STAGES;        // [STAGES]
@@ -952,7 +948,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                         float v[32];
 #pragma unroll
                         for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-                        epilogue_chunk(R, v, nbase + c * 32, j, thr, cnt);
+                        epilogue_chunk(R, v, nbase + c * 32, j, thr, cnt, sRow + (threadIdx.x - 64) * ROW_LD);
                     }
                 }
                 ptx::tc_fence_before();
@@ -1360,7 +1356,7 @@ constexpr int stages_for(int nkb, int bn) {
 
 size_t tc_smem_bytes(int nkb, int bn) {
     const int S = stages_for(nkb, bn);
-    return 1024 + (size_t)nkb * A_KBLK_BYTES + (size_t)S * nkb * bn * KBLK * 2 + 4 * 256 * 4 +
+    return 1024 + (size_t)nkb * A_KBLK_BYTES + (size_t)S * nkb * bn * KBLK * 2 + 128 * ROW_LD * 4 + 4 * 256 * 4 +
            (2 * S + 14) * 8;
 }
 
