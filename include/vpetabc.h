@@ -312,7 +312,9 @@ int abc_summarize(const float* theta_dev, int32_t ldtheta, const int64_t* model_
 size_t abc_mlp_param_count(int32_t D, int32_t H, int32_t O);
 
 /* Bytes of device workspace abc_mlp_forward / abc_mlp_loss_grad need for a
- * batch of B rows (0 on bad sizes). */
+ * batch of B rows (0 on bad sizes): the activations and their gradients, and
+ * a fixed slab area where the weight-gradient GEMMs keep per-slice partial
+ * sums that are added in a fixed order (gradients are bitwise reproducible). */
 size_t abc_mlp_workspace_size(int32_t D, int32_t H, int32_t O, int64_t B);
 
 /* Weights uniform in +-1/sqrt(fan_in) from Philox4x32-10 (counter = parameter
@@ -377,7 +379,9 @@ size_t abc_local_abc_smem_bytes(int32_t T, int32_t L, int32_t M);
  * where table_dev (T x L) holds G(a_i) = frame means of e^{-a_i t} (*) C_p at
  * a_i = a_max (i / (T - 1))^2 (row 0 = frame means of 1 (*) C_p) and
  * cp_frames_dev the L frame means of C_p, read by cubic Lagrange interpolation
- * in i; d_ji = sum_l w_l (y_jl - x_l)^2; the k nearest kept (ties to the lower
+ * in i; d_ji = sum_l w_l (y_jl - x_l)^2, evaluated as y.y - 2 y.x + x.x from
+ * weighted dot products of y, cp, G(0) and the table rows (interpolated alike);
+ * the k nearest kept (ties to the lower
  * proposal index); weights W = (1/q(u)) normalised over the accepted set
  * (uniform prior).  Outputs (J x 5, columns K1, k2, k3, Vb, K_i = K1 k3/(k2+k3)):
  * weighted mean, weighted SD sqrt(sum W (v - m)^2), and weighted 2.5 / 97.5 %

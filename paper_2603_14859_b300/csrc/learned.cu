@@ -18,7 +18,9 @@
 //    a = k2 + k3, so every frame mean is a fixed combination of G(0), G(a) and
 //    the frame mean of C_p, G(a) = frame mean of e^{-a t} (*) C_p.  G is
 //    tabulated once per scan (with abc_simulate) on a_i = a_max (i / (T-1))^2
-//    and read back by the cubic Lagrange interpolant through four nodes.
+//    and read back by the cubic Lagrange interpolant through four nodes; the
+//    distance is evaluated as y.y - 2 y.x + x.x from weighted dot products of
+//    y, C_p, G(0) and G(a_i), tabulated and interpolated the same way.
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -76,8 +78,9 @@ __global__ void k_features(const float* __restrict__ y, int64_t J, int ldy, int 
 // ------------------------------------------------------------------ GEMM
 // C[m, n] = sum_k A(m, k) B(k, n) (+ bias[n]), A(m, k) = gelu?(A[m sam + k sak]),
 // B(k, n) = gelu?/bf16?(B[k sbk + n sbn]).  64 x 64 tiles, 256 threads, 4 x 4
-// outputs per thread.  With split-K (gridDim.z > 1) each z-slice adds its
-// partial sum atomically into a zeroed C.
+// outputs per thread.  With split-K (gridDim.z > 1) each z-slice stores its
+// partial sums in its own M x N slab and k_splitk_sum adds the slabs in z
+// order, so the result does not depend on the order the blocks finish in.
 struct GemmArgs {
     const float* A;
     int64_t sam, sak;
@@ -90,7 +93,13 @@ struct GemmArgs {
     int actA;    // 1 = GELU of the loaded A value
     int actB;    // 1 = GELU of the loaded B value
     int roundB;  // 1 = B rounded to bf16 (weights)
+    float* part = nullptr;     // split-K slabs (null: no split)
+    int64_t part_cap = 0;      // floats available there
 };
+
+// floats of split-K slab space in the training workspace: enough for about
+// three waves of 64 x 64 tiles on up to 192 SMs
+constexpr int64_t GEMM_PART_FLOATS = 3LL * 192 * GT * GT;
 
 __global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int kchunk) {
     __shared__ float sa[GK][GT + 4];
@@ -146,12 +155,27 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int kchunk) {
             const int n = n0 + tx * 4 + q;
             if (n >= g.N) continue;
             float v = acc[i][q];
-            if (g.bias && blockIdx.z == 0) v += g.bias[n];
-            float* c = g.C + (int64_t)m * g.ldc + n;
-            if (gridDim.z > 1) atomicAdd(c, v);
-            else *c = v;
+            if (gridDim.z > 1) {
+                g.part[((int64_t)blockIdx.z * g.M + m) * g.N + n] = v;
+            } else {
+                if (g.bias) v += g.bias[n];
+                g.C[(int64_t)m * g.ldc + n] = v;
+            }
         }
     }
+}
+
+// C[m, n] = sum_z part[z, m, n] (+ bias[n]), z ascending
+__global__ void k_splitk_sum(const float* __restrict__ part, int split, int M, int N, const float* __restrict__ bias,
+                             float* __restrict__ C, int64_t ldc) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t MN = (int64_t)M * N;
+    if (e >= MN) return;
+    const int m = (int)(e / N), n = (int)(e - (int64_t)m * N);
+    float v = 0.0f;
+    for (int z = 0; z < split; ++z) v += part[z * MN + e];
+    if (bias) v += bias[n];
+    C[(int64_t)m * ldc + n] = v;
 }
 
 int g_sms = 0;
@@ -165,21 +189,25 @@ int gemm(const GemmArgs& a, cudaStream_t s) {
     const int64_t tiles = vpet_ceil_div(a.N, GT) * vpet_ceil_div(a.M, GT);
     // split K when the output has too few tiles to fill the GPU (weight gradients)
     int64_t split = 1;
-    if (tiles < g_sms && a.K >= 8 * GK) {
+    if (a.part && tiles < g_sms && a.K >= 8 * GK) {
         split = vpet_ceil_div(2 * g_sms, tiles);
         const int64_t maxsplit = a.K / (4 * GK);
+        const int64_t capsplit = a.part_cap / ((int64_t)a.M * a.N);
         if (split > maxsplit) split = maxsplit;
+        if (split > capsplit) split = capsplit;
         if (split < 1) split = 1;
     }
     const int kchunk = (int)vpet_round_up(vpet_ceil_div(a.K, split), GK);
     split = vpet_ceil_div(a.K, kchunk);
-    if (split > 1) {
-        VPET_ARG(a.ldc == a.N, "gemm: split-K needs a contiguous output");
-        VPET_CUDA(cudaMemsetAsync(a.C, 0, sizeof(float) * (size_t)a.M * a.N, s));
-    }
     const dim3 grid((unsigned)vpet_ceil_div(a.N, GT), (unsigned)vpet_ceil_div(a.M, GT), (unsigned)split);
     k_gemm<<<grid, 256, 0, s>>>(a, kchunk);
     VPET_LAUNCH_CHECK();
+    if (split > 1) {
+        const int64_t MN = (int64_t)a.M * a.N;
+        k_splitk_sum<<<(unsigned)vpet_ceil_div(MN, 256), 256, 0, s>>>(a.part, (int)split, a.M, a.N, a.bias, a.C,
+                                                                      a.ldc);
+        VPET_LAUNCH_CHECK();
+    }
     return ABC_OK;
 }
 
@@ -361,7 +389,7 @@ struct LocalArgs {
 struct TnParams {         // truncated normal on [0, 1], per voxel and parameter
     float mu, sg, lnorm;  // lnorm = log sigma + log Z + log sqrt(2 pi)
     float pa, pb;         // CDF at the bounds, taken in the tail where it is accurate
-    int upper;            // pa, pb are upper-tail probabilities
+    float sgs;            // sg, negated when pa, pb are upper-tail probabilities
 };
 
 __device__ __forceinline__ TnParams tn_params(float mu_raw, float s_raw, float sigma_scale) {
@@ -371,9 +399,10 @@ __device__ __forceinline__ TnParams tn_params(float mu_raw, float s_raw, float s
     t.sg = expf(s);
     const float a = -t.mu / t.sg, b = (1.0f - t.mu) / t.sg;
     t.lnorm = s + logf(fmaxf(norm_mass(a, b), 1e-30f)) + 0.91893853320467274f;
-    t.upper = a + b > 0.0f;
-    if (t.upper) { t.pa = normcdff(-a); t.pb = normcdff(-b); }
+    const bool upper = a + b > 0.0f;
+    if (upper) { t.pa = normcdff(-a); t.pb = normcdff(-b); }
     else { t.pa = normcdff(a); t.pb = normcdff(b); }
+    t.sgs = upper ? -t.sg : t.sg;
     return t;
 }
 
@@ -382,7 +411,7 @@ __device__ __forceinline__ float tn_draw(const TnParams& t, float u) {
     // pa (1 - u) + pb u: two non-negative terms (1 - u is exact for these uniforms), no cancellation
     const float p = fminf(fmaxf(fmaf(t.pa, 1.0f - u, u * t.pb), 1e-30f), 1.0f - 6e-8f);
     const float zq = normcdfinvf(p);
-    const float v = t.mu + t.sg * (t.upper ? -zq : zq);
+    const float v = fmaf(t.sgs, zq, t.mu);
     return fminf(fmaxf(v, 0.0f), 1.0f);
 }
 
@@ -402,22 +431,29 @@ __device__ __forceinline__ void draw_u(const LocalArgs& A, const TnParams* tp, i
 }
 
 // Block-wide radix select over n fp32 keys in shared memory: the exact key of
-// the given rank (0-based), returned to all threads.
-__device__ uint32_t block_select(const float* keys, int n, int rank, uint32_t* hist, int* sh) {
+// the given rank (0-based), returned to all threads.  *ties_rank receives the
+// rank of that key among the keys equal to it (rank minus the number of keys
+// strictly below it).  Lanes with the same digit add their count once (the
+// keys of one voxel share few leading digits, so per-key atomics would queue
+// on a handful of bins).
+__device__ uint32_t block_select(const float* keys, int n, int rank, uint32_t* hist, int* sh, int* ties_rank) {
     uint32_t prefix = 0;
     int r = rank;
+    const int lane = threadIdx.x & 31;
     for (int lv = 0; lv < 4; ++lv) {
         const int shift = 24 - 8 * lv;
         const uint32_t mask = lv == 0 ? 0u : (0xFFFFFFFFu << (shift + 8));
         for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint32_t k = f2key(keys[i]);
-            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+            const int i = i0 + threadIdx.x;
+            const uint32_t k = i < n ? f2key(keys[i]) : 0u;
+            const uint32_t bin = (i < n && (k & mask) == prefix) ? (k >> shift) & 255u : 256u;
+            const uint32_t same = __match_any_sync(0xFFFFFFFFu, bin);
+            if (bin < 256u && lane == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
         }
         __syncthreads();
         if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
             uint32_t loc[8], sum = 0;
 #pragma unroll
             for (int b = 0; b < 8; ++b) { loc[b] = hist[lane * 8 + b]; sum += loc[b]; }
@@ -445,6 +481,7 @@ __device__ uint32_t block_select(const float* keys, int n, int rank, uint32_t* h
         r = sh[1];
         __syncthreads();
     }
+    if (ties_rank) *ties_rank = r;
     return prefix;
 }
 
@@ -477,22 +514,48 @@ __device__ __forceinline__ float block_max(float v, float* red) {
 // values of all five columns, weighted quantiles.
 __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
     extern __shared__ __align__(16) uint8_t sm[];
-    float* tab = (float*)sm;                              // T x ldt
+    float4* qt = (float4*)sm;                             // T: (y . G(a_i) per voxel, cp . G(a_i), G(0) . G(a_i),
+                                                          //     G(a_i) . G(a_i)), all frame-weighted
+    float* tab = (float*)(qt + A.T);                      // T x ldt
     float* cps = tab + (size_t)A.T * A.ldt;               // MAXL
     float* ys = cps + MAXL;                               // MAXL
-    float* keys = ys + MAXL;                              // M
-    int32_t* acc = (int32_t*)(keys + A.M);                // LA_KMAX accepted proposal indices
+    float* keys = ys + MAXL;                              // max(M, 2 LA_C LA_KMAX): distances, then
+    float* sv = keys;                                     //   LA_C x LA_KMAX values (sorted in place) and
+    float* sw = sv + LA_C * LA_KMAX;                      //   LA_C x LA_KMAX weights once the keys are done
+    const int kreg = A.M > 2 * LA_C * LA_KMAX ? A.M : 2 * LA_C * LA_KMAX;
+    int32_t* acc = (int32_t*)(keys + kreg);               // LA_KMAX accepted proposal indices
     float* wacc = (float*)(acc + LA_KMAX);                // LA_KMAX normalised weights
-    float* sv = wacc + LA_KMAX;                           // LA_C x LA_KMAX values (sorted in place)
-    float* sw = sv + LA_C * LA_KMAX;                      // LA_C x LA_KMAX weights (permuted alongside)
-    float* red = sw + LA_C * LA_KMAX;                     // 64
+    float* red = wacc + LA_KMAX;                          // 64
     uint32_t* hist = (uint32_t*)(red + 64);               // 256
     int* sh = (int*)(hist + 256);                         // 8
     int* wcnt = sh + 8;                                   // 2 x 16 warp counts
+    float* scal = (float*)(wcnt + 32);                    // 8: cp . cp, y . y, y . cp
     __shared__ TnParams tp[LA_P];
 
     for (int e = threadIdx.x; e < A.T * A.L; e += blockDim.x) tab[(e / A.L) * A.ldt + e % A.L] = A.table[e];
     for (int l = threadIdx.x; l < A.L; l += blockDim.x) cps[l] = A.cpf[l];
+    __syncthreads();
+    // With x = alpha cp + beta G(0) + gamma G(a) (alpha = Vb, beta = (1 - Vb) K1 k3 / a,
+    // gamma = (1 - Vb) K1 k2 / a), d = sum_l w_l (y_l - x_l)^2 is a quadratic form in
+    // (alpha, beta, gamma) whose coefficients are weighted dot products of y, cp, G(0) and
+    // G(a).  The ones involving G(a) are tabulated on the a_i grid (per block, and y . G(a_i)
+    // per voxel) and interpolated like G itself (the products are linear in G, or smooth).
+    for (int i = threadIdx.x; i < A.T; i += blockDim.x) {
+        const float* r = tab + (size_t)i * A.ldt;
+        float a = 0.0f, b = 0.0f, c = 0.0f;
+        for (int l = 0; l < A.L; ++l) {
+            const float wr = A.w[l] * r[l];
+            a = fmaf(wr, cps[l], a);
+            b = fmaf(wr, tab[l], b);
+            c = fmaf(wr, r[l], c);
+        }
+        qt[i] = make_float4(0.0f, a, b, c);
+    }
+    if (threadIdx.x == 0) {
+        float cc = 0.0f;
+        for (int l = 0; l < A.L; ++l) cc = fmaf(A.w[l] * cps[l], cps[l], cc);
+        scal[0] = cc;
+    }
     const float scale = (float)(A.T - 1) * rsqrtf(A.a_max);
     const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 
@@ -503,6 +566,24 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
             tp[threadIdx.x] = tn_params(A.prop[j * 2 * LA_P + 2 * threadIdx.x],
                                         A.prop[j * 2 * LA_P + 2 * threadIdx.x + 1], A.sigma_scale);
         __syncthreads();
+        for (int i = threadIdx.x; i < A.T; i += blockDim.x) {
+            const float* r = tab + (size_t)i * A.ldt;
+            float a = 0.0f;
+            for (int l = 0; l < A.L; ++l) a = fmaf(A.w[l] * ys[l], r[l], a);
+            qt[i].x = a;
+        }
+        if (threadIdx.x == 0) {
+            float yy = 0.0f, yc = 0.0f;
+            for (int l = 0; l < A.L; ++l) {
+                yy = fmaf(A.w[l] * ys[l], ys[l], yy);
+                yc = fmaf(A.w[l] * ys[l], cps[l], yc);
+            }
+            scal[1] = yy;
+            scal[2] = yc;
+        }
+        __syncthreads();
+        const float4 q00 = qt[0];
+        const float cc = scal[0], yy = scal[1], yc = scal[2], yg0 = q00.x, cg0 = q00.y, g00 = q00.w;
 
         // proposals, their TACs and distances
         for (int i = threadIdx.x; i < A.M; i += blockDim.x) {
@@ -521,15 +602,18 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
             const float c0 = -t * tm * t2 * (1.0f / 6.0f), c1 = 0.5f * tp1 * tm * t2, c2 = -0.5f * tp1 * t * t2,
                         c3 = tp1 * t * tm * (1.0f / 6.0f);
             const float ca = (1.0f - Vb) * K1 / a;
-            const float* r0 = tab + (size_t)(i0 - 1) * A.ldt;
-            float d = 0.0f;
-            for (int l = 0; l < A.L; ++l) {
-                const float g =
-                    fmaf(c0, r0[l], fmaf(c1, r0[A.ldt + l], fmaf(c2, r0[2 * A.ldt + l], c3 * r0[3 * A.ldt + l])));
-                const float x = fmaf(ca, fmaf(k3, tab[l], k2 * g), Vb * cps[l]);
-                const float e = ys[l] - x;
-                d = fmaf(A.w[l] * e, e, d);
-            }
+            const float al = Vb, be = ca * k3, ga = ca * k2;
+            const int b0 = i0 - 1;
+            const float4 q0 = qt[b0], q1 = qt[b0 + 1], q2 = qt[b0 + 2], q3 = qt[b0 + 3];
+            const float yg = fmaf(c0, q0.x, fmaf(c1, q1.x, fmaf(c2, q2.x, c3 * q3.x)));
+            const float cg = fmaf(c0, q0.y, fmaf(c1, q1.y, fmaf(c2, q2.y, c3 * q3.y)));
+            const float g0g = fmaf(c0, q0.z, fmaf(c1, q1.z, fmaf(c2, q2.z, c3 * q3.z)));
+            const float gg = fmaf(c0, q0.w, fmaf(c1, q1.w, fmaf(c2, q2.w, c3 * q3.w)));
+            // d = y.y - 2 y.x + x.x
+            const float yx = fmaf(al, yc, fmaf(be, yg0, ga * yg));
+            const float xx = fmaf(al * al, cc, fmaf(be * be, g00, fmaf(ga * ga, gg,
+                             2.0f * fmaf(al * be, cg0, fmaf(al * ga, cg, be * ga * g0g)))));
+            const float d = fmaf(-2.0f, yx, yy) + xx;
             keys[i] = d;
             if (A.u_dump) {
 #pragma unroll
@@ -540,36 +624,50 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
         __syncthreads();
 
         // accepted set: every key below the k-th, then the lowest-index keys equal to it
-        const uint32_t K = block_select(keys, A.M, A.k - 1, hist, sh);
-        int nless = 0;
-        for (int i = threadIdx.x; i < A.M; i += blockDim.x) nless += f2key(keys[i]) < K;
-        const int n_less = (int)(block_sum((float)nless, red) + 0.5f);
-        const int need_ties = A.k - n_less;
-        int base_less = 0, base_tie = 0;
-        for (int c0 = 0; c0 < A.M; c0 += blockDim.x) {
-            const int i = c0 + threadIdx.x;
-            const uint32_t kk = i < A.M ? f2key(keys[i]) : 0xFFFFFFFFu;
-            const bool isl = i < A.M && kk < K, ist = i < A.M && kk == K;
-            const uint32_t bl = __ballot_sync(0xFFFFFFFFu, isl), bt = __ballot_sync(0xFFFFFFFFu, ist);
-            __syncthreads();
-            if (lane == 0) { wcnt[wp] = __popc(bl); wcnt[16 + wp] = __popc(bt); }
-            __syncthreads();
-            int pl = base_less, pt = base_tie, tl = 0, tt = 0;
-            for (int q = 0; q < nw; ++q) {
-                if (q < wp) { pl += wcnt[q]; pt += wcnt[16 + q]; }
-                tl += wcnt[q];
-                tt += wcnt[16 + q];
+        int tie_rank = 0;
+        const uint32_t K = block_select(keys, A.M, A.k - 1, hist, sh, &tie_rank);
+        const int need_ties = tie_rank + 1;   // k minus the number of keys strictly below K
+        // Ordered compaction: warp w scans the contiguous index segment [s0, s1), so the
+        // accepted indices come out in increasing order with one block barrier: a counting
+        // pass per warp, the warps' exclusive prefix, then a placing pass.
+        {
+            const int seg = (A.M + nw - 1) / nw;
+            const int s0 = min(A.M, wp * seg), s1 = min(A.M, s0 + seg);
+            int cl = 0, ct = 0;
+            for (int i0 = s0; i0 < s1; i0 += 32) {
+                const int i = i0 + lane;
+                const uint32_t kk = i < s1 ? f2key(keys[i]) : 0u;
+                cl += __popc(__ballot_sync(0xFFFFFFFFu, i < s1 && kk < K));
+                ct += __popc(__ballot_sync(0xFFFFFFFFu, i < s1 && kk == K));
             }
+            if (lane == 0) { wcnt[wp] = cl; wcnt[16 + wp] = ct; }
+            __syncthreads();
+            int pl0 = 0, pt0 = 0;
+            for (int q = 0; q < wp; ++q) { pl0 += wcnt[q]; pt0 += wcnt[16 + q]; }
             const uint32_t below = (1u << lane) - 1u;
-            pl += __popc(bl & below);
-            pt += __popc(bt & below);
-            if (isl) acc[pl + min(pt, need_ties)] = i;
-            else if (ist && pt < need_ties) acc[pl + pt] = i;
-            base_less += tl;
-            base_tie += tt;
+            for (int i0 = s0; i0 < s1; i0 += 32) {
+                const int i = i0 + lane;
+                const uint32_t kk = i < s1 ? f2key(keys[i]) : 0u;
+                const bool isl = i < s1 && kk < K, ist = i < s1 && kk == K;
+                const uint32_t bl = __ballot_sync(0xFFFFFFFFu, isl), bt = __ballot_sync(0xFFFFFFFFu, ist);
+                const int pl = pl0 + __popc(bl & below), pt = pt0 + __popc(bt & below);
+                if (isl) acc[pl + min(pt, need_ties)] = i;
+                else if (ist && pt < need_ties) acc[pl + pt] = i;
+                pl0 += __popc(bl);
+                pt0 += __popc(bt);
+            }
         }
         __syncthreads();
 
+        // median accepted distance: the ((k - 1) / 2)-th smallest key, selected among the k
+        // accepted keys (gathered into the weights' space before the keys' space is reused)
+        if (threadIdx.x < A.k) wacc[threadIdx.x] = keys[acc[threadIdx.x]];
+        __syncthreads();
+        {
+            const uint32_t Km = block_select(wacc, A.k, (A.k - 1) / 2, hist, sh, nullptr);
+            if (threadIdx.x == 0) A.dmed[j] = key2f(Km);
+        }
+        __syncthreads();
         // weights 1/q, normalised over the accepted set; accepted values
         float lw = -3.0e38f;
         float vals[LA_C] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -597,31 +695,30 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
                 sw[c * LA_KMAX + threadIdx.x] = W;
             }
         }
-        // weighted mean and SD per column (fp64 sums over the k accepted)
+        // weighted mean and SD per column: per-lane partial sums over the k accepted, then a
+        // shuffle tree (two passes, so the spread is summed about the mean)
         __syncthreads();
         if (wp < LA_C) {
             const int c = wp;
-            double m = 0.0;
-            for (int r = lane; r < A.k; r += 32) m += (double)wacc[r] * sv[c * LA_KMAX + r];
+            float m = 0.0f;
+            for (int r = lane; r < A.k; r += 32) m = fmaf(wacc[r], sv[c * LA_KMAX + r], m);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xFFFFFFFFu, m, o);
-            double v2 = 0.0;
+            float v2 = 0.0f;
             for (int r = lane; r < A.k; r += 32) {
-                const double e = (double)sv[c * LA_KMAX + r] - m;
-                v2 += (double)wacc[r] * e * e;
+                const float e = sv[c * LA_KMAX + r] - m;
+                v2 = fmaf(wacc[r] * e, e, v2);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xFFFFFFFFu, v2, o);
             if (lane == 0) {
-                A.mean[j * LA_C + c] = (float)m;
-                A.sd[j * LA_C + c] = (float)sqrt(v2);
+                A.mean[j * LA_C + c] = m;
+                A.sd[j * LA_C + c] = sqrtf(v2);
             }
         }
         if (threadIdx.x == 0) {
             A.ess[j] = 1.0f / s2;
-            float yn = 0.0f;
-            for (int l = 0; l < A.L; ++l) yn = fmaf(A.w[l] * ys[l], ys[l], yn);
-            A.ynorm[j] = yn;
+            A.ynorm[j] = yy;
         }
         // bitonic sort of the five 256-entry columns by value, weights alongside
         for (int size = 2; size <= LA_KMAX; size <<= 1) {
@@ -681,9 +778,6 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
                 A.qhi[j * LA_C + c] = v[min(fh, A.k - 1)];
             }
         }
-        // median accepted distance: the ((k - 1) / 2)-th smallest key
-        const uint32_t Km = block_select(keys, A.M, (A.k - 1) / 2, hist, sh);
-        if (threadIdx.x == 0) A.dmed[j] = key2f(Km);
     }
 }
 
@@ -719,8 +813,8 @@ extern "C" size_t abc_mlp_param_count(int32_t D, int32_t H, int32_t O) {
 
 extern "C" size_t abc_mlp_workspace_size(int32_t D, int32_t H, int32_t O, int64_t B) {
     if (D < 1 || H < 1 || O < 1 || B < 1) return 0;
-    // z1, z2, dh, dz (B x H each), out, dout (B x O each)
-    return sizeof(float) * ((size_t)B * H * 4 + (size_t)B * O * 2) + 256;
+    // z1, z2, dh, dz (B x H each), out, dout (B x O each), split-K slabs
+    return sizeof(float) * ((size_t)B * H * 4 + (size_t)B * O * 2 + (size_t)GEMM_PART_FLOATS) + 256;
 }
 
 extern "C" int abc_mlp_init(uint64_t seed, int32_t D, int32_t H, int32_t O, float* params_dev, void* stream) {
@@ -786,6 +880,7 @@ extern "C" int abc_mlp_loss_grad(const float* params_dev, int32_t D, int32_t H, 
     float* dz = dh + (size_t)B * H;
     float* out = dz + (size_t)B * H;
     float* dout = out + (size_t)B * O;
+    float* part = dout + (size_t)B * O;
     if ((rc = mlp_forward(params_dev, D, H, O, X_dev, B, out, z1, z2, s))) return rc;
     VPET_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(float), s));
     k_trunc_nll<<<(unsigned)vpet_ceil_div(B * P, 256), 256, 0, s>>>(out, T_dev, (int)B, P, dout, loss_dev);
@@ -800,21 +895,21 @@ extern "C" int abc_mlp_loss_grad(const float* params_dev, int32_t D, int32_t H, 
     float* gb3 = gW3 + (size_t)O * H;
     const int Bi = (int)B;
     // layer 3: gW3 = dout^T gelu(z2), gb3 = colsum(dout), dh = dout bf16(W3)
-    if ((rc = gemm(GemmArgs{dout, 1, O, z2, H, 1, gW3, H, nullptr, O, H, Bi, 0, 1, 0}, s))) return rc;
+    if ((rc = gemm(GemmArgs{dout, 1, O, z2, H, 1, gW3, H, nullptr, O, H, Bi, 0, 1, 0, part, GEMM_PART_FLOATS}, s))) return rc;
     k_colsum<<<(unsigned)vpet_ceil_div(O, 32), 256, 0, s>>>(dout, Bi, O, gb3);
     VPET_LAUNCH_CHECK();
     if ((rc = gemm(GemmArgs{dout, O, 1, W3, H, 1, dh, H, nullptr, Bi, H, O, 0, 0, 1}, s))) return rc;
     // layer 2: dz = dh gelu'(z2), gW2 = dz^T gelu(z1), gb2 = colsum(dz), dh = dz bf16(W2)
     k_gelu_back<<<(unsigned)vpet_ceil_div(B * H, 256), 256, 0, s>>>(dh, z2, dz, B * H);
     VPET_LAUNCH_CHECK();
-    if ((rc = gemm(GemmArgs{dz, 1, H, z1, H, 1, gW2, H, nullptr, H, H, Bi, 0, 1, 0}, s))) return rc;
+    if ((rc = gemm(GemmArgs{dz, 1, H, z1, H, 1, gW2, H, nullptr, H, H, Bi, 0, 1, 0, part, GEMM_PART_FLOATS}, s))) return rc;
     k_colsum<<<(unsigned)vpet_ceil_div(H, 32), 256, 0, s>>>(dz, Bi, H, gb2);
     VPET_LAUNCH_CHECK();
     if ((rc = gemm(GemmArgs{dz, H, 1, W2, H, 1, dh, H, nullptr, Bi, H, H, 0, 0, 1}, s))) return rc;
     // layer 1: dz = dh gelu'(z1), gW1 = dz^T X, gb1 = colsum(dz)
     k_gelu_back<<<(unsigned)vpet_ceil_div(B * H, 256), 256, 0, s>>>(dh, z1, dz, B * H);
     VPET_LAUNCH_CHECK();
-    if ((rc = gemm(GemmArgs{dz, 1, H, X_dev, D, 1, gW1, D, nullptr, H, D, Bi, 0, 0, 0}, s))) return rc;
+    if ((rc = gemm(GemmArgs{dz, 1, H, X_dev, D, 1, gW1, D, nullptr, H, D, Bi, 0, 0, 0, part, GEMM_PART_FLOATS}, s))) return rc;
     k_colsum<<<(unsigned)vpet_ceil_div(H, 32), 256, 0, s>>>(dz, Bi, H, gb1);
     VPET_LAUNCH_CHECK();
     return ABC_OK;
@@ -880,8 +975,8 @@ extern "C" int abc_add_noise(const float* x_dev, int64_t N, int32_t ldx, const a
 extern "C" size_t abc_local_abc_smem_bytes(int32_t T, int32_t L, int32_t M) {
     if (T < 1 || L < 1 || M < 1) return 0;
     const size_t ldt = (size_t)(L | 1);
-    return sizeof(float) * ((size_t)T * ldt + 2 * MAXL + (size_t)M + 2 * LA_KMAX + 2 * LA_C * LA_KMAX + 64 + 256 +
-                            8 + 32);
+    const size_t kreg = (size_t)M > 2 * LA_C * LA_KMAX ? (size_t)M : 2 * LA_C * LA_KMAX;
+    return sizeof(float) * ((size_t)T * ldt + 2 * MAXL + kreg + 2 * LA_KMAX + 64 + 256 + 8 + 32 + 4 * (size_t)T + 8);
 }
 
 extern "C" int abc_local_abc(const float* y_dev, int64_t J, int32_t ldy, int32_t L, const float* w_host,

@@ -262,6 +262,20 @@ def test_local_abc_edge_cases(c3_small):
     assert np.allclose(tie["ess"].cpu().numpy(), 50, rtol=1e-4)
 
 
+def test_training_is_bitwise_reproducible(c3_small):
+    """Two trainings from the same seeds end with identical parameters (the
+    weight-gradient GEMMs add their split-K partial sums in a fixed order)."""
+    from paper_2603_14859_b300 import synth as S
+    from paper_2603_14859_b300.learned import LearnedLocalAbc
+    W = c3_small[0]
+    ps = []
+    for _ in range(2):
+        model = LearnedLocalAbc(W.ts, W.te, W.input_for(S.TCM2_IRR), W.half_life, q_lo=0.1, q_hi=0.1)
+        model.train(n_pairs=8192 * 40, batch=8192, log_every=0)
+        ps.append(model.params.clone())
+    assert torch.equal(ps[0], ps[1])
+
+
 def test_learned_proposal_beats_prior_proposal(c3_small):
     """At the same draw budget per voxel, proposals from the trained network give
     posterior means much closer to the truth than prior-like proposals; the
@@ -270,8 +284,8 @@ def test_learned_proposal_beats_prior_proposal(c3_small):
     from paper_2603_14859_b300.learned import GlobalIrr, LearnedLocalAbc, run_learned
     W, y, irr, truth = c3_small
     model = LearnedLocalAbc(W.ts, W.te, W.input_for(S.TCM2_IRR), W.half_life, q_lo=0.1, q_hi=0.1)
-    log = model.train(n_pairs=10_000_000, batch=8192)
-    first, last = log.losses[0][1], log.losses[-1][1]
+    log = model.train(n_pairs=10_000_000, batch=8192, log_every=20)
+    first, last = log.losses[0][1], float(np.mean([l for _, l in log.losses[-5:]]))
     assert last < first - 3.0, log.losses
     rows = irr[:1024]
     yj = y[torch.from_numpy(rows).cuda()].contiguous()
