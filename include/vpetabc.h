@@ -366,6 +366,12 @@ int abc_add_noise(const float* x_dev, int64_t N, int32_t ldx, const abc_frames* 
 /* Shared memory abc_local_abc needs per block (it must stay <= 227 KB). */
 size_t abc_local_abc_smem_bytes(int32_t T, int32_t L, int32_t M);
 
+/* The G table in the layout abc_local_abc reads: table_dev[l * T + i] =
+ * rows_dev[i * ld + l] for the T rows (one per grid node a_i, L frames each,
+ * row stride ld >= L) that abc_simulate writes.  table_dev: L x T floats,
+ * caller-owned.  ABC_ERR_ARG on bad sizes or null pointers. */
+int abc_local_abc_table(const float* rows_dev, int32_t T, int32_t L, int32_t ld, float* table_dev, void* stream);
+
 /* Importance-weighted local ABC for the irreversible 2TCM, P = 4 parameters
  * (K1, k2, k3, Vb) on the prior box [lo, hi] (host, 4 entries each, lo >= 0).
  * For each voxel j: M proposals u_i ~ TN(mu_jp, sigma_jp) on [0, 1] per
@@ -376,13 +382,16 @@ size_t abc_local_abc_smem_bytes(int32_t T, int32_t L, int32_t M);
  * (i, j lo, j hi, 0x4C4F43) and key (seed lo, seed hi); theta = lo + (hi - lo) u; the TAC
  * of each proposal from
  *   x_l = Vb cp_l + (1 - Vb) K1 / a (k3 G_l(0) + k2 G_l(a)),  a = k2 + k3,
- * where table_dev (T x L) holds G(a_i) = frame means of e^{-a_i t} (*) C_p at
- * a_i = a_max (i / (T - 1))^2 (row 0 = frame means of 1 (*) C_p) and
+ * where table_dev (L x T, frame-major: table_dev[l * T + i], see
+ * abc_local_abc_table) holds G(a_i) = frame means of e^{-a_i t} (*) C_p at
+ * a_i = a_max (i / (T - 1))^2 (column 0 = frame means of 1 (*) C_p) and
  * cp_frames_dev the L frame means of C_p, read by cubic Lagrange interpolation
  * in i; d_ji = sum_l w_l (y_jl - x_l)^2, evaluated as y.y - 2 y.x + x.x from
  * weighted dot products of y, cp, G(0) and the table rows (interpolated alike);
  * the k nearest kept (ties to the lower
- * proposal index); weights W = (1/q(u)) normalised over the accepted set
+ * proposal index; the k-th distance is found exactly, by radix selection over
+ * the candidates a pilot sample of the first proposals brackets, or over all
+ * M distances when the bracket misses); weights W = (1/q(u)) normalised over the accepted set
  * (uniform prior).  Outputs (J x 5, columns K1, k2, k3, Vb, K_i = K1 k3/(k2+k3)):
  * weighted mean, weighted SD sqrt(sum W (v - m)^2), and weighted 2.5 / 97.5 %
  * quantiles (the smallest accepted value whose cumulative weight reaches the

@@ -281,11 +281,20 @@ def local_abc_smem_bytes(T, L, M):
     return lib().abc_local_abc_smem_bytes(T, L, M)
 
 
+def local_abc_table(rows, stream=None):
+    """The G table in the layout abc_local_abc reads: (T, L) rows -> (L, T) frame-major."""
+    T, L = rows.shape
+    out = torch.empty((L, T), device="cuda", dtype=torch.float32)
+    check(lib().abc_local_abc_table(_ptr(rows), T, L, rows.stride(0), _ptr(out), _stream(stream)))
+    return out
+
+
 def local_abc(y, L, w, prop, table, a_max, cp_frames, lo, hi, M, k, seed, sigma_scale=1.0, dump=False, out=None,
               stream=None):
-    """Importance-weighted local ABC (2TCM-irr) -> dict of device tensors."""
+    """Importance-weighted local ABC (2TCM-irr) -> dict of device tensors; table is
+    the frame-major (L, T) G table from local_abc_table."""
     J = y.shape[0]
-    T = table.shape[0]
+    T = table.shape[1]
     w = _np(w, np.float32)
     lo = _np(lo, np.float64)
     hi = _np(hi, np.float64)

@@ -38,6 +38,8 @@ constexpr int LA_THREADS = 512;
 constexpr int LA_P = 4;         // K1, k2, k3, Vb
 constexpr int LA_C = LA_P + 1;  // ... and K_i
 constexpr int LA_KMAX = 256;
+constexpr int LA_CAP = 1024;    // bracketed candidates kept for exact selection
+constexpr int LA_PILOT = 1024;  // pilot sample that brackets the k-th distance
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_d(float z) {
@@ -367,9 +369,10 @@ struct LocalArgs {
     int ldy, L;
     float w[MAXL];
     const float* prop;     // J x 2P network outputs (mu, log sigma) per parameter
-    const float* table;    // T x L: row i = G(a_i); row 0 = G(0) = frame means of 1 (*) C_p
+    const float* table;    // L x T, frame-major: column i = G(a_i); column 0 = G(0) = frame means of 1 (*) C_p
     const float* cpf;      // L frame means of C_p
-    int T, ldt;            // ldt: table row stride in shared memory (odd)
+    int T;
+    int n_pilot, r_lo, r_hi;  // pilot sample size (0: no bracketing) and the ranks of its two pivots
     float a_max;
     float lo[LA_P], hi[LA_P];
     int M, k;
@@ -430,59 +433,71 @@ __device__ __forceinline__ void draw_u(const LocalArgs& A, const TnParams* tp, i
     u[3] = tn_draw(tp[3], u01(r.w));
 }
 
-// Block-wide radix select over n fp32 keys in shared memory: the exact key of
-// the given rank (0-based), returned to all threads.  *ties_rank receives the
-// rank of that key among the keys equal to it (rank minus the number of keys
-// strictly below it).  Lanes with the same digit add their count once (the
-// keys of one voxel share few leading digits, so per-key atomics would queue
-// on a handful of bins).
-__device__ uint32_t block_select(const float* keys, int n, int rank, uint32_t* hist, int* sh, int* ties_rank) {
-    uint32_t prefix = 0;
-    int r = rank;
-    const int lane = threadIdx.x & 31;
+// One warp: the bin of hist[256] that holds the key of rank r (0-based) and that
+// key's rank within the bin.
+__device__ __forceinline__ void warp_find_bin(const uint32_t* hist, int r, int lane, int* bin_out, int* r_out) {
+    uint32_t loc[8], sum = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) { loc[b] = hist[lane * 8 + b]; sum += loc[b]; }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    uint32_t c = incl - sum;
+    int found = -1, newr = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if (found < 0 && c + loc[b] > (uint32_t)r) { found = lane * 8 + b; newr = r - (int)c; }
+        c += loc[b];
+    }
+    const uint32_t who = __ballot_sync(0xFFFFFFFFu, found >= 0);
+    const int src = who ? __ffs(who) - 1 : 31;
+    const int bin = __shfl_sync(0xFFFFFFFFu, found, src);
+    const int nr = __shfl_sync(0xFFFFFFFFu, newr, src);
+    if (lane == 0) { *bin_out = bin < 0 ? 255 : bin; *r_out = nr; }
+}
+
+// Block-wide radix select (8-bit digits, most significant first) of two ranks at
+// once over n fp32 keys in shared memory: out[q] = the exact key of rank rank[q]
+// (0-based), ties[q] = its rank among the keys equal to it (rank minus the
+// number of keys strictly below).  Lanes with the same digit add their count
+// once (the keys of one voxel share few leading digits, so per-key atomics
+// would queue on a handful of bins).  h holds 2 x 256 counters.
+__device__ void block_select2(const float* keys, int n, int rank0, int rank1, uint32_t* h, int* sh, uint32_t* out,
+                              int* ties) {
+    uint32_t p0 = 0, p1 = 0;
+    int r0 = rank0, r1 = rank1;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     for (int lv = 0; lv < 4; ++lv) {
         const int shift = 24 - 8 * lv;
         const uint32_t mask = lv == 0 ? 0u : (0xFFFFFFFFu << (shift + 8));
-        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+        for (int b = threadIdx.x; b < 512; b += blockDim.x) h[b] = 0;
         __syncthreads();
         for (int i0 = 0; i0 < n; i0 += blockDim.x) {
             const int i = i0 + threadIdx.x;
             const uint32_t k = i < n ? f2key(keys[i]) : 0u;
-            const uint32_t bin = (i < n && (k & mask) == prefix) ? (k >> shift) & 255u : 256u;
-            const uint32_t same = __match_any_sync(0xFFFFFFFFu, bin);
-            if (bin < 256u && lane == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
+            const uint32_t d = (k >> shift) & 255u;
+            const uint32_t b0 = (i < n && (k & mask) == p0) ? d : 256u;
+            const uint32_t b1 = (i < n && (k & mask) == p1) ? d : 256u;
+            const uint32_t s0 = __match_any_sync(0xFFFFFFFFu, b0);
+            if (b0 < 256u && lane == __ffs(s0) - 1) atomicAdd(&h[b0], (uint32_t)__popc(s0));
+            const uint32_t s1 = __match_any_sync(0xFFFFFFFFu, b1);
+            if (b1 < 256u && lane == __ffs(s1) - 1) atomicAdd(&h[256 + b1], (uint32_t)__popc(s1));
         }
         __syncthreads();
-        if (threadIdx.x < 32) {
-            uint32_t loc[8], sum = 0;
-#pragma unroll
-            for (int b = 0; b < 8; ++b) { loc[b] = hist[lane * 8 + b]; sum += loc[b]; }
-            uint32_t incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            uint32_t c = incl - sum;
-            int found = -1, newr = 0;
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                if (found < 0 && c + loc[b] > (uint32_t)r) { found = lane * 8 + b; newr = r - (int)c; }
-                c += loc[b];
-            }
-            const uint32_t who = __ballot_sync(0xFFFFFFFFu, found >= 0);
-            const int src = who ? __ffs(who) - 1 : 31;
-            const int bin = __shfl_sync(0xFFFFFFFFu, found, src);
-            const int nr = __shfl_sync(0xFFFFFFFFu, newr, src);
-            if (lane == 0) { sh[0] = bin < 0 ? 255 : bin; sh[1] = nr; }
-        }
+        if (wp < 2) warp_find_bin(h + 256 * wp, wp ? r1 : r0, lane, &sh[2 * wp], &sh[2 * wp + 1]);
         __syncthreads();
-        prefix |= (uint32_t)sh[0] << shift;
-        r = sh[1];
+        p0 |= (uint32_t)sh[0] << shift;
+        r0 = sh[1];
+        p1 |= (uint32_t)sh[2] << shift;
+        r1 = sh[3];
         __syncthreads();
     }
-    if (ties_rank) *ties_rank = r;
-    return prefix;
+    out[0] = p0;
+    out[1] = p1;
+    if (ties) { ties[0] = r0; ties[1] = r1; }
 }
 
 __device__ __forceinline__ float block_sum(float v, float* red) {
@@ -507,32 +522,34 @@ __device__ __forceinline__ float block_max(float v, float* red) {
     return t;
 }
 
-// Persistent blocks over voxels; the G table stays in shared memory for the
-// block's lifetime.  Per voxel: M proposals and distances, exact k-th distance
-// by radix select, ordered compaction of the accepted set (ties at the k-th
-// distance to the lower proposal index), weights, bitonic sort of the accepted
-// values of all five columns, weighted quantiles.
+// Persistent blocks over voxels.  Per voxel: M proposals and their distances (a
+// quadratic form in three TAC coefficients over tabulated dot products), the
+// exact k-th distance (a pilot sample brackets it; exact selection runs over
+// the bracketed candidates, or over all keys when the bracket misses), ordered
+// compaction of the accepted set (ties at the k-th distance to the lower
+// proposal index), importance weights, weighted moments and weighted
+// quantiles (bisection on the value order, one warp per column).
 __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
     extern __shared__ __align__(16) uint8_t sm[];
     float4* qt = (float4*)sm;                             // T: (y . G(a_i) per voxel, cp . G(a_i), G(0) . G(a_i),
                                                           //     G(a_i) . G(a_i)), all frame-weighted
-    float* tab = (float*)(qt + A.T);                      // T x ldt
-    float* cps = tab + (size_t)A.T * A.ldt;               // MAXL
+    float* cps = (float*)(qt + A.T);                      // MAXL
     float* ys = cps + MAXL;                               // MAXL
-    float* keys = ys + MAXL;                              // max(M, 2 LA_C LA_KMAX): distances, then
-    float* sv = keys;                                     //   LA_C x LA_KMAX values (sorted in place) and
-    float* sw = sv + LA_C * LA_KMAX;                      //   LA_C x LA_KMAX weights once the keys are done
-    const int kreg = A.M > 2 * LA_C * LA_KMAX ? A.M : 2 * LA_C * LA_KMAX;
+    float* keys = ys + MAXL;                              // max(M, LA_C LA_KMAX): distances, then the
+    float* sv = keys;                                     //   LA_C x LA_KMAX accepted values
+    const int kreg = A.M > LA_C * LA_KMAX ? A.M : LA_C * LA_KMAX;
     int32_t* acc = (int32_t*)(keys + kreg);               // LA_KMAX accepted proposal indices
     float* wacc = (float*)(acc + LA_KMAX);                // LA_KMAX normalised weights
     float* red = wacc + LA_KMAX;                          // 64
-    uint32_t* hist = (uint32_t*)(red + 64);               // 256
-    int* sh = (int*)(hist + 256);                         // 8
+    uint32_t* hist = (uint32_t*)(red + 64);               // 2 x 256
+    int* sh = (int*)(hist + 512);                         // 8
     int* wcnt = sh + 8;                                   // 2 x 16 warp counts
     float* scal = (float*)(wcnt + 32);                    // 8: cp . cp, y . y, y . cp
+    float* ckey = scal + 8;                               // LA_CAP candidate keys
+    int32_t* cidx = (int32_t*)(ckey + LA_CAP);            // LA_CAP candidate proposal indices
     __shared__ TnParams tp[LA_P];
+    const float* G = A.table;                             // L x T, frame-major
 
-    for (int e = threadIdx.x; e < A.T * A.L; e += blockDim.x) tab[(e / A.L) * A.ldt + e % A.L] = A.table[e];
     for (int l = threadIdx.x; l < A.L; l += blockDim.x) cps[l] = A.cpf[l];
     __syncthreads();
     // With x = alpha cp + beta G(0) + gamma G(a) (alpha = Vb, beta = (1 - Vb) K1 k3 / a,
@@ -541,13 +558,13 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
     // G(a).  The ones involving G(a) are tabulated on the a_i grid (per block, and y . G(a_i)
     // per voxel) and interpolated like G itself (the products are linear in G, or smooth).
     for (int i = threadIdx.x; i < A.T; i += blockDim.x) {
-        const float* r = tab + (size_t)i * A.ldt;
         float a = 0.0f, b = 0.0f, c = 0.0f;
         for (int l = 0; l < A.L; ++l) {
-            const float wr = A.w[l] * r[l];
+            const float g = G[(size_t)l * A.T + i];
+            const float wr = A.w[l] * g;
             a = fmaf(wr, cps[l], a);
-            b = fmaf(wr, tab[l], b);
-            c = fmaf(wr, r[l], c);
+            b = fmaf(wr, G[(size_t)l * A.T], b);
+            c = fmaf(wr, g, c);
         }
         qt[i] = make_float4(0.0f, a, b, c);
     }
@@ -558,6 +575,9 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
     }
     const float scale = (float)(A.T - 1) * rsqrtf(A.a_max);
     const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const uint32_t below = (1u << lane) - 1u;
+    const int seg = (A.M + nw - 1) / nw;                  // warp wp owns proposals [s0, s1)
+    const int s0 = min(A.M, wp * seg), s1 = min(A.M, s0 + seg);
 
     for (int64_t j = blockIdx.x; j < A.J; j += gridDim.x) {
         __syncthreads();
@@ -565,11 +585,11 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
         if (threadIdx.x < LA_P)
             tp[threadIdx.x] = tn_params(A.prop[j * 2 * LA_P + 2 * threadIdx.x],
                                         A.prop[j * 2 * LA_P + 2 * threadIdx.x + 1], A.sigma_scale);
+        if (threadIdx.x == 0) sh[4] = 0;
         __syncthreads();
         for (int i = threadIdx.x; i < A.T; i += blockDim.x) {
-            const float* r = tab + (size_t)i * A.ldt;
             float a = 0.0f;
-            for (int l = 0; l < A.L; ++l) a = fmaf(A.w[l] * ys[l], r[l], a);
+            for (int l = 0; l < A.L; ++l) a = fmaf(A.w[l] * ys[l], G[(size_t)l * A.T + i], a);
             qt[i].x = a;
         }
         if (threadIdx.x == 0) {
@@ -623,16 +643,63 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
         }
         __syncthreads();
 
-        // accepted set: every key below the k-th, then the lowest-index keys equal to it
-        int tie_rank = 0;
-        const uint32_t K = block_select(keys, A.M, A.k - 1, hist, sh, &tie_rank);
-        const int need_ties = tie_rank + 1;   // k minus the number of keys strictly below K
-        // Ordered compaction: warp w scans the contiguous index segment [s0, s1), so the
-        // accepted indices come out in increasing order with one block barrier: a counting
-        // pass per warp, the warps' exclusive prefix, then a placing pass.
-        {
-            const int seg = (A.M + nw - 1) / nw;
-            const int s0 = min(A.M, wp * seg), s1 = min(A.M, s0 + seg);
+        // ---- the k-th distance K (and the median accepted distance Km)
+        uint32_t K = 0, Km = 0;
+        int need_ties = 1;
+        bool fast = A.n_pilot > 0, have_med = false;
+        if (fast) {
+            // pivots: order statistics of the first n_pilot proposals (an i.i.d. sample)
+            uint32_t piv[2];
+            block_select2(keys, A.n_pilot, A.r_lo, A.r_hi, hist, sh, piv, nullptr);
+            const uint32_t lo = piv[0], hi = piv[1];
+            int cl = 0;
+            for (int i0 = s0; i0 < s1; i0 += 32) {
+                const int i = i0 + lane;
+                const float kf = i < s1 ? keys[i] : 0.0f;
+                const uint32_t kk = f2key(kf);
+                cl += __popc(__ballot_sync(0xFFFFFFFFu, i < s1 && kk < lo));
+                const bool in = i < s1 && kk >= lo && kk <= hi;
+                const uint32_t bc = __ballot_sync(0xFFFFFFFFu, in);
+                if (bc) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&sh[4], __popc(bc));
+                    base = __shfl_sync(0xFFFFFFFFu, base, 0) + __popc(bc & below);
+                    if (in && base < LA_CAP) { ckey[base] = kf; cidx[base] = i; }
+                }
+            }
+            if (lane == 0) { wcnt[wp] = cl; wcnt[16 + wp] = 0; }
+            __syncthreads();
+            const int n_c = sh[4];
+            int n_lt = 0;
+            for (int q = 0; q < nw; ++q) n_lt += wcnt[q];
+            fast = n_lt <= A.k - 1 && n_lt + n_c >= A.k && n_c <= LA_CAP;   // block-uniform
+            if (fast) {
+                const int rm = (A.k - 1) / 2;
+                have_med = rm >= n_lt;
+                uint32_t sel[2];
+                int ties[2];
+                block_select2(ckey, n_c, A.k - 1 - n_lt, have_med ? rm - n_lt : A.k - 1 - n_lt, hist, sh, sel,
+                              ties);
+                K = sel[0];
+                Km = sel[1];
+                need_ties = ties[0] + 1;     // k minus the number of keys strictly below K
+                for (int c = threadIdx.x; c < n_c; c += blockDim.x) {
+                    const uint32_t kk = f2key(ckey[c]);
+                    const int w = cidx[c] / seg;
+                    if (kk < K) atomicAdd(&wcnt[w], 1);
+                    else if (kk == K) atomicAdd(&wcnt[16 + w], 1);
+                }
+                __syncthreads();
+            }
+        }
+        if (!fast) {
+            uint32_t sel[2];
+            int ties[2];
+            block_select2(keys, A.M, A.k - 1, (A.k - 1) / 2, hist, sh, sel, ties);
+            K = sel[0];
+            Km = sel[1];
+            have_med = true;
+            need_ties = ties[0] + 1;
             int cl = 0, ct = 0;
             for (int i0 = s0; i0 < s1; i0 += 32) {
                 const int i = i0 + lane;
@@ -642,9 +709,13 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
             }
             if (lane == 0) { wcnt[wp] = cl; wcnt[16 + wp] = ct; }
             __syncthreads();
+        }
+
+        // ---- ordered compaction: warp wp places its segment's accepted indices after
+        // those of the lower warps, so acc lists the accepted set by increasing index
+        {
             int pl0 = 0, pt0 = 0;
             for (int q = 0; q < wp; ++q) { pl0 += wcnt[q]; pt0 += wcnt[16 + q]; }
-            const uint32_t below = (1u << lane) - 1u;
             for (int i0 = s0; i0 < s1; i0 += 32) {
                 const int i = i0 + lane;
                 const uint32_t kk = i < s1 ? f2key(keys[i]) : 0u;
@@ -658,16 +729,17 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
             }
         }
         __syncthreads();
-
-        // median accepted distance: the ((k - 1) / 2)-th smallest key, selected among the k
-        // accepted keys (gathered into the weights' space before the keys' space is reused)
-        if (threadIdx.x < A.k) wacc[threadIdx.x] = keys[acc[threadIdx.x]];
-        __syncthreads();
-        {
-            const uint32_t Km = block_select(wacc, A.k, (A.k - 1) / 2, hist, sh, nullptr);
-            if (threadIdx.x == 0) A.dmed[j] = key2f(Km);
+        if (!have_med) {
+            // the median lies below the bracket: select it among the k accepted keys
+            if (threadIdx.x < A.k) wacc[threadIdx.x] = keys[acc[threadIdx.x]];
+            __syncthreads();
+            uint32_t sel[2];
+            block_select2(wacc, A.k, (A.k - 1) / 2, (A.k - 1) / 2, hist, sh, sel, nullptr);
+            Km = sel[0];
         }
+        if (threadIdx.x == 0) A.dmed[j] = key2f(Km);
         __syncthreads();
+
         // weights 1/q, normalised over the accepted set; accepted values
         float lw = -3.0e38f;
         float vals[LA_C] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -690,92 +762,70 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
         if (threadIdx.x < LA_KMAX) {
             wacc[threadIdx.x] = W;
 #pragma unroll
-            for (int c = 0; c < LA_C; ++c) {
-                sv[c * LA_KMAX + threadIdx.x] = threadIdx.x < A.k ? vals[c] : __int_as_float(0x7F800000);
-                sw[c * LA_KMAX + threadIdx.x] = W;
-            }
-        }
-        // weighted mean and SD per column: per-lane partial sums over the k accepted, then a
-        // shuffle tree (two passes, so the spread is summed about the mean)
-        __syncthreads();
-        if (wp < LA_C) {
-            const int c = wp;
-            float m = 0.0f;
-            for (int r = lane; r < A.k; r += 32) m = fmaf(wacc[r], sv[c * LA_KMAX + r], m);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xFFFFFFFFu, m, o);
-            float v2 = 0.0f;
-            for (int r = lane; r < A.k; r += 32) {
-                const float e = sv[c * LA_KMAX + r] - m;
-                v2 = fmaf(wacc[r] * e, e, v2);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xFFFFFFFFu, v2, o);
-            if (lane == 0) {
-                A.mean[j * LA_C + c] = m;
-                A.sd[j * LA_C + c] = sqrtf(v2);
-            }
+            for (int c = 0; c < LA_C; ++c) sv[c * LA_KMAX + threadIdx.x] = vals[c];
         }
         if (threadIdx.x == 0) {
             A.ess[j] = 1.0f / s2;
             A.ynorm[j] = yy;
         }
-        // bitonic sort of the five 256-entry columns by value, weights alongside
-        for (int size = 2; size <= LA_KMAX; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                __syncthreads();
-                for (int e = threadIdx.x; e < LA_C * (LA_KMAX / 2); e += blockDim.x) {
-                    const int c = e / (LA_KMAX / 2), q = e % (LA_KMAX / 2);
-                    const int i = 2 * q - (q & (stride - 1));
-                    const int pi = i + stride;
-                    const bool asc = (i & size) == 0;
-                    float* v = sv + c * LA_KMAX;
-                    float* ww = sw + c * LA_KMAX;
-                    const float a = v[i], b = v[pi];
-                    if ((a > b) == asc) {
-                        v[i] = b;
-                        v[pi] = a;
-                        const float t = ww[i];
-                        ww[i] = ww[pi];
-                        ww[pi] = t;
-                    }
-                }
-            }
-        }
         __syncthreads();
-        // weighted 2.5 / 97.5 % quantiles: smallest value whose cumulative weight reaches q
+        // per column (one warp each): weighted mean and SD (two passes, per-lane partial
+        // sums then a shuffle tree), and the weighted 2.5 / 97.5 % quantiles: the smallest
+        // accepted value v whose cumulative weight sum_{v_r <= v} W_r reaches the level,
+        // found by bisection on the order-preserving integer image of the values
         if (wp < LA_C) {
             const int c = wp;
-            const float* v = sv + c * LA_KMAX;
-            const float* ww = sw + c * LA_KMAX;
             constexpr int PER = LA_KMAX / 32;
-            float loc[PER], s = 0.0f;
-#pragma unroll
-            for (int q = 0; q < PER; ++q) { s += ww[lane * PER + q]; loc[q] = s; }
-            float incl = s;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const float excl = incl - s;
-            int fl = LA_KMAX, fh = LA_KMAX;
+            float v[PER], wv[PER];
+            uint32_t kv[PER];
+            float m = 0.0f;
+            uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
-                const int r = lane * PER + q;
-                if (r < A.k) {
-                    if (fl == LA_KMAX && excl + loc[q] >= 0.025f) fl = r;
-                    if (fh == LA_KMAX && excl + loc[q] >= 0.975f) fh = r;
-                }
+                const int r = q * 32 + lane;
+                const bool ok = r < A.k;
+                v[q] = ok ? sv[c * LA_KMAX + r] : 0.0f;
+                wv[q] = ok ? wacc[r] : 0.0f;
+                kv[q] = ok ? f2key(v[q]) : 0xFFFFFFFFu;
+                m = fmaf(wv[q], v[q], m);
+                if (ok) { kmin = min(kmin, kv[q]); kmax = max(kmax, kv[q]); }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                fl = min(fl, __shfl_xor_sync(0xFFFFFFFFu, fl, o));
-                fh = min(fh, __shfl_xor_sync(0xFFFFFFFFu, fh, o));
+                m += __shfl_xor_sync(0xFFFFFFFFu, m, o);
+                kmin = min(kmin, __shfl_xor_sync(0xFFFFFFFFu, kmin, o));
+                kmax = max(kmax, __shfl_xor_sync(0xFFFFFFFFu, kmax, o));
+            }
+            float v2 = 0.0f;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const float e = v[q] - m;
+                v2 = fmaf(wv[q] * e, e, v2);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xFFFFFFFFu, v2, o);
+            uint32_t lo0 = kmin, hi0 = kmax, lo1 = kmin, hi1 = kmax;
+            while (lo0 < hi0 || lo1 < hi1) {
+                const uint32_t mid0 = lo0 + ((hi0 - lo0) >> 1), mid1 = lo1 + ((hi1 - lo1) >> 1);
+                float c0 = 0.0f, c1 = 0.0f;
+#pragma unroll
+                for (int q = 0; q < PER; ++q) {
+                    c0 += kv[q] <= mid0 ? wv[q] : 0.0f;
+                    c1 += kv[q] <= mid1 ? wv[q] : 0.0f;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    c0 += __shfl_xor_sync(0xFFFFFFFFu, c0, o);
+                    c1 += __shfl_xor_sync(0xFFFFFFFFu, c1, o);
+                }
+                if (lo0 < hi0) { if (c0 >= 0.025f) hi0 = mid0; else lo0 = mid0 + 1; }
+                if (lo1 < hi1) { if (c1 >= 0.975f) hi1 = mid1; else lo1 = mid1 + 1; }
             }
             if (lane == 0) {
-                A.qlo[j * LA_C + c] = v[min(fl, A.k - 1)];
-                A.qhi[j * LA_C + c] = v[min(fh, A.k - 1)];
+                A.mean[j * LA_C + c] = m;
+                A.sd[j * LA_C + c] = sqrtf(v2);
+                A.qlo[j * LA_C + c] = key2f(lo0);
+                A.qhi[j * LA_C + c] = key2f(lo1);
             }
         }
     }
@@ -974,9 +1024,28 @@ extern "C" int abc_add_noise(const float* x_dev, int64_t N, int32_t ldx, const a
 
 extern "C" size_t abc_local_abc_smem_bytes(int32_t T, int32_t L, int32_t M) {
     if (T < 1 || L < 1 || M < 1) return 0;
-    const size_t ldt = (size_t)(L | 1);
-    const size_t kreg = (size_t)M > 2 * LA_C * LA_KMAX ? (size_t)M : 2 * LA_C * LA_KMAX;
-    return sizeof(float) * ((size_t)T * ldt + 2 * MAXL + kreg + 2 * LA_KMAX + 64 + 256 + 8 + 32 + 4 * (size_t)T + 8);
+    const size_t kreg = (size_t)M > (size_t)LA_C * LA_KMAX ? (size_t)M : (size_t)LA_C * LA_KMAX;
+    // qt (4 T), cps + ys, keys, acc + wacc, red, 2 histograms, sh, warp counts, scal, candidates
+    return sizeof(float) * (4 * (size_t)T + 2 * MAXL + kreg + 2 * LA_KMAX + 64 + 512 + 8 + 32 + 8 + 2 * LA_CAP);
+}
+
+__global__ void k_table_frame_major(const float* __restrict__ rows, int T, int L, int ld, float* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= T * L) return;
+    const int l = e / T, i = e - l * T;
+    out[e] = rows[(size_t)i * ld + l];
+}
+
+extern "C" int abc_local_abc_table(const float* rows_dev, int32_t T, int32_t L, int32_t ld, float* table_dev,
+                                   void* stream) {
+    vpet::clear_error();
+    VPET_ARG(T >= 1 && L >= 1 && L <= MAXL && ld >= L && (int64_t)T * L < (1LL << 31),
+             "abc_local_abc_table: bad sizes");
+    VPET_ARG(rows_dev && table_dev, "abc_local_abc_table: null pointer");
+    k_table_frame_major<<<(unsigned)vpet_ceil_div((int64_t)T * L, 256), 256, 0, (cudaStream_t)stream>>>(
+        rows_dev, T, L, ld, table_dev);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
 }
 
 extern "C" int abc_local_abc(const float* y_dev, int64_t J, int32_t ldy, int32_t L, const float* w_host,
@@ -995,7 +1064,7 @@ extern "C" int abc_local_abc(const float* y_dev, int64_t J, int32_t ldy, int32_t
     VPET_ARG(lo_host[1] + lo_host[2] > 0.0 && hi_host[1] + hi_host[2] <= a_max,
              "abc_local_abc: k2 + k3 must stay in (0, a_max]");
     const size_t smem = abc_local_abc_smem_bytes(T, L, M);
-    VPET_ARG(smem <= 227 * 1024, "abc_local_abc: table (T x L) and M distances exceed 227 KB of shared memory");
+    VPET_ARG(smem <= 227 * 1024, "abc_local_abc: T tabulated products and M distances exceed 227 KB of shared memory");
     if (J == 0) return ABC_OK;
     VPET_ARG(y_dev && prop_dev && table_dev && cp_frames_dev, "abc_local_abc: null device input");
     VPET_ARG(mean_dev && sd_dev && qlo_dev && qhi_dev && ess_dev && dmed_dev && ynorm_dev,
@@ -1011,7 +1080,22 @@ extern "C" int abc_local_abc(const float* y_dev, int64_t J, int32_t ldy, int32_t
     A.table = table_dev;
     A.cpf = cp_frames_dev;
     A.T = T;
-    A.ldt = L | 1;
+    // Bracketing of the k-th distance by a pilot sample: pivots at the sample ranks
+    // 4 standard deviations (plus one) either side of where the k-th of M falls; used
+    // when the keys expected below the lower pivot leave room for the median and the
+    // expected candidates fit the buffer with a factor 2 to spare.
+    if (M >= 2048) {
+        const int n = M < LA_PILOT ? M : LA_PILOT;
+        const double pq = (k - 0.5) / M, mu = n * pq, sd = sqrt(n * pq * (1.0 - pq)) + 1.0;
+        const int rl = (int)floor(mu - 4.0 * sd) - 1, rh = (int)ceil(mu + 4.0 * sd) + 1;
+        const int r_lo = rl < 0 ? 0 : rl, r_hi = rh > n - 1 ? n - 1 : rh;
+        const double below = (r_lo + 1.0) * M / (n + 1.0), cand = (r_hi - r_lo + 1.0) * M / (n + 1.0);
+        if (below <= 0.5 * (k - 1) && cand <= 0.5 * LA_CAP) {
+            A.n_pilot = n;
+            A.r_lo = r_lo;
+            A.r_hi = r_hi;
+        }
+    }
     A.a_max = (float)a_max;
     for (int p = 0; p < LA_P; ++p) {
         A.lo[p] = (float)lo_host[p];

@@ -73,7 +73,7 @@ class LearnedLocalAbc:
         th[T] = [1.0, 1.0, 1.0, 1.0, 0, 0, 0, 0]   # Vb = 1: C_p itself
         th_d = torch.from_numpy(th).cuda()
         x = api.simulate(S.TCM2_IRR, self.ts, self.te, self.inp, th_d, ldx=self.L)
-        table = x[:T].contiguous()
+        table = api.local_abc_table(x[:T])          # (L, T), frame-major
         cp = x[T].contiguous()
         # the grid must be the fp32 one the kernel assumes: a_i rounded to fp32 exactly as above
         return table, cp

@@ -147,6 +147,8 @@ def test_learned_sizes_and_validation_without_gpu(lib):
     assert lib.abc_local_abc(*args(100, 60000, 1024, 2.5)) == _lib.ABC_ERR_ARG     # shared memory
     assert "shared memory" in lib.abc_last_error().decode()
     assert lib.abc_local_abc_smem_bytes(512, 29, 10000) <= 227 * 1024
+    assert lib.abc_local_abc_table(P(16), 512, 29, 28, P(16), None) == _lib.ABC_ERR_ARG   # ld < L
+    assert lib.abc_local_abc_table(None, 512, 29, 29, P(16), None) == _lib.ABC_ERR_ARG
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])

@@ -151,9 +151,11 @@ def c3_small():
     return W, y, irr, truth
 
 
-def test_local_abc_stage_parity(orc, c3_small):
+@pytest.mark.parametrize("M,k", [(2000, 64), (10_000, 200)])
+def test_local_abc_stage_parity(orc, c3_small, M, k):
     """Proposals, distances, accepted set, weights and summaries of the local
-    kernel against the oracle fed the GPU's own proposals."""
+    kernel against the oracle fed the GPU's own proposals (M = 2000: selection
+    over all distances; M = 10^4: over the candidates a pilot sample brackets)."""
     from paper_2603_14859_b300 import synth as S
     from paper_2603_14859_b300.learned import LearnedLocalAbc
     W, y, irr, truth = c3_small
@@ -169,7 +171,7 @@ def test_local_abc_stage_parity(orc, c3_small):
     prop[:, 1::2] = np.log(rng.uniform(0.03, 0.3, u_true.shape))
     prop[0, 0::2] = [-0.5, 0.3, 1.4, 0.5]          # means outside the box on both sides
     yj = y[torch.from_numpy(rows).cuda()].contiguous()
-    M, k, seed = 2000, 64, 4242
+    seed = 4242
     out = model.local(yj, torch.from_numpy(prop).cuda(), M=M, k=k, seed=seed, dump=True)
     u = out["u"].cpu().numpy().astype(np.float64)
     d = out["d"].cpu().numpy().astype(np.float64)
@@ -253,13 +255,15 @@ def test_local_abc_edge_cases(c3_small):
     pt = torch.zeros((3, 8), device="cuda")
     pt[:, 0::2] = -3.0
     pt[:, 1::2] = -30.0
-    tie = model.local(yj, pt, M=700, k=50, seed=2, dump=True)
-    dd = tie["d"].cpu().numpy()
-    assert np.all(tie["u"].cpu().numpy() == 0.0)
-    assert np.all(dd == dd[:, :1])
-    assert np.allclose(tie["mean"][:, :4].cpu().numpy(), model.lo.astype(np.float32), rtol=1e-6)
-    assert np.all(tie["sd"].cpu().numpy() <= 1e-6)
-    assert np.allclose(tie["ess"].cpu().numpy(), 50, rtol=1e-4)
+    for M in (700, 4096):     # 4096: the pilot bracket holds every distance and selection falls back
+        tie = model.local(yj, pt, M=M, k=50, seed=2, dump=True)
+        dd = tie["d"].cpu().numpy()
+        assert np.all(tie["u"].cpu().numpy() == 0.0)
+        assert np.all(dd == dd[:, :1])
+        assert np.allclose(tie["mean"][:, :4].cpu().numpy(), model.lo.astype(np.float32), rtol=1e-6)
+        assert np.all(tie["sd"].cpu().numpy() <= 1e-6)
+        assert np.allclose(tie["ess"].cpu().numpy(), 50, rtol=1e-4)
+        assert np.all(tie["dmed"].cpu().numpy() == dd[:, 0])
 
 
 def test_training_is_bitwise_reproducible(c3_small):
