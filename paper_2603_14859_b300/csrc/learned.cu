@@ -769,16 +769,17 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
             A.ynorm[j] = yy;
         }
         __syncthreads();
-        // per column (one warp each): weighted mean and SD (two passes, per-lane partial
-        // sums then a shuffle tree), and the weighted 2.5 / 97.5 % quantiles: the smallest
-        // accepted value v whose cumulative weight sum_{v_r <= v} W_r reaches the level,
-        // found by bisection on the order-preserving integer image of the values
-        if (wp < LA_C) {
-            const int c = wp;
+        // per column c, warps 2c and 2c + 1: the weighted mean and SD (two passes, per-lane
+        // partial sums then a shuffle tree; warp 2c), and the weighted 2.5 % (warp 2c) or
+        // 97.5 % (warp 2c + 1) quantile: the smallest accepted value v whose cumulative weight
+        // sum_{v_r <= v} W_r reaches the level, found by bisection on the order-preserving
+        // integer image of the values
+        if (wp < 2 * LA_C) {
+            const int c = wp >> 1;
+            const bool upper = wp & 1;
             constexpr int PER = LA_KMAX / 32;
             float v[PER], wv[PER];
             uint32_t kv[PER];
-            float m = 0.0f;
             uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
@@ -787,45 +788,46 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
                 v[q] = ok ? sv[c * LA_KMAX + r] : 0.0f;
                 wv[q] = ok ? wacc[r] : 0.0f;
                 kv[q] = ok ? f2key(v[q]) : 0xFFFFFFFFu;
-                m = fmaf(wv[q], v[q], m);
                 if (ok) { kmin = min(kmin, kv[q]); kmax = max(kmax, kv[q]); }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                m += __shfl_xor_sync(0xFFFFFFFFu, m, o);
                 kmin = min(kmin, __shfl_xor_sync(0xFFFFFFFFu, kmin, o));
                 kmax = max(kmax, __shfl_xor_sync(0xFFFFFFFFu, kmax, o));
             }
-            float v2 = 0.0f;
+            const float level = upper ? 0.975f : 0.025f;
+            uint32_t lo = kmin, hi = kmax;
+            while (lo < hi) {
+                const uint32_t mid = lo + ((hi - lo) >> 1);
+                float cw = 0.0f;
 #pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const float e = v[q] - m;
-                v2 = fmaf(wv[q] * e, e, v2);
+                for (int q = 0; q < PER; ++q) cw += kv[q] <= mid ? wv[q] : 0.0f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cw += __shfl_xor_sync(0xFFFFFFFFu, cw, o);
+                if (cw >= level) hi = mid;
+                else lo = mid + 1;
             }
+            if (upper) {
+                if (lane == 0) A.qhi[j * LA_C + c] = key2f(lo);
+            } else {
+                float m = 0.0f;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xFFFFFFFFu, v2, o);
-            uint32_t lo0 = kmin, hi0 = kmax, lo1 = kmin, hi1 = kmax;
-            while (lo0 < hi0 || lo1 < hi1) {
-                const uint32_t mid0 = lo0 + ((hi0 - lo0) >> 1), mid1 = lo1 + ((hi1 - lo1) >> 1);
-                float c0 = 0.0f, c1 = 0.0f;
+                for (int q = 0; q < PER; ++q) m = fmaf(wv[q], v[q], m);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xFFFFFFFFu, m, o);
+                float v2 = 0.0f;
 #pragma unroll
                 for (int q = 0; q < PER; ++q) {
-                    c0 += kv[q] <= mid0 ? wv[q] : 0.0f;
-                    c1 += kv[q] <= mid1 ? wv[q] : 0.0f;
+                    const float e = v[q] - m;
+                    v2 = fmaf(wv[q] * e, e, v2);
                 }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    c0 += __shfl_xor_sync(0xFFFFFFFFu, c0, o);
-                    c1 += __shfl_xor_sync(0xFFFFFFFFu, c1, o);
+                for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xFFFFFFFFu, v2, o);
+                if (lane == 0) {
+                    A.mean[j * LA_C + c] = m;
+                    A.sd[j * LA_C + c] = sqrtf(v2);
+                    A.qlo[j * LA_C + c] = key2f(lo);
                 }
-                if (lo0 < hi0) { if (c0 >= 0.025f) hi0 = mid0; else lo0 = mid0 + 1; }
-                if (lo1 < hi1) { if (c1 >= 0.975f) hi1 = mid1; else lo1 = mid1 + 1; }
-            }
-            if (lane == 0) {
-                A.mean[j * LA_C + c] = m;
-                A.sd[j * LA_C + c] = sqrtf(v2);
-                A.qlo[j * LA_C + c] = key2f(lo0);
-                A.qhi[j * LA_C + c] = key2f(lo1);
             }
         }
     }
