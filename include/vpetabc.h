@@ -282,8 +282,9 @@ int abc_model_select(const int32_t* idx_dev, int64_t J, int32_t k, const int64_t
  * columns P_m..Pmax-1 are NaN, and column Pmax holds K_i when has_ki[m] (K1,
  * k2, k3 read from theta columns ki_cols[0..2]) else NaN.
  *   mean: arithmetic mean;  sd: standard deviation with ddof = 1 (0 for one
- *   sample), accumulated in fp64;  lo / hi: the 0.025 / 0.975 quantiles by
- *   linear interpolation between order statistics (type 7).
+ *   sample), two passes about the mean;  lo / hi: the 0.025 / 0.975 quantiles
+ *   by linear interpolation between order statistics (type 7).  Sums are
+ *   compensated fp32 (relative error near 2^-24 for any k).
  * Each output is J x ncols fp32, row-major. */
 int abc_summarize(const float* theta_dev, int32_t ldtheta, const int64_t* model_offsets_host, int32_t M,
                   const int32_t* nparams_host, const int32_t* has_ki_host, const int32_t* ki_cols_host,

@@ -56,10 +56,27 @@ struct SumParams {
     int Pmax, ncols, k, p2, ldt;
 };
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+// Compensated fp32 accumulation (Neumaier's variant of Kahan summation): the
+// running sum s and the lost low-order parts c; the value is s + c.
+struct CSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float t = s + v;
+        c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+};
+
+// Warp total of per-lane compensated sums: pairs of (sum, compensation) are
+// combined the same way along a butterfly, so every lane gets the same value.
+__device__ __forceinline__ float warp_csum(CSum a) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xFFFFFFFFu, a.s, o), c2 = __shfl_xor_sync(0xFFFFFFFFu, a.c, o);
+        a.c += c2;
+        a.add(s2);
+    }
+    return a.s + a.c;
 }
 
 __device__ __forceinline__ uint32_t f2o(float f) {
@@ -170,42 +187,45 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
         const bool isk = col == Q.Pmax;
         float o0 = qnan, o1 = qnan, o2 = qnan, o3 = qnan;
         if (n > 0 && ((isk && ki) || (!isk && col < P))) {
-            double s = 0.0;
+            // fp32 throughout (compensated sums): the values are fp32 and the sums'
+            // relative error stays near 2^-24 for any k
+            CSum s;
             for (int i = lane; i < n; i += 32) {
                 const float* th = theta + (int64_t)sel[i] * Q.ldt;
                 float v;
                 if (isk) {
-                    const double K1 = th[Q.ki[0]], k2 = th[Q.ki[1]], k3 = th[Q.ki[2]];
-                    v = (float)(K1 * k3 / (k2 + k3));
+                    const float K1 = th[Q.ki[0]], k2 = th[Q.ki[1]], k3 = th[Q.ki[2]];
+                    v = K1 * k3 / (k2 + k3);
                 } else {
                     v = th[col];
                 }
                 vals[i] = v;
-                s += v;
+                s.add(v);
             }
-            s = warp_sum_d(s);
-            const double mu = s / n;
-            double ss = 0.0;
+            const float mu = warp_csum(s) / (float)n;
+            CSum ss;
             __syncwarp();
             for (int i = lane; i < n; i += 32) {
-                const double e = (double)vals[i] - mu;
-                ss += e * e;
+                const float e = vals[i] - mu;
+                ss.add(e * e);
             }
-            ss = warp_sum_d(ss);
-            // type-7 quantiles from the two order statistics around each level
-            double qv[2];
+            const float sst = warp_csum(ss);
+            // type-7 quantiles from the two order statistics around each level; the
+            // position h = (n - 1) q is formed in fp64 once (exact floor at integer h)
+            float qv[2];
             const double qs[2] = {0.025, 0.975};
             for (int t = 0; t < 2; ++t) {
                 const double h = (n - 1) * qs[t];
                 const int a = (int)floor(h);
+                const float fr = (float)(h - a);
                 float va, vb;
                 warp_pair(vals, n, a, hist, lane, va, vb);
-                qv[t] = (double)va + (h - a) * ((double)vb - (double)va);
+                qv[t] = fmaf(fr, vb - va, va);
             }
-            o0 = (float)mu;
-            o1 = n > 1 ? (float)sqrt(ss / (n - 1)) : 0.0f;
-            o2 = (float)qv[0];
-            o3 = (float)qv[1];
+            o0 = mu;
+            o1 = n > 1 ? sqrtf(sst / (float)(n - 1)) : 0.0f;
+            o2 = qv[0];
+            o3 = qv[1];
             __syncwarp();
         }
         if (lane == 0) {

@@ -1093,11 +1093,12 @@ __device__ __forceinline__ float lane_dist(const float* ys, const float* ws, con
     return p[0];
 }
 
-// NR rows per group of G lanes, all loads issued before the arithmetic;
-// every lane of the warp must call it (full-warp shuffles).
+// NR rows per group of G lanes, all loads issued before the arithmetic; the
+// lane's four frames 4h..4h+3 of y and w come in registers (yq, wq; zero
+// weight past L).  Every lane of the warp must call it (full-warp shuffles).
 template <int NR>
-__device__ __forceinline__ void group_dist_n(const float* ys, const float* ws, const float* const (&xr)[NR], int L,
-                                             int h, int G, float (&d)[NR]) {
+__device__ __forceinline__ void group_dist_n(const float (&yq)[4], const float (&wq)[4], const float* const (&xr)[NR],
+                                             int L, int h, int G, float (&d)[NR]) {
     const int l = 4 * h;
     float4 v[NR];
 #pragma unroll
@@ -1112,8 +1113,8 @@ __device__ __forceinline__ void group_dist_n(const float* ys, const float* ws, c
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (l + q < L) {
-                    const float e = ys[l + q] - xv[q];
-                    d[r] = fmaf(ws[l + q] * e, e, d[r]);
+                    const float e = yq[q] - xv[q];
+                    d[r] = fmaf(wq[q] * e, e, d[r]);
                 }
         }
     }
@@ -1123,7 +1124,7 @@ __device__ __forceinline__ void group_dist_n(const float* ys, const float* ws, c
     }
 }
 
-__global__ void k_finalize(const __grid_constant__ BatchFin B) {
+__global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ BatchFin B) {
     extern __shared__ __align__(16) uint8_t fsm[];
     const int warps = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1169,6 +1170,13 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
         // 2. exact fp32 re-score of the net (list entries are packed draw rows, read from the
         // packed fp32 copy): G lanes per row, four rows per group in flight
         constexpr int NR = 4;
+        float yq[4], wq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int l = 4 * h + q;
+            yq[q] = l < P.L ? ys[l] : 0.0f;
+            wq[q] = l < P.L ? ws[l] : 0.0f;
+        }
         for (int i0 = 0; i0 < cnt; i0 += NR * R) {
             const float* xr[NR];
 #pragma unroll
@@ -1177,7 +1185,7 @@ __global__ void k_finalize(const __grid_constant__ BatchFin B) {
                 xr[r] = P.xs + (int64_t)ij[i < cnt ? i : cnt - 1] * P.ldxs;
             }
             float d[NR];
-            group_dist_n<NR>(ys, ws, xr, P.L, h, G, d);
+            group_dist_n<NR>(yq, wq, xr, P.L, h, G, d);
             __syncwarp();
             if (h == 0) {
 #pragma unroll
