@@ -58,7 +58,8 @@ extern "C" {
  *                    certified is resolved by an exact fp32 scan.  The accepted
  *                    set is the exact fp32 top-k.
  *  ABC_BF16_RESCORE: one bf16 product per term; each voxel keeps its 4k
- *                    nearest by the bf16 distance, which are re-scored exactly
+ *                    nearest by the bf16 distance (and the few that share the
+ *                    4k-th's bin of a 256-bin cut), which are re-scored exactly
  *                    in fp32 before the final k are chosen (certification is
  *                    reported, not enforced).
  *  ABC_SPLIT_DRAWS:  the draw operand split into bf16 hi + lo, the voxel

@@ -75,6 +75,104 @@ __device__ __forceinline__ uint32_t warp_select(const float* keys, int cnt, int 
     return low_bits > 0 ? (prefix | ((1u << low_bits) - 1u)) : prefix;
 }
 
+// Cut for "at least the rank + 1 smallest" without an exact selection: 256
+// equal-width bins over [min, max] of keys[0..cnt) (bin(v) = floor((v - min) *
+// scale), monotone in v), and the bin b that holds the element of that rank.
+// Keeping every key with bin(key) <= b keeps at least rank + 1 keys, and every
+// dropped key exceeds every kept one.  Two passes (range, histogram) instead of
+// one per radix digit.  hist: 256 words of this warp's shared memory.
+struct LinearCut {
+    float mn, scale;
+    int bin;
+};
+
+__device__ __forceinline__ int linear_bin(float v, const LinearCut& c) {
+    const float t = (v - c.mn) * c.scale;
+    return t < 255.0f ? (int)t : 255;
+}
+
+__device__ __forceinline__ LinearCut warp_cut_linear(const float* keys, int cnt, int rank, uint32_t* hist, int lane) {
+    float mn = 3.0e38f, mx = -3.0e38f;
+    for (int i = lane; i < cnt; i += 32) {
+        const float v = keys[i];
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    }
+    LinearCut c;
+    c.mn = mn;
+    const float span = mx - mn;
+    c.scale = span > 0.0f && span < 3.0e38f ? 256.0f / span : 0.0f;
+    c.bin = 255;
+    if (c.scale == 0.0f) return c;          // one distinct value (or an unbounded range): keep all
+#pragma unroll
+    for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0;
+    __syncwarp();
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        const uint32_t bin = i < cnt ? (uint32_t)linear_bin(keys[i], c) : (0x100u | (uint32_t)lane);
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin);
+        if (i < cnt && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+    }
+    __syncwarp();
+    uint32_t loc[8], sum = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) { loc[b] = hist[lane * 8 + b]; sum += loc[b]; }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    uint32_t cum = incl - sum;
+    int found = -1;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if (found < 0 && cum + loc[b] > (uint32_t)rank) found = lane * 8 + b;
+        cum += loc[b];
+    }
+    const uint32_t who = __ballot_sync(0xFFFFFFFFu, found >= 0);
+    c.bin = who ? __shfl_sync(0xFFFFFFFFu, found, __ffs(who) - 1) : 255;
+    __syncwarp();
+    return c;
+}
+
+// In-place stable compaction of (keys, idx)[0..cnt) to the entries in bins <= c.bin;
+// returns the number kept and (in kmax) the largest kept key.
+__device__ __forceinline__ int warp_compact_cut(float* keys, int32_t* idx, int cnt, const LinearCut& c, int lane,
+                                                float& kmax) {
+    int out = 0;
+    float mx = -3.0e38f;
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        float k = 0.0f;
+        int32_t id = 0;
+        bool keep = false;
+        if (i < cnt) {
+            k = keys[i];
+            id = idx[i];
+            keep = linear_bin(k, c) <= c.bin;
+        }
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+        const int pos = out + __popc(bal & ((1u << lane) - 1u));
+        if (keep) {
+            keys[pos] = k;
+            idx[pos] = id;
+            mx = fmaxf(mx, k);
+        }
+        out += __popc(bal);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    kmax = mx;
+    __syncwarp();
+    return out;
+}
+
 // In-place stable compaction of (keys, idx)[0..cnt) to the entries with key <= T.
 // At most `cap` entries are written; returns the number that qualified (which
 // may exceed cap).

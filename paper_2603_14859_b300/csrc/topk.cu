@@ -39,7 +39,9 @@
 // the prediction for correctness: a list always holds every draw below its
 // voxel's threshold.
 //
-// Kernel `k_finalize` (one warp per voxel) re-scores the net exactly as
+// Kernel `k_finalize` (one warp per voxel; for ABC_BF16_RESCORE first cutting a
+// list to its kt smallest keys plus the rest of their bin of 256 equal-width
+// bins over the list's key range) re-scores the net exactly as
 // sum_l w_l (y_l - x_l)^2 in fp32, selects the exact k-th distance d_k, and
 // certifies the result: with E bounding |computed d' - exact d'| for any draw
 // that could beat d_k (its ||xh|| <= ||yh|| + sqrt(d_k)), every draw outside
@@ -1163,9 +1165,11 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
         // 1. the net: every draw outside it has computed key > T_out
         float T_out = P.thr[j];
         if (P.mode != ABC_FP32 && cnt > P.kt) {
-            const uint32_t T = warp_select(kj, cnt, P.kt - 1, 3, hist, lane);
-            cnt = warp_compact(kj, ij, cnt, T, P.C, lane);
-            T_out = key2f(T);
+            // the net: the kt smallest keys and the rest of their linear bin (a few more)
+            const LinearCut cut = warp_cut_linear(kj, cnt, P.kt - 1, hist, lane);
+            float kmax;
+            cnt = warp_compact_cut(kj, ij, cnt, cut, lane, kmax);
+            T_out = kmax;
         }
         // 2. exact fp32 re-score of the net (list entries are packed draw rows, read from the
         // packed fp32 copy): G lanes per row, four rows per group in flight
