@@ -1181,29 +1181,65 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
             yq[q] = l < P.L ? ys[l] : 0.0f;
             wq[q] = l < P.L ? ws[l] : 0.0f;
         }
-        for (int i0 = 0; i0 < cnt; i0 += NR * R) {
-            const float* xr[NR];
+        if (NR * R <= 32) {
+            // row indices come a 32-row chunk at a time (lane t holds row cb + t), the next
+            // chunk's already in flight, so a gather never waits on its own index load; the
+            // chunk's global draw indices (ties break by them) are written back as it ends
+            int cb = 0;
+            int idx_cur = lane < cnt ? ij[lane] : 0;
+            int idx_nxt = 32 + lane < cnt ? ij[32 + lane] : 0;
+            int gx_cur = P.xperm ? P.xperm[idx_cur] : idx_cur;
+            for (int i0 = 0; i0 < cnt; i0 += NR * R) {
+                if (i0 - cb >= 32) {
+                    if (cb + lane < cnt) ij[cb + lane] = gx_cur;
+                    cb += 32;
+                    idx_cur = idx_nxt;
+                    idx_nxt = cb + 32 + lane < cnt ? ij[cb + 32 + lane] : 0;
+                    gx_cur = P.xperm ? P.xperm[idx_cur] : idx_cur;
+                }
+                const float* xr[NR];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const int i = i0 + r * R + grp;
-                xr[r] = P.xs + (int64_t)ij[i < cnt ? i : cnt - 1] * P.ldxs;
+                for (int r = 0; r < NR; ++r) {
+                    const int row = __shfl_sync(0xFFFFFFFFu, idx_cur, (i0 + r * R + grp - cb) & 31);
+                    xr[r] = P.xs + (int64_t)row * P.ldxs;
+                }
+                float d[NR];
+                group_dist_n<NR>(yq, wq, xr, P.L, h, G, d);
+                if (h == 0) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const int i = i0 + r * R + grp;
+                        if (i < cnt) kj[i] = d[r];
+                    }
+                }
             }
-            float d[NR];
-            group_dist_n<NR>(yq, wq, xr, P.L, h, G, d);
+            if (cb + lane < cnt) ij[cb + lane] = gx_cur;
             __syncwarp();
-            if (h == 0) {
+        } else {
+            for (int i0 = 0; i0 < cnt; i0 += NR * R) {
+                const float* xr[NR];
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     const int i = i0 + r * R + grp;
-                    if (i < cnt) kj[i] = d[r];
+                    xr[r] = P.xs + (int64_t)ij[i < cnt ? i : cnt - 1] * P.ldxs;
+                }
+                float d[NR];
+                group_dist_n<NR>(yq, wq, xr, P.L, h, G, d);
+                __syncwarp();
+                if (h == 0) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const int i = i0 + r * R + grp;
+                        if (i < cnt) kj[i] = d[r];
+                    }
                 }
             }
-        }
-        __syncwarp();
-        // back to global draw indices (ties break by them)
-        if (P.xperm) {
-            for (int i = lane; i < cnt; i += 32) ij[i] = P.xperm[ij[i]];
             __syncwarp();
+            // back to global draw indices (ties break by them)
+            if (P.xperm) {
+                for (int i = lane; i < cnt; i += 32) ij[i] = P.xperm[ij[i]];
+                __syncwarp();
+            }
         }
         // 3. exact k-th distance and the certificate
         bool cert = false;
