@@ -84,6 +84,7 @@ __device__ __forceinline__ uint32_t warp_select(const float* keys, int cnt, int 
 struct LinearCut {
     float mn, scale;
     int bin;
+    int below, inbin;   // keys in the bins below `bin`, and in `bin`
 };
 
 __device__ __forceinline__ int linear_bin(float v, const LinearCut& c) {
@@ -108,6 +109,8 @@ __device__ __forceinline__ LinearCut warp_cut_linear(const float* keys, int cnt,
     const float span = mx - mn;
     c.scale = span > 0.0f && span < 3.0e38f ? 256.0f / span : 0.0f;
     c.bin = 255;
+    c.below = 0;
+    c.inbin = cnt;
     if (c.scale == 0.0f) return c;          // one distinct value (or an unbounded range): keep all
 #pragma unroll
     for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0;
@@ -129,16 +132,70 @@ __device__ __forceinline__ LinearCut warp_cut_linear(const float* keys, int cnt,
         if (lane >= o) incl += v;
     }
     uint32_t cum = incl - sum;
-    int found = -1;
+    int found = -1, below = 0, inbin = 0;
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-        if (found < 0 && cum + loc[b] > (uint32_t)rank) found = lane * 8 + b;
+        if (found < 0 && cum + loc[b] > (uint32_t)rank) { found = lane * 8 + b; below = (int)cum; inbin = (int)loc[b]; }
         cum += loc[b];
     }
     const uint32_t who = __ballot_sync(0xFFFFFFFFu, found >= 0);
-    c.bin = who ? __shfl_sync(0xFFFFFFFFu, found, __ffs(who) - 1) : 255;
+    const int src = who ? __ffs(who) - 1 : 0;
+    c.bin = who ? __shfl_sync(0xFFFFFFFFu, found, src) : 255;
+    c.below = who ? __shfl_sync(0xFFFFFFFFu, below, src) : 0;
+    c.inbin = who ? __shfl_sync(0xFFFFFFFFu, inbin, src) : cnt;
     __syncwarp();
     return c;
+}
+
+// Exact key of the given rank (0-based) among keys[0..cnt): the linear cut finds
+// the bin holding it; that bin's keys (at most cap of them) are gathered into
+// buf (this warp's shared memory) and the one of rank rank - below among them is
+// found by counting, for each, the gathered keys below and equal to it.  A bin
+// with more than cap keys falls back to the four-digit radix select.  Returns
+// the order-preserving integer image of the key (as warp_select with 4 levels).
+__device__ __forceinline__ uint32_t warp_select_exact(const float* keys, int cnt, int rank, uint32_t* hist,
+                                                      float* buf, int cap, int lane) {
+    const LinearCut c = warp_cut_linear(keys, cnt, rank, hist, lane);
+    if (c.scale == 0.0f) {
+        // a single distinct value, or a range too wide for fp32 bins
+        float mn = 3.0e38f, mx = -3.0e38f;
+        for (int i = lane; i < cnt; i += 32) { mn = fminf(mn, keys[i]); mx = fmaxf(mx, keys[i]); }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+            mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+        }
+        if (mn == mx) return f2key(mn);
+        return warp_select(keys, cnt, rank, 4, hist, lane);
+    }
+    if (c.inbin > cap) return warp_select(keys, cnt, rank, 4, hist, lane);
+    int m = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        const float v = i < cnt ? keys[i] : 0.0f;
+        const bool in = i < cnt && linear_bin(v, c) == c.bin;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in);
+        if (in) buf[m + __popc(bal & ((1u << lane) - 1u))] = v;
+        m += __popc(bal);
+    }
+    __syncwarp();
+    const int r = rank - c.below;
+    uint32_t K = 0u;
+    bool got = false;
+    for (int a = lane; a < m; a += 32) {
+        const float v = buf[a];
+        int lt = 0, eq = 0;
+        for (int b = 0; b < m; ++b) {
+            const float u = buf[b];
+            lt += u < v;
+            eq += u == v;
+        }
+        if (lt <= r && r < lt + eq) { K = f2key(v); got = true; }
+    }
+    const uint32_t who = __ballot_sync(0xFFFFFFFFu, got);
+    K = __shfl_sync(0xFFFFFFFFu, K, who ? __ffs(who) - 1 : 0);
+    __syncwarp();
+    return K;
 }
 
 // In-place stable compaction of (keys, idx)[0..cnt) to the entries in bins <= c.bin;

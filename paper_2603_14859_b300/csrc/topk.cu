@@ -1244,7 +1244,7 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
         // 3. exact k-th distance and the certificate
         bool cert = false;
         if (cnt >= P.k) {
-            K = warp_select(kj, cnt, P.k - 1, 4, hist, lane);
+            K = warp_select_exact(kj, cnt, P.k - 1, hist, (float*)sbuf, 2 * B.sortcap, lane);
             const float dk = key2f(K);
             dbound = dk;
             const float yn = P.ynorm[j];

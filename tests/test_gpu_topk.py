@@ -122,6 +122,30 @@ def test_ties_resolved_by_index():
         assert idx[0].cpu().tolist() == [17, 300, 450]
 
 
+def test_many_ties_at_the_kth_distance():
+    """Ties that fill the k-th distance's bin past the gather capacity (radix fallback)
+    and a scan whose distances all tie (a single distinct value): the accepted set is
+    the lowest indices, in every exact mode."""
+    from paper_2603_14859_b300 import api
+    W = S.workload("brain_fdg_2tcm", J=4, N_per_model=4)
+    lo, hi = S.PRIORS[S.TCM2_IRR]
+    th = api.sample_prior(5, S.TCM2_IRR, lo, hi, 600)
+    x = api.simulate(S.TCM2_IRR, W.ts, W.te, W.inp, th)
+    x[300:500] = x[17]
+    y = x[17:18].clone()
+    w = W.weights.astype(np.float32)
+    for prec in (0, 2):
+        idx, dist = api.discrepancy_topk(y, x, W.L, w, 10, prec)
+        assert idx[0].cpu().tolist() == [17] + list(range(300, 309))
+        assert torch.all(dist[0] == 0)
+    xe = x[:250].clone()
+    xe[:] = x[40]
+    for prec in (0, 1, 2):
+        idx, dist = api.discrepancy_topk(y, xe, W.L, w, 10, prec)
+        assert idx[0].cpu().tolist() == list(range(10))
+        assert torch.all(dist[0] == dist[0, 0])
+
+
 def test_argument_errors():
     from paper_2603_14859_b300 import api
     from paper_2603_14859_b300._lib import AbcError
