@@ -222,8 +222,8 @@ int abc_discrepancy_topk_noalloc(const float* y_dev, int64_t J, int32_t ldy, con
  *               (ABC_FP32 voxels whose tensor-core result could not be
  *               certified, or whose candidate list overflowed; exact results);
  *   status[2] = number of voxels with more candidates tied at the k-th
- *               distance than the final sort holds (those ties are cut in
- *               list order rather than by index);
+ *               distance than the final sort holds (the ties kept are then
+ *               chosen by a selection on their draw indices: still the lowest);
  *   status[3] = ABC_BF16_RESCORE voxels whose accepted set could not be
  *               certified exact from the bf16 error bound (the 4k net may
  *               have missed a member of the exact top-k);

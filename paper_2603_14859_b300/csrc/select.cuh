@@ -147,14 +147,32 @@ __device__ __forceinline__ LinearCut warp_cut_linear(const float* keys, int cnt,
     return c;
 }
 
+// The k-th key with the number of keys strictly below it and equal to it.
+struct KthKey {
+    uint32_t K;
+    int n_less, n_eq;
+};
+
+__device__ __forceinline__ KthKey warp_count_key(const float* keys, int cnt, uint32_t K, int lane) {
+    int lt = 0, eq = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        const uint32_t k = i < cnt ? f2key(keys[i]) : 0xFFFFFFFFu;
+        lt += __popc(__ballot_sync(0xFFFFFFFFu, i < cnt && k < K));
+        eq += __popc(__ballot_sync(0xFFFFFFFFu, i < cnt && k == K));
+    }
+    return KthKey{K, lt, eq};
+}
+
 // Exact key of the given rank (0-based) among keys[0..cnt): the linear cut finds
 // the bin holding it; that bin's keys (at most cap of them) are gathered into
 // buf (this warp's shared memory) and the one of rank rank - below among them is
 // found by counting, for each, the gathered keys below and equal to it.  A bin
 // with more than cap keys falls back to the four-digit radix select.  Returns
-// the order-preserving integer image of the key (as warp_select with 4 levels).
-__device__ __forceinline__ uint32_t warp_select_exact(const float* keys, int cnt, int rank, uint32_t* hist,
-                                                      float* buf, int cap, int lane) {
+// the order-preserving integer image of the key (as warp_select with 4 levels)
+// and the counts of keys below and equal to it.
+__device__ __forceinline__ KthKey warp_select_exact(const float* keys, int cnt, int rank, uint32_t* hist,
+                                                    float* buf, int cap, int lane) {
     const LinearCut c = warp_cut_linear(keys, cnt, rank, hist, lane);
     if (c.scale == 0.0f) {
         // a single distinct value, or a range too wide for fp32 bins
@@ -165,10 +183,10 @@ __device__ __forceinline__ uint32_t warp_select_exact(const float* keys, int cnt
             mn = fminf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
             mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
         }
-        if (mn == mx) return f2key(mn);
-        return warp_select(keys, cnt, rank, 4, hist, lane);
+        if (mn == mx) return KthKey{f2key(mn), 0, cnt};
+        return warp_count_key(keys, cnt, warp_select(keys, cnt, rank, 4, hist, lane), lane);
     }
-    if (c.inbin > cap) return warp_select(keys, cnt, rank, 4, hist, lane);
+    if (c.inbin > cap) return warp_count_key(keys, cnt, warp_select(keys, cnt, rank, 4, hist, lane), lane);
     int m = 0;
     for (int base = 0; base < cnt; base += 32) {
         const int i = base + lane;
@@ -181,6 +199,7 @@ __device__ __forceinline__ uint32_t warp_select_exact(const float* keys, int cnt
     __syncwarp();
     const int r = rank - c.below;
     uint32_t K = 0u;
+    int nlt = 0, neq = 0;
     bool got = false;
     for (int a = lane; a < m; a += 32) {
         const float v = buf[a];
@@ -190,12 +209,89 @@ __device__ __forceinline__ uint32_t warp_select_exact(const float* keys, int cnt
             lt += u < v;
             eq += u == v;
         }
-        if (lt <= r && r < lt + eq) { K = f2key(v); got = true; }
+        if (lt <= r && r < lt + eq) { K = f2key(v); nlt = lt; neq = eq; got = true; }
     }
     const uint32_t who = __ballot_sync(0xFFFFFFFFu, got);
-    K = __shfl_sync(0xFFFFFFFFu, K, who ? __ffs(who) - 1 : 0);
+    const int src = who ? __ffs(who) - 1 : 0;
+    K = __shfl_sync(0xFFFFFFFFu, K, src);
+    nlt = __shfl_sync(0xFFFFFFFFu, nlt, src);
+    neq = __shfl_sync(0xFFFFFFFFu, neq, src);
     __syncwarp();
-    return K;
+    return KthKey{K, c.below + nlt, neq};
+}
+
+// Radix select over the draw indices (non-negative int32) of the entries whose
+// key equals K: the index of the given rank among them.  hist: 256 words.
+__device__ __forceinline__ uint32_t warp_select_tie_index(const float* keys, const int32_t* idx, int cnt, uint32_t K,
+                                                          int rank, uint32_t* hist, int lane) {
+    uint32_t prefix = 0;
+    int r = rank;
+    for (int lv = 0; lv < 4; ++lv) {
+        const int shift = 24 - 8 * lv;
+        const uint32_t mask = lv == 0 ? 0u : (0xFFFFFFFFu << (shift + 8));
+#pragma unroll
+        for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0;
+        __syncwarp();
+        for (int base = 0; base < cnt; base += 32) {
+            const int i = base + lane;
+            const uint32_t v = i < cnt ? (uint32_t)idx[i] : 0u;
+            const bool in = i < cnt && f2key(keys[i]) == K && (v & mask) == prefix;
+            const uint32_t bin = in ? (v >> shift) & 255u : (0x100u | (uint32_t)lane);
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin);
+            if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+        }
+        __syncwarp();
+        uint32_t loc[8], sum = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) { loc[b] = hist[lane * 8 + b]; sum += loc[b]; }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        uint32_t cum = incl - sum;
+        int found = -1, newr = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            if (found < 0 && cum + loc[b] > (uint32_t)r) { found = lane * 8 + b; newr = r - (int)cum; }
+            cum += loc[b];
+        }
+        const uint32_t who = __ballot_sync(0xFFFFFFFFu, found >= 0);
+        const int src = who ? __ffs(who) - 1 : 31;
+        const int bin = __shfl_sync(0xFFFFFFFFu, found, src);
+        r = __shfl_sync(0xFFFFFFFFu, newr, src);
+        prefix |= (uint32_t)(bin < 0 ? 255 : bin) << shift;
+        __syncwarp();
+    }
+    return prefix;
+}
+
+// In-place stable compaction to the entries with key < K, or key == K and index <= Ti.
+__device__ __forceinline__ int warp_compact_ties(float* keys, int32_t* idx, int cnt, uint32_t K, uint32_t Ti,
+                                                 int lane) {
+    int out = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        float k = 0.0f;
+        int32_t id = 0;
+        bool keep = false;
+        if (i < cnt) {
+            k = keys[i];
+            id = idx[i];
+            const uint32_t kk = f2key(k);
+            keep = kk < K || (kk == K && (uint32_t)id <= Ti);
+        }
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+        const int pos = out + __popc(bal & ((1u << lane) - 1u));
+        if (keep) {
+            keys[pos] = k;
+            idx[pos] = id;
+        }
+        out += __popc(bal);
+    }
+    __syncwarp();
+    return out;
 }
 
 // In-place stable compaction of (keys, idx)[0..cnt) to the entries in bins <= c.bin;

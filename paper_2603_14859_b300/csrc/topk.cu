@@ -1160,6 +1160,7 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
         else if (cnt < P.kt) atomicAdd(&B.status[6], 1);
     }
     uint32_t K = 0;
+    int n_less = -1, n_eq = -1;                   // keys below / at K (-1: not counted yet)
     float dbound = __int_as_float(0x7F800000);   // exact k-th distance of the net: bounds the true one
     if (!scan) {
         // 1. the net: every draw outside it has computed key > T_out
@@ -1244,7 +1245,10 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
         // 3. exact k-th distance and the certificate
         bool cert = false;
         if (cnt >= P.k) {
-            K = warp_select_exact(kj, cnt, P.k - 1, hist, (float*)sbuf, 2 * B.sortcap, lane);
+            const KthKey kth = warp_select_exact(kj, cnt, P.k - 1, hist, (float*)sbuf, 2 * B.sortcap, lane);
+            K = kth.K;
+            n_less = kth.n_less;
+            n_eq = kth.n_eq;
             const float dk = key2f(K);
             dbound = dk;
             const float yn = P.ynorm[j];
@@ -1331,9 +1335,21 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
     }
     // 4. keep everything at or below the exact k-th distance, sort by (distance, index)
     if (cnt > P.k) {
-        const int gq = warp_compact(kj, ij, cnt, K, P.sortcap, lane);
-        if (gq > P.sortcap && lane == 0) atomicAdd(&B.status[2], 1);
-        cnt = gq < P.sortcap ? gq : P.sortcap;
+        if (n_less < 0) {
+            const KthKey c = warp_count_key(kj, cnt, K, lane);
+            n_less = c.n_less;
+            n_eq = c.n_eq;
+        }
+        if (n_less + n_eq > P.sortcap) {
+            // more entries at the k-th distance than the sort holds: keep the ties with the
+            // lowest draw indices (global by now), chosen by a selection on the indices
+            if (lane == 0) atomicAdd(&B.status[2], 1);
+            const uint32_t Ti = warp_select_tie_index(kj, ij, cnt, K, P.k - n_less - 1, hist, lane);
+            cnt = warp_compact_ties(kj, ij, cnt, K, Ti, lane);
+        } else {
+            const int gq = warp_compact(kj, ij, cnt, K, P.sortcap, lane);
+            cnt = gq < P.sortcap ? gq : P.sortcap;
+        }
     }
     int n2 = 32;
     while (n2 < cnt) n2 <<= 1;
