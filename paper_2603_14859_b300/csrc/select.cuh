@@ -115,11 +115,20 @@ __device__ __forceinline__ LinearCut warp_cut_linear(const float* keys, int cnt,
 #pragma unroll
     for (int b = 0; b < 8; ++b) hist[lane * 8 + b] = 0;
     __syncwarp();
-    for (int base = 0; base < cnt; base += 32) {
-        const int i = base + lane;
-        const uint32_t bin = i < cnt ? (uint32_t)linear_bin(keys[i], c) : (0x100u | (uint32_t)lane);
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin);
-        if (i < cnt && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+    for (int base = 0; base < cnt; base += 128) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + 32 * u + lane;
+            v[u] = i < cnt ? keys[i] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + 32 * u + lane;
+            const uint32_t bin = i < cnt ? (uint32_t)linear_bin(v[u], c) : (0x100u | (uint32_t)lane);
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin);
+            if (i < cnt && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+        }
     }
     __syncwarp();
     uint32_t loc[8], sum = 0;
@@ -300,24 +309,31 @@ __device__ __forceinline__ int warp_compact_cut(float* keys, int32_t* idx, int c
                                                 float& kmax) {
     int out = 0;
     float mx = -3.0e38f;
-    for (int base = 0; base < cnt; base += 32) {
-        const int i = base + lane;
-        float k = 0.0f;
-        int32_t id = 0;
-        bool keep = false;
-        if (i < cnt) {
-            k = keys[i];
-            id = idx[i];
-            keep = linear_bin(k, c) <= c.bin;
+    // four rows of 32 read before any is written back: every write goes to a position
+    // below the batch's first unread entry, so reading ahead is safe in place
+    for (int base = 0; base < cnt; base += 128) {
+        float k[4];
+        int32_t id[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + 32 * u + lane;
+            k[u] = i < cnt ? keys[i] : 0.0f;
+            id[u] = i < cnt ? idx[i] : 0;
         }
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
-        const int pos = out + __popc(bal & ((1u << lane) - 1u));
-        if (keep) {
-            keys[pos] = k;
-            idx[pos] = id;
-            mx = fmaxf(mx, k);
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + 32 * u + lane;
+            const bool keep = i < cnt && linear_bin(k[u], c) <= c.bin;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+            const int pos = out + __popc(bal & ((1u << lane) - 1u));
+            if (keep) {
+                keys[pos] = k[u];
+                idx[pos] = id[u];
+                mx = fmaxf(mx, k[u]);
+            }
+            out += __popc(bal);
         }
-        out += __popc(bal);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
@@ -331,23 +347,29 @@ __device__ __forceinline__ int warp_compact_cut(float* keys, int32_t* idx, int c
 // may exceed cap).
 __device__ __forceinline__ int warp_compact(float* keys, int32_t* idx, int cnt, uint32_t T, int cap, int lane) {
     int out = 0;
-    for (int base = 0; base < cnt; base += 32) {
-        const int i = base + lane;
-        float k = 0.0f;
-        int32_t id = 0;
-        bool keep = false;
-        if (i < cnt) {
-            k = keys[i];
-            id = idx[i];
-            keep = f2key(k) <= T;
+    // four rows of 32 read ahead (safe in place: writes land below the batch)
+    for (int base = 0; base < cnt; base += 128) {
+        float k[4];
+        int32_t id[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + 32 * u + lane;
+            k[u] = i < cnt ? keys[i] : 0.0f;
+            id[u] = i < cnt ? idx[i] : 0;
         }
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
-        const int pos = out + __popc(bal & ((1u << lane) - 1u));
-        if (keep && pos < cap) {
-            keys[pos] = k;
-            idx[pos] = id;
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = base + 32 * u + lane;
+            const bool keep = i < cnt && f2key(k[u]) <= T;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+            const int pos = out + __popc(bal & ((1u << lane) - 1u));
+            if (keep && pos < cap) {
+                keys[pos] = k[u];
+                idx[pos] = id[u];
+            }
+            out += __popc(bal);
         }
-        out += __popc(bal);
     }
     __syncwarp();
     return out;
