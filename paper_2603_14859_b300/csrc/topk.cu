@@ -74,6 +74,10 @@ constexpr int ORDER_BUCKET_BITS = 18;
 constexpr int ORDER_BUCKETS = 1 << ORDER_BUCKET_BITS;   // counting-sort buckets
 constexpr int MAX_PILOT_LEVELS = 4;
 constexpr int ROW_LD = 36;                     // floats per epilogue thread's key row (16-byte rows, conflict-free)
+// A pilot level with a small target rank keeps each voxel's r smallest keys per
+// epilogue thread in shared memory (the key rows and compaction histograms,
+// unused in that mode): at most this many.
+constexpr int TOPR_MAX = (128 * ROW_LD + 4 * 256) / 128;
 constexpr int MAX_ITEMS = 64;                 // scans per batched launch
 
 struct Weights {
@@ -657,6 +661,8 @@ struct __align__(64) ItemTc {
     const int32_t* ktile;        // kept draw tiles per voxel tile (null: every tile)
     const int32_t* kcount;
     int64_t kstride;
+    int rsel;                    // > 0: pilot that keeps the rsel smallest keys per voxel, no lists
+    float* thr_out;              // ... and writes its threshold here
 };
 
 struct BatchTc {
@@ -751,11 +757,75 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
     }
 }
 
+// Element b (0..31, any lane-varying value) of a register array, by a select tree.
+__device__ __forceinline__ float pick32(const float (&v)[32], int b) {
+    float l4[16], l3[8], l2[4], l1[2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) l4[i] = (b & 1) ? v[2 * i + 1] : v[2 * i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) l3[i] = (b & 2) ? l4[2 * i + 1] : l4[2 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) l2[i] = (b & 4) ? l3[2 * i + 1] : l3[2 * i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) l1[i] = (b & 8) ? l2[2 * i + 1] : l2[2 * i];
+    return (b & 16) ? l1[1] : l1[0];
+}
+
+// Per-thread state of a top-r pilot: the voxel's kept keys A[i * 128] (i < n_in,
+// unordered), their maximum amax at position imax once n_in = r, and the
+// quick-reject threshold thr = min(thr_in, amax) (thr_in alone until r keys are in).
+struct TopR {
+    float* A;
+    int r, n_in, imax;
+    float amax, thr_in, thr;
+};
+
+// One 32-column chunk of a top-r pilot: keys <= thr join the kept set (the
+// largest kept key leaves once r are kept), so the set ends as the r smallest
+// keys that are <= thr_in.  Rare after the first tiles.
+__device__ __forceinline__ void topr_chunk(TopR& S, float (&v)[32], int64_t n0, int64_t N) {
+    if (n0 + 32 > N) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (n0 + i >= N) v[i] = __int_as_float(0x7F800000);
+    }
+    const float g0 = min8(v, 0), g1 = min8(v, 8), g2 = min8(v, 16), g3 = min8(v, 24);
+    float gm;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(gm) : "f"(g0), "f"(g1), "f"(g2));
+    if (fminf(gm, g3) > S.thr) return;
+    uint32_t m = 0;
+    if (g0 <= S.thr) m |= mask8(v, 0, S.thr);
+    if (g1 <= S.thr) m |= mask8(v, 8, S.thr) << 8;
+    if (g2 <= S.thr) m |= mask8(v, 16, S.thr) << 16;
+    if (g3 <= S.thr) m |= mask8(v, 24, S.thr) << 24;
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        const float x = pick32(v, b);
+        if (S.n_in < S.r) {
+            S.A[S.n_in * 128] = x;
+            if (S.n_in == 0 || x > S.amax) { S.amax = x; S.imax = S.n_in; }
+            if (++S.n_in == S.r) S.thr = fminf(S.thr_in, S.amax);
+        } else if (x < S.amax) {
+            S.A[S.imax * 128] = x;
+            float mx = S.A[0];
+            int im = 0;
+            for (int i = 1; i < S.r; ++i) {
+                const float a = S.A[i * 128];
+                if (a > mx) { mx = a; im = i; }
+            }
+            S.amax = mx;
+            S.imax = im;
+            S.thr = fminf(S.thr_in, mx);
+        }
+    }
+}
+
 // Persistent fused kernel over the (scan, 128-voxel tile) work items of a batch,
 // handed out round-robin in the order of the work index space (costliest
 // scans first).  All roles walk the same sequence; the shared-memory ring and
 // the TMEM accumulators keep their phases across items.
-template <int NKB, int STAGES, int BN, bool DUMP>
+template <int NKB, int STAGES, int BN, bool DUMP, bool TOPR>
 __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant__ BatchTc P) {
     constexpr int B_KBLK_BYTES = BN * KBLK * 2;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -920,6 +990,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
             const bool valid = j < I.J;
             float thr = valid ? (I.thr0 ? I.thr0[j] : 3.0e38f) : -3.0e38f;
             int cnt = 0;
+            TopR S{sRow + (threadIdx.x - 64), TOPR ? I.rsel : 0, 0, 0, -3.0e38f, thr, thr};
             for (int t = 0; t < ntiles; ++t, ++gt) {
                 const uint32_t acc = gt & 1u;
                 const uint32_t aph = (gt >> 1) & 1u;
@@ -950,13 +1021,14 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                         float v[32];
 #pragma unroll
                         for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-                        epilogue_chunk(R, v, nbase + c * 32, j, thr, cnt, sRow + (threadIdx.x - 64) * ROW_LD);
+                        if constexpr (TOPR) topr_chunk(S, v, nbase + c * 32, R.N);
+                        else epilogue_chunk(R, v, nbase + c * 32, j, thr, cnt, sRow + (threadIdx.x - 64) * ROW_LD);
                     }
                 }
                 ptx::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&tempty[acc]));
-                if (DUMP) continue;
+                if (DUMP || TOPR) continue;
                 // compaction of lists that might not fit the next tile
                 // a list without a threshold yet (the coarsest pilot) is first cut early, at
                 // lim0: from then on far fewer keys pass than the everything of a +inf start
@@ -973,8 +1045,16 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                 }
             }
             if (valid && !DUMP && !stop) {
-                atomicOr(&I.cnt[j], cnt);      // cnt[] was zeroed; keeps the overflow bit
-                I.thr[j] = thr;
+                if (TOPR) {
+                    // the r-th smallest key, rounded up to its 24-bit prefix (as the list
+                    // pilots' three-digit selection gives it), or none
+                    const float t = S.n_in == S.r ? key2f(f2key(S.amax) | 0xFFu) : 3.0e38f;
+                    I.thr_out[j] = t;
+                    if (t >= 3.0e38f) atomicAdd(&P.status[7], 1);
+                } else {
+                    atomicOr(&I.cnt[j], cnt);      // cnt[] was zeroed; keeps the overflow bit
+                    I.thr[j] = thr;
+                }
             }
         }
     }
@@ -1436,21 +1516,21 @@ int num_sms() {
     return sms[dev];
 }
 
-template <int NKB, int BN, bool DUMP>
+template <int NKB, int BN, bool DUMP, bool TOPR>
 int launch_tc(const BatchTc& P, int ctas_per_sm, cudaStream_t s) {
     constexpr int S = stages_for(NKB, BN);
     const size_t smem = tc_smem_bytes(NKB, BN);
     static bool configured = false;
     static int max_resident = 1;
     if (!configured) {
-        VPET_CUDA(cudaFuncSetAttribute(k_tc_topk<NKB, S, BN, DUMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        VPET_CUDA(cudaFuncSetAttribute(k_tc_topk<NKB, S, BN, DUMP, TOPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         // all of the unified L1 / shared storage as shared memory, so that the
         // residency the tuning asks for is actually available
-        VPET_CUDA(cudaFuncSetAttribute(k_tc_topk<NKB, S, BN, DUMP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        VPET_CUDA(cudaFuncSetAttribute(k_tc_topk<NKB, S, BN, DUMP, TOPR>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        (int)cudaSharedmemCarveoutMaxShared));
         // residency from the limits that apply: shared memory, registers, TMEM columns
         cudaFuncAttributes fa;
-        VPET_CUDA(cudaFuncGetAttributes(&fa, k_tc_topk<NKB, S, BN, DUMP>));
+        VPET_CUDA(cudaFuncGetAttributes(&fa, k_tc_topk<NKB, S, BN, DUMP, TOPR>));
         int dev = 0, smem_sm = 0, resv = 0;
         VPET_CUDA(cudaGetDevice(&dev));
         VPET_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
@@ -1471,24 +1551,25 @@ int launch_tc(const BatchTc& P, int ctas_per_sm, cudaStream_t s) {
     if (grid > total) grid = total;
     if (grid < 1) return ABC_OK;
     g_last_grid = grid;
-    k_tc_topk<NKB, S, BN, DUMP><<<(unsigned)grid, TC_THREADS, smem, s>>>(P);
+    k_tc_topk<NKB, S, BN, DUMP, TOPR><<<(unsigned)grid, TC_THREADS, smem, s>>>(P);
     VPET_LAUNCH_CHECK();
     return ABC_OK;
 }
 
+// topr: every item of the batch is a top-r pilot (rsel > 0)
 template <bool DUMP>
-int dispatch_tc(int nkb, int bn, const BatchTc& P, int ctas_per_sm, cudaStream_t s) {
+int dispatch_tc(int nkb, int bn, const BatchTc& P, int ctas_per_sm, cudaStream_t s, bool topr = false) {
     if (bn == 128) {
         switch (nkb) {
-            case 1: return launch_tc<1, 128, DUMP>(P, ctas_per_sm, s);
-            case 2: return launch_tc<2, 128, DUMP>(P, ctas_per_sm, s);
-            case 3: return launch_tc<3, 128, DUMP>(P, ctas_per_sm, s);
+            case 1: return topr ? launch_tc<1, 128, false, true>(P, ctas_per_sm, s) : launch_tc<1, 128, DUMP, false>(P, ctas_per_sm, s);
+            case 2: return topr ? launch_tc<2, 128, false, true>(P, ctas_per_sm, s) : launch_tc<2, 128, DUMP, false>(P, ctas_per_sm, s);
+            case 3: return topr ? launch_tc<3, 128, false, true>(P, ctas_per_sm, s) : launch_tc<3, 128, DUMP, false>(P, ctas_per_sm, s);
         }
     } else if (!DUMP && bn == 64) {
         switch (nkb) {
-            case 1: return launch_tc<1, 64, false>(P, ctas_per_sm, s);
-            case 2: return launch_tc<2, 64, false>(P, ctas_per_sm, s);
-            case 3: return launch_tc<3, 64, false>(P, ctas_per_sm, s);
+            case 1: return topr ? launch_tc<1, 64, false, true>(P, ctas_per_sm, s) : launch_tc<1, 64, false, false>(P, ctas_per_sm, s);
+            case 2: return topr ? launch_tc<2, 64, false, true>(P, ctas_per_sm, s) : launch_tc<2, 64, false, false>(P, ctas_per_sm, s);
+            case 3: return topr ? launch_tc<3, 64, false, true>(P, ctas_per_sm, s) : launch_tc<3, 64, false, false>(P, ctas_per_sm, s);
         }
     }
     vpet::set_error("unsupported tile shape (K-blocks %d, BN %d)", nkb, bn);
@@ -1787,7 +1868,11 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     for (int lv = maxlev - 1; lv >= 0; --lv) {
         memset(&T, 0, sizeof T);
         memset(&PB, 0, sizeof PB);
-        int m = 0;
+        int m = 0, mp = 0;
+        // a level whose ranks are all small runs as top-r pilots (one kernel variant per launch)
+        bool lev_topr = true;
+        for (int i = 0; i < n; ++i)
+            if (BL.lay[i].nlev > lv && BL.lay[i].lev_rank[lv] > TOPR_MAX) lev_topr = false;
         for (int oi = 0; oi < n; ++oi) {
             const int i = order[oi];
             const Layout& L = BL.lay[i];
@@ -1806,18 +1891,28 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
                 T.item[m].kstride = L.nt64;
             }
             T.vt_prefix[m + 1] = T.vt_prefix[m] + L.Jp / BM;
-            PB.item[m] = PilotItem{ptr[i].keys, ptr[i].cnt, ptr[i].thr0, L.J, L.C, r};
-            PB.v_prefix[m + 1] = PB.v_prefix[m] + L.J;
+            if (lev_topr) {
+                // small rank: the kernel keeps each voxel's r smallest keys itself and
+                // writes the threshold; no lists, no selection pass
+                T.item[m].rsel = r;
+                T.item[m].thr_out = ptr[i].thr0;
+            } else {
+                PB.item[mp] = PilotItem{ptr[i].keys, ptr[i].cnt, ptr[i].thr0, L.J, L.C, r};
+                PB.v_prefix[mp + 1] = PB.v_prefix[mp] + L.J;
+                ++mp;
+            }
             ++m;
         }
         T.n_items = m;
         T.status = status;
         T.counter = counters + (lv + 1);
-        PB.n_items = m;
+        PB.n_items = mp;
         PB.status = status;
-        if ((rc = dispatch_tc<false>(nkb, tu.bn, T, tu.ctas_per_sm, s))) return rc;
-        k_pilot_threshold<<<(unsigned)vpet_ceil_div(PB.v_prefix[m], 8), 256, 0, s>>>(PB);
-        VPET_LAUNCH_CHECK();
+        if ((rc = dispatch_tc<false>(nkb, tu.bn, T, tu.ctas_per_sm, s, lev_topr))) return rc;
+        if (mp > 0) {
+            k_pilot_threshold<<<(unsigned)vpet_ceil_div(PB.v_prefix[mp], 8), 256, 0, s>>>(PB);
+            VPET_LAUNCH_CHECK();
+        }
     }
     // draw tiles the main pass can skip (needs the pilot thresholds and the ordered draws)
     unsigned long long* tally = (unsigned long long*)(wsb + 192);
