@@ -361,11 +361,11 @@ __global__ void k_order_scatter(const float* __restrict__ feat, const uint32_t* 
 // delta = bf16(yh) - yh: c0 = -2 delta . yh and dn = ||delta|| (certificate).
 // Weighted sums of the three consecutive thirds of a TAC (the features of the
 // tile bound), computed by a warp; every lane gets them.
-__device__ __forceinline__ void seg_features(const float* r, int L, const Weights& W, int lane, float (&f)[3]) {
+__device__ __forceinline__ void seg_features(const float* r, int L, const float* w, int lane, float (&f)[3]) {
     f[0] = f[1] = f[2] = 0.0f;
     for (int l = lane; l < L; l += 32) {
         const int c = (3 * l) / L;
-        const float v = W.w[l] * r[l];
+        const float v = w[l] * r[l];
         f[0] += c == 0 ? v : 0.0f;
         f[1] += c == 1 ? v : 0.0f;
         f[2] += c == 2 ? v : 0.0f;
@@ -375,11 +375,29 @@ __device__ __forceinline__ void seg_features(const float* r, int L, const Weight
     f[2] = warp_sum(f[2]);
 }
 
+// The frame weights, their square roots and the centring means in shared memory:
+// read by lane-varying frame index, which the kernel parameter space would
+// serialise across the warp.
+struct FrameConsts {
+    float w[MAXL], sw[MAXL], mu[MAXL];
+};
+
+__device__ __forceinline__ void stage_frame_consts(FrameConsts& S, const Weights& W, const float* mu, int L) {
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        S.w[l] = W.w[l];
+        S.sw[l] = W.sw[l];
+        S.mu[l] = mu[l];
+    }
+    __syncthreads();
+}
+
 // Row j of A is voxel perm[j] (perm = null: voxel j); fy[3 j + c] = its segment features.
 __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int ldy, int L, int Kp, int mode,
                          Weights W, const float* __restrict__ mu, const int32_t* __restrict__ perm,
                          __nv_bfloat16* __restrict__ A, float* __restrict__ ynorm, float* __restrict__ c0,
                          float* __restrict__ dn, float* __restrict__ fy) {
+    __shared__ FrameConsts F;
+    stage_frame_consts(F, W, mu, L);
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= Jp) return;
@@ -396,7 +414,7 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
     const float* yr = y + (perm ? (int64_t)perm[j] : j) * ldy;
     float ss = 0.0f, sc = 0.0f, sd = 0.0f;
     for (int l = lane; l < L; l += 32) {
-        const float v = W.sw[l] * (yr[l] - mu[l]);
+        const float v = F.sw[l] * (yr[l] - F.mu[l]);
         ss = fmaf(v, v, ss);
         const float dl = __bfloat162float(bf(v)) - v;       // exact in fp32
         sc = fmaf(dl, v, sc);
@@ -406,7 +424,7 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
     sc = warp_sum(sc);
     sd = warp_sum(sd);
     float f[3];
-    seg_features(yr, L, W, lane, f);
+    seg_features(yr, L, F.w, lane, f);
     if (lane == 0) {
         ynorm[j] = ss;
         c0[j] = -2.0f * sc;
@@ -420,7 +438,7 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
         if (mode == ABC_FP32) {
             if (e < 3 * L) {
                 const int l = e % L;
-                const float v = W.sw[l] * (yr[l] - mu[l]);
+                const float v = F.sw[l] * (yr[l] - F.mu[l]);
                 const float hi = __bfloat162float(bf(v));
                 out = e < 2 * L ? hi : v - hi;
             } else if (e < 3 * L + 3) {
@@ -429,12 +447,12 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
         } else if (mode == ABC_SPLIT_DRAWS) {
             if (e < 2 * L) {
                 const int l = e % L;
-                out = W.sw[l] * (yr[l] - mu[l]);                // the same bf16 row against x_hi and x_lo
+                out = F.sw[l] * (yr[l] - F.mu[l]);              // the same bf16 row against x_hi and x_lo
             } else if (e < 2 * L + 3) {
                 out = 1.0f;
             }
         } else {
-            if (e < L) out = W.sw[e] * (yr[e] - mu[e]);
+            if (e < L) out = F.sw[e] * (yr[e] - F.mu[e]);
             else if (e < L + 3) out = 1.0f;
         }
         row[e] = bf(out);
@@ -449,6 +467,8 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
                          Weights W, const float* __restrict__ mu, const int32_t* __restrict__ xperm,
                          __nv_bfloat16* __restrict__ B, float* __restrict__ fx, float* __restrict__ xs,
                          int ldxs) {
+    __shared__ FrameConsts F;
+    stage_frame_consts(F, W, mu, L);
     const int lane = threadIdx.x & 31;
     const int64_t n = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (n >= Np) return;
@@ -461,7 +481,7 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
     for (int l = lane; l < ldxs; l += 32) xs[n * ldxs + l] = l < L ? xr[l] : 0.0f;
     {
         float f[3];
-        seg_features(xr, L, W, lane, f);
+        seg_features(xr, L, F.w, lane, f);
         if (lane == 0) {
             fx[3 * n] = f[0];
             fx[3 * n + 1] = f[1];
@@ -470,7 +490,7 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
     }
     float ss = 0.0f;
     for (int l = lane; l < L; l += 32) {
-        float v = W.sw[l] * (xr[l] - mu[l]);
+        float v = F.sw[l] * (xr[l] - F.mu[l]);
         if (mode == ABC_BF16_RESCORE) v = __bfloat162float(bf(v));   // norm of the rounded vector
         ss = fmaf(v, v, ss);
     }
@@ -484,7 +504,7 @@ __global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int
         float out = 0.0f;
         if (e < aug) {
             const int l = e % L;
-            const float v = W.sw[l] * (xr[l] - mu[l]);
+            const float v = F.sw[l] * (xr[l] - F.mu[l]);
             const float hi = __bfloat162float(bf(v));
             if (mode == ABC_FP32) out = -2.0f * ((e >= L && e < 2 * L) ? (v - hi) : hi);
             else if (mode == ABC_SPLIT_DRAWS) out = -2.0f * (e >= L ? (v - hi) : hi);
