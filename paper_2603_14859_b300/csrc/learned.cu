@@ -63,12 +63,16 @@ struct FrameW {
 
 // f_l = y_l / s (l < L), f_L = log(s) / 10, s = sqrt(sum_l w_l y_l^2) + 1e-30; one warp per voxel
 __global__ void k_features(const float* __restrict__ y, int64_t J, int ldy, int L, FrameW W, float* __restrict__ f) {
+    // the weights in shared memory: a lane-indexed read of the parameter space is serialised
+    __shared__ float sw[MAXL];
+    for (int l = threadIdx.x; l < L; l += blockDim.x) sw[l] = W.w[l];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= J) return;
     const float* yr = y + j * ldy;
     float ss = 0.0f;
-    for (int l = lane; l < L; l += 32) ss = fmaf(W.w[l] * yr[l], yr[l], ss);
+    for (int l = lane; l < L; l += 32) ss = fmaf(sw[l] * yr[l], yr[l], ss);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
     const float s = sqrtf(ss) + 1e-30f;
@@ -328,6 +332,12 @@ struct NoiseFrames {
 
 __global__ void k_add_noise(const float* __restrict__ x, int64_t N, int ldx, NoiseFrames F, float lambda, float q_lo,
                             float q_hi, uint64_t seed, int64_t first, float* __restrict__ y, int ldy) {
+    __shared__ float s_tmid[MAXL], s_dt[MAXL];
+    for (int l = threadIdx.x; l < F.L; l += blockDim.x) {
+        s_tmid[l] = F.tmid[l];
+        s_dt[l] = F.dt[l];
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t n = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (n >= N) return;
@@ -340,7 +350,7 @@ __global__ void k_add_noise(const float* __restrict__ x, int64_t N, int ldx, Noi
         const int l = lane + 32 * h;
         if (l >= F.L) continue;
         xv[h] = xr[l];
-        const float s = sqrtf(fmaxf(xv[h], 0.0f) * expf(lambda * F.tmid[l]) / F.dt[l]);
+        const float s = sqrtf(fmaxf(xv[h], 0.0f) * expf(lambda * s_tmid[l]) / s_dt[l]);
         sig[h] = s;
         sx = fmaf(xv[h], xv[h], sx);
         ss = fmaf(s, s, ss);
