@@ -1011,13 +1011,17 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
             float thr = valid ? (I.thr0 ? I.thr0[j] : 3.0e38f) : -3.0e38f;
             int cnt = 0;
             TopR S{sRow + (threadIdx.x - 64), TOPR ? I.rsel : 0, 0, 0, -3.0e38f, thr, thr};
+            // the next tile's draw offset is loaded a tile ahead, off the path from the
+            // accumulator's arrival to its first use
+            int tnext = kt_list && ntiles > 0 ? kt_list[0] : 0;
             for (int t = 0; t < ntiles; ++t, ++gt) {
+                const int64_t nbase = (int64_t)(kt_list ? tnext : t) * BN;
+                if (kt_list && t + 1 < ntiles) tnext = kt_list[t + 1];
                 const uint32_t acc = gt & 1u;
                 const uint32_t aph = (gt >> 1) & 1u;
                 if (!ptx::mbar_wait(ptx::smem_u32(&tfull[acc]), aph, WAIT_NS)) { *s_err = 1; }
                 if (__any_sync(0xFFFFFFFFu, *s_err != 0)) { stop = true; break; }
                 ptx::tc_fence_after();
-                const int64_t nbase = (int64_t)(kt_list ? kt_list[t] : t) * BN;
                 const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
                 if (DUMP) {
                     for (int c = 0; c < BN / 32; ++c) {
