@@ -86,18 +86,22 @@ __device__ __forceinline__ uint32_t f2o(float f) {
 __device__ __forceinline__ float o2f(uint32_t k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k); }
 
 // The r-th smallest (0-based) of the n floats in s (shared memory), exactly: a
-// 4-level radix select on the order-preserving integer image, 8 bits per level;
-// hist is 256 words of this warp's shared memory.
-__device__ float warp_kth(const float* s, int n, int r, uint32_t* hist, int lane) {
+// 4-level radix select on the order-preserving integer image, 8 bits per level
+// (lanes with the same digit add their count once); hist is 256 words of this
+// warp's shared memory.
+__device__ float warp_kth_radix(const float* s, int n, int r, uint32_t* hist, int lane) {
     uint32_t prefix = 0;
     for (int lv = 0; lv < 4; ++lv) {
         const int shift = 24 - 8 * lv;
         const uint32_t mask = lv == 0 ? 0u : (0xFFFFFFFFu << (shift + 8));
         for (int b = lane; b < 256; b += 32) hist[b] = 0;
         __syncwarp();
-        for (int i = lane; i < n; i += 32) {
-            const uint32_t k = f2o(s[i]);
-            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            const uint32_t k = i < n ? f2o(s[i]) : 0u;
+            const uint32_t bin = (i < n && (k & mask) == prefix) ? (k >> shift) & 255u : (0x100u | (uint32_t)lane);
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin);
+            if (bin < 256u && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
         }
         __syncwarp();
         uint32_t loc[8], sum = 0;
@@ -126,28 +130,118 @@ __device__ float warp_kth(const float* s, int n, int r, uint32_t* hist, int lane
     return o2f(prefix);
 }
 
-// Order statistics a and a + 1 (clamped to n - 1) of the n floats in s.
-__device__ void warp_pair(const float* s, int n, int a, uint32_t* hist, int lane, float& va, float& vb) {
-    va = warp_kth(s, n, a, hist, lane);
-    if (a + 1 >= n) {
-        vb = va;
-        return;
-    }
-    // the next order statistic: va again if more than a + 1 values are <= va, else the smallest above it
-    int le = 0;
-    float up = __int_as_float(0x7F800000);
+// Order statistics of ranks rk[0..3] (each in [0, n)) of the n floats in s,
+// exactly, with one histogram: 256 equal-width bins over [min, max] locate the
+// bin of each rank; the members of those bins (at most 256 in all) are gathered
+// into hist and each rank resolved by counting within its bin.  Crowded bins
+// (or an unbounded range) take the radix select per rank.
+__device__ void warp_order4(const float* s, int n, const int (&rk)[4], uint32_t* hist, int lane, float (&out)[4]) {
+    float mn = 3.0e38f, mx = -3.0e38f;
     for (int i = lane; i < n; i += 32) {
-        const float v = s[i];
-        le += v <= va;
-        if (v > va) up = fminf(up, v);
+        mn = fminf(mn, s[i]);
+        mx = fmaxf(mx, s[i]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        le += __shfl_xor_sync(0xFFFFFFFFu, le, o);
-        up = fminf(up, __shfl_xor_sync(0xFFFFFFFFu, up, o));
+        mn = fminf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
     }
-    vb = le > a + 1 ? va : up;
+    if (mn == mx) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[q] = mn;
+        return;
+    }
+    const float span = mx - mn;
+    if (!(span < 3.0e38f)) {
+        for (int q = 0; q < 4; ++q) out[q] = warp_kth_radix(s, n, rk[q], hist, lane);
+        return;
+    }
+    const float scale = 256.0f / span;
+    auto bin_of = [&](float v) -> int {
+        const float t = (v - mn) * scale;
+        return t < 255.0f ? (int)t : 255;
+    };
+    for (int b = lane; b < 256; b += 32) hist[b] = 0;
+    __syncwarp();
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const uint32_t bin = i < n ? (uint32_t)bin_of(s[i]) : (0x100u | (uint32_t)lane);
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin);
+        if (bin < 256u && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+    }
+    __syncwarp();
+    uint32_t loc[8], sum = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) { loc[b] = hist[lane * 8 + b]; sum += loc[b]; }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t excl = incl - sum;
+    int tb[4], tbelow[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t c = excl;
+        int found = -1, below = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            if (found < 0 && c + loc[b] > (uint32_t)rk[q]) { found = lane * 8 + b; below = (int)c; }
+            c += loc[b];
+        }
+        const uint32_t who = __ballot_sync(0xFFFFFFFFu, found >= 0);
+        const int src = __ffs(who) - 1;
+        tb[q] = __shfl_sync(0xFFFFFFFFu, found, src);
+        tbelow[q] = __shfl_sync(0xFFFFFFFFu, below, src);
+    }
+    __syncwarp();   // the histogram is in registers now; its words become the gather buffer
+    float* buf = (float*)hist;
+    int m = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        float v = 0.0f;
+        bool in = false;
+        if (i < n) {
+            v = s[i];
+            const int b = bin_of(v);
+            in = b == tb[0] || b == tb[1] || b == tb[2] || b == tb[3];
+        }
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in);
+        const int pos = m + __popc(bal & ((1u << lane) - 1u));
+        if (in && pos < 256) buf[pos] = v;
+        m += __popc(bal);
+    }
+    __syncwarp();
+    if (m > 256) {
+        for (int q = 0; q < 4; ++q) out[q] = warp_kth_radix(s, n, rk[q], hist, lane);
+        return;
+    }
+    float res[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    uint32_t got = 0;
+    for (int a = lane; a < m; a += 32) {
+        const float v = buf[a];
+        const int bv = bin_of(v);
+        int lt = 0, eq = 0;
+        for (int u = 0; u < m; ++u) {
+            const float w = buf[u];
+            if (bin_of(w) == bv) {
+                lt += w < v;
+                eq += w == v;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (tb[q] == bv && tbelow[q] + lt <= rk[q] && rk[q] < tbelow[q] + lt + eq) { res[q] = v; got |= 1u << q; }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t who = __ballot_sync(0xFFFFFFFFu, (got >> q) & 1u);
+        out[q] = __shfl_sync(0xFFFFFFFFu, res[q], who ? __ffs(who) - 1 : 0);
+    }
+    __syncwarp();
 }
+
 
 __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __restrict__ idx, int64_t J,
                             const int8_t* __restrict__ pref, SumParams Q, float* __restrict__ mean,
@@ -214,14 +308,17 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
             // position h = (n - 1) q is formed in fp64 once (exact floor at integer h)
             float qv[2];
             const double qs[2] = {0.025, 0.975};
+            int rk[4];
+            float fr[2], os[4];
             for (int t = 0; t < 2; ++t) {
                 const double h = (n - 1) * qs[t];
                 const int a = (int)floor(h);
-                const float fr = (float)(h - a);
-                float va, vb;
-                warp_pair(vals, n, a, hist, lane, va, vb);
-                qv[t] = fmaf(fr, vb - va, va);
+                fr[t] = (float)(h - a);
+                rk[2 * t] = a;
+                rk[2 * t + 1] = a + 1 < n ? a + 1 : n - 1;
             }
+            warp_order4(vals, n, rk, hist, lane, os);
+            for (int t = 0; t < 2; ++t) qv[t] = fmaf(fr[t], os[2 * t + 1] - os[2 * t], os[2 * t]);
             o0 = mu;
             o1 = n > 1 ? sqrtf(sst / (float)(n - 1)) : 0.0f;
             o2 = qv[0];
