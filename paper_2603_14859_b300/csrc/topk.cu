@@ -1111,6 +1111,7 @@ struct BatchPilot {
 
 __global__ void k_pilot_threshold(const __grid_constant__ BatchPilot B) {
     __shared__ uint32_t hist[8][256];
+    __shared__ float gbuf[8][256];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t g = (int64_t)blockIdx.x * 8 + wid;
     if (g >= B.v_prefix[B.n_items]) return;
@@ -1121,7 +1122,9 @@ __global__ void k_pilot_threshold(const __grid_constant__ BatchPilot B) {
     const int raw = I.cnt[j];
     const int c = raw & 0x3FFFFFFF;
     float t = 3.0e38f;
-    if (!(raw & 0x40000000) && c >= I.r) t = key2f(warp_select(I.keys + j * I.C, c, I.r - 1, 3, hist[wid], lane));
+    // the r-th smallest key, rounded up to its 24-bit prefix
+    if (!(raw & 0x40000000) && c >= I.r)
+        t = key2f(warp_select_exact(I.keys + j * I.C, c, I.r - 1, hist[wid], gbuf[wid], 256, lane).K | 0xFFu);
     if (lane == 0) {
         I.thr0[j] = t;
         I.cnt[j] = 0;
