@@ -260,19 +260,30 @@ __host__ __device__ __forceinline__ void phis(float z, float& p1, float& p2, flo
         return;
     }
     float a1 = 0.0f, a2 = 0.0f, a3 = 0.0f, pw = 1.0f;
+    if (z <= 0.125f) {
+        // |z|^6 / 7! < 1e-9: six terms reach fp32 rounding
 #pragma unroll
-    for (int j = 0; j < 10; ++j) {
-        a1 = fmaf(pw, inv_fact(j + 1), a1);
-        a2 = fmaf(pw, inv_fact(j + 2), a2);
-        a3 = fmaf(pw, inv_fact(j + 3), a3);
-        pw *= -z;
+        for (int j = 0; j < 6; ++j) {
+            a1 = fmaf(pw, inv_fact(j + 1), a1);
+            a2 = fmaf(pw, inv_fact(j + 2), a2);
+            a3 = fmaf(pw, inv_fact(j + 3), a3);
+            pw *= -z;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+            a1 = fmaf(pw, inv_fact(j + 1), a1);
+            a2 = fmaf(pw, inv_fact(j + 2), a2);
+            a3 = fmaf(pw, inv_fact(j + 3), a3);
+            pw *= -z;
+        }
     }
     p1 = a1; p2 = a2; p3 = a3;
 }
 
-__host__ __device__ __forceinline__ float gamma_variate(float t, float tD, float tPmD, float alpha) {
+__host__ __device__ __forceinline__ float gamma_variate(float t, float tD, float inv_tp, float alpha) {
     if (t <= tD) return 0.0f;
-    const float x = (t - tD) / tPmD;
+    const float x = (t - tD) * inv_tp;      // inv_tp = 1 / (t_P - t_D)
     return expf(alpha * (logf(x) + 1.0f - x));
 }
 
@@ -319,7 +330,8 @@ __host__ __device__ void simulate_draw(const SimParams& p, const float* th, floa
             // t_D (h = t - t_D, at least lp_h / 4096) up to lp_h, which resolves the
             // x^alpha onset of the gamma variate.
             float cr0 = input_at(p, t);
-            float g0 = gamma_variate(t, tD, tPmD, alpha);
+            const float inv_tp = 1.0f / tPmD;
+            float g0 = gamma_variate(t, tD, inv_tp, alpha);
             for (int l = lsplit; l < p.L; ++l) {
                 const float ts_l = p.ts[l], te = p.ts[l] + p.dt[l];
                 float integ = 0.0f;
@@ -328,8 +340,8 @@ __host__ __device__ void simulate_draw(const SimParams& p, const float* th, floa
                     const float stop = t < ts_l ? ts_l : te;     // land exactly on frame edges (gaps allowed)
                     const float h = fminf(fminf(stop - t, p.lp_h), fmaxf(t - tD, p.lp_h * (1.0f / 4096.0f)));
                     // a(t) averaged over the step by Simpson's rule; forcing b = (k2 - R1 a) C_r linear
-                    const float gm = gamma_variate(t + 0.5f * h, tD, tPmD, alpha);
-                    const float g1 = gamma_variate(t + h, tD, tPmD, alpha);
+                    const float gm = gamma_variate(t + 0.5f * h, tD, inv_tp, alpha);
+                    const float g1 = gamma_variate(t + h, tD, inv_tp, alpha);
                     const float abar = k2a + gam * (g0 + 4.0f * gm + g1) * (1.0f / 6.0f);
                     const float cr1 = input_at(p, t + h);
                     const float b0 = (k2 - R1 * (k2a + gam * g0)) * cr0;

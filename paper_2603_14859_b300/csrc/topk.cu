@@ -188,12 +188,12 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.off_thr0 = o; o = align256(o + (size_t)s.Jp * sizeof(float));
     s.off_perm = o; o = align256(o + (size_t)s.Jp * sizeof(int32_t));
     s.off_feat = o; o = align256(o + (size_t)3 * s.Jp * sizeof(float) + 8 * sizeof(uint32_t));
-    s.off_hist = o; o = align256(o + (size_t)ORDER_BUCKETS * sizeof(uint32_t));
+    s.off_hist = o; o = align256(o + (size_t)(ORDER_BUCKETS + ORDER_BUCKETS / 1024) * sizeof(uint32_t));
     s.nt64 = s.Np / 64;
     s.nvt = s.Jp / BM;
     s.off_xperm = o; o = align256(o + (size_t)s.Np * sizeof(int32_t));
     s.off_xfeat = o; o = align256(o + (size_t)3 * s.Np * sizeof(float) + 8 * sizeof(uint32_t));
-    s.off_xhist = o; o = align256(o + (size_t)ORDER_BUCKETS * sizeof(uint32_t));
+    s.off_xhist = o; o = align256(o + (size_t)(ORDER_BUCKETS + ORDER_BUCKETS / 1024) * sizeof(uint32_t));
     s.off_fy = o; o = align256(o + (size_t)3 * s.Jp * sizeof(float));
     s.off_fx = o; o = align256(o + (size_t)3 * s.Np * sizeof(float));
     s.off_tbox = o; o = align256(o + (size_t)6 * s.nt64 * sizeof(float));
@@ -326,26 +326,58 @@ __global__ void k_order_hist(const float* __restrict__ feat, const uint32_t* __r
 }
 
 // exclusive scan of the ORDER_BUCKETS counts, in place (one block of 1024 threads)
-__global__ void __launch_bounds__(1024) k_order_scan(uint32_t* __restrict__ hist) {
-    __shared__ uint32_t part[1024];
-    constexpr int PER = ORDER_BUCKETS / 1024;
-    const int t = threadIdx.x;
-    uint32_t s = 0;
-    for (int i = 0; i < PER; ++i) s += hist[t * PER + i];
-    part[t] = s;
+// Exclusive scan of the ORDER_BUCKETS bucket counts in three launches of
+// coalesced 1024-entry blocks: block totals, a scan of the totals, then each
+// block's scan plus its offset.
+constexpr int SCAN_BLOCKS = ORDER_BUCKETS / 1024;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan_1024(uint32_t v, uint32_t* wsum, uint32_t& total) {
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[wp] = incl;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const uint32_t v = t >= o ? part[t - o] : 0u;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    if (wp == 0) {
+        const uint32_t x = wsum[lane];
+        uint32_t xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, xi, o);
+            if (lane >= o) xi += u;
+        }
+        wsum[lane] = xi - x;
+        if (lane == 31) wsum[32] = xi;
     }
-    uint32_t run = part[t] - s;
-    for (int i = 0; i < PER; ++i) {
-        const uint32_t c = hist[t * PER + i];
-        hist[t * PER + i] = run;
-        run += c;
-    }
+    __syncthreads();
+    total = wsum[32];
+    return wsum[wp] + incl - v;
+}
+
+__global__ void __launch_bounds__(1024) k_order_scan_sums(const uint32_t* __restrict__ hist, uint32_t* __restrict__ sums) {
+    __shared__ uint32_t wsum[33];
+    uint32_t total;
+    block_exclusive_scan_1024(hist[blockIdx.x * 1024 + threadIdx.x], wsum, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_order_scan_top(uint32_t* __restrict__ sums) {
+    __shared__ uint32_t wsum[33];
+    uint32_t total;
+    const uint32_t v = threadIdx.x < SCAN_BLOCKS ? sums[threadIdx.x] : 0u;
+    const uint32_t e = block_exclusive_scan_1024(v, wsum, total);
+    if (threadIdx.x < SCAN_BLOCKS) sums[threadIdx.x] = e;
+}
+
+__global__ void __launch_bounds__(1024) k_order_scan(uint32_t* __restrict__ hist, const uint32_t* __restrict__ sums) {
+    __shared__ uint32_t wsum[33];
+    uint32_t total;
+    const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    const uint32_t e = block_exclusive_scan_1024(hist[i], wsum, total);
+    hist[i] = sums[blockIdx.x] + e;
 }
 
 // perm[position] = voxel; voxels of one bucket land in arrival order
@@ -1694,8 +1726,8 @@ bool layout_consistent(const Layout& L) {
     const size_t len[] = {MAXL * 4, (size_t)L.npart * MAXL * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
                           (size_t)L.Jp * L.Kp * 2, (size_t)L.Np * L.Kp * 2, (size_t)L.J * L.C * 4,
                           (size_t)L.J * L.C * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
-                          (size_t)L.Jp * 4, (size_t)3 * L.Jp * 4 + 32, (size_t)ORDER_BUCKETS * 4,
-                          (size_t)L.Np * 4, (size_t)3 * L.Np * 4 + 32, (size_t)ORDER_BUCKETS * 4,
+                          (size_t)L.Jp * 4, (size_t)3 * L.Jp * 4 + 32, (size_t)(ORDER_BUCKETS + ORDER_BUCKETS / 1024) * 4,
+                          (size_t)L.Np * 4, (size_t)3 * L.Np * 4 + 32, (size_t)(ORDER_BUCKETS + ORDER_BUCKETS / 1024) * 4,
                           (size_t)3 * L.Jp * 4, (size_t)3 * L.Np * 4, (size_t)6 * L.nt64 * 4,
                           (size_t)L.nvt * L.nt64 * 4, (size_t)L.nvt * 4, (size_t)L.Np * L.ldxs * 4};
     const int n = (int)(sizeof off / sizeof off[0]);
@@ -1797,7 +1829,9 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             VPET_LAUNCH_CHECK();
             k_order_hist<<<gb, 256, 0, s>>>(p.feat, p.mm, L.J, 0, 1, p.hist);
             VPET_LAUNCH_CHECK();
-            k_order_scan<<<1, 1024, 0, s>>>(p.hist);
+            k_order_scan_sums<<<SCAN_BLOCKS, 1024, 0, s>>>(p.hist, p.hist + ORDER_BUCKETS);
+            k_order_scan_top<<<1, 1024, 0, s>>>(p.hist + ORDER_BUCKETS);
+            k_order_scan<<<SCAN_BLOCKS, 1024, 0, s>>>(p.hist, p.hist + ORDER_BUCKETS);
             VPET_LAUNCH_CHECK();
             k_order_scatter<<<gb, 256, 0, s>>>(p.feat, p.mm, L.J, 0, 1, p.hist, p.perm);
             VPET_LAUNCH_CHECK();
@@ -1816,7 +1850,9 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             VPET_LAUNCH_CHECK();
             k_order_hist<<<gb, 256, 0, s>>>(p.xfeat, p.xmm, L.N, L.nlev, tu.pilot_stride, p.xhist);
             VPET_LAUNCH_CHECK();
-            k_order_scan<<<1, 1024, 0, s>>>(p.xhist);
+            k_order_scan_sums<<<SCAN_BLOCKS, 1024, 0, s>>>(p.xhist, p.xhist + ORDER_BUCKETS);
+            k_order_scan_top<<<1, 1024, 0, s>>>(p.xhist + ORDER_BUCKETS);
+            k_order_scan<<<SCAN_BLOCKS, 1024, 0, s>>>(p.xhist, p.xhist + ORDER_BUCKETS);
             VPET_LAUNCH_CHECK();
             k_order_scatter<<<gb, 256, 0, s>>>(p.xfeat, p.xmm, L.N, L.nlev, tu.pilot_stride, p.xhist, p.xperm);
             VPET_LAUNCH_CHECK();
