@@ -46,7 +46,10 @@ struct SimParams {
     float c[SIM_MAXT];
     float a[SIM_MAXT][3];          // coefficient of Conv(c^(m+1)), i.e. a_m * m!
     float lp_h;                    // lp-ntPET integrator step (min)
+    int lp_ntab;                   // lp-ntPET: C_r tabulated at t = i lp_h, i < lp_ntab (0: none)
 };
+
+constexpr int SIM_MAX_TAB = 4096;
 
 // 1/n! for n = 0..19 (folds to a constant wherever n is known at compile time).
 __host__ __device__ __forceinline__ float inv_fact(int n) {
@@ -289,8 +292,9 @@ __host__ __device__ __forceinline__ float gamma_variate(float t, float tD, float
 
 // ---------------------------------------------------------------- kernel
 // Frame means of one draw: acc[l * SIM_THREADS] receives x_l (acc zeroed by the caller).
+// crtab: C_r at t = i lp_h for i < p.lp_ntab (lp-ntPET; null: evaluate every step).
 template <int MODEL>
-__host__ __device__ void simulate_draw(const SimParams& p, const float* th, float* acc) {
+__host__ __device__ void simulate_draw(const SimParams& p, const float* th, float* acc, const float* crtab = nullptr) {
     if (MODEL == ABC_2TCM_IRR || MODEL == ABC_2TCM_REV) {
         const float K1 = th[0], k2 = th[1], k3 = th[2];
         const float k4 = MODEL == ABC_2TCM_REV ? th[3] : 0.0f;
@@ -343,7 +347,14 @@ __host__ __device__ void simulate_draw(const SimParams& p, const float* th, floa
                     const float gm = gamma_variate(t + 0.5f * h, tD, inv_tp, alpha);
                     const float g1 = gamma_variate(t + h, tD, inv_tp, alpha);
                     const float abar = k2a + gam * (g0 + 4.0f * gm + g1) * (1.0f / 6.0f);
-                    const float cr1 = input_at(p, t + h);
+                    // C_r at the step's end: from the table when that end lies on the lp_h grid
+                    // (every step between frame edges that are themselves on it), the same
+                    // function of the same fp32 time otherwise
+                    const float t1 = t + h;
+                    const float qf = t1 / p.lp_h;
+                    const int qi = (int)qf;
+                    const float cr1 = (crtab && (float)qi == qf && qi < p.lp_ntab && (float)qi * p.lp_h == t1)
+                                          ? crtab[qi] : input_at(p, t1);
                     const float b0 = (k2 - R1 * (k2a + gam * g0)) * cr0;
                     const float b1 = (k2 - R1 * (k2a + gam * g1)) * cr1;
                     float p1, p2, p3;
@@ -372,8 +383,14 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(SimParams p, const flo
     const int64_t n = n0 + tid;
     float* acc = s_acc + tid;
     for (int l = 0; l < p.L; ++l) acc[l * SIM_THREADS] = 0.0f;
+    float* crtab = nullptr;
+    if (MODEL == ABC_LPNTPET && p.lp_ntab > 0) {
+        crtab = s_acc + p.L * SIM_THREADS;
+        for (int i = tid; i < p.lp_ntab; i += SIM_THREADS) crtab[i] = input_at(p, (float)i * p.lp_h);
+        __syncthreads();
+    }
     if (n < N) {
-        simulate_draw<MODEL>(p, theta + n * ldt, acc);
+        simulate_draw<MODEL>(p, theta + n * ldt, acc, crtab);
     }
     __syncthreads();
     // coalesced write-out of the block's rows
@@ -445,7 +462,12 @@ extern "C" int abc_simulate(int32_t model, const abc_frames* fr, const abc_polye
     VPET_ARG(N == 0 || (theta_dev && x_dev), "abc_simulate: null device pointer");
     VPET_ARG(ldx >= fr->L, "abc_simulate: ldx < L");
     if (N == 0) return ABC_OK;
-    const size_t smem = (size_t)p.L * SIM_THREADS * sizeof(float);
+    if (model == ABC_LPNTPET) {
+        const double tend = (double)fr->t_end[fr->L - 1];
+        const double nt = floor(tend / (double)p.lp_h) + 1.0;
+        p.lp_ntab = nt < SIM_MAX_TAB ? (int)nt : SIM_MAX_TAB;
+    }
+    const size_t smem = ((size_t)p.L * SIM_THREADS + (size_t)p.lp_ntab) * sizeof(float);
     const unsigned grid = (unsigned)vpet_ceil_div(N, SIM_THREADS);
     cudaStream_t s = (cudaStream_t)stream;
     switch (model) {
