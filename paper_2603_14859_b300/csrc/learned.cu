@@ -658,10 +658,43 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
         int need_ties = 1;
         bool fast = A.n_pilot > 0, have_med = false;
         if (fast) {
-            // pivots: order statistics of the first n_pilot proposals (an i.i.d. sample)
-            uint32_t piv[2];
-            block_select2(keys, A.n_pilot, A.r_lo, A.r_hi, hist, sh, piv, nullptr);
-            const uint32_t lo = piv[0], hi = piv[1];
+            // pivots: 256 bins over the order-preserving integer image of the first n_pilot
+            // proposals' keys (an i.i.d. sample), each 2^shift integers wide; lo = the lower
+            // edge of the bin holding sample rank r_lo, hi = the upper edge of the bin holding
+            // rank r_hi, so lo <= that order statistic <= ... <= hi exactly
+            uint32_t* redu = (uint32_t*)red;
+            uint32_t kmn = 0xFFFFFFFFu, kmx = 0u;
+            for (int i = threadIdx.x; i < A.n_pilot; i += blockDim.x) {
+                const uint32_t k = f2key(keys[i]);
+                kmn = min(kmn, k);
+                kmx = max(kmx, k);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                kmn = min(kmn, __shfl_xor_sync(0xFFFFFFFFu, kmn, o));
+                kmx = max(kmx, __shfl_xor_sync(0xFFFFFFFFu, kmx, o));
+            }
+            if (lane == 0) { redu[wp] = kmn; redu[16 + wp] = kmx; }
+            for (int b2 = threadIdx.x; b2 < 512; b2 += blockDim.x) hist[b2] = 0;
+            __syncthreads();
+            kmn = redu[0];
+            kmx = redu[16];
+            for (int q = 1; q < nw; ++q) { kmn = min(kmn, redu[q]); kmx = max(kmx, redu[16 + q]); }
+            int shift = 0;
+            while (((kmx - kmn) >> shift) >= 256u) ++shift;
+            for (int i0 = 0; i0 < A.n_pilot; i0 += blockDim.x) {
+                const int i = i0 + threadIdx.x;
+                const uint32_t bin = i < A.n_pilot ? (f2key(keys[i]) - kmn) >> shift : 256u;
+                const uint32_t same = __match_any_sync(0xFFFFFFFFu, bin);
+                if (bin < 256u && lane == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
+            }
+            __syncthreads();
+            if (wp == 0) warp_find_bin(hist, A.r_lo, lane, &sh[0], &sh[1]);
+            if (wp == 1) warp_find_bin(hist, A.r_hi, lane, &sh[2], &sh[3]);
+            __syncthreads();
+            const uint32_t lo = kmn + ((uint32_t)sh[0] << shift);
+            const uint64_t hi64 = (uint64_t)kmn + ((uint64_t)(sh[2] + 1) << shift) - 1u;
+            const uint32_t hi = hi64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)hi64;
             int cl = 0;
             for (int i0 = s0; i0 < s1; i0 += 32) {
                 const int i = i0 + lane;
@@ -678,6 +711,7 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
                 }
             }
             if (lane == 0) { wcnt[wp] = cl; wcnt[16 + wp] = 0; }
+            for (int b2 = threadIdx.x; b2 < 512; b2 += blockDim.x) hist[b2] = 0;
             __syncthreads();
             const int n_c = sh[4];
             int n_lt = 0;
@@ -686,13 +720,73 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
             if (fast) {
                 const int rm = (A.k - 1) / 2;
                 have_med = rm >= n_lt;
-                uint32_t sel[2];
-                int ties[2];
-                block_select2(ckey, n_c, A.k - 1 - n_lt, have_med ? rm - n_lt : A.k - 1 - n_lt, hist, sh, sel,
-                              ties);
-                K = sel[0];
-                Km = sel[1];
-                need_ties = ties[0] + 1;     // k minus the number of keys strictly below K
+                const int rk0 = A.k - 1 - n_lt, rk1 = have_med ? rm - n_lt : rk0;
+                // the candidates' keys lie in [lo, hi]: 256 bins of 2^shift2 integers there,
+                // then the members of the bins holding the two ranks, resolved by counting
+                int shift2 = 0;
+                while (((hi - lo) >> shift2) >= 256u) ++shift2;
+                for (int c0 = 0; c0 < n_c; c0 += blockDim.x) {
+                    const int c = c0 + threadIdx.x;
+                    const uint32_t bin = c < n_c ? (f2key(ckey[c]) - lo) >> shift2 : 256u;
+                    const uint32_t same = __match_any_sync(0xFFFFFFFFu, bin);
+                    if (bin < 256u && lane == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
+                }
+                __syncthreads();
+                if (wp == 0) warp_find_bin(hist, rk0, lane, &sh[0], &sh[1]);
+                if (wp == 1) warp_find_bin(hist, rk1, lane, &sh[2], &sh[3]);
+                __syncthreads();
+                const int b0 = sh[0], r0 = sh[1], b1 = sh[2], r1 = sh[3];
+                const int m0 = (int)hist[b0], m1 = (int)hist[b1];
+                bool small = m0 <= 128 && m1 <= 128;
+                if (small) {
+                    // gather both bins' members (as integer keys) into the two halves of hist
+                    __syncthreads();
+                    if (threadIdx.x < 2) sh[5 + threadIdx.x] = 0;
+                    __syncthreads();
+                    for (int c0 = 0; c0 < n_c; c0 += blockDim.x) {
+                        const int c = c0 + threadIdx.x;
+                        const uint32_t k = c < n_c ? f2key(ckey[c]) : 0u;
+                        const int bin = c < n_c ? (int)((k - lo) >> shift2) : -1;
+                        if (bin == b0) hist[atomicAdd(&sh[5], 1)] = k;
+                        if (bin == b1 && b1 != b0) hist[256 + atomicAdd(&sh[6], 1)] = k;
+                    }
+                    __syncthreads();
+                    // warp 0: the member of rank r0 in bin b0 (and its rank among equal keys);
+                    // warp 1: the member of rank r1 in bin b1
+                    if (wp < 2) {
+                        const uint32_t* mem = (wp == 1 && b1 != b0) ? hist + 256 : hist;
+                        const int m = (wp == 1 && b1 != b0) ? m1 : m0;
+                        const int r = wp == 0 ? r0 : r1;
+                        uint32_t kv = 0u;
+                        int tr = 0;
+                        bool got = false;
+                        for (int a2 = lane; a2 < m; a2 += 32) {
+                            const uint32_t v = mem[a2];
+                            int lt = 0, eq = 0;
+                            for (int u = 0; u < m; ++u) {
+                                lt += mem[u] < v;
+                                eq += mem[u] == v;
+                            }
+                            if (lt <= r && r < lt + eq) { kv = v; tr = r - lt; got = true; }
+                        }
+                        const uint32_t who = __ballot_sync(0xFFFFFFFFu, got);
+                        const int src = who ? __ffs(who) - 1 : 0;
+                        kv = __shfl_sync(0xFFFFFFFFu, kv, src);
+                        tr = __shfl_sync(0xFFFFFFFFu, tr, src);
+                        if (lane == 0) { sh[7 * wp] = (int)kv; if (wp == 0) sh[1] = tr; }
+                    }
+                    __syncthreads();
+                    K = (uint32_t)sh[0];
+                    Km = (uint32_t)sh[7];
+                    need_ties = sh[1] + 1;     // k minus the number of keys strictly below K
+                } else {
+                    uint32_t sel[2];
+                    int ties[2];
+                    block_select2(ckey, n_c, rk0, rk1, hist, sh, sel, ties);
+                    K = sel[0];
+                    Km = sel[1];
+                    need_ties = ties[0] + 1;
+                }
                 for (int c = threadIdx.x; c < n_c; c += blockDim.x) {
                     const uint32_t kk = f2key(ckey[c]);
                     const int w = cidx[c] / seg;
