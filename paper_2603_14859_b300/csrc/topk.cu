@@ -1265,6 +1265,42 @@ __device__ __forceinline__ void group_dist_n(const float (&yq)[4], const float (
     }
 }
 
+// Four rows per group of G >= 4 lanes, as group_dist_n, but the butterfly is a
+// reduce-scatter: the first level keeps two of the four rows per lane, the second
+// one, the rest sum that one; each addition pairs the same operands as the full
+// butterfly, so every row's value is the same.  Lanes h with h % (G / 4) == 0
+// return row 2 [h & G/2] + [h & G/4].
+__device__ __forceinline__ float group_dist_scatter4(const float (&yq)[4], const float (&wq)[4],
+                                                     const float* const (&xr)[4], int L, int h, int G, int& row) {
+    const int l = 4 * h;
+    float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float4 v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        if (l < L) v[r] = __ldg((const float4*)xr[r] + h);
+    if (l < L) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float xv[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (l + q < L) {
+                    const float e = yq[q] - xv[q];
+                    d[r] = fmaf(wq[q] * e, e, d[r]);
+                }
+        }
+    }
+    const int o1 = G >> 1, o2 = G >> 2;
+    const bool b1 = (h & o1) != 0, b2 = (h & o2) != 0;
+    const float s0 = b1 ? d[0] : d[2], s1 = b1 ? d[1] : d[3];
+    const float x0 = (b1 ? d[2] : d[0]) + __shfl_xor_sync(0xFFFFFFFFu, s0, o1);
+    const float x1 = (b1 ? d[3] : d[1]) + __shfl_xor_sync(0xFFFFFFFFu, s1, o1);
+    float y = (b2 ? x1 : x0) + __shfl_xor_sync(0xFFFFFFFFu, b2 ? x0 : x1, o2);
+    for (int o = o2 >> 1; o > 0; o >>= 1) y += __shfl_xor_sync(0xFFFFFFFFu, y, o);
+    row = (b1 ? 2 : 0) + (b2 ? 1 : 0);
+    return y;
+}
+
 __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ BatchFin B) {
     extern __shared__ __align__(16) uint8_t fsm[];
     const int warps = blockDim.x >> 5;
@@ -1343,13 +1379,20 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
                     const int row = __shfl_sync(0xFFFFFFFFu, idx_cur, (i0 + r * R + grp - cb) & 31);
                     xr[r] = P.xs + (int64_t)row * P.ldxs;
                 }
-                float d[NR];
-                group_dist_n<NR>(yq, wq, xr, P.L, h, G, d);
-                if (h == 0) {
+                if (G >= 4) {
+                    int rr;
+                    const float dv = group_dist_scatter4(yq, wq, xr, P.L, h, G, rr);
+                    const int i = i0 + rr * R + grp;
+                    if ((h & ((G >> 2) - 1)) == 0 && i < cnt) kj[i] = dv;
+                } else {
+                    float d[NR];
+                    group_dist_n<NR>(yq, wq, xr, P.L, h, G, d);
+                    if (h == 0) {
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        const int i = i0 + r * R + grp;
-                        if (i < cnt) kj[i] = d[r];
+                        for (int r = 0; r < NR; ++r) {
+                            const int i = i0 + r * R + grp;
+                            if (i < cnt) kj[i] = d[r];
+                        }
                     }
                 }
             }
