@@ -254,7 +254,7 @@ def run_batched(args, world, rank, local):
     kept, total_tiles = api.topk_work(bp.ws)
     cols = {0: 3, 1: 1, 2: 2}[prec]
     kp = max(-(-(cols * W.L + 3) // 64) * 64 for W in scans)
-    executed = (2.0 * 128 * bp.tuning["bn"] * kp * kept) if total_tiles else flops * kp / max(W.L for W in scans)
+    executed = (2.0 * 128 * 64 * kp * kept) if total_tiles else flops * kp / max(W.L for W in scans)   # 64-draw tiles
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("bf16_tflops_sustained", 1400.0)
@@ -272,7 +272,7 @@ def run_batched(args, world, rank, local):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "k_tc_topk main pass (all scans, one persistent launch)",
                      "kernel_ms": tc_ms, "executed_flops_per_launch": executed,
-                     "executed": "bf16 MMA flops of the draw tiles processed (128 x BN x Kp x 2 per tile)",
+                     "executed": "bf16 MMA flops of the draw tiles processed (128 x 64 x Kp x 2 per 64-draw tile)",
                      "tiles_processed": kept, "tiles_without_skipping": total_tiles,
                      "algorithmic_flops_per_launch": flops,
                      "algorithmic_equivalent_tflops": flops / (tc_ms / 1000.0) / 1e12,
@@ -624,9 +624,8 @@ def main():
     value = voxels / (ms / 1000.0)
     flops = 2.0 * W.L * W.J * W.N
     kept, total_tiles = api.topk_work(run.ws)
-    bn = api.default_tuning(prec)["bn"]
     kp = -(-(({0: 3, 1: 1, 2: 2}[prec]) * W.L + 3) // 64) * 64
-    executed = (2.0 * 128 * bn * kp * kept) if total_tiles else 2.0 * kp * W.J * W.N
+    executed = (2.0 * 128 * 64 * kp * kept) if total_tiles else 2.0 * kp * W.J * W.N   # kept: 64-draw tiles
     achieved = executed / (tc_ms / 1000.0) / 1e12
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -649,7 +648,7 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_tc_topk main pass (fused discrepancy + top-k filter)", "kernel_ms": tc_ms,
                      "executed_flops_per_launch": executed,
-                     "executed": "bf16 MMA flops of the draw tiles processed (128 x BN x Kp x 2 per tile)",
+                     "executed": "bf16 MMA flops of the draw tiles processed (128 x 64 x Kp x 2 per 64-draw tile)",
                      "tiles_processed": kept, "tiles_without_skipping": total_tiles,
                      "algorithmic_flops_per_launch": flops,
                      "algorithmic_equivalent_tflops": flops / (tc_ms / 1000.0) / 1e12,

@@ -151,8 +151,10 @@ typedef struct {
 } abc_tuning;
 
 /* The tuning used for `precision` when none is passed: the built-in choice
- * (64-draw tiles, 3 CTAs/SM for ABC_BF16_RESCORE; 128-draw tiles for ABC_FP32)
- * unless abc_set_default_tuning replaced it. */
+ * (64-draw tiles, 3 CTAs/SM for ABC_BF16_RESCORE and ABC_SPLIT_DRAWS; 128-draw
+ * tiles for ABC_FP32) unless abc_set_default_tuning replaced it.  A call whose
+ * largest k is 400 or more runs ABC_BF16_RESCORE with 128-draw tiles and 2
+ * CTAs/SM instead (faster there on B300); this reports the k < 400 choice. */
 int abc_default_tuning(int32_t precision, abc_tuning* out);
 
 /* Replaces the process-wide default tuning for both precisions (NULL restores
@@ -233,8 +235,9 @@ int abc_discrepancy_topk_noalloc(const float* y_dev, int64_t J, int32_t ldy, con
 int abc_topk_status(const void* workspace, int32_t status_host[8], void* stream);
 
 /* Work done by the last main pass on this workspace: out_host[0] = draw tiles it
- * processed, out_host[1] = draw tiles a pass without skipping would process,
- * summed over voxel tiles (both 0 when no tile was skipped).  The main pass
+ * processed, out_host[1] = draw tiles a pass without skipping would process, in
+ * units of 64 draws whatever the tile width, summed over voxel tiles (both 0
+ * when no tile was skipped).  The main pass
  * skips a draw tile when a lower bound on every voxel-draw distance of the two
  * tiles, (F_c(y) - F_c(x))^2 / W_c summed over the three consecutive thirds c
  * of the frames (F_c = sum over the third of w_l v_l, W_c = sum of its w_l; a

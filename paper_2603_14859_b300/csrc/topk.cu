@@ -93,11 +93,16 @@ struct Tuning {
     float pilot_factor;   // predicted candidates / net size at the next finer level (>= 1.25)
 };
 
-// Built-in defaults (measured on B300 for the brain lp-ntPET workload): bf16
-// operands fit three 64-draw CTAs per SM; the fp32-split operands (3 K-blocks)
-// fit one CTA per SM, where 128-draw tiles are faster.
-Tuning default_tuning(int mode) {
-    return mode == ABC_FP32 ? Tuning{128, 2, 16, 1.5f} : Tuning{64, 3, 16, 1.5f};
+// Built-in defaults (measured on B300): bf16 operands fit three 64-draw CTAs
+// per SM, the fastest choice at k = 200 (total-body FDG) and for the split-draws
+// form; at k >= 400 (brain lp-ntPET, k = 500) 128-draw tiles with two CTAs per SM
+// are faster (each accumulator hand-off then serves four 32-column chunks).  The
+// fp32-split operands (3 K-blocks) fit one CTA per SM, where 128-draw tiles are
+// faster.
+Tuning default_tuning(int mode, int kmax = 0) {
+    if (mode == ABC_FP32) return Tuning{128, 2, 16, 1.5f};
+    if (mode == ABC_BF16_RESCORE && kmax >= 400) return Tuning{128, 2, 16, 1.5f};
+    return Tuning{64, 3, 16, 1.5f};
 }
 
 // bf16 columns of the packed operands per frame: products per term of the key.
@@ -689,9 +694,9 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
     }
     if (tid == 0) {
         K.kcount[vt] = base;
-        if (K.tally) {
-            atomicAdd(&K.tally[0], (unsigned long long)base);
-            atomicAdd(&K.tally[1], (unsigned long long)ntiles);
+        if (K.tally) {      // in 64-draw units, whatever the tile width
+            atomicAdd(&K.tally[0], (unsigned long long)base * per);
+            atomicAdd(&K.tally[1], (unsigned long long)ntiles * per);
         }
     }
 }
@@ -2109,16 +2114,16 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
 bool g_has_default = false;   // abc_set_default_tuning was called
 Tuning g_default_tuning = default_tuning(ABC_BF16_RESCORE);
 
-Tuning tuning_for(int mode) { return g_has_default ? g_default_tuning : default_tuning(mode); }
+Tuning tuning_for(int mode, int kmax) { return g_has_default ? g_default_tuning : default_tuning(mode, kmax); }
 
 ScanSpec single(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w, int k,
                 int32_t* idx, float* dist) {
     return ScanSpec{y, J, ldy, x, N, ldx, L, w, k, idx, dist};
 }
 
-int to_tuning(const abc_tuning* t, int mode, Tuning* out) {
+int to_tuning(const abc_tuning* t, int mode, int kmax, Tuning* out) {
     if (!t) {
-        *out = tuning_for(mode);
+        *out = tuning_for(mode, kmax);
         return ABC_OK;
     }
     *out = Tuning{t->bn, t->ctas_per_sm, t->pilot_stride, t->pilot_factor};
@@ -2142,7 +2147,7 @@ namespace vpet {
 size_t topk_workspace_bytes(int64_t J, int64_t N, int L, int k, int precision) {
     ScanSpec c = single(nullptr, J, L, nullptr, N, L, L, nullptr, k, nullptr, nullptr);
     BatchLayout* B = new BatchLayout;
-    make_batch_layout(&c, 1, precision, tuning_for(precision), B);
+    make_batch_layout(&c, 1, precision, tuning_for(precision, k), B);
     const size_t t = B->total;
     delete B;
     return t;
@@ -2151,7 +2156,7 @@ size_t topk_workspace_bytes(int64_t J, int64_t N, int L, int k, int precision) {
 int topk_on_workspace(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w,
                       int k, int precision, void* ws, size_t ws_bytes, int32_t* idx, float* dist, cudaStream_t s) {
     const ScanSpec c = single(y, J, ldy, x, N, ldx, L, w, k, idx, dist);
-    return run_batch(&c, 1, precision, g_default_tuning, ws, ws_bytes, nullptr, 0, s);
+    return run_batch(&c, 1, precision, tuning_for(precision, k), ws, ws_bytes, nullptr, 0, s);
 }
 
 }  // namespace vpet
@@ -2187,7 +2192,7 @@ extern "C" int abc_default_tuning(int32_t precision, abc_tuning* out) {
     VPET_ARG(out, "abc_default_tuning: null pointer");
     VPET_ARG(precision == ABC_FP32 || precision == ABC_BF16_RESCORE || precision == ABC_SPLIT_DRAWS,
              "abc_default_tuning: unknown precision");
-    const Tuning t = tuning_for(precision);
+    const Tuning t = tuning_for(precision, 0);
     out->bn = t.bn;
     out->ctas_per_sm = t.ctas_per_sm;
     out->pilot_stride = t.pilot_stride;
@@ -2198,7 +2203,7 @@ extern "C" int abc_default_tuning(int32_t precision, abc_tuning* out) {
 extern "C" int abc_set_default_tuning(const abc_tuning* t) {
     vpet::clear_error();
     Tuning tu;
-    const int rc = to_tuning(t, ABC_BF16_RESCORE, &tu);
+    const int rc = to_tuning(t, ABC_BF16_RESCORE, 0, &tu);
     if (rc) return rc;
     g_has_default = t != nullptr;
     if (t) g_default_tuning = tu;
@@ -2215,7 +2220,9 @@ extern "C" size_t abc_batch_workspace_size(const abc_scan* scans, int32_t n_scan
         sp[i] = ScanSpec{c.y_dev, c.J, c.ldy, c.x_dev, c.N, c.ldx, c.L, c.w_host, c.k, c.idx_dev, c.dist_dev};
     }
     BatchLayout* B = new BatchLayout;
-    make_batch_layout(sp, n_scans, precision, tuning_for(precision), B);
+    int kmax = 0;
+    for (int i = 0; i < n_scans; ++i) kmax = sp[i].k > kmax ? sp[i].k : kmax;
+    make_batch_layout(sp, n_scans, precision, tuning_for(precision, kmax), B);
     const size_t t = B->total;
     delete B;
     return t;
@@ -2228,7 +2235,9 @@ extern "C" int abc_batch_discrepancy_topk(const abc_scan* scans, int32_t n_scans
     int rc = gather_scans(scans, n_scans, sp);
     if (rc) return rc;
     Tuning tu;
-    if ((rc = to_tuning(tuning, precision, &tu))) return rc;
+    int kmax = 0;
+    for (int i = 0; i < n_scans; ++i) kmax = sp[i].k > kmax ? sp[i].k : kmax;
+    if ((rc = to_tuning(tuning, precision, kmax, &tu))) return rc;
     return run_batch(sp, n_scans, precision, tu, workspace, ws_bytes, nullptr, 0, (cudaStream_t)stream);
 }
 
@@ -2258,7 +2267,7 @@ extern "C" int abc_debug_gemm_keys(const float* y_dev, int64_t J, int32_t ldy, c
     vpet::clear_error();
     VPET_ARG(dump_dev && ld_dump >= vpet_round_up(N, 128), "abc_debug_gemm_keys: dump too small");
     const ScanSpec c = single(y_dev, J, ldy, x_dev, N, ldx, L, w_host, 1, nullptr, nullptr);
-    return run_batch(&c, 1, precision, tuning_for(precision), workspace, ws_bytes, dump_dev, ld_dump,
+    return run_batch(&c, 1, precision, tuning_for(precision, 1), workspace, ws_bytes, dump_dev, ld_dump,
                      (cudaStream_t)stream);
 }
 
