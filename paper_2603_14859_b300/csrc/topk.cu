@@ -66,7 +66,12 @@ namespace {
 constexpr int BM = 128;                       // voxels per CTA tile = TMEM lanes
 constexpr int KBLK = 64;                      // bf16 per K-block (128-byte rows)
 constexpr int A_KBLK_BYTES = BM * KBLK * 2;   // 16 KB
-constexpr int TC_THREADS = 192;
+// Fused kernel: TMA warp, MMA warp, then the epilogue warps: four (one thread per
+// voxel and tile: top-r pilots and 64-draw tiles) or eight with 128-draw tiles
+// (two per TMEM lane quadrant, each taking every other 32-column chunk of a tile
+// and keeping its own half of the voxel's candidate list).
+constexpr int tc_epi_warps(bool topr, int bn) { return (topr || bn == 64) ? 4 : 8; }
+constexpr int tc_threads(bool topr, int bn) { return 64 + 32 * tc_epi_warps(topr, bn); }
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any barrier wait
 constexpr int MAXL = 64;
 constexpr int ORDER_BITS = 10;                 // bits per ordering feature (30-bit Morton key)
@@ -188,8 +193,8 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.off_b = o; o = align256(o + (size_t)s.Np * s.Kp * 2);
     s.off_keys = o; o = align256(o + (size_t)J * s.C * sizeof(float));
     s.off_idx = o; o = align256(o + (size_t)J * s.C * sizeof(int32_t));
-    s.off_cnt = o; o = align256(o + (size_t)s.Jp * sizeof(int32_t));
-    s.off_thr = o; o = align256(o + (size_t)s.Jp * sizeof(float));
+    s.off_cnt = o; o = align256(o + (size_t)2 * s.Jp * sizeof(int32_t));     // two half-lists per voxel
+    s.off_thr = o; o = align256(o + (size_t)2 * s.Jp * sizeof(float));
     s.off_thr0 = o; o = align256(o + (size_t)s.Jp * sizeof(float));
     s.off_perm = o; o = align256(o + (size_t)s.Jp * sizeof(int32_t));
     s.off_feat = o; o = align256(o + (size_t)3 * s.Jp * sizeof(float) + 8 * sizeof(uint32_t));
@@ -712,15 +717,18 @@ struct __align__(64) ItemTc {
     int32_t* cnt;
     float* thr;                  // final running threshold per voxel
     const float* thr0;           // initial threshold per voxel (pilot), or null = +huge
-    int ntiles, C, kt, cap;
-    int lim;                     // a list is compacted once it could exceed lim entries (lim <= C)
+    int ntiles, C, kt, cap;      // cap: entries a half-list keeps after a compaction (<= C2)
+    int C2;                      // each voxel's list row holds two half-lists of C2 entries
+    int lim;                     // a half-list is compacted once it could exceed lim entries (lim <= C2)
     int lim0;                    // ... or lim0 entries while its voxel has no finite threshold yet
+    int rsel;                    // > 0: pilot that keeps the rsel smallest keys per voxel, no lists
+    int hstride;                 // cnt[] / thr[] entry of half 1 of voxel j: j + hstride
     const int32_t* ktile;        // kept draw tiles per voxel tile (null: every tile)
     const int32_t* kcount;
     int64_t kstride;
-    int rsel;                    // > 0: pilot that keeps the rsel smallest keys per voxel, no lists
-    float* thr_out;              // ... and writes its threshold here
+    float* thr_out;              // top-r pilot: its thresholds
 };
+static_assert(sizeof(ItemTc) == 384, "ItemTc layout");
 
 struct BatchTc {
     ItemTc item[MAX_ITEMS];
@@ -741,15 +749,16 @@ __device__ __forceinline__ int item_of(const BatchTc& P, int64_t w) {
 // Bound on |computed d' - exact d'| for any draw with ||xh|| <= R.
 __device__ __forceinline__ float err_bound(float cE, float ry, float R) { return cE * (2.0f * ry * R + R * R); }
 
-// Tightens voxel j's candidate list to the keys <= its kt-th key; returns the new
-// threshold and updates cnt.
-__device__ __forceinline__ float compact_list(const ItemTc& I, int64_t j, int& cnt, uint32_t* hist, int lane) {
-    float* kj = I.keys + j * I.C;
-    int32_t* ij = I.idx + j * I.C;
+// Tightens half h of voxel j's candidate list to the keys <= its kt-th key;
+// returns the new threshold and updates cnt.  Each half keeps its own kt
+// smallest, so the two halves together always hold the voxel's kt smallest.
+__device__ __forceinline__ float compact_list(const ItemTc& I, int64_t j, int h, int& cnt, uint32_t* hist, int lane) {
+    float* kj = I.keys + j * I.C + h * I.C2;
+    int32_t* ij = I.idx + j * I.C + h * I.C2;
     const uint32_t T = warp_select(kj, cnt, I.kt - 1, 4, hist, lane);   // exact kt-th key
     const int q = warp_compact(kj, ij, cnt, T, I.cap, lane);
     cnt = q < I.cap ? q : I.cap;
-    if (q > I.cap && lane == 0) atomicOr(&I.cnt[j], 0x40000000);   // overflow: resolved by an exact scan
+    if (q > I.cap && lane == 0) atomicOr(&I.cnt[j + h * I.hstride], 0x40000000);   // overflow: exact scan
     return key2f(T);
 }
 
@@ -778,12 +787,13 @@ __device__ __forceinline__ uint32_t mask8(const float (&v)[32], int o, float thr
     return m;
 }
 
-// One 32-column chunk of the epilogue, per thread (= voxel j): the minima of
+// One 32-column chunk of the epilogue, per thread (= voxel): the minima of
 // the four 8-key groups against the voxel's threshold; a thread with a passing
 // group builds the mask of passing keys (passing groups only), copies its 32
 // keys to its own row of shared memory (row_s) and appends each passing key,
-// read back by position, to the voxel's list.  Threads never wait for one another.
-__device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32], int64_t n0, int64_t j, float thr,
+// read back by position, to its half-list (starting at entry lbase).  Threads
+// never wait for one another.
+__device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32], int64_t n0, int64_t lbase, float thr,
                                                int& cnt, float* row_s) {
     if (n0 + 32 > I.N) {
 #pragma unroll
@@ -804,12 +814,11 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
     float4* dst = (float4*)row_s;
 #pragma unroll
     for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    const int64_t row = j * (int64_t)I.C;
     while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
-        I.keys[row + cnt] = row_s[b];
-        I.idx[row + cnt] = (int32_t)(n0 + b);
+        I.keys[lbase + cnt] = row_s[b];
+        I.idx[lbase + cnt] = (int32_t)(n0 + b);
         ++cnt;
     }
 }
@@ -883,15 +892,18 @@ __device__ __forceinline__ void topr_chunk(TopR& S, float (&v)[32], int64_t n0, 
 // scans first).  All roles walk the same sequence; the shared-memory ring and
 // the TMEM accumulators keep their phases across items.
 template <int NKB, int STAGES, int BN, bool DUMP, bool TOPR>
-__global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant__ BatchTc P) {
+__global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) == 8 ? 2 : 3)
+    k_tc_topk(const __grid_constant__ BatchTc P) {
     constexpr int B_KBLK_BYTES = BN * KBLK * 2;
+    constexpr int EPI = tc_epi_warps(TOPR, BN);                  // epilogue warps
+    constexpr int CSTEP = EPI / 4;                               // chunk stride of an epilogue warp
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;                                          // NKB x 16 KB
     uint8_t* sB = smem + NKB * A_KBLK_BYTES;                     // STAGES x NKB x BN rows
-    float* sRow = (float*)(sB + STAGES * NKB * B_KBLK_BYTES);         // 128 threads x ROW_LD
-    uint32_t* hist = (uint32_t*)(sRow + 128 * ROW_LD);                  // 4 warps x 256
-    uint64_t* bars = (uint64_t*)(hist + 4 * 256);
+    float* sRow = (float*)(sB + STAGES * NKB * B_KBLK_BYTES);         // 32 EPI threads x ROW_LD
+    uint32_t* hist = (uint32_t*)(sRow + 32 * EPI * ROW_LD);             // EPI warps x 256
+    uint64_t* bars = (uint64_t*)(hist + EPI * 256);
     uint64_t* full = bars;                  // [STAGES]
     uint64_t* empty = bars + STAGES;        // [STAGES]
     uint64_t* tfull = bars + 2 * STAGES;    // [2]
@@ -914,13 +926,13 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
         }
         for (int a = 0; a < 2; ++a) {
             ptx::mbar_init(ptx::smem_u32(&tfull[a]), 1);
-            ptx::mbar_init(ptx::smem_u32(&tempty[a]), 4);
+            ptx::mbar_init(ptx::smem_u32(&tempty[a]), EPI);
         }
         ptx::mbar_init(ptx::smem_u32(afull), 1);
         ptx::mbar_init(ptx::smem_u32(aempty), 1);
         for (int a = 0; a < 2; ++a) {
             ptx::mbar_init(ptx::smem_u32(&ifull[a]), 1);
-            ptx::mbar_init(ptx::smem_u32(&iempty[a]), 5);   // MMA thread + 4 epilogue warps
+            ptx::mbar_init(ptx::smem_u32(&iempty[a]), 1 + EPI);   // MMA thread + the epilogue warps
         }
         *s_err = 0;
         ptx::fence_mbar_init();
@@ -1021,10 +1033,12 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
             }
         }
     } else {
-        // ---------------- epilogue: warps 2..5, thread <-> voxel
+        // ---------------- epilogue: warps 2 .. 2 + EPI - 1, thread <-> voxel
         const int q = warp & 3;                          // TMEM lane quadrant of this warp
+        const int hh = (warp - 2) >> 2;                  // chunk parity and half-list (0 with 4 warps)
         const int row = q * 32 + lane;
         uint32_t* whist = hist + (warp - 2) * 256;
+        float* row_s = sRow + (threadIdx.x - 64) * ROW_LD;
         uint32_t gt = 0;
         bool stop = false;
         for (uint32_t ic = 0; !stop; ++ic) {
@@ -1047,6 +1061,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
             const bool valid = j < I.J;
             float thr = valid ? (I.thr0 ? I.thr0[j] : 3.0e38f) : -3.0e38f;
             int cnt = 0;
+            const int64_t lbase = j * (int64_t)I.C + hh * I.C2;   // this thread's half-list
             TopR S{sRow + (threadIdx.x - 64), TOPR ? I.rsel : 0, 0, 0, -3.0e38f, thr, thr};
             // the next tile's draw offset is loaded a tile ahead, off the path from the
             // accumulator's arrival to its first use
@@ -1061,7 +1076,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                 ptx::tc_fence_after();
                 const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
                 if (DUMP) {
-                    for (int c = 0; c < BN / 32; ++c) {
+                    for (int c = hh; c < BN / 32; c += CSTEP) {
                         uint32_t r[32];
                         ptx::tmem_ld32_async(ta + c * 32, r);
                         ptx::tmem_wait_ld();
@@ -1074,7 +1089,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                     // one 32-column load at a time (fewer live registers than overlapping two
                     // loads, which measured slower)
 #pragma unroll 1
-                    for (int c = 0; c < BN / 32; ++c) {
+                    for (int c = hh; c < BN / 32; c += CSTEP) {
                         uint32_t r[32];
                         ptx::tmem_ld32_async(ta + c * 32, r);
                         ptx::tmem_wait_ld();
@@ -1083,7 +1098,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
 #pragma unroll
                         for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
                         if constexpr (TOPR) topr_chunk(S, v, nbase + c * 32, R.N);
-                        else epilogue_chunk(R, v, nbase + c * 32, j, thr, cnt, sRow + (threadIdx.x - 64) * ROW_LD);
+                        else epilogue_chunk(R, v, nbase + c * 32, lbase, thr, cnt, row_s);
                     }
                 }
                 ptx::tc_fence_before();
@@ -1093,12 +1108,12 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                 // compaction of lists that might not fit the next tile
                 // a list without a threshold yet (the coarsest pilot) is first cut early, at
                 // lim0: from then on far fewer keys pass than the everything of a +inf start
-                uint32_t need = __ballot_sync(0xFFFFFFFFu, valid && cnt > (thr >= 3.0e38f ? lim0 : lim) - BN);
+                uint32_t need = __ballot_sync(0xFFFFFFFFu, valid && cnt > (thr >= 3.0e38f ? lim0 : lim) - BN / CSTEP);
                 while (need) {
                     const int src = __ffs(need) - 1;
                     need &= need - 1;
                     int c2 = __shfl_sync(0xFFFFFFFFu, cnt, src);
-                    const float nt = compact_list(I, jbase + src, c2, whist, lane);
+                    const float nt = compact_list(I, jbase + src, hh, c2, whist, lane);
                     if (lane == src) {
                         cnt = c2;
                         thr = nt;
@@ -1113,8 +1128,9 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_tc_topk(const __grid_constant
                     I.thr_out[j] = t;
                     if (t >= 3.0e38f) atomicAdd(&P.status[7], 1);
                 } else {
-                    atomicOr(&I.cnt[j], cnt);      // cnt[] was zeroed; keeps the overflow bit
-                    I.thr[j] = thr;
+                    atomicOr(&I.cnt[j + hh * I.hstride], cnt);      // cnt[] was zeroed; keeps the overflow bit
+                    I.thr[j + hh * I.hstride] = thr;
+                    if (EPI == 4) I.thr[j + I.hstride] = 3.0e38f;   // the unused half-list bounds nothing
                 }
             }
         }
@@ -1137,7 +1153,32 @@ struct PilotItem {
     float* thr0;
     int64_t J;
     int C, r;
+    int C2;
+    int64_t hstride;
 };
+
+// Moves half-list 1 of a list row (entries [C2, C2 + c1)) to follow half-list 0
+// (entries [0, c0)), keys and (when given) draw indices.  Rows of 32 are read
+// before they are written, and every write lands below the next row's reads
+// (c0 <= C2), so the copy is safe in place.
+__device__ __forceinline__ void merge_halves(float* kj, int32_t* ij, int C2, int c0, int c1, int lane) {
+    if (c0 == C2 || c1 == 0) return;
+    for (int base = 0; base < c1; base += 32) {
+        const int i = base + lane;
+        float k = 0.0f;
+        int32_t id = 0;
+        if (i < c1) {
+            k = kj[C2 + i];
+            if (ij) id = ij[C2 + i];
+        }
+        __syncwarp();
+        if (i < c1) {
+            kj[c0 + i] = k;
+            if (ij) ij[c0 + i] = id;
+        }
+    }
+    __syncwarp();
+}
 
 struct BatchPilot {
     PilotItem item[MAX_ITEMS];
@@ -1156,15 +1197,19 @@ __global__ void k_pilot_threshold(const __grid_constant__ BatchPilot B) {
     while (it + 1 < B.n_items && g >= B.v_prefix[it + 1]) ++it;
     const PilotItem& I = B.item[it];
     const int64_t j = g - B.v_prefix[it];
-    const int raw = I.cnt[j];
-    const int c = raw & 0x3FFFFFFF;
+    const int raw0 = I.cnt[j], raw1 = I.cnt[j + I.hstride];
+    const int c0 = raw0 & 0x3FFFFFFF, c1 = raw1 & 0x3FFFFFFF, c = c0 + c1;
     float t = 3.0e38f;
-    // the r-th smallest key, rounded up to its 24-bit prefix
-    if (!(raw & 0x40000000) && c >= I.r)
-        t = key2f(warp_select_exact(I.keys + j * I.C, c, I.r - 1, hist[wid], gbuf[wid], 256, lane).K | 0xFFu);
+    // the r-th smallest key of the two half-lists, rounded up to its 24-bit prefix
+    if (!((raw0 | raw1) & 0x40000000) && c >= I.r) {
+        float* kj = I.keys + j * I.C;
+        merge_halves(kj, nullptr, I.C2, c0, c1, lane);
+        t = key2f(warp_select_exact(kj, c, I.r - 1, hist[wid], gbuf[wid], 256, lane).K | 0xFFu);
+    }
     if (lane == 0) {
         I.thr0[j] = t;
         I.cnt[j] = 0;
+        I.cnt[j + I.hstride] = 0;
         if (t >= 3.0e38f) atomicAdd(&B.status[7], 1);     // diagnostics: pilot level without a threshold
     }
 }
@@ -1173,6 +1218,8 @@ __global__ void k_pilot_threshold(const __grid_constant__ BatchPilot B) {
 struct FinItem {
     int64_t J, N;
     int L, k, C, kt, mode, sortcap;
+    int C2;                      // the list row's two half-lists start at 0 and C2
+    int64_t hstride;             // cnt[] / thr[] of half 1: row + hstride
     float cE;
     int ldy, ldx;
     const float* y;
@@ -1323,8 +1370,11 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
     const int64_t vox = P.perm ? (int64_t)P.perm[j] : j;   // voxel of that row
     float* kj = P.keys + j * P.C;
     int32_t* ij = P.idx + j * P.C;
-    const int raw = P.cnt[j];
-    int cnt = raw & 0x3FFFFFFF;
+    const int raw0 = P.cnt[j], raw1 = P.cnt[j + P.hstride];
+    const int raw = raw0 | raw1;                          // an overflow flag from either half
+    const int c0h = raw0 & 0x3FFFFFFF, c1h = raw1 & 0x3FFFFFFF;
+    int cnt = c0h + c1h;
+    if (!(raw & 0x40000000)) merge_halves(kj, ij, P.C2, c0h, c1h, lane);   // one contiguous list
     for (int l = lane; l < P.L; l += 32) {
         ys[l] = P.y[vox * P.ldy + l];
         ws[l] = P.w[l];
@@ -1344,7 +1394,7 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
     float dbound = __int_as_float(0x7F800000);   // exact k-th distance of the net: bounds the true one
     if (!scan) {
         // 1. the net: every draw outside it has computed key > T_out
-        float T_out = P.thr[j];
+        float T_out = fminf(P.thr[j], P.thr[j + P.hstride]);   // both halves dropped only keys above theirs
         if (P.mode != ABC_FP32 && cnt > P.kt) {
             // the net: the kt smallest keys and the rest of their linear bin (a few more)
             const LinearCut cut = warp_cut_linear(kj, cnt, P.kt - 1, hist, lane);
@@ -1601,14 +1651,18 @@ int make_tmap(CUtensorMap* m, void* base, int64_t rows, int Kp, int box_rows, in
     return ABC_OK;
 }
 
+// TMA ring depth per shape: as deep as shared memory allows next to the A tile and
+// the epilogue warps' key rows and histograms (<= 227 KB per CTA; two CTAs per SM
+// for one K-block)
 constexpr int stages_for(int nkb, int bn) {
-    return nkb == 1 ? 4 : (nkb == 2 ? (bn == 128 ? 4 : 3) : (bn == 128 ? 3 : 4));
+    return nkb == 1 ? (bn == 128 ? 3 : 4) : (nkb == 2 ? (bn == 128 ? 4 : 3) : (bn == 128 ? 2 : 4));
 }
 
-size_t tc_smem_bytes(int nkb, int bn) {
+size_t tc_smem_bytes(int nkb, int bn, bool topr) {
     const int S = stages_for(nkb, bn);
-    return 1024 + (size_t)nkb * A_KBLK_BYTES + (size_t)S * nkb * bn * KBLK * 2 + 128 * ROW_LD * 4 + 4 * 256 * 4 +
-           (2 * S + 14) * 8;
+    const int epi = tc_epi_warps(topr, bn);
+    return 1024 + (size_t)nkb * A_KBLK_BYTES + (size_t)S * nkb * bn * KBLK * 2 + (size_t)32 * epi * ROW_LD * 4 +
+           (size_t)epi * 256 * 4 + (2 * S + 14) * 8;
 }
 
 int num_sms() {
@@ -1626,7 +1680,7 @@ int num_sms() {
 template <int NKB, int BN, bool DUMP, bool TOPR>
 int launch_tc(const BatchTc& P, int ctas_per_sm, cudaStream_t s) {
     constexpr int S = stages_for(NKB, BN);
-    const size_t smem = tc_smem_bytes(NKB, BN);
+    const size_t smem = tc_smem_bytes(NKB, BN, TOPR);
     static bool configured = false;
     static int max_resident = 1;
     if (!configured) {
@@ -1644,7 +1698,7 @@ int launch_tc(const BatchTc& P, int ctas_per_sm, cudaStream_t s) {
         VPET_CUDA(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
         const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + resv);
         const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
-        const int by_regs = 65536 / (regs_warp * (TC_THREADS / 32));
+        const int by_regs = 65536 / (regs_warp * (tc_threads(TOPR, BN) / 32));
         const int by_tmem = 512 / (2 * BN);
         max_resident = by_smem < by_regs ? by_smem : by_regs;
         if (max_resident > by_tmem) max_resident = by_tmem;
@@ -1658,7 +1712,7 @@ int launch_tc(const BatchTc& P, int ctas_per_sm, cudaStream_t s) {
     if (grid > total) grid = total;
     if (grid < 1) return ABC_OK;
     g_last_grid = grid;
-    k_tc_topk<NKB, S, BN, DUMP, TOPR><<<(unsigned)grid, TC_THREADS, smem, s>>>(P);
+    k_tc_topk<NKB, S, BN, DUMP, TOPR><<<(unsigned)grid, tc_threads(TOPR, BN), smem, s>>>(P);
     VPET_LAUNCH_CHECK();
     return ABC_OK;
 }
@@ -1773,7 +1827,7 @@ bool layout_consistent(const Layout& L) {
                           L.off_kcount, L.off_xs};
     const size_t len[] = {MAXL * 4, (size_t)L.npart * MAXL * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
                           (size_t)L.Jp * L.Kp * 2, (size_t)L.Np * L.Kp * 2, (size_t)L.J * L.C * 4,
-                          (size_t)L.J * L.C * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
+                          (size_t)L.J * L.C * 4, (size_t)2 * L.Jp * 4, (size_t)2 * L.Jp * 4, (size_t)L.Jp * 4,
                           (size_t)L.Jp * 4, (size_t)3 * L.Jp * 4 + 32, (size_t)(ORDER_BUCKETS + ORDER_BUCKETS / 1024) * 4,
                           (size_t)L.Np * 4, (size_t)3 * L.Np * 4 + 32, (size_t)(ORDER_BUCKETS + ORDER_BUCKETS / 1024) * 4,
                           (size_t)3 * L.Jp * 4, (size_t)3 * L.Np * 4, (size_t)6 * L.nt64 * 4,
@@ -1863,7 +1917,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             W.w[l] = sc[i].w[l];
             W.sw[l] = sqrtf(sc[i].w[l]);
         }
-        VPET_CUDA(cudaMemsetAsync(p.cnt, 0, (size_t)L.Jp * sizeof(int32_t), s));
+        VPET_CUDA(cudaMemsetAsync(p.cnt, 0, (size_t)2 * L.Jp * sizeof(int32_t), s));
         k_colmean_part<<<L.npart, 256, 0, s>>>(sc[i].y, L.J, sc[i].ldy, L.L, p.part, L.npart);
         VPET_LAUNCH_CHECK();
         k_colmean_final<<<1, MAXL, 0, s>>>(p.part, L.npart, L.J, p.mu);
@@ -1943,10 +1997,19 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         I.thr0 = thr0;
         I.ntiles = (int)vpet_ceil_div(I.N, tu.bn);
         I.C = L.C;
+        // with 128-draw tiles two epilogue threads serve a voxel, each with its own
+        // half-list that keeps its own kt smallest and receives half of every tile;
+        // with 64-draw tiles one thread uses the whole list (half 1 stays empty)
+        const bool halves = tu.bn == 128;
+        I.C2 = halves ? L.C / 2 : L.C;
+        I.hstride = (int)L.Jp;
         I.kt = kt;
-        I.cap = kt + (kt / 4 > 64 ? kt / 4 : 64);
-        I.lim = lim;
-        I.lim0 = 2 * kt + tu.bn < lim ? 2 * kt + tu.bn : lim;
+        const int per_tile = halves ? tu.bn / 2 : tu.bn;
+        const int cap = kt + (kt / 4 > 64 ? kt / 4 : 64);
+        I.cap = cap < I.C2 ? cap : I.C2;
+        const int limh = halves ? lim / 2 : lim;
+        I.lim = limh < I.C2 ? limh : I.C2;
+        I.lim0 = 2 * kt + per_tile < I.lim ? 2 * kt + per_tile : I.lim;
         return ABC_OK;
     };
     int maxlev = 0;
@@ -2008,7 +2071,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
                 T.item[m].rsel = r;
                 T.item[m].thr_out = ptr[i].thr0;
             } else {
-                PB.item[mp] = PilotItem{ptr[i].keys, ptr[i].cnt, ptr[i].thr0, L.J, L.C, r};
+                PB.item[mp] = PilotItem{ptr[i].keys, ptr[i].cnt, ptr[i].thr0, L.J, L.C, r, tu.bn == 128 ? L.C / 2 : L.C, L.Jp};
                 PB.v_prefix[mp + 1] = PB.v_prefix[mp] + L.J;
                 ++mp;
             }
@@ -2066,6 +2129,8 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         f.L = L.L;
         f.k = L.k;
         f.C = L.C;
+        f.C2 = tu.bn == 128 ? L.C / 2 : L.C;
+        f.hstride = L.Jp;
         f.kt = L.kt;
         f.mode = mode;
         f.sortcap = L.sortcap;
