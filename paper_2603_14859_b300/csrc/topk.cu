@@ -1035,7 +1035,7 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
     } else {
         // ---------------- epilogue: warps 2 .. 2 + EPI - 1, thread <-> voxel
         const int q = warp & 3;                          // TMEM lane quadrant of this warp
-        const int hh = (warp - 2) >> 2;                  // chunk parity and half-list (0 with 4 warps)
+        const int hh = EPI == 8 ? (warp - 2) >> 2 : 0;   // chunk parity and half-list (0 with 4 warps)
         const int row = q * 32 + lane;
         uint32_t* whist = hist + (warp - 2) * 256;
         float* row_s = sRow + (threadIdx.x - 64) * ROW_LD;
