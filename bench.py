@@ -297,7 +297,7 @@ LOCAL_FLOPS_PER_FRAME = 18
 # Thread instructions the local ABC kernel issues per proposal (ncu smsp__inst_executed x 32 / proposals,
 # measured on the 40,000-voxel learned case).  The kernel is issue-bound, so its roofline is instruction
 # issue against the SIMT issue peak.
-LOCAL_INST_PER_PROPOSAL = 538.0
+LOCAL_INST_PER_PROPOSAL = 523.0
 
 
 def cpu_baseline_learned(W, M, k, model_params, D, H, seconds_budget=20.0):
