@@ -92,10 +92,15 @@ __device__ __forceinline__ int linear_bin(float v, const LinearCut& c) {
     return t < 255.0f ? (int)t : 255;
 }
 
-__device__ __forceinline__ LinearCut warp_cut_linear(const float* keys, int cnt, int rank, uint32_t* hist, int lane) {
+// Logical entry i of a list stored as two segments, [0, c0) and [off1, off1 + cnt - c0)
+// (off1 >= c0; one segment when c0 >= cnt).
+__device__ __forceinline__ int seg_pos(int i, int c0, int off1) { return i < c0 ? i : off1 + (i - c0); }
+
+__device__ __forceinline__ LinearCut warp_cut_linear(const float* keys, int cnt, int rank, uint32_t* hist, int lane,
+                                                     int c0 = 0x7FFFFFFF, int off1 = 0) {
     float mn = 3.0e38f, mx = -3.0e38f;
     for (int i = lane; i < cnt; i += 32) {
-        const float v = keys[i];
+        const float v = keys[seg_pos(i, c0, off1)];
         mn = fminf(mn, v);
         mx = fmaxf(mx, v);
     }
@@ -120,7 +125,7 @@ __device__ __forceinline__ LinearCut warp_cut_linear(const float* keys, int cnt,
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int i = base + 32 * u + lane;
-            v[u] = i < cnt ? keys[i] : 0.0f;
+            v[u] = i < cnt ? keys[seg_pos(i, c0, off1)] : 0.0f;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -306,7 +311,7 @@ __device__ __forceinline__ int warp_compact_ties(float* keys, int32_t* idx, int 
 // In-place stable compaction of (keys, idx)[0..cnt) to the entries in bins <= c.bin;
 // returns the number kept and (in kmax) the largest kept key.
 __device__ __forceinline__ int warp_compact_cut(float* keys, int32_t* idx, int cnt, const LinearCut& c, int lane,
-                                                float& kmax) {
+                                                float& kmax, int c0 = 0x7FFFFFFF, int off1 = 0) {
     int out = 0;
     float mx = -3.0e38f;
     // four rows of 32 read before any is written back: every write goes to a position
@@ -317,8 +322,9 @@ __device__ __forceinline__ int warp_compact_cut(float* keys, int32_t* idx, int c
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int i = base + 32 * u + lane;
-            k[u] = i < cnt ? keys[i] : 0.0f;
-            id[u] = i < cnt ? idx[i] : 0;
+            const int p = seg_pos(i, c0, off1);
+            k[u] = i < cnt ? keys[p] : 0.0f;
+            id[u] = i < cnt ? idx[p] : 0;
         }
         __syncwarp();
 #pragma unroll

@@ -1374,7 +1374,10 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
     const int raw = raw0 | raw1;                          // an overflow flag from either half
     const int c0h = raw0 & 0x3FFFFFFF, c1h = raw1 & 0x3FFFFFFF;
     int cnt = c0h + c1h;
-    if (!(raw & 0x40000000)) merge_halves(kj, ij, P.C2, c0h, c1h, lane);   // one contiguous list
+    // one contiguous list: the BF16 net cut below reads both half-lists and writes the net in
+    // front; everything else joins them first
+    const bool cut_joins = P.mode != ABC_FP32 && cnt > P.kt;
+    if (!(raw & 0x40000000) && !cut_joins) merge_halves(kj, ij, P.C2, c0h, c1h, lane);
     for (int l = lane; l < P.L; l += 32) {
         ys[l] = P.y[vox * P.ldy + l];
         ws[l] = P.w[l];
@@ -1397,9 +1400,9 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
         float T_out = fminf(P.thr[j], P.thr[j + P.hstride]);   // both halves dropped only keys above theirs
         if (P.mode != ABC_FP32 && cnt > P.kt) {
             // the net: the kt smallest keys and the rest of their linear bin (a few more)
-            const LinearCut cut = warp_cut_linear(kj, cnt, P.kt - 1, hist, lane);
+            const LinearCut cut = warp_cut_linear(kj, cnt, P.kt - 1, hist, lane, c0h, P.C2);
             float kmax;
-            cnt = warp_compact_cut(kj, ij, cnt, cut, lane, kmax);
+            cnt = warp_compact_cut(kj, ij, cnt, cut, lane, kmax, c0h, P.C2);
             T_out = kmax;
         }
         // 2. exact fp32 re-score of the net (list entries are packed draw rows, read from the
