@@ -151,10 +151,8 @@ typedef struct {
 } abc_tuning;
 
 /* The tuning used for `precision` when none is passed: the built-in choice
- * (64-draw tiles, 3 CTAs/SM for ABC_BF16_RESCORE and ABC_SPLIT_DRAWS; 128-draw
- * tiles for ABC_FP32) unless abc_set_default_tuning replaced it.  A call whose
- * largest k is 400 or more runs ABC_BF16_RESCORE with 128-draw tiles and 2
- * CTAs/SM instead (faster there on B300); this reports the k < 400 choice. */
+ * (128-draw tiles, 2 CTAs/SM for ABC_BF16_RESCORE and ABC_FP32; 64-draw tiles,
+ * 3 CTAs/SM for ABC_SPLIT_DRAWS) unless abc_set_default_tuning replaced it. */
 int abc_default_tuning(int32_t precision, abc_tuning* out);
 
 /* Replaces the process-wide default tuning for both precisions (NULL restores

@@ -98,16 +98,15 @@ struct Tuning {
     float pilot_factor;   // predicted candidates / net size at the next finer level (>= 1.25)
 };
 
-// Built-in defaults (measured on B300): bf16 operands fit three 64-draw CTAs
-// per SM, the fastest choice at k = 200 (total-body FDG) and for the split-draws
-// form; at k >= 400 (brain lp-ntPET, k = 500) 128-draw tiles with two CTAs per SM
-// are faster (each accumulator hand-off then serves four 32-column chunks).  The
-// fp32-split operands (3 K-blocks) fit one CTA per SM, where 128-draw tiles are
-// faster.
+// Built-in defaults (measured on B300): 128-draw tiles, two CTAs per SM with
+// eight epilogue warps, for the bf16 and fp32-split operands (brain lp-ntPET
+// k = 500: main pass 30.5 ms against 37.5 with three 64-draw CTAs; total-body
+// FDG k = 200: step 385 ms against 397); the split-draws operands (two K-blocks)
+// keep three 64-draw CTAs per SM, as 128-draw tiles would leave one CTA per SM.
 Tuning default_tuning(int mode, int kmax = 0) {
-    if (mode == ABC_FP32) return Tuning{128, 2, 16, 1.5f};
-    if (mode == ABC_BF16_RESCORE && kmax >= 400) return Tuning{128, 2, 16, 1.5f};
-    return Tuning{64, 3, 16, 1.5f};
+    (void)kmax;
+    if (mode == ABC_SPLIT_DRAWS) return Tuning{64, 3, 16, 1.5f};
+    return Tuning{128, 2, 16, 1.5f};
 }
 
 // bf16 columns of the packed operands per frame: products per term of the key.
@@ -2010,8 +2009,9 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         const int per_tile = halves ? tu.bn / 2 : tu.bn;
         const int cap = kt + (kt / 4 > 64 ? kt / 4 : 64);
         I.cap = cap < I.C2 ? cap : I.C2;
-        const int limh = halves ? lim / 2 : lim;
-        I.lim = limh < I.C2 ? limh : I.C2;
+        // a half-list may grow to the whole list's limit (its capacity allows it): halving
+        // the limit would double a pilot's compactions
+        I.lim = lim < I.C2 ? lim : I.C2;
         I.lim0 = 2 * kt + per_tile < I.lim ? 2 * kt + per_tile : I.lim;
         return ABC_OK;
     };
