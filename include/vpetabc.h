@@ -64,7 +64,7 @@ extern "C" {
  *                    reported, not enforced).
  *  ABC_SPLIT_DRAWS:  the draw operand split into bf16 hi + lo, the voxel
  *                    operand rounded once (two bf16 products per term, fp32
- *                    accumulate); each voxel keeps its 4k nearest, re-scores
+ *                    accumulate); each voxel keeps its 8k nearest, re-scores
  *                    them exactly in fp32, and certifies the result with a bound
  *                    that tracks the voxel row's rounding exactly (its common
  *                    part shifts every key of the voxel alike; the rest is at

@@ -28,7 +28,8 @@
 // one coalesced store.  When a list could overflow, the warp compacts it
 // (radix select of the kt-th key, in-place filtering) and tightens the
 // threshold, so each list always holds every draw whose key is at most the
-// kt-th smallest seen (the "net": kt = 2k for ABC_FP32, else 4k).
+// kt-th smallest seen (the "net": kt = 2k for ABC_FP32, 4k for ABC_BF16_RESCORE,
+// 8k for ABC_SPLIT_DRAWS, whose voxel-row rounding widens the certificate).
 //
 // Pilot passes of the same kernel over every 16th (then 256th, ...) draw (a
 // strided TMA tensor map) first find each voxel's r-th smallest key,
@@ -149,7 +150,7 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.Kp = (int)vpet_round_up(kcols, KBLK);
     if (s.Kp < kp_min) s.Kp = kp_min;
     s.nkb = s.Kp / KBLK;
-    const int64_t net = (int64_t)(mode == ABC_FP32 ? 2 : 4) * k;
+    const int64_t net = (int64_t)(mode == ABC_FP32 ? 2 : (mode == ABC_SPLIT_DRAWS ? 8 : 4)) * k;
     s.kt = (int)(net < N ? net : N);
     s.cap = s.kt + (s.kt / 4 > 64 ? s.kt / 4 : 64);
     // Pilot levels: level i uses every stride^i-th draw and a target rank
