@@ -156,17 +156,17 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     // Pilot levels: level i uses every stride^i-th draw and a target rank
     // r_i = ceil(f r_{i-1} / stride), r_0 = kt, so that about f r_{i-1} draws of
     // the next finer level fall below its threshold.  For a small r_i the rank
-    // statistic is noisy (relative sd ~ 1 / sqrt(r_i)), so r_i grows until an
+    // statistic is noisy (relative sd ~ 1 / sqrt(r_i)), so r_i grows in steps of 1/8 until an
     // under-prediction is more than ~4 sd away.
     s.nlev = 0;
     int64_t rr = s.kt, stride = 1;
     const double f0 = tu.pilot_factor;
     while (s.nlev < MAX_PILOT_LEVELS) {
         int64_t r_next = (int64_t)ceil(f0 * (double)rr / tu.pilot_stride);
-        for (int it = 0; it < 8; ++it) {
+        for (int it = 0; it < 40; ++it) {
             const double f = (double)r_next * tu.pilot_stride / (double)rr;   // predicted count / needed
             if (1.0 - 1.0 / f >= 4.0 / sqrt((double)r_next)) break;
-            r_next = r_next + r_next / 2 + 1;
+            r_next = r_next + r_next / 8 + 1;
         }
         const int64_t n_next = N / (stride * tu.pilot_stride);
         if (n_next < 8 * r_next || n_next < 512) break;
