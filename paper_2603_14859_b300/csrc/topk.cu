@@ -104,9 +104,13 @@ struct Tuning {
 // k = 500: main pass 30.5 ms against 37.5 with three 64-draw CTAs; total-body
 // FDG k = 200: step 385 ms against 397); the split-draws operands (two K-blocks)
 // keep three 64-draw CTAs per SM, as 128-draw tiles would leave one CTA per SM.
+// ABC_FP32 aims its pilots at 2.25 kt candidates: its net (2k) takes the list as
+// it stands, whose threshold must clear the certificate's error margin (at 1.5 kt
+// ten times more C2 voxels fell back to the exact scan).
 Tuning default_tuning(int mode, int kmax = 0) {
     (void)kmax;
     if (mode == ABC_SPLIT_DRAWS) return Tuning{64, 3, 16, 1.5f};
+    if (mode == ABC_FP32) return Tuning{128, 2, 16, 2.25f};
     return Tuning{128, 2, 16, 1.5f};
 }
 
