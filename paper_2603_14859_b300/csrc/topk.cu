@@ -107,8 +107,7 @@ struct Tuning {
 // ABC_FP32 aims its pilots at 2.25 kt candidates: its net (2k) takes the list as
 // it stands, whose threshold must clear the certificate's error margin (at 1.5 kt
 // ten times more C2 voxels fell back to the exact scan).
-Tuning default_tuning(int mode, int kmax = 0) {
-    (void)kmax;
+Tuning default_tuning(int mode) {
     if (mode == ABC_SPLIT_DRAWS) return Tuning{64, 3, 16, 1.5f};
     if (mode == ABC_FP32) return Tuning{128, 2, 16, 2.25f};
     return Tuning{128, 2, 16, 1.5f};
@@ -2187,16 +2186,16 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
 bool g_has_default = false;   // abc_set_default_tuning was called
 Tuning g_default_tuning = default_tuning(ABC_BF16_RESCORE);
 
-Tuning tuning_for(int mode, int kmax) { return g_has_default ? g_default_tuning : default_tuning(mode, kmax); }
+Tuning tuning_for(int mode) { return g_has_default ? g_default_tuning : default_tuning(mode); }
 
 ScanSpec single(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w, int k,
                 int32_t* idx, float* dist) {
     return ScanSpec{y, J, ldy, x, N, ldx, L, w, k, idx, dist};
 }
 
-int to_tuning(const abc_tuning* t, int mode, int kmax, Tuning* out) {
+int to_tuning(const abc_tuning* t, int mode, Tuning* out) {
     if (!t) {
-        *out = tuning_for(mode, kmax);
+        *out = tuning_for(mode);
         return ABC_OK;
     }
     *out = Tuning{t->bn, t->ctas_per_sm, t->pilot_stride, t->pilot_factor};
@@ -2220,7 +2219,7 @@ namespace vpet {
 size_t topk_workspace_bytes(int64_t J, int64_t N, int L, int k, int precision) {
     ScanSpec c = single(nullptr, J, L, nullptr, N, L, L, nullptr, k, nullptr, nullptr);
     BatchLayout* B = new BatchLayout;
-    make_batch_layout(&c, 1, precision, tuning_for(precision, k), B);
+    make_batch_layout(&c, 1, precision, tuning_for(precision), B);
     const size_t t = B->total;
     delete B;
     return t;
@@ -2229,7 +2228,7 @@ size_t topk_workspace_bytes(int64_t J, int64_t N, int L, int k, int precision) {
 int topk_on_workspace(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w,
                       int k, int precision, void* ws, size_t ws_bytes, int32_t* idx, float* dist, cudaStream_t s) {
     const ScanSpec c = single(y, J, ldy, x, N, ldx, L, w, k, idx, dist);
-    return run_batch(&c, 1, precision, tuning_for(precision, k), ws, ws_bytes, nullptr, 0, s);
+    return run_batch(&c, 1, precision, tuning_for(precision), ws, ws_bytes, nullptr, 0, s);
 }
 
 }  // namespace vpet
@@ -2265,7 +2264,7 @@ extern "C" int abc_default_tuning(int32_t precision, abc_tuning* out) {
     VPET_ARG(out, "abc_default_tuning: null pointer");
     VPET_ARG(precision == ABC_FP32 || precision == ABC_BF16_RESCORE || precision == ABC_SPLIT_DRAWS,
              "abc_default_tuning: unknown precision");
-    const Tuning t = tuning_for(precision, 0);
+    const Tuning t = tuning_for(precision);
     out->bn = t.bn;
     out->ctas_per_sm = t.ctas_per_sm;
     out->pilot_stride = t.pilot_stride;
@@ -2276,7 +2275,7 @@ extern "C" int abc_default_tuning(int32_t precision, abc_tuning* out) {
 extern "C" int abc_set_default_tuning(const abc_tuning* t) {
     vpet::clear_error();
     Tuning tu;
-    const int rc = to_tuning(t, ABC_BF16_RESCORE, 0, &tu);
+    const int rc = to_tuning(t, ABC_BF16_RESCORE, &tu);
     if (rc) return rc;
     g_has_default = t != nullptr;
     if (t) g_default_tuning = tu;
@@ -2293,9 +2292,7 @@ extern "C" size_t abc_batch_workspace_size(const abc_scan* scans, int32_t n_scan
         sp[i] = ScanSpec{c.y_dev, c.J, c.ldy, c.x_dev, c.N, c.ldx, c.L, c.w_host, c.k, c.idx_dev, c.dist_dev};
     }
     BatchLayout* B = new BatchLayout;
-    int kmax = 0;
-    for (int i = 0; i < n_scans; ++i) kmax = sp[i].k > kmax ? sp[i].k : kmax;
-    make_batch_layout(sp, n_scans, precision, tuning_for(precision, kmax), B);
+    make_batch_layout(sp, n_scans, precision, tuning_for(precision), B);
     const size_t t = B->total;
     delete B;
     return t;
@@ -2308,9 +2305,7 @@ extern "C" int abc_batch_discrepancy_topk(const abc_scan* scans, int32_t n_scans
     int rc = gather_scans(scans, n_scans, sp);
     if (rc) return rc;
     Tuning tu;
-    int kmax = 0;
-    for (int i = 0; i < n_scans; ++i) kmax = sp[i].k > kmax ? sp[i].k : kmax;
-    if ((rc = to_tuning(tuning, precision, kmax, &tu))) return rc;
+    if ((rc = to_tuning(tuning, precision, &tu))) return rc;
     return run_batch(sp, n_scans, precision, tu, workspace, ws_bytes, nullptr, 0, (cudaStream_t)stream);
 }
 
@@ -2340,7 +2335,7 @@ extern "C" int abc_debug_gemm_keys(const float* y_dev, int64_t J, int32_t ldy, c
     vpet::clear_error();
     VPET_ARG(dump_dev && ld_dump >= vpet_round_up(N, 128), "abc_debug_gemm_keys: dump too small");
     const ScanSpec c = single(y_dev, J, ldy, x_dev, N, ldx, L, w_host, 1, nullptr, nullptr);
-    return run_batch(&c, 1, precision, tuning_for(precision, 1), workspace, ws_bytes, dump_dev, ld_dump,
+    return run_batch(&c, 1, precision, tuning_for(precision), workspace, ws_bytes, dump_dev, ld_dump,
                      (cudaStream_t)stream);
 }
 
