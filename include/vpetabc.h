@@ -288,7 +288,8 @@ int abc_model_select(const int32_t* idx_dev, int64_t J, int32_t k, const int64_t
  *   sample), two passes about the mean;  lo / hi: the 0.025 / 0.975 quantiles
  *   by linear interpolation between order statistics (type 7).  Sums are
  *   compensated fp32 (relative error near 2^-24 for any k).
- * Each output is J x ncols fp32, row-major. */
+ * Each output is J x ncols fp32, row-major.  k in 1..2048, J <= 2^31 - 1;
+ * ABC_ERR_ARG for arguments out of range (nothing launched). */
 int abc_summarize(const float* theta_dev, int32_t ldtheta, const int64_t* model_offsets_host, int32_t M,
                   const int32_t* nparams_host, const int32_t* has_ki_host, const int32_t* ki_cols_host,
                   const int32_t* idx_dev, int64_t J, int32_t k, const int8_t* preferred_dev, int32_t ncols,

@@ -128,12 +128,8 @@ __device__ __forceinline__ LinearCut warp_cut_linear(const float* keys, int cnt,
             v[u] = i < cnt ? keys[seg_pos(i, c0, off1)] : 0.0f;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = base + 32 * u + lane;
-            const uint32_t bin = i < cnt ? (uint32_t)linear_bin(v[u], c) : (0x100u | (uint32_t)lane);
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin);
-            if (i < cnt && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
-        }
+        for (int u = 0; u < 4; ++u)
+            if (base + 32 * u + lane < cnt) atomicAdd(&hist[linear_bin(v[u], c)], 1u);
     }
     __syncwarp();
     uint32_t loc[8], sum = 0;

@@ -1,6 +1,6 @@
 // Posterior model probabilities and posterior summaries over each voxel's
 // accepted draws (Sec. II-B Eq. 6, Sec. II-D, Sec. III-B).  One warp per voxel;
-// fp64 accumulation for means and variances; credible intervals from exact
+// compensated fp32 sums for means and variances; credible intervals from exact
 // order statistics (radix selection, type-7 interpolation).
 #include <string.h>
 
@@ -29,10 +29,20 @@ __global__ void k_model_select(const int32_t* __restrict__ idx, int64_t J, int k
     int cnt[MAXM];
 #pragma unroll
     for (int m = 0; m < MAXM; ++m) cnt[m] = 0;
-    for (int r = lane; r < k; r += 32) {
-        const int m = model_of(idx[j * k + r], S);
+    // four 32-index chunks per round, their loads in flight together
+    for (int base = 0; base < k; base += 128) {
+        int32_t id[4];
 #pragma unroll
-        for (int q = 0; q < MAXM; ++q) cnt[q] += (q == m);
+        for (int u = 0; u < 4; ++u) {
+            const int r = base + 32 * u + lane;
+            id[u] = r < k ? idx[j * k + r] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int m = base + 32 * u + lane < k ? model_of(id[u], S) : -1;
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q) cnt[q] += (q == m);
+        }
     }
     int best = 0, bestc = -1;
 #pragma unroll
@@ -135,12 +145,9 @@ __device__ float warp_kth_radix(const float* s, int n, int r, uint32_t* hist, in
 // bin of each rank; the members of those bins (at most 256 in all) are gathered
 // into hist and each rank resolved by counting within its bin.  Crowded bins
 // (or an unbounded range) take the radix select per rank.
-__device__ void warp_order4(const float* s, int n, const int (&rk)[4], uint32_t* hist, int lane, float (&out)[4]) {
-    float mn = 3.0e38f, mx = -3.0e38f;
-    for (int i = lane; i < n; i += 32) {
-        mn = fminf(mn, s[i]);
-        mx = fmaxf(mx, s[i]);
-    }
+// mn / mx: this lane's minimum and maximum over its values s[lane + 32 i].
+__device__ void warp_order4(const float* s, int n, const int (&rk)[4], uint32_t* hist, int lane, float mn, float mx,
+                            float (&out)[4]) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mn = fminf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
@@ -163,12 +170,7 @@ __device__ void warp_order4(const float* s, int n, const int (&rk)[4], uint32_t*
     };
     for (int b = lane; b < 256; b += 32) hist[b] = 0;
     __syncwarp();
-    for (int i0 = 0; i0 < n; i0 += 32) {
-        const int i = i0 + lane;
-        const uint32_t bin = i < n ? (uint32_t)bin_of(s[i]) : (0x100u | (uint32_t)lane);
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin);
-        if (bin < 256u && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
-    }
+    for (int i = lane; i < n; i += 32) atomicAdd(&hist[bin_of(s[i])], 1u);
     __syncwarp();
     uint32_t loc[8], sum = 0;
 #pragma unroll
@@ -263,17 +265,20 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
         }
     // accepted draws of the summarised model, in accepted order
     int n = 0;
-    for (int base = 0; base < Q.k; base += 32) {
-        const int r = base + lane;
-        int32_t id = 0;
-        bool take = false;
-        if (r < Q.k) {
-            id = idx[j * Q.k + r];
-            take = id >= 0 && (pm < 0 || model_of(id, Q.S) == pm);
+    for (int base = 0; base < Q.k; base += 128) {
+        int32_t id[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = base + 32 * u + lane;
+            id[u] = r < Q.k ? idx[j * Q.k + r] : -1;
         }
-        const uint32_t b = __ballot_sync(0xFFFFFFFFu, take);
-        if (take) sel[n + __popc(b & ((1u << lane) - 1u))] = id;
-        n += __popc(b);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool take = id[u] >= 0 && (pm < 0 || model_of(id[u], Q.S) == pm);
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, take);
+            if (take) sel[n + __popc(b & ((1u << lane) - 1u))] = id[u];
+            n += __popc(b);
+        }
     }
     __syncwarp();
     const float qnan = __int_as_float(0x7FC00000);
@@ -283,18 +288,35 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
         if (n > 0 && ((isk && ki) || (!isk && col < P))) {
             // fp32 throughout (compensated sums): the values are fp32 and the sums'
             // relative error stays near 2^-24 for any k
+            // eight 32-value rounds per gather, their loads in flight together
             CSum s;
-            for (int i = lane; i < n; i += 32) {
-                const float* th = theta + (int64_t)sel[i] * Q.ldt;
-                float v;
-                if (isk) {
-                    const float K1 = th[Q.ki[0]], k2 = th[Q.ki[1]], k3 = th[Q.ki[2]];
-                    v = K1 * k3 / (k2 + k3);
-                } else {
-                    v = th[col];
+            float mn = 3.0e38f, mx = -3.0e38f;
+            for (int i0 = 0; i0 < n; i0 += 256) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + 32 * u + lane;
+                    v[u] = 0.0f;
+                    if (i < n) {
+                        const float* th = theta + (int64_t)sel[i] * Q.ldt;
+                        if (isk) {
+                            const float K1 = th[Q.ki[0]], k2 = th[Q.ki[1]], k3 = th[Q.ki[2]];
+                            v[u] = K1 * k3 / (k2 + k3);
+                        } else {
+                            v[u] = th[col];
+                        }
+                    }
                 }
-                vals[i] = v;
-                s.add(v);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + 32 * u + lane;
+                    if (i < n) {
+                        vals[i] = v[u];
+                        s.add(v[u]);
+                        mn = fminf(mn, v[u]);
+                        mx = fmaxf(mx, v[u]);
+                    }
+                }
             }
             const float mu = warp_csum(s) / (float)n;
             CSum ss;
@@ -317,7 +339,7 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
                 rk[2 * t] = a;
                 rk[2 * t + 1] = a + 1 < n ? a + 1 : n - 1;
             }
-            warp_order4(vals, n, rk, hist, lane, os);
+            warp_order4(vals, n, rk, hist, lane, mn, mx, os);
             for (int t = 0; t < 2; ++t) qv[t] = fmaf(fr[t], os[2 * t + 1] - os[2 * t], os[2 * t]);
             o0 = mu;
             o1 = n > 1 ? sqrtf(sst / (float)(n - 1)) : 0.0f;

@@ -42,3 +42,30 @@ def test_select_and_summaries(orc, k):
         m = ~np.isnan(b)
         assert np.array_equal(np.isnan(a), np.isnan(b))
         assert np.all(np.abs(a[m] - b[m]) <= 1e-5 * np.abs(b[m]) + 1e-7)
+
+
+@pytest.mark.parametrize("k,P", [(2048, 30), (777, 12)])
+def test_summaries_wide_rows(orc, k, P):
+    """Many parameters at the largest k (the rows' columns are gathered in groups when
+    one voxel's columns do not fit in shared memory together)."""
+    from paper_2603_14859_b300 import api
+    rng = np.random.default_rng(k + P)
+    N = 6000
+    off = [0, 2500, 6000]
+    ld = P + 2
+    theta = rng.gamma(2.0, 0.3, (N, ld)).astype(np.float32)
+    J = 23
+    idx = np.stack([rng.choice(N, k, replace=False) for _ in range(J)]).astype(np.int32)
+    ti, tt = torch.from_numpy(idx).cuda(), torch.from_numpy(theta).cuda()
+    _, pref = api.model_select(ti, off)
+    _, opref = orc.model_select(idx, off)
+    nparams, has_ki = [P - 3, P], [0, 1]
+    for pr, opr in ((pref, opref), (None, None)):
+        g = api.summarize(tt, off, nparams, has_ki, [1, 4, 2], ti, pr)
+        o = orc.summarize(theta, off, nparams, has_ki, [1, 4, 2], idx, opr)
+        for a, b in zip(g, o):
+            a = a.cpu().numpy().astype(np.float64)
+            assert a.shape == (J, P + 1)
+            assert np.array_equal(np.isnan(a), np.isnan(b))
+            m = ~np.isnan(b)
+            assert np.all(np.abs(a[m] - b[m]) <= 1e-5 * np.abs(b[m]) + 1e-7)
