@@ -682,12 +682,7 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
             for (int q = 1; q < nw; ++q) { kmn = min(kmn, redu[q]); kmx = max(kmx, redu[16 + q]); }
             int shift = 0;
             while (((kmx - kmn) >> shift) >= 256u) ++shift;
-            for (int i0 = 0; i0 < A.n_pilot; i0 += blockDim.x) {
-                const int i = i0 + threadIdx.x;
-                const uint32_t bin = i < A.n_pilot ? (f2key(keys[i]) - kmn) >> shift : 256u;
-                const uint32_t same = __match_any_sync(0xFFFFFFFFu, bin);
-                if (bin < 256u && lane == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
-            }
+            for (int i = threadIdx.x; i < A.n_pilot; i += blockDim.x) atomicAdd(&hist[(f2key(keys[i]) - kmn) >> shift], 1u);
             __syncthreads();
             if (wp == 0) warp_find_bin(hist, A.r_lo, lane, &sh[0], &sh[1]);
             if (wp == 1) warp_find_bin(hist, A.r_hi, lane, &sh[2], &sh[3]);
@@ -725,12 +720,7 @@ __global__ void __launch_bounds__(LA_THREADS, 2) k_local_abc(LocalArgs A) {
                 // then the members of the bins holding the two ranks, resolved by counting
                 int shift2 = 0;
                 while (((hi - lo) >> shift2) >= 256u) ++shift2;
-                for (int c0 = 0; c0 < n_c; c0 += blockDim.x) {
-                    const int c = c0 + threadIdx.x;
-                    const uint32_t bin = c < n_c ? (f2key(ckey[c]) - lo) >> shift2 : 256u;
-                    const uint32_t same = __match_any_sync(0xFFFFFFFFu, bin);
-                    if (bin < 256u && lane == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
-                }
+                for (int c = threadIdx.x; c < n_c; c += blockDim.x) atomicAdd(&hist[(f2key(ckey[c]) - lo) >> shift2], 1u);
                 __syncthreads();
                 if (wp == 0) warp_find_bin(hist, rk0, lane, &sh[0], &sh[1]);
                 if (wp == 1) warp_find_bin(hist, rk1, lane, &sh[2], &sh[3]);
