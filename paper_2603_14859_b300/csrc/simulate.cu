@@ -380,8 +380,31 @@ __global__ void __launch_bounds__(SIM_THREADS) k_simulate(SimParams p, const flo
     extern __shared__ float s_acc[];   // [L][SIM_THREADS]: frame integrals of this block's draws
     const int tid = threadIdx.x;
     const int64_t n0 = (int64_t)blockIdx.x * SIM_THREADS;
-    const int64_t n = n0 + tid;
-    float* acc = s_acc + tid;
+    int slot = tid;                    // the block's draw this thread simulates
+    if (MODEL == ABC_LPNTPET) {
+        // threads take the block's draws in order of t_D (the integrator runs from t_D to
+        // the last frame, so a warp's lanes then take similar numbers of steps); ranks by
+        // (order-preserving bits of t_D, position) are a permutation for any values
+        __shared__ uint32_t s_key[SIM_THREADS];
+        __shared__ int s_slot[SIM_THREADS];
+        uint32_t key = 0xFFFFFFFFu;
+        if (n0 + tid < N) {
+            const uint32_t b = __float_as_uint(theta[(n0 + tid) * ldt + 4]);
+            key = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+        }
+        s_key[tid] = key;
+        __syncthreads();
+        int rank = 0;
+        for (int i = 0; i < SIM_THREADS; ++i) {
+            const uint32_t o = s_key[i];
+            rank += (o < key) || (o == key && i < tid);
+        }
+        s_slot[rank] = tid;
+        __syncthreads();
+        slot = s_slot[tid];
+    }
+    const int64_t n = n0 + slot;
+    float* acc = s_acc + slot;
     for (int l = 0; l < p.L; ++l) acc[l * SIM_THREADS] = 0.0f;
     float* crtab = nullptr;
     if (MODEL == ABC_LPNTPET && p.lp_ntab > 0) {
