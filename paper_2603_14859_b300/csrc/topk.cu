@@ -504,64 +504,92 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
     }
 }
 
-// One warp per draw row: B row of the GEMM.
+// One warp per four draw rows: B rows of the GEMM.
 // Row n of B is draw xperm[n] (xperm = null: draw n); fx[3 n + c] = its segment
 // features; xs row n (stride ldxs, zero-padded) = that draw's fp32 TAC, so that
-// the exact re-score reads the draws in packed order.
-__global__ void k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int ldx, int L, int Kp, int mode,
-                         Weights W, const float* __restrict__ mu, const int32_t* __restrict__ xperm,
-                         __nv_bfloat16* __restrict__ B, float* __restrict__ fx, float* __restrict__ xs,
-                         int ldxs) {
+// the exact re-score reads the draws in packed order.  The warp's four source
+// rows are read into shared memory with all their loads in flight together.
+constexpr int PACK_ROWS = 4;
+__global__ void __launch_bounds__(256) k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int ldx, int L,
+                                                int Kp, int mode, Weights W, const float* __restrict__ mu,
+                                                const int32_t* __restrict__ xperm, __nv_bfloat16* __restrict__ B,
+                                                float* __restrict__ fx, float* __restrict__ xs, int ldxs) {
     __shared__ FrameConsts F;
+    __shared__ float s_rows[8][PACK_ROWS][MAXL];
     stage_frame_consts(F, W, mu, L);
-    const int lane = threadIdx.x & 31;
-    const int64_t n = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (n >= Np) return;
-    __nv_bfloat16* row = B + n * Kp;
-    if (n >= N) {
-        for (int e = lane; e < Kp; e += 32) row[e] = bf(0.0f);
-        return;
-    }
-    const float* xr = x + (xperm ? (int64_t)xperm[n] : n) * ldx;
-    for (int l = lane; l < ldxs; l += 32) xs[n * ldxs + l] = l < L ? xr[l] : 0.0f;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t nb = ((int64_t)blockIdx.x * 8 + wid) * PACK_ROWS;
+    if (nb >= Np) return;
     {
-        float f[3];
-        seg_features(xr, L, F.w, lane, f);
-        if (lane == 0) {
-            fx[3 * n] = f[0];
-            fx[3 * n + 1] = f[1];
-            fx[3 * n + 2] = f[2];
+        int64_t src[PACK_ROWS];
+#pragma unroll
+        for (int u = 0; u < PACK_ROWS; ++u) {
+            const int64_t n = nb + u;
+            src[u] = n < N ? (xperm ? (int64_t)xperm[n] : n) : -1;
         }
+        float v[PACK_ROWS][2];
+#pragma unroll
+        for (int u = 0; u < PACK_ROWS; ++u)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int l = lane + 32 * q;
+                v[u][q] = (src[u] >= 0 && l < L) ? x[src[u] * ldx + l] : 0.0f;
+            }
+#pragma unroll
+        for (int u = 0; u < PACK_ROWS; ++u)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) s_rows[wid][u][lane + 32 * q] = v[u][q];
+        __syncwarp();
     }
-    float ss = 0.0f;
-    for (int l = lane; l < L; l += 32) {
-        float v = F.sw[l] * (xr[l] - F.mu[l]);
-        if (mode == ABC_BF16_RESCORE) v = __bfloat162float(bf(v));   // norm of the rounded vector
-        ss = fmaf(v, v, ss);
-    }
-    ss = warp_sum(ss);
-    const float n1 = __bfloat162float(bf(ss));
-    const float r1 = ss - n1;
-    const float n2 = __bfloat162float(bf(r1));
-    const float n3 = r1 - n2;
-    const int aug = cols_per_frame(mode) * L;
-    for (int e = lane; e < Kp; e += 32) {
-        float out = 0.0f;
-        if (e < aug) {
-            const int l = e % L;
-            const float v = F.sw[l] * (xr[l] - F.mu[l]);
-            const float hi = __bfloat162float(bf(v));
-            if (mode == ABC_FP32) out = -2.0f * ((e >= L && e < 2 * L) ? (v - hi) : hi);
-            else if (mode == ABC_SPLIT_DRAWS) out = -2.0f * (e >= L ? (v - hi) : hi);
-            else out = -2.0f * hi;
-        } else if (e == aug) {
-            out = n1;
-        } else if (e == aug + 1) {
-            out = n2;
-        } else if (e == aug + 2) {
-            out = n3;
+    for (int u = 0; u < PACK_ROWS; ++u) {
+        const int64_t n = nb + u;
+        if (n >= Np) break;
+        __nv_bfloat16* row = B + n * Kp;
+        if (n >= N) {
+            for (int e = lane; e < Kp; e += 32) row[e] = bf(0.0f);
+            continue;
         }
-        row[e] = bf(out);
+        const float* xr = s_rows[wid][u];
+        for (int l = lane; l < ldxs; l += 32) xs[n * ldxs + l] = l < L ? xr[l] : 0.0f;
+        {
+            float f[3];
+            seg_features(xr, L, F.w, lane, f);
+            if (lane == 0) {
+                fx[3 * n] = f[0];
+                fx[3 * n + 1] = f[1];
+                fx[3 * n + 2] = f[2];
+            }
+        }
+        float ss = 0.0f;
+        for (int l = lane; l < L; l += 32) {
+            float v = F.sw[l] * (xr[l] - F.mu[l]);
+            if (mode == ABC_BF16_RESCORE) v = __bfloat162float(bf(v));   // norm of the rounded vector
+            ss = fmaf(v, v, ss);
+        }
+        ss = warp_sum(ss);
+        const float n1 = __bfloat162float(bf(ss));
+        const float r1 = ss - n1;
+        const float n2 = __bfloat162float(bf(r1));
+        const float n3 = r1 - n2;
+        const int aug = cols_per_frame(mode) * L;
+        for (int e = lane; e < Kp; e += 32) {
+            float out = 0.0f;
+            if (e < aug) {
+                const int l = e % L;
+                const float v = F.sw[l] * (xr[l] - F.mu[l]);
+                const float hi = __bfloat162float(bf(v));
+                if (mode == ABC_FP32) out = -2.0f * ((e >= L && e < 2 * L) ? (v - hi) : hi);
+                else if (mode == ABC_SPLIT_DRAWS) out = -2.0f * (e >= L ? (v - hi) : hi);
+                else out = -2.0f * hi;
+            } else if (e == aug) {
+                out = n1;
+            } else if (e == aug + 1) {
+                out = n2;
+            } else if (e == aug + 2) {
+                out = n3;
+            }
+            row[e] = bf(out);
+        }
     }
 }
 
@@ -1965,7 +1993,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             k_order_scatter<<<gb, 256, 0, s>>>(p.xfeat, p.xmm, L.N, L.nlev, tu.pilot_stride, p.xhist, p.xperm);
             VPET_LAUNCH_CHECK();
         }
-        k_pack_x<<<(unsigned)vpet_ceil_div(L.Np, 8), 256, 0, s>>>(sc[i].x, L.N, L.Np, sc[i].ldx, L.L, L.Kp, mode, W,
+        k_pack_x<<<(unsigned)vpet_ceil_div(L.Np, 8 * PACK_ROWS), 256, 0, s>>>(sc[i].x, L.N, L.Np, sc[i].ldx, L.L, L.Kp, mode, W,
                                                                   p.mu, xorder ? p.xperm : nullptr, p.B, p.fx, p.xs,
                                                                   L.ldxs);
         VPET_LAUNCH_CHECK();
