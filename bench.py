@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--proposals", type=int, default=10_000, help="learned workload: proposals per voxel")
     ap.add_argument("--train-pairs", type=int, default=10_000_000, help="learned workload: training pairs")
     ap.add_argument("--sigma-scale", type=float, default=1.0, help="learned workload: proposal widening")
+    ap.add_argument("--tuning", default=None,
+                    help="single-scan workloads: launch tuning bn,ctas_per_sm,pilot_stride,pilot_factor "
+                         "(default: the library's per-precision default)")
     return ap.parse_args()
 
 
@@ -525,6 +528,11 @@ def main():
            "voxels_per_gpu": W.J, "draws": W.N, "frames": W.L, "k": W.k,
            "precision": args.precision, "l2": "inputs larger than L2 (draw operands + candidate lists > 126 MB)",
            "parallelism": f"voxel shards x{args.gpus}" if args.gpus > 1 else "single GPU"}
+    if args.tuning and args.impl != "reference":
+        from paper_2603_14859_b300 import api as _api
+        bn, cps, st, fac = args.tuning.split(",")
+        _api.set_default_tuning(int(bn), int(cps), int(st), float(fac))
+        cfg["tuning"] = {"bn": int(bn), "ctas_per_sm": int(cps), "pilot_stride": int(st), "pilot_factor": float(fac)}
 
     if args.impl == "reference":
         if rank != 0:
