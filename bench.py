@@ -76,6 +76,15 @@ def parse():
     return ap.parse_args()
 
 
+def kernel_source_sha1() -> str:
+    """Hash of the sources the fused kernel is built from; a traffic record taken
+    from an older build is not reported."""
+    h = hashlib.sha1()
+    for f in ("topk.cu", "select.cuh", "tc_ptx.cuh", "topk_internal.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2603_14859_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples every 200 ms while the timed region runs."""
@@ -641,8 +650,7 @@ def main():
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
-        src = open(os.path.join(ROOT, "paper_2603_14859_b300", "csrc", "topk.cu"), "rb").read()
-        h = hashlib.sha1(src).hexdigest()[:12]
+        h = kernel_source_sha1()
         rec = json.load(open(tp)).get(f"{args.workload}/{args.precision}")
         if rec and rec.get("source_sha1") == h:
             traffic = rec["bytes_per_launch"]
