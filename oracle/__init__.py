@@ -53,6 +53,7 @@ def lib():
         L.orc_model_select.argtypes = [P, i64, ctypes.c_int, P, ctypes.c_int, P, P]
         L.orc_summarize.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, P, P, P, i64, ctypes.c_int, P,
                                     ctypes.c_int, P, P, P, P]
+        L.orc_response_cri.argtypes = [P, ctypes.c_int, P, i64, ctypes.c_int, i64, i64, P, ctypes.c_int, P, P, P]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_Phi.argtypes = [f64]
         L.orc_Phi.restype = f64
@@ -189,6 +190,20 @@ def summarize(theta, offsets, nparams, has_ki, ki_cols, idx, pref=None):
     pr = _c(pref, np.int8) if pref is not None else None
     lib().orc_summarize(_p(th), th.shape[1], _p(off), len(off) - 1, _p(npar), _p(hk), _p(kc), _p(idx), J, k,
                         _p(pr) if pr is not None else None, Pmax, *[_p(o) for o in outs])
+    return tuple(outs)
+
+
+def response_cri(theta, first, last, t, idx):
+    """Posterior mean and 95 % band (type 7) of the lp-ntPET response function
+    1 + (gamma / k2a) g(t) at the times t; each J x T."""
+    th = _c(theta, np.float32)
+    idx = _c(idx, np.int32)
+    tt = _c(t, np.float64)
+    J, k = idx.shape
+    T = len(tt)
+    outs = [np.zeros((J, T)) for _ in range(3)]
+    lib().orc_response_cri(_p(th), th.shape[1], _p(idx), J, k, int(first), int(last), _p(tt), T,
+                           *[_p(o) for o in outs])
     return tuple(outs)
 
 

@@ -22,7 +22,9 @@
  *   - model probabilities and preferred model (Sec. III-B, "more than 50 %");
  *   - posterior summaries: mean, SD (ddof = 1), equal-tailed 95 % interval
  *     by type-7 interpolation, and K_i = K1 k3 / (k2 + k3) per accepted sample
- *     (Sec. II-D point estimates; Sec. III-B K_i map).
+ *     (Sec. II-D point estimates; Sec. III-B K_i map);
+ *   - the lp-ntPET response function 1 + (gamma / k2a) g(t) and its 95 %
+ *     credible band over a time grid (Sec. II-D).
  *
  * Parity status of each function is listed next to it ("pinned by" names the
  * tests that tie it to something other than itself).
@@ -557,6 +559,39 @@ int orc_summarize(const float* theta, int ldtheta, const int64_t* off, int M, co
             hi[j * nc + col] = o[3];
         }
     }
+    free(v);
+    return 0;
+}
+
+/* Response function of the lp-ntPET model (Sec. II-D, the response-function
+ * figure): k2a(t) / k2a = 1 + (gamma / k2a) g(t), with k2a = k2 / (1 + BP_ND) and g
+ * the gamma variate above.  For voxel j, over its accepted draws whose global
+ * index lies in [first, last) (the lp-ntPET draws: columns R1, k2, BP_ND, gamma,
+ * t_D, t_P - t_D, alpha), at each time t[m]: the posterior mean and the 0.025 /
+ * 0.975 type-7 quantiles of the response.  NaN where no accepted draw qualifies.
+ * Pinned by: gamma = 0 (flat response 1), times before every t_D (1), a single
+ * accepted draw at t = t_P (1 + gamma / k2a exactly), and numpy's quantiles of
+ * values computed from the closed form of g in tests/test_oracle_sim.py. */
+int orc_response_cri(const float* theta, int ldtheta, const int32_t* idx, int64_t J, int k, int64_t first,
+                     int64_t last, const double* t, int T, double* mean, double* lo, double* hi) {
+    double* v = (double*)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    for (int64_t j = 0; j < J; ++j)
+        for (int m = 0; m < T; ++m) {
+            int n = 0;
+            for (int r = 0; r < k; ++r) {
+                const int64_t i = idx[j * k + r];
+                if (i < first || i >= last) continue;
+                const float* th = theta + i * ldtheta;
+                const double k2a = (double)th[1] / (1.0 + (double)th[2]);
+                const double tD = th[4], tP = (double)th[4] + (double)th[5];
+                v[n++] = 1.0 + (double)th[3] / k2a * orc_gamma_variate(t[m], tD, tP, th[6]);
+            }
+            double o[4] = {NAN, NAN, NAN, NAN};
+            if (n > 0) stats(v, n, o);
+            mean[j * T + m] = o[0];
+            lo[j * T + m] = o[2];
+            hi[j * T + m] = o[3];
+        }
     free(v);
     return 0;
 }

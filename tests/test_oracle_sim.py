@@ -185,3 +185,60 @@ def test_gauss_legendre_nodes_exact_on_polynomials(orc):
     for deg in range(0, 40):
         exact = 0.0 if deg % 2 else 2.0 / (deg + 1)
         assert (w * x**deg).sum() == pytest.approx(exact, abs=1e-14)
+
+
+def _lp_rows(rng, n, gamma=None):
+    """lp-ntPET parameter rows (R1, k2, BP_ND, gamma, t_D, t_P - t_D, alpha) inside the priors."""
+    lo, hi = S.PRIORS[S.LPNTPET]
+    th = rng.uniform(lo, hi, (n, 7)).astype(np.float32)
+    if gamma is not None:
+        th[:, 3] = gamma
+    return th
+
+
+def test_response_band_flat_without_activation(orc):
+    """gamma = 0 leaves k2a(t) = k2a: the band is the constant 1 at every time."""
+    rng = np.random.default_rng(11)
+    th = _lp_rows(rng, 300, gamma=0.0)
+    idx = rng.integers(0, 300, (5, 40)).astype(np.int32)
+    mean, lo, hi = orc.response_cri(th, 0, 300, np.linspace(0, 60, 13), idx)
+    assert np.all(mean == 1.0) and np.all(lo == 1.0) and np.all(hi == 1.0)
+
+
+def test_response_band_before_onset_and_at_peak(orc):
+    """Before every t_D the response is 1; one accepted draw at its own t_P gives
+    1 + gamma / k2a = 1 + gamma (1 + BP_ND) / k2 (g(t_P) = 1)."""
+    rng = np.random.default_rng(12)
+    th = _lp_rows(rng, 50)
+    idx = np.arange(50, dtype=np.int32).reshape(5, 10)
+    mean, lo, hi = orc.response_cri(th, 0, 50, [0.0, 5.0, float(th[:, 4].min()) - 1e-3], idx)
+    assert np.all(mean == 1.0) and np.all(lo == 1.0) and np.all(hi == 1.0)
+    for i in (0, 17, 49):
+        r = th[i].astype(np.float64)
+        tP = r[4] + r[5]
+        m, a, b = orc.response_cri(th, 0, 50, [tP], np.array([[i]], np.int32))
+        want = 1.0 + r[3] * (1.0 + r[2]) / r[1]
+        assert m[0, 0] == pytest.approx(want, rel=1e-12) and a[0, 0] == m[0, 0] and b[0, 0] == m[0, 0]
+
+
+def test_response_band_matches_direct_quantiles(orc):
+    """Mean and type-7 quantiles against numpy on responses written from the closed
+    form x^alpha exp(alpha (1 - x)), x = (t - t_D) / (t_P - t_D); draws outside
+    [first, last) (the other model's) are ignored; none left gives NaN."""
+    rng = np.random.default_rng(13)
+    th = np.vstack([rng.uniform(0, 1, (400, 7)).astype(np.float32), _lp_rows(rng, 600)])
+    first, last = 400, 1000
+    idx = rng.integers(0, 1000, (6, 75)).astype(np.int32)
+    idx[5] = rng.integers(0, 400, 75)                # no lp-ntPET draw accepted
+    ts = np.array([21.0, 30.0, 37.5, 45.0, 59.0])
+    mean, lo, hi = orc.response_cri(th, first, last, ts, idx)
+    for j in range(5):
+        rows = th[idx[j][(idx[j] >= first) & (idx[j] < last)]].astype(np.float64)
+        for m, t in enumerate(ts):
+            x = (t - rows[:, 4]) / rows[:, 5]
+            g = np.where(x > 0, np.abs(x) ** rows[:, 6] * np.exp(rows[:, 6] * (1.0 - x)), 0.0)
+            v = 1.0 + rows[:, 3] * (1.0 + rows[:, 2]) / rows[:, 1] * g
+            assert mean[j, m] == pytest.approx(v.mean(), rel=1e-12)
+            assert lo[j, m] == pytest.approx(np.quantile(v, 0.025), rel=1e-12, abs=1e-15)
+            assert hi[j, m] == pytest.approx(np.quantile(v, 0.975), rel=1e-12, abs=1e-15)
+    assert np.all(np.isnan(mean[5])) and np.all(np.isnan(lo[5])) and np.all(np.isnan(hi[5]))
