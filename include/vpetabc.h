@@ -295,6 +295,25 @@ int abc_summarize(const float* theta_dev, int32_t ldtheta, const int64_t* model_
                   const int32_t* idx_dev, int64_t J, int32_t k, const int8_t* preferred_dev, int32_t ncols,
                   float* mean_dev, float* sd_dev, float* lo_dev, float* hi_dev, void* stream);
 
+/* Posterior band of the lp-ntPET response function (Sec. II-D and its
+ * response-function figure): k2a(t) / k2a = 1 + (gamma / k2a) g(t), k2a =
+ * k2 / (1 + BP_ND), g the gamma variate of Eq. 4 normalised to 1 at t_P (0 before
+ * t_D; x^alpha e^{alpha (1 - x)}, x = (t - t_D) / (t_P - t_D), after).
+ *   theta_dev: draw parameters, row i at theta_dev + i * ldtheta (ldtheta >= 7); the
+ *     lp-ntPET draws are the global indices [first, last), their columns R1, k2,
+ *     BP_ND, gamma, t_D, t_P - t_D, alpha (the caller keeps last within theta).
+ *   idx_dev: J x k accepted global draw indices (e.g. abc_discrepancy_topk's output);
+ *     entries outside [first, last) (other models' draws, -1) are skipped.
+ *   t_host: T times (minutes; 1 <= T <= 256), copied at the call.
+ *   mean_dev / lo_dev / hi_dev: J x T fp32, row-major: the mean (compensated fp32 sum)
+ *     and the 0.025 / 0.975 type-7 quantiles of the responses of voxel j's accepted
+ *     lp-ntPET draws at time t[m]; NaN where the voxel accepted none.
+ * Evaluated in fp32 (responses within a few ulp of the exact value). ABC_ERR_ARG for
+ * arguments out of range (nothing launched). */
+int abc_response_cri(const float* theta_dev, int32_t ldtheta, const int32_t* idx_dev, int64_t J, int32_t k,
+                     int64_t first, int64_t last, const float* t_host, int32_t T, float* mean_dev,
+                     float* lo_dev, float* hi_dev, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Learned proposal and importance-weighted local ABC.  A build extra: the paper
  * has no counterpart; it replaces the global scan of Algorithm 1 for the

@@ -175,6 +175,20 @@ def launch_info():
     return g.value, r.value, n.value
 
 
+def response_cri(theta, first, last, t, idx, out=None, stream=None):
+    """Posterior mean and 95 % band of the lp-ntPET response function
+    1 + (gamma / k2a) g(t) at the times t (minutes), over each voxel's accepted
+    draws with global index in [first, last) -> (mean, lo, hi), each J x T fp32."""
+    J, k = idx.shape
+    tt = np.ascontiguousarray(np.asarray(t, dtype=np.float32).ravel())
+    T = len(tt)
+    if out is None:
+        out = tuple(torch.empty((J, T), dtype=torch.float32, device="cuda") for _ in range(3))
+    check(lib().abc_response_cri(_ptr(theta), theta.shape[1], _ptr(idx), J, k, int(first), int(last),
+                                 tt.ctypes.data_as(ctypes.c_void_p), T, *[_ptr(o) for o in out], _stream(stream)))
+    return out
+
+
 def set_default_tuning(bn=None, ctas_per_sm=2, pilot_stride=16, pilot_factor=1.5):
     """Process-wide default tuning; bn=None restores the built-in per-precision defaults."""
     if bn is None:

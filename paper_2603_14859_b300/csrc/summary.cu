@@ -356,6 +356,107 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
     }
 }
 
+// ---------------------------------------------------------------- response band
+// lp-ntPET response function k2a(t) / k2a = 1 + (gamma / k2a) g(t) (Sec. II-D), g
+// the gamma variate normalised to 1 at t_P: g = 0 before t_D, x^alpha e^{alpha (1 - x)}
+// with x = (t - t_D) / (t_P - t_D) after.
+constexpr int RESP_MAXT = 256;
+
+struct RespParams {
+    int64_t first, last;      // the lp-ntPET draws: global indices [first, last)
+    int ldt, k, T, p2;
+    float t[RESP_MAXT];
+};
+
+__device__ __forceinline__ float gamma_variate_at(float t, float tD, float tPmD, float alpha) {
+    if (t < tD) return 0.0f;
+    const float x = (t - tD) / tPmD;
+    if (alpha == 0.0f) return 1.0f;
+    if (x == 0.0f) return 0.0f;
+    return expf(alpha * (logf(x) + 1.0f - x));
+}
+
+// One warp per voxel: the accepted lp-ntPET draws' (gamma / k2a, t_D, t_P - t_D,
+// alpha) go to this warp's shared memory once; then per time the responses, their
+// compensated mean and the two type-7 quantiles (four order statistics, one histogram).
+__global__ void k_response_cri(const float* __restrict__ theta, const int32_t* __restrict__ idx, int64_t J,
+                               const __grid_constant__ RespParams Q, float* __restrict__ mean,
+                               float* __restrict__ lo, float* __restrict__ hi) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* cg = (float*)sm + (size_t)wid * 5 * Q.p2;
+    float* td = cg + Q.p2;
+    float* tw = td + Q.p2;
+    float* al = tw + Q.p2;
+    float* vals = al + Q.p2;
+    uint32_t* hist = (uint32_t*)((float*)sm + (size_t)warps * 5 * Q.p2) + (size_t)wid * 256;
+    const int64_t j = (int64_t)blockIdx.x * warps + wid;
+    if (j >= J) return;
+    int n = 0;
+    for (int base = 0; base < Q.k; base += 128) {
+        int32_t id[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = base + 32 * u + lane;
+            id[u] = r < Q.k ? idx[j * Q.k + r] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool take = base + 32 * u + lane < Q.k && (int64_t)id[u] >= Q.first && (int64_t)id[u] < Q.last;
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, take);
+            if (take) {
+                const int pos = n + __popc(b & ((1u << lane) - 1u));
+                const float* th = theta + (int64_t)id[u] * Q.ldt;
+                const float k2a = th[1] / (1.0f + th[2]);
+                cg[pos] = th[3] / k2a;
+                td[pos] = th[4];
+                tw[pos] = th[5];
+                al[pos] = th[6];
+            }
+            n += __popc(b);
+        }
+    }
+    __syncwarp();
+    const float qnan = __int_as_float(0x7FC00000);
+    int rk[4];
+    float fr[2];
+    const double qs[2] = {0.025, 0.975};
+    for (int q = 0; q < 2; ++q) {
+        const double h = (n - 1) * qs[q];
+        const int a = (int)floor(h);
+        fr[q] = (float)(h - a);
+        rk[2 * q] = a;
+        rk[2 * q + 1] = a + 1 < n ? a + 1 : n - 1;
+    }
+    for (int m = 0; m < Q.T; ++m) {
+        float o0 = qnan, o1 = qnan, o2 = qnan;
+        if (n > 0) {
+            const float t = Q.t[m];
+            CSum s;
+            float mn = 3.0e38f, mx = -3.0e38f;
+            for (int i = lane; i < n; i += 32) {
+                const float v = 1.0f + cg[i] * gamma_variate_at(t, td[i], tw[i], al[i]);
+                vals[i] = v;
+                s.add(v);
+                mn = fminf(mn, v);
+                mx = fmaxf(mx, v);
+            }
+            __syncwarp();
+            o0 = warp_csum(s) / (float)n;
+            float os[4];
+            warp_order4(vals, n, rk, hist, lane, mn, mx, os);
+            o1 = fmaf(fr[0], os[1] - os[0], os[0]);
+            o2 = fmaf(fr[1], os[3] - os[2], os[2]);
+            __syncwarp();
+        }
+        if (lane == 0) {
+            mean[j * Q.T + m] = o0;
+            lo[j * Q.T + m] = o1;
+            hi[j * Q.T + m] = o2;
+        }
+    }
+}
+
 int fill_segs(const int64_t* off, int M, Segs* s) {
     VPET_ARG(off, "model offsets: null pointer");
     VPET_ARG(M >= 1 && M <= MAXM, "model count must be in 1..%d", MAXM);
@@ -421,6 +522,44 @@ extern "C" int abc_summarize(const float* theta_dev, int32_t ldtheta, const int6
     const size_t smem = (size_t)warps * (p2 * 8 + 1024);
     k_summarize<<<(unsigned)vpet_ceil_div(J, warps), warps * 32, smem, (cudaStream_t)stream>>>(
         theta_dev, idx_dev, J, preferred_dev, Q, mean_dev, sd_dev, lo_dev, hi_dev);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}
+
+extern "C" int abc_response_cri(const float* theta_dev, int32_t ldtheta, const int32_t* idx_dev, int64_t J,
+                                int32_t k, int64_t first, int64_t last, const float* t_host, int32_t T,
+                                float* mean_dev, float* lo_dev, float* hi_dev, void* stream) {
+    vpet::clear_error();
+    VPET_ARG(ldtheta >= 7, "abc_response_cri: ldtheta must hold the 7 lp-ntPET parameters");
+    VPET_ARG(k >= 1 && k <= 2048, "abc_response_cri: k must be in 1..2048");
+    VPET_ARG(J >= 0, "abc_response_cri: negative J");
+    VPET_ARG(first >= 0 && first <= last, "abc_response_cri: need 0 <= first <= last");
+    VPET_ARG(T >= 1 && T <= RESP_MAXT, "abc_response_cri: T must be in 1..%d", RESP_MAXT);
+    VPET_ARG(t_host, "abc_response_cri: null time grid");
+    RespParams Q;
+    memset(&Q, 0, sizeof Q);
+    Q.first = first;
+    Q.last = last;
+    Q.ldt = ldtheta;
+    Q.k = k;
+    Q.T = T;
+    for (int m = 0; m < T; ++m) {
+        VPET_ARG(t_host[m] == t_host[m], "abc_response_cri: time %d is NaN", m);
+        Q.t[m] = t_host[m];
+    }
+    int p2 = 32;
+    while (p2 < k) p2 <<= 1;
+    Q.p2 = p2;
+    if (J == 0) return ABC_OK;
+    VPET_ARG(theta_dev && idx_dev && mean_dev && lo_dev && hi_dev, "abc_response_cri: null pointer");
+    const size_t per_warp = (size_t)p2 * 5 * 4 + 1024;
+    int warps = 8;
+    while (warps > 1 && (size_t)warps * per_warp > 96 * 1024) warps >>= 1;
+    const size_t smem = (size_t)warps * per_warp;
+    if (smem > 48 * 1024)
+        VPET_CUDA(cudaFuncSetAttribute(k_response_cri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_response_cri<<<(unsigned)vpet_ceil_div(J, warps), warps * 32, smem, (cudaStream_t)stream>>>(
+        theta_dev, idx_dev, J, Q, mean_dev, lo_dev, hi_dev);
     VPET_LAUNCH_CHECK();
     return ABC_OK;
 }

@@ -168,3 +168,29 @@ def test_batch_layout_of_mixed_widths_without_gpu(lib, prec):
     rc = lib.abc_batch_discrepancy_topk(scans, len(shapes), prec, None, P(256), need - 256, None)
     assert rc == _lib.ABC_ERR_WORKSPACE
     assert b"workspace needs" in lib.abc_last_error()
+
+
+def test_response_band_validation_without_gpu(lib):
+    """abc_response_cri checks its arguments on the host before any launch."""
+    from paper_2603_14859_b300 import _lib
+    P = ctypes.c_void_p
+    t = np.linspace(0, 60, 5).astype(np.float32)
+    tp = t.ctypes.data_as(P)
+    ok = dict(theta=P(16), ld=7, idx=P(16), J=10, k=50, first=0, last=100, t=tp, T=5)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return lib.abc_response_cri(a["theta"], a["ld"], a["idx"], a["J"], a["k"], a["first"], a["last"], a["t"],
+                                    a["T"], P(16), P(16), P(16), None)
+    assert call(ld=6) == _lib.ABC_ERR_ARG                 # fewer than the 7 lp-ntPET columns
+    assert call(k=0) == _lib.ABC_ERR_ARG
+    assert call(k=2049) == _lib.ABC_ERR_ARG
+    assert call(J=-1) == _lib.ABC_ERR_ARG
+    assert call(first=5, last=4) == _lib.ABC_ERR_ARG
+    assert call(T=0) == _lib.ABC_ERR_ARG
+    assert call(T=257) == _lib.ABC_ERR_ARG
+    assert call(t=None) == _lib.ABC_ERR_ARG
+    assert call(theta=None) == _lib.ABC_ERR_ARG
+    nan = np.array([1.0, np.nan], np.float32)
+    assert call(t=nan.ctypes.data_as(P), T=2) == _lib.ABC_ERR_ARG
+    assert call(J=0) == _lib.ABC_OK                        # nothing to do, nothing launched

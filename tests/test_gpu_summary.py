@@ -69,3 +69,40 @@ def test_summaries_wide_rows(orc, k, P):
             assert np.array_equal(np.isnan(a), np.isnan(b))
             m = ~np.isnan(b)
             assert np.all(np.abs(a[m] - b[m]) <= 1e-5 * np.abs(b[m]) + 1e-7)
+
+
+@pytest.mark.parametrize("k", [1, 7, 200, 500, 2048])
+def test_response_band(orc, k):
+    """Posterior band of the lp-ntPET response function 1 + (gamma / k2a) g(t)
+    against the oracle: draws of another model and padding (-1) are skipped, a voxel
+    with no accepted lp-ntPET draw gives NaN, gamma = 0 gives exactly 1."""
+    from paper_2603_14859_b300 import api
+    from paper_2603_14859_b300 import synth as S
+    rng = np.random.default_rng(100 + k)
+    lo_p, hi_p = S.PRIORS[S.LPNTPET]
+    n_other, n_lp = 3000, 5000
+    th = np.zeros((n_other + n_lp, 8), np.float32)
+    th[:n_other, :3] = rng.uniform(0.1, 1.0, (n_other, 3))
+    th[n_other:, :7] = rng.uniform(lo_p, hi_p, (n_lp, 7))
+    th[n_other:n_other + 500, 3] = 0.0                           # no activation
+    first, last = n_other, n_other + n_lp
+    J = 97
+    idx = rng.integers(0, n_other + n_lp, (J, k)).astype(np.int32)
+    idx[0] = rng.integers(0, n_other, k)                         # nothing from lp-ntPET
+    idx[1] = n_other + rng.integers(0, 500, k)                   # only gamma = 0 draws
+    if k > 3:
+        idx[2, ::3] = -1
+    ts = np.concatenate([[0.0, 19.5], np.linspace(20.0, 60.0, 17), [float(th[n_other + 7, 4]),
+                                                                     float(th[n_other + 7, 4] + th[n_other + 7, 5])]])
+    ts = ts.astype(np.float32)
+    g = api.response_cri(torch.from_numpy(th).cuda(), first, last, ts, torch.from_numpy(idx).cuda())
+    o = orc.response_cri(th, first, last, ts.astype(np.float64), idx)
+    for a, b in zip(g, o):
+        a = a.cpu().numpy().astype(np.float64)
+        assert a.shape == (J, len(ts))
+        assert np.array_equal(np.isnan(a), np.isnan(b))
+        m = ~np.isnan(b)
+        assert np.all(np.abs(a[m] - b[m]) <= 1e-5 * np.maximum(1.0, np.abs(b[m])) + 1e-6)
+    assert np.all(np.isnan(g[0][0].cpu().numpy()))
+    for a in g:
+        assert np.all(a[1].cpu().numpy() == 1.0)
