@@ -632,6 +632,7 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / Ke
     e2e_ms = sharding.max_over_ranks([e2e_ms], dist, device="cuda")[0]
+    resp = response_band_timing(W, run, stream, clk) if rank == 0 else None
 
     if rank != 0:
         dist.destroy_process_group()
@@ -676,11 +677,55 @@ def main():
         "topk_status": {"error": st[0], "exact_scan_voxels": st[1], "tie_overflow_voxels": st[2], "uncertified_voxels": st[3],
                         "diagnostics": list(st[4:8])},
     }
+    if resp is not None:
+        line["response_band"] = resp
     if n_gpu == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+# thread instructions per response evaluation of k_response_cri (evaluation, compensated
+# mean and the histogram order statistics over the accepted lp-ntPET draws), measured by
+# ncu (smsp__thread_inst_executed.sum) on the brain lp-ntPET workload
+RESP_INST_PER_RESPONSE = None
+
+
+def response_band_timing(W, run, stream, clk, reps=3):
+    """Posterior band of the lp-ntPET response function at the frame mid-times for
+    every voxel of the last step (an extra output, outside the timed step)."""
+    import torch
+    from paper_2603_14859_b300 import api
+    from paper_2603_14859_b300 import synth as S
+    if S.LPNTPET not in W.models:
+        return None
+    mi = list(W.models).index(S.LPNTPET)
+    first, last = int(run.offsets[mi]), int(run.offsets[mi + 1])
+    tmid = ((np.asarray(W.ts) + np.asarray(W.te)) / 2.0).astype(np.float32)
+    out = api.response_cri(run.theta, first, last, tmid, run.idx, stream=stream)
+    api.response_cri(run.theta, first, last, tmid, run.idx, out=out, stream=stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        api.response_cri(run.theta, first, last, tmid, run.idx, out=out, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    r_ms = a.elapsed_time(b) / reps
+    n_acc = int(((run.idx >= first) & (run.idx < last)).sum().item())
+    n_resp = n_acc * len(tmid)
+    rec = {"kernel": "k_response_cri", "kernel_ms": r_ms, "voxels": W.J, "times": len(tmid),
+           "accepted_lpntpet_draws": n_acc, "responses_per_s": n_resp / (r_ms / 1000.0),
+           "voxels_per_s": W.J / (r_ms / 1000.0)}
+    if RESP_INST_PER_RESPONSE is not None:
+        sm_mhz = clk["sm_mhz"] if clk else 2032.0
+        peak = 148 * 4 * 32 * sm_mhz * 1e6 / 1e12
+        achieved = RESP_INST_PER_RESPONSE * n_resp / (r_ms / 1000.0) / 1e12
+        rec["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T thread-instructions/s",
+                           "frac": achieved / peak, "instructions_per_response": RESP_INST_PER_RESPONSE,
+                           "peak_source": "SIMT issue: 148 SMs x 4 schedulers x 32 lanes x median SM clock"}
+    return rec
 
 
 if __name__ == "__main__":

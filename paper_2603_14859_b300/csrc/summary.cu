@@ -148,6 +148,21 @@ __device__ float warp_kth_radix(const float* s, int n, int r, uint32_t* hist, in
 // mn / mx: this lane's minimum and maximum over its values s[lane + 32 i].
 __device__ void warp_order4(const float* s, int n, const int (&rk)[4], uint32_t* hist, int lane, float mn, float mx,
                             float (&out)[4]) {
+    if (n <= 32) {
+        // one value per lane: a bitonic sort across the warp's registers
+        float x = lane < n ? s[lane] : __int_as_float(0x7F800000);
+#pragma unroll
+        for (int size = 2; size <= 32; size <<= 1)
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                const float y = __shfl_xor_sync(0xFFFFFFFFu, x, stride);
+                const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0 || size == 32);
+                x = keep_min ? fminf(x, y) : fmaxf(x, y);
+            }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[q] = __shfl_sync(0xFFFFFFFFu, x, rk[q]);
+        return;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mn = fminf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
@@ -182,20 +197,21 @@ __device__ void warp_order4(const float* s, int n, const int (&rk)[4], uint32_t*
         if (lane >= o) incl += v;
     }
     const uint32_t excl = incl - sum;
-    int tb[4], tbelow[4];
+    int tb[4], tbelow[4], tcnt[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         uint32_t c = excl;
-        int found = -1, below = 0;
+        int found = -1, below = 0, inbin = 0;
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-            if (found < 0 && c + loc[b] > (uint32_t)rk[q]) { found = lane * 8 + b; below = (int)c; }
+            if (found < 0 && c + loc[b] > (uint32_t)rk[q]) { found = lane * 8 + b; below = (int)c; inbin = (int)loc[b]; }
             c += loc[b];
         }
         const uint32_t who = __ballot_sync(0xFFFFFFFFu, found >= 0);
         const int src = __ffs(who) - 1;
         tb[q] = __shfl_sync(0xFFFFFFFFu, found, src);
         tbelow[q] = __shfl_sync(0xFFFFFFFFu, below, src);
+        tcnt[q] = __shfl_sync(0xFFFFFFFFu, inbin, src);
     }
     __syncwarp();   // the histogram is in registers now; its words become the gather buffer
     float* buf = (float*)hist;
@@ -217,6 +233,41 @@ __device__ void warp_order4(const float* s, int n, const int (&rk)[4], uint32_t*
     __syncwarp();
     if (m > 256) {
         for (int q = 0; q < 4; ++q) out[q] = warp_kth_radix(s, n, rk[q], hist, lane);
+        return;
+    }
+    if (m > 64) {
+        // many members (typically many equal values): sort them; the members of the
+        // target bins then follow one another in bin order, so rank r of bin b sits at
+        // (members of the lower target bins) + (r - keys below bin b)
+        int m2 = 64;
+        while (m2 < m) m2 <<= 1;
+        for (int i = m + lane; i < m2; i += 32) buf[i] = __int_as_float(0x7F800000);
+        for (int size = 2; size <= m2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                __syncwarp();
+                for (int t = lane; t < (m2 >> 1); t += 32) {
+                    const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+                    const float a = buf[lo], b = buf[hi];
+                    if ((a > b) == ((lo & size) == 0)) {
+                        buf[lo] = b;
+                        buf[hi] = a;
+                    }
+                }
+            }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int off = 0;
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) {
+                bool first = tb[q2] < tb[q];
+#pragma unroll
+                for (int q3 = 0; q3 < q2; ++q3) first = first && tb[q3] != tb[q2];
+                if (first) off += tcnt[q2];
+            }
+            out[q] = buf[off + rk[q] - tbelow[q]];
+        }
+        __syncwarp();
         return;
     }
     float res[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -431,20 +482,42 @@ __global__ void k_response_cri(const float* __restrict__ theta, const int32_t* _
     for (int m = 0; m < Q.T; ++m) {
         float o0 = qnan, o1 = qnan, o2 = qnan;
         if (n > 0) {
+            // responses equal to 1 (before t_D, gamma = 0) are only counted; the others are
+            // compacted into vals, and a rank falls on 1, below the ones or above them
             const float t = Q.t[m];
             CSum s;
             float mn = 3.0e38f, mx = -3.0e38f;
-            for (int i = lane; i < n; i += 32) {
-                const float v = 1.0f + cg[i] * gamma_variate_at(t, td[i], tw[i], al[i]);
-                vals[i] = v;
-                s.add(v);
-                mn = fminf(mn, v);
-                mx = fmaxf(mx, v);
+            int nb = 0, nv = 0;
+            for (int i0 = 0; i0 < n; i0 += 32) {
+                const int i = i0 + lane;
+                float v = 1.0f;
+                if (i < n) v = 1.0f + cg[i] * gamma_variate_at(t, td[i], tw[i], al[i]);
+                if (i < n) s.add(v);
+                const bool keep = i < n && v != 1.0f;
+                const uint32_t bk = __ballot_sync(0xFFFFFFFFu, keep);
+                if (keep) {
+                    vals[nv + __popc(bk & ((1u << lane) - 1u))] = v;
+                    mn = fminf(mn, v);
+                    mx = fmaxf(mx, v);
+                }
+                nv += __popc(bk);
+                nb += __popc(__ballot_sync(0xFFFFFFFFu, i < n && v < 1.0f));
             }
             __syncwarp();
             o0 = warp_csum(s) / (float)n;
+            const int n1 = n - nv;
             float os[4];
-            warp_order4(vals, n, rk, hist, lane, mn, mx, os);
+            int rv[4];
+            bool one[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                one[q] = rk[q] >= nb && rk[q] < nb + n1;
+                rv[q] = one[q] ? 0 : (rk[q] < nb ? rk[q] : rk[q] - n1);
+            }
+            if (nv > 0 && !(one[0] && one[1] && one[2] && one[3])) warp_order4(vals, nv, rv, hist, lane, mn, mx, os);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (one[q]) os[q] = 1.0f;
             o1 = fmaf(fr[0], os[1] - os[0], os[0]);
             o2 = fmaf(fr[1], os[3] - os[2], os[2]);
             __syncwarp();
