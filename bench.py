@@ -689,7 +689,7 @@ def main():
 # thread instructions per response evaluation of k_response_cri (evaluation, compensated
 # mean and the histogram order statistics over the accepted lp-ntPET draws), measured by
 # ncu (smsp__thread_inst_executed.sum) on the brain lp-ntPET workload
-RESP_INST_PER_RESPONSE = None
+RESP_INST_PER_RESPONSE = 205.8
 
 
 def response_band_timing(W, run, stream, clk, reps=3):

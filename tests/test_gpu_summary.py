@@ -46,8 +46,8 @@ def test_select_and_summaries(orc, k):
 
 @pytest.mark.parametrize("k,P", [(2048, 30), (777, 12)])
 def test_summaries_wide_rows(orc, k, P):
-    """Many parameters at the largest k (the rows' columns are gathered in groups when
-    one voxel's columns do not fit in shared memory together)."""
+    """Many parameters at the largest k (every column's values fill the shared-memory
+    buffer the order statistics use)."""
     from paper_2603_14859_b300 import api
     rng = np.random.default_rng(k + P)
     N = 6000
