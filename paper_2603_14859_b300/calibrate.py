@@ -6,7 +6,9 @@ a target parameter's posterior mean against the truth; the MSE-versus-n curve is
 U-shaped for a small enough threshold, so a smooth curve (a quadratic in log n)
 is fitted and its minimum picks n.  For model selection: over the same kind of
 grid, the accuracy of the preferred model and the ROC AUC of the posterior model
-probability; the working point is the elbow of the AUC curve.
+probability; the working point is the elbow of the AUC curve.  For activation
+detection on the lp-ntPET simulation study's shapes (Sec. IV-A): sensitivity and
+specificity of the MRTM / lp-ntPET selection under Gaussian and Poisson noise.
 
 Every ABC step runs in the CUDA library (`pipeline.AbcPipeline`); this module
 only loops over the grid and reduces the outputs (the fit, the AUC and the elbow
@@ -95,10 +97,10 @@ class SweepPoint:
     auc: float | None = None         # ROC AUC of P(second model) for the truth "second model"
 
 
-def _run(name, n, k, p, J, seed, precision):
+def _run(name, n, k, p, J, seed, precision, **wkw):
     import torch
     from . import _lib, pipeline
-    W = S.workload(name, seed=seed, J=J, N_per_model=n)
+    W = S.workload(name, seed=seed, J=J, N_per_model=n, **wkw)
     W.k = min(W.N, int(k) if k is not None else max(1, int(round(p * W.N))))
     prec = {"fp32": _lib.ABC_FP32, "bf16r": _lib.ABC_BF16_RESCORE, "split": _lib.ABC_SPLIT_DRAWS}[precision]
     run = pipeline.AbcPipeline(W, prec)
@@ -145,9 +147,39 @@ def selection_sweep(n_grid, k=None, p=None, name="raclopride_lpntpet", J=8192, s
     return pts
 
 
+@dataclasses.dataclass
+class DetectionPoint:
+    noise: str
+    level: str
+    n_per_model: int
+    k: int
+    sensitivity: float      # activated voxels whose preferred model is lp-ntPET
+    specificity: float      # voxels without activation whose preferred model is MRTM
+    auc: float              # ROC AUC of the posterior probability of lp-ntPET
+    seconds: float
+
+
+def detection_sweep(n_grid, k=None, p=None, noises=("gaussian", "poisson"), levels=("low", "high"), J=4000,
+                    seed=None, precision="bf16r"):
+    """Activation detection on the lp-ntPET simulation study's shapes (Sec. IV-A: 61
+    one-minute frames, half the TACs activated, Gaussian and Poisson noise at two
+    levels): sensitivity, specificity and AUC of the MRTM / lp-ntPET selection per n."""
+    pts = []
+    for noise in noises:
+        for level in levels:
+            for n in n_grid:
+                W, out, sec = _run("raclopride_e2", int(n), k, p, J, seed, precision, noise=noise, level=level)
+                prob = out.prob.cpu().numpy().astype(np.float64)
+                pref = out.pref.cpu().numpy()
+                act = W.truth_model == S.LPNTPET
+                pts.append(DetectionPoint(noise, level, int(n), W.k, float((pref[act] == 1).mean()),
+                                          float((pref[~act] == 0).mean()), roc_auc(prob[:, 1], act), sec))
+    return pts
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--mode", choices=["mse", "selection"], default="mse")
+    ap.add_argument("--mode", choices=["mse", "selection", "detection"], default="mse")
     ap.add_argument("--workload", default=None)
     ap.add_argument("--n", default="10000,20000,50000,100000,200000", help="draws per model, comma-separated")
     ap.add_argument("--k", type=int, default=None, help="accepted draws (fixed)")
@@ -167,6 +199,9 @@ def main(argv=None):
         res = {"mode": "mse", "workload": name, "model": model, "column": a.column, "n": grid,
                "k": [pt.k for pt in pts], "mse": curve, "fit": coef, "n_best": best,
                "seconds": [pt.seconds for pt in pts]}
+    elif a.mode == "detection":
+        pts = detection_sweep(grid, a.k, a.p, J=a.voxels or 4000)
+        res = {"mode": "detection", "workload": "raclopride_e2", "points": [dataclasses.asdict(pt) for pt in pts]}
     else:
         name = a.workload or "raclopride_lpntpet"
         pts = selection_sweep(grid, a.k, a.p, name, a.voxels or 8192)

@@ -98,7 +98,10 @@ def make_y_gpu(W: S.Workload, stream=None) -> torch.Tensor:
         xc = api.simulate(model, W.ts, W.te, W.input_for(model), torch.from_numpy(np.ascontiguousarray(th)).cuda(),
                           stream=stream)
         x_clean[rows] = xc[:, :L].cpu().numpy()
-    y = S.add_noise(x_clean, W.ts, W.te, W.half_life, W.q, W.z)
+    if W.noise == "poisson":
+        y = S.add_noise_poisson(x_clean, S.poisson_scale(x_clean, W.noise_q), W.noise_seed)
+    else:
+        y = S.add_noise(x_clean, W.ts, W.te, W.half_life, W.q, W.z)
     out = torch.zeros((W.J, ldy), dtype=torch.float32)
     out[:, :L] = torch.from_numpy(y)
     return out.cuda()

@@ -216,6 +216,22 @@ def add_noise(x_clean: np.ndarray, ts, te, half_life: float, q: np.ndarray, z: n
     return (x + lv[:, None] * sig * z).astype(np.float32)
 
 
+def poisson_scale(x_clean: np.ndarray, q: float) -> float:
+    """Counting-noise constant l2 at which the median voxel's Poisson noise has
+    relative size q: E||y - x||^2 = sum_l x_l / l2 = q^2 ||x||^2 (the paper estimates
+    its l2 from scanner data, which this build does not have)."""
+    x = np.maximum(np.asarray(x_clean, np.float64), 0.0)
+    r = x.sum(1) / np.maximum((x * x).sum(1), 1e-300)
+    return float(np.median(r) / (q * q))
+
+
+def add_noise_poisson(x_clean: np.ndarray, l2: float, seed: int) -> np.ndarray:
+    """Poisson counting noise of the lp-ntPET simulation study (Sec. IV-A):
+    y_l = Pois(l2 x_l) / l2, mean x_l and variance x_l / l2.  Returns float32."""
+    x = np.maximum(np.asarray(x_clean, np.float64), 0.0)
+    return (_rng(seed, 71).poisson(l2 * x) / l2).astype(np.float32)
+
+
 def mask_indices(shape, J: int) -> np.ndarray:
     """Linear indices of the J voxels closest to the centre of an ellipsoid
     inscribed in `shape` (a compact voxel list for a masked volume)."""
@@ -245,6 +261,9 @@ class Workload:
     prior_seed: int
     precision: str = "fp32"
     model_inp: dict | None = None  # per-model input when the models need different ones
+    noise: str = "gaussian"        # "gaussian": add_noise with levels q; "poisson": add_noise_poisson
+    noise_q: float = 0.0           # poisson: relative noise size of the median voxel (sets l2)
+    noise_seed: int = 0
 
     def input_for(self, model):
         if self.model_inp and model in self.model_inp:
@@ -278,8 +297,10 @@ class Workload:
         return np.asarray(lo, float), np.asarray(hi, float)
 
 
-def workload(name: str, seed: int | None = None, J: int | None = None, N_per_model: int | None = None) -> Workload:
-    """Named synthetic workload.  `J` and `N_per_model` shrink it for tests."""
+def workload(name: str, seed: int | None = None, J: int | None = None, N_per_model: int | None = None,
+             noise: str = "gaussian", level: str = "high") -> Workload:
+    """Named synthetic workload.  `J` and `N_per_model` shrink it for tests; `noise`
+    and `level` select the noise model of the lp-ntPET detection study."""
     if name == "brain_fdg_2tcm":            # plain ABC, 2TCM-irr, 22 frames
         seed = 1001 if seed is None else seed
         J = 2048 if J is None else J
@@ -309,6 +330,28 @@ def workload(name: str, seed: int | None = None, J: int | None = None, N_per_mod
         return Workload(name, ts, te, [MRTM, LPNTPET], [n, n], 500, cr, HALF_LIFE_C11, tm,
                         [th_m, th_a], [rows_m, rows_a], noise_levels(seed, J, 0.05, 0.20),
                         standard_normals(seed, J, len(ts)), seed + 7, "bf16r")
+    if name == "raclopride_e2":             # lp-ntPET detection study: 61 one-minute frames, half activated
+        seed = 1006 if seed is None else seed
+        J = 4000 if J is None else J
+        n = 1_000_000 if N_per_model is None else N_per_model
+        ts, te = frames_from_blocks([(61, 60)])
+        beta, kap = draw_feng(seed, avoid=[REF_K2])
+        cr = reference_tissue_polyexp(feng_polyexp(beta, kap))
+        act = np.zeros(J, bool)
+        act[_rng(seed, 61).permutation(J)[: J // 2]] = True
+        tm = np.where(act, LPNTPET, MRTM).astype(np.int32)
+        rows_a, rows_m = np.nonzero(act)[0], np.nonzero(~act)[0]
+        lo, hi = PRIORS[LPNTPET]
+        lo = list(lo); lo[3] = 0.05
+        th_a = uniform_truth(seed, LPNTPET, len(rows_a), lo, hi)
+        th_m = uniform_truth(seed, MRTM, len(rows_m))
+        q = {"low": 0.03, "high": 0.10}[level]
+        if noise not in ("gaussian", "poisson"):
+            raise KeyError(noise)
+        return Workload(name, ts, te, [MRTM, LPNTPET], [n, n], 500, cr, HALF_LIFE_C11, tm,
+                        [th_m, th_a], [rows_m, rows_a], noise_levels(seed, J, q, q),
+                        standard_normals(seed, J, len(ts)), seed + 7, "bf16r", noise=noise, noise_q=q,
+                        noise_seed=seed + 11)
     if name == "totalbody_fdg":             # 2TCM irr vs rev, 29 frames, lognormal clusters
         seed = 1003 if seed is None else seed
         J = 4_000_000 if J is None else J

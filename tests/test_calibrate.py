@@ -62,3 +62,43 @@ def test_small_sweeps_run_on_the_gpu_path():
     sel = C.selection_sweep([20000, 80000], k=100, J=1024)
     for pt in sel:
         assert 0.0 <= pt.accuracy <= 1.0 and 0.0 <= pt.auc <= 1.0
+
+
+def test_poisson_noise_statistics():
+    """y = Pois(l2 x) / l2 has mean x and variance x / l2 (checked on 200,000 draws
+    per frame, within 5 standard errors), and never a negative value."""
+    from paper_2603_14859_b300 import synth as S
+    x = np.tile(np.array([[0.5, 2.0, 7.5]]), (200_000, 1))
+    l2 = 3.0
+    y = S.add_noise_poisson(x, l2, seed=9).astype(np.float64)
+    m, v = y.mean(0), y.var(0)
+    se_m = np.sqrt(x[0] / l2 / len(y))
+    assert np.all(np.abs(m - x[0]) < 5 * se_m)
+    assert np.all(np.abs(v / (x[0] / l2) - 1.0) < 0.02)
+    assert y.min() >= 0.0
+    # the scale puts the median voxel's expected relative noise at q
+    xc = np.array([[1.0, 2.0, 3.0], [2.0, 2.0, 2.0], [4.0, 0.0, 4.0]])
+    q = 0.1
+    l2 = S.poisson_scale(xc, q)
+    r = np.sqrt(xc.sum(1) / l2) / np.linalg.norm(xc, axis=1)
+    assert np.median(r) == pytest.approx(q, rel=1e-12)
+
+
+def test_detection_workload_shape():
+    """61 one-minute frames, exactly half of the TACs activated (gamma >= 0.05)."""
+    from paper_2603_14859_b300 import synth as S
+    W = S.workload("raclopride_e2", J=400, N_per_model=1000, noise="poisson", level="low")
+    assert W.L == 61 and np.allclose(W.te - W.ts, 1.0)
+    act = W.truth_model == S.LPNTPET
+    assert act.sum() == 200
+    (th_m, th_a) = W.truth
+    assert th_a.shape == (200, 7) and np.all(th_a[:, 3] >= 0.05)
+    assert W.noise == "poisson" and W.noise_q == 0.03
+
+
+@pytest.mark.gpu
+def test_small_detection_sweep_on_the_gpu_path():
+    pts = C.detection_sweep([20000], k=100, J=400)
+    assert len(pts) == 4
+    for pt in pts:
+        assert 0.0 <= pt.sensitivity <= 1.0 and 0.0 <= pt.specificity <= 1.0 and 0.0 <= pt.auc <= 1.0
