@@ -53,6 +53,7 @@ def lib():
         L.orc_model_select.argtypes = [P, i64, ctypes.c_int, P, ctypes.c_int, P, P]
         L.orc_summarize.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, P, P, P, i64, ctypes.c_int, P,
                                     ctypes.c_int, P, P, P, P]
+        L.orc_topk_l1.argtypes = L.orc_topk.argtypes
         L.orc_response_cri.argtypes = [P, ctypes.c_int, P, i64, ctypes.c_int, i64, i64, P, ctypes.c_int, P, P, P]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_Phi.argtypes = [f64]
@@ -150,6 +151,21 @@ def topk(y, x, w, k, nthreads=0):
     rc = lib().orc_topk(_p(y), J, L, _p(x), N, x.shape[1], L, _p(w), k, _p(idx), _p(dist), nthreads)
     if rc != 0:
         raise ValueError("orc_topk failed")
+    return idx, dist
+
+
+def topk_l1(y, x, w, k, nthreads=0):
+    """Per voxel the k nearest draws by the frame-weighted L1 distance, (distance, index) order."""
+    y = _c(y, np.float32)
+    x = _c(x, np.float64)
+    w = _c(w, np.float64)
+    J, L = y.shape
+    N = x.shape[0]
+    idx = np.zeros((J, k), np.int32)
+    dist = np.zeros((J, k), np.float64)
+    rc = lib().orc_topk_l1(_p(y), J, L, _p(x), N, x.shape[1], L, _p(w), k, _p(idx), _p(dist), nthreads)
+    if rc != 0:
+        raise ValueError("orc_topk_l1 failed")
     return idx, dist
 
 

@@ -16,7 +16,8 @@
  *   - MRTM: Eq. 3 with gamma = 0 in its closed (convolution) form;
  *   - lp-ntPET: the differential form of Eq. 3-4, integrated with an adaptive
  *     Dormand-Prince 5(4) scheme, the frame integral carried as an extra state;
- *   - distance: frame-weighted squared Euclidean distance computed directly;
+ *   - distance: frame-weighted squared Euclidean distance computed directly
+ *     (and the frame-weighted L1 distance Sec. V recommends);
  *   - top-k: full sort of (distance, draw index) per voxel, first k kept
  *     (Algorithm 1, step 5; fixed-budget rejection, Sec. II-C);
  *   - model probabilities and preferred model (Sec. III-B, "more than 50 %");
@@ -450,6 +451,39 @@ int orc_topk(const float* y, int64_t J, int ldy, const double* x, int64_t N, int
 #endif
         for (int64_t j = 0; j < J; ++j) {
             for (int64_t n = 0; n < N; ++n) { buf[n].d = wdist(y + j * ldy, x + n * ldx, w, L); buf[n].i = n; }
+            qsort(buf, (size_t)N, sizeof(di_pair), di_cmp);
+            for (int r = 0; r < k; ++r) { idx[j * k + r] = (int32_t)buf[r].i; dist[j * k + r] = buf[r].d; }
+        }
+        free(buf);
+    }
+    return 0;
+}
+
+/* Frame-weighted L1 distance sum_l w_l |y_l - x_l| (the distance Sec. V recommends),
+ * summed directly in fp64. */
+static double wdist_l1(const float* y, const double* x, const double* w, int L) {
+    double s = 0.0;
+    for (int l = 0; l < L; ++l) s += w[l] * fabs((double)y[l] - x[l]);
+    return s;
+}
+
+/* Top-k by the L1 distance: full sort of (distance, draw index) per voxel, first k.
+ * Pinned by: brute force on tiny inputs, the L1 triangle inequality and the
+ * single-frame case (a sort of |y - x|) in tests/test_oracle_topk.py. */
+int orc_topk_l1(const float* y, int64_t J, int ldy, const double* x, int64_t N, int ldx, int L, const double* w,
+                int k, int32_t* idx, double* dist, int nthreads) {
+    if (k < 1 || k > N) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        di_pair* buf = (di_pair*)malloc(sizeof(di_pair) * (size_t)N);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t j = 0; j < J; ++j) {
+            for (int64_t n = 0; n < N; ++n) { buf[n].d = wdist_l1(y + j * ldy, x + n * ldx, w, L); buf[n].i = n; }
             qsort(buf, (size_t)N, sizeof(di_pair), di_cmp);
             for (int r = 0; r < k; ++r) { idx[j * k + r] = (int32_t)buf[r].i; dist[j * k + r] = buf[r].d; }
         }

@@ -124,3 +124,54 @@ def test_summary_model_without_ki(orc):
     idx = np.arange(10, dtype=np.int32)[None, :]
     mean, sd, lo, hi = orc.summarize(theta, [0, 20], [3], [0], [0, 1, 2], idx)
     assert np.isnan(mean[0, 3]) and np.isfinite(mean[0, :3]).all()
+
+
+def test_l1_topk_brute_force_and_single_frame(orc):
+    """L1 top-k (Sec. V): brute force on tiny inputs (sum_l w_l |y_l - x_l| written out
+    per pair, then sorted by (distance, index)), and with one frame the order of
+    |y - x| itself."""
+    rng = np.random.default_rng(31)
+    J, N, L, k = 5, 60, 7, 9
+    y = rng.normal(size=(J, L)).astype(np.float32)
+    x = rng.normal(size=(N, L))
+    x[17] = x[3]                                   # an exact tie, broken by the index
+    w = rng.uniform(0.1, 1.0, L)
+    idx, dist = orc.topk_l1(y, x, w, k)
+    for j in range(J):
+        d = [sum(w[l] * abs(float(y[j, l]) - x[n, l]) for l in range(L)) for n in range(N)]
+        order = sorted(range(N), key=lambda n: (d[n], n))[:k]
+        assert list(idx[j]) == order
+        assert np.allclose(dist[j], [d[n] for n in order], rtol=1e-14, atol=0)
+    y1 = rng.normal(size=(3, 1)).astype(np.float32)
+    x1 = rng.normal(size=(40, 1))
+    idx1, d1 = orc.topk_l1(y1, x1, np.array([2.0]), 5)
+    for j in range(3):
+        assert list(idx1[j]) == list(np.argsort(np.abs(float(y1[j, 0]) - x1[:, 0]), kind="stable")[:5])
+        assert np.allclose(d1[j], 2.0 * np.sort(np.abs(float(y1[j, 0]) - x1[:, 0]))[:5], rtol=1e-14)
+
+
+def test_l1_distance_is_a_metric_and_differs_from_l2(orc):
+    """The L1 distances satisfy the triangle inequality through a third point, and the
+    L1 and squared-L2 orders differ on a case built for it (one large frame difference
+    against many small ones)."""
+    rng = np.random.default_rng(32)
+    L = 6
+    w = np.ones(L)
+    y = rng.normal(size=(1, L)).astype(np.float32)
+    x = rng.normal(size=(200, L))
+    _, d_all = orc.topk_l1(y, x, w, 200)
+    i_sorted, _ = orc.topk_l1(y, x, w, 200)
+    dy = np.empty(200)
+    dy[i_sorted[0]] = d_all[0]
+    # d(y, x_n) <= d(y, x_0) + d(x_0, x_n) for every n (x_0 exactly representable)
+    x[0] = x[0].astype(np.float32)
+    _, d_0 = orc.topk_l1(x[:1].astype(np.float32), x, w, 200)
+    i0, _ = orc.topk_l1(x[:1].astype(np.float32), x, w, 200)
+    d0 = np.empty(200)
+    d0[i0[0]] = d_0[0]
+    assert np.all(dy <= dy[0] + d0 + 1e-12)
+    yy = np.zeros((1, 4), np.float32)
+    xx = np.array([[2.0, 0, 0, 0], [0.9, 0.9, 0.9, 0.9]])      # L1: 2.0 vs 3.6; squared L2: 4.0 vs 3.24
+    i_l1, _ = orc.topk_l1(yy, xx, np.ones(4), 1)
+    i_l2, _ = orc.topk(yy, xx, np.ones(4), 1)
+    assert i_l1[0, 0] == 0 and i_l2[0, 0] == 1
