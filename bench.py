@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--proposals", type=int, default=10_000, help="learned workload: proposals per voxel")
     ap.add_argument("--train-pairs", type=int, default=10_000_000, help="learned workload: training pairs")
     ap.add_argument("--sigma-scale", type=float, default=1.0, help="learned workload: proposal widening")
+    ap.add_argument("--distance", default="l2", choices=["l2", "l1"],
+                    help="single-scan workloads: frame-weighted squared L2 (tensor cores) or L1 (Sec. V; SIMT scan)")
     ap.add_argument("--tuning", default=None,
                     help="single-scan workloads: launch tuning bn,ctas_per_sm,pilot_stride,pilot_factor "
                          "(default: the library's per-precision default)")
@@ -572,7 +574,8 @@ def main():
     else:
         torch.cuda.set_device(0)
     prec = PRECISIONS[args.precision]
-    run = pipeline.AbcPipeline(W, prec)
+    l1 = args.distance == "l1"
+    run = pipeline.AbcPipeline(W, prec, distance=args.distance)
     y = pipeline.make_y_gpu(W)
     stream = torch.cuda.current_stream()
 
@@ -584,7 +587,7 @@ def main():
     for _ in range(args.warmup):
         run.step(y)
     torch.cuda.synchronize()
-    st = api.topk_status(run.ws)
+    st = api.topk_status(run.ws) if not l1 else [0, 0, api.l1_status(run.ws, W.J, W.k), 0, 0, 0, 0, 0]
     launches0 = api.launch_info()[2]
     # timed region (device time on the launching stream)
     K = args.steps
@@ -600,7 +603,8 @@ def main():
     clocks.start()
     e0.record(stream)
     for i in range(K):
-        api.profile_events(*ev[i])
+        if not l1:
+            api.profile_events(*ev[i])
         run.step(y)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -608,7 +612,15 @@ def main():
     launches = api.launch_info()[2] - launches0
     barrier()
     ms = e0.elapsed_time(e1) / K
-    tc_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    if l1:      # the L1 scan + final selection, timed alone on the same inputs
+        a, b = ev[0]
+        a.record(stream)
+        api.discrepancy_topk_l1(y, run.x, W.L, run.weights, W.k, run.ws, run.idx, run.dist, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tc_ms = a.elapsed_time(b)
+    else:
+        tc_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     clk = clocks.stop()
     ms, tc_ms = sharding.max_over_ranks([ms, tc_ms], dist, device="cuda")
 
@@ -641,7 +653,7 @@ def main():
     voxels = W.J * n_gpu
     value = voxels / (ms / 1000.0)
     flops = 2.0 * W.L * W.J * W.N
-    kept, total_tiles = api.topk_work(run.ws)
+    kept, total_tiles = api.topk_work(run.ws) if not l1 else (0, 0)
     kp = -(-(({0: 3, 1: 1, 2: 2}[prec]) * W.L + 3) // 64) * 64
     executed = (2.0 * 128 * 64 * kp * kept) if total_tiles else 2.0 * kp * W.J * W.N   # kept: 64-draw tiles
     achieved = executed / (tc_ms / 1000.0) / 1e12
@@ -677,9 +689,21 @@ def main():
         "topk_status": {"error": st[0], "exact_scan_voxels": st[1], "tie_overflow_voxels": st[2], "uncertified_voxels": st[3],
                         "diagnostics": list(st[4:8])},
     }
+    if l1:
+        sm_mhz = clk["sm_mhz"] if clk else 2032.0
+        lane_peak = 148 * 128 * sm_mhz * 1e6 / 1e12
+        inst = 2.0 * W.L * W.J * W.N            # per (voxel, draw, frame): a subtraction and an fma
+        line["dtype"] = "f32"
+        line["config"]["distance"] = "frame-weighted L1 (Sec. V)"
+        line["roofline"] = {"bound": "alu", "achieved": inst / (tc_ms / 1000.0) / 1e12, "peak": lane_peak,
+                            "unit": "T FP32 lane-instructions/s", "frac": inst / (tc_ms / 1000.0) / 1e12 / lane_peak,
+                            "traffic": None, "kernel": "k_l1_scan + k_l1_final (SIMT L1 scan, lists, selection)",
+                            "kernel_ms": tc_ms, "instructions_per_launch": inst,
+                            "peak_source": "FP32 lanes: 148 SMs x 128 x median SM clock under load"}
+        line["topk_status"] = {"tie_overflow_voxels": st[2]}
     if resp is not None:
         line["response_band"] = resp
-    if n_gpu == 1 and not args.no_cpu_baseline:
+    if n_gpu == 1 and not args.no_cpu_baseline and not l1:
         line["cpu_baseline"] = cpu_baseline(W)
     print(json.dumps(line))
     if dist is not None:

@@ -295,6 +295,28 @@ int abc_summarize(const float* theta_dev, int32_t ldtheta, const int64_t* model_
                   const int32_t* idx_dev, int64_t J, int32_t k, const int8_t* preferred_dev, int32_t ncols,
                   float* mean_dev, float* sd_dev, float* lo_dev, float* hi_dev, void* stream);
 
+/* Top-k by the frame-weighted L1 distance d(y, x) = sum_l w_l |y_l - x_l|, the
+ * distance Sec. V recommends (Algorithm 1, steps 4-5 with rho = L1).  Same layouts as
+ * abc_discrepancy_topk: y_dev J x ldy, x_dev N x ldx (fp32, row-major, first L
+ * columns used), w_host L weights (finite, >= 0, copied at the call); outputs idx_dev /
+ * dist_dev J x k, per voxel the k nearest draws sorted by (distance, draw index), ties
+ * to the lower draw index.  Distances are exact fp32 sums over the frames in order
+ * (d += w_l |y_l - x_l| by fma), within (L + 1) 2^-24 d of the exact value.  No
+ * tensor-core form exists for L1: a SIMT scan of shared-memory draw tiles with a
+ * running threshold per voxel.  L in 1..64, k in 1..2048, k <= N <= 2^31 - 1, J <=
+ * 2^31 - 1.  workspace_dev: at least abc_l1_workspace_size(J, k) bytes (candidate
+ * lists, 2k + 512 entries per voxel, and a counter).  ABC_ERR_ARG for arguments out of
+ * range or a short workspace (nothing launched). */
+size_t abc_l1_workspace_size(int64_t J, int32_t k);
+int abc_discrepancy_topk_l1(const float* y_dev, int64_t J, int32_t ldy, const float* x_dev, int64_t N, int32_t ldx,
+                            int32_t L, const float* w_host, int32_t k, int32_t* idx_dev, float* dist_dev,
+                            void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Diagnostics of the last abc_discrepancy_topk_l1 call that used this workspace
+ * (synchronous): the number of voxels at which more candidates tied at a cut's k-th
+ * distance than the list holds (the ties with the lowest draw indices were kept). */
+int abc_l1_status(const void* workspace_dev, int64_t J, int32_t k, int32_t* tie_overflow_host);
+
 /* Posterior band of the lp-ntPET response function (Sec. II-D and its
  * response-function figure): k2a(t) / k2a = 1 + (gamma / k2a) g(t), k2a =
  * k2 / (1 + BP_ND), g the gamma variate of Eq. 4 normalised to 1 at t_P (0 before

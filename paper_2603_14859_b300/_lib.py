@@ -30,6 +30,7 @@ EXPORTS = [
     "abc_mlp_param_count", "abc_mlp_workspace_size", "abc_mlp_init", "abc_mlp_features", "abc_mlp_forward",
     "abc_mlp_loss_grad", "abc_adam_update", "abc_add_noise", "abc_local_abc_smem_bytes", "abc_local_abc",
     "abc_unit_box", "abc_topk_work", "abc_local_abc_table", "abc_response_cri",
+    "abc_l1_workspace_size", "abc_discrepancy_topk_l1", "abc_l1_status",
 ]
 
 
@@ -107,6 +108,10 @@ def lib():
     L.abc_local_abc_table.argtypes = [P, i32, i32, i32, P, P]
     L.abc_local_abc_smem_bytes.restype = sz
     L.abc_response_cri.argtypes = [P, i32, P, i64, i32, i64, i64, P, i32, P, P, P, P]
+    L.abc_l1_workspace_size.argtypes = [i64, i32]
+    L.abc_l1_workspace_size.restype = sz
+    L.abc_discrepancy_topk_l1.argtypes = [P, i64, i32, P, i64, i32, i32, P, i32, P, P, P, sz, P]
+    L.abc_l1_status.argtypes = [P, i64, i32, P]
     L.abc_local_abc.argtypes = [P, i64, i32, i32, P, P, P, i32, f64, P, P, P, i32, i32, f32, u64,
                                 P, P, P, P, P, P, P, P, P, P]
     for fn in ["abc_feng_input", "abc_sample_prior", "abc_simulate", "abc_discrepancy_topk", "abc_topk_status",
@@ -114,7 +119,7 @@ def lib():
                "abc_discrepancy_topk_noalloc", "abc_default_tuning", "abc_set_default_tuning",
                "abc_batch_discrepancy_topk", "abc_launch_info", "abc_mlp_init", "abc_mlp_features",
                "abc_mlp_forward", "abc_mlp_loss_grad", "abc_adam_update", "abc_add_noise", "abc_local_abc", "abc_unit_box", "abc_topk_work",
-               "abc_local_abc_table", "abc_response_cri"]:
+               "abc_local_abc_table", "abc_response_cri", "abc_discrepancy_topk_l1", "abc_l1_status"]:
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L

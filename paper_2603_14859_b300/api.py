@@ -175,6 +175,32 @@ def launch_info():
     return g.value, r.value, n.value
 
 
+def l1_workspace_size(J, k):
+    return int(lib().abc_l1_workspace_size(J, k))
+
+
+def discrepancy_topk_l1(y, x, L, w, k, workspace=None, idx=None, dist=None, stream=None):
+    """Per voxel the k nearest draws by the frame-weighted L1 distance -> (idx int32, dist fp32), J x k."""
+    J, N = y.shape[0], x.shape[0]
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+    if workspace is None:
+        workspace = torch.empty(max(1, l1_workspace_size(J, k)), dtype=torch.uint8, device="cuda")
+    if idx is None:
+        idx = torch.empty((J, k), dtype=torch.int32, device="cuda")
+    if dist is None:
+        dist = torch.empty((J, k), dtype=torch.float32, device="cuda")
+    check(lib().abc_discrepancy_topk_l1(_ptr(y), J, y.shape[1], _ptr(x), N, x.shape[1], L,
+                                        w.ctypes.data_as(ctypes.c_void_p), k, _ptr(idx), _ptr(dist), _ptr(workspace),
+                                        workspace.numel(), _stream(stream)))
+    return idx, dist
+
+
+def l1_status(workspace, J, k):
+    v = ctypes.c_int32(0)
+    check(lib().abc_l1_status(_ptr(workspace), J, k, ctypes.byref(v)))
+    return v.value
+
+
 def response_cri(theta, first, last, t, idx, out=None, stream=None):
     """Posterior mean and 95 % band of the lp-ntPET response function
     1 + (gamma / k2a) g(t) at the times t (minutes), over each voxel's accepted

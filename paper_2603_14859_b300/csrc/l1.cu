@@ -1,0 +1,233 @@
+// Top-k by the frame-weighted L1 distance d(y, x) = sum_l w_l |y_l - x_l|, the
+// distance Sec. V recommends (Algorithm 1, steps 4-5 with rho = L1).  The L1
+// distance has no inner-product expansion, so there is no tensor-core form: a
+// block of voxels (one warp each) walks the draws in shared-memory tiles, every
+// lane accumulating eight draws' distances in fp32 over the frames in order, and
+// appends the draws at or below its voxel's running threshold to the voxel's
+// candidate list; a list near its capacity is cut to its k smallest (exact
+// radix select), which sets the threshold.  A second kernel selects and sorts
+// the final k per voxel by (distance, draw index).
+#include <string.h>
+
+#include "common.cuh"
+#include "select.cuh"
+
+namespace {
+
+using vpet::f2key;
+using vpet::key2f;
+
+constexpr int L1_TILE = 256;            // draws per shared-memory tile (8 per lane)
+constexpr int L1_TS = L1_TILE + 1;      // padded row of the transposed tile (no bank conflicts)
+constexpr int L1_MAXL = 64;
+
+struct L1Args {
+    const float* y;
+    int64_t J;
+    int ldy;
+    const float* x;
+    int64_t N;
+    int ldx;
+    int L, k, C;                        // frames, accepted draws, list capacity per voxel
+    float w[L1_MAXL];
+    float* keys;                        // J x C candidate distances
+    int32_t* idx;                       // J x C candidate draw indices (increasing within a list)
+    int32_t* cnt;                       // J list lengths
+    int32_t* status;                    // [0] voxels whose ties at a cut exceeded the list
+    float* out_dist;
+    int32_t* out_idx;
+    int sortcap;
+};
+
+// Cuts a list (in increasing draw order) to its entries <= T, T its exact k-th key,
+// keeping at most cap: when more entries tie at T than fit, the ties with the lowest
+// draw indices stay and later draws must be strictly below T.  Returns the new
+// threshold; cnt becomes the new length.
+__device__ float cut_list(float* kj, int32_t* ij, int& cnt, int k, int cap, uint32_t* hist, int lane,
+                          int32_t* status) {
+    const uint32_t T = vpet::warp_select(kj, cnt, k - 1, 4, hist, lane);
+    const vpet::KthKey c = vpet::warp_count_key(kj, cnt, T, lane);
+    if (c.n_less + c.n_eq <= cap) {
+        cnt = vpet::warp_compact(kj, ij, cnt, T, cap, lane);
+        return key2f(T);
+    }
+    const uint32_t Ti = vpet::warp_select_tie_index(kj, ij, cnt, T, cap - c.n_less - 1, hist, lane);
+    cnt = vpet::warp_compact_ties(kj, ij, cnt, T, Ti, lane);
+    if (lane == 0) atomicAdd(&status[0], 1);
+    return key2f(T - 1u);               // the largest float below T
+}
+
+__global__ void __launch_bounds__(1024) k_l1_scan(const __grid_constant__ L1Args A) {
+    extern __shared__ __align__(16) float sm[];
+    const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* xs = sm;                                          // [L][L1_TS]: x_l of the tile's draws
+    float* wsh = xs + A.L * L1_TS;                           // [L1_MAXL]: w_l
+    float* ys = wsh + L1_MAXL;                               // [warps][L1_MAXL]: y_l
+    uint32_t* hist = (uint32_t*)(ys + warps * L1_MAXL) + wid * 256;
+    const int64_t j = (int64_t)blockIdx.x * warps + wid;
+    const bool valid = j < A.J;
+    float* yw = ys + wid * L1_MAXL;
+    for (int l = lane; l < A.L; l += 32) yw[l] = valid ? A.y[j * A.ldy + l] : 0.0f;
+    for (int l = threadIdx.x; l < A.L; l += blockDim.x) wsh[l] = A.w[l];
+    float* kj = A.keys + (valid ? j : 0) * (int64_t)A.C;
+    int32_t* ij = A.idx + (valid ? j : 0) * (int64_t)A.C;
+    float thr = __int_as_float(0x7F800000);                 // +inf until the first cut
+    int cnt = 0;
+    for (int64_t t0 = 0; t0 < A.N; t0 += L1_TILE) {
+        const int nt = A.N - t0 < L1_TILE ? (int)(A.N - t0) : L1_TILE;
+        __syncthreads();                                     // the previous tile is consumed
+        for (int e = threadIdx.x; e < L1_TILE * A.L; e += blockDim.x) {
+            const int u = e / A.L, l = e - u * A.L;
+            xs[l * L1_TS + u] = u < nt ? A.x[(t0 + u) * A.ldx + l] : 0.0f;
+        }
+        __syncthreads();
+        if (!valid) continue;
+        float d[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) d[u] = 0.0f;
+        for (int l = 0; l < A.L; ++l) {                     // frames in order: one fixed summation
+            const float yl = yw[l], wl = wsh[l];
+            const float* xr = xs + l * L1_TS + lane;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) d[u] = fmaf(wl, fabsf(yl - xr[32 * u]), d[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int uu = 32 * u + lane;
+            const bool take = uu < nt && d[u] <= thr;
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, take);
+            if (take) {
+                const int pos = cnt + __popc(b & ((1u << lane) - 1u));
+                kj[pos] = d[u];
+                ij[pos] = (int32_t)(t0 + uu);
+            }
+            cnt += __popc(b);
+        }
+        if (cnt > A.C - L1_TILE) {                           // no room for another tile: cut
+            __syncwarp();
+            thr = cut_list(kj, ij, cnt, A.k, A.C - L1_TILE, hist, lane, A.status);
+        }
+    }
+    if (valid && lane == 0) A.cnt[j] = cnt;
+}
+
+// Final k per voxel: exact k-th key, entries at or below it (ties beyond the sort
+// buffer by lowest draw index), sorted by (distance, draw index).
+__global__ void k_l1_final(const __grid_constant__ L1Args A) {
+    extern __shared__ __align__(16) uint8_t fsm[];
+    const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t* hist = (uint32_t*)fsm + wid * 256;
+    unsigned long long* sbuf = (unsigned long long*)(fsm + warps * 1024) + (size_t)wid * A.sortcap;
+    const int64_t j = (int64_t)blockIdx.x * warps + wid;
+    if (j >= A.J) return;
+    float* kj = A.keys + j * (int64_t)A.C;
+    int32_t* ij = A.idx + j * (int64_t)A.C;
+    int cnt = A.cnt[j];
+    if (cnt > A.k) {
+        const uint32_t K = vpet::warp_select(kj, cnt, A.k - 1, 4, hist, lane);
+        const vpet::KthKey c = vpet::warp_count_key(kj, cnt, K, lane);
+        if (c.n_less + c.n_eq > A.sortcap) {
+            const uint32_t Ti = vpet::warp_select_tie_index(kj, ij, cnt, K, A.k - c.n_less - 1, hist, lane);
+            cnt = vpet::warp_compact_ties(kj, ij, cnt, K, Ti, lane);
+        } else {
+            cnt = vpet::warp_compact(kj, ij, cnt, K, A.sortcap, lane);
+        }
+    }
+    int n2 = 32;
+    while (n2 < cnt) n2 <<= 1;
+    for (int i = lane; i < n2; i += 32)
+        sbuf[i] = i < cnt ? (((unsigned long long)f2key(kj[i]) << 32) | (uint32_t)ij[i]) : ~0ull;
+    vpet::warp_bitonic_sort(sbuf, n2, lane);
+    for (int r = lane; r < A.k; r += 32) {
+        const unsigned long long e = r < cnt ? sbuf[r] : ~0ull;
+        A.out_idx[j * A.k + r] = r < cnt ? (int32_t)(uint32_t)e : -1;
+        A.out_dist[j * A.k + r] = r < cnt ? key2f((uint32_t)(e >> 32)) : __int_as_float(0x7F800000);
+    }
+}
+
+int l1_capacity(int k) { return (int)vpet_round_up(2 * (int64_t)k + 2 * L1_TILE, 32); }
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" size_t abc_l1_workspace_size(int64_t J, int32_t k) {
+    if (J < 0 || k < 1 || k > 2048) return 0;
+    const size_t C = (size_t)l1_capacity(k);
+    return align256((size_t)J * C * 4) * 2 + align256((size_t)J * 4) + 512;   // + alignment slack, counter
+}
+
+extern "C" int abc_discrepancy_topk_l1(const float* y_dev, int64_t J, int32_t ldy, const float* x_dev, int64_t N,
+                                       int32_t ldx, int32_t L, const float* w_host, int32_t k, int32_t* idx_dev,
+                                       float* dist_dev, void* workspace_dev, size_t workspace_bytes,
+                                       void* stream) {
+    vpet::clear_error();
+    VPET_ARG(L >= 1 && L <= L1_MAXL, "abc_discrepancy_topk_l1: L must be in 1..%d", L1_MAXL);
+    VPET_ARG(k >= 1 && k <= 2048, "abc_discrepancy_topk_l1: k must be in 1..2048");
+    VPET_ARG(J >= 0 && J <= 0x7FFFFFFF, "abc_discrepancy_topk_l1: J must be in 0..2^31-1");
+    VPET_ARG(N >= k && N <= 0x7FFFFFFF, "abc_discrepancy_topk_l1: need k <= N <= 2^31 - 1");
+    VPET_ARG(ldy >= L && ldx >= L, "abc_discrepancy_topk_l1: ldy and ldx must be >= L");
+    VPET_ARG(w_host, "abc_discrepancy_topk_l1: null weights");
+    L1Args A;
+    memset(&A, 0, sizeof A);
+    for (int l = 0; l < L; ++l) {
+        VPET_ARG(w_host[l] >= 0.0f && w_host[l] < 3.0e38f, "abc_discrepancy_topk_l1: weight %d must be finite, >= 0", l);
+        A.w[l] = w_host[l];
+    }
+    const size_t need = abc_l1_workspace_size(J, k);
+    VPET_ARG(workspace_bytes >= need, "abc_discrepancy_topk_l1: workspace %zu < %zu bytes", workspace_bytes, need);
+    if (J == 0) return ABC_OK;
+    VPET_ARG(y_dev && x_dev && idx_dev && dist_dev && workspace_dev, "abc_discrepancy_topk_l1: null pointer");
+    A.y = y_dev;
+    A.J = J;
+    A.ldy = ldy;
+    A.x = x_dev;
+    A.N = N;
+    A.ldx = ldx;
+    A.L = L;
+    A.k = k;
+    A.C = l1_capacity(k);
+    uint8_t* ws = (uint8_t*)(((uintptr_t)workspace_dev + 255) & ~(uintptr_t)255);
+    A.keys = (float*)ws;
+    A.idx = (int32_t*)(ws + align256((size_t)J * A.C * 4));
+    A.cnt = (int32_t*)(ws + 2 * align256((size_t)J * A.C * 4));
+    A.out_dist = dist_dev;
+    A.out_idx = idx_dev;
+    int sortcap = 64;
+    while (sortcap < k + 8) sortcap <<= 1;
+    A.sortcap = sortcap;
+    cudaStream_t s = (cudaStream_t)stream;
+    // tie-overflow counter: the last 256 bytes of the workspace
+    A.status = (int32_t*)(ws + 2 * align256((size_t)J * A.C * 4) + align256((size_t)J * 4));
+    VPET_CUDA(cudaMemsetAsync(A.status, 0, 4, s));
+    const int warps = J >= 32 * 2 * 148 ? 32 : 8;
+    const size_t smem = ((size_t)L * L1_TS + L1_MAXL + (size_t)warps * L1_MAXL + (size_t)warps * 256) * 4;
+    static size_t configured = 0;
+    if (smem > 48 * 1024 && smem > configured) {
+        VPET_CUDA(cudaFuncSetAttribute(k_l1_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = smem;
+    }
+    k_l1_scan<<<(unsigned)vpet_ceil_div(J, warps), warps * 32, smem, s>>>(A);
+    VPET_LAUNCH_CHECK();
+    int fw = 8;
+    while (fw > 1 && (size_t)fw * (1024 + (size_t)sortcap * 8) > 96 * 1024) fw >>= 1;
+    const size_t fsmem = (size_t)fw * (1024 + (size_t)sortcap * 8);
+    static size_t fconfigured = 0;
+    if (fsmem > 48 * 1024 && fsmem > fconfigured) {
+        VPET_CUDA(cudaFuncSetAttribute(k_l1_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+        fconfigured = fsmem;
+    }
+    k_l1_final<<<(unsigned)vpet_ceil_div(J, fw), fw * 32, fsmem, s>>>(A);
+    VPET_LAUNCH_CHECK();
+    return ABC_OK;
+}
+
+extern "C" int abc_l1_status(const void* workspace_dev, int64_t J, int32_t k, int32_t* tie_overflow_host) {
+    vpet::clear_error();
+    VPET_ARG(workspace_dev && tie_overflow_host && J >= 0 && k >= 1 && k <= 2048, "abc_l1_status: bad argument");
+    const int C = l1_capacity(k);
+    const uint8_t* ws = (const uint8_t*)(((uintptr_t)workspace_dev + 255) & ~(uintptr_t)255);
+    const int32_t* st = (const int32_t*)(ws + 2 * align256((size_t)J * C * 4) + align256((size_t)J * 4));
+    VPET_CUDA(cudaMemcpy(tie_overflow_host, st, 4, cudaMemcpyDeviceToHost));
+    return ABC_OK;
+}

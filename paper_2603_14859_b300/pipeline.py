@@ -33,7 +33,8 @@ class StepOutput:
 
 
 class AbcPipeline:
-    def __init__(self, W: S.Workload, precision: int | None = None, ldtheta: int = 8, own_workspace: bool = True):
+    def __init__(self, W: S.Workload, precision: int | None = None, ldtheta: int = 8, own_workspace: bool = True,
+                 distance: str = "l2"):
         self.W = W
         self.precision = (_lib.ABC_FP32 if W.precision == "fp32" else _lib.ABC_BF16_RESCORE) if precision is None \
             else precision
@@ -48,7 +49,11 @@ class AbcPipeline:
         dev = "cuda"
         self.theta = torch.zeros((self.N, ldtheta), dtype=torch.float32, device=dev)
         self.x = torch.zeros((self.N, self.ldx), dtype=torch.float32, device=dev)
-        self.ws = api.alloc_workspace(self.J, self.N, self.L, self.k, self.precision) if own_workspace else None
+        self.distance = distance
+        if distance == "l1":      # Sec. V's L1 distance: SIMT scan, its own candidate-list workspace
+            self.ws = torch.empty(api.l1_workspace_size(self.J, self.k), dtype=torch.uint8, device="cuda")
+        else:
+            self.ws = api.alloc_workspace(self.J, self.N, self.L, self.k, self.precision) if own_workspace else None
         self.idx = torch.empty((self.J, self.k), dtype=torch.int32, device=dev)
         self.dist = torch.empty((self.J, self.k), dtype=torch.float32, device=dev)
         M = len(W.models)
@@ -69,8 +74,11 @@ class AbcPipeline:
 
     def select(self, y, stream=None):
         """Algorithm 1, steps 4-5 plus model probabilities and summaries."""
-        api.discrepancy_topk(y, self.x, self.L, self.weights, self.k, self.precision, self.ws, self.idx, self.dist,
-                             stream=stream)
+        if self.distance == "l1":
+            api.discrepancy_topk_l1(y, self.x, self.L, self.weights, self.k, self.ws, self.idx, self.dist, stream=stream)
+        else:
+            api.discrepancy_topk(y, self.x, self.L, self.weights, self.k, self.precision, self.ws, self.idx,
+                                 self.dist, stream=stream)
         api.model_select(self.idx, self.offsets, self.prob, self.pref, stream=stream)
         pref = self.pref if len(self.W.models) > 1 else None
         api.summarize(self.theta, self.offsets, self.nparams, self.has_ki, [0, 1, 2], self.idx, pref, out=self.summ,

@@ -194,3 +194,27 @@ def test_response_band_validation_without_gpu(lib):
     nan = np.array([1.0, np.nan], np.float32)
     assert call(t=nan.ctypes.data_as(P), T=2) == _lib.ABC_ERR_ARG
     assert call(J=0) == _lib.ABC_OK                        # nothing to do, nothing launched
+
+
+def test_l1_validation_without_gpu(lib):
+    """abc_discrepancy_topk_l1 and its workspace size check their arguments on the host."""
+    from paper_2603_14859_b300 import _lib
+    P = ctypes.c_void_p
+    w = np.ones(64, np.float32)
+    wp = w.ctypes.data_as(P)
+    assert lib.abc_l1_workspace_size(100, 0) == 0 and lib.abc_l1_workspace_size(-1, 5) == 0
+    ws = lib.abc_l1_workspace_size(100, 50)
+    assert ws >= 100 * (2 * 50 + 512) * 8
+
+    def call(J=100, ldy=64, N=1000, ldx=64, L=60, w=wp, k=50, wsb=ws):
+        return lib.abc_discrepancy_topk_l1(P(16), J, ldy, P(16), N, ldx, L, w, k, P(16), P(16), P(16), wsb, None)
+    assert call(L=0) == _lib.ABC_ERR_ARG and call(L=65) == _lib.ABC_ERR_ARG
+    assert call(k=0) == _lib.ABC_ERR_ARG and call(k=2049) == _lib.ABC_ERR_ARG
+    assert call(N=49) == _lib.ABC_ERR_ARG                      # fewer draws than k
+    assert call(ldy=59) == _lib.ABC_ERR_ARG and call(ldx=59) == _lib.ABC_ERR_ARG
+    assert call(w=None) == _lib.ABC_ERR_ARG
+    assert call(wsb=ws - 1) == _lib.ABC_ERR_ARG
+    neg = np.ones(60, np.float32)
+    neg[7] = -1.0
+    assert call(w=neg.ctypes.data_as(P)) == _lib.ABC_ERR_ARG
+    assert call(J=0, wsb=lib.abc_l1_workspace_size(0, 50)) == _lib.ABC_OK
