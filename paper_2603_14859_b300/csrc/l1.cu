@@ -1,8 +1,9 @@
 // Top-k by the frame-weighted L1 distance d(y, x) = sum_l w_l |y_l - x_l|, the
 // distance Sec. V recommends (Algorithm 1, steps 4-5 with rho = L1).  The L1
 // distance has no inner-product expansion, so there is no tensor-core form: a
-// block of voxels (one warp each) walks the draws in shared-memory tiles, every
-// lane accumulating eight draws' distances in fp32 over the frames in order, and
+// block of voxels (four per warp) walks the draws in shared-memory tiles, every
+// lane accumulating eight draws' distances to each of its warp's four voxels in
+// fp32 over the frames in order (each draw value read once serves four), and
 // appends the draws at or below its voxel's running threshold to the voxel's
 // candidate list; a list near its capacity is cut to its k smallest (exact
 // radix select), which sets the threshold.  A second kernel selects and sorts
@@ -57,22 +58,34 @@ __device__ float cut_list(float* kj, int32_t* ij, int& cnt, int k, int cap, uint
     return key2f(T - 1u);               // the largest float below T
 }
 
-__global__ void __launch_bounds__(1024) k_l1_scan(const __grid_constant__ L1Args A) {
+constexpr int L1_V = 4;                 // voxels per warp (each loaded draw value serves four)
+
+__global__ void __launch_bounds__(256, 2) k_l1_scan(const __grid_constant__ L1Args A) {
     extern __shared__ __align__(16) float sm[];
     const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* xs = sm;                                          // [L][L1_TS]: x_l of the tile's draws
     float* wsh = xs + A.L * L1_TS;                           // [L1_MAXL]: w_l
-    float* ys = wsh + L1_MAXL;                               // [warps][L1_MAXL]: y_l
-    uint32_t* hist = (uint32_t*)(ys + warps * L1_MAXL) + wid * 256;
-    const int64_t j = (int64_t)blockIdx.x * warps + wid;
-    const bool valid = j < A.J;
-    float* yw = ys + wid * L1_MAXL;
-    for (int l = lane; l < A.L; l += 32) yw[l] = valid ? A.y[j * A.ldy + l] : 0.0f;
+    float* ys = wsh + L1_MAXL;                               // [warps][L1_V][L1_MAXL]: y_l
+    uint32_t* hist = (uint32_t*)(ys + warps * L1_V * L1_MAXL) + wid * 256;
+    const int64_t j0 = ((int64_t)blockIdx.x * warps + wid) * L1_V;
+    float* yw = ys + wid * L1_V * L1_MAXL;
+    float* kj[L1_V];
+    int32_t* ij[L1_V];
+    float thr[L1_V];
+    int cnt[L1_V];
+    bool valid[L1_V];
+#pragma unroll
+    for (int v = 0; v < L1_V; ++v) {
+        const int64_t j = j0 + v;
+        valid[v] = j < A.J;
+        for (int l = lane; l < A.L; l += 32) yw[v * L1_MAXL + l] = valid[v] ? A.y[j * A.ldy + l] : 0.0f;
+        kj[v] = A.keys + (valid[v] ? j : 0) * (int64_t)A.C;
+        ij[v] = A.idx + (valid[v] ? j : 0) * (int64_t)A.C;
+        thr[v] = __int_as_float(0x7F800000);               // +inf until the first cut
+        cnt[v] = 0;
+    }
     for (int l = threadIdx.x; l < A.L; l += blockDim.x) wsh[l] = A.w[l];
-    float* kj = A.keys + (valid ? j : 0) * (int64_t)A.C;
-    int32_t* ij = A.idx + (valid ? j : 0) * (int64_t)A.C;
-    float thr = __int_as_float(0x7F800000);                 // +inf until the first cut
-    int cnt = 0;
+    const bool any = valid[0];
     for (int64_t t0 = 0; t0 < A.N; t0 += L1_TILE) {
         const int nt = A.N - t0 < L1_TILE ? (int)(A.N - t0) : L1_TILE;
         __syncthreads();                                     // the previous tile is consumed
@@ -81,34 +94,49 @@ __global__ void __launch_bounds__(1024) k_l1_scan(const __grid_constant__ L1Args
             xs[l * L1_TS + u] = u < nt ? A.x[(t0 + u) * A.ldx + l] : 0.0f;
         }
         __syncthreads();
-        if (!valid) continue;
-        float d[8];
+        if (!any) continue;
+        float d[L1_V][8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) d[u] = 0.0f;
+        for (int v = 0; v < L1_V; ++v)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) d[v][u] = 0.0f;
         for (int l = 0; l < A.L; ++l) {                     // frames in order: one fixed summation
-            const float yl = yw[l], wl = wsh[l];
+            const float wl = wsh[l];
+            float xv[8];
             const float* xr = xs + l * L1_TS + lane;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) d[u] = fmaf(wl, fabsf(yl - xr[32 * u]), d[u]);
+            for (int u = 0; u < 8; ++u) xv[u] = xr[32 * u];
+#pragma unroll
+            for (int v = 0; v < L1_V; ++v) {
+                const float yl = yw[v * L1_MAXL + l];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) d[v][u] = fmaf(wl, fabsf(yl - xv[u]), d[v][u]);
+            }
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int uu = 32 * u + lane;
-            const bool take = uu < nt && d[u] <= thr;
-            const uint32_t b = __ballot_sync(0xFFFFFFFFu, take);
-            if (take) {
-                const int pos = cnt + __popc(b & ((1u << lane) - 1u));
-                kj[pos] = d[u];
-                ij[pos] = (int32_t)(t0 + uu);
+        for (int v = 0; v < L1_V; ++v) {
+            if (!valid[v]) continue;                         // warp-uniform
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int uu = 32 * u + lane;
+                const bool take = uu < nt && d[v][u] <= thr[v];
+                const uint32_t b = __ballot_sync(0xFFFFFFFFu, take);
+                if (take) {
+                    const int pos = cnt[v] + __popc(b & ((1u << lane) - 1u));
+                    kj[v][pos] = d[v][u];
+                    ij[v][pos] = (int32_t)(t0 + uu);
+                }
+                cnt[v] += __popc(b);
             }
-            cnt += __popc(b);
-        }
-        if (cnt > A.C - L1_TILE) {                           // no room for another tile: cut
-            __syncwarp();
-            thr = cut_list(kj, ij, cnt, A.k, A.C - L1_TILE, hist, lane, A.status);
+            if (cnt[v] > A.C - L1_TILE) {                    // no room for another tile: cut
+                __syncwarp();
+                thr[v] = cut_list(kj[v], ij[v], cnt[v], A.k, A.C - L1_TILE, hist, lane, A.status);
+            }
         }
     }
-    if (valid && lane == 0) A.cnt[j] = cnt;
+#pragma unroll
+    for (int v = 0; v < L1_V; ++v)
+        if (valid[v] && lane == 0) A.cnt[j0 + v] = cnt[v];
 }
 
 // Final k per voxel: exact k-th key, entries at or below it (ties beyond the sort
@@ -200,14 +228,16 @@ extern "C" int abc_discrepancy_topk_l1(const float* y_dev, int64_t J, int32_t ld
     // tie-overflow counter: the last 256 bytes of the workspace
     A.status = (int32_t*)(ws + 2 * align256((size_t)J * A.C * 4) + align256((size_t)J * 4));
     VPET_CUDA(cudaMemsetAsync(A.status, 0, 4, s));
-    const int warps = J >= 32 * 2 * 148 ? 32 : 8;
-    const size_t smem = ((size_t)L * L1_TS + L1_MAXL + (size_t)warps * L1_MAXL + (size_t)warps * 256) * 4;
+    // 8 warps (32 voxels) per block when the grid still fills two blocks per SM, else 4
+    const int warps = J >= (int64_t)8 * L1_V * 2 * 148 ? 8 : 4;
+    const size_t smem =
+        ((size_t)L * L1_TS + L1_MAXL + (size_t)warps * L1_V * L1_MAXL + (size_t)warps * 256) * 4;
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
         VPET_CUDA(cudaFuncSetAttribute(k_l1_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = smem;
     }
-    k_l1_scan<<<(unsigned)vpet_ceil_div(J, warps), warps * 32, smem, s>>>(A);
+    k_l1_scan<<<(unsigned)vpet_ceil_div(J, (int64_t)warps * L1_V), warps * 32, smem, s>>>(A);
     VPET_LAUNCH_CHECK();
     int fw = 8;
     while (fw > 1 && (size_t)fw * (1024 + (size_t)sortcap * 8) > 96 * 1024) fw >>= 1;
