@@ -138,9 +138,9 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
-def cpu_baseline(W, seconds_budget=20.0):
+def cpu_baseline(W, seconds_budget=20.0, distance="l2"):
     """The FP64 oracle as it stands, timed on this host on a bounded sample of the
-    workload and scaled to voxels/s of the full volume."""
+    workload and scaled to voxels/s of the full volume (with the step's distance)."""
     import oracle
     from paper_2603_14859_b300 import synth as S
     oracle.build()
@@ -167,13 +167,13 @@ def cpu_baseline(W, seconds_budget=20.0):
     y = (xs[rng.integers(0, len(xs), 64)] * (1 + 0.1 * rng.standard_normal((64, L)))).astype(np.float32)
     k = min(W.k, len(xs))
     t0 = time.perf_counter()
-    oracle.topk(y, xs, W.weights, k)
+    (oracle.topk_l1 if distance == "l1" else oracle.topk)(y, xs, W.weights, k)
     dt = time.perf_counter() - t0
     per_pair = dt / (64 * len(xs))
     t_topk = per_pair * W.J * W.N * math.log(W.N) / math.log(len(xs))   # n log n sort
     total = t_sim + t_topk
     return {"value": W.J / total, "unit": "voxels/s", "cores": cores, "kind": "oracle",
-            "sample": (f"simulation timed on {', '.join(sim_desc)}; distance+sort timed on 64 voxels x "
+            "sample": (f"simulation timed on {', '.join(sim_desc)}; {distance} distance+sort timed on 64 voxels x "
                        f"{len(xs)} draws; scaled to {W.J} voxels x {W.N} draws (sort as n log n)"),
             "pairs_per_s": W.J * W.N / total}
 
@@ -552,7 +552,7 @@ def main():
         vals = []
         cb = None
         for _ in range(args.warmup + args.steps):
-            cb = cpu_baseline(W)
+            cb = cpu_baseline(W, distance=args.distance)
             vals.append(cb["value"])
         v = statistics.median(vals[args.warmup:]) if args.steps else vals[-1]
         cb["value"] = v
@@ -703,8 +703,8 @@ def main():
         line["topk_status"] = {"tie_overflow_voxels": st[2]}
     if resp is not None:
         line["response_band"] = resp
-    if n_gpu == 1 and not args.no_cpu_baseline and not l1:
-        line["cpu_baseline"] = cpu_baseline(W)
+    if n_gpu == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(W, distance=args.distance)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
