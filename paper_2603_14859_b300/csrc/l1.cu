@@ -19,7 +19,7 @@ using vpet::f2key;
 using vpet::key2f;
 
 constexpr int L1_TILE = 256;            // draws per shared-memory tile (8 per lane)
-constexpr int L1_TS = L1_TILE + 1;      // padded row of the transposed tile (no bank conflicts)
+constexpr int L1_TS = L1_TILE + 2;      // padded row of the transposed tile (8-byte aligned; few bank conflicts)
 constexpr int L1_MAXL = 64;
 
 struct L1Args {
@@ -32,7 +32,7 @@ struct L1Args {
     int L, k, C;                        // frames, accepted draws, list capacity per voxel
     float w[L1_MAXL];
     float* keys;                        // J x C candidate distances
-    int32_t* idx;                       // J x C candidate draw indices (increasing within a list)
+    int32_t* idx;                       // J x C candidate draw indices
     int32_t* cnt;                       // J list lengths
     int32_t* status;                    // [0] voxels whose ties at a cut exceeded the list
     float* out_dist;
@@ -59,6 +59,33 @@ __device__ float cut_list(float* kj, int32_t* ij, int& cnt, int k, int cap, uint
 }
 
 constexpr int L1_V = 4;                 // voxels per warp (each loaded draw value serves four)
+
+// Packed fp32 pairs (two lanes of arithmetic per instruction, each rounded as the
+// scalar operation would be).
+__device__ __forceinline__ unsigned long long pk(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float pk_lo(unsigned long long v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo;
+}
+__device__ __forceinline__ float pk_hi(unsigned long long v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return hi;
+}
+// d + w |y - x| on both halves
+__device__ __forceinline__ unsigned long long l1_step2(unsigned long long w, unsigned long long y, unsigned long long x,
+                                                       unsigned long long d) {
+    unsigned long long t, r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(y), "l"(x));
+    t &= 0x7FFFFFFF7FFFFFFFull;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(w), "l"(t), "l"(d));
+    return r;
+}
 
 __global__ void __launch_bounds__(256, 2) k_l1_scan(const __grid_constant__ L1Args A) {
     extern __shared__ __align__(16) float sm[];
@@ -95,22 +122,25 @@ __global__ void __launch_bounds__(256, 2) k_l1_scan(const __grid_constant__ L1Ar
         }
         __syncthreads();
         if (!any) continue;
-        float d[L1_V][8];
+        // lane draws 2 lane + 64 p + {0, 1} (p < 4), distances in packed pairs
+        unsigned long long d2[L1_V][4];
 #pragma unroll
         for (int v = 0; v < L1_V; ++v)
 #pragma unroll
-            for (int u = 0; u < 8; ++u) d[v][u] = 0.0f;
+            for (int q = 0; q < 4; ++q) d2[v][q] = 0ull;
         for (int l = 0; l < A.L; ++l) {                     // frames in order: one fixed summation
             const float wl = wsh[l];
-            float xv[8];
-            const float* xr = xs + l * L1_TS + lane;
+            const unsigned long long w2 = pk(wl, wl);
+            unsigned long long x2[4];
+            const unsigned long long* xr = (const unsigned long long*)(xs + l * L1_TS) + lane;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) xv[u] = xr[32 * u];
+            for (int q = 0; q < 4; ++q) x2[q] = xr[32 * q];
 #pragma unroll
             for (int v = 0; v < L1_V; ++v) {
                 const float yl = yw[v * L1_MAXL + l];
+                const unsigned long long y2 = pk(yl, yl);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) d[v][u] = fmaf(wl, fabsf(yl - xv[u]), d[v][u]);
+                for (int q = 0; q < 4; ++q) d2[v][q] = l1_step2(w2, y2, x2[q], d2[v][q]);
             }
         }
 #pragma unroll
@@ -118,12 +148,13 @@ __global__ void __launch_bounds__(256, 2) k_l1_scan(const __grid_constant__ L1Ar
             if (!valid[v]) continue;                         // warp-uniform
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int uu = 32 * u + lane;
-                const bool take = uu < nt && d[v][u] <= thr[v];
+                const int uu = 64 * (u >> 1) + 2 * lane + (u & 1);
+                const float du = (u & 1) ? pk_hi(d2[v][u >> 1]) : pk_lo(d2[v][u >> 1]);
+                const bool take = uu < nt && du <= thr[v];
                 const uint32_t b = __ballot_sync(0xFFFFFFFFu, take);
                 if (take) {
                     const int pos = cnt[v] + __popc(b & ((1u << lane) - 1u));
-                    kj[v][pos] = d[v][u];
+                    kj[v][pos] = du;
                     ij[v][pos] = (int32_t)(t0 + uu);
                 }
                 cnt[v] += __popc(b);
