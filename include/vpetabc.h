@@ -305,7 +305,8 @@ int abc_summarize(const float* theta_dev, int32_t ldtheta, const int64_t* model_
  * tensor-core form exists for L1: a SIMT scan of shared-memory draw tiles with a
  * running threshold per voxel.  L in 1..64, k in 1..2048, k <= N <= 2^31 - 1, J <=
  * 2^31 - 1.  workspace_dev: at least abc_l1_workspace_size(J, k) bytes (candidate
- * lists, 2k + 512 entries per voxel, and a counter).  ABC_ERR_ARG for arguments out of
+ * lists of 2k + 512 entries per voxel, up to 16 per voxel when few voxels leave the
+ * draws split across blocks, and a counter).  ABC_ERR_ARG for arguments out of
  * range or a short workspace (nothing launched). */
 size_t abc_l1_workspace_size(int64_t J, int32_t k);
 int abc_discrepancy_topk_l1(const float* y_dev, int64_t J, int32_t ldy, const float* x_dev, int64_t N, int32_t ldx,

@@ -6,8 +6,10 @@
 // fp32 over the frames in order (each draw value read once serves four), and
 // appends the draws at or below its voxel's running threshold to the voxel's
 // candidate list; a list near its capacity is cut to its k smallest (exact
-// radix select), which sets the threshold.  A second kernel selects and sorts
-// the final k per voxel by (distance, draw index).
+// radix select), which sets the threshold.  With few voxels the draws are split
+// into segments scanned by separate blocks (one list per voxel and segment).  A
+// second kernel joins a voxel's lists, selects and sorts the final k by
+// (distance, draw index).
 #include <string.h>
 
 #include "common.cuh"
@@ -29,11 +31,13 @@ struct L1Args {
     const float* x;
     int64_t N;
     int ldx;
-    int L, k, C;                        // frames, accepted draws, list capacity per voxel
+    int L, k, C;                        // frames, accepted draws, list capacity per voxel and segment
+    int S;                              // draw segments (blockIdx.y): lists per voxel
+    int64_t seg_len;                    // draws per segment (a multiple of the tile)
     float w[L1_MAXL];
-    float* keys;                        // J x C candidate distances
-    int32_t* idx;                       // J x C candidate draw indices
-    int32_t* cnt;                       // J list lengths
+    float* keys;                        // J x S x C candidate distances
+    int32_t* idx;                       // J x S x C candidate draw indices
+    int32_t* cnt;                       // J x S list lengths
     int32_t* status;                    // [0] voxels whose ties at a cut exceeded the list
     float* out_dist;
     int32_t* out_idx;
@@ -95,6 +99,9 @@ __global__ void __launch_bounds__(256, 2) k_l1_scan(const __grid_constant__ L1Ar
     float* ys = wsh + L1_MAXL;                               // [warps][L1_V][L1_MAXL]: y_l
     uint32_t* hist = (uint32_t*)(ys + warps * L1_V * L1_MAXL) + wid * 256;
     const int64_t j0 = ((int64_t)blockIdx.x * warps + wid) * L1_V;
+    const int seg = blockIdx.y;
+    const int64_t tb = (int64_t)seg * A.seg_len;
+    const int64_t te = tb + A.seg_len < A.N ? tb + A.seg_len : A.N;
     float* yw = ys + wid * L1_V * L1_MAXL;
     float* kj[L1_V];
     int32_t* ij[L1_V];
@@ -106,15 +113,15 @@ __global__ void __launch_bounds__(256, 2) k_l1_scan(const __grid_constant__ L1Ar
         const int64_t j = j0 + v;
         valid[v] = j < A.J;
         for (int l = lane; l < A.L; l += 32) yw[v * L1_MAXL + l] = valid[v] ? A.y[j * A.ldy + l] : 0.0f;
-        kj[v] = A.keys + (valid[v] ? j : 0) * (int64_t)A.C;
-        ij[v] = A.idx + (valid[v] ? j : 0) * (int64_t)A.C;
+        kj[v] = A.keys + ((valid[v] ? j : 0) * A.S + seg) * (int64_t)A.C;
+        ij[v] = A.idx + ((valid[v] ? j : 0) * A.S + seg) * (int64_t)A.C;
         thr[v] = __int_as_float(0x7F800000);               // +inf until the first cut
         cnt[v] = 0;
     }
     for (int l = threadIdx.x; l < A.L; l += blockDim.x) wsh[l] = A.w[l];
     const bool any = valid[0];
-    for (int64_t t0 = 0; t0 < A.N; t0 += L1_TILE) {
-        const int nt = A.N - t0 < L1_TILE ? (int)(A.N - t0) : L1_TILE;
+    for (int64_t t0 = tb; t0 < te; t0 += L1_TILE) {
+        const int nt = te - t0 < L1_TILE ? (int)(te - t0) : L1_TILE;
         __syncthreads();                                     // the previous tile is consumed
         for (int e = threadIdx.x; e < L1_TILE * A.L; e += blockDim.x) {
             const int u = e / A.L, l = e - u * A.L;
@@ -167,7 +174,7 @@ __global__ void __launch_bounds__(256, 2) k_l1_scan(const __grid_constant__ L1Ar
     }
 #pragma unroll
     for (int v = 0; v < L1_V; ++v)
-        if (valid[v] && lane == 0) A.cnt[j0 + v] = cnt[v];
+        if (valid[v] && lane == 0) A.cnt[(j0 + v) * A.S + seg] = cnt[v];
 }
 
 // Final k per voxel: exact k-th key, entries at or below it (ties beyond the sort
@@ -179,9 +186,32 @@ __global__ void k_l1_final(const __grid_constant__ L1Args A) {
     unsigned long long* sbuf = (unsigned long long*)(fsm + warps * 1024) + (size_t)wid * A.sortcap;
     const int64_t j = (int64_t)blockIdx.x * warps + wid;
     if (j >= A.J) return;
-    float* kj = A.keys + j * (int64_t)A.C;
-    int32_t* ij = A.idx + j * (int64_t)A.C;
-    int cnt = A.cnt[j];
+    float* kj = A.keys + j * A.S * (int64_t)A.C;
+    int32_t* ij = A.idx + j * A.S * (int64_t)A.C;
+    // the segments' lists, one after another (each moves down: rows of 32 are read
+    // before they are written, and every write lands at or below its read)
+    int cnt = A.cnt[j * A.S];
+    for (int sg = 1; sg < A.S; ++sg) {
+        const int c = A.cnt[j * A.S + sg];
+        const int src = sg * A.C;
+        if (src != cnt)
+            for (int b = 0; b < c; b += 32) {
+                const int i = b + lane;
+                float kv = 0.0f;
+                int32_t iv = 0;
+                if (i < c) {
+                    kv = kj[src + i];
+                    iv = ij[src + i];
+                }
+                __syncwarp();
+                if (i < c) {
+                    kj[cnt + i] = kv;
+                    ij[cnt + i] = iv;
+                }
+                __syncwarp();
+            }
+        cnt += c;
+    }
     if (cnt > A.k) {
         const uint32_t K = vpet::warp_select(kj, cnt, A.k - 1, 4, hist, lane);
         const vpet::KthKey c = vpet::warp_count_key(kj, cnt, K, lane);
@@ -206,14 +236,23 @@ __global__ void k_l1_final(const __grid_constant__ L1Args A) {
 
 int l1_capacity(int k) { return (int)vpet_round_up(2 * (int64_t)k + 2 * L1_TILE, 32); }
 
+// Voxels per scan block, and the most draw segments for J voxels: enough blocks for
+// two per SM of a 148-SM B300 (at most 16 segments).
+constexpr int L1_BLOCK_VOXELS = 8 * L1_V;
+int l1_max_segments(int64_t J) {
+    const int64_t groups = J > 0 ? vpet_ceil_div(J, L1_BLOCK_VOXELS) : 1;
+    const int64_t s = vpet_ceil_div(2 * 148, groups);
+    return (int)(s < 1 ? 1 : (s > 16 ? 16 : s));
+}
+size_t l1_list_bytes(int64_t J, int k) { return (size_t)J * l1_max_segments(J) * (size_t)l1_capacity(k) * 4; }
+
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 }  // namespace
 
 extern "C" size_t abc_l1_workspace_size(int64_t J, int32_t k) {
     if (J < 0 || k < 1 || k > 2048) return 0;
-    const size_t C = (size_t)l1_capacity(k);
-    return align256((size_t)J * C * 4) * 2 + align256((size_t)J * 4) + 512;   // + alignment slack, counter
+    return align256(l1_list_bytes(J, k)) * 2 + align256((size_t)J * l1_max_segments(J) * 4) + 512;   // + slack, counter
 }
 
 extern "C" int abc_discrepancy_topk_l1(const float* y_dev, int64_t J, int32_t ldy, const float* x_dev, int64_t N,
@@ -248,8 +287,15 @@ extern "C" int abc_discrepancy_topk_l1(const float* y_dev, int64_t J, int32_t ld
     A.C = l1_capacity(k);
     uint8_t* ws = (uint8_t*)(((uintptr_t)workspace_dev + 255) & ~(uintptr_t)255);
     A.keys = (float*)ws;
-    A.idx = (int32_t*)(ws + align256((size_t)J * A.C * 4));
-    A.cnt = (int32_t*)(ws + 2 * align256((size_t)J * A.C * 4));
+    A.idx = (int32_t*)(ws + align256(l1_list_bytes(J, k)));
+    A.cnt = (int32_t*)(ws + 2 * align256(l1_list_bytes(J, k)));
+    // split the draws into segments when there are too few voxel blocks; a segment
+    // holds at least four tiles
+    int S = l1_max_segments(J);
+    const int64_t smax = N / (4 * L1_TILE);
+    if (S > smax) S = smax < 1 ? 1 : (int)smax;
+    A.seg_len = vpet_round_up(vpet_ceil_div(N, S), L1_TILE);
+    A.S = (int)vpet_ceil_div(N, A.seg_len);
     A.out_dist = dist_dev;
     A.out_idx = idx_dev;
     int sortcap = 64;
@@ -257,10 +303,9 @@ extern "C" int abc_discrepancy_topk_l1(const float* y_dev, int64_t J, int32_t ld
     A.sortcap = sortcap;
     cudaStream_t s = (cudaStream_t)stream;
     // tie-overflow counter: the last 256 bytes of the workspace
-    A.status = (int32_t*)(ws + 2 * align256((size_t)J * A.C * 4) + align256((size_t)J * 4));
+    A.status = (int32_t*)(ws + 2 * align256(l1_list_bytes(J, k)) + align256((size_t)J * l1_max_segments(J) * 4));
     VPET_CUDA(cudaMemsetAsync(A.status, 0, 4, s));
-    // 8 warps (32 voxels) per block when the grid still fills two blocks per SM, else 4
-    const int warps = J >= (int64_t)8 * L1_V * 2 * 148 ? 8 : 4;
+    const int warps = L1_BLOCK_VOXELS / L1_V;
     const size_t smem =
         ((size_t)L * L1_TS + L1_MAXL + (size_t)warps * L1_V * L1_MAXL + (size_t)warps * 256) * 4;
     static size_t configured = 0;
@@ -268,7 +313,7 @@ extern "C" int abc_discrepancy_topk_l1(const float* y_dev, int64_t J, int32_t ld
         VPET_CUDA(cudaFuncSetAttribute(k_l1_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = smem;
     }
-    k_l1_scan<<<(unsigned)vpet_ceil_div(J, (int64_t)warps * L1_V), warps * 32, smem, s>>>(A);
+    k_l1_scan<<<dim3((unsigned)vpet_ceil_div(J, (int64_t)L1_BLOCK_VOXELS), (unsigned)A.S), warps * 32, smem, s>>>(A);
     VPET_LAUNCH_CHECK();
     int fw = 8;
     while (fw > 1 && (size_t)fw * (1024 + (size_t)sortcap * 8) > 96 * 1024) fw >>= 1;
@@ -286,9 +331,9 @@ extern "C" int abc_discrepancy_topk_l1(const float* y_dev, int64_t J, int32_t ld
 extern "C" int abc_l1_status(const void* workspace_dev, int64_t J, int32_t k, int32_t* tie_overflow_host) {
     vpet::clear_error();
     VPET_ARG(workspace_dev && tie_overflow_host && J >= 0 && k >= 1 && k <= 2048, "abc_l1_status: bad argument");
-    const int C = l1_capacity(k);
     const uint8_t* ws = (const uint8_t*)(((uintptr_t)workspace_dev + 255) & ~(uintptr_t)255);
-    const int32_t* st = (const int32_t*)(ws + 2 * align256((size_t)J * C * 4) + align256((size_t)J * 4));
+    const int32_t* st =
+        (const int32_t*)(ws + 2 * align256(l1_list_bytes(J, k)) + align256((size_t)J * l1_max_segments(J) * 4));
     VPET_CUDA(cudaMemcpy(tie_overflow_host, st, 4, cudaMemcpyDeviceToHost));
     return ABC_OK;
 }

@@ -43,20 +43,24 @@ def test_l1_topk_against_oracle(orc, J, N, L, k):
 
 
 def test_l1_ties_and_list_cuts(orc):
-    """Many draws at exactly the same distance (duplicated rows) across the list cuts:
-    the k kept are the lowest-index ones; the tie-overflow diagnostic counts voxels
-    whose ties outgrew a list."""
+    """Many draws at exactly the same distance (duplicated rows) across the list cuts
+    and the draw segments: the k kept are the lowest-index ones; with more ties than a
+    list holds, the tie-overflow diagnostic counts the cuts that kept only the
+    lowest-index ties (at least one per voxel)."""
     from paper_2603_14859_b300 import api
     rng = np.random.default_rng(77)
     L, k, N, J = 16, 20, 20000, 12
     base = rng.normal(size=(1, L)).astype(np.float32)
-    x = rng.normal(size=(N, L)).astype(np.float32) * 3.0
-    x[::37] = base[0] + 0.5                                     # 541 draws at one exact distance
     y = np.repeat(base, J, 0)
     w = np.ones(L, np.float32)
-    ws = torch.empty(api.l1_workspace_size(J, k), dtype=torch.uint8, device="cuda")
-    idx, dist = api.discrepancy_topk_l1(torch.from_numpy(y).cuda(), torch.from_numpy(x).cuda(), L, w, k,
-                                        workspace=ws)
-    oi, od = orc.topk_l1(y, x.astype(np.float64), w.astype(np.float64), k)
-    assert np.array_equal(idx.cpu().numpy(), oi)                 # the first 20 duplicates by index
-    assert api.l1_status(ws, J, k) == J                          # 541 ties > a list of 2k + 512 - 256
+    for stride, overflow in ((37, False), (2, True)):       # 541 ties (fit the lists), 10,000 (do not)
+        x = rng.normal(size=(N, L)).astype(np.float32) * 3.0
+        x[::stride] = base[0] + 0.5
+        ws = torch.empty(api.l1_workspace_size(J, k), dtype=torch.uint8, device="cuda")
+        idx, dist = api.discrepancy_topk_l1(torch.from_numpy(y).cuda(), torch.from_numpy(x).cuda(), L, w, k,
+                                            workspace=ws)
+        oi, od = orc.topk_l1(y[:1], x.astype(np.float64), w.astype(np.float64), k)
+        assert np.array_equal(idx.cpu().numpy(), np.repeat(oi, J, 0))
+        assert np.array_equal(oi[0], np.arange(k) * stride)
+        st = api.l1_status(ws, J, k)
+        assert (st >= J) if overflow else (st == 0)
