@@ -91,11 +91,19 @@ __device__ __forceinline__ unsigned long long l1_step2(unsigned long long w, uns
     return r;
 }
 
-__global__ void __launch_bounds__(256, 2) k_l1_scan(const __grid_constant__ L1Args A) {
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__global__ void __launch_bounds__(512, 1) k_l1_scan(const __grid_constant__ L1Args A) {
     extern __shared__ __align__(16) float sm[];
     const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* xs = sm;                                          // [L][L1_TS]: x_l of the tile's draws
-    float* wsh = xs + A.L * L1_TS;                           // [L1_MAXL]: w_l
+    float* xbuf = sm;                                        // 2 x [L][L1_TS]: x_l of two tiles' draws
+    float* wsh = xbuf + 2 * A.L * L1_TS;                     // [L1_MAXL]: w_l
     float* ys = wsh + L1_MAXL;                               // [warps][L1_V][L1_MAXL]: y_l
     uint32_t* hist = (uint32_t*)(ys + warps * L1_V * L1_MAXL) + wid * 256;
     const int64_t j0 = ((int64_t)blockIdx.x * warps + wid) * L1_V;
@@ -120,15 +128,29 @@ __global__ void __launch_bounds__(256, 2) k_l1_scan(const __grid_constant__ L1Ar
     }
     for (int l = threadIdx.x; l < A.L; l += blockDim.x) wsh[l] = A.w[l];
     const bool any = valid[0];
-    for (int64_t t0 = tb; t0 < te; t0 += L1_TILE) {
+    // tiles stream through two buffers: the next tile's asynchronous copies are in
+    // flight while this one is scanned (draws past the segment are zero-filled)
+    auto stage = [&](int64_t t0, float* dst) {
         const int nt = te - t0 < L1_TILE ? (int)(te - t0) : L1_TILE;
-        __syncthreads();                                     // the previous tile is consumed
         for (int e = threadIdx.x; e < L1_TILE * A.L; e += blockDim.x) {
             const int u = e / A.L, l = e - u * A.L;
-            xs[l * L1_TS + u] = u < nt ? A.x[(t0 + u) * A.ldx + l] : 0.0f;
+            cp_async4(dst + l * L1_TS + u, A.x + (t0 + (u < nt ? u : 0)) * A.ldx + l, u < nt);
         }
-        __syncthreads();
-        if (!any) continue;
+        cp_async_commit();
+    };
+    stage(tb, xbuf);
+    int buf = 0;
+    for (int64_t t0 = tb; t0 < te; t0 += L1_TILE, buf ^= 1) {
+        const int nt = te - t0 < L1_TILE ? (int)(te - t0) : L1_TILE;
+        if (t0 + L1_TILE < te) {
+            stage(t0 + L1_TILE, xbuf + (buf ^ 1) * A.L * L1_TS);
+            cp_async_wait_1();
+        } else {
+            cp_async_wait_0();
+        }
+        __syncthreads();                                     // this tile is in shared memory
+        const float* xs = xbuf + buf * A.L * L1_TS;
+        if (any) {
         // lane draws 2 lane + 64 p + {0, 1} (p < 4), distances in packed pairs
         unsigned long long d2[L1_V][4];
 #pragma unroll
@@ -171,6 +193,8 @@ __global__ void __launch_bounds__(256, 2) k_l1_scan(const __grid_constant__ L1Ar
                 thr[v] = cut_list(kj[v], ij[v], cnt[v], A.k, A.C - L1_TILE, hist, lane, A.status);
             }
         }
+        }
+        __syncthreads();                                     // this buffer is free for the tile after next
     }
 #pragma unroll
     for (int v = 0; v < L1_V; ++v)
@@ -238,7 +262,7 @@ int l1_capacity(int k) { return (int)vpet_round_up(2 * (int64_t)k + 2 * L1_TILE,
 
 // Voxels per scan block, and the most draw segments for J voxels: enough blocks for
 // two per SM of a 148-SM B300 (at most 16 segments).
-constexpr int L1_BLOCK_VOXELS = 8 * L1_V;
+constexpr int L1_BLOCK_VOXELS = 16 * L1_V;
 int l1_max_segments(int64_t J) {
     const int64_t groups = J > 0 ? vpet_ceil_div(J, L1_BLOCK_VOXELS) : 1;
     const int64_t s = vpet_ceil_div(2 * 148, groups);
@@ -307,7 +331,7 @@ extern "C" int abc_discrepancy_topk_l1(const float* y_dev, int64_t J, int32_t ld
     VPET_CUDA(cudaMemsetAsync(A.status, 0, 4, s));
     const int warps = L1_BLOCK_VOXELS / L1_V;
     const size_t smem =
-        ((size_t)L * L1_TS + L1_MAXL + (size_t)warps * L1_V * L1_MAXL + (size_t)warps * 256) * 4;
+        ((size_t)2 * L * L1_TS + L1_MAXL + (size_t)warps * L1_V * L1_MAXL + (size_t)warps * 256) * 4;
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
         VPET_CUDA(cudaFuncSetAttribute(k_l1_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
