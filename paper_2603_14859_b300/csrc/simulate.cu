@@ -361,8 +361,8 @@ __host__ __device__ void simulate_draw(const SimParams& p, const float* th, floa
                     phis(abar * h, p1, p2, p3);
                     // int_0^h Z = Z0 h phi1 + h^2 (b0 phi2 + (b1 - b0) phi3)
                     if (t >= ts_l) integ += h * fmaf(Z, p1, h * fmaf(b1 - b0, p3, b0 * p2));
-                    // Z(h) = e^{-abar h} Z0 + h (b0 phi1 + (b1 - b0) phi2)
-                    Z = expf(-abar * h) * Z + h * fmaf(b1 - b0, p2, b0 * p1);
+                    // Z(h) = e^{-abar h} Z0 + h (b0 phi1 + (b1 - b0) phi2), e^{-z} = 1 - z phi1(z)
+                    Z = fmaf(-abar * h, p1, 1.0f) * Z + h * fmaf(b1 - b0, p2, b0 * p1);
                     cr0 = cr1;
                     g0 = g1;
                     t += h;
