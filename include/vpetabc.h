@@ -152,8 +152,8 @@ typedef struct {
 
 /* The tuning used for `precision` when none is passed: the built-in choice
  * (128-draw tiles, 2 CTAs/SM for ABC_BF16_RESCORE and ABC_FP32, the latter with
- * pilot factor 2.25; 64-draw tiles, 3 CTAs/SM for ABC_SPLIT_DRAWS; pilot stride
- * 16, factor 1.5) unless abc_set_default_tuning replaced it. */
+ * pilot stride 8 and factor 2.25; 64-draw tiles, 3 CTAs/SM for ABC_SPLIT_DRAWS;
+ * otherwise pilot stride 16, factor 1.5) unless abc_set_default_tuning replaced it. */
 int abc_default_tuning(int32_t precision, abc_tuning* out);
 
 /* Replaces the process-wide default tuning for both precisions (NULL restores

@@ -109,7 +109,7 @@ struct Tuning {
 // ten times more C2 voxels fell back to the exact scan).
 Tuning default_tuning(int mode) {
     if (mode == ABC_SPLIT_DRAWS) return Tuning{64, 3, 16, 1.5f};
-    if (mode == ABC_FP32) return Tuning{128, 2, 16, 2.25f};
+    if (mode == ABC_FP32) return Tuning{128, 2, 8, 2.25f};
     return Tuning{128, 2, 16, 1.5f};
 }
 
