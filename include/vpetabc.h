@@ -50,27 +50,27 @@ extern "C" {
 #define ABC_LPNTPET 3
 
 /* Precision of the tensor-core discrepancy (Sec. II-C distance, Alg. 1 step 4).
- *  ABC_FP32:         operands split into bf16 hi+lo pairs (three bf16 products
- *                    per term, fp32 accumulate); each voxel keeps its 2k
- *                    nearest by that distance, re-scores them exactly in fp32,
- *                    and certifies from the product error bound that no other
- *                    draw can be nearer than the k-th; a voxel that cannot be
- *                    certified is resolved by an exact fp32 scan.  The accepted
- *                    set is the exact fp32 top-k.
- *  ABC_BF16_RESCORE: one bf16 product per term; each voxel keeps its 4k
- *                    nearest by the bf16 distance (and the few that share the
- *                    4k-th's bin of a 256-bin cut), which are re-scored exactly
- *                    in fp32 before the final k are chosen (certification is
- *                    reported, not enforced).
- *  ABC_SPLIT_DRAWS:  the draw operand split into bf16 hi + lo, the voxel
- *                    operand rounded once (two bf16 products per term, fp32
- *                    accumulate); each voxel keeps its 8k nearest, re-scores
- *                    them exactly in fp32, and certifies the result with a bound
- *                    that tracks the voxel row's rounding exactly (its common
- *                    part shifts every key of the voxel alike; the rest is at
- *                    most 2 ||delta|| sqrt(d)); an uncertified voxel is resolved
- *                    by an exact fp32 scan.  Like ABC_FP32, the accepted set is
- *                    the exact fp32 top-k. */
+ * Every form returns the exact fp32 top-k: the k draws of smallest fp32 re-scored
+ * distance, ties to the lower draw index.  They differ in how the tensor cores rank.
+ *  ABC_BF16_RESCORE: the fast form.  bf16 operands, fp32 accumulate: the voxel row
+ *                    rounded once, the draw row as bf16 hi + lo (two bf16 products
+ *                    per term) with its rounding residual folded into the draw's
+ *                    norm column, so that a key's error is at most
+ *                    2 sqrt(d) (||delta|| + 2^-16 ||x||) plus fp32 accumulation
+ *                    (delta = the voxel row's rounding).  The finest pilot pass sets
+ *                    each voxel's threshold from that bound and its rank-rk pilot key,
+ *                    so the candidate list (the net) holds every draw the certificate
+ *                    can need; the net is re-scored exactly in fp32, the k-th
+ *                    distance d_k found, and the result certified (no draw outside the
+ *                    net can have distance <= d_k).  An uncertified voxel is resolved by
+ *                    an exact fp32 scan of all draws (counted by abc_topk_status).
+ *  ABC_SPLIT_DRAWS:  the same computation as ABC_BF16_RESCORE (the name of the
+ *                    operand layout it uses).
+ *  ABC_FP32:         both operands split into bf16 hi + lo pairs (three bf16
+ *                    products per term); each voxel keeps its 2k nearest by that
+ *                    key, re-scores them exactly in fp32 and certifies from the
+ *                    product error bound; an uncertified voxel is resolved by an
+ *                    exact fp32 scan. */
 #define ABC_FP32 0
 #define ABC_BF16_RESCORE 1
 #define ABC_SPLIT_DRAWS 2
@@ -151,9 +151,10 @@ typedef struct {
 } abc_tuning;
 
 /* The tuning used for `precision` when none is passed: the built-in choice
- * (128-draw tiles, 2 CTAs/SM for ABC_BF16_RESCORE and ABC_FP32, the latter with
- * pilot stride 8 and factor 2.25; 64-draw tiles, 3 CTAs/SM for ABC_SPLIT_DRAWS;
- * otherwise pilot stride 16, factor 1.5) unless abc_set_default_tuning replaced it. */
+ * (128-draw tiles and 2 CTAs/SM, pilot stride 8 and factor 2.25 for ABC_FP32,
+ * pilot stride 16 and factor 1.5 otherwise; a single-scan call of the fast form
+ * with more than 30 frames, whose operands take two K-blocks, uses 64-draw tiles
+ * and 3 CTAs/SM) unless abc_set_default_tuning replaced it. */
 int abc_default_tuning(int32_t precision, abc_tuning* out);
 
 /* Replaces the process-wide default tuning for both precisions (NULL restores
@@ -210,10 +211,18 @@ int abc_batch_discrepancy_topk(const abc_scan* scans, int32_t n_scans, int32_t p
  *  - Every call shares the one array, which keeps the previous call's contents
  *    (the call clears what must start at zero).  Calls that overlap on the GPU
  *    (concurrent streams, or several host threads) race on it: serialise them.
- *  - abc_topk_status is not available for this variant. */
+ *  - Its status words (abc_topk_status's) live in that array: read them with
+ *    abc_topk_status_noalloc after the call, before trusting idx_dev / dist_dev
+ *    (a bounded device wait that ran out leaves them invalid). */
 int abc_discrepancy_topk_noalloc(const float* y_dev, int64_t J, int32_t ldy, const float* x_dev, int64_t N,
                                  int32_t ldx, int32_t L, const float* w_host, int32_t k, int32_t precision,
                                  int32_t* idx_dev, float* dist_dev, void* stream);
+
+/* Status of the last abc_discrepancy_topk_noalloc on the current device, in the
+ * layout of abc_topk_status (status_host[0] = ABC_OK or ABC_ERR_TIMEOUT, ...).
+ * Blocks on `stream`; like the call itself it allocates nothing.  ABC_ERR_ARG
+ * when no abc_discrepancy_topk_noalloc has run on this device yet. */
+int abc_topk_status_noalloc(int32_t status_host[8], void* stream);
 
 /* Status of the last abc_discrepancy_topk that used this workspace.  Blocks
  * on `stream`.  Writes
@@ -225,9 +234,9 @@ int abc_discrepancy_topk_noalloc(const float* y_dev, int64_t J, int32_t ldy, con
  *   status[2] = number of voxels with more candidates tied at the k-th
  *               distance than the final sort holds (the ties kept are then
  *               chosen by a selection on their draw indices: still the lowest);
- *   status[3] = ABC_BF16_RESCORE voxels whose accepted set could not be
- *               certified exact from the bf16 error bound (the 4k net may
- *               have missed a member of the exact top-k);
+ *   status[3] = ABC_BF16_RESCORE / ABC_SPLIT_DRAWS voxels whose pilot-sized net
+ *               could not be certified (resolved by the exact scan, also
+ *               counted in status[1]);
  *   status[4..7] = diagnostics: voxels whose candidate list overflowed, voxels
  *               left with fewer than k / fewer than the net size of candidates,
  *               and (voxel, pilot level) pairs left without a pilot threshold. */
@@ -250,6 +259,17 @@ int abc_topk_work(const void* workspace, int64_t out_host[2], void* stream);
  * time that kernel alone with cudaEventElapsedTime.  NULL, NULL turns it off.
  * Process-wide setting; the events stay owned by the caller. */
 int abc_profile_events(void* start_event, void* stop_event);
+
+/* Test hook for the bounded waits of the fused tensor-core kernel.  Every
+ * barrier wait of that kernel gives up after a time limit, flags
+ * ABC_ERR_TIMEOUT (abc_topk_status), waits (with the same limit) for the copies
+ * and MMAs its CTA has in flight, frees its tensor memory and returns, so the
+ * CUDA context stays usable.  This hook makes later calls exercise that path:
+ * with withheld_tile >= 0 the TMA producer of every CTA skips the load of its
+ * draw tile with that sequence number, so the waits behind it run out; wait_ns
+ * (1 ms .. 10 s, or 0 for the 2 s default) replaces the limit.  withheld_tile
+ * < 0 turns the stall off.  Process-wide; for tests only. */
+int abc_debug_inject_stall(int64_t withheld_tile, uint64_t wait_ns);
 
 /* Diagnostics: grid size of the last fused-kernel launch of this process, the
  * CTAs per SM its variant can keep resident (shared memory, registers and TMEM

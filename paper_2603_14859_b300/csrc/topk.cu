@@ -5,52 +5,43 @@
 // yh = sqrt(w)(y - mu), xh = sqrt(w)(x - mu) (mu = mean voxel TAC; distances
 // are translation invariant).  The ranking key d' = ||xh||^2 - 2 yh . xh is one
 // GEMM: voxel rows A = [yh .., 1, 1, 1], draw rows B = [-2 xh .., n_hi, n_mid, n_lo]
-// where n = ||xh||^2 is split over three bf16 columns.
+// where the norm column n is split over three bf16 columns.
 //   ABC_FP32:  yh, xh split into bf16 hi + lo; A = [yh_hi, yh_hi, yh_lo, 1,1,1],
 //              B = [-2xh_hi, -2xh_lo, -2xh_hi, n_hi, n_mid, n_lo]: three bf16
 //              products per term, |error| <= E(voxel) (bound below).
-//   ABC_BF16_RESCORE: one bf16 product per term.
-//   ABC_SPLIT_DRAWS: only xh split; A = [yh_bf, yh_bf, 1,1,1], B = [-2xh_hi,
-//              -2xh_lo, n_hi, n_mid, n_lo]: two products per term.  The key is
-//              then exact up to the voxel row's own rounding delta, whose
-//              effect c0 - 2 delta . (xh - yh) is a per-voxel constant plus a
-//              term bounded by 2 ||delta|| sqrt(d), which the certificate uses.
+//   split form (ABC_BF16_RESCORE, ABC_SPLIT_DRAWS): A = [yh_bf, yh_bf, 1,1,1],
+//              B = [-2xh_hi, -2xh_lo, n_hi, n_mid, n_lo] with n = ||xh||^2 - 2 xh.r
+//              (r = xh - xh_hi - xh_lo): two products per term.  The key is then
+//              exact up to c0 (a per-voxel constant) and 2 (yh - xh).(r + delta)
+//              (delta = the voxel row's rounding), which vanishes with the distance
+//              (need_key / dist_ub below).
 //
 // Kernel `k_tc_topk`: one CTA owns 128 voxels (one TMEM lane each) and streams
-// every draw tile of 128 rows through shared memory (TMA, 128-byte swizzle).
-// Warp roles: 0 = TMA producer, 1 = TMEM allocator + MMA issuer (one thread),
-// 2..5 = epilogue (thread <-> voxel).  Accumulators are double-buffered in TMEM
-// (2 x 128 fp32 columns) so MMA of tile t+1 overlaps the epilogue of tile t.
-// The epilogue reads 32 columns at a time and takes their minimum; a thread
-// whose minimum is within its voxel's running threshold stages the 32 keys in
-// shared memory, and the warp then appends each such voxel's passing
-// (key, draw index) pairs to that voxel's candidate list in global memory with
-// one coalesced store.  When a list could overflow, the warp compacts it
-// (radix select of the kt-th key, in-place filtering) and tightens the
-// threshold, so each list always holds every draw whose key is at most the
-// kt-th smallest seen (the "net": kt = 2k for ABC_FP32, 4k for ABC_BF16_RESCORE,
-// 8k for ABC_SPLIT_DRAWS, whose voxel-row rounding widens the certificate).
+// the draw tiles through shared memory (TMA, 128-byte swizzle).  Warp roles:
+// 0 = TMA producer, 1 = TMEM allocator + MMA issuer (one thread), 2.. = epilogue
+// (thread <-> voxel).  Accumulators are double-buffered in TMEM so the MMA of tile
+// t+1 overlaps the epilogue of tile t.  The epilogue reads 32 columns at a time and
+// takes their minimum; a thread whose minimum is within its voxel's threshold
+// appends each passing (key, draw index) pair to the voxel's candidate list.  When
+// a list could overflow, the warp compacts it (radix select of the kt-th key,
+// in-place filtering) and tightens the threshold, so a list always holds every draw
+// whose key is at most its voxel's threshold.
 //
 // Pilot passes of the same kernel over every 16th (then 256th, ...) draw (a
-// strided TMA tensor map) first find each voxel's r-th smallest key,
-// r = 1.5 kt / 16; as draws are i.i.d. within each model, about 1.5 kt of all N
-// draws fall below it, so the main pass starts from that threshold, appends
-// ~1.5 kt candidates per voxel and normally never compacts.  Each pilot starts
-// from the next coarser pilot's threshold in the same way.  Nothing relies on
-// the prediction for correctness: a list always holds every draw below its
-// voxel's threshold.
+// strided TMA tensor map) set each voxel's threshold for the next pass.  The
+// coarser levels aim at a rank (about 1.5 kt draws of the next finer level); the
+// finest level of the split form instead finds the key of rank rk (the k-th
+// distance's upper bound, four standard deviations safe) and k_need_threshold turns
+// it into need_key(dist_ub(key)): every draw the certificate below can ask for.
+// Nothing relies on the prediction for correctness.
 //
-// Kernel `k_finalize` (one warp per voxel; for ABC_BF16_RESCORE first cutting a
-// list to its kt smallest keys plus the rest of their bin of 256 equal-width
-// bins over the list's key range) re-scores the net exactly as
+// Kernel `k_finalize` (one warp per voxel) re-scores the net exactly as
 // sum_l w_l (y_l - x_l)^2 in fp32, selects the exact k-th distance d_k, and
-// certifies the result: with E bounding |computed d' - exact d'| for any draw
-// that could beat d_k (its ||xh|| <= ||yh|| + sqrt(d_k)), every draw outside
-// the net has computed key > T_out, so none can beat d_k when
-// T_out >= d_k - ||yh||^2 + E (for ABC_SPLIT_DRAWS: + c0 + 2 ||delta|| sqrt(d_k)).
-// ABC_FP32 and ABC_SPLIT_DRAWS resolve an uncertified voxel by an exact fp32
-// scan of all draws, which makes their accepted sets the exact fp32 top-k;
-// ABC_BF16_RESCORE counts uncertified voxels (abc_topk_status).
+// certifies the result: every draw outside the net has computed key > T_out, so
+// none can be within d_k when T_out >= the largest key a draw within d_k can have
+// (need_key for the split form; d_k - ||yh||^2 + E for ABC_FP32).  An uncertified
+// voxel is resolved by an exact fp32 scan of all draws, which makes every accepted
+// set the exact fp32 top-k.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -73,7 +64,7 @@ constexpr int A_KBLK_BYTES = BM * KBLK * 2;   // 16 KB
 // and keeping its own half of the voxel's candidate list).
 constexpr int tc_epi_warps(bool topr, int bn) { return (topr || bn == 64) ? 4 : 8; }
 constexpr int tc_threads(bool topr, int bn) { return 64 + 32 * tc_epi_warps(topr, bn); }
-constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any barrier wait
+constexpr uint64_t WAIT_NS_DEFAULT = 2000000000ull;   // 2 s bound on any barrier wait
 constexpr int MAXL = 64;
 constexpr int ORDER_BITS = 10;                 // bits per ordering feature (30-bit Morton key)
 constexpr int ORDER_BUCKET_BITS = 18;
@@ -108,17 +99,28 @@ struct Tuning {
 // it stands, whose threshold must clear the certificate's error margin (at 1.5 kt
 // ten times more C2 voxels fell back to the exact scan).
 Tuning default_tuning(int mode) {
-    if (mode == ABC_SPLIT_DRAWS) return Tuning{64, 3, 16, 1.5f};
     if (mode == ABC_FP32) return Tuning{128, 2, 8, 2.25f};
     return Tuning{128, 2, 16, 1.5f};
 }
 
+// The built-in tuning for a shape: the split form's operands take two K-blocks past 30
+// frames, where 128-draw tiles would leave one CTA per SM; there it runs 64-draw tiles.
+Tuning default_tuning_for_shape(int mode, int L) {
+    Tuning t = default_tuning(mode);
+    if (mode != ABC_FP32 && 2 * L + 3 > KBLK) {
+        t.bn = 64;
+        t.ctas_per_sm = 3;
+    }
+    return t;
+}
+
 // bf16 columns of the packed operands per frame: products per term of the key.
-__host__ __device__ inline int cols_per_frame(int mode) { return mode == ABC_FP32 ? 3 : (mode == ABC_SPLIT_DRAWS ? 2 : 1); }
+__host__ __device__ inline int cols_per_frame(int mode) { return mode == ABC_FP32 ? 3 : 2; }
 
 struct Layout {
-    int mode;          // ABC_FP32 / ABC_BF16_RESCORE / ABC_SPLIT_DRAWS
+    int mode;          // ABC_FP32 or ABC_SPLIT_DRAWS (ABC_BF16_RESCORE runs as the latter)
     int L, k, Kp, nkb, C, kt, cap, sortcap;
+    int rk;                            // split form: rank of the k-th-distance bound in the finest pilot
     int nlev;                          // pilot levels (finest first)
     int lev_rank[MAX_PILOT_LEVELS];
     int64_t lev_stride[MAX_PILOT_LEVELS];
@@ -153,9 +155,26 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.Kp = (int)vpet_round_up(kcols, KBLK);
     if (s.Kp < kp_min) s.Kp = kp_min;
     s.nkb = s.Kp / KBLK;
-    const int64_t net = (int64_t)(mode == ABC_FP32 ? 2 : (mode == ABC_SPLIT_DRAWS ? 8 : 4)) * k;
+    // kt: the net of the FP32 form and the compaction target of every form (2k).  The
+    // split form's lists instead hold every draw below a per-voxel threshold that the
+    // finest pilot derives from the certificate's own bound (need_key), up to the
+    // capacity C below.
+    const int64_t net = 2 * (int64_t)k;
     s.kt = (int)(net < N ? net : N);
     s.cap = s.kt + (s.kt / 4 > 64 ? s.kt / 4 : 64);
+    // rank, in the finest pilot sample, of the key whose distance bounds the k-th
+    // distance from above unless the sample under-represents the draws below it by
+    // more than four standard deviations (split form only)
+    s.rk = 0;
+    if (mode != ABC_FP32) {
+        const double sd = tu.pilot_stride;
+        int64_t r = (int64_t)ceil((double)k / sd);
+        for (int it = 0; it < 200; ++it) {
+            if (1.0 - (double)k / (sd * (double)r) >= 4.0 / sqrt((double)r)) break;
+            r = r + r / 8 + 1;
+        }
+        s.rk = (int)r;
+    }
     // Pilot levels: level i uses every stride^i-th draw and a target rank
     // r_i = ceil(f r_{i-1} / stride), r_0 = kt, so that about f r_{i-1} draws of
     // the next finer level fall below its threshold.  For a small r_i the rank
@@ -171,6 +190,7 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
             if (1.0 - 1.0 / f >= 4.0 / sqrt((double)r_next)) break;
             r_next = r_next + r_next / 8 + 1;
         }
+        if (s.nlev == 0 && r_next < s.rk) r_next = s.rk;    // the finest pilot list must hold rank rk
         const int64_t n_next = N / (stride * tu.pilot_stride);
         if (n_next < 8 * r_next || n_next < 512) break;
         stride *= tu.pilot_stride;
@@ -179,7 +199,10 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
         s.lev_stride[s.nlev] = stride;
         s.nlev++;
     }
-    s.C = (int)vpet_round_up(3 * (int64_t)s.kt + 256, 32);
+    // list capacity: the FP32 form's net is the list as it stands (~2.25 kt); a split-form
+    // list holds its voxel's need-sized net, at most 12 k (the certificate's nets measured on
+    // the brain and total-body workloads stay below 12 k; a voxel past it takes the exact scan)
+    s.C = (int)vpet_round_up(mode == ABC_FP32 ? 3 * (int64_t)s.kt + 256 : 12 * (int64_t)k + 256, 32);
     s.sortcap = next_pow2(k + 8);     // k plus a few ties at the k-th distance
     if (s.sortcap < 64) s.sortcap = 64;
     s.Jp = vpet_round_up(J > 0 ? J : 1, BM);
@@ -216,6 +239,51 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.off_xs = o; o = align256(o + (size_t)s.Np * s.ldxs * sizeof(float));
     s.total = o;
     return s;
+}
+
+// ------------------------------------------------------------------ split-form key bounds
+// The split form's key of voxel row a (yh, fp32) and draw row b (xh, fp32): the voxel row
+// rounded once to bf16, a' = a + da; the draw row as bf16 hi + lo with residual
+// r = b - hi - lo (|r_l| <= 2^-16 |b_l|); the draw's norm column N = ||b||^2 - 2 b.r.
+// The MMA computes key = N - 2 a'.(hi + lo), which is exactly
+//   key = ||a - b||^2 - ||a||^2 + c0 + 2 (a - b).(r + da) + 2 da.r      (c0 = -2 da.a)
+// plus its fp32 accumulation.  The variable part is at most 2 ||a - b|| (||r|| + ||da||):
+// it scales with the square root of the distance, so nearby draws are ranked almost
+// exactly.  need_key and dist_ub turn that into two bounds, used by the certificate,
+// the per-voxel pilot threshold and the tile bound.
+struct SplitCoef {
+    float cacc;    // fp32 accumulation of the MMA over Kp columns and the split norm: (3 Kp + L + 16) 2^-24
+    float slack;   // fp32 sums of the re-score and of ||yh||^2: 4 L 2^-24
+};
+
+// The largest computed key a draw can have if its distance to the voxel (as the exact
+// fp32 re-score computes it) is at most D.  yn = ||yh||^2, c0, dn = ||da|| of the voxel row.
+__host__ __device__ __forceinline__ float need_key(float D, float yn, float c0, float dn, const SplitCoef& c) {
+    const float ry = sqrtf(fmaxf(yn, 0.0f));
+    const float s = sqrtf(fmaxf(D, 0.0f) * (1.0f + c.slack)) * (1.0f + 0x1p-20f);   // bounds the real distance's root
+    const float sp = s + 0x1p-21f * (2.0f * ry + s);       // ||a - b||: fp32 centring and scaling of both rows
+    const float R = ry + sp;                                 // >= ||b||
+    const float e1 = dn * (1.0f + 0x1p-10f) + 0x1p-16f * R;   // >= ||da|| + ||r||
+    const float t = sp * sp - yn * (1.0f - c.slack) + c0 + 2.0f * sp * e1 + 0x1p-15f * dn * (ry + R) +
+                    c.cacc * (2.0f * ry * R + R * R);
+    return t + 0x1p-20f * (yn + sp * sp + fabsf(c0));
+}
+
+// An upper bound on the exact distance of any draw whose computed key is at most T:
+// key >= q^2 - ||a||^2 + c0 - 2 q e1 - (rest) with q = ||a - b||, solved for q.
+__host__ __device__ __forceinline__ float dist_ub(float T, float yn, float c0, float dn, const SplitCoef& c) {
+    if (!(T < 1.0e30f)) return 3.0e38f;
+    const float ry = sqrtf(fmaxf(yn, 0.0f));
+    const float dnp = dn * (1.0f + 0x1p-10f);
+    const float A = 1.0f - 0x1p-15f - c.cacc;
+    const float B = 2.0f * dnp + 0x1p-15f * (ry + dn) + 4.0f * c.cacc * ry;
+    const float C = T + yn * (1.0f + c.slack) - c0 + 0x1p-14f * dn * ry + 3.0f * c.cacc * yn +
+                    0x1p-20f * (yn + fabsf(T) + fabsf(c0));
+    const float disc = B * B + 4.0f * A * C;
+    if (!(disc >= 0.0f)) return 0.0f;                        // no draw has such a key
+    const float q = fmaxf((B + sqrtf(disc)) / (2.0f * A), 0.0f);
+    const float sq = q + 0x1p-21f * (2.0f * ry + q);         // back to the exact rows
+    return sq * sq * (1.0f + c.slack) * (1.0f + 0x1p-20f);
 }
 
 // ------------------------------------------------------------------ packing
@@ -489,16 +557,13 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
             } else if (e < 3 * L + 3) {
                 out = 1.0f;
             }
-        } else if (mode == ABC_SPLIT_DRAWS) {
+        } else {
             if (e < 2 * L) {
                 const int l = e % L;
                 out = F.sw[l] * (yr[l] - F.mu[l]);              // the same bf16 row against x_hi and x_lo
             } else if (e < 2 * L + 3) {
                 out = 1.0f;
             }
-        } else {
-            if (e < L) out = F.sw[e] * (yr[e] - F.mu[e]);
-            else if (e < L + 3) out = 1.0f;
         }
         row[e] = bf(out);
     }
@@ -560,13 +625,20 @@ __global__ void __launch_bounds__(256) k_pack_x(const float* __restrict__ x, int
                 fx[3 * n + 2] = f[2];
             }
         }
-        float ss = 0.0f;
+        float ss = 0.0f, sr = 0.0f;
         for (int l = lane; l < L; l += 32) {
-            float v = F.sw[l] * (xr[l] - F.mu[l]);
-            if (mode == ABC_BF16_RESCORE) v = __bfloat162float(bf(v));   // norm of the rounded vector
+            const float v = F.sw[l] * (xr[l] - F.mu[l]);
             ss = fmaf(v, v, ss);
+            if (mode != ABC_FP32) {
+                // the residual of the hi + lo split, r = v - hi - lo (exact in fp32)
+                const float h = __bfloat162float(bf(v)), d1 = v - h;
+                sr = fmaf(v, d1 - __bfloat162float(bf(d1)), sr);
+            }
         }
         ss = warp_sum(ss);
+        // split form: the norm column carries ||b||^2 - 2 b.r, so that the key's error from the
+        // draw row's split is 2 (a - b).r, which vanishes with the distance
+        if (mode != ABC_FP32) ss -= 2.0f * warp_sum(sr);
         const float n1 = __bfloat162float(bf(ss));
         const float r1 = ss - n1;
         const float n2 = __bfloat162float(bf(r1));
@@ -579,8 +651,7 @@ __global__ void __launch_bounds__(256) k_pack_x(const float* __restrict__ x, int
                 const float v = F.sw[l] * (xr[l] - F.mu[l]);
                 const float hi = __bfloat162float(bf(v));
                 if (mode == ABC_FP32) out = -2.0f * ((e >= L && e < 2 * L) ? (v - hi) : hi);
-                else if (mode == ABC_SPLIT_DRAWS) out = -2.0f * (e >= L ? (v - hi) : hi);
-                else out = -2.0f * hi;
+                else out = -2.0f * (e >= L ? (v - hi) : hi);
             } else if (e == aug) {
                 out = n1;
             } else if (e == aug + 1) {
@@ -644,7 +715,11 @@ struct KeepArgs {
     unsigned long long* tally;   // [0] += kept, [1] += all (diagnostics)
     int64_t J, N, nt64;
     float Wc[3];                 // segment weight sums
-    float cE;                    // error coefficient of the keys (0: the key threshold is used as is)
+    float cE;                    // ABC_FP32: error coefficient of the keys
+    int split;                   // split form: thresholds become distances by dist_ub
+    SplitCoef sc;
+    const float* c0;             // split form: per packed row
+    const float* dn;
     int bn;                      // draw-tile width of the pass, 64 or 128
 };
 
@@ -663,11 +738,17 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
         if (j < K.J) {
             const float t = K.thr0[j];
             const float yn = K.ynorm[j];
-            float td = t + yn;
-            if (K.cE > 0.0f && td < 1.0e30f) {
-                const float ry = sqrtf(fmaxf(yn, 0.0f));
-                const float R = ry + sqrtf(fmaxf(td, 0.0f));
-                td += K.cE * (2.0f * ry * R + R * R);
+            float td;
+            if (K.split) {
+                // every draw whose key can pass t lies within this distance
+                td = dist_ub(t, yn, K.c0[j], K.dn[j], K.sc);
+            } else {
+                td = t + yn;
+                if (td < 1.0e30f) {
+                    const float ry = sqrtf(fmaxf(yn, 0.0f));
+                    const float R = ry + sqrtf(fmaxf(td, 0.0f));
+                    td += K.cE * (2.0f * ry * R + R * R);
+                }
             }
             td = td >= 1.0e30f ? 3.0e38f : td * (1.0f + 0x1p-10f) + 1e-30f;
 #pragma unroll
@@ -754,6 +835,7 @@ struct __align__(64) ItemTc {
     int lim0;                    // ... or lim0 entries while its voxel has no finite threshold yet
     int rsel;                    // > 0: pilot that keeps the rsel smallest keys per voxel, no lists
     int hstride;                 // cnt[] / thr[] entry of half 1 of voxel j: j + hstride
+    int rk;                      // top-r pilot > 0: write the rk-th smallest key (exact) instead of the r-th
     const int32_t* ktile;        // kept draw tiles per voxel tile (null: every tile)
     const int32_t* kcount;
     int64_t kstride;
@@ -769,6 +851,9 @@ struct BatchTc {
     int32_t* status;
     float* dump;                 // debug probe: raw keys, Jp x Np (null in production)
     int64_t ld_dump;
+    uint64_t wait_ns;            // bound on every barrier wait (2 s unless a test shortens it)
+    int64_t withhold;            // test hook: the TMA producer never loads its draw tile of this
+                                 // sequence number (< 0: off), so the waits behind it run out
 };
 
 __device__ __forceinline__ int item_of(const BatchTc& P, int64_t w) {
@@ -918,6 +1003,22 @@ __device__ __forceinline__ void topr_chunk(TopR& S, float (&v)[32], int64_t n0, 
     }
 }
 
+// The rk-th smallest (1-based) of the n keys col[i * 128], i < n (rk <= n).
+__device__ __forceinline__ float kth_of_column(const float* col, int n, int rk) {
+    float out = 3.0e38f;
+    for (int i = 0; i < n; ++i) {
+        const float v = col[i * 128];
+        int lt = 0, eq = 0;
+        for (int q = 0; q < n; ++q) {
+            const float u = col[q * 128];
+            lt += u < v;
+            eq += u == v;
+        }
+        if (lt < rk && rk <= lt + eq) out = v;
+    }
+    return out;
+}
+
 // Persistent fused kernel over the (scan, 128-voxel tile) work items of a batch,
 // handed out round-robin in the order of the work index space (costliest
 // scans first).  All roles walk the same sequence; the shared-memory ring and
@@ -946,9 +1047,11 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
     volatile long long* slot = (volatile long long*)(bars + 2 * STAGES + 10);   // [2]
     uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 12);
     volatile int* s_err = (volatile int*)(tmem_holder + 1);
+    uint64_t* drain = bars + 2 * STAGES + 13;   // MMA thread: all of its MMAs complete
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t total = P.vt_prefix[P.n_items];
+    const uint64_t WAIT_NS = P.wait_ns;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -961,6 +1064,7 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
         }
         ptx::mbar_init(ptx::smem_u32(afull), 1);
         ptx::mbar_init(ptx::smem_u32(aempty), 1);
+        ptx::mbar_init(ptx::smem_u32(drain), 1);
         for (int a = 0; a < 2; ++a) {
             ptx::mbar_init(ptx::smem_u32(&ifull[a]), 1);
             ptx::mbar_init(ptx::smem_u32(&iempty[a]), 1 + EPI);   // MMA thread + the epilogue warps
@@ -981,6 +1085,10 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
         // ---------------- TMA producer
         if (lane == 0) {
             uint32_t gt = 0;
+            // loads this thread issued and has not seen land: per ring stage the parity of the
+            // phase it last loaded, and the A tile's; waited for before the CTA exits, so no
+            // copy into this CTA's shared memory is still in flight after a bounded wait ran out
+            uint32_t st_issued = 0, st_parity = 0, a_issued = 0, a_parity = 0;
             for (uint32_t ic = 0;; ++ic) {
                 // take the next work item and post it to the other roles
                 long long w = (long long)atomicAdd(P.counter, 1ull);
@@ -1004,18 +1112,27 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                 ptx::mbar_arrive_expect_tx(ab, NKB * A_KBLK_BYTES);
                 for (int kb = 0; kb < NKB; ++kb)
                     ptx::tma_load_2d(ptx::smem_u32(sA + kb * A_KBLK_BYTES), &I.tmA, ab, kb * KBLK, (int32_t)m0);
+                a_issued = 1;
+                a_parity = ic & 1u;
                 for (int t = 0; t < ntiles; ++t, ++gt) {
                     const uint32_t s = gt % STAGES;
                     const uint32_t ph = (gt / STAGES) & 1u;
                     if (!ptx::mbar_wait(ptx::smem_u32(&empty[s]), ph ^ 1u, WAIT_NS)) { *s_err = 1; break; }
                     if (*s_err) break;
+                    if ((int64_t)gt == P.withhold) continue;   // test hook: this stage never fills
                     const uint32_t fb = ptx::smem_u32(&full[s]);
                     ptx::mbar_arrive_expect_tx(fb, NKB * B_KBLK_BYTES);
                     for (int kb = 0; kb < NKB; ++kb)
                         ptx::tma_load_2d(ptx::smem_u32(sB + (s * NKB + kb) * B_KBLK_BYTES), &I.tmB, fb, kb * KBLK,
                                          (kt_list ? kt_list[t] : t) * BN);
+                    st_issued |= 1u << s;
+                    st_parity = (st_parity & ~(1u << s)) | (ph << s);
                 }
             }
+            for (int s = 0; s < STAGES; ++s)
+                if ((st_issued >> s) & 1u)
+                    if (!ptx::mbar_wait(ptx::smem_u32(&full[s]), (st_parity >> s) & 1u, WAIT_NS)) *s_err = 1;
+            if (a_issued && !ptx::mbar_wait(ptx::smem_u32(afull), a_parity, WAIT_NS)) *s_err = 1;
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer (single thread)
@@ -1039,6 +1156,7 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                     const uint32_t ph = (gt / STAGES) & 1u;
                     const uint32_t acc = gt & 1u;
                     const uint32_t aph = (gt >> 1) & 1u;
+                    if (*s_err) break;
                     if (!ptx::mbar_wait(ptx::smem_u32(&tempty[acc]), aph ^ 1u, WAIT_NS) ||
                         !ptx::mbar_wait(ptx::smem_u32(&full[s]), ph, WAIT_NS)) {
                         *s_err = 1;
@@ -1062,6 +1180,10 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                 }
                 ptx::mma_commit(ptx::smem_u32(aempty));   // A tile free once these MMAs complete
             }
+            // every MMA this thread issued has completed before TMEM is freed, also when a
+            // bounded wait ran out and no epilogue waited for the last accumulators
+            ptx::mma_commit(ptx::smem_u32(drain));
+            if (!ptx::mbar_wait(ptx::smem_u32(drain), 0u, WAIT_NS)) *s_err = 1;
         }
     } else {
         // ---------------- epilogue: warps 2 .. 2 + EPI - 1, thread <-> voxel
@@ -1102,6 +1224,7 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                 if (kt_list && t + 1 < ntiles) tnext = kt_list[t + 1];
                 const uint32_t acc = gt & 1u;
                 const uint32_t aph = (gt >> 1) & 1u;
+                if (__any_sync(0xFFFFFFFFu, *s_err != 0)) { stop = true; break; }
                 if (!ptx::mbar_wait(ptx::smem_u32(&tfull[acc]), aph, WAIT_NS)) { *s_err = 1; }
                 if (__any_sync(0xFFFFFFFFu, *s_err != 0)) { stop = true; break; }
                 ptx::tc_fence_after();
@@ -1154,8 +1277,10 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
             if (valid && !DUMP && !stop) {
                 if (TOPR) {
                     // the r-th smallest key, rounded up to its 24-bit prefix (as the list
-                    // pilots' three-digit selection gives it), or none
-                    const float t = S.n_in == S.r ? key2f(f2key(S.amax) | 0xFFu) : 3.0e38f;
+                    // pilots' three-digit selection gives it), or none; a finest split-form
+                    // pilot writes its rk-th smallest key (turned into a need threshold next)
+                    const float t = I.rk > 0 ? (S.n_in >= I.rk ? kth_of_column(S.A, S.n_in, I.rk) : 3.0e38f)
+                                             : (S.n_in == S.r ? key2f(f2key(S.amax) | 0xFFu) : 3.0e38f);
                     I.thr_out[j] = t;
                     if (t >= 3.0e38f) atomicAdd(&P.status[7], 1);
                 } else {
@@ -1245,19 +1370,50 @@ __global__ void k_pilot_threshold(const __grid_constant__ BatchPilot B) {
     }
 }
 
+// Split form, after the finest pilot: the pilot key K of rank rk bounds the voxel's k-th
+// distance by D = dist_ub(K) (unless the sample misled by four standard deviations), so the
+// main pass keeps every draw with key <= need_key(D): all the certificate can ask for.
+struct NeedItem {
+    float* thr0;
+    const float* ynorm;
+    const float* c0;
+    const float* dn;
+    int64_t J;
+    SplitCoef sc;
+};
+
+struct BatchNeed {
+    NeedItem item[MAX_ITEMS];
+    int64_t v_prefix[MAX_ITEMS + 1];
+    int n_items;
+};
+
+__global__ void k_need_threshold(const __grid_constant__ BatchNeed B) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= B.v_prefix[B.n_items]) return;
+    int it = 0;
+    while (it + 1 < B.n_items && g >= B.v_prefix[it + 1]) ++it;
+    const NeedItem& I = B.item[it];
+    const int64_t j = g - B.v_prefix[it];
+    const float K = I.thr0[j];
+    if (!(K < 1.0e30f)) return;          // no pilot threshold: the main pass starts without one
+    const float yn = I.ynorm[j], c0 = I.c0[j], dn = I.dn[j];
+    I.thr0[j] = need_key(dist_ub(K, yn, c0, dn, I.sc), yn, c0, dn, I.sc);
+}
+
 // ------------------------------------------------------------------ finalize
 struct FinItem {
     int64_t J, N;
     int L, k, C, kt, mode, sortcap;
     int C2;                      // the list row's two half-lists start at 0 and C2
     int64_t hstride;             // cnt[] / thr[] of half 1: row + hstride
-    float cE;
+    float cacc;                  // (3 Kp + L + 16) 2^-24: the keys' fp32 accumulation (both certificates)
     int ldy, ldx;
     const float* y;
     const float* x;
     const float* ynorm;
-    const float* c0;             // ABC_SPLIT_DRAWS: -2 delta . yh per voxel
-    const float* dn;             // ABC_SPLIT_DRAWS: ||delta|| per voxel
+    const float* c0;             // split form: -2 delta . yh per list row
+    const float* dn;             // split form: ||delta|| per list row
     const int32_t* perm;         // list row -> voxel (null: identity)
     const int32_t* xperm;        // packed draw row -> draw (null: identity)
     const float* xs;             // draws in packed order, fp32 (row stride ldxs)
@@ -1405,10 +1561,8 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
     const int raw = raw0 | raw1;                          // an overflow flag from either half
     const int c0h = raw0 & 0x3FFFFFFF, c1h = raw1 & 0x3FFFFFFF;
     int cnt = c0h + c1h;
-    // one contiguous list: the BF16 net cut below reads both half-lists and writes the net in
-    // front; everything else joins them first
-    const bool cut_joins = P.mode != ABC_FP32 && cnt > P.kt;
-    if (!(raw & 0x40000000) && !cut_joins) merge_halves(kj, ij, P.C2, c0h, c1h, lane);
+    // one contiguous list
+    if (!(raw & 0x40000000)) merge_halves(kj, ij, P.C2, c0h, c1h, lane);
     for (int l = lane; l < P.L; l += 32) {
         ys[l] = P.y[vox * P.ldy + l];
         ws[l] = P.w[l];
@@ -1427,15 +1581,9 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
     int n_less = -1, n_eq = -1;                   // keys below / at K (-1: not counted yet)
     float dbound = __int_as_float(0x7F800000);   // exact k-th distance of the net: bounds the true one
     if (!scan) {
-        // 1. the net: every draw outside it has computed key > T_out
-        float T_out = fminf(P.thr[j], P.thr[j + P.hstride]);   // both halves dropped only keys above theirs
-        if (P.mode != ABC_FP32 && cnt > P.kt) {
-            // the net: the kt smallest keys and the rest of their linear bin (a few more)
-            const LinearCut cut = warp_cut_linear(kj, cnt, P.kt - 1, hist, lane, c0h, P.C2);
-            float kmax;
-            cnt = warp_compact_cut(kj, ij, cnt, cut, lane, kmax, c0h, P.C2);
-            T_out = kmax;
-        }
+        // 1. the net is the whole list: every draw outside it has computed key > T_out
+        // (both halves dropped only keys above their own thresholds)
+        const float T_out = fminf(P.thr[j], P.thr[j + P.hstride]);
         // 2. exact fp32 re-score of the net (list entries are packed draw rows, read from the
         // packed fp32 copy): G lanes per row, four rows per group in flight
         constexpr int NR = 4;
@@ -1523,21 +1671,21 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
             const float dk = key2f(K);
             dbound = dk;
             const float yn = P.ynorm[j];
+            float need;
             const float slack = 4.0f * (float)P.L * 0x1p-24f;
-            const float ry = sqrtf(yn);
-            const float R = ry + sqrtf(dk * (1.0f + slack)) + 1e-30f;
-            float need = dk * (1.0f + slack) - yn * (1.0f - slack) + err_bound(P.cE, ry, R);
-            if (P.mode == ABC_SPLIT_DRAWS) {
-                // the voxel row was rounded once: key - d' = c0 - 2 delta . (xh - yh) + (bounded above),
-                // |2 delta . (xh - yh)| <= 2 ||delta|| sqrt(d) <= 2 ||delta|| sqrt(d_k) for the k nearest
-                const float c0 = P.c0[j], dd = P.dn[j] * (1.0f + 0x1p-10f);
-                need += c0 + 2.0f * dd * sqrtf(dk * (1.0f + slack)) + fabsf(c0) * 0x1p-16f;
+            if (P.mode == ABC_FP32) {
+                const float ry = sqrtf(yn);
+                const float R = ry + sqrtf(dk * (1.0f + slack)) + 1e-30f;
+                need = dk * (1.0f + slack) - yn * (1.0f - slack) + err_bound(3.0f * 0x1p-16f + P.cacc, ry, R);
+            } else {
+                // every draw at exact distance <= d_k has key <= need_key(d_k)
+                need = need_key(dk, yn, P.c0[j], P.dn[j], SplitCoef{P.cacc, slack});
             }
             cert = T_out >= 2.9e38f || T_out >= need;
         }
         if (!cert) {
-            if (P.mode != ABC_BF16_RESCORE || cnt < P.k) scan = true;
-            else if (lane == 0) atomicAdd(&B.status[3], 1);
+            scan = true;
+            if (P.mode != ABC_FP32 && lane == 0) atomicAdd(&B.status[3], 1);
         }
     }
     if (scan) {
@@ -1641,6 +1789,10 @@ static_assert(sizeof(BatchPilot) <= 32000, "BatchPilot exceeds the kernel parame
 
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+// Test hook (abc_debug_inject_stall): bound on the fused kernel's barrier waits and
+// the draw-tile sequence number its TMA producers withhold (-1: none).
+uint64_t g_wait_ns = WAIT_NS_DEFAULT;
+int64_t g_withhold = -1;
 cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
 int g_last_resident = 0;     // residency of the last configured fused-kernel variant
 int64_t g_last_grid = 0;     // grid of the last fused-kernel launch
@@ -1715,8 +1867,14 @@ template <int NKB, int BN, bool DUMP, bool TOPR>
 int launch_tc(const BatchTc& P, int ctas_per_sm, cudaStream_t s) {
     constexpr int S = stages_for(NKB, BN);
     const size_t smem = tc_smem_bytes(NKB, BN, TOPR);
-    static bool configured = false;
-    static int max_resident = 1;
+    // kernel attributes are per device: configured once for each device that launches
+    static bool configured_dev[64] = {};
+    static int max_resident_dev[64] = {};
+    int cur = 0;
+    VPET_CUDA(cudaGetDevice(&cur));
+    VPET_ARG(cur >= 0 && cur < 64, "device ordinal %d out of range", cur);
+    bool& configured = configured_dev[cur];
+    int& max_resident = max_resident_dev[cur];
     if (!configured) {
         VPET_CUDA(cudaFuncSetAttribute(k_tc_topk<NKB, S, BN, DUMP, TOPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         // all of the unified L1 / shared storage as shared memory, so that the
@@ -1772,17 +1930,16 @@ int dispatch_tc(int nkb, int bn, const BatchTc& P, int ctas_per_sm, cudaStream_t
 }
 
 float error_coef(const Layout& lay) {
-    // |d' error| <= cE (2 ||yh|| R + R^2) for a draw with ||xh|| <= R.
-    //  ABC_FP32: bf16 hi + lo of each operand leaves |a - a_hi - a_lo| <= 2^-16 |a|,
-    //   |a_lo| <= 2^-8 |a|, so the three products miss at most 3 * 2^-16 |a b|;
-    //  ABC_BF16_RESCORE: one rounding of each operand and of the norm, 2^-8 each.
-    // Both add fp32 accumulation over Kp terms, the fp32 norm and the fp32
-    // centring / scaling of the operands.
-    //  ABC_SPLIT_DRAWS: the draw operand as hi + lo (2^-16 |x| left); the voxel
-    //   row's single rounding is handled exactly by the certificate (c0, dn).
-    const float split = lay.mode == ABC_FP32 ? 3.0f * 0x1p-16f
-                                            : (lay.mode == ABC_SPLIT_DRAWS ? 3.0f * 0x1p-16f : 3.0f * 0x1p-8f);
-    return split + (float)(3 * lay.Kp + lay.L + 16) * 0x1p-24f;
+    // ABC_FP32: |d' error| <= cE (2 ||yh|| R + R^2) for a draw with ||xh|| <= R.  bf16
+    // hi + lo of each operand leaves |a - a_hi - a_lo| <= 2^-16 |a|, |a_lo| <= 2^-8 |a|, so the
+    // three products miss at most 3 * 2^-16 |a b|; plus fp32 accumulation over Kp terms, the
+    // fp32 norm and the fp32 centring / scaling of the operands.
+    return 3.0f * 0x1p-16f + (float)(3 * lay.Kp + lay.L + 16) * 0x1p-24f;
+}
+
+// Split form: the coefficients of need_key / dist_ub.
+SplitCoef split_coef(const Layout& lay) {
+    return SplitCoef{(float)(3 * lay.Kp + lay.L + 16) * 0x1p-24f, 4.0f * (float)lay.L * 0x1p-24f};
 }
 
 // One scan of a batch as the host sees it.
@@ -2066,7 +2223,11 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         K.N = npass;
         K.nt64 = L.nt64;
         for (int l = 0; l < L.L; ++l) K.Wc[(3 * l) / L.L] += sc[i].w[l];
-        K.cE = mode == ABC_BF16_RESCORE ? 0.0f : error_coef(L);
+        K.cE = error_coef(L);
+        K.split = mode != ABC_FP32;
+        K.sc = split_coef(L);
+        K.c0 = ptr[i].c0;
+        K.dn = ptr[i].dn;
         K.bn = tu.bn;
         k_keep_tiles<<<(unsigned)L.nvt, 256, 0, s>>>(K);
         VPET_LAUNCH_CHECK();
@@ -2100,13 +2261,17 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
                 T.item[m].kstride = L.nt64;
             }
             T.vt_prefix[m + 1] = T.vt_prefix[m] + L.Jp / BM;
+            // the finest split-form pilot reports its rank-rk key, which k_need_threshold turns
+            // into the voxel's need threshold for the main pass
+            const int rsel = (lv == 0 && L.rk > 0) ? L.rk : r;
             if (lev_topr) {
                 // small rank: the kernel keeps each voxel's r smallest keys itself and
                 // writes the threshold; no lists, no selection pass
                 T.item[m].rsel = r;
+                T.item[m].rk = lv == 0 ? L.rk : 0;
                 T.item[m].thr_out = ptr[i].thr0;
             } else {
-                PB.item[mp] = PilotItem{ptr[i].keys, ptr[i].cnt, ptr[i].thr0, L.J, L.C, r, tu.bn == 128 ? L.C / 2 : L.C, L.Jp};
+                PB.item[mp] = PilotItem{ptr[i].keys, ptr[i].cnt, ptr[i].thr0, L.J, L.C, rsel, tu.bn == 128 ? L.C / 2 : L.C, L.Jp};
                 PB.v_prefix[mp + 1] = PB.v_prefix[mp] + L.J;
                 ++mp;
             }
@@ -2115,12 +2280,31 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         T.n_items = m;
         T.status = status;
         T.counter = counters + (lv + 1);
+        T.wait_ns = g_wait_ns;
+        T.withhold = g_withhold;
         PB.n_items = mp;
         PB.status = status;
         if ((rc = dispatch_tc<false>(nkb, tu.bn, T, tu.ctas_per_sm, s, lev_topr))) return rc;
         if (mp > 0) {
             k_pilot_threshold<<<(unsigned)vpet_ceil_div(PB.v_prefix[mp], 8), 256, 0, s>>>(PB);
             VPET_LAUNCH_CHECK();
+        }
+        if (lv == 0 && mode != ABC_FP32) {
+            BatchNeed NB;
+            memset(&NB, 0, sizeof NB);
+            int mn = 0;
+            for (int i = 0; i < n; ++i) {
+                const Layout& L = BL.lay[i];
+                if (L.nlev <= 0) continue;
+                NB.item[mn] = NeedItem{ptr[i].thr0, ptr[i].ynorm, ptr[i].c0, ptr[i].dn, L.J, split_coef(L)};
+                NB.v_prefix[mn + 1] = NB.v_prefix[mn] + L.J;
+                ++mn;
+            }
+            NB.n_items = mn;
+            if (mn > 0) {
+                k_need_threshold<<<(unsigned)vpet_ceil_div(NB.v_prefix[mn], 256), 256, 0, s>>>(NB);
+                VPET_LAUNCH_CHECK();
+            }
         }
     }
     // draw tiles the main pass can skip (needs the pilot thresholds and the ordered draws)
@@ -2149,6 +2333,8 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     T.counter = counters;
     T.dump = dump;
     T.ld_dump = ld_dump;
+    T.wait_ns = g_wait_ns;
+    T.withhold = g_withhold;
     if (dump) return dispatch_tc<true>(nkb, 128, T, tu.ctas_per_sm, s);
     if (g_prof_start) VPET_CUDA(record_event(g_prof_start, s));
     if ((rc = dispatch_tc<false>(nkb, tu.bn, T, tu.ctas_per_sm, s))) return rc;
@@ -2169,7 +2355,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         f.kt = L.kt;
         f.mode = mode;
         f.sortcap = L.sortcap;
-        f.cE = error_coef(L);
+        f.cacc = split_coef(L).cacc;
         f.y = sc[i].y;
         f.ldy = sc[i].ldy;
         f.x = sc[i].x;
@@ -2201,10 +2387,13 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     int warps = 8;
     while (warps > 1 && (size_t)warps * sortcap * 8 > 64 * 1024) warps >>= 1;
     const size_t fsmem = (size_t)warps * (1024 + 2 * MAXL * 4 + (size_t)sortcap * 8);
-    static size_t fin_configured = 0;
-    if (fsmem > 48 * 1024 && fsmem > fin_configured) {
+    static size_t fin_configured_dev[64] = {};
+    int fdev = 0;
+    VPET_CUDA(cudaGetDevice(&fdev));
+    VPET_ARG(fdev >= 0 && fdev < 64, "device ordinal %d out of range", fdev);
+    if (fsmem > 48 * 1024 && fsmem > fin_configured_dev[fdev]) {
         VPET_CUDA(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
-        fin_configured = fsmem;
+        fin_configured_dev[fdev] = fsmem;
     }
     k_finalize<<<(unsigned)vpet_ceil_div(F.v_prefix[n], warps), warps * 32, fsmem, s>>>(F);
     VPET_LAUNCH_CHECK();
@@ -2215,6 +2404,7 @@ bool g_has_default = false;   // abc_set_default_tuning was called
 Tuning g_default_tuning = default_tuning(ABC_BF16_RESCORE);
 
 Tuning tuning_for(int mode) { return g_has_default ? g_default_tuning : default_tuning(mode); }
+Tuning tuning_for(int mode, int L) { return g_has_default ? g_default_tuning : default_tuning_for_shape(mode, L); }
 
 ScanSpec single(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w, int k,
                 int32_t* idx, float* dist) {
@@ -2247,7 +2437,7 @@ namespace vpet {
 size_t topk_workspace_bytes(int64_t J, int64_t N, int L, int k, int precision) {
     ScanSpec c = single(nullptr, J, L, nullptr, N, L, L, nullptr, k, nullptr, nullptr);
     BatchLayout* B = new BatchLayout;
-    make_batch_layout(&c, 1, precision, tuning_for(precision), B);
+    make_batch_layout(&c, 1, precision, tuning_for(precision, L), B);
     const size_t t = B->total;
     delete B;
     return t;
@@ -2256,7 +2446,7 @@ size_t topk_workspace_bytes(int64_t J, int64_t N, int L, int k, int precision) {
 int topk_on_workspace(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w,
                       int k, int precision, void* ws, size_t ws_bytes, int32_t* idx, float* dist, cudaStream_t s) {
     const ScanSpec c = single(y, J, ldy, x, N, ldx, L, w, k, idx, dist);
-    return run_batch(&c, 1, precision, tuning_for(precision), ws, ws_bytes, nullptr, 0, s);
+    return run_batch(&c, 1, precision, tuning_for(precision, L), ws, ws_bytes, nullptr, 0, s);
 }
 
 }  // namespace vpet
@@ -2335,6 +2525,15 @@ extern "C" int abc_batch_discrepancy_topk(const abc_scan* scans, int32_t n_scans
     Tuning tu;
     if ((rc = to_tuning(tuning, precision, &tu))) return rc;
     return run_batch(sp, n_scans, precision, tu, workspace, ws_bytes, nullptr, 0, (cudaStream_t)stream);
+}
+
+extern "C" int abc_debug_inject_stall(int64_t withheld_tile, uint64_t wait_ns) {
+    vpet::clear_error();
+    VPET_ARG(wait_ns == 0 || (wait_ns >= 1000000ull && wait_ns <= 10000000000ull),
+             "abc_debug_inject_stall: wait_ns must be 0 (default) or in [1 ms, 10 s]");
+    g_withhold = withheld_tile < 0 ? -1 : withheld_tile;
+    g_wait_ns = wait_ns == 0 ? WAIT_NS_DEFAULT : wait_ns;
+    return ABC_OK;
 }
 
 extern "C" int abc_profile_events(void* start_event, void* stop_event) {

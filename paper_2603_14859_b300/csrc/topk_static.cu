@@ -72,3 +72,22 @@ extern "C" int abc_discrepancy_topk_noalloc(const float* y_dev, int64_t J, int32
     return vpet::topk_on_workspace(y_dev, J, ldy, x_dev, N, ldx, L, w_host, k, precision, scratch,
                                    kStaticScratchBytes, idx_dev, dist_dev, (cudaStream_t)stream);
 }
+
+extern "C" int abc_topk_status_noalloc(int32_t status_host[8], void* stream) {
+    vpet::clear_error();
+    VPET_ARG(status_host, "abc_topk_status_noalloc: null pointer");
+    int dev = -1;
+    VPET_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        vpet::set_error("abc_topk_status_noalloc: device ordinal %d out of range", dev);
+        return ABC_ERR_UNSUPPORTED;
+    }
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        scratch = g_scratch_ptr[dev];
+    }
+    // the status words are the first bytes of the scratch array, as of any workspace
+    VPET_ARG(scratch, "abc_topk_status_noalloc: no abc_discrepancy_topk_noalloc call has run on device %d", dev);
+    return abc_topk_status(scratch, status_host, stream);
+}
