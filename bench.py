@@ -266,7 +266,7 @@ def run_batched(args, world, rank, local):
     pairs = sum(W.J * W.N for W in scans)
     flops = sum(2.0 * W.L * W.J * W.N for W in scans)
     kept, total_tiles = api.topk_work(bp.ws)
-    cols = {0: 3, 1: 1, 2: 2}[prec]
+    cols = {0: 3, 1: 2, 2: 2}[prec]
     kp = max(-(-(cols * W.L + 3) // 64) * 64 for W in scans)
     executed = (2.0 * 128 * 64 * kp * kept) if total_tiles else flops * kp / max(W.L for W in scans)   # 64-draw tiles
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -654,7 +654,7 @@ def main():
     value = voxels / (ms / 1000.0)
     flops = 2.0 * W.L * W.J * W.N
     kept, total_tiles = api.topk_work(run.ws) if not l1 else (0, 0)
-    kp = -(-(({0: 3, 1: 1, 2: 2}[prec]) * W.L + 3) // 64) * 64
+    kp = -(-(({0: 3, 1: 2, 2: 2}[prec]) * W.L + 3) // 64) * 64
     executed = (2.0 * 128 * 64 * kp * kept) if total_tiles else 2.0 * kp * W.J * W.N   # kept: 64-draw tiles
     achieved = executed / (tc_ms / 1000.0) / 1e12
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(

@@ -271,6 +271,12 @@ int abc_profile_events(void* start_event, void* stop_event);
  * < 0 turns the stall off.  Process-wide; for tests only. */
 int abc_debug_inject_stall(int64_t withheld_tile, uint64_t wait_ns);
 
+/* Test hook for the split form's second pass: with on != 0, later calls treat every
+ * voxel's first net as uncertified, so every voxel is queued for the rescue pass (a
+ * quarter of the voxels fit the queue; the rest take the exact fp32 scan).  Results do not
+ * change, only the path.  Process-wide; for tests only. */
+int abc_debug_force_rescue(int32_t on);
+
 /* Diagnostics: grid size of the last fused-kernel launch of this process, the
  * CTAs per SM its variant can keep resident (shared memory, registers and TMEM
  * columns), and how many kernels this library has launched in this process

@@ -31,7 +31,7 @@ EXPORTS = [
     "abc_mlp_loss_grad", "abc_adam_update", "abc_add_noise", "abc_local_abc_smem_bytes", "abc_local_abc",
     "abc_unit_box", "abc_topk_work", "abc_local_abc_table", "abc_response_cri",
     "abc_l1_workspace_size", "abc_discrepancy_topk_l1", "abc_l1_status", "abc_topk_status_noalloc",
-    "abc_debug_inject_stall",
+    "abc_debug_inject_stall", "abc_debug_force_rescue",
 ]
 
 
@@ -86,6 +86,7 @@ def lib():
     L.abc_discrepancy_topk_noalloc.argtypes = [P, i64, i32, P, i64, i32, i32, P, i32, i32, P, P, P]
     L.abc_topk_status_noalloc.argtypes = [P, P]
     L.abc_debug_inject_stall.argtypes = [i64, u64]
+    L.abc_debug_force_rescue.argtypes = [i32]
     L.abc_default_tuning.argtypes = [i32, ctypes.POINTER(Tuning)]
     L.abc_set_default_tuning.argtypes = [ctypes.POINTER(Tuning)]
     L.abc_launch_info.argtypes = [P, P, P]
@@ -123,7 +124,7 @@ def lib():
                "abc_batch_discrepancy_topk", "abc_launch_info", "abc_mlp_init", "abc_mlp_features",
                "abc_mlp_forward", "abc_mlp_loss_grad", "abc_adam_update", "abc_add_noise", "abc_local_abc", "abc_unit_box", "abc_topk_work",
                "abc_local_abc_table", "abc_response_cri", "abc_discrepancy_topk_l1", "abc_l1_status",
-               "abc_topk_status_noalloc", "abc_debug_inject_stall"]:
+               "abc_topk_status_noalloc", "abc_debug_inject_stall", "abc_debug_force_rescue"]:
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L

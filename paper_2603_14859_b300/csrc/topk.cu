@@ -76,6 +76,9 @@ constexpr int ROW_LD = 36;                     // floats per epilogue thread's k
 // unused in that mode): at most this many.
 constexpr int TOPR_MAX = (128 * ROW_LD + 4 * 256) / 128;
 constexpr int MAX_ITEMS = 64;                 // scans per batched launch
+// Work items per rescued voxel tile: the rescue pass usually has few voxel tiles, each of
+// which would otherwise stream all its draw tiles through one CTA.
+constexpr int RESCUE_SEGMENTS = 8;
 
 struct Weights {
     float w[MAXL];
@@ -100,7 +103,10 @@ struct Tuning {
 // ten times more C2 voxels fell back to the exact scan).
 Tuning default_tuning(int mode) {
     if (mode == ABC_FP32) return Tuning{128, 2, 8, 2.25f};
-    return Tuning{128, 2, 16, 1.5f};
+    // split form: the finest pilot (every 8th draw) estimates the k-th distance for the
+    // main pass's per-voxel threshold; a finer sample needs less rank margin, so lists
+    // are shorter and fewer reach their capacity
+    return Tuning{128, 2, 8, 1.5f};
 }
 
 // The built-in tuning for a shape: the split form's operands take two K-blocks past 30
@@ -128,7 +134,8 @@ struct Layout {
     int npart;
     size_t off_mu, off_part, off_ynorm, off_c0, off_dn, off_a, off_b, off_keys, off_idx, off_cnt, off_thr, off_thr0,
         off_perm, off_feat, off_hist, off_xperm, off_xfeat, off_xhist, off_fy, off_fx, off_tbox, off_ktile,
-        off_kcount, off_xs, total;
+        off_kcount, off_xs, off_w, off_rq, off_rrow, off_rthr, off_ra, total;
+    int64_t rcap;                      // split form: voxels the rescue pass can take (0: none)
     int ldxs;                          // row stride (floats) of the packed fp32 draw copy
     int64_t nt64;                      // 64-draw tiles of the draw operand
     int64_t nvt;                       // 128-voxel tiles
@@ -143,7 +150,10 @@ int next_pow2(int x) {
 }
 
 // kp_min: the packed K width is at least this (a batch pads every scan to its widest).
-Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& tu, int kp_min = 0) {
+// roomy: a single-scan call, whose split-form lists may take twice the capacity while they
+// stay within ROOMY_LIST_BYTES (fewer voxels whose net outgrows its list).
+constexpr double ROOMY_LIST_BYTES = 32.0e9;
+Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& tu, int kp_min = 0, bool roomy = false) {
     Layout s;
     memset(&s, 0, sizeof s);
     s.mode = mode;
@@ -202,7 +212,10 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     // list capacity: the FP32 form's net is the list as it stands (~2.25 kt); a split-form
     // list holds its voxel's need-sized net, at most 12 k (the certificate's nets measured on
     // the brain and total-body workloads stay below 12 k; a voxel past it takes the exact scan)
-    s.C = (int)vpet_round_up(mode == ABC_FP32 ? 3 * (int64_t)s.kt + 256 : 12 * (int64_t)k + 256, 32);
+    int64_t cap_entries = mode == ABC_FP32 ? 3 * (int64_t)s.kt + 256 : 12 * (int64_t)k + 256;
+    if (mode != ABC_FP32 && roomy && (double)J * (24.0 * k + 256.0) * 8.0 <= ROOMY_LIST_BYTES)
+        cap_entries = 24 * (int64_t)k + 256;
+    s.C = (int)vpet_round_up(cap_entries, 32);
     s.sortcap = next_pow2(k + 8);     // k plus a few ties at the k-th distance
     if (s.sortcap < 64) s.sortcap = 64;
     s.Jp = vpet_round_up(J > 0 ? J : 1, BM);
@@ -237,6 +250,14 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.off_kcount = o; o = align256(o + (size_t)s.nvt * sizeof(int32_t));
     s.ldxs = (int)vpet_round_up(L, 4);
     s.off_xs = o; o = align256(o + (size_t)s.Np * s.ldxs * sizeof(float));
+    s.off_w = o; o = align256(o + MAXL * sizeof(float));
+    // rescue queue of the split form: a quarter of the voxels (the rest of an unusually
+    // bad scan takes the exact scan)
+    s.rcap = mode == ABC_FP32 ? 0 : vpet_round_up(vpet_ceil_div(J > 0 ? J : 1, 4), BM);
+    s.off_rq = o; o = align256(o + 2 * sizeof(int32_t));
+    s.off_rrow = o; o = align256(o + (size_t)s.rcap * sizeof(int32_t));
+    s.off_rthr = o; o = align256(o + (size_t)s.rcap * 2 * sizeof(float));   // thresholds, then first-net d_k
+    s.off_ra = o; o = align256(o + (size_t)s.rcap * s.Kp * 2);
     s.total = o;
     return s;
 }
@@ -302,11 +323,14 @@ __global__ void k_colmean_part(const float* __restrict__ y, int64_t J, int ldy, 
     if (g == 0) part[(size_t)blockIdx.x * MAXL + l] = red[0][l] + red[1][l] + red[2][l] + red[3][l];
 }
 
-__global__ void k_colmean_final(const float* __restrict__ part, int npart, int64_t J, float* __restrict__ mu) {
+// mu = column means; wdev = the frame weights, kept on the device for the finalize
+__global__ void k_colmean_final(const float* __restrict__ part, int npart, int64_t J, float* __restrict__ mu,
+                                Weights W, float* __restrict__ wdev) {
     const int l = threadIdx.x;
     double s = 0.0;
     for (int b = 0; b < npart; ++b) s += part[(size_t)b * MAXL + l];
     mu[l] = (float)(s / (double)J);
+    wdev[l] = W.w[l];
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -720,6 +744,8 @@ struct KeepArgs {
     SplitCoef sc;
     const float* c0;             // split form: per packed row
     const float* dn;
+    const int32_t* rows;         // rescue pass: list row of each voxel position (thr0 is positional), or null
+    const int32_t* count;        // rescue pass: queued voxels
     int bn;                      // draw-tile width of the pass, 64 or 128
 };
 
@@ -731,12 +757,18 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
     __shared__ int wcount[8];
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     const int64_t vt = blockIdx.x;
+    const int64_t nv = K.count ? (int64_t)*K.count : K.J;   // voxel positions in use
+    if (vt * BM >= nv) {
+        if (tid == 0) K.kcount[vt] = 0;
+        return;
+    }
     if (tid < 7) box[tid] = (tid < 6 && (tid & 1) == 0) ? 0xFFFFFFFFu : 0u;
     __syncthreads();
     if (tid < BM) {
-        const int64_t j = vt * BM + tid;
-        if (j < K.J) {
-            const float t = K.thr0[j];
+        const int64_t p = vt * BM + tid;
+        const int64_t j = K.rows && p < nv ? (int64_t)K.rows[p] : p;   // packed row of the voxel
+        if (p < nv && p < K.J) {
+            const float t = K.thr0[p];
             const float yn = K.ynorm[j];
             float td;
             if (K.split) {
@@ -839,7 +871,10 @@ struct __align__(64) ItemTc {
     const int32_t* ktile;        // kept draw tiles per voxel tile (null: every tile)
     const int32_t* kcount;
     int64_t kstride;
-    float* thr_out;              // top-r pilot: its thresholds
+    union {
+        float* thr_out;          // top-r pilot: its thresholds
+        const int32_t* rows;     // rescue pass: list row of each voxel position (-1: none), or null
+    };
 };
 static_assert(sizeof(ItemTc) == 384, "ItemTc layout");
 
@@ -851,6 +886,9 @@ struct BatchTc {
     int32_t* status;
     float* dump;                 // debug probe: raw keys, Jp x Np (null in production)
     int64_t ld_dump;
+    const int32_t* dyn_count[MAX_ITEMS];   // rescue pass: voxels queued per item (null: all J)
+    int nseg;                    // > 1 (rescue pass): work items per voxel tile, each an interleaved
+                                 // share of its draw tiles
     uint64_t wait_ns;            // bound on every barrier wait (2 s unless a test shortens it)
     int64_t withhold;            // test hook: the TMA producer never loads its draw tile of this
                                  // sequence number (< 0: off), so the waits behind it run out
@@ -860,6 +898,25 @@ __device__ __forceinline__ int item_of(const BatchTc& P, int64_t w) {
     int it = 0;
     while (it + 1 < P.n_items && w >= P.vt_prefix[it + 1]) ++it;
     return it;
+}
+
+// Work item w of a launch: its item, voxel tile and draw-tile segment.  With nseg > 1 (the
+// rescue pass) each voxel tile is nseg work items; segment s takes the tile's kept draw tiles
+// s, s + nseg, s + 2 nseg, ..., so a few voxel tiles still spread over many CTAs.
+struct WorkPos {
+    int it;
+    int64_t vt;
+    int seg, nseg;
+};
+
+__device__ __forceinline__ WorkPos decode_work(const BatchTc& P, int64_t w) {
+    WorkPos r;
+    r.it = item_of(P, w);
+    r.nseg = P.nseg > 1 ? P.nseg : 1;
+    const int64_t loc = w - P.vt_prefix[r.it];
+    r.vt = loc / r.nseg;
+    r.seg = (int)(loc - r.vt * r.nseg);
+    return r;
 }
 
 // Bound on |computed d' - exact d'| for any draw with ||xh|| <= R.
@@ -884,6 +941,7 @@ struct ItemRegs {
     float* keys;
     int32_t* idx;
     int C;
+    int C2;                      // entries of a half-list
 };
 
 // Minimum of the 8 keys v[o .. o+7] (three-input min instructions).
@@ -909,8 +967,11 @@ __device__ __forceinline__ uint32_t mask8(const float (&v)[32], int o, float thr
 // keys to its own row of shared memory (row_s) and appends each passing key,
 // read back by position, to its half-list (starting at entry lbase).  Threads
 // never wait for one another.
+// acnt != null (rescue pass): several CTAs append to the voxel's half-list, each chunk
+// reserving its entries by an atomic add on the list's count; a list that would pass its
+// capacity is flagged (0x40000000) instead, and its voxel takes the exact scan.
 __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32], int64_t n0, int64_t lbase, float thr,
-                                               int& cnt, float* row_s) {
+                                               int& cnt, float* row_s, int* acnt) {
     if (n0 + 32 > I.N) {
 #pragma unroll
         for (int i = 0; i < 32; ++i)
@@ -930,6 +991,22 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
     float4* dst = (float4*)row_s;
 #pragma unroll
     for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    if (acnt) {
+        const int n = __popc(m);
+        int pos = atomicAdd(acnt, n);
+        if (pos + n > I.C2) {
+            atomicOr(acnt, 0x40000000);
+            return;
+        }
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            I.keys[lbase + pos] = row_s[b];
+            I.idx[lbase + pos] = (int32_t)(n0 + b);
+            ++pos;
+        }
+        return;
+    }
     while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
@@ -1090,17 +1167,24 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
             // copy into this CTA's shared memory is still in flight after a bounded wait ran out
             uint32_t st_issued = 0, st_parity = 0, a_issued = 0, a_parity = 0;
             for (uint32_t ic = 0;; ++ic) {
-                // take the next work item and post it to the other roles
+                // take the next work item and post it to the other roles (a rescue item's voxel
+                // tiles past its queued voxels are skipped)
                 long long w = (long long)atomicAdd(P.counter, 1ull);
+                while (w < total && !*s_err) {
+                    const WorkPos wp = decode_work(P, w);
+                    const int32_t* dc = P.dyn_count[wp.it];
+                    if (!dc || wp.vt * BM < (long long)*dc) break;
+                    w = (long long)atomicAdd(P.counter, 1ull);
+                }
                 if (w >= total || *s_err) w = -1;
                 const uint32_t sl = ic & 1u;
                 if (!ptx::mbar_wait(ptx::smem_u32(&iempty[sl]), ((ic >> 1) & 1u) ^ 1u, WAIT_NS)) { *s_err = 1; w = -1; }
                 slot[sl] = w;
                 ptx::mbar_arrive(ptx::smem_u32(&ifull[sl]));
                 if (w < 0) break;
-                const int it = item_of(P, w);
-                const ItemTc& I = P.item[it];
-                const int64_t vt = w - P.vt_prefix[it];
+                const WorkPos wp = decode_work(P, w);
+                const ItemTc& I = P.item[wp.it];
+                const int64_t vt = wp.vt;
                 const int64_t m0 = vt * BM;
                 const int ntiles = I.ktile ? I.kcount[vt] : I.ntiles;
                 const int32_t* kt_list = I.ktile ? I.ktile + vt * I.kstride : nullptr;
@@ -1114,7 +1198,7 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                     ptx::tma_load_2d(ptx::smem_u32(sA + kb * A_KBLK_BYTES), &I.tmA, ab, kb * KBLK, (int32_t)m0);
                 a_issued = 1;
                 a_parity = ic & 1u;
-                for (int t = 0; t < ntiles; ++t, ++gt) {
+                for (int t = wp.seg; t < ntiles; t += wp.nseg, ++gt) {
                     const uint32_t s = gt % STAGES;
                     const uint32_t ph = (gt / STAGES) & 1u;
                     if (!ptx::mbar_wait(ptx::smem_u32(&empty[s]), ph ^ 1u, WAIT_NS)) { *s_err = 1; break; }
@@ -1147,11 +1231,11 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                 else *s_err = 1;
                 ptx::mbar_arrive(ptx::smem_u32(&iempty[sl]));
                 if (w < 0) break;
-                const int itm = item_of(P, w);
-                const ItemTc& IM = P.item[itm];
-                const int ntiles = IM.ktile ? IM.kcount[w - P.vt_prefix[itm]] : IM.ntiles;
+                const WorkPos wp = decode_work(P, w);
+                const ItemTc& IM = P.item[wp.it];
+                const int ntiles = IM.ktile ? IM.kcount[wp.vt] : IM.ntiles;
                 if (!ptx::mbar_wait(ptx::smem_u32(afull), ic & 1u, WAIT_NS)) { *s_err = 1; break; }
-                for (int t = 0; t < ntiles; ++t, ++gt) {
+                for (int t = wp.seg; t < ntiles; t += wp.nseg, ++gt) {
                     const uint32_t s = gt % STAGES;
                     const uint32_t ph = (gt / STAGES) & 1u;
                     const uint32_t acc = gt & 1u;
@@ -1202,26 +1286,32 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&iempty[sl]));
             if (w < 0) break;
-            const int it = item_of(P, w);
-            const ItemTc& I = P.item[it];
-            const ItemRegs R{I.N, I.keys, I.idx, I.C};
-            const int64_t vt = w - P.vt_prefix[it];
+            const WorkPos wp = decode_work(P, w);
+            const ItemTc& I = P.item[wp.it];
+            const ItemRegs R{I.N, I.keys, I.idx, I.C, I.C2};
+            const int64_t vt = wp.vt;
             const int ntiles = I.ktile ? I.kcount[vt] : I.ntiles, lim = I.lim, lim0 = I.lim0;
             const int32_t* kt_list = I.ktile ? I.ktile + vt * I.kstride : nullptr;
             const int64_t m0 = vt * BM;
             const int64_t jbase = m0 + q * 32;
             const int64_t j = jbase + lane;
-            const bool valid = j < I.J;
+            // the voxel's list row (a rescue pass maps positions to the rows of queued voxels)
+            const int64_t jrow = (!TOPR && I.rows) ? (j < I.J ? (int64_t)I.rows[j] : -1) : j;
+            const bool valid = j < I.J && jrow >= 0;
             float thr = valid ? (I.thr0 ? I.thr0[j] : 3.0e38f) : -3.0e38f;
             int cnt = 0;
-            const int64_t lbase = j * (int64_t)I.C + hh * I.C2;   // this thread's half-list
+            const int64_t lbase = jrow * (int64_t)I.C + hh * I.C2;   // this thread's half-list
+            // rescue pass: the voxel's threshold is fixed and its draw tiles are shared among
+            // several CTAs, which reserve list entries atomically (no compaction)
+            const bool shared_list = !TOPR && I.rows != nullptr;
+            int* acnt = (shared_list && valid) ? &I.cnt[jrow + hh * I.hstride] : nullptr;
             TopR S{sRow + (threadIdx.x - 64), TOPR ? I.rsel : 0, 0, 0, -3.0e38f, thr, thr};
             // the next tile's draw offset is loaded a tile ahead, off the path from the
             // accumulator's arrival to its first use
-            int tnext = kt_list && ntiles > 0 ? kt_list[0] : 0;
-            for (int t = 0; t < ntiles; ++t, ++gt) {
+            int tnext = kt_list && ntiles > wp.seg ? kt_list[wp.seg] : 0;
+            for (int t = wp.seg; t < ntiles; t += wp.nseg, ++gt) {
                 const int64_t nbase = (int64_t)(kt_list ? tnext : t) * BN;
-                if (kt_list && t + 1 < ntiles) tnext = kt_list[t + 1];
+                if (kt_list && t + wp.nseg < ntiles) tnext = kt_list[t + wp.nseg];
                 const uint32_t acc = gt & 1u;
                 const uint32_t aph = (gt >> 1) & 1u;
                 if (__any_sync(0xFFFFFFFFu, *s_err != 0)) { stop = true; break; }
@@ -1251,14 +1341,17 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                         float v[32];
 #pragma unroll
                         for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-                        if constexpr (TOPR) topr_chunk(S, v, nbase + c * 32, R.N);
-                        else epilogue_chunk(R, v, nbase + c * 32, lbase, thr, cnt, row_s);
+                        // a lane without a voxel (padding rows) keeps nothing, whatever its keys
+                        if (valid) {
+                            if constexpr (TOPR) topr_chunk(S, v, nbase + c * 32, R.N);
+                            else epilogue_chunk(R, v, nbase + c * 32, lbase, thr, cnt, row_s, acnt);
+                        }
                     }
                 }
                 ptx::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&tempty[acc]));
-                if (DUMP || TOPR) continue;
+                if (DUMP || TOPR || shared_list) continue;
                 // compaction of lists that might not fit the next tile
                 // a list without a threshold yet (the coarsest pilot) is first cut early, at
                 // lim0: from then on far fewer keys pass than the everything of a +inf start
@@ -1267,7 +1360,7 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                     const int src = __ffs(need) - 1;
                     need &= need - 1;
                     int c2 = __shfl_sync(0xFFFFFFFFu, cnt, src);
-                    const float nt = compact_list(I, jbase + src, hh, c2, whist, lane);
+                    const float nt = compact_list(I, __shfl_sync(0xFFFFFFFFu, jrow, src), hh, c2, whist, lane);
                     if (lane == src) {
                         cnt = c2;
                         thr = nt;
@@ -1284,9 +1377,11 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                     I.thr_out[j] = t;
                     if (t >= 3.0e38f) atomicAdd(&P.status[7], 1);
                 } else {
-                    atomicOr(&I.cnt[j + hh * I.hstride], cnt);      // cnt[] was zeroed; keeps the overflow bit
-                    I.thr[j + hh * I.hstride] = thr;
-                    if (EPI == 4) I.thr[j + I.hstride] = 3.0e38f;   // the unused half-list bounds nothing
+                    // cnt[] was zeroed (a shared list counted its entries as they were reserved);
+                    // keeps the overflow bit
+                    if (!shared_list) atomicOr(&I.cnt[jrow + hh * I.hstride], cnt);
+                    I.thr[jrow + hh * I.hstride] = thr;
+                    if (EPI == 4) I.thr[jrow + I.hstride] = 3.0e38f;   // the unused half-list bounds nothing
                 }
             }
         }
@@ -1370,9 +1465,12 @@ __global__ void k_pilot_threshold(const __grid_constant__ BatchPilot B) {
     }
 }
 
-// Split form, after the finest pilot: the pilot key K of rank rk bounds the voxel's k-th
-// distance by D = dist_ub(K) (unless the sample misled by four standard deviations), so the
-// main pass keeps every draw with key <= need_key(D): all the certificate can ask for.
+// Split form, after the finest pilot: the pilot key K of rank rk (four standard deviations
+// above the rank of the k-th draw) gives the distance estimate K + ||yh||^2 - c0, and the
+// main pass keeps every draw with key <= need_key(that estimate).  This covers the
+// finalize's net in all but a small fraction of voxels (measured: under 1 %), which its
+// certificate detects and the rescue pass resolves; bounding the estimate once more
+// (dist_ub) would cover them all at about twice the list length.
 struct NeedItem {
     float* thr0;
     const float* ynorm;
@@ -1398,7 +1496,58 @@ __global__ void k_need_threshold(const __grid_constant__ BatchNeed B) {
     const float K = I.thr0[j];
     if (!(K < 1.0e30f)) return;          // no pilot threshold: the main pass starts without one
     const float yn = I.ynorm[j], c0 = I.c0[j], dn = I.dn[j];
-    I.thr0[j] = need_key(dist_ub(K, yn, c0, dn, I.sc), yn, c0, dn, I.sc);
+    I.thr0[j] = need_key(fmaxf(K + yn - c0, 0.0f), yn, c0, dn, I.sc);
+}
+
+// Rescue pass set-up (split form): the voxels the first finalize queued get a compact
+// A operand of their packed rows (positions 0 .. n - 1), their candidate-list counts
+// reset, and position -1 marks the rest of the last 128-voxel tile.  eff = the queue
+// length clipped to its capacity, read by every later kernel of the pass.
+struct RescueItem {
+    const int32_t* count;        // voxels the first finalize tried to queue
+    int32_t* eff;
+    int32_t* rows;
+    int64_t cap;
+    const __nv_bfloat16* A;
+    __nv_bfloat16* RA;
+    int Kp;
+    int32_t* cnt;
+    int64_t hstride;
+};
+
+struct BatchRescue {
+    RescueItem item[MAX_ITEMS];
+    int n_items;
+};
+
+__global__ void k_rescue_prep(const __grid_constant__ BatchRescue B) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int it = 0; it < B.n_items; ++it) {
+        const RescueItem& I = B.item[it];
+        const int64_t c = *I.count;
+        const int64_t n = c < I.cap ? c : I.cap;
+        if (w0 == 0 && lane == 0) *I.eff = (int32_t)n;
+        const int64_t np = (n + BM - 1) / BM * BM;
+        for (int64_t p = w0; p < np; p += nw) {
+            if (p >= n) {
+                // the rest of the last tile: no voxel, an all-zero operand row
+                uint4* dst = (uint4*)(I.RA + p * I.Kp);
+                for (int q = lane; q < I.Kp / 8; q += 32) dst[q] = make_uint4(0u, 0u, 0u, 0u);
+                if (lane == 0) I.rows[p] = -1;
+                continue;
+            }
+            const int64_t row = I.rows[p];
+            const uint4* src = (const uint4*)(I.A + row * I.Kp);
+            uint4* dst = (uint4*)(I.RA + p * I.Kp);
+            for (int q = lane; q < I.Kp / 8; q += 32) dst[q] = src[q];
+            if (lane == 0) {
+                I.cnt[row] = 0;
+                I.cnt[row + I.hstride] = 0;
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------ finalize
@@ -1428,7 +1577,14 @@ struct FinItem {
     const float* thr;
     int32_t* out_idx;
     float* out_dist;
-    float w[MAXL];
+    const float* w;              // frame weights (device copy in the workspace)
+    const int32_t* rows;         // rescue pass: list row of each voxel position, or null (position = row)
+    const int32_t* rcount;       // rescue pass: voxels queued
+    int32_t* rq_rows;            // first pass of the split form: the rescue queue (null: no rescue)
+    float* rq_thr;
+    float* rq_dk;                // the queued net's exact k-th distance (first pass writes, rescue reads)
+    int32_t* rq_count;
+    int64_t rq_cap;
 };
 
 struct BatchFin {
@@ -1437,6 +1593,7 @@ struct BatchFin {
     int n_items;
     int sortcap;                 // largest sortcap of the batch (shared-memory sizing)
     int32_t* status;
+    int force_uncertified;       // test hook: a first net is never certified (rescue and exact scan run)
 };
 
 // Exact fp32 distance sum_l w_l (y_l - x_l)^2 of a draw row in one fixed
@@ -1553,8 +1710,10 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
     int it = 0;
     while (it + 1 < B.n_items && g >= B.v_prefix[it + 1]) ++it;
     const FinItem& P = B.item[it];
-    const int64_t j = g - B.v_prefix[it];                  // list row
-    const int64_t vox = P.perm ? (int64_t)P.perm[j] : j;   // voxel of that row
+    const int64_t gpos = g - B.v_prefix[it];               // voxel position
+    if (P.rows && gpos >= (int64_t)*P.rcount) return;
+    const int64_t j = P.rows ? (int64_t)P.rows[gpos] : gpos;   // list row
+    const int64_t vox = P.perm ? (int64_t)P.perm[j] : j;        // voxel of that row
     float* kj = P.keys + j * P.C;
     int32_t* ij = P.idx + j * P.C;
     const int raw0 = P.cnt[j], raw1 = P.cnt[j + P.hstride];
@@ -1579,13 +1738,12 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
     }
     uint32_t K = 0;
     int n_less = -1, n_eq = -1;                   // keys below / at K (-1: not counted yet)
-    float dbound = __int_as_float(0x7F800000);   // exact k-th distance of the net: bounds the true one
+    // exact k-th distance of a net: bounds the true one (a rescued voxel starts from its first net's)
+    float dbound = P.rows ? P.rq_dk[gpos] : __int_as_float(0x7F800000);
     if (!scan) {
-        // 1. the net is the whole list: every draw outside it has computed key > T_out
-        // (both halves dropped only keys above their own thresholds)
-        const float T_out = fminf(P.thr[j], P.thr[j + P.hstride]);
-        // 2. exact fp32 re-score of the net (list entries are packed draw rows, read from the
-        // packed fp32 copy): G lanes per row, four rows per group in flight
+        // 1. the net: every draw outside it has computed key > T_out (both halves dropped only
+        // keys above their own thresholds)
+        float T_out = fminf(P.thr[j], P.thr[j + P.hstride]);
         constexpr int NR = 4;
         float yq[4], wq[4];
 #pragma unroll
@@ -1594,6 +1752,76 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
             yq[q] = l < P.L ? ys[l] : 0.0f;
             wq[q] = l < P.L ? ws[l] : 0.0f;
         }
+        // split form: the net need not be the whole list.  The k smallest keys are re-scored
+        // first (their rows gathered into sbuf); the largest of their exact distances, d1,
+        // bounds the k-th distance from above, so every draw the certificate can ask for has
+        // key <= need_key(d1).  The list is cut there and only the rest is re-scored.
+        int n1 = 0;                          // entries of that first set, in sbuf: (distance, packed row)
+        if (P.mode != ABC_FP32 && cnt > P.k) {
+            const KthKey k1 = warp_select_exact(kj, cnt, P.k - 1, hist, (float*)sbuf, 2 * B.sortcap, lane);
+            if (k1.n_less + k1.n_eq <= B.sortcap) {
+                for (int base = 0; base < cnt; base += 32) {
+                    const int i = base + lane;
+                    const bool in = i < cnt && f2key(kj[i]) <= k1.K;
+                    const uint32_t row = in ? (uint32_t)ij[i] : 0u;
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in);
+                    if (in) sbuf[n1 + __popc(bal & ((1u << lane) - 1u))] = row;
+                    n1 += __popc(bal);
+                }
+                __syncwarp();
+                float d1 = 0.0f;
+                for (int i0 = 0; i0 < n1; i0 += NR * R) {
+                    const float* xr[NR];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const int i = i0 + r * R + grp;
+                        xr[r] = P.xs + (int64_t)(uint32_t)sbuf[i < n1 ? i : 0] * P.ldxs;
+                    }
+                    float d[NR];
+                    group_dist_n<NR>(yq, wq, xr, P.L, h, G, d);
+                    if (h == 0) {
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            const int i = i0 + r * R + grp;
+                            if (i < n1) {
+                                sbuf[i] = ((unsigned long long)__float_as_uint(d[r]) << 32) | (uint32_t)sbuf[i];
+                                d1 = fmaxf(d1, d[r]);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) d1 = fmaxf(d1, __shfl_xor_sync(0xFFFFFFFFu, d1, o));
+                const float Tc = fminf(need_key(d1, P.ynorm[j], P.c0[j], P.dn[j],
+                                                SplitCoef{P.cacc, 4.0f * (float)P.L * 0x1p-24f}), T_out);
+                // keep K1 < key <= Tc (the first set is in sbuf), in place
+                int out = 0;
+                for (int base = 0; base < cnt; base += 32) {
+                    const int i = base + lane;
+                    float kv = 0.0f;
+                    int32_t iv = 0;
+                    bool keep = false;
+                    if (i < cnt) {
+                        kv = kj[i];
+                        iv = ij[i];
+                        keep = f2key(kv) > k1.K && kv <= Tc;
+                    }
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+                    if (keep) {
+                        const int pos = out + __popc(bal & ((1u << lane) - 1u));
+                        kj[pos] = kv;
+                        ij[pos] = iv;
+                    }
+                    out += __popc(bal);
+                }
+                __syncwarp();
+                cnt = out;
+                T_out = Tc;
+            }
+        }
+        // 2. exact fp32 re-score of the (rest of the) net (list entries are packed draw rows, read
+        // from the packed fp32 copy): G lanes per row, four rows per group in flight
         if (NR * R <= 32) {
             // row indices come a 32-row chunk at a time (lane t holds row cb + t), the next
             // chunk's already in flight, so a gather never waits on its own index load; the
@@ -1661,6 +1889,17 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
                 __syncwarp();
             }
         }
+        // the first set joins the re-scored net: exact distances and global draw indices
+        if (n1 > 0) {
+            for (int i = lane; i < n1; i += 32) {
+                const unsigned long long e = sbuf[i];
+                const int32_t row = (int32_t)(uint32_t)e;
+                kj[cnt + i] = __uint_as_float((uint32_t)(e >> 32));
+                ij[cnt + i] = P.xperm ? P.xperm[row] : row;
+            }
+            cnt += n1;
+            __syncwarp();
+        }
         // 3. exact k-th distance and the certificate
         bool cert = false;
         if (cnt >= P.k) {
@@ -1669,7 +1908,7 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
             n_less = kth.n_less;
             n_eq = kth.n_eq;
             const float dk = key2f(K);
-            dbound = dk;
+            dbound = fminf(dbound, dk);
             const float yn = P.ynorm[j];
             float need;
             const float slack = 4.0f * (float)P.L * 0x1p-24f;
@@ -1681,11 +1920,30 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
                 // every draw at exact distance <= d_k has key <= need_key(d_k)
                 need = need_key(dk, yn, P.c0[j], P.dn[j], SplitCoef{P.cacc, slack});
             }
-            cert = T_out >= 2.9e38f || T_out >= need;
+            cert = (T_out >= 2.9e38f || T_out >= need) && !(B.force_uncertified && P.rq_rows);
         }
         if (!cert) {
+            // split form, first pass: the net's d_k bounds the exact k-th distance, so
+            // need_key(d_k) is a threshold that collects every draw the certificate can ask
+            // for; the voxel is queued for a second tensor-core pass with it, whose own
+            // finalize writes its outputs.  Otherwise (queue full, or the second pass) the
+            // exact scan below resolves it.
+            if (P.rq_rows && cnt >= P.k) {
+                int pos = 0;
+                if (lane == 0) pos = atomicAdd(P.rq_count, 1);
+                pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
+                if (pos < P.rq_cap) {
+                    if (lane == 0) {
+                        P.rq_rows[pos] = (int32_t)j;
+                        P.rq_dk[pos] = dbound;
+                        P.rq_thr[pos] = need_key(dbound, P.ynorm[j], P.c0[j], P.dn[j],
+                                                 SplitCoef{P.cacc, 4.0f * (float)P.L * 0x1p-24f});
+                        atomicAdd(&B.status[3], 1);
+                    }
+                    return;
+                }
+            }
             scan = true;
-            if (P.mode != ABC_FP32 && lane == 0) atomicAdd(&B.status[3], 1);
         }
     }
     if (scan) {
@@ -1793,6 +2051,7 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 // the draw-tile sequence number its TMA producers withhold (-1: none).
 uint64_t g_wait_ns = WAIT_NS_DEFAULT;
 int64_t g_withhold = -1;
+int g_force_uncertified = 0;   // test hook (abc_debug_force_rescue)
 cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
 int g_last_resident = 0;     // residency of the last configured fused-kernel variant
 int64_t g_last_grid = 0;     // grid of the last fused-kernel launch
@@ -1994,6 +2253,7 @@ struct BatchLayout {
 };
 
 void make_batch_layout(const ScanSpec* sc, int n, int mode, const Tuning& tu, BatchLayout* B) {
+    const bool roomy = n == 1;   // a single scan may use roomier candidate lists
     B->n = n;
     int kp = 0;
     for (int i = 0; i < n; ++i) {
@@ -2003,7 +2263,7 @@ void make_batch_layout(const ScanSpec* sc, int n, int mode, const Tuning& tu, Ba
     // one K-width per launch: every scan is laid out at the widest
     size_t o = 256;
     for (int i = 0; i < n; ++i) {
-        B->lay[i] = make_layout(sc[i].J, sc[i].N, sc[i].L, sc[i].k, mode, tu, kp);
+        B->lay[i] = make_layout(sc[i].J, sc[i].N, sc[i].L, sc[i].k, mode, tu, kp, roomy);
         B->off[i] = o;
         o = align256(o + B->lay[i].total);
     }
@@ -2015,14 +2275,15 @@ bool layout_consistent(const Layout& L) {
     const size_t off[] = {L.off_mu, L.off_part, L.off_ynorm, L.off_c0, L.off_dn, L.off_a, L.off_b, L.off_keys,
                           L.off_idx, L.off_cnt, L.off_thr, L.off_thr0, L.off_perm, L.off_feat, L.off_hist,
                           L.off_xperm, L.off_xfeat, L.off_xhist, L.off_fy, L.off_fx, L.off_tbox, L.off_ktile,
-                          L.off_kcount, L.off_xs};
+                          L.off_kcount, L.off_xs, L.off_w, L.off_rq, L.off_rrow, L.off_rthr, L.off_ra};
     const size_t len[] = {MAXL * 4, (size_t)L.npart * MAXL * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
                           (size_t)L.Jp * L.Kp * 2, (size_t)L.Np * L.Kp * 2, (size_t)L.J * L.C * 4,
                           (size_t)L.J * L.C * 4, (size_t)2 * L.Jp * 4, (size_t)2 * L.Jp * 4, (size_t)L.Jp * 4,
                           (size_t)L.Jp * 4, (size_t)3 * L.Jp * 4 + 32, (size_t)(ORDER_BUCKETS + ORDER_BUCKETS / 1024) * 4,
                           (size_t)L.Np * 4, (size_t)3 * L.Np * 4 + 32, (size_t)(ORDER_BUCKETS + ORDER_BUCKETS / 1024) * 4,
                           (size_t)3 * L.Jp * 4, (size_t)3 * L.Np * 4, (size_t)6 * L.nt64 * 4,
-                          (size_t)L.nvt * L.nt64 * 4, (size_t)L.nvt * 4, (size_t)L.Np * L.ldxs * 4};
+                          (size_t)L.nvt * L.nt64 * 4, (size_t)L.nvt * 4, (size_t)L.Np * L.ldxs * 4, MAXL * 4, 8,
+                          (size_t)L.rcap * 4, (size_t)L.rcap * 8, (size_t)L.rcap * L.Kp * 2};
     const int n = (int)(sizeof off / sizeof off[0]);
     for (int i = 0; i < n; ++i) {
         if (off[i] + len[i] > (i + 1 < n ? off[i + 1] : L.total)) return false;
@@ -2069,8 +2330,11 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         int32_t *perm, *xperm, *ktile, *kcount;
         float* xs;
         uint32_t *mm, *hist, *xmm, *xhist;
-        __nv_bfloat16 *A, *B;
+        __nv_bfloat16 *A, *B, *RA;
         int32_t *idx, *cnt;
+        float* wdev;
+        int32_t *rq, *rrow;
+        float* rthr;
     } ptr[MAX_ITEMS];
     for (int i = 0; i < n; ++i) {
         const Layout& L = BL.lay[i];
@@ -2102,6 +2366,11 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         p.ktile = (int32_t*)(base + L.off_ktile);
         p.kcount = (int32_t*)(base + L.off_kcount);
         p.xs = (float*)(base + L.off_xs);
+        p.wdev = (float*)(base + L.off_w);
+        p.rq = (int32_t*)(base + L.off_rq);
+        p.rrow = (int32_t*)(base + L.off_rrow);
+        p.rthr = (float*)(base + L.off_rthr);
+        p.RA = (__nv_bfloat16*)(base + L.off_ra);
         Weights W;
         memset(&W, 0, sizeof W);
         for (int l = 0; l < L.L; ++l) {
@@ -2109,9 +2378,10 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             W.sw[l] = sqrtf(sc[i].w[l]);
         }
         VPET_CUDA(cudaMemsetAsync(p.cnt, 0, (size_t)2 * L.Jp * sizeof(int32_t), s));
+        VPET_CUDA(cudaMemsetAsync(p.rq, 0, 2 * sizeof(int32_t), s));
         k_colmean_part<<<L.npart, 256, 0, s>>>(sc[i].y, L.J, sc[i].ldy, L.L, p.part, L.npart);
         VPET_LAUNCH_CHECK();
-        k_colmean_final<<<1, MAXL, 0, s>>>(p.part, L.npart, L.J, p.mu);
+        k_colmean_final<<<1, MAXL, 0, s>>>(p.part, L.npart, L.J, p.mu, W, p.wdev);
         VPET_LAUNCH_CHECK();
         const bool order = dump == nullptr && L.J > 1;   // the debug dump keeps voxel order
         if (order) {
@@ -2377,13 +2647,21 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         f.thr = ptr[i].thr;
         f.out_idx = sc[i].idx;
         f.out_dist = sc[i].dist;
-        for (int l = 0; l < L.L; ++l) f.w[l] = sc[i].w[l];
+        f.w = ptr[i].wdev;
+        if (L.rcap > 0 && dump == nullptr) {
+            f.rq_rows = ptr[i].rrow;
+            f.rq_thr = ptr[i].rthr;
+            f.rq_dk = ptr[i].rthr + L.rcap;
+            f.rq_count = ptr[i].rq;
+            f.rq_cap = L.rcap;
+        }
         F.v_prefix[i + 1] = F.v_prefix[i] + L.J;
         if (L.sortcap > sortcap) sortcap = L.sortcap;
     }
     F.n_items = n;
     F.sortcap = sortcap;
     F.status = status;
+    F.force_uncertified = g_force_uncertified;
     int warps = 8;
     while (warps > 1 && (size_t)warps * sortcap * 8 > 64 * 1024) warps >>= 1;
     const size_t fsmem = (size_t)warps * (1024 + 2 * MAXL * 4 + (size_t)sortcap * 8);
@@ -2394,6 +2672,84 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     if (fsmem > 48 * 1024 && fsmem > fin_configured_dev[fdev]) {
         VPET_CUDA(cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
         fin_configured_dev[fdev] = fsmem;
+    }
+    k_finalize<<<(unsigned)vpet_ceil_div(F.v_prefix[n], warps), warps * 32, fsmem, s>>>(F);
+    VPET_LAUNCH_CHECK();
+    if (mode == ABC_FP32 || dump != nullptr) return ABC_OK;
+
+    // rescue pass of the split form: the voxels the finalize queued, each with the exact
+    // threshold its net's k-th distance asks for, go through the fused kernel once more
+    // (their candidate lists rebuilt in their own rows) and a second finalize.  Queue
+    // lengths stay on the device: positions past them are skipped.
+    BatchRescue RB;
+    memset(&RB, 0, sizeof RB);
+    for (int i = 0; i < n; ++i) {
+        const Layout& L = BL.lay[i];
+        RB.item[i] = RescueItem{ptr[i].rq, ptr[i].rq + 1, ptr[i].rrow, L.rcap, ptr[i].A, ptr[i].RA, L.Kp, ptr[i].cnt,
+                                L.Jp};
+    }
+    RB.n_items = n;
+    k_rescue_prep<<<(unsigned)num_sms() * 4, 256, 0, s>>>(RB);
+    VPET_LAUNCH_CHECK();
+    memset(&T, 0, sizeof T);
+    for (int oi = 0; oi < n; ++oi) {
+        const int i = order[oi];
+        const Layout& L = BL.lay[i];
+        const Ptrs& p = ptr[i];
+        const bool xorder = L.N > 1;
+        if (xorder) {
+            KeepArgs K;
+            memset(&K, 0, sizeof K);
+            K.fy = p.fy;
+            K.thr0 = p.rthr;
+            K.ynorm = p.ynorm;
+            K.tbox = p.tbox;
+            K.ktile = p.ktile;
+            K.kcount = p.kcount;
+            K.J = L.rcap;
+            K.N = L.N;
+            K.nt64 = L.nt64;
+            for (int l = 0; l < L.L; ++l) K.Wc[(3 * l) / L.L] += sc[i].w[l];
+            K.cE = error_coef(L);
+            K.split = 1;
+            K.sc = split_coef(L);
+            K.c0 = p.c0;
+            K.dn = p.dn;
+            K.rows = p.rrow;
+            K.count = p.rq + 1;
+            K.bn = tu.bn;
+            k_keep_tiles<<<(unsigned)(L.rcap / BM), 256, 0, s>>>(K);
+            VPET_LAUNCH_CHECK();
+        }
+        if ((rc = fill_item(T.item[oi], i, 1, L.kt, L.C, p.rthr))) return rc;
+        if ((rc = make_tmap(&T.item[oi].tmA, p.RA, L.rcap, L.Kp, BM, 1))) return rc;
+        T.item[oi].J = L.rcap;
+        T.item[oi].rows = p.rrow;
+        if (xorder) {
+            T.item[oi].ktile = p.ktile;
+            T.item[oi].kcount = p.kcount;
+            T.item[oi].kstride = L.nt64;
+        }
+        T.dyn_count[oi] = p.rq + 1;
+        T.vt_prefix[oi + 1] = T.vt_prefix[oi] + L.rcap / BM * RESCUE_SEGMENTS;
+    }
+    T.nseg = RESCUE_SEGMENTS;
+    T.n_items = n;
+    T.status = status;
+    T.counter = counters + (MAX_PILOT_LEVELS + 1);
+    T.wait_ns = g_wait_ns;
+    T.withhold = g_withhold;
+    if ((rc = dispatch_tc<false>(nkb, tu.bn, T, tu.ctas_per_sm, s))) return rc;
+    for (int i = 0; i < n; ++i) {
+        FinItem& f = F.item[i];
+        f.rows = ptr[i].rrow;
+        f.rcount = ptr[i].rq + 1;
+        f.rq_rows = nullptr;
+        f.rq_thr = nullptr;
+        f.rq_dk = ptr[i].rthr + BL.lay[i].rcap;   // read by the rescue finalize
+        f.rq_count = nullptr;
+        f.rq_cap = 0;
+        F.v_prefix[i + 1] = F.v_prefix[i] + BL.lay[i].rcap;
     }
     k_finalize<<<(unsigned)vpet_ceil_div(F.v_prefix[n], warps), warps * 32, fsmem, s>>>(F);
     VPET_LAUNCH_CHECK();
@@ -2533,6 +2889,12 @@ extern "C" int abc_debug_inject_stall(int64_t withheld_tile, uint64_t wait_ns) {
              "abc_debug_inject_stall: wait_ns must be 0 (default) or in [1 ms, 10 s]");
     g_withhold = withheld_tile < 0 ? -1 : withheld_tile;
     g_wait_ns = wait_ns == 0 ? WAIT_NS_DEFAULT : wait_ns;
+    return ABC_OK;
+}
+
+extern "C" int abc_debug_force_rescue(int32_t on) {
+    vpet::clear_error();
+    g_force_uncertified = on ? 1 : 0;
     return ABC_OK;
 }
 

@@ -47,6 +47,7 @@ def test_batch_equals_single_scan_calls(batch, prec):
     for r in bp.runs:
         r.simulate_draws()
     bp.set_inputs(ys)
+    bp.ws.fill_(0xFF)                                  # stale workspace contents must not matter
     bp.topk()
     torch.cuda.synchronize()
     st = api.topk_status(bp.ws)
@@ -65,6 +66,7 @@ def test_batch_oracle_parity(batch, orc, prec):
     for r in bp.runs:
         r.simulate_draws()
     bp.set_inputs(ys)
+    bp.ws.fill_(0xFF)                                  # stale workspace contents must not matter
     bp.topk()
     torch.cuda.synchronize()
     seen = set()
@@ -87,6 +89,7 @@ def test_batch_graph_replay(batch):
     scans, ys = batch
     bp = pipeline.BatchPipeline(scans, 1)
     bp.set_inputs(ys)
+    bp.ws.fill_(0xFF)                                  # stale workspace contents must not matter
     bp.step()
     torch.cuda.synchronize()
     ref = [(r.idx.clone(), r.dist.clone(), r.prob.clone(), r.summ[0].clone()) for r in bp.runs]
@@ -112,6 +115,7 @@ def test_autotune_choice_and_invariance(batch, tmp_path, monkeypatch):
     for r in bp.runs:
         r.simulate_draws()
     bp.set_inputs(ys)
+    bp.ws.fill_(0xFF)                                  # stale workspace contents must not matter
     bp.topk()
     torch.cuda.synchronize()
     ref = [r.idx.clone() for r in bp.runs]

@@ -37,11 +37,13 @@ def _gpu_case(name, J, n, orc):
     return W, torch.from_numpy(yp).cuda(), x
 
 
-def _compare(orc, W, y, x, k, prec, tau_extra=0.0):
+def _compare(orc, W, y, x, k, prec, tau_extra=0.0, ws=None):
     from paper_2603_14859_b300 import api
     L = W.L
     w = W.weights.astype(np.float32)
-    ws = api.alloc_workspace(W.J, x.shape[0], L, k, prec)
+    if ws is None:
+        ws = api.alloc_workspace(W.J, x.shape[0], L, k, prec)
+        ws.fill_(0xFF)                                 # stale workspace contents must not matter
     idx, dist = api.discrepancy_topk(y, x, L, w, k, prec, ws)
     st = api.topk_status(ws)
     assert st[0] == 0 and st[2] == 0, f"status {st}"
@@ -163,13 +165,28 @@ def test_argument_errors():
     assert e.value.code == -3
 
 
-@pytest.mark.parametrize("prec,k", [(2, 10), (0, 2)])
-def test_exact_scan_path_matches_oracle(orc, prec, k):
-    """With a small k the exact forms cannot certify many voxels of this case (the net's
-    kt-th key is too close to the k-th distance for the error bound); they go through the
-    exact scan over the tiles whose segment-feature bound admits the net's k-th distance.
-    The accepted sets still match the oracle's."""
+@pytest.mark.parametrize("prec,k", [(2, 10), (1, 50), (0, 2)])
+def test_uncertified_voxels_match_oracle(orc, prec, k):
+    """Voxels whose first net cannot be certified.  The FP32 form resolves them by the
+    exact scan over the tiles whose segment-feature bound admits the net's k-th distance
+    (with k = 2 many voxels of this case).  The split form queues them for its second
+    tensor-core pass (rescue) with the threshold their net's k-th distance asks for; the
+    test hook abc_debug_force_rescue fails every first net, so every voxel is queued, a
+    quarter of them fit the queue and the rest take the exact scan.  The accepted sets
+    still match the oracle's."""
+    from paper_2603_14859_b300 import _lib, api
     W, y, x = _gpu_case("raclopride_lpntpet", 512, 20000, orc)
-    swaps, worst, scanned = _compare(orc, W, y, x, k, prec)
-    assert scanned > 0
+    L = W.L
+    ws = api.alloc_workspace(W.J, x.shape[0], L, k, prec)
+    ws.fill_(0xFF)                                     # stale workspace contents must not matter
+    _lib.check(_lib.lib().abc_debug_force_rescue(1))
+    try:
+        swaps, worst, scanned = _compare(orc, W, y, x, k, prec, ws=ws)
+        st = api.topk_status(ws)
+    finally:
+        _lib.check(_lib.lib().abc_debug_force_rescue(0))
+    if prec == 0:
+        assert scanned > 0
+    else:
+        assert st[3] == W.J // 4 and st[1] >= W.J - W.J // 4, f"status {st}"
     assert swaps == 0
