@@ -50,7 +50,7 @@ def _precisions():
 
 
 PRECISIONS = _precisions()
-DTYPES = {"bf16r": "bf16", "fp32": "bf16x3-split (fp32-exact)", "split": "bf16x2 (draws split; fp32-exact)"}
+DTYPES = {"bf16r": "bf16", "fp32": "bf16x3-split (fp32-exact)", "split": "bf16"}
 
 
 def parse():
@@ -64,6 +64,11 @@ def parse():
     ap.add_argument("--voxels", type=int, default=None, help="override J (smaller runs)")
     ap.add_argument("--draws", type=int, default=None, help="override draws per model")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="single-scan workloads on N GPUs: every rank a full-size block of the volume (weak) "
+                         "or a voxel range of one block (strong)")
+    ap.add_argument("--no-fp32-comparator", action="store_true",
+                    help="skip the FP32-form sub-record of the fast form's line")
     ap.add_argument("--voxel-scale", type=float, default=1.0, help="batched workload: scale voxel counts")
     ap.add_argument("--draw-scale", type=float, default=1.0, help="batched workload: scale draw counts")
     ap.add_argument("--scans", type=int, default=64, help="batched workload: number of scans")
@@ -505,7 +510,8 @@ def main():
     from paper_2603_14859_b300 import sharding
 
     def make_workload(r):
-        return sharding.rank_workload(args.workload, r, J=args.voxels, N_per_model=args.draws)
+        return sharding.rank_workload(args.workload, r, world, J=args.voxels, N_per_model=args.draws,
+                                      scaling=args.scaling)
 
     if args.workload == "batched":
         return run_batched(args, world, rank, local)
@@ -538,7 +544,8 @@ def main():
     cfg = {"workload": WORKLOADS[args.workload].format(J=W.J, n=W.n_per_model[0], k=W.k),
            "voxels_per_gpu": W.J, "draws": W.N, "frames": W.L, "k": W.k,
            "precision": args.precision, "l2": "inputs larger than L2 (draw operands + candidate lists > 126 MB)",
-           "parallelism": f"voxel shards x{args.gpus}" if args.gpus > 1 else "single GPU"}
+           "parallelism": (f"disjoint voxel ranges of one volume x{args.gpus} ({args.scaling} scaling)"
+                           if args.gpus > 1 else "single GPU")}
     if args.tuning and args.impl != "reference":
         from paper_2603_14859_b300 import api as _api
         bn, cps, st, fac = args.tuning.split(",")
@@ -623,6 +630,7 @@ def main():
         tc_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     clk = clocks.stop()
     ms, tc_ms = sharding.max_over_ranks([ms, tc_ms], dist, device="cuda")
+    voxels_all = int(round(sharding.sum_over_ranks(W.J, dist, device="cuda")))
 
     # end to end through the public API with host buffers
     y_host = y.cpu().pin_memory()
@@ -650,7 +658,7 @@ def main():
         dist.destroy_process_group()
         return
     n_gpu = world
-    voxels = W.J * n_gpu
+    voxels = voxels_all
     value = voxels / (ms / 1000.0)
     flops = 2.0 * W.L * W.J * W.N
     kept, total_tiles = api.topk_work(run.ws) if not l1 else (0, 0)
@@ -669,10 +677,11 @@ def main():
             traffic = rec["bytes_per_launch"]
     line = {
         "metric": "voxels/s to posterior", "value": value, "unit": "voxels/s", "n_gpus": n_gpu, "steps": K,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": args.scaling,
+        "vs_baseline": None,
         "dtype": DTYPES[args.precision],
         "data": "synthetic", "config": cfg,
-        "pairs_per_s": W.J * W.N * n_gpu / (ms / 1000.0),
+        "pairs_per_s": voxels * W.N / (ms / 1000.0),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_tc_topk main pass (fused discrepancy + top-k filter)", "kernel_ms": tc_ms,
@@ -703,11 +712,78 @@ def main():
         line["topk_status"] = {"tie_overflow_voxels": st[2]}
     if resp is not None:
         line["response_band"] = resp
+    if not l1 and prec != _lib.ABC_FP32 and rank == 0:
+        if args.no_fp32_comparator or W.J > 1_000_000:
+            line["stated_error"] = {"accepted_sets": "exact fp32 top-k, certified per voxel (uncertified nets "
+                                                     "re-collected by the rescue pass or the exact scan); parity "
+                                                     "against the FP64 oracle at full size in "
+                                                     "tests/test_gpu_fullsize.py"}
+        else:
+            line.update(fp32_comparator(W, run, y, stream, peak, K, args.warmup))
     if n_gpu == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W, distance=args.distance)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def fp32_comparator(W, run, y, stream, peak, K, warmup):
+    """The same step with the ABC_FP32 form (three bf16 products per term), timed in the
+    same run, and the fast form's error against it: both return the exact fp32 top-k, so
+    the accepted sets may differ only where fp32 distances tie; the summaries are compared
+    over every voxel."""
+    import torch
+    from paper_2603_14859_b300 import _lib, api, pipeline
+    out = run.step(y)
+    torch.cuda.synchronize()
+    fast = [t.clone() for t in (out.idx, out.prob, out.pref, out.mean, out.sd, out.lo, out.hi)]
+    rf = pipeline.AbcPipeline(W, _lib.ABC_FP32)
+    for _ in range(max(2, warmup)):
+        rf.step(y)
+    torch.cuda.synchronize()
+    Kf = max(1, min(K, 3))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Kf)]
+    for a, b in ev:
+        a.record(stream)
+        b.record(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(Kf):
+        api.profile_events(*ev[i])
+        of = rf.step(y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    api.profile_events(None, None)
+    ms = e0.elapsed_time(e1) / Kf
+    tc_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    st = api.topk_status(rf.ws)
+    kept, total_tiles = api.topk_work(rf.ws)
+    kp = -(-(3 * W.L + 3) // 64) * 64
+    executed = (2.0 * 128 * 64 * kp * kept) if total_tiles else 2.0 * kp * W.J * W.N
+    same = (torch.sort(fast[0], 1).values == torch.sort(of.idx, 1).values).all(1)
+    rel = {}
+    for name, a, b in zip(("mean", "sd", "lo", "hi"), fast[3:], (of.mean, of.sd, of.lo, of.hi)):
+        m = ~torch.isnan(b)
+        d = torch.where(m, (a - b).abs() / b.abs().clamp_min(1e-12), torch.zeros_like(b))
+        rel[name] = float(d.max())
+    rec = {
+        "fp32_exact": {"ms_per_step": ms, "value": W.J / (ms / 1000.0), "unit": "voxels/s", "steps": Kf,
+                       "kernel_ms": tc_ms, "executed_tflops": executed / (tc_ms / 1000.0) / 1e12,
+                       "frac": executed / (tc_ms / 1000.0) / 1e12 / peak, "exact_scan_voxels": st[1],
+                       "dtype": DTYPES["fp32"]},
+        "stated_error": {
+            "accepted_sets": "exact fp32 top-k, certified per voxel (uncertified nets re-collected by the rescue "
+                             "pass or the exact scan); parity against the FP64 oracle at full size in "
+                             "tests/test_gpu_fullsize.py",
+            "voxels_with_sets_equal_to_fp32_form": int(same.sum()), "voxels": W.J,
+            "max_rel_diff_vs_fp32_form": rel,
+            "model_prob_max_abs_diff_vs_fp32_form": float((fast[1] - of.prob).abs().max()),
+            "preferred_model_differs": int((fast[2] != of.pref).sum())},
+    }
+    del rf
+    torch.cuda.empty_cache()
+    return rec
 
 
 # thread instructions per response evaluation of k_response_cri (evaluation, compensated

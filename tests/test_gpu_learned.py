@@ -306,12 +306,11 @@ def test_learned_proposal_beats_prior_proposal(c3_small):
         return np.array(e + [np.sqrt(((o["mean"][:, 4].cpu().numpy() - ki) ** 2).mean()) / ki.std()])
 
     el, ef = err(learned), err(flat)
-    # K1 is the best identified parameter and gains most; over the four kinetic parameters the
-    # error drops clearly; K_i (already well determined by prior-like proposals) must not get
-    # materially worse despite the importance weights' variance (ESS ~ k/4)
-    assert el[0] < 0.6 * ef[0], (el, ef)
-    assert el[:4].mean() < 0.9 * ef[:4].mean(), (el, ef)
-    assert el[4] < 1.25 * ef[4], (el, ef)
+    # K1, Vb and K_i are identified by the data and must gain; k2 and k3 barely are (the global
+    # path's own error on them is ~0.35 of the box), so for those only require no loss.  With
+    # these seeds (training is bitwise reproducible) the ratios are 0.22, 0.67, 0.99, 0.54, 0.90
+    assert el[0] < 0.5 * ef[0] and el[3] < 0.8 * ef[3] and el[4] < 0.95 * ef[4], (el, ef)
+    assert el[1] < 1.05 * ef[1] and el[2] < 1.05 * ef[2], (el, ef)
     # fallback: with a calibrated threshold, voxels whose local run is unreliable take the global path
     g = GlobalIrr(model, N=200_000, k=k)
     rel = g.calibrate(yj[:128])
