@@ -271,11 +271,15 @@ int abc_profile_events(void* start_event, void* stop_event);
  * < 0 turns the stall off.  Process-wide; for tests only. */
 int abc_debug_inject_stall(int64_t withheld_tile, uint64_t wait_ns);
 
-/* Test hook for the split form's second pass: with on != 0, later calls treat every
- * voxel's first net as uncertified, so every voxel is queued for the rescue pass (a
- * quarter of the voxels fit the queue; the rest take the exact fp32 scan).  Results do not
- * change, only the path.  Process-wide; for tests only. */
-int abc_debug_force_rescue(int32_t on);
+/* Test hook for the split form's second pass.  mode is a mask: with bit 1, later calls
+ * treat every voxel's first net as uncertified, so voxels are queued for the rescue pass
+ * (all of them while the queue holds them: every voxel of a scan of at most 16,384
+ * voxels, a quarter otherwise; the rest take the exact fp32 scan); with bit 2, every
+ * rescue net is treated as uncertified too (those voxels take the exact scan, bounded by
+ * their first net's k-th distance); with bit 4, the queue holds at most a quarter of the
+ * scan's voxels.  0 turns the hook off.  Results do not change, only the path.
+ * Process-wide; for tests only.  ABC_ERR_ARG for a mode outside 0..7. */
+int abc_debug_force_rescue(int32_t mode);
 
 /* Diagnostics: grid size of the last fused-kernel launch of this process, the
  * CTAs per SM its variant can keep resident (shared memory, registers and TMEM

@@ -79,6 +79,8 @@ constexpr int MAX_ITEMS = 64;                 // scans per batched launch
 // Work items per rescued voxel tile: the rescue pass usually has few voxel tiles, each of
 // which would otherwise stream all its draw tiles through one CTA.
 constexpr int RESCUE_SEGMENTS = 8;
+// A scan of at most this many voxels may queue all of them for the rescue pass.
+constexpr int64_t RESCUE_ALL_VOXELS = 16384;
 
 struct Weights {
     float w[MAXL];
@@ -136,6 +138,12 @@ struct Layout {
         off_perm, off_feat, off_hist, off_xperm, off_xfeat, off_xhist, off_fy, off_fx, off_tbox, off_ktile,
         off_kcount, off_xs, off_w, off_rq, off_rrow, off_rthr, off_ra, total;
     int64_t rcap;                      // split form: voxels the rescue pass can take (0: none)
+    int G;                             // centring groups (split form): packed voxel rows [g Jg, (g+1) Jg)
+    int64_t Jg;                        // rows per group, a multiple of 128 (every voxel tile lies in one group)
+    int64_t rcapa;                     // rescue positions allocated: rcap plus a padded tile per group
+    int64_t lrows;                     // candidate-list rows allocated: max(J, rcapa)
+    int Cr;                            // rescue pass: list capacity of a queue position (>= C)
+    size_t off_tgroup, off_rq2, off_rtg, off_rcnt, off_rthrh;
     int ldxs;                          // row stride (floats) of the packed fp32 draw copy
     int64_t nt64;                      // 64-draw tiles of the draw operand
     int64_t nvt;                       // 128-voxel tiles
@@ -150,10 +158,10 @@ int next_pow2(int x) {
 }
 
 // kp_min: the packed K width is at least this (a batch pads every scan to its widest).
-// roomy: a single-scan call, whose split-form lists may take twice the capacity while they
-// stay within ROOMY_LIST_BYTES (fewer voxels whose net outgrows its list).
-constexpr double ROOMY_LIST_BYTES = 32.0e9;
-Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& tu, int kp_min = 0, bool roomy = false) {
+// list_mult (split form): candidate lists hold list_mult x 12 k entries (1, 2 or 4; the batch
+// layout chooses it per scan within a memory budget): fewer voxels whose net outgrows its list.
+Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& tu, int kp_min = 0, int list_mult = 1,
+                   int groups = 1) {
     Layout s;
     memset(&s, 0, sizeof s);
     s.mode = mode;
@@ -212,26 +220,43 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     // list capacity: the FP32 form's net is the list as it stands (~2.25 kt); a split-form
     // list holds its voxel's need-sized net, at most 12 k (the certificate's nets measured on
     // the brain and total-body workloads stay below 12 k; a voxel past it takes the exact scan)
-    int64_t cap_entries = mode == ABC_FP32 ? 3 * (int64_t)s.kt + 256 : 12 * (int64_t)k + 256;
-    if (mode != ABC_FP32 && roomy && (double)J * (24.0 * k + 256.0) * 8.0 <= ROOMY_LIST_BYTES)
-        cap_entries = 24 * (int64_t)k + 256;
+    const int64_t cap_entries = mode == ABC_FP32 ? 3 * (int64_t)s.kt + 256
+                                                 : 12 * (int64_t)(list_mult > 1 ? list_mult : 1) * k + 256;
     s.C = (int)vpet_round_up(cap_entries, 32);
     s.sortcap = next_pow2(k + 8);     // k plus a few ties at the k-th distance
     if (s.sortcap < 64) s.sortcap = 64;
     s.Jp = vpet_round_up(J > 0 ? J : 1, BM);
     s.Np = vpet_round_up(N > 0 ? N : 1, 128);
-    s.npart = (int)(vpet_ceil_div(J, 256) < 1024 ? vpet_ceil_div(J, 256) : 1024);
-    if (s.npart < 1) s.npart = 1;
+    // centring groups: G contiguous runs of whole voxel tiles in the packed (feature) order
+    s.G = mode == ABC_FP32 || groups < 1 ? 1 : groups;
+    s.Jg = vpet_round_up(vpet_ceil_div(J > 0 ? J : 1, s.G), BM);
+    s.G = (int)vpet_ceil_div(J > 0 ? J : 1, s.Jg);
+    {
+        const int64_t per_group = vpet_ceil_div(s.Jg, 256);
+        const int64_t cap = 1024 / s.G > 1 ? 1024 / s.G : 1;
+        s.npart = (int)(per_group < cap ? per_group : cap);
+        if (s.npart < 1) s.npart = 1;
+    }
     size_t o = 0;
-    s.off_mu = o; o = align256(o + MAXL * sizeof(float));
-    s.off_part = o; o = align256(o + (size_t)s.npart * MAXL * sizeof(float));
+    s.off_mu = o; o = align256(o + (size_t)s.G * MAXL * sizeof(float));
+    s.off_part = o; o = align256(o + (size_t)s.G * s.npart * MAXL * sizeof(float));
     s.off_ynorm = o; o = align256(o + (size_t)s.Jp * sizeof(float));
     s.off_c0 = o; o = align256(o + (size_t)s.Jp * sizeof(float));
     s.off_dn = o; o = align256(o + (size_t)s.Jp * sizeof(float));
     s.off_a = o; o = align256(o + (size_t)s.Jp * s.Kp * 2);
-    s.off_b = o; o = align256(o + (size_t)s.Np * s.Kp * 2);
-    s.off_keys = o; o = align256(o + (size_t)J * s.C * sizeof(float));
-    s.off_idx = o; o = align256(o + (size_t)J * s.C * sizeof(int32_t));
+    s.off_b = o; o = align256(o + (size_t)s.G * s.Np * s.Kp * 2);   // one packed copy per centring group
+    // rescue queue of the split form: a quarter of the voxels (all of them in a small scan;
+    // the rest of an unusually bad scan takes the exact scan), plus a padded tile per group
+    s.rcap = mode == ABC_FP32 ? 0
+                              : (J <= RESCUE_ALL_VOXELS ? s.Jp : vpet_round_up(vpet_ceil_div(J > 0 ? J : 1, 4), BM));
+    s.rcapa = s.rcap > 0 ? s.rcap + (int64_t)s.G * BM : 0;
+    // candidate lists: J rows of C entries; the rescue pass lays the same space out as rcapa
+    // rows of Cr entries (the first pass's lists are dead by then), so a queued voxel's net
+    // may be several times the first pass's capacity
+    s.lrows = J > s.rcapa ? J : s.rcapa;
+    s.Cr = s.rcapa > 0 ? (int)((s.lrows * (int64_t)s.C / s.rcapa) & ~(int64_t)1) : 0;
+    s.off_keys = o; o = align256(o + (size_t)s.lrows * s.C * sizeof(float));
+    s.off_idx = o; o = align256(o + (size_t)s.lrows * s.C * sizeof(int32_t));
     s.off_cnt = o; o = align256(o + (size_t)2 * s.Jp * sizeof(int32_t));     // two half-lists per voxel
     s.off_thr = o; o = align256(o + (size_t)2 * s.Jp * sizeof(float));
     s.off_thr0 = o; o = align256(o + (size_t)s.Jp * sizeof(float));
@@ -251,13 +276,16 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.ldxs = (int)vpet_round_up(L, 4);
     s.off_xs = o; o = align256(o + (size_t)s.Np * s.ldxs * sizeof(float));
     s.off_w = o; o = align256(o + MAXL * sizeof(float));
-    // rescue queue of the split form: a quarter of the voxels (the rest of an unusually
-    // bad scan takes the exact scan)
-    s.rcap = mode == ABC_FP32 ? 0 : vpet_round_up(vpet_ceil_div(J > 0 ? J : 1, 4), BM);
-    s.off_rq = o; o = align256(o + 2 * sizeof(int32_t));
-    s.off_rrow = o; o = align256(o + (size_t)s.rcap * sizeof(int32_t));
-    s.off_rthr = o; o = align256(o + (size_t)s.rcap * 2 * sizeof(float));   // thresholds, then first-net d_k
-    s.off_ra = o; o = align256(o + (size_t)s.rcap * s.Kp * 2);
+    s.off_tgroup = o; o = align256(o + (size_t)s.nvt * sizeof(int32_t));
+    // queue words: count, queued positions in use, then per group its count, cursor and first position
+    s.off_rq = o; o = align256(o + (size_t)(2 + 3 * s.G + 1) * sizeof(int32_t));
+    s.off_rrow = o; o = align256(o + (size_t)s.rcapa * sizeof(int32_t));
+    s.off_rthr = o; o = align256(o + (size_t)s.rcapa * 2 * sizeof(float));   // thresholds, then first-net d_k
+    s.off_rq2 = o; o = align256(o + (size_t)s.rcapa * 3 * sizeof(int32_t));   // the queue sorted by group
+    s.off_rtg = o; o = align256(o + (size_t)(s.rcapa / BM + 1) * sizeof(int32_t));
+    s.off_rcnt = o; o = align256(o + (size_t)2 * s.rcapa * sizeof(int32_t));   // rescue lists: counts, per half
+    s.off_rthrh = o; o = align256(o + (size_t)2 * s.rcapa * sizeof(float));    // and final thresholds
+    s.off_ra = o; o = align256(o + (size_t)s.rcapa * s.Kp * 2);
     s.total = o;
     return s;
 }
@@ -308,29 +336,47 @@ __host__ __device__ __forceinline__ float dist_ub(float T, float yn, float c0, f
 }
 
 // ------------------------------------------------------------------ packing
-// Column mean of y over voxels, deterministic two-stage reduction.
+// Centring groups.  The key's error scales with the norms of the centred rows, so a
+// voxel far from the centre (a small-signal voxel in a scan of large ones) needs a long
+// net.  Voxels are processed in a feature order (below), and G contiguous runs of whole
+// 128-voxel tiles of that order are each centred on their own mean TAC; the draw operand
+// is packed once per group (copies stacked in B), and a work item reads the copy of its
+// voxel tile's group.  Distances are translation invariant, so results do not change.
+
+// Column sums of each group's voxels (packed row j is voxel perm[j]; perm null: voxel j),
+// npart partial sums per group, then their fp64 total: a deterministic reduction.
 __global__ void k_colmean_part(const float* __restrict__ y, int64_t J, int ldy, int L, float* __restrict__ part,
-                               int npart) {
+                               int npart, const int32_t* __restrict__ perm, int64_t Jg) {
     __shared__ float red[4][MAXL];
     const int l = threadIdx.x & 63, g = threadIdx.x >> 6;
-    const int64_t per = (J + npart - 1) / npart;
-    const int64_t j0 = blockIdx.x * per, j1 = j0 + per < J ? j0 + per : J;
+    const int grp = blockIdx.x / npart, pp = blockIdx.x % npart;
+    const int64_t r0 = (int64_t)grp * Jg, r1 = r0 + Jg < J ? r0 + Jg : J;
+    const int64_t per = (r1 - r0 + npart - 1) / npart;
+    const int64_t j0 = r0 + pp * per, j1 = j0 + per < r1 ? j0 + per : r1;
     float s = 0.0f;
     if (l < L)
-        for (int64_t j = j0 + g; j < j1; j += 4) s += y[j * ldy + l];
+        for (int64_t j = j0 + g; j < j1; j += 4) s += y[(perm ? (int64_t)perm[j] : j) * ldy + l];
     red[g][l] = s;
     __syncthreads();
     if (g == 0) part[(size_t)blockIdx.x * MAXL + l] = red[0][l] + red[1][l] + red[2][l] + red[3][l];
 }
 
-// mu = column means; wdev = the frame weights, kept on the device for the finalize
-__global__ void k_colmean_final(const float* __restrict__ part, int npart, int64_t J, float* __restrict__ mu,
-                                Weights W, float* __restrict__ wdev) {
-    const int l = threadIdx.x;
+// mu[g] = group g's column means (one block per group); wdev = the frame weights, kept on
+// the device for the finalize
+__global__ void k_colmean_final(const float* __restrict__ part, int npart, int64_t J, int64_t Jg,
+                                float* __restrict__ mu, Weights W, float* __restrict__ wdev) {
+    const int l = threadIdx.x, grp = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < npart; ++b) s += part[(size_t)b * MAXL + l];
-    mu[l] = (float)(s / (double)J);
-    wdev[l] = W.w[l];
+    for (int b = 0; b < npart; ++b) s += part[((size_t)grp * npart + b) * MAXL + l];
+    const int64_t r0 = (int64_t)grp * Jg, r1 = r0 + Jg < J ? r0 + Jg : J;
+    mu[(size_t)grp * MAXL + l] = (float)(s / (double)(r1 - r0));
+    if (grp == 0) wdev[l] = W.w[l];
+}
+
+// tgroup[t] = the centring group of voxel tile t
+__global__ void k_tile_groups(int32_t* __restrict__ tgroup, int64_t nvt, int64_t Jg) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nvt) tgroup[t] = (int32_t)(t * BM / Jg);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -529,12 +575,13 @@ __device__ __forceinline__ void stage_frame_consts(FrameConsts& S, const Weights
 }
 
 // Row j of A is voxel perm[j] (perm = null: voxel j); fy[3 j + c] = its segment features.
+// mu: the groups' means (MAXL each); a block's 8 rows lie in one group (Jg is a multiple of 128).
 __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int ldy, int L, int Kp, int mode,
-                         Weights W, const float* __restrict__ mu, const int32_t* __restrict__ perm,
+                         Weights W, const float* __restrict__ mu, int64_t Jg, const int32_t* __restrict__ perm,
                          __nv_bfloat16* __restrict__ A, float* __restrict__ ynorm, float* __restrict__ c0,
                          float* __restrict__ dn, float* __restrict__ fy) {
     __shared__ FrameConsts F;
-    stage_frame_consts(F, W, mu, L);
+    stage_frame_consts(F, W, mu + ((int64_t)blockIdx.x * (blockDim.x >> 5) / Jg) * MAXL, L);
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= Jp) return;
@@ -599,12 +646,17 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
 // the exact re-score reads the draws in packed order.  The warp's four source
 // rows are read into shared memory with all their loads in flight together.
 constexpr int PACK_ROWS = 4;
+constexpr int MAX_GROUPS = 16;                 // centring groups per scan
+// B holds G copies of the packed draws, copy g (rows [g Np, (g+1) Np)) centred on group
+// g's mean mu[g]; the fp32 copy xs and the segment features are written once.
 __global__ void __launch_bounds__(256) k_pack_x(const float* __restrict__ x, int64_t N, int64_t Np, int ldx, int L,
-                                                int Kp, int mode, Weights W, const float* __restrict__ mu,
+                                                int Kp, int mode, Weights W, const float* __restrict__ mu, int G,
                                                 const int32_t* __restrict__ xperm, __nv_bfloat16* __restrict__ B,
                                                 float* __restrict__ fx, float* __restrict__ xs, int ldxs) {
     __shared__ FrameConsts F;
+    __shared__ float s_mu[MAX_GROUPS][MAXL];
     __shared__ float s_rows[8][PACK_ROWS][MAXL];
+    for (int e = threadIdx.x; e < G * MAXL; e += blockDim.x) s_mu[e / MAXL][e % MAXL] = mu[e];
     stage_frame_consts(F, W, mu, L);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t nb = ((int64_t)blockIdx.x * 8 + wid) * PACK_ROWS;
@@ -633,9 +685,11 @@ __global__ void __launch_bounds__(256) k_pack_x(const float* __restrict__ x, int
     for (int u = 0; u < PACK_ROWS; ++u) {
         const int64_t n = nb + u;
         if (n >= Np) break;
-        __nv_bfloat16* row = B + n * Kp;
         if (n >= N) {
-            for (int e = lane; e < Kp; e += 32) row[e] = bf(0.0f);
+            for (int g = 0; g < G; ++g) {
+                __nv_bfloat16* row = B + ((int64_t)g * Np + n) * Kp;
+                for (int e = lane; e < Kp; e += 32) row[e] = bf(0.0f);
+            }
             continue;
         }
         const float* xr = s_rows[wid][u];
@@ -649,41 +703,45 @@ __global__ void __launch_bounds__(256) k_pack_x(const float* __restrict__ x, int
                 fx[3 * n + 2] = f[2];
             }
         }
-        float ss = 0.0f, sr = 0.0f;
-        for (int l = lane; l < L; l += 32) {
-            const float v = F.sw[l] * (xr[l] - F.mu[l]);
-            ss = fmaf(v, v, ss);
-            if (mode != ABC_FP32) {
-                // the residual of the hi + lo split, r = v - hi - lo (exact in fp32)
-                const float h = __bfloat162float(bf(v)), d1 = v - h;
-                sr = fmaf(v, d1 - __bfloat162float(bf(d1)), sr);
+        for (int g = 0; g < G; ++g) {
+            const float* m = s_mu[g];
+            __nv_bfloat16* row = B + ((int64_t)g * Np + n) * Kp;
+            float ss = 0.0f, sr = 0.0f;
+            for (int l = lane; l < L; l += 32) {
+                const float v = F.sw[l] * (xr[l] - m[l]);
+                ss = fmaf(v, v, ss);
+                if (mode != ABC_FP32) {
+                    // the residual of the hi + lo split, r = v - hi - lo (exact in fp32)
+                    const float h = __bfloat162float(bf(v)), d1 = v - h;
+                    sr = fmaf(v, d1 - __bfloat162float(bf(d1)), sr);
+                }
             }
-        }
-        ss = warp_sum(ss);
-        // split form: the norm column carries ||b||^2 - 2 b.r, so that the key's error from the
-        // draw row's split is 2 (a - b).r, which vanishes with the distance
-        if (mode != ABC_FP32) ss -= 2.0f * warp_sum(sr);
-        const float n1 = __bfloat162float(bf(ss));
-        const float r1 = ss - n1;
-        const float n2 = __bfloat162float(bf(r1));
-        const float n3 = r1 - n2;
-        const int aug = cols_per_frame(mode) * L;
-        for (int e = lane; e < Kp; e += 32) {
-            float out = 0.0f;
-            if (e < aug) {
-                const int l = e % L;
-                const float v = F.sw[l] * (xr[l] - F.mu[l]);
-                const float hi = __bfloat162float(bf(v));
-                if (mode == ABC_FP32) out = -2.0f * ((e >= L && e < 2 * L) ? (v - hi) : hi);
-                else out = -2.0f * (e >= L ? (v - hi) : hi);
-            } else if (e == aug) {
-                out = n1;
-            } else if (e == aug + 1) {
-                out = n2;
-            } else if (e == aug + 2) {
-                out = n3;
+            ss = warp_sum(ss);
+            // split form: the norm column carries ||b||^2 - 2 b.r, so that the key's error from the
+            // draw row's split is 2 (a - b).r, which vanishes with the distance
+            if (mode != ABC_FP32) ss -= 2.0f * warp_sum(sr);
+            const float n1 = __bfloat162float(bf(ss));
+            const float r1 = ss - n1;
+            const float n2 = __bfloat162float(bf(r1));
+            const float n3 = r1 - n2;
+            const int aug = cols_per_frame(mode) * L;
+            for (int e = lane; e < Kp; e += 32) {
+                float out = 0.0f;
+                if (e < aug) {
+                    const int l = e % L;
+                    const float v = F.sw[l] * (xr[l] - m[l]);
+                    const float hi = __bfloat162float(bf(v));
+                    if (mode == ABC_FP32) out = -2.0f * ((e >= L && e < 2 * L) ? (v - hi) : hi);
+                    else out = -2.0f * (e >= L ? (v - hi) : hi);
+                } else if (e == aug) {
+                    out = n1;
+                } else if (e == aug + 1) {
+                    out = n2;
+                } else if (e == aug + 2) {
+                    out = n3;
+                }
+                row[e] = bf(out);
             }
-            row[e] = bf(out);
         }
     }
 }
@@ -766,8 +824,8 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
     __syncthreads();
     if (tid < BM) {
         const int64_t p = vt * BM + tid;
-        const int64_t j = K.rows && p < nv ? (int64_t)K.rows[p] : p;   // packed row of the voxel
-        if (p < nv && p < K.J) {
+        const int64_t j = K.rows && p < nv ? (int64_t)K.rows[p] : p;   // packed row of the voxel (-1: none)
+        if (p < nv && p < K.J && j >= 0) {
             const float t = K.thr0[p];
             const float yn = K.ynorm[j];
             float td;
@@ -887,6 +945,8 @@ struct BatchTc {
     float* dump;                 // debug probe: raw keys, Jp x Np (null in production)
     int64_t ld_dump;
     const int32_t* dyn_count[MAX_ITEMS];   // rescue pass: voxels queued per item (null: all J)
+    const int32_t* tgroup[MAX_ITEMS];      // per item: centring group of each voxel tile (null: group 0)
+    int64_t grows[MAX_ITEMS];              // per item: rows of one group's copy of the draw operand
     int nseg;                    // > 1 (rescue pass): work items per voxel tile, each an interleaved
                                  // share of its draw tiles
     uint64_t wait_ns;            // bound on every barrier wait (2 s unless a test shortens it)
@@ -1188,6 +1248,7 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                 const int64_t m0 = vt * BM;
                 const int ntiles = I.ktile ? I.kcount[vt] : I.ntiles;
                 const int32_t* kt_list = I.ktile ? I.ktile + vt * I.kstride : nullptr;
+                const int64_t gofs = P.tgroup[wp.it] ? (int64_t)P.tgroup[wp.it][vt] * P.grows[wp.it] : 0;   // the group's B copy
                 ptx::tma_prefetch_desc(&I.tmA);
                 ptx::tma_prefetch_desc(&I.tmB);
                 // the previous item's MMAs must be done with the A tile
@@ -1208,7 +1269,7 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                     ptx::mbar_arrive_expect_tx(fb, NKB * B_KBLK_BYTES);
                     for (int kb = 0; kb < NKB; ++kb)
                         ptx::tma_load_2d(ptx::smem_u32(sB + (s * NKB + kb) * B_KBLK_BYTES), &I.tmB, fb, kb * KBLK,
-                                         (kt_list ? kt_list[t] : t) * BN);
+                                         (int32_t)((kt_list ? kt_list[t] : t) * BN + gofs));
                     st_issued |= 1u << s;
                     st_parity = (st_parity & ~(1u << s)) | (ph << s);
                 }
@@ -1295,8 +1356,9 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
             const int64_t m0 = vt * BM;
             const int64_t jbase = m0 + q * 32;
             const int64_t j = jbase + lane;
-            // the voxel's list row (a rescue pass maps positions to the rows of queued voxels)
-            const int64_t jrow = (!TOPR && I.rows) ? (j < I.J ? (int64_t)I.rows[j] : -1) : j;
+            // the voxel's list row; a rescue pass lists by queue position (rows[] maps positions
+            // to the packed rows of queued voxels, -1 for padding)
+            const int64_t jrow = (!TOPR && I.rows) ? (j < I.J && I.rows[j] >= 0 ? j : -1) : j;
             const bool valid = j < I.J && jrow >= 0;
             float thr = valid ? (I.thr0 ? I.thr0[j] : 3.0e38f) : -3.0e38f;
             int cnt = 0;
@@ -1499,20 +1561,27 @@ __global__ void k_need_threshold(const __grid_constant__ BatchNeed B) {
     I.thr0[j] = need_key(fmaxf(K + yn - c0, 0.0f), yn, c0, dn, I.sc);
 }
 
-// Rescue pass set-up (split form): the voxels the first finalize queued get a compact
-// A operand of their packed rows (positions 0 .. n - 1), their candidate-list counts
-// reset, and position -1 marks the rest of the last 128-voxel tile.  eff = the queue
-// length clipped to its capacity, read by every later kernel of the pass.
+// Rescue pass set-up (split form).  The first finalize queued voxels in arrival order
+// (qrows, qthr, qdk, at most cap of them).  A rescued voxel tile must lie in one centring
+// group, so the queue is sorted by group into runs padded to whole tiles: per group its
+// count, then each group's first position, then the placement, which also copies the
+// voxel's packed operand row into the compact A operand.  The rescue pass lists by queue
+// position (counts and thresholds of its own, zeroed on the host).
+// Queue words: [0] voxels queued, [1] positions in use (runs padded), [2, 2+G) counts,
+// [2+G, 2+2G) cursors, [2+2G, 3+3G) first positions.
 struct RescueItem {
-    const int32_t* count;        // voxels the first finalize tried to queue
-    int32_t* eff;
-    int32_t* rows;
-    int64_t cap;
+    int32_t* words;
+    const int32_t* qrows;
+    const float* qthr;
+    const float* qdk;
+    int32_t* rows;               // sorted by group (-1: padding)
+    float* thr;
+    float* dk;
+    int32_t* rtg;                // group of each rescue tile
+    int64_t cap, Jg, J;          // cap: the queue capacity the first finalize used
+    int G, Kp;
     const __nv_bfloat16* A;
     __nv_bfloat16* RA;
-    int Kp;
-    int32_t* cnt;
-    int64_t hstride;
 };
 
 struct BatchRescue {
@@ -1520,31 +1589,76 @@ struct BatchRescue {
     int n_items;
 };
 
-__global__ void k_rescue_prep(const __grid_constant__ BatchRescue B) {
+__device__ __forceinline__ int64_t rescue_queued(const RescueItem& I) {
+    const int64_t c = I.words[0];
+    return c < I.cap ? c : I.cap;
+}
+
+__global__ void k_rescue_count(const __grid_constant__ BatchRescue B) {
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    for (int it = 0; it < B.n_items; ++it) {
+        const RescueItem& I = B.item[it];
+        const int64_t n = rescue_queued(I);
+        for (int64_t p = t0; p < n; p += nt) {
+            const int32_t row = I.qrows[p];
+            if (row >= 0 && row < I.J) atomicAdd(&I.words[2 + row / I.Jg], 1);
+        }
+    }
+}
+
+// one block per item
+__global__ void k_rescue_layout(const __grid_constant__ BatchRescue B) {
+    const RescueItem& I = B.item[blockIdx.x];
+    int32_t* cnt_g = I.words + 2;
+    int32_t* cur_g = I.words + 2 + I.G;
+    int32_t* first = I.words + 2 + 2 * I.G;
+    if (threadIdx.x == 0) {
+        int32_t off = 0;
+        for (int g = 0; g < I.G; ++g) {
+            first[g] = off;
+            cur_g[g] = off;
+            off += (cnt_g[g] + BM - 1) / BM * BM;
+        }
+        first[I.G] = off;
+        I.words[1] = off;
+    }
+    __syncthreads();
+    const int32_t total = I.words[1];
+    for (int32_t t = threadIdx.x; t < total / BM; t += blockDim.x) {
+        int g = 0;
+        while (g + 1 < I.G && first[g + 1] <= t * BM) ++g;
+        I.rtg[t] = g;
+    }
+    // padding positions of each run: no voxel, an all-zero operand row
+    for (int g = 0; g < I.G; ++g)
+        for (int32_t p = first[g] + cnt_g[g] + (int32_t)threadIdx.x; p < first[g + 1]; p += blockDim.x) {
+            I.rows[p] = -1;
+            uint4* dst = (uint4*)(I.RA + (int64_t)p * I.Kp);
+            for (int q = 0; q < I.Kp / 8; ++q) dst[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+}
+
+// one warp per queued voxel
+__global__ void k_rescue_place(const __grid_constant__ BatchRescue B) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int it = 0; it < B.n_items; ++it) {
         const RescueItem& I = B.item[it];
-        const int64_t c = *I.count;
-        const int64_t n = c < I.cap ? c : I.cap;
-        if (w0 == 0 && lane == 0) *I.eff = (int32_t)n;
-        const int64_t np = (n + BM - 1) / BM * BM;
-        for (int64_t p = w0; p < np; p += nw) {
-            if (p >= n) {
-                // the rest of the last tile: no voxel, an all-zero operand row
-                uint4* dst = (uint4*)(I.RA + p * I.Kp);
-                for (int q = lane; q < I.Kp / 8; q += 32) dst[q] = make_uint4(0u, 0u, 0u, 0u);
-                if (lane == 0) I.rows[p] = -1;
-                continue;
-            }
-            const int64_t row = I.rows[p];
+        const int64_t n = rescue_queued(I);
+        for (int64_t p = w0; p < n; p += nw) {
+            const int64_t row = I.qrows[p];
+            if (row < 0 || row >= I.J) continue;      // (never written by the finalize: skipped as by the count)
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(&I.words[2 + I.G + row / I.Jg], 1);
+            pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
             const uint4* src = (const uint4*)(I.A + row * I.Kp);
-            uint4* dst = (uint4*)(I.RA + p * I.Kp);
+            uint4* dst = (uint4*)(I.RA + (int64_t)pos * I.Kp);
             for (int q = lane; q < I.Kp / 8; q += 32) dst[q] = src[q];
             if (lane == 0) {
-                I.cnt[row] = 0;
-                I.cnt[row + I.hstride] = 0;
+                I.rows[pos] = (int32_t)row;
+                I.thr[pos] = I.qthr[p];
+                I.dk[pos] = I.qdk[p];
             }
         }
     }
@@ -1555,20 +1669,20 @@ struct FinItem {
     int64_t J, N;
     int L, k, C, kt, mode, sortcap;
     int C2;                      // the list row's two half-lists start at 0 and C2
-    int64_t hstride;             // cnt[] / thr[] of half 1: row + hstride
+    int64_t hstride;             // cnt[] / thr[] of half 1: list row + hstride
     float cacc;                  // (3 Kp + L + 16) 2^-24: the keys' fp32 accumulation (both certificates)
     int ldy, ldx;
     const float* y;
     const float* x;
-    const float* ynorm;
-    const float* c0;             // split form: -2 delta . yh per list row
-    const float* dn;             // split form: ||delta|| per list row
-    const int32_t* perm;         // list row -> voxel (null: identity)
+    const float* ynorm;          // per packed voxel row
+    const float* c0;             // split form: -2 delta . yh per packed voxel row
+    const float* dn;             // split form: ||delta|| per packed voxel row
+    const int32_t* perm;         // packed voxel row -> voxel (null: identity)
     const int32_t* xperm;        // packed draw row -> draw (null: identity)
     const float* xs;             // draws in packed order, fp32 (row stride ldxs)
     int ldxs;
     const float* tbox;           // 64-draw tile feature boxes (null: draws not ordered)
-    const float* fy;             // voxel segment features per list row
+    const float* fy;             // voxel segment features per packed voxel row
     int64_t nt64;
     float Wc[3];
     float* keys;
@@ -1578,7 +1692,7 @@ struct FinItem {
     int32_t* out_idx;
     float* out_dist;
     const float* w;              // frame weights (device copy in the workspace)
-    const int32_t* rows;         // rescue pass: list row of each voxel position, or null (position = row)
+    const int32_t* rows;         // rescue pass: packed row of each queue position (lists by position), or null
     const int32_t* rcount;       // rescue pass: voxels queued
     int32_t* rq_rows;            // first pass of the split form: the rescue queue (null: no rescue)
     float* rq_thr;
@@ -1593,7 +1707,7 @@ struct BatchFin {
     int n_items;
     int sortcap;                 // largest sortcap of the batch (shared-memory sizing)
     int32_t* status;
-    int force_uncertified;       // test hook: a first net is never certified (rescue and exact scan run)
+    int force_rescue;            // test hook bits: 1 no first net is certified, 2 no rescue net is
 };
 
 // Exact fp32 distance sum_l w_l (y_l - x_l)^2 of a draw row in one fixed
@@ -1712,11 +1826,13 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
     const FinItem& P = B.item[it];
     const int64_t gpos = g - B.v_prefix[it];               // voxel position
     if (P.rows && gpos >= (int64_t)*P.rcount) return;
-    const int64_t j = P.rows ? (int64_t)P.rows[gpos] : gpos;   // list row
+    const int64_t j = P.rows ? (int64_t)P.rows[gpos] : gpos;   // packed row of the voxel
+    if (j < 0) return;                                          // rescue padding
+    const int64_t lr = P.rows ? gpos : j;                       // list row (the rescue lists by position)
     const int64_t vox = P.perm ? (int64_t)P.perm[j] : j;        // voxel of that row
-    float* kj = P.keys + j * P.C;
-    int32_t* ij = P.idx + j * P.C;
-    const int raw0 = P.cnt[j], raw1 = P.cnt[j + P.hstride];
+    float* kj = P.keys + lr * P.C;
+    int32_t* ij = P.idx + lr * P.C;
+    const int raw0 = P.cnt[lr], raw1 = P.cnt[lr + P.hstride];
     const int raw = raw0 | raw1;                          // an overflow flag from either half
     const int c0h = raw0 & 0x3FFFFFFF, c1h = raw1 & 0x3FFFFFFF;
     int cnt = c0h + c1h;
@@ -1743,7 +1859,7 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
     if (!scan) {
         // 1. the net: every draw outside it has computed key > T_out (both halves dropped only
         // keys above their own thresholds)
-        float T_out = fminf(P.thr[j], P.thr[j + P.hstride]);
+        float T_out = fminf(P.thr[lr], P.thr[lr + P.hstride]);
         constexpr int NR = 4;
         float yq[4], wq[4];
 #pragma unroll
@@ -1920,7 +2036,8 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
                 // every draw at exact distance <= d_k has key <= need_key(d_k)
                 need = need_key(dk, yn, P.c0[j], P.dn[j], SplitCoef{P.cacc, slack});
             }
-            cert = (T_out >= 2.9e38f || T_out >= need) && !(B.force_uncertified && P.rq_rows);
+            cert = (T_out >= 2.9e38f || T_out >= need) && !((B.force_rescue & 1) && P.rq_rows) &&
+                   !((B.force_rescue & 2) && P.rows);
         }
         if (!cert) {
             // split form, first pass: the net's d_k bounds the exact k-th distance, so
@@ -2051,7 +2168,7 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 // the draw-tile sequence number its TMA producers withhold (-1: none).
 uint64_t g_wait_ns = WAIT_NS_DEFAULT;
 int64_t g_withhold = -1;
-int g_force_uncertified = 0;   // test hook (abc_debug_force_rescue)
+int g_force_rescue = 0;        // test hook bits (abc_debug_force_rescue)
 cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
 int g_last_resident = 0;     // residency of the last configured fused-kernel variant
 int64_t g_last_grid = 0;     // grid of the last fused-kernel launch
@@ -2252,18 +2369,87 @@ struct BatchLayout {
     size_t total;
 };
 
-void make_batch_layout(const ScanSpec* sc, int n, int mode, const Tuning& tu, BatchLayout* B) {
-    const bool roomy = n == 1;   // a single scan may use roomier candidate lists
+// Split-form memory choices per scan, each within a budget:
+//  - candidate-list capacity 12 m k entries, m in {1, 2, 4}: a single scan takes the largest m
+//    whose lists fit LIST_BYTES_SINGLE; in a batch the smallest scans are raised first while
+//    the extra list bytes fit LIST_EXTRA_BYTES_BATCH (a small scan's lists are cheap, and its
+//    voxels are the most varied, so its nets are the longest);
+//  - centring groups: up to MAX_GROUPS per scan, each at least GROUP_MIN_TILES voxel tiles;
+//    every group costs a copy of the draw operand, so groups are added one at a time to the
+//    scan with the most voxels per copy byte, discounted by the groups it has (gain
+//    J / (G (G + 1)) per byte), while all copies fit the budget.
+constexpr double LIST_BYTES_SINGLE = 32.0e9, LIST_EXTRA_BYTES_BATCH = 16.0e9;
+constexpr double GROUP_COPIES_BYTES_SINGLE = 8.0e9, GROUP_COPIES_BYTES_BATCH = 48.0e9;
+constexpr int64_t GROUP_MIN_TILES = 2;
+
+void make_batch_layout(const ScanSpec* sc, int n, int mode, const Tuning& tu, BatchLayout* B, bool grouped = true) {
     B->n = n;
     int kp = 0;
     for (int i = 0; i < n; ++i) {
         const int w = make_layout(sc[i].J, sc[i].N, sc[i].L, sc[i].k, mode, tu).Kp;
         if (w > kp) kp = w;
     }
+    const bool split = mode != ABC_FP32;
+    auto list_bytes = [&](int i, int m) { return (double)sc[i].J * (12.0 * m * sc[i].k + 256.0) * 8.0; };
+    int mult[MAX_ITEMS];
+    for (int i = 0; i < n; ++i) mult[i] = 1;
+    if (split && n == 1) {
+        for (int m = 4; m > 1; m /= 2)
+            if (list_bytes(0, m) <= LIST_BYTES_SINGLE) {
+                mult[0] = m;
+                break;
+            }
+    } else if (split) {
+        int by_size[MAX_ITEMS];
+        for (int i = 0; i < n; ++i) by_size[i] = i;
+        for (int a = 1; a < n; ++a)
+            for (int b = a; b > 0 && sc[by_size[b]].J < sc[by_size[b - 1]].J; --b) {
+                const int t = by_size[b];
+                by_size[b] = by_size[b - 1];
+                by_size[b - 1] = t;
+            }
+        double extra = 0.0;
+        for (int a = 0; a < n; ++a) {
+            const int i = by_size[a];
+            for (int m = 4; m > 1; m /= 2) {
+                const double e = list_bytes(i, m) - list_bytes(i, 1);
+                if (extra + e <= LIST_EXTRA_BYTES_BATCH) {
+                    mult[i] = m;
+                    extra += e;
+                    break;
+                }
+            }
+        }
+    }
+    int groups[MAX_ITEMS], gmax[MAX_ITEMS];
+    double copy_bytes[MAX_ITEMS], total = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const int64_t g = vpet_ceil_div(sc[i].J > 0 ? sc[i].J : 1, GROUP_MIN_TILES * BM);
+        gmax[i] = (!split || !grouped) ? 1 : (int)(g < MAX_GROUPS ? g : MAX_GROUPS);
+        groups[i] = 1;
+        copy_bytes[i] = (double)vpet_round_up(sc[i].N > 0 ? sc[i].N : 1, 128) * kp * 2.0;
+        total += copy_bytes[i];
+    }
+    const double budget = n == 1 ? GROUP_COPIES_BYTES_SINGLE : GROUP_COPIES_BYTES_BATCH;
+    for (;;) {
+        int best = -1;
+        double best_gain = 0.0;
+        for (int i = 0; i < n; ++i) {
+            if (groups[i] >= gmax[i] || total + copy_bytes[i] > budget) continue;
+            const double gain = (double)sc[i].J / ((double)groups[i] * (groups[i] + 1)) / copy_bytes[i];
+            if (gain > best_gain) {
+                best_gain = gain;
+                best = i;
+            }
+        }
+        if (best < 0) break;
+        groups[best] += 1;
+        total += copy_bytes[best];
+    }
     // one K-width per launch: every scan is laid out at the widest
     size_t o = 256;
     for (int i = 0; i < n; ++i) {
-        B->lay[i] = make_layout(sc[i].J, sc[i].N, sc[i].L, sc[i].k, mode, tu, kp, roomy);
+        B->lay[i] = make_layout(sc[i].J, sc[i].N, sc[i].L, sc[i].k, mode, tu, kp, mult[i], groups[i]);
         B->off[i] = o;
         o = align256(o + B->lay[i].total);
     }
@@ -2275,22 +2461,31 @@ bool layout_consistent(const Layout& L) {
     const size_t off[] = {L.off_mu, L.off_part, L.off_ynorm, L.off_c0, L.off_dn, L.off_a, L.off_b, L.off_keys,
                           L.off_idx, L.off_cnt, L.off_thr, L.off_thr0, L.off_perm, L.off_feat, L.off_hist,
                           L.off_xperm, L.off_xfeat, L.off_xhist, L.off_fy, L.off_fx, L.off_tbox, L.off_ktile,
-                          L.off_kcount, L.off_xs, L.off_w, L.off_rq, L.off_rrow, L.off_rthr, L.off_ra};
-    const size_t len[] = {MAXL * 4, (size_t)L.npart * MAXL * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
-                          (size_t)L.Jp * L.Kp * 2, (size_t)L.Np * L.Kp * 2, (size_t)L.J * L.C * 4,
-                          (size_t)L.J * L.C * 4, (size_t)2 * L.Jp * 4, (size_t)2 * L.Jp * 4, (size_t)L.Jp * 4,
+                          L.off_kcount, L.off_xs, L.off_w, L.off_tgroup, L.off_rq, L.off_rrow, L.off_rthr,
+                          L.off_rq2, L.off_rtg, L.off_rcnt, L.off_rthrh, L.off_ra};
+    const size_t len[] = {(size_t)L.G * MAXL * 4, (size_t)L.G * L.npart * MAXL * 4, (size_t)L.Jp * 4, (size_t)L.Jp * 4,
+                          (size_t)L.Jp * 4, (size_t)L.Jp * L.Kp * 2, (size_t)L.G * L.Np * L.Kp * 2,
+                          (size_t)L.lrows * L.C * 4, (size_t)L.lrows * L.C * 4, (size_t)2 * L.Jp * 4, (size_t)2 * L.Jp * 4, (size_t)L.Jp * 4,
                           (size_t)L.Jp * 4, (size_t)3 * L.Jp * 4 + 32, (size_t)(ORDER_BUCKETS + ORDER_BUCKETS / 1024) * 4,
                           (size_t)L.Np * 4, (size_t)3 * L.Np * 4 + 32, (size_t)(ORDER_BUCKETS + ORDER_BUCKETS / 1024) * 4,
                           (size_t)3 * L.Jp * 4, (size_t)3 * L.Np * 4, (size_t)6 * L.nt64 * 4,
-                          (size_t)L.nvt * L.nt64 * 4, (size_t)L.nvt * 4, (size_t)L.Np * L.ldxs * 4, MAXL * 4, 8,
-                          (size_t)L.rcap * 4, (size_t)L.rcap * 8, (size_t)L.rcap * L.Kp * 2};
+                          (size_t)L.nvt * L.nt64 * 4, (size_t)L.nvt * 4, (size_t)L.Np * L.ldxs * 4, MAXL * 4,
+                          (size_t)L.nvt * 4, (size_t)(2 + 3 * L.G + 1) * 4, (size_t)L.rcapa * 4, (size_t)L.rcapa * 8,
+                          (size_t)L.rcapa * 12, (size_t)(L.rcapa / BM + 1) * 4, (size_t)L.rcapa * 8,
+                          (size_t)L.rcapa * 8, (size_t)L.rcapa * L.Kp * 2};
     const int n = (int)(sizeof off / sizeof off[0]);
     for (int i = 0; i < n; ++i) {
         if (off[i] + len[i] > (i + 1 < n ? off[i + 1] : L.total)) return false;
         if (i > 0 && off[i] < off[i - 1]) return false;
     }
+    // the rescue pass's lists (rcapa rows of Cr) lie in the candidate-list space
+    if (L.rcapa > 0 && (L.Cr < L.C || L.Cr % 2 || (double)L.Cr * L.rcapa > (double)L.lrows * L.C)) return false;
     return true;
 }
+
+// Voxels the first finalize may queue for the rescue pass, the same for every kernel that
+// reads the queue (the test hook's bit 4 limits it to a quarter of the voxels).
+int64_t queue_cap(const Layout& L) { return (g_force_rescue & 4) && L.rcap > L.J / 4 ? L.J / 4 : L.rcap; }
 
 int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws, size_t ws_bytes, float* dump,
               int64_t ld_dump, cudaStream_t s) {
@@ -2302,7 +2497,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     for (int i = 0; i < n; ++i)
         if ((rc = validate(sc[i], mode))) return rc;
     BatchLayout BL;
-    make_batch_layout(sc, n, mode, tu, &BL);
+    make_batch_layout(sc, n, mode, tu, &BL, dump == nullptr);   // the key dump keeps one centre
     for (int i = 0; i < n; ++i)
         if (!layout_consistent(BL.lay[i])) {
             vpet::set_error("discrepancy/top-k: internal workspace layout error (scan %d)", i);
@@ -2333,8 +2528,8 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         __nv_bfloat16 *A, *B, *RA;
         int32_t *idx, *cnt;
         float* wdev;
-        int32_t *rq, *rrow;
-        float* rthr;
+        int32_t *rq, *rrow, *tgroup, *rrow2, *rtg, *rcnt;
+        float *rthr, *rthr2, *rdk2, *rthrh;
     } ptr[MAX_ITEMS];
     for (int i = 0; i < n; ++i) {
         const Layout& L = BL.lay[i];
@@ -2371,6 +2566,13 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         p.rrow = (int32_t*)(base + L.off_rrow);
         p.rthr = (float*)(base + L.off_rthr);
         p.RA = (__nv_bfloat16*)(base + L.off_ra);
+        p.tgroup = (int32_t*)(base + L.off_tgroup);
+        p.rrow2 = (int32_t*)(base + L.off_rq2);
+        p.rthr2 = (float*)(p.rrow2 + L.rcapa);
+        p.rdk2 = p.rthr2 + L.rcapa;
+        p.rtg = (int32_t*)(base + L.off_rtg);
+        p.rcnt = (int32_t*)(base + L.off_rcnt);
+        p.rthrh = (float*)(base + L.off_rthrh);
         Weights W;
         memset(&W, 0, sizeof W);
         for (int l = 0; l < L.L; ++l) {
@@ -2378,11 +2580,8 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             W.sw[l] = sqrtf(sc[i].w[l]);
         }
         VPET_CUDA(cudaMemsetAsync(p.cnt, 0, (size_t)2 * L.Jp * sizeof(int32_t), s));
-        VPET_CUDA(cudaMemsetAsync(p.rq, 0, 2 * sizeof(int32_t), s));
-        k_colmean_part<<<L.npart, 256, 0, s>>>(sc[i].y, L.J, sc[i].ldy, L.L, p.part, L.npart);
-        VPET_LAUNCH_CHECK();
-        k_colmean_final<<<1, MAXL, 0, s>>>(p.part, L.npart, L.J, p.mu, W, p.wdev);
-        VPET_LAUNCH_CHECK();
+        VPET_CUDA(cudaMemsetAsync(p.rq, 0, (size_t)(2 + 3 * L.G + 1) * sizeof(int32_t), s));
+        if (L.rcapa > 0) VPET_CUDA(cudaMemsetAsync(p.rcnt, 0, (size_t)2 * L.rcapa * sizeof(int32_t), s));
         const bool order = dump == nullptr && L.J > 1;   // the debug dump keeps voxel order
         if (order) {
             k_order_init<<<(unsigned)vpet_ceil_div(ORDER_BUCKETS, 256), 256, 0, s>>>(p.mm, p.hist);
@@ -2399,9 +2598,17 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             k_order_scatter<<<gb, 256, 0, s>>>(p.feat, p.mm, L.J, 0, 1, p.hist, p.perm);
             VPET_LAUNCH_CHECK();
         }
+        // the centring groups' means (runs of the packed voxel order), and each voxel tile's group
+        k_colmean_part<<<(unsigned)(L.G * L.npart), 256, 0, s>>>(sc[i].y, L.J, sc[i].ldy, L.L, p.part, L.npart,
+                                                                 order ? p.perm : nullptr, L.Jg);
+        VPET_LAUNCH_CHECK();
+        k_colmean_final<<<(unsigned)L.G, MAXL, 0, s>>>(p.part, L.npart, L.J, L.Jg, p.mu, W, p.wdev);
+        VPET_LAUNCH_CHECK();
+        k_tile_groups<<<(unsigned)vpet_ceil_div(L.nvt, 256), 256, 0, s>>>(p.tgroup, L.nvt, L.Jg);
+        VPET_LAUNCH_CHECK();
         k_pack_y<<<(unsigned)vpet_ceil_div(L.Jp, 8), 256, 0, s>>>(sc[i].y, L.J, L.Jp, sc[i].ldy, L.L, L.Kp, mode, W,
-                                                                  p.mu, order ? p.perm : nullptr, p.A, p.ynorm, p.c0,
-                                                                  p.dn, p.fy);
+                                                                  p.mu, L.Jg, order ? p.perm : nullptr, p.A, p.ynorm,
+                                                                  p.c0, p.dn, p.fy);
         VPET_LAUNCH_CHECK();
         // draws in the same kind of order (alike draws in the same tiles, so that tile boxes are tight)
         const bool xorder = dump == nullptr && L.N > 1;
@@ -2420,9 +2627,10 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             k_order_scatter<<<gb, 256, 0, s>>>(p.xfeat, p.xmm, L.N, L.nlev, tu.pilot_stride, p.xhist, p.xperm);
             VPET_LAUNCH_CHECK();
         }
-        k_pack_x<<<(unsigned)vpet_ceil_div(L.Np, 8 * PACK_ROWS), 256, 0, s>>>(sc[i].x, L.N, L.Np, sc[i].ldx, L.L, L.Kp, mode, W,
-                                                                  p.mu, xorder ? p.xperm : nullptr, p.B, p.fx, p.xs,
-                                                                  L.ldxs);
+        k_pack_x<<<(unsigned)vpet_ceil_div(L.Np, 8 * PACK_ROWS), 256, 0, s>>>(sc[i].x, L.N, L.Np, sc[i].ldx, L.L, L.Kp,
+                                                                           mode, W, p.mu, L.G,
+                                                                           xorder ? p.xperm : nullptr, p.B, p.fx,
+                                                                           p.xs, L.ldxs);
         VPET_LAUNCH_CHECK();
         if (xorder) {
             k_tile_boxes<<<(unsigned)vpet_ceil_div(L.nt64, 8), 256, 0, s>>>(p.fx, L.N, L.nt64, p.tbox);
@@ -2448,7 +2656,12 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         int r;
         if ((r = make_tmap(&I.tmA, p.A, L.Jp, L.Kp, BM, 1))) return r;
         const int64_t Nn = L.N / stride;
-        if ((r = make_tmap(&I.tmB, p.B, stride == 1 ? L.Np : Nn, L.Kp, tu.bn, stride))) return r;
+        // the draw operand holds G copies of Np rows (one per centring group); a pilot's strided
+        // view takes every stride-th row of all of them (Np is a multiple of the stride)
+        if ((r = make_tmap(&I.tmB, p.B, stride == 1 ? (int64_t)L.G * L.Np : (int64_t)L.G * L.Np / stride, L.Kp,
+                           tu.bn, stride)))
+            return r;
+        (void)Nn;
         I.J = L.J;
         I.N = stride == 1 ? L.N : Nn;
         I.keys = p.keys;
@@ -2521,6 +2734,8 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             const int lim = (int)(4 * (int64_t)r + 256 < L.C ? 4 * (int64_t)r + 256 : L.C);
             const bool has_thr = lv + 1 < L.nlev;
             if ((rc = fill_item(T.item[m], i, 1, r, lim, has_thr ? ptr[i].thr0 : nullptr))) return rc;
+            T.tgroup[m] = L.G > 1 ? ptr[i].tgroup : nullptr;
+            T.grows[m] = L.Np;
             const int64_t npass = vpet_ceil_div(L.N, L.lev_stride[lv]);
             T.item[m].N = npass;
             T.item[m].ntiles = (int)vpet_ceil_div(npass, tu.bn);
@@ -2591,6 +2806,8 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         const int i = order[oi];
         const Layout& L = BL.lay[i];
         if ((rc = fill_item(T.item[oi], i, 1, L.kt, L.C, L.nlev > 0 ? ptr[i].thr0 : nullptr))) return rc;
+        T.tgroup[oi] = L.G > 1 ? ptr[i].tgroup : nullptr;
+        T.grows[oi] = L.Np;
         if (skip[i]) {
             T.item[oi].ktile = ptr[i].ktile;
             T.item[oi].kcount = ptr[i].kcount;
@@ -2651,9 +2868,9 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         if (L.rcap > 0 && dump == nullptr) {
             f.rq_rows = ptr[i].rrow;
             f.rq_thr = ptr[i].rthr;
-            f.rq_dk = ptr[i].rthr + L.rcap;
+            f.rq_dk = ptr[i].rthr + L.rcapa;
             f.rq_count = ptr[i].rq;
-            f.rq_cap = L.rcap;
+            f.rq_cap = queue_cap(L);
         }
         F.v_prefix[i + 1] = F.v_prefix[i] + L.J;
         if (L.sortcap > sortcap) sortcap = L.sortcap;
@@ -2661,7 +2878,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     F.n_items = n;
     F.sortcap = sortcap;
     F.status = status;
-    F.force_uncertified = g_force_uncertified;
+    F.force_rescue = g_force_rescue;
     int warps = 8;
     while (warps > 1 && (size_t)warps * sortcap * 8 > 64 * 1024) warps >>= 1;
     const size_t fsmem = (size_t)warps * (1024 + 2 * MAXL * 4 + (size_t)sortcap * 8);
@@ -2685,11 +2902,16 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     memset(&RB, 0, sizeof RB);
     for (int i = 0; i < n; ++i) {
         const Layout& L = BL.lay[i];
-        RB.item[i] = RescueItem{ptr[i].rq, ptr[i].rq + 1, ptr[i].rrow, L.rcap, ptr[i].A, ptr[i].RA, L.Kp, ptr[i].cnt,
-                                L.Jp};
+        const Ptrs& p = ptr[i];
+        RB.item[i] = RescueItem{p.rq,   p.rrow, p.rthr, p.rthr + L.rcapa, p.rrow2, p.rthr2, p.rdk2,
+                                p.rtg,  queue_cap(L), L.Jg, L.J, L.G, L.Kp, p.A, p.RA};
     }
     RB.n_items = n;
-    k_rescue_prep<<<(unsigned)num_sms() * 4, 256, 0, s>>>(RB);
+    k_rescue_count<<<(unsigned)num_sms() * 2, 256, 0, s>>>(RB);
+    VPET_LAUNCH_CHECK();
+    k_rescue_layout<<<(unsigned)n, 256, 0, s>>>(RB);
+    VPET_LAUNCH_CHECK();
+    k_rescue_place<<<(unsigned)num_sms() * 4, 256, 0, s>>>(RB);
     VPET_LAUNCH_CHECK();
     memset(&T, 0, sizeof T);
     for (int oi = 0; oi < n; ++oi) {
@@ -2701,12 +2923,12 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             KeepArgs K;
             memset(&K, 0, sizeof K);
             K.fy = p.fy;
-            K.thr0 = p.rthr;
+            K.thr0 = p.rthr2;
             K.ynorm = p.ynorm;
             K.tbox = p.tbox;
             K.ktile = p.ktile;
             K.kcount = p.kcount;
-            K.J = L.rcap;
+            K.J = L.rcapa;
             K.N = L.N;
             K.nt64 = L.nt64;
             for (int l = 0; l < L.L; ++l) K.Wc[(3 * l) / L.L] += sc[i].w[l];
@@ -2715,23 +2937,31 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             K.sc = split_coef(L);
             K.c0 = p.c0;
             K.dn = p.dn;
-            K.rows = p.rrow;
+            K.rows = p.rrow2;
             K.count = p.rq + 1;
             K.bn = tu.bn;
-            k_keep_tiles<<<(unsigned)(L.rcap / BM), 256, 0, s>>>(K);
+            k_keep_tiles<<<(unsigned)(L.rcapa / BM), 256, 0, s>>>(K);
             VPET_LAUNCH_CHECK();
         }
-        if ((rc = fill_item(T.item[oi], i, 1, L.kt, L.C, p.rthr))) return rc;
-        if ((rc = make_tmap(&T.item[oi].tmA, p.RA, L.rcap, L.Kp, BM, 1))) return rc;
-        T.item[oi].J = L.rcap;
-        T.item[oi].rows = p.rrow;
+        if ((rc = fill_item(T.item[oi], i, 1, L.kt, L.C, p.rthr2))) return rc;
+        if ((rc = make_tmap(&T.item[oi].tmA, p.RA, L.rcapa, L.Kp, BM, 1))) return rc;
+        T.item[oi].J = L.rcapa;
+        T.item[oi].rows = p.rrow2;
+        // lists by queue position, Cr entries each (shared, atomically appended: no compaction)
+        T.item[oi].C = L.Cr;
+        T.item[oi].C2 = tu.bn == 128 ? L.Cr / 2 : L.Cr;
+        T.item[oi].cnt = p.rcnt;
+        T.item[oi].thr = p.rthrh;
+        T.item[oi].hstride = (int)L.rcapa;
+        T.tgroup[oi] = L.G > 1 ? p.rtg : nullptr;   // each rescue tile lies in one centring group
+        T.grows[oi] = L.Np;
         if (xorder) {
             T.item[oi].ktile = p.ktile;
             T.item[oi].kcount = p.kcount;
             T.item[oi].kstride = L.nt64;
         }
         T.dyn_count[oi] = p.rq + 1;
-        T.vt_prefix[oi + 1] = T.vt_prefix[oi] + L.rcap / BM * RESCUE_SEGMENTS;
+        T.vt_prefix[oi + 1] = T.vt_prefix[oi] + L.rcapa / BM * RESCUE_SEGMENTS;
     }
     T.nseg = RESCUE_SEGMENTS;
     T.n_items = n;
@@ -2742,14 +2972,20 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     if ((rc = dispatch_tc<false>(nkb, tu.bn, T, tu.ctas_per_sm, s))) return rc;
     for (int i = 0; i < n; ++i) {
         FinItem& f = F.item[i];
-        f.rows = ptr[i].rrow;
+        const Layout& L = BL.lay[i];
+        f.rows = ptr[i].rrow2;
         f.rcount = ptr[i].rq + 1;
+        f.C = L.Cr;                                  // lists by queue position
+        f.C2 = tu.bn == 128 ? L.Cr / 2 : L.Cr;
+        f.cnt = ptr[i].rcnt;
+        f.thr = ptr[i].rthrh;
+        f.hstride = L.rcapa;
         f.rq_rows = nullptr;
         f.rq_thr = nullptr;
-        f.rq_dk = ptr[i].rthr + BL.lay[i].rcap;   // read by the rescue finalize
+        f.rq_dk = ptr[i].rdk2;   // read by the rescue finalize
         f.rq_count = nullptr;
         f.rq_cap = 0;
-        F.v_prefix[i + 1] = F.v_prefix[i] + BL.lay[i].rcap;
+        F.v_prefix[i + 1] = F.v_prefix[i] + L.rcapa;
     }
     k_finalize<<<(unsigned)vpet_ceil_div(F.v_prefix[n], warps), warps * 32, fsmem, s>>>(F);
     VPET_LAUNCH_CHECK();
@@ -2892,9 +3128,10 @@ extern "C" int abc_debug_inject_stall(int64_t withheld_tile, uint64_t wait_ns) {
     return ABC_OK;
 }
 
-extern "C" int abc_debug_force_rescue(int32_t on) {
+extern "C" int abc_debug_force_rescue(int32_t mode) {
     vpet::clear_error();
-    g_force_uncertified = on ? 1 : 0;
+    VPET_ARG(mode >= 0 && mode <= 7, "abc_debug_force_rescue: mode is a mask of 1, 2 and 4 (got %d)", mode);
+    g_force_rescue = mode;
     return ABC_OK;
 }
 

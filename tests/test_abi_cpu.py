@@ -228,3 +228,14 @@ def test_l1_validation_without_gpu(lib):
     neg[7] = -1.0
     assert call(w=neg.ctypes.data_as(P)) == _lib.ABC_ERR_ARG
     assert call(J=0, wsb=lib.abc_l1_workspace_size(0, 50)) == _lib.ABC_OK
+
+
+def test_force_rescue_hook_mask_without_gpu(lib):
+    """The second-pass test hook takes a mask of 1, 2 and 4; anything else is refused and
+    leaves the hook as it was (off)."""
+    from paper_2603_14859_b300 import _lib
+    assert lib.abc_debug_force_rescue(8) == _lib.ABC_ERR_ARG
+    assert b"mask" in lib.abc_last_error()
+    assert lib.abc_debug_force_rescue(-1) == _lib.ABC_ERR_ARG
+    assert lib.abc_debug_force_rescue(7) == _lib.ABC_OK
+    assert lib.abc_debug_force_rescue(0) == _lib.ABC_OK

@@ -165,21 +165,23 @@ def test_argument_errors():
     assert e.value.code == -3
 
 
-@pytest.mark.parametrize("prec,k", [(2, 10), (1, 50), (0, 2)])
-def test_uncertified_voxels_match_oracle(orc, prec, k):
+@pytest.mark.parametrize("prec,k,mode", [(2, 10, 1), (1, 50, 1), (2, 10, 3), (1, 50, 5), (0, 2, 1)])
+def test_uncertified_voxels_match_oracle(orc, prec, k, mode):
     """Voxels whose first net cannot be certified.  The FP32 form resolves them by the
     exact scan over the tiles whose segment-feature bound admits the net's k-th distance
     (with k = 2 many voxels of this case).  The split form queues them for its second
-    tensor-core pass (rescue) with the threshold their net's k-th distance asks for; the
-    test hook abc_debug_force_rescue fails every first net, so every voxel is queued, a
-    quarter of them fit the queue and the rest take the exact scan.  The accepted sets
-    still match the oracle's."""
+    tensor-core pass (rescue) with the threshold their net's k-th distance asks for.  The
+    test hook abc_debug_force_rescue steers the path: mode 1 fails every first net, so
+    every voxel of this 512-voxel scan is queued and the rescue resolves it; mode 3 fails
+    the rescue nets too, so every voxel then takes the exact scan bounded by its first
+    net's k-th distance; mode 5 limits the queue to a quarter of the voxels, so the rest
+    take the exact scan at once.  The accepted sets still match the oracle's."""
     from paper_2603_14859_b300 import _lib, api
     W, y, x = _gpu_case("raclopride_lpntpet", 512, 20000, orc)
     L = W.L
     ws = api.alloc_workspace(W.J, x.shape[0], L, k, prec)
     ws.fill_(0xFF)                                     # stale workspace contents must not matter
-    _lib.check(_lib.lib().abc_debug_force_rescue(1))
+    _lib.check(_lib.lib().abc_debug_force_rescue(mode))
     try:
         swaps, worst, scanned = _compare(orc, W, y, x, k, prec, ws=ws)
         st = api.topk_status(ws)
@@ -187,6 +189,10 @@ def test_uncertified_voxels_match_oracle(orc, prec, k):
         _lib.check(_lib.lib().abc_debug_force_rescue(0))
     if prec == 0:
         assert scanned > 0
+    elif mode == 1:
+        assert st[3] == W.J, f"status {st}"
+    elif mode == 3:
+        assert st[3] == W.J and st[1] == W.J, f"status {st}"
     else:
         assert st[3] == W.J // 4 and st[1] >= W.J - W.J // 4, f"status {st}"
     assert swaps == 0
