@@ -386,6 +386,10 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 __device__ __forceinline__ __nv_bfloat16 bf(float v) { return __float2bfloat16_rn(v); }
+// Two values rounded to bf16, a in the low half (the lower address)
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
+    return (uint32_t)__bfloat16_as_ushort(bf(a)) | ((uint32_t)__bfloat16_as_ushort(bf(b)) << 16);
+}
 
 // One warp per voxel row: A row of the GEMM and ||yh||^2.
 // ------------------------------------------------------------------ voxel order
@@ -646,6 +650,7 @@ __global__ void k_pack_y(const float* __restrict__ y, int64_t J, int64_t Jp, int
 // the exact re-score reads the draws in packed order.  The warp's four source
 // rows are read into shared memory with all their loads in flight together.
 constexpr int PACK_ROWS = 4;
+constexpr int PACK_KMAX = 256;                 // widest packed row (3 x 64 frames + 3 norm columns)
 constexpr int MAX_GROUPS = 16;                 // centring groups per scan
 // B holds G copies of the packed draws, copy g (rows [g Np, (g+1) Np)) centred on group
 // g's mean mu[g]; the fp32 copy xs and the segment features are written once.
@@ -654,11 +659,21 @@ __global__ void __launch_bounds__(256) k_pack_x(const float* __restrict__ x, int
                                                 const int32_t* __restrict__ xperm, __nv_bfloat16* __restrict__ B,
                                                 float* __restrict__ fx, float* __restrict__ xs, int ldxs) {
     __shared__ FrameConsts F;
-    __shared__ float s_mu[MAX_GROUPS][MAXL];
+    __shared__ __align__(16) float s_mu[MAX_GROUPS][MAXL];
     __shared__ float s_rows[8][PACK_ROWS][MAXL];
+    __shared__ __align__(16) __nv_bfloat16 s_rowbuf[8][PACK_KMAX];
     for (int e = threadIdx.x; e < G * MAXL; e += blockDim.x) s_mu[e / MAXL][e % MAXL] = mu[e];
     stage_frame_consts(F, W, mu, L);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // Each lane owns the frame pair l0 = 2 lane, l1 = l0 + 1 (zero weight past L); a
+    // packed row is assembled in the warp's row buffer (bf16, Kp columns; its columns past
+    // the norm parts stay zero) and leaves as 16-byte stores.
+    const int l0 = 2 * lane, l1 = l0 + 1;
+    const float sw0 = l0 < L ? F.sw[l0] : 0.0f, sw1 = l1 < L ? F.sw[l1] : 0.0f;
+    __nv_bfloat16* rb = s_rowbuf[wid];
+    const int aug = cols_per_frame(mode) * L;
+    for (int e = lane; e < Kp; e += 32) rb[e] = bf(0.0f);
+    __syncwarp();
     const int64_t nb = ((int64_t)blockIdx.x * 8 + wid) * PACK_ROWS;
     if (nb >= Np) return;
     {
@@ -687,8 +702,8 @@ __global__ void __launch_bounds__(256) k_pack_x(const float* __restrict__ x, int
         if (n >= Np) break;
         if (n >= N) {
             for (int g = 0; g < G; ++g) {
-                __nv_bfloat16* row = B + ((int64_t)g * Np + n) * Kp;
-                for (int e = lane; e < Kp; e += 32) row[e] = bf(0.0f);
+                uint2* row = (uint2*)(B + ((int64_t)g * Np + n) * Kp);
+                for (int e = lane; e < Kp / 4; e += 32) row[e] = make_uint2(0u, 0u);
             }
             continue;
         }
@@ -703,45 +718,49 @@ __global__ void __launch_bounds__(256) k_pack_x(const float* __restrict__ x, int
                 fx[3 * n + 2] = f[2];
             }
         }
+        const float x0 = xr[l0], x1 = xr[l1];
         for (int g = 0; g < G; ++g) {
-            const float* m = s_mu[g];
-            __nv_bfloat16* row = B + ((int64_t)g * Np + n) * Kp;
-            float ss = 0.0f, sr = 0.0f;
-            for (int l = lane; l < L; l += 32) {
-                const float v = F.sw[l] * (xr[l] - m[l]);
-                ss = fmaf(v, v, ss);
-                if (mode != ABC_FP32) {
-                    // the residual of the hi + lo split, r = v - hi - lo (exact in fp32)
-                    const float h = __bfloat162float(bf(v)), d1 = v - h;
-                    sr = fmaf(v, d1 - __bfloat162float(bf(d1)), sr);
+            const float2 m = *(const float2*)&s_mu[g][l0];
+            const float v0 = sw0 * (x0 - m.x), v1 = sw1 * (x1 - m.y);
+            const __nv_bfloat162 hp = __floats2bfloat162_rn(v0, v1);
+            const float h0 = __low2float(hp), h1 = __high2float(hp);
+            const float d0 = v0 - h0, d1 = v1 - h1;
+            const __nv_bfloat162 lp = __floats2bfloat162_rn(d0, d1);
+            float ss = fmaf(v1, v1, v0 * v0);
+            // split form: b.r with r = v - hi - lo, exact in fp32
+            float sr = fmaf(v1, d1 - __high2float(lp), v0 * (d0 - __low2float(lp)));
+            // -2 hi and -2 lo are exact in bf16
+            const __nv_bfloat162 ho = __floats2bfloat162_rn(-2.0f * h0, -2.0f * h1);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(-2.0f * __low2float(lp), -2.0f * __high2float(lp));
+            if (l1 < L) {
+                *(__nv_bfloat162*)&rb[l0] = ho;                       // 4-byte aligned (l0 even)
+                rb[L + l0] = __low2bfloat16(lo);
+                rb[L + l1] = __high2bfloat16(lo);
+                if (mode == ABC_FP32) {
+                    rb[2 * L + l0] = __low2bfloat16(ho);
+                    rb[2 * L + l1] = __high2bfloat16(ho);
                 }
+            } else if (l0 < L) {
+                rb[l0] = __low2bfloat16(ho);
+                rb[L + l0] = __low2bfloat16(lo);
+                if (mode == ABC_FP32) rb[2 * L + l0] = __low2bfloat16(ho);
             }
             ss = warp_sum(ss);
             // split form: the norm column carries ||b||^2 - 2 b.r, so that the key's error from the
             // draw row's split is 2 (a - b).r, which vanishes with the distance
             if (mode != ABC_FP32) ss -= 2.0f * warp_sum(sr);
-            const float n1 = __bfloat162float(bf(ss));
-            const float r1 = ss - n1;
-            const float n2 = __bfloat162float(bf(r1));
-            const float n3 = r1 - n2;
-            const int aug = cols_per_frame(mode) * L;
-            for (int e = lane; e < Kp; e += 32) {
-                float out = 0.0f;
-                if (e < aug) {
-                    const int l = e % L;
-                    const float v = F.sw[l] * (xr[l] - m[l]);
-                    const float hi = __bfloat162float(bf(v));
-                    if (mode == ABC_FP32) out = -2.0f * ((e >= L && e < 2 * L) ? (v - hi) : hi);
-                    else out = -2.0f * (e >= L ? (v - hi) : hi);
-                } else if (e == aug) {
-                    out = n1;
-                } else if (e == aug + 1) {
-                    out = n2;
-                } else if (e == aug + 2) {
-                    out = n3;
-                }
-                row[e] = bf(out);
+            if (lane == 0) {
+                const float n1 = __bfloat162float(bf(ss));
+                const float r1 = ss - n1;
+                const float n2 = __bfloat162float(bf(r1));
+                rb[aug] = bf(n1);
+                rb[aug + 1] = bf(n2);
+                rb[aug + 2] = bf(r1 - n2);
             }
+            __syncwarp();
+            if (lane < Kp / 8)
+                ((uint4*)(B + ((int64_t)g * Np + n) * Kp))[lane] = ((const uint4*)rb)[lane];
+            __syncwarp();
         }
     }
 }
@@ -789,7 +808,7 @@ __global__ void k_tile_boxes(const float* __restrict__ fx, int64_t N, int64_t nt
 
 struct KeepArgs {
     const float* fy;             // packed voxel rows x 3
-    const float* thr0;           // key threshold per packed row
+    const float* thr0;           // key threshold per packed row (null: none, every tile is kept)
     const float* ynorm;          // ||yh||^2 per packed row
     const float* tbox;           // 64-draw tile boxes
     int32_t* ktile;              // kept tile indices, nvt x nt64 (row stride nt64)
@@ -805,14 +824,21 @@ struct KeepArgs {
     const int32_t* rows;         // rescue pass: list row of each voxel position (thr0 is positional), or null
     const int32_t* count;        // rescue pass: queued voxels
     int bn;                      // draw-tile width of the pass, 64 or 128
+    int order;                   // list a voxel tile's kept tiles nearest first (at most KEEP_SORT_MAX)
 };
 
+// Kept-tile lists up to this long can be put in nearest-first order (a pilot's).
+constexpr int KEEP_SORT_MAX = 4096;
+
 // One block (256 threads) per 128-voxel tile: the voxel tile's feature box and
-// largest distance threshold, then the ordered list of draw tiles that cannot
-// be skipped.
+// largest distance threshold, then the list of draw tiles that cannot be skipped,
+// in draw order, or (order) by the distance between the centres of the voxel tile's
+// box and the draw tile's: a pilot that meets the nearest draws first keeps its
+// smallest keys early and rejects most later keys by its group-minimum test.
 __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ KeepArgs K) {
     __shared__ uint32_t box[7];                 // ordered-int min/max x 3, max threshold
     __shared__ int wcount[8];
+    __shared__ unsigned long long sk[KEEP_SORT_MAX];   // (centre distance, tile) of the kept tiles
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     const int64_t vt = blockIdx.x;
     const int64_t nv = K.count ? (int64_t)*K.count : K.J;   // voxel positions in use
@@ -826,10 +852,12 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
         const int64_t p = vt * BM + tid;
         const int64_t j = K.rows && p < nv ? (int64_t)K.rows[p] : p;   // packed row of the voxel (-1: none)
         if (p < nv && p < K.J && j >= 0) {
-            const float t = K.thr0[p];
+            const float t = K.thr0 ? K.thr0[p] : 3.0e38f;
             const float yn = K.ynorm[j];
             float td;
-            if (K.split) {
+            if (!K.thr0) {
+                td = 3.0e38f;
+            } else if (K.split) {
                 // every draw whose key can pass t lies within this distance
                 td = dist_ub(t, yn, K.c0[j], K.dn[j], K.sc);
             } else {
@@ -898,6 +926,54 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
         if (keep) K.ktile[vt * K.nt64 + pos] = (int32_t)t;
         base += tot;
         __syncthreads();
+    }
+    if (K.order && base > 1 && base <= KEEP_SORT_MAX) {
+        int n2 = 2;
+        while (n2 < base) n2 <<= 1;
+        int32_t* list = K.ktile + vt * K.nt64;
+        float yc[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) yc[c] = 0.5f * (ylo[c] + yhi[c]);
+        for (int i = tid; i < n2; i += 256) {
+            unsigned long long e = ~0ull;
+            if (i < base) {
+                const int64_t t = list[i];
+                float d = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float xl = 3.0e38f, xh = -3.0e38f;
+                    for (int q = 0; q < per; ++q) {
+                        const int64_t u = t * per + q;
+                        if (u < K.nt64) {
+                            xl = fminf(xl, K.tbox[6 * u + 2 * c]);
+                            xh = fmaxf(xh, K.tbox[6 * u + 2 * c + 1]);
+                        }
+                    }
+                    const float g = 0.5f * (xl + xh) - yc[c];
+                    if (K.Wc[c] > 0.0f) d += g * g / K.Wc[c];
+                }
+                e = ((unsigned long long)ord_f2u(d) << 32) | (uint32_t)t;
+            }
+            sk[i] = e;
+        }
+        __syncthreads();
+        // bitonic sort, ascending
+        for (int len = 2; len <= n2; len <<= 1)
+            for (int st = len >> 1; st > 0; st >>= 1) {
+                for (int i = tid; i < n2; i += 256) {
+                    const int o = i ^ st;
+                    if (o > i) {
+                        const bool up = (i & len) == 0;
+                        const unsigned long long a = sk[i], b = sk[o];
+                        if ((a > b) == up) {
+                            sk[i] = b;
+                            sk[o] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = tid; i < base; i += 256) list[i] = (int32_t)(uint32_t)sk[i];
     }
     if (tid == 0) {
         K.kcount[vt] = base;
@@ -2691,12 +2767,14 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     for (int i = 0; i < n; ++i) maxlev = BL.lay[i].nlev > maxlev ? BL.lay[i].nlev : maxlev;
     if (dump) maxlev = 0;
     // draw tiles a pass can skip, from the thresholds in thr0 (needs the ordered draws)
-    auto keep_tiles = [&](int i, int64_t npass, unsigned long long* tally) -> int {
+    // with_thr: the pass has thresholds in thr0 (else every tile is kept); order: nearest first
+    auto keep_tiles = [&](int i, int64_t npass, unsigned long long* tally, bool with_thr, bool order) -> int {
         const Layout& L = BL.lay[i];
         KeepArgs K;
         memset(&K, 0, sizeof K);
         K.fy = ptr[i].fy;
-        K.thr0 = ptr[i].thr0;
+        K.thr0 = with_thr ? ptr[i].thr0 : nullptr;
+        K.order = order ? 1 : 0;
         K.ynorm = ptr[i].ynorm;
         K.tbox = ptr[i].tbox;
         K.ktile = ptr[i].ktile;
@@ -2739,12 +2817,12 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             const int64_t npass = vpet_ceil_div(L.N, L.lev_stride[lv]);
             T.item[m].N = npass;
             T.item[m].ntiles = (int)vpet_ceil_div(npass, tu.bn);
-            if (has_thr) {
-                if ((rc = keep_tiles(i, npass, nullptr))) return rc;
-                T.item[m].ktile = ptr[i].ktile;
-                T.item[m].kcount = ptr[i].kcount;
-                T.item[m].kstride = L.nt64;
-            }
+            // the pass's draw tiles nearest first (all of them at the coarsest level, which has no
+            // threshold yet): the pilot's kept keys settle early (its result does not depend on the order)
+            if ((rc = keep_tiles(i, npass, nullptr, has_thr, true))) return rc;
+            T.item[m].ktile = ptr[i].ktile;
+            T.item[m].kcount = ptr[i].kcount;
+            T.item[m].kstride = L.nt64;
             T.vt_prefix[m + 1] = T.vt_prefix[m] + L.Jp / BM;
             // the finest split-form pilot reports its rank-rk key, which k_need_threshold turns
             // into the voxel's need threshold for the main pass
@@ -2798,7 +2876,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
     for (int i = 0; i < n; ++i) {
         const Layout& L = BL.lay[i];
         skip[i] = dump == nullptr && L.nlev > 0 && L.N > 1;
-        if (skip[i] && (rc = keep_tiles(i, L.N, tally))) return rc;
+        if (skip[i] && (rc = keep_tiles(i, L.N, tally, true, false))) return rc;
     }
     // main pass
     memset(&T, 0, sizeof T);
