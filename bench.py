@@ -397,13 +397,7 @@ def run_learned_bench(args, world, rank, local):
         model.local(yd, prop, M=M, k=k, sigma_scale=args.sigma_scale, out=outs)
         if rec is not None:
             rec[1].record(stream)
-        bad = (outs["ess"] < k / 4.0) | (outs["dmed"] > rel * outs["ynorm"])
-        fb = torch.nonzero(bad).flatten()
-        if fb.numel():
-            r = g.run(yd.index_select(0, fb).contiguous())
-            for key in ("mean", "sd", "lo", "hi"):
-                outs[key].index_copy_(0, fb, r[key])
-        return fb.numel()
+        return learned.fallback_to_global(outs, yd, k, g, rel)[1]
 
     for _ in range(args.warmup):
         step(y)

@@ -383,7 +383,17 @@ int abc_response_cri(const float* theta_dev, int32_t ldtheta, const int32_t* idx
  * coordinate u_p = (theta_p - lo_p) / (hi_p - lo_p); mu is clamped to [-3, 4]
  * and log sigma to [-7, 2] wherever they are used.  All buffers are device
  * memory owned by the caller; calls are asynchronous on `stream`.
+ * The network's matrix products run on the tensor cores (bf16 products, fp32
+ * accumulation): every fp32 activation or gradient operand is split into three
+ * bf16 parts (hi + mid + lo, its full 24 bits) and a weight is its bf16 value,
+ * so a product equals the fp32 sum up to accumulation rounding (terms of order
+ * 2^-24 relative are dropped where both operands are split).
  * ------------------------------------------------------------------------- */
+
+/* Bounded waits of the network's tensor-core products: *timeout_host = 1 if one of them
+ * ran out since the last query (the outputs of that call are then not valid), else 0;
+ * the flag is cleared.  Synchronous. */
+int abc_mlp_status(int32_t* timeout_host);
 
 /* Number of fp32 parameters of a D -> H -> H -> O network (0 on bad sizes). */
 size_t abc_mlp_param_count(int32_t D, int32_t H, int32_t O);
@@ -483,6 +493,44 @@ int abc_local_abc(const float* y_dev, int64_t J, int32_t ldy, int32_t L, const f
                   float* sd_dev,
                   float* qlo_dev, float* qhi_dev, float* ess_dev, float* dmed_dev, float* ynorm_dev,
                   float* u_dump_dev, float* d_dump_dev, void* stream);
+
+/* Reliability check of the learned path (a workload extension with no counterpart in the
+ * paper): the voxels whose local run is handed to the global path (Algorithm 1).
+ * For j < J, voxel j falls back when !(ess_dev[j] >= k / 4) (a NaN ESS included) or, with
+ * rel_max > 0, when dmed_dev[j] > rel_max * ynorm_dev[j] (the abc_local_abc outputs;
+ * dmed_dev and ynorm_dev may be NULL when rel_max <= 0).  rows_dev (J int32, device)
+ * receives the fallback voxels in ascending order, *count_dev (one int32, device) their
+ * number; nothing is read back, so the call is one asynchronous enqueue on stream.
+ * scratch_dev: abc_fallback_scratch_size(J) bytes of device memory, caller-owned.
+ * ABC_ERR_ARG for J outside 1 .. 2^31 - 1, k < 1, a null pointer or a short scratch. */
+size_t abc_fallback_scratch_size(int64_t J);
+int abc_fallback_rows(const float* ess_dev, const float* dmed_dev, const float* ynorm_dev, int64_t J, int32_t k,
+                      float rel_max, int32_t* rows_dev, int32_t* count_dev, void* scratch_dev, size_t scratch_bytes,
+                      void* stream);
+
+/* Row moves for the fallback (fp32, device): gather dst[i, 0:width) = src[rows[i], 0:width),
+ * scatter dst[rows[i], 0:width) = src[i, 0:width), for i < min(*count_dev, max_rows) (the
+ * count is read on the device, so a count from abc_fallback_rows needs no host copy).
+ * Row strides ld_src, ld_dst >= width, in floats.  ABC_ERR_ARG on a null pointer or bad
+ * sizes. */
+int abc_gather_rows(const float* src_dev, int32_t ld_src, const int32_t* rows_dev, const int32_t* count_dev,
+                    int64_t max_rows, int32_t width, float* dst_dev, int32_t ld_dst, void* stream);
+int abc_scatter_rows(const float* src_dev, int32_t ld_src, const int32_t* rows_dev, const int32_t* count_dev,
+                     int64_t max_rows, int32_t width, float* dst_dev, int32_t ld_dst, void* stream);
+
+/* Calibration of the fallback threshold: over voxels j < J, the relative median accepted
+ * distance rel_j = dist_dev[j k + (k - 1) / 2] / sum_l w_l y_jl^2 (dist_dev: J x k accepted
+ * distances of the global path, ascending per voxel; y_dev: J x L TACs, row stride ldy;
+ * w_host: L frame weights), and its q-quantile by linear interpolation between the order
+ * statistics floor(h) and floor(h) + 1, h = q (J - 1) (numpy's default), both found exactly
+ * by a radix selection on the device; the result goes to *out_host (blocks on stream).
+ * scratch_dev: abc_quantile_scratch_size(J) bytes.  ABC_ERR_ARG for J outside
+ * 1 .. 2^31 - 1, k < 1, L outside 1 .. 64, ldy < L, q outside [0, 1], a null pointer or a
+ * short scratch. */
+size_t abc_quantile_scratch_size(int64_t J);
+int abc_median_rel_quantile(const float* dist_dev, int64_t J, int32_t k, const float* y_dev, int32_t ldy, int32_t L,
+                            const float* w_host, double q, float* out_host, void* scratch_dev, size_t scratch_bytes,
+                            void* stream);
 
 /* Description of the last error on this thread ("" if none). */
 const char* abc_last_error(void);

@@ -31,7 +31,9 @@ EXPORTS = [
     "abc_mlp_loss_grad", "abc_adam_update", "abc_add_noise", "abc_local_abc_smem_bytes", "abc_local_abc",
     "abc_unit_box", "abc_topk_work", "abc_local_abc_table", "abc_response_cri",
     "abc_l1_workspace_size", "abc_discrepancy_topk_l1", "abc_l1_status", "abc_topk_status_noalloc",
-    "abc_debug_inject_stall", "abc_debug_force_rescue",
+    "abc_debug_inject_stall", "abc_debug_force_rescue", "abc_fallback_scratch_size", "abc_fallback_rows",
+    "abc_gather_rows", "abc_scatter_rows", "abc_quantile_scratch_size", "abc_median_rel_quantile",
+    "abc_mlp_status",
 ]
 
 
@@ -118,12 +120,22 @@ def lib():
     L.abc_l1_status.argtypes = [P, i64, i32, P]
     L.abc_local_abc.argtypes = [P, i64, i32, i32, P, P, P, i32, f64, P, P, P, i32, i32, f32, u64,
                                 P, P, P, P, P, P, P, P, P, P]
+    L.abc_fallback_scratch_size.argtypes = [i64]
+    L.abc_fallback_scratch_size.restype = sz
+    L.abc_fallback_rows.argtypes = [P, P, P, i64, i32, f32, P, P, P, sz, P]
+    L.abc_gather_rows.argtypes = [P, i32, P, P, i64, i32, P, i32, P]
+    L.abc_scatter_rows.argtypes = [P, i32, P, P, i64, i32, P, i32, P]
+    L.abc_quantile_scratch_size.argtypes = [i64]
+    L.abc_quantile_scratch_size.restype = sz
+    L.abc_median_rel_quantile.argtypes = [P, i64, i32, P, i32, i32, P, f64, P, P, sz, P]
+    L.abc_mlp_status.argtypes = [P]
     for fn in ["abc_feng_input", "abc_sample_prior", "abc_simulate", "abc_discrepancy_topk", "abc_topk_status",
                "abc_model_select", "abc_summarize", "abc_debug_gemm_keys", "abc_profile_events",
                "abc_discrepancy_topk_noalloc", "abc_default_tuning", "abc_set_default_tuning",
                "abc_batch_discrepancy_topk", "abc_launch_info", "abc_mlp_init", "abc_mlp_features",
                "abc_mlp_forward", "abc_mlp_loss_grad", "abc_adam_update", "abc_add_noise", "abc_local_abc", "abc_unit_box", "abc_topk_work",
                "abc_local_abc_table", "abc_response_cri", "abc_discrepancy_topk_l1", "abc_l1_status",
+               "abc_fallback_rows", "abc_gather_rows", "abc_scatter_rows", "abc_median_rel_quantile", "abc_mlp_status",
                "abc_topk_status_noalloc", "abc_debug_inject_stall", "abc_debug_force_rescue"]:
         getattr(L, fn).restype = ctypes.c_int
     _lib = L

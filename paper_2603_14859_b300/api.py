@@ -351,3 +351,44 @@ def local_abc(y, L, w, prop, table, a_max, cp_frames, lo, hi, M, k, seed, sigma_
                               _ptr(out["hi"]), _ptr(out["ess"]), _ptr(out["dmed"]), _ptr(out["ynorm"]),
                               _ptr(out.get("u")), _ptr(out.get("d")), _stream(stream)))
     return out
+
+
+def fallback_rows(ess, dmed, ynorm, k, rel_max=None, stream=None):
+    """Voxels the learned path hands to the global path: ESS below k/4 (or NaN), or (rel_max
+    given) a median accepted distance above rel_max times sum_l w_l y_l^2.  Returns (rows, count):
+    a device int32 tensor whose first count entries are those voxels, ascending, and the count
+    as a one-element device tensor."""
+    J = ess.shape[0]
+    rows = torch.empty(J, dtype=torch.int32, device="cuda")
+    count = torch.empty(1, dtype=torch.int32, device="cuda")
+    scratch = torch.empty(lib().abc_fallback_scratch_size(J), dtype=torch.uint8, device="cuda")
+    check(lib().abc_fallback_rows(_ptr(ess), _ptr(dmed), _ptr(ynorm), J, k, float(rel_max or 0.0), _ptr(rows),
+                                  _ptr(count), _ptr(scratch), scratch.numel(), _stream(stream)))
+    return rows, count
+
+
+def gather_rows(src, rows, count, n_rows, stream=None):
+    """Device rows src[rows[i]] for i < count (count a device tensor; n_rows bounds it) -> (n_rows, width)."""
+    out = torch.empty((n_rows, src.shape[1]), dtype=torch.float32, device="cuda")
+    check(lib().abc_gather_rows(_ptr(src), src.stride(0), _ptr(rows), _ptr(count), n_rows, src.shape[1], _ptr(out),
+                                out.stride(0), _stream(stream)))
+    return out
+
+
+def scatter_rows(src, rows, count, dst, stream=None):
+    """dst[rows[i]] = src[i] for i < count (device count, at most src.shape[0]), in place."""
+    check(lib().abc_scatter_rows(_ptr(src), src.stride(0), _ptr(rows), _ptr(count), src.shape[0], src.shape[1],
+                                 _ptr(dst), dst.stride(0), _stream(stream)))
+    return dst
+
+
+def median_rel_quantile(dist, k, y, L, w, q, stream=None):
+    """The q-quantile (numpy's linear interpolation) over voxels of the median accepted distance
+    (column (k-1)/2 of dist) relative to sum_l w_l y_l^2."""
+    J = dist.shape[0]
+    w = _np(w, np.float32)
+    scratch = torch.empty(lib().abc_quantile_scratch_size(J), dtype=torch.uint8, device="cuda")
+    out = ctypes.c_float(0.0)
+    check(lib().abc_median_rel_quantile(_ptr(dist), J, k, _ptr(y), y.stride(0), L, _vp(w), float(q), ctypes.byref(out),
+                                        _ptr(scratch), scratch.numel(), _stream(stream)))
+    return float(out.value)

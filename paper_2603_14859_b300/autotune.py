@@ -5,7 +5,9 @@ The fused kernel exposes four launch choices (`abc_tuning`): draws per tile
 SM, the draw stride between pilot levels and the pilot safety factor.  None
 changes results, only speed.  `tune()` times every candidate on a calibration
 view of the batch (each scan truncated to a bounded number of voxels and
-draws, without copying) and returns the fastest; results are cached in a JSON
+draws, without copying), then times the fastest few on the whole batch (the
+view misranks choices whose cost depends on the full draw count, such as the
+pilot stride) and returns the fastest there; results are cached in a JSON
 file keyed by the GPU and a coarse signature of the batch shape.
 """
 from __future__ import annotations
@@ -75,8 +77,21 @@ def _calibration_structs(batch, max_voxels: int, max_draws: int):
     return arr, ws_w
 
 
+def _time_call(L, arr, n, precision, t, ws, s, reps):
+    times = []
+    for _ in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        _lib.check(L.abc_batch_discrepancy_topk(arr, n, precision, ctypes.byref(t), ctypes.c_void_p(ws.data_ptr()),
+                                                ws.numel(), ctypes.c_void_p(s.cuda_stream)))
+        e1.record(s)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times[1:])
+
+
 def tune(batch, precision: int | None = None, max_voxels: int = 4096, max_draws: int = 400_000, reps: int = 2,
-         use_cache: bool = True, verbose: bool = False) -> dict:
+         finalists: int = 3, use_cache: bool = True, verbose: bool = False) -> dict:
     """Pick the fastest tuning for `batch` (a pipeline.BatchPipeline with inputs set)."""
     precision = batch.precision if precision is None else precision
     key = signature(batch, precision)
@@ -92,22 +107,23 @@ def tune(batch, precision: int | None = None, max_voxels: int = 4096, max_draws:
     results = []
     for cand in CANDIDATES:
         t = _lib.Tuning(cand["bn"], cand["ctas_per_sm"], cand["pilot_stride"], cand["pilot_factor"])
-        times = []
-        for _ in range(reps + 1):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            _lib.check(L.abc_batch_discrepancy_topk(arr, len(batch.runs), precision, ctypes.byref(t),
-                                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(),
-                                                    ctypes.c_void_p(s.cuda_stream)))
-            e1.record(s)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-        ms = statistics.median(times[1:])
+        ms = _time_call(L, arr, len(batch.runs), precision, t, ws, s, reps)
         results.append((ms, cand))
         if verbose:
             print(f"  tune {cand}: {ms:.2f} ms")
-    best = min(results, key=lambda r: r[0])
+    results.sort(key=lambda r: r[0])
+    # the finalists on the whole batch (its own structs and workspace)
+    full = []
+    if finalists > 1 and batch._scan_structs is not None and batch.ws is not None:
+        for _, cand in results[:finalists]:
+            t = _lib.Tuning(cand["bn"], cand["ctas_per_sm"], cand["pilot_stride"], cand["pilot_factor"])
+            ms = _time_call(L, batch._scan_structs, len(batch.runs), precision, t, batch.ws, s, 1)
+            full.append((ms, cand))
+            if verbose:
+                print(f"  full batch {cand}: {ms:.2f} ms")
+    best = min(full, key=lambda r: r[0]) if full else results[0]
     if use_cache:
-        cache[key] = {"tuning": best[1], "ms": best[0], "candidates": [[m, c] for m, c in results]}
+        cache[key] = {"tuning": best[1], "ms": best[0], "candidates": [[m, c] for m, c in results],
+                      "finalists": [[m, c] for m, c in full]}
         _save(cache)
     return best[1]

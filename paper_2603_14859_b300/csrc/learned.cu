@@ -26,14 +26,14 @@
 
 #include "common.cuh"
 #include "select.cuh"
+#include "tc_ptx.cuh"
 
 using namespace vpet;
 
 namespace {
 
 constexpr int MAXL = 64;
-constexpr int GT = 64;          // GEMM tile (M and N)
-constexpr int GK = 16;          // GEMM K step
+constexpr int GT = 64;          // unit of the split-K slab space
 constexpr int LA_THREADS = 512;
 constexpr int LA_P = 4;         // K1, k2, k3, Vb
 constexpr int LA_C = LA_P + 1;  // ... and K_i
@@ -45,7 +45,6 @@ __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(
 __device__ __forceinline__ float gelu_d(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
-__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ float nphi(float z) { return 0.39894228040143268f * expf(-0.5f * z * z); }
 
 // P(a < Z < b), a < b, without cancellation in either tail.
@@ -83,10 +82,19 @@ __global__ void k_features(const float* __restrict__ y, int64_t J, int ldy, int 
 
 // ------------------------------------------------------------------ GEMM
 // C[m, n] = sum_k A(m, k) B(k, n) (+ bias[n]), A(m, k) = gelu?(A[m sam + k sak]),
-// B(k, n) = gelu?/bf16?(B[k sbk + n sbn]).  64 x 64 tiles, 256 threads, 4 x 4
-// outputs per thread.  With split-K (gridDim.z > 1) each z-slice stores its
-// partial sums in its own M x N slab and k_splitk_sum adds the slabs in z
-// order, so the result does not depend on the order the blocks finish in.
+// B(k, n) = gelu?/bf16?(B[k sbk + n sbn]), on the tensor cores (tcgen05, fp32 accumulators
+// in TMEM).  The fp32 operands are split into bf16 parts: an activation (or gradient) into
+// three, hi + mid + lo, which hold its 24 bits; a weight, rounded to bf16 at every use, is
+// one part.  Products of parts are exact in fp32, so C equals the fp32 sum up to the
+// accumulation's rounding: with a one-part B the three products hi.B, mid.B, lo.B; with
+// two three-part operands the six whose weight is at least 2^-16 (hi.hi, hi.mid, mid.hi,
+// hi.lo, mid.mid, lo.hi), leaving terms of order 2^-24 relative.  One CTA computes a
+// 128 x BN tile: its 256 threads load a 64-wide K block of A and B, apply GELU / the
+// rounding, split and store the parts in the 128-byte-swizzled K-major layout of the
+// MMA's shared-memory descriptors (two stages, so loading one block overlaps the MMAs of
+// the previous), and one thread issues the MMAs.  With split-K (gridDim.z > 1) each
+// z-slice stores its partial sums in its own M x N slab and k_splitk_sum adds the slabs in
+// z order, so the result does not depend on the order the blocks finish in.
 struct GemmArgs {
     const float* A;
     int64_t sam, sak;
@@ -98,7 +106,7 @@ struct GemmArgs {
     int M, N, K;
     int actA;    // 1 = GELU of the loaded A value
     int actB;    // 1 = GELU of the loaded B value
-    int roundB;  // 1 = B rounded to bf16 (weights)
+    int roundB;  // 1 = B rounded to bf16 (weights: one part)
     float* part = nullptr;     // split-K slabs (null: no split)
     int64_t part_cap = 0;      // floats available there
 };
@@ -107,68 +115,184 @@ struct GemmArgs {
 // three waves of 64 x 64 tiles on up to 192 SMs
 constexpr int64_t GEMM_PART_FLOATS = 3LL * 192 * GT * GT;
 
-__global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int kchunk) {
-    __shared__ float sa[GK][GT + 4];
-    __shared__ float sb[GK][GT + 4];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-    const int kbeg = blockIdx.z * kchunk, kend = min(g.K, kbeg + kchunk);
-    float acc[4][4] = {};
-    for (int k0 = kbeg; k0 < kend; k0 += GK) {
-        for (int e = threadIdx.x; e < GK * GT; e += 256) {
-            // consecutive threads walk the unit-stride dimension of the operand
-            int kk, mm;
-            if (g.sak == 1) { kk = e % GK; mm = e / GK; } else { kk = e / GT; mm = e % GT; }
-            const int m = m0 + mm, k = k0 + kk;
-            float a = 0.0f;
-            if (m < g.M && k < kend) {
-                a = g.A[m * g.sam + k * g.sak];
-                if (g.actA) a = gelu(a);
-            }
-            sa[kk][mm] = a;
-        }
-        for (int e = threadIdx.x; e < GK * GT; e += 256) {
-            int kk, nn;
-            if (g.sbk == 1) { kk = e % GK; nn = e / GK; } else { kk = e / GT; nn = e % GT; }
-            const int n = n0 + nn, k = k0 + kk;
-            float b = 0.0f;
-            if (n < g.N && k < kend) {
-                b = g.B[k * g.sbk + n * g.sbn];
-                if (g.actB) b = gelu(b);
-                if (g.roundB) b = bf16r(b);
-            }
-            sb[kk][nn] = b;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; ++kk) {
-            float av[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) { av[i] = sa[kk][ty * 4 + i]; bv[i] = sb[kk][tx * 4 + i]; }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(av[i], bv[q], acc[i][q]);
-        }
-        __syncthreads();
+constexpr int TC_M = 128;                       // tile rows (TMEM lanes)
+constexpr int TC_KB = 64;                       // K per block: one 128-byte row of bf16
+constexpr int TC_THREADS = 256;                 // 8 warps: two per TMEM lane quarter
+constexpr int TC_APARTS = 3;
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // bound on every barrier wait
+
+struct TcGemm {
+    GemmArgs g;
+    int bn;                      // tile width in N (multiple of 16, <= 256)
+    int pb;                      // parts of B: 1 (weights) or 3
+    int kchunk;                  // K per z-slice (a multiple of TC_KB)
+    int tmem_cols;
+    int* err;                    // set when a bounded wait ran out
+};
+
+__device__ int g_mlp_timeout = 0;
+
+// byte offset of element (r, k), k < 64, in a 128-byte-swizzled K-major tile
+__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
+    return (uint32_t)r * 128u + ((((uint32_t)k >> 3) ^ ((uint32_t)r & 7u)) << 4) + ((uint32_t)k & 7u) * 2u;
+}
+
+__device__ __forceinline__ void split3(float v, __nv_bfloat16 (&p)[3]) {
+    p[0] = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(p[0]);
+    p[1] = __float2bfloat16_rn(r1);
+    p[2] = __float2bfloat16_rn(r1 - __bfloat162float(p[1]));
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const __grid_constant__ TcGemm T) {
+    extern __shared__ __align__(1024) uint8_t tc_raw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tmem_base;
+    const GemmArgs& g = T.g;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bn = T.bn, pb = T.pb;
+    const uint32_t a_bytes = TC_M * 128, b_bytes = (uint32_t)bn * 128;
+    const uint32_t stage_bytes = TC_APARTS * a_bytes + (uint32_t)pb * b_bytes;
+    const int64_t m0 = (int64_t)blockIdx.y * TC_M, n0 = (int64_t)blockIdx.x * bn;
+    const int kbeg = blockIdx.z * T.kchunk, kend = min(g.K, kbeg + T.kchunk);
+    const int nkb = (kend - kbeg + TC_KB - 1) / TC_KB;
+    if (tid == 0) {
+        ptx::mbar_init(ptx::smem_u32(&bar[0]), 1);
+        ptx::mbar_init(ptx::smem_u32(&bar[1]), 1);
+        ptx::fence_mbar_init();
     }
+    if (warp == 0) {
+        ptx::tmem_alloc(ptx::smem_u32(&tmem_base), (uint32_t)T.tmem_cols);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = ptx::idesc_bf16_f32(TC_M, bn);
+    bool failed = false;
+    int issued = -1;                             // last K block whose MMAs were issued
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int st = kb & 1;
+        uint8_t* sa = sm + st * stage_bytes;
+        uint8_t* sb = sa + TC_APARTS * a_bytes;
+        // the MMAs two blocks back read this stage
+        bool ok = true;
+        if (kb >= 2) ok = ptx::mbar_wait(ptx::smem_u32(&bar[st]), ((kb - 2) >> 1) & 1, TC_WAIT_NS);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        const int k0 = kbeg + kb * TC_KB;
+        // eight independent loads in flight per thread, then their GELU, split and stores
+        constexpr int CH = 8;
+        for (int e0 = tid; e0 < TC_M * TC_KB; e0 += TC_THREADS * CH) {
+            float v[CH];
+            uint32_t off[CH];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int m = m0 + ty * 4 + i;
-        if (m >= g.M) continue;
+            for (int u = 0; u < CH; ++u) {
+                const int e = e0 + u * TC_THREADS;
+                int r, kk;
+                if (g.sak == 1) { r = e >> 6; kk = e & 63; } else { r = e & 127; kk = e >> 7; }
+                const int64_t m = m0 + r;
+                const int k = k0 + kk;
+                off[u] = sw128_off(r, kk);
+                v[u] = (m < g.M && k < kend) ? g.A[m * g.sam + (int64_t)k * g.sak] : 0.0f;
+            }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int n = n0 + tx * 4 + q;
-            if (n >= g.N) continue;
-            float v = acc[i][q];
-            if (gridDim.z > 1) {
-                g.part[((int64_t)blockIdx.z * g.M + m) * g.N + n] = v;
-            } else {
-                if (g.bias) v += g.bias[n];
-                g.C[(int64_t)m * g.ldc + n] = v;
+            for (int u = 0; u < CH; ++u) {
+                __nv_bfloat16 p[3];
+                split3(g.actA ? gelu(v[u]) : v[u], p);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) *(__nv_bfloat16*)(sa + q * a_bytes + off[u]) = p[q];
+            }
+        }
+        for (int e0 = tid; e0 < bn * TC_KB; e0 += TC_THREADS * CH) {
+            float v[CH];
+            uint32_t off[CH];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int e = e0 + u * TC_THREADS;
+                int r, kk;
+                if (g.sbk == 1) { r = e >> 6; kk = e & 63; } else { r = e % bn; kk = e / bn; }
+                const int64_t n = n0 + r;
+                const int k = k0 + kk;
+                off[u] = e < bn * TC_KB ? sw128_off(r, kk) : 0xFFFFFFFFu;
+                v[u] = (e < bn * TC_KB && n < g.N && k < kend) ? g.B[(int64_t)k * g.sbk + n * g.sbn] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                if (off[u] == 0xFFFFFFFFu) continue;
+                const float b = g.actB ? gelu(v[u]) : v[u];
+                if (pb == 1) {
+                    *(__nv_bfloat16*)(sb + off[u]) = __float2bfloat16_rn(b);
+                } else {
+                    __nv_bfloat16 p[3];
+                    split3(b, p);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) *(__nv_bfloat16*)(sb + q * b_bytes + off[u]) = p[q];
+                }
+            }
+        }
+        // the generic-proxy stores must be visible to the tensor cores' async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            ptx::tc_fence_after();
+            // (A part, B part) products: three with a one-part B, six with three parts
+            const int np = pb == 1 ? 3 : 6;
+            const int pa_of[6] = {0, 1, 2, 0, 1, 0}, pb_of[6] = {0, 0, 0, 1, 1, 2};
+            for (int q = 0; q < np; ++q) {
+                const uint32_t abase = ptx::smem_u32(sa + pa_of[q] * a_bytes);
+                const uint32_t bbase = ptx::smem_u32(sb + (pb == 1 ? 0 : pb_of[q]) * b_bytes);
+#pragma unroll
+                for (int ks = 0; ks < TC_KB / 16; ++ks)
+                    ptx::mma_bf16(tmem, ptx::desc_sw128(abase + ks * 32), ptx::desc_sw128(bbase + ks * 32), idesc,
+                                  (kb > 0 || q > 0 || ks > 0) ? 1u : 0u);
+            }
+            ptx::mma_commit(ptx::smem_u32(&bar[st]));
+        }
+        issued = kb;
+    }
+    // the last commit covers every MMA this CTA issued
+    if (issued >= 0) {
+        const bool ok = ptx::mbar_wait(ptx::smem_u32(&bar[issued & 1]), (issued >> 1) & 1, TC_WAIT_NS);
+        if (__syncthreads_or(!ok)) failed = true;
+    }
+    ptx::tc_fence_after();
+    if (!failed && issued >= 0) {
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows), every other 32-column chunk
+        const int quarter = warp & 3;
+        const int64_t m = m0 + quarter * 32 + lane;
+        for (int c0 = (warp >> 2) * 32; c0 < bn; c0 += 64) {
+            uint32_t r[32];
+            ptx::tmem_ld32_async(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, r);
+            ptx::tmem_wait_ld();
+            ptx::tmem_fence_regs(r);
+            if (m < g.M) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int64_t n = n0 + c0 + i;
+                    if (n >= g.N) break;
+                    float v = __uint_as_float(r[i]);
+                    if (gridDim.z > 1) {
+                        g.part[((int64_t)blockIdx.z * g.M + m) * g.N + n] = v;
+                    } else {
+                        if (g.bias) v += g.bias[n];
+                        g.C[m * g.ldc + n] = v;
+                    }
+                }
             }
         }
     }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, (uint32_t)T.tmem_cols);
+    }
+    if (failed && tid == 0) atomicExch(T.err, 1);
 }
 
 // C[m, n] = sum_z part[z, m, n] (+ bias[n]), z ascending
@@ -185,6 +309,8 @@ __global__ void k_splitk_sum(const float* __restrict__ part, int split, int M, i
 }
 
 int g_sms = 0;
+size_t g_tc_smem_set = 0;
+int* g_timeout_flag = nullptr;   // device address of g_mlp_timeout
 
 int gemm(const GemmArgs& a, cudaStream_t s) {
     if (g_sms == 0) {
@@ -192,21 +318,42 @@ int gemm(const GemmArgs& a, cudaStream_t s) {
         VPET_CUDA(cudaGetDevice(&dev));
         VPET_CUDA(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev));
     }
-    const int64_t tiles = vpet_ceil_div(a.N, GT) * vpet_ceil_div(a.M, GT);
+    TcGemm T;
+    T.g = a;
+    T.pb = a.roundB ? 1 : 3;
+    // a tile of 128 x bn; three-part B tiles are narrower so that two stages fit in shared memory
+    int bn_max = T.pb == 1 ? 256 : 128;
+    // narrower tiles when the wide ones would leave most SMs idle (the training batch)
+    if (vpet_ceil_div(a.M, TC_M) * vpet_ceil_div(a.N, bn_max) < 2 * g_sms) bn_max = 64;
+    const int64_t nr = vpet_round_up(a.N, 16);
+    T.bn = (int)(nr < bn_max ? nr : bn_max);
+    int cols = 32;
+    while (cols < T.bn) cols <<= 1;
+    T.tmem_cols = cols;
+    if (!g_timeout_flag) VPET_CUDA(cudaGetSymbolAddress((void**)&g_timeout_flag, g_mlp_timeout));
+    T.err = g_timeout_flag;
+    const int64_t ntn = vpet_ceil_div(a.N, T.bn), ntm = vpet_ceil_div(a.M, TC_M);
+    VPET_ARG(ntm <= 65535 && ntn <= 65535, "mlp: %d rows exceed one launch's grid (at most %d)", a.M, 65535 * TC_M);
+    const int64_t tiles = ntn * ntm;
     // split K when the output has too few tiles to fill the GPU (weight gradients)
     int64_t split = 1;
-    if (a.part && tiles < g_sms && a.K >= 8 * GK) {
+    if (a.part && tiles < g_sms && a.K >= 8 * TC_KB) {
         split = vpet_ceil_div(2 * g_sms, tiles);
-        const int64_t maxsplit = a.K / (4 * GK);
+        const int64_t maxsplit = a.K / (4 * TC_KB);
         const int64_t capsplit = a.part_cap / ((int64_t)a.M * a.N);
         if (split > maxsplit) split = maxsplit;
         if (split > capsplit) split = capsplit;
         if (split < 1) split = 1;
     }
-    const int kchunk = (int)vpet_round_up(vpet_ceil_div(a.K, split), GK);
-    split = vpet_ceil_div(a.K, kchunk);
-    const dim3 grid((unsigned)vpet_ceil_div(a.N, GT), (unsigned)vpet_ceil_div(a.M, GT), (unsigned)split);
-    k_gemm<<<grid, 256, 0, s>>>(a, kchunk);
+    T.kchunk = (int)vpet_round_up(vpet_ceil_div(a.K, split), TC_KB);
+    split = vpet_ceil_div(a.K, T.kchunk);
+    const size_t smem = 1024 + 2 * ((size_t)TC_APARTS * TC_M * 128 + (size_t)T.pb * T.bn * 128);
+    if (smem > g_tc_smem_set) {
+        VPET_CUDA(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        g_tc_smem_set = smem;
+    }
+    const dim3 grid((unsigned)ntn, (unsigned)ntm, (unsigned)split);
+    k_gemm_tc<<<grid, TC_THREADS, smem, s>>>(T);
     VPET_LAUNCH_CHECK();
     if (split > 1) {
         const int64_t MN = (int64_t)a.M * a.N;
@@ -951,6 +1098,19 @@ int mlp_forward(const float* prm, int D, int H, int O, const float* X, int64_t B
 }
 
 }  // namespace
+
+extern "C" int abc_mlp_status(int32_t* timeout_host) {
+    vpet::clear_error();
+    VPET_ARG(timeout_host, "abc_mlp_status: null pointer");
+    int v = 0;
+    VPET_CUDA(cudaMemcpyFromSymbol(&v, g_mlp_timeout, sizeof v));
+    *timeout_host = v;
+    if (v) {
+        const int zero = 0;
+        VPET_CUDA(cudaMemcpyToSymbol(g_mlp_timeout, &zero, sizeof zero));
+    }
+    return ABC_OK;
+}
 
 extern "C" size_t abc_mlp_param_count(int32_t D, int32_t H, int32_t O) {
     if (D < 1 || H < 1 || O < 1) return 0;

@@ -177,13 +177,22 @@ class GlobalIrr:
 
     def calibrate(self, y, quantile: float = 0.99) -> float:
         """Relative median accepted distance (d_med / sum w y^2) the global path
-        reaches on these voxels, at the given quantile."""
+        reaches on these voxels, at the given quantile (computed by the library)."""
         r = self.run(y)
-        med = r["dist"][:, (self.k - 1) // 2]
-        w = torch.from_numpy(self.m.w).cuda()
-        yn = (y[:, :self.m.L] ** 2 * w).sum(1)
-        rel = (med / yn).cpu().numpy()
-        return float(np.quantile(rel, quantile))
+        return api.median_rel_quantile(r["dist"], self.k, y, self.m.L, self.m.w, quantile)
+
+
+def fallback_to_global(out, y, k: int, global_path: GlobalIrr, rel_max: float | None):
+    """Voxels whose local run is unreliable (the library's predicate: ESS below k/4, or a
+    median accepted distance above rel_max sum w y^2) take the global path's summaries, in
+    place in out.  Returns the fallback voxels (device int32, ascending) and their number."""
+    rows, count = api.fallback_rows(out["ess"], out["dmed"], out["ynorm"], k, rel_max)
+    n = int(count.item())
+    if n > 0:
+        g = global_path.run(api.gather_rows(y, rows, count, n))
+        for key in ("mean", "sd", "lo", "hi"):
+            api.scatter_rows(g[key], rows, count, out[key])
+    return rows[:n], n
 
 
 def run_learned(model: LearnedLocalAbc, y, M: int, k: int, global_path: GlobalIrr | None, rel_max: float | None,
@@ -192,15 +201,8 @@ def run_learned(model: LearnedLocalAbc, y, M: int, k: int, global_path: GlobalIr
     Returns (outputs dict, fallback voxel indices)."""
     prop = model.propose(y)
     out = model.local(y, prop, M=M, k=k, seed=seed, sigma_scale=sigma_scale)
-    fb = torch.zeros(0, dtype=torch.int64, device="cuda")
+    fb = torch.zeros(0, dtype=torch.int32, device="cuda")
     if global_path is not None:
-        bad = out["ess"] < (k / 4.0)
-        if rel_max is not None:
-            bad |= out["dmed"] > rel_max * out["ynorm"]
-        fb = torch.nonzero(bad).flatten()
-        if fb.numel() > 0:
-            g = global_path.run(y.index_select(0, fb).contiguous())
-            for key in ("mean", "sd", "lo", "hi"):
-                out[key].index_copy_(0, fb, g[key])
+        fb, _ = fallback_to_global(out, y, k, global_path, rel_max)
     out["prop"] = prop
     return out, fb

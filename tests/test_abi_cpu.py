@@ -239,3 +239,28 @@ def test_force_rescue_hook_mask_without_gpu(lib):
     assert lib.abc_debug_force_rescue(-1) == _lib.ABC_ERR_ARG
     assert lib.abc_debug_force_rescue(7) == _lib.ABC_OK
     assert lib.abc_debug_force_rescue(0) == _lib.ABC_OK
+
+
+def test_fallback_and_quantile_validation_without_gpu(lib):
+    """Argument checks of the learned path's reliability calls, before any device work."""
+    from paper_2603_14859_b300 import _lib
+    P = ctypes.c_void_p
+    assert lib.abc_fallback_scratch_size(0) == 0 and lib.abc_fallback_scratch_size(1) > 0
+    assert lib.abc_quantile_scratch_size(0) == 0 and lib.abc_quantile_scratch_size(10) >= 40
+    need = lib.abc_fallback_scratch_size(1000)
+    assert lib.abc_fallback_rows(P(16), P(16), P(16), 0, 200, 0.0, P(16), P(16), P(16), need, None) == _lib.ABC_ERR_ARG
+    assert lib.abc_fallback_rows(P(16), P(16), P(16), 1000, 0, 0.0, P(16), P(16), P(16), need, None) == _lib.ABC_ERR_ARG
+    assert lib.abc_fallback_rows(P(16), None, None, 1000, 200, 0.1, P(16), P(16), P(16), need, None) \
+        == _lib.ABC_ERR_ARG                                   # rel_max > 0 needs dmed and ynorm
+    assert lib.abc_fallback_rows(P(16), P(16), P(16), 1000, 200, 0.0, P(16), P(16), P(16), need - 1, None) \
+        == _lib.ABC_ERR_ARG
+    assert b"scratch" in lib.abc_last_error()
+    assert lib.abc_gather_rows(P(16), 4, P(16), P(16), 10, 5, P(16), 5, None) == _lib.ABC_ERR_ARG   # ld_src < width
+    assert lib.abc_scatter_rows(None, 5, P(16), P(16), 10, 5, P(16), 5, None) == _lib.ABC_ERR_ARG
+    w = np.ones(29, np.float32)
+    qn = lib.abc_quantile_scratch_size(100)
+    out = ctypes.c_float()
+    for args in [(100, 9, 29, 29, 1.5), (100, 9, 65, 65, 0.5), (100, 0, 29, 29, 0.5), (100, 9, 29, 28, 0.5)]:
+        J, k, L, ldy, q = args
+        assert lib.abc_median_rel_quantile(P(16), J, k, P(16), ldy, L, w.ctypes.data, q, ctypes.byref(out), P(16),
+                                           qn, None) == _lib.ABC_ERR_ARG, args
