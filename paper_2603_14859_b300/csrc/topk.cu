@@ -839,6 +839,10 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
     __shared__ uint32_t box[7];                 // ordered-int min/max x 3, max threshold
     __shared__ int wcount[8];
     __shared__ unsigned long long sk[KEEP_SORT_MAX];   // (centre distance, tile) of the kept tiles
+    // per voxel (packed order; td = -1: no voxel): its features widened by their rounding slack
+    // (f - s, f + s) and its distance bound; per 16 consecutive voxels their box and largest bound
+    __shared__ float4 sv_lo[BM], sv_hi[BM];
+    __shared__ float4 sb_lo[BM / 16], sb_hi[BM / 16];
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     const int64_t vt = blockIdx.x;
     const int64_t nv = K.count ? (int64_t)*K.count : K.J;   // voxel positions in use
@@ -849,6 +853,8 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
     if (tid < 7) box[tid] = (tid < 6 && (tid & 1) == 0) ? 0xFFFFFFFFu : 0u;
     __syncthreads();
     if (tid < BM) {
+        sv_lo[tid] = make_float4(3.0e38f, 3.0e38f, 3.0e38f, -1.0f);
+        sv_hi[tid] = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.0f);
         const int64_t p = vt * BM + tid;
         const int64_t j = K.rows && p < nv ? (int64_t)K.rows[p] : p;   // packed row of the voxel (-1: none)
         if (p < nv && p < K.J && j >= 0) {
@@ -875,6 +881,30 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
                 atomicMax(&box[2 * c + 1], ord_f2u(K.fy[3 * j + c]));
             }
             atomicMax(&box[6], ord_f2u(td));
+            float f[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) f[c] = K.fy[3 * j + c];
+            // the voxel's share of the features' rounding slack, 2^-18 x 2 |f|
+            sv_lo[tid] = make_float4(f[0] - 0x1p-17f * fabsf(f[0]), f[1] - 0x1p-17f * fabsf(f[1]),
+                                     f[2] - 0x1p-17f * fabsf(f[2]), td);
+            sv_hi[tid] = make_float4(f[0] + 0x1p-17f * fabsf(f[0]), f[1] + 0x1p-17f * fabsf(f[1]),
+                                     f[2] + 0x1p-17f * fabsf(f[2]), 0.0f);
+        }
+        // the 16-voxel sub-boxes (half-warp reductions)
+        float4 lo = sv_lo[tid], hi = sv_hi[tid];
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+            lo.x = fminf(lo.x, __shfl_xor_sync(0xFFFFFFFFu, lo.x, o));
+            lo.y = fminf(lo.y, __shfl_xor_sync(0xFFFFFFFFu, lo.y, o));
+            lo.z = fminf(lo.z, __shfl_xor_sync(0xFFFFFFFFu, lo.z, o));
+            lo.w = fmaxf(lo.w, __shfl_xor_sync(0xFFFFFFFFu, lo.w, o));
+            hi.x = fmaxf(hi.x, __shfl_xor_sync(0xFFFFFFFFu, hi.x, o));
+            hi.y = fmaxf(hi.y, __shfl_xor_sync(0xFFFFFFFFu, hi.y, o));
+            hi.z = fmaxf(hi.z, __shfl_xor_sync(0xFFFFFFFFu, hi.z, o));
+        }
+        if ((tid & 15) == 0) {
+            sb_lo[tid >> 4] = lo;
+            sb_hi[tid >> 4] = hi;
         }
     }
     __syncthreads();
@@ -886,6 +916,9 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
     }
     const float tmax = ord_u2f(box[6]);
     const bool all = !(tmax < 1.0e30f);
+    float invW[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) invW[c] = K.Wc[c] > 0.0f ? 1.0f / K.Wc[c] : 0.0f;
     const int per = K.bn / 64;
     const int64_t ntiles = (K.N + K.bn - 1) / K.bn;
     int base = 0;
@@ -895,23 +928,47 @@ __global__ void __launch_bounds__(256) k_keep_tiles(const __grid_constant__ Keep
         if (t < ntiles) {
             keep = all;
             if (!keep) {
-                float lb = 0.0f;
+                float xl[3], xh[3], lb = 0.0f;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    float xl = 3.0e38f, xh = -3.0e38f;
+                    xl[c] = 3.0e38f;
+                    xh[c] = -3.0e38f;
                     for (int q = 0; q < per; ++q) {
                         const int64_t u = t * per + q;
                         if (u < K.nt64) {
-                            xl = fminf(xl, K.tbox[6 * u + 2 * c]);
-                            xh = fmaxf(xh, K.tbox[6 * u + 2 * c + 1]);
+                            xl[c] = fminf(xl[c], K.tbox[6 * u + 2 * c]);
+                            xh[c] = fmaxf(xh[c], K.tbox[6 * u + 2 * c + 1]);
                         }
                     }
                     // a gap smaller than the features' rounding is treated as none
-                    const float slack = 0x1p-18f * (fabsf(xl) + fabsf(xh) + fabsf(ylo[c]) + fabsf(yhi[c]));
-                    const float gap = fmaxf(fmaxf(xl - yhi[c], ylo[c] - xh) - slack, 0.0f);
-                    if (K.Wc[c] > 0.0f) lb += gap * gap / K.Wc[c];
+                    const float slack = 0x1p-18f * (fabsf(xl[c]) + fabsf(xh[c]) + fabsf(ylo[c]) + fabsf(yhi[c]));
+                    const float gap = fmaxf(fmaxf(xl[c] - yhi[c], ylo[c] - xh[c]) - slack, 0.0f);
+                    lb = fmaf(gap * gap, invW[c], lb);
                 }
                 keep = lb * (1.0f - 0x1p-10f) <= tmax;
+                // the box bound passes: keep the tile only if some voxel's own features are
+                // within its own distance bound of the draw tile's box (the same bound, per voxel)
+                if (keep) {
+                    keep = false;
+                    float st[3];                  // the draw tile's share of the slack
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) st[c] = 0x1p-18f * (fabsf(xl[c]) + fabsf(xh[c]));
+                    // the gap bound of the draw tile's box against a (sub-)box [lo, hi] of voxel features
+                    auto lower = [&](const float4& lo, const float4& hi) {
+                        const float g0 = fmaxf(fmaxf(xl[0] - hi.x, lo.x - xh[0]) - st[0], 0.0f);
+                        const float g1 = fmaxf(fmaxf(xl[1] - hi.y, lo.y - xh[1]) - st[1], 0.0f);
+                        const float g2 = fmaxf(fmaxf(xl[2] - hi.z, lo.z - xh[2]) - st[2], 0.0f);
+                        return fmaf(g2 * g2, invW[2], fmaf(g1 * g1, invW[1], g0 * g0 * invW[0])) * (1.0f - 0x1p-10f);
+                    };
+                    for (int b = 0; b < BM / 16 && !keep; ++b) {
+                        const float4 blo = sb_lo[b];
+                        if (!(lower(blo, sb_hi[b]) <= blo.w)) continue;     // no voxel of the sub-box
+                        for (int v = 16 * b; v < 16 * b + 16 && !keep; ++v) {
+                            const float4 lo = sv_lo[v];
+                            keep = lower(lo, sv_hi[v]) <= lo.w;
+                        }
+                    }
+                }
             }
         }
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
