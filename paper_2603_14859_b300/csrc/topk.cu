@@ -64,6 +64,11 @@ constexpr int A_KBLK_BYTES = BM * KBLK * 2;   // 16 KB
 // and keeping its own half of the voxel's candidate list).
 constexpr int tc_epi_warps(bool topr, int bn) { return (topr || bn == 64) ? 4 : 8; }
 constexpr int tc_threads(bool topr, int bn) { return 64 + 32 * tc_epi_warps(topr, bn); }
+// Per-thread key rows: the top-r variants keep their kept keys there, the one-K-block list
+// variants read passing keys back from them (shared memory allows it next to two CTAs per
+// SM); the wider list variants pick passing keys from registers instead.
+constexpr bool tc_rows(int nkb, bool topr) { return topr || nkb == 1; }
+
 constexpr uint64_t WAIT_NS_DEFAULT = 2000000000ull;   // 2 s bound on any barrier wait
 constexpr int MAXL = 64;
 constexpr int ORDER_BITS = 10;                 // bits per ordering feature (30-bit Morton key)
@@ -111,15 +116,11 @@ Tuning default_tuning(int mode) {
     return Tuning{128, 2, 8, 1.5f};
 }
 
-// The built-in tuning for a shape: the split form's operands take two K-blocks past 30
-// frames, where 128-draw tiles would leave one CTA per SM; there it runs 64-draw tiles.
+// The built-in tuning for a shape (the same for every shape: 128-draw tiles; with two
+// K-blocks their list variants keep two CTAs per SM by picking passing keys from registers).
 Tuning default_tuning_for_shape(int mode, int L) {
-    Tuning t = default_tuning(mode);
-    if (mode != ABC_FP32 && 2 * L + 3 > KBLK) {
-        t.bn = 64;
-        t.ctas_per_sm = 3;
-    }
-    return t;
+    (void)L;
+    return default_tuning(mode);
 }
 
 // bf16 columns of the packed operands per frame: products per term of the key.
@@ -1154,6 +1155,20 @@ __device__ __forceinline__ uint32_t mask8(const float (&v)[32], int o, float thr
     return m;
 }
 
+// Element b (0..31, any lane-varying value) of a register array, by a select tree.
+__device__ __forceinline__ float pick32(const float (&v)[32], int b) {
+    float l4[16], l3[8], l2[4], l1[2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) l4[i] = (b & 1) ? v[2 * i + 1] : v[2 * i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) l3[i] = (b & 2) ? l4[2 * i + 1] : l4[2 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) l2[i] = (b & 4) ? l3[2 * i + 1] : l3[2 * i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) l1[i] = (b & 8) ? l2[2 * i + 1] : l2[2 * i];
+    return (b & 16) ? l1[1] : l1[0];
+}
+
 // One 32-column chunk of the epilogue, per thread (= voxel): the minima of
 // the four 8-key groups against the voxel's threshold; a thread with a passing
 // group builds the mask of passing keys (passing groups only), copies its 32
@@ -1180,10 +1195,13 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
     if (g1 <= thr) m |= mask8(v, 8, thr) << 8;
     if (g2 <= thr) m |= mask8(v, 16, thr) << 16;
     if (g3 <= thr) m |= mask8(v, 24, thr) << 24;
-    // the passing keys are read back by position from this thread's own row of shared memory
-    float4* dst = (float4*)row_s;
+    // the passing keys are read back by position from this thread's own row of shared memory,
+    // or (row_s null: passing keys are rare) picked from the registers by a select tree
+    if (row_s) {
+        float4* dst = (float4*)row_s;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
     if (acnt) {
         const int n = __popc(m);
         int pos = atomicAdd(acnt, n);
@@ -1194,7 +1212,7 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
         while (m) {
             const int b = __ffs(m) - 1;
             m &= m - 1;
-            I.keys[lbase + pos] = row_s[b];
+            I.keys[lbase + pos] = (row_s ? row_s[b] : pick32(v, b));
             I.idx[lbase + pos] = (int32_t)(n0 + b);
             ++pos;
         }
@@ -1203,25 +1221,12 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
     while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
-        I.keys[lbase + cnt] = row_s[b];
+        I.keys[lbase + cnt] = (row_s ? row_s[b] : pick32(v, b));
         I.idx[lbase + cnt] = (int32_t)(n0 + b);
         ++cnt;
     }
 }
 
-// Element b (0..31, any lane-varying value) of a register array, by a select tree.
-__device__ __forceinline__ float pick32(const float (&v)[32], int b) {
-    float l4[16], l3[8], l2[4], l1[2];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) l4[i] = (b & 1) ? v[2 * i + 1] : v[2 * i];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) l3[i] = (b & 2) ? l4[2 * i + 1] : l4[2 * i];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) l2[i] = (b & 4) ? l3[2 * i + 1] : l3[2 * i];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) l1[i] = (b & 8) ? l2[2 * i + 1] : l2[2 * i];
-    return (b & 16) ? l1[1] : l1[0];
-}
 
 // Per-thread state of a top-r pilot: the voxel's kept keys A[i * 128] (i < n_in,
 // unordered), their maximum amax at position imax once n_in = r, and the
@@ -1303,8 +1308,9 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;                                          // NKB x 16 KB
     uint8_t* sB = smem + NKB * A_KBLK_BYTES;                     // STAGES x NKB x BN rows
-    float* sRow = (float*)(sB + STAGES * NKB * B_KBLK_BYTES);         // 32 EPI threads x ROW_LD
-    uint32_t* hist = (uint32_t*)(sRow + 32 * EPI * ROW_LD);             // EPI warps x 256
+    constexpr int ROW_FLOATS = tc_rows(NKB, TOPR) ? 32 * EPI * ROW_LD : 0;
+    float* sRow = (float*)(sB + STAGES * NKB * B_KBLK_BYTES);         // 32 EPI threads x ROW_LD (if any)
+    uint32_t* hist = (uint32_t*)(sRow + ROW_FLOATS);                    // EPI warps x 256
     uint64_t* bars = (uint64_t*)(hist + EPI * 256);
     uint64_t* full = bars;                  // [STAGES]
     uint64_t* empty = bars + STAGES;        // [STAGES]
@@ -1469,7 +1475,7 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
         const int hh = EPI == 8 ? (warp - 2) >> 2 : 0;   // chunk parity and half-list (0 with 4 warps)
         const int row = q * 32 + lane;
         uint32_t* whist = hist + (warp - 2) * 256;
-        float* row_s = sRow + (threadIdx.x - 64) * ROW_LD;
+        float* row_s = tc_rows(NKB, TOPR) ? sRow + (threadIdx.x - 64) * ROW_LD : nullptr;
         uint32_t gt = 0;
         bool stop = false;
         for (uint32_t ic = 0; !stop; ++ic) {
@@ -2346,17 +2352,19 @@ int make_tmap(CUtensorMap* m, void* base, int64_t rows, int Kp, int box_rows, in
     return ABC_OK;
 }
 
-// TMA ring depth per shape: as deep as shared memory allows next to the A tile and
-// the epilogue warps' key rows and histograms (<= 227 KB per CTA; two CTAs per SM
-// for one K-block)
-constexpr int stages_for(int nkb, int bn) {
-    return nkb == 1 ? (bn == 128 ? 3 : 4) : (nkb == 2 ? (bn == 128 ? 4 : 3) : (bn == 128 ? 2 : 4));
+// TMA ring depth per shape: as deep as shared memory allows next to the A tile, the key rows
+// (if any) and the epilogue warps' histograms; two K-blocks of 128-draw tiles without rows:
+// two stages, so that two CTAs fit on an SM
+constexpr int stages_for(int nkb, int bn, bool topr) {
+    return nkb == 1 ? (bn == 128 ? 3 : 4)
+                    : (nkb == 2 ? (topr ? (bn == 128 ? 4 : 3) : (bn == 128 ? 2 : 4)) : (bn == 128 ? 2 : 4));
 }
 
 size_t tc_smem_bytes(int nkb, int bn, bool topr) {
-    const int S = stages_for(nkb, bn);
+    const int S = stages_for(nkb, bn, topr);
     const int epi = tc_epi_warps(topr, bn);
-    return 1024 + (size_t)nkb * A_KBLK_BYTES + (size_t)S * nkb * bn * KBLK * 2 + (size_t)32 * epi * ROW_LD * 4 +
+    return 1024 + (size_t)nkb * A_KBLK_BYTES + (size_t)S * nkb * bn * KBLK * 2 +
+           (tc_rows(nkb, topr) ? (size_t)32 * epi * ROW_LD * 4 : 0) +
            (size_t)epi * 256 * 4 + (2 * S + 14) * 8;
 }
 
@@ -2374,7 +2382,7 @@ int num_sms() {
 
 template <int NKB, int BN, bool DUMP, bool TOPR>
 int launch_tc(const BatchTc& P, int ctas_per_sm, cudaStream_t s) {
-    constexpr int S = stages_for(NKB, BN);
+    constexpr int S = stages_for(NKB, BN, TOPR);
     const size_t smem = tc_smem_bytes(NKB, BN, TOPR);
     // kernel attributes are per device: configured once for each device that launches
     static bool configured_dev[64] = {};
