@@ -2518,9 +2518,12 @@ struct BatchLayout {
 //  - centring groups: up to MAX_GROUPS per scan, each at least GROUP_MIN_TILES voxel tiles;
 //    every group costs a copy of the draw operand, so groups are added one at a time to the
 //    scan with the most voxels per copy byte, discounted by the groups it has (gain
-//    J / (G (G + 1)) per byte), while all copies fit the budget.
+//    J / (G (G + 1)) per byte), while all copies fit the budget.  Each copy also costs the
+//    main pass L2 reuse (CTAs working on different groups read different copies): for one
+//    scan about 2 GB of copies (the brain volume: 4 of 512 MB) measured best, a batch of many
+//    small, varied scans needs far more (the 64-scan batch: 64 GB).
 constexpr double LIST_BYTES_SINGLE = 32.0e9, LIST_EXTRA_BYTES_BATCH = 16.0e9;
-constexpr double GROUP_COPIES_BYTES_SINGLE = 8.0e9, GROUP_COPIES_BYTES_BATCH = 48.0e9;
+constexpr double GROUP_COPIES_BYTES_SINGLE = 2.1e9, GROUP_COPIES_BYTES_BATCH = 64.0e9;
 constexpr int64_t GROUP_MIN_TILES = 2;
 
 void make_batch_layout(const ScanSpec* sc, int n, int mode, const Tuning& tu, BatchLayout* B, bool grouped = true) {
@@ -2791,6 +2794,9 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         }
         order[b] = v;
     }
+    // draw-tile width of the pass being set up: the tuning's, except for top-r pilot levels, which
+    // run 64-draw tiles (their key rows leave room for two CTAs per SM only there)
+    int pass_bn = tu.bn;
     auto fill_item = [&](ItemTc& I, int i, int64_t stride, int kt, int lim, const float* thr0) -> int {
         const Layout& L = BL.lay[i];
         const Ptrs& p = ptr[i];
@@ -2800,7 +2806,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         // the draw operand holds G copies of Np rows (one per centring group); a pilot's strided
         // view takes every stride-th row of all of them (Np is a multiple of the stride)
         if ((r = make_tmap(&I.tmB, p.B, stride == 1 ? (int64_t)L.G * L.Np : (int64_t)L.G * L.Np / stride, L.Kp,
-                           tu.bn, stride)))
+                           pass_bn, stride)))
             return r;
         (void)Nn;
         I.J = L.J;
@@ -2810,16 +2816,16 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         I.cnt = p.cnt;
         I.thr = p.thr;
         I.thr0 = thr0;
-        I.ntiles = (int)vpet_ceil_div(I.N, tu.bn);
+        I.ntiles = (int)vpet_ceil_div(I.N, pass_bn);
         I.C = L.C;
         // with 128-draw tiles two epilogue threads serve a voxel, each with its own
         // half-list that keeps its own kt smallest and receives half of every tile;
         // with 64-draw tiles one thread uses the whole list (half 1 stays empty)
-        const bool halves = tu.bn == 128;
+        const bool halves = pass_bn == 128;
         I.C2 = halves ? L.C / 2 : L.C;
         I.hstride = (int)L.Jp;
         I.kt = kt;
-        const int per_tile = halves ? tu.bn / 2 : tu.bn;
+        const int per_tile = halves ? pass_bn / 2 : pass_bn;
         const int cap = kt + (kt / 4 > 64 ? kt / 4 : 64);
         I.cap = cap < I.C2 ? cap : I.C2;
         // a half-list may grow to the whole list's limit (its capacity allows it): halving
@@ -2854,7 +2860,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         K.sc = split_coef(L);
         K.c0 = ptr[i].c0;
         K.dn = ptr[i].dn;
-        K.bn = tu.bn;
+        K.bn = pass_bn;
         k_keep_tiles<<<(unsigned)L.nvt, 256, 0, s>>>(K);
         VPET_LAUNCH_CHECK();
         return ABC_OK;
@@ -2869,6 +2875,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         bool lev_topr = true;
         for (int i = 0; i < n; ++i)
             if (BL.lay[i].nlev > lv && BL.lay[i].lev_rank[lv] > TOPR_MAX) lev_topr = false;
+        pass_bn = lev_topr ? 64 : tu.bn;
         for (int oi = 0; oi < n; ++oi) {
             const int i = order[oi];
             const Layout& L = BL.lay[i];
@@ -2881,7 +2888,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             T.grows[m] = L.Np;
             const int64_t npass = vpet_ceil_div(L.N, L.lev_stride[lv]);
             T.item[m].N = npass;
-            T.item[m].ntiles = (int)vpet_ceil_div(npass, tu.bn);
+            T.item[m].ntiles = (int)vpet_ceil_div(npass, pass_bn);
             // the pass's draw tiles nearest first (all of them at the coarsest level, which has no
             // threshold yet): the pilot's kept keys settle early (its result does not depend on the order)
             if ((rc = keep_tiles(i, npass, nullptr, has_thr, true))) return rc;
@@ -2899,7 +2906,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
                 T.item[m].rk = lv == 0 ? L.rk : 0;
                 T.item[m].thr_out = ptr[i].thr0;
             } else {
-                PB.item[mp] = PilotItem{ptr[i].keys, ptr[i].cnt, ptr[i].thr0, L.J, L.C, rsel, tu.bn == 128 ? L.C / 2 : L.C, L.Jp};
+                PB.item[mp] = PilotItem{ptr[i].keys, ptr[i].cnt, ptr[i].thr0, L.J, L.C, rsel, pass_bn == 128 ? L.C / 2 : L.C, L.Jp};
                 PB.v_prefix[mp + 1] = PB.v_prefix[mp] + L.J;
                 ++mp;
             }
@@ -2912,7 +2919,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         T.withhold = g_withhold;
         PB.n_items = mp;
         PB.status = status;
-        if ((rc = dispatch_tc<false>(nkb, tu.bn, T, tu.ctas_per_sm, s, lev_topr))) return rc;
+        if ((rc = dispatch_tc<false>(nkb, pass_bn, T, tu.ctas_per_sm, s, lev_topr))) return rc;
         if (mp > 0) {
             k_pilot_threshold<<<(unsigned)vpet_ceil_div(PB.v_prefix[mp], 8), 256, 0, s>>>(PB);
             VPET_LAUNCH_CHECK();
@@ -2935,6 +2942,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             }
         }
     }
+    pass_bn = tu.bn;
     // draw tiles the main pass can skip (needs the pilot thresholds and the ordered draws)
     unsigned long long* tally = (unsigned long long*)(wsb + 192);
     bool skip[MAX_ITEMS];
