@@ -151,10 +151,10 @@ typedef struct {
 } abc_tuning;
 
 /* The tuning used for `precision` when none is passed: the built-in choice
- * (128-draw tiles and 2 CTAs/SM, pilot stride 8 and factor 2.25 for ABC_FP32,
- * pilot stride 16 and factor 1.5 otherwise; a single-scan call of the fast form
- * with more than 30 frames, whose operands take two K-blocks, uses 64-draw tiles
- * and 3 CTAs/SM) unless abc_set_default_tuning replaced it. */
+ * (128-draw tiles and 2 CTAs/SM; pilot stride 8 and factor 2.25 for ABC_FP32,
+ * pilot stride 8 and factor 1.5 otherwise, where a single-scan call with
+ * k >= 400 uses pilot stride 16) unless abc_set_default_tuning replaced it.
+ * This call reports the choice for a batch (no single-scan adjustment). */
 int abc_default_tuning(int32_t precision, abc_tuning* out);
 
 /* Replaces the process-wide default tuning for both precisions (NULL restores

@@ -116,11 +116,18 @@ Tuning default_tuning(int mode) {
     return Tuning{128, 2, 8, 1.5f};
 }
 
-// The built-in tuning for a shape (the same for every shape: 128-draw tiles; with two
-// K-blocks their list variants keep two CTAs per SM by picking passing keys from registers).
-Tuning default_tuning_for_shape(int mode, int L) {
+// The built-in tuning of a single-scan call: 128-draw tiles for every shape (with two K-blocks
+// their list variants keep two CTAs per SM by picking passing keys from registers); the fast
+// form's finest pilot takes every 16th draw when k >= 400.  The finest pilot's rank rk must
+// sit four standard deviations above k / stride, which costs relatively less margin the larger
+// k / stride is: for k = 500 stride 16 places the threshold near rank 2.1 k (stride 8: 1.9 k) at
+// half the pilot's work (brain volume: 73.3 against 77.2 ms per step), for k = 200 near 3.2 k
+// (stride 8: 2.2 k; total body: 231.9 against 222.4 ms).
+Tuning default_tuning_for_shape(int mode, int L, int k) {
     (void)L;
-    return default_tuning(mode);
+    Tuning t = default_tuning(mode);
+    if (mode != ABC_FP32 && k >= 400) t.pilot_stride = 16;
+    return t;
 }
 
 // bf16 columns of the packed operands per frame: products per term of the key.
@@ -3147,7 +3154,9 @@ bool g_has_default = false;   // abc_set_default_tuning was called
 Tuning g_default_tuning = default_tuning(ABC_BF16_RESCORE);
 
 Tuning tuning_for(int mode) { return g_has_default ? g_default_tuning : default_tuning(mode); }
-Tuning tuning_for(int mode, int L) { return g_has_default ? g_default_tuning : default_tuning_for_shape(mode, L); }
+Tuning tuning_for(int mode, int L, int k) {
+    return g_has_default ? g_default_tuning : default_tuning_for_shape(mode, L, k);
+}
 
 ScanSpec single(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w, int k,
                 int32_t* idx, float* dist) {
@@ -3180,7 +3189,7 @@ namespace vpet {
 size_t topk_workspace_bytes(int64_t J, int64_t N, int L, int k, int precision) {
     ScanSpec c = single(nullptr, J, L, nullptr, N, L, L, nullptr, k, nullptr, nullptr);
     BatchLayout* B = new BatchLayout;
-    make_batch_layout(&c, 1, precision, tuning_for(precision, L), B);
+    make_batch_layout(&c, 1, precision, tuning_for(precision, L, k), B);
     const size_t t = B->total;
     delete B;
     return t;
@@ -3189,7 +3198,7 @@ size_t topk_workspace_bytes(int64_t J, int64_t N, int L, int k, int precision) {
 int topk_on_workspace(const float* y, int64_t J, int ldy, const float* x, int64_t N, int ldx, int L, const float* w,
                       int k, int precision, void* ws, size_t ws_bytes, int32_t* idx, float* dist, cudaStream_t s) {
     const ScanSpec c = single(y, J, ldy, x, N, ldx, L, w, k, idx, dist);
-    return run_batch(&c, 1, precision, tuning_for(precision, L), ws, ws_bytes, nullptr, 0, s);
+    return run_batch(&c, 1, precision, tuning_for(precision, L, k), ws, ws_bytes, nullptr, 0, s);
 }
 
 }  // namespace vpet
