@@ -117,7 +117,7 @@ def tune(batch, precision: int | None = None, max_voxels: int = 4096, max_draws:
     if finalists > 1 and batch._scan_structs is not None and batch.ws is not None:
         for _, cand in results[:finalists]:
             t = _lib.Tuning(cand["bn"], cand["ctas_per_sm"], cand["pilot_stride"], cand["pilot_factor"])
-            ms = _time_call(L, batch._scan_structs, len(batch.runs), precision, t, batch.ws, s, 1)
+            ms = _time_call(L, batch._scan_structs, len(batch.runs), precision, t, batch.ws, s, 2)
             full.append((ms, cand))
             if verbose:
                 print(f"  full batch {cand}: {ms:.2f} ms")
