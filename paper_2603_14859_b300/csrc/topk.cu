@@ -1617,23 +1617,29 @@ struct PilotItem {
 };
 
 // Moves half-list 1 of a list row (entries [C2, C2 + c1)) to follow half-list 0
-// (entries [0, c0)), keys and (when given) draw indices.  Rows of 32 are read
-// before they are written, and every write lands below the next row's reads
-// (c0 <= C2), so the copy is safe in place.
+// (entries [0, c0)), keys and (when given) draw indices, four rows of 32 at a time with
+// their loads in flight together.  A batch is read before it is written, and every write
+// lands below the next batch's reads (c0 <= C2), so the copy is safe in place.
 __device__ __forceinline__ void merge_halves(float* kj, int32_t* ij, int C2, int c0, int c1, int lane) {
     if (c0 == C2 || c1 == 0) return;
-    for (int base = 0; base < c1; base += 32) {
-        const int i = base + lane;
-        float k = 0.0f;
-        int32_t id = 0;
-        if (i < c1) {
-            k = kj[C2 + i];
-            if (ij) id = ij[C2 + i];
+    constexpr int RA = 4;
+    for (int base = 0; base < c1; base += 32 * RA) {
+        float k[RA];
+        int32_t id[RA];
+#pragma unroll
+        for (int r = 0; r < RA; ++r) {
+            const int i = base + 32 * r + lane;
+            k[r] = i < c1 ? kj[C2 + i] : 0.0f;
+            id[r] = (ij && i < c1) ? ij[C2 + i] : 0;
         }
         __syncwarp();
-        if (i < c1) {
-            kj[c0 + i] = k;
-            if (ij) ij[c0 + i] = id;
+#pragma unroll
+        for (int r = 0; r < RA; ++r) {
+            const int i = base + 32 * r + lane;
+            if (i < c1) {
+                kj[c0 + i] = k[r];
+                if (ij) ij[c0 + i] = id[r];
+            }
         }
     }
     __syncwarp();
@@ -2022,13 +2028,25 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
         if (P.mode != ABC_FP32 && cnt > P.k) {
             const KthKey k1 = warp_select_exact(kj, cnt, P.k - 1, hist, (float*)sbuf, 2 * B.sortcap, lane);
             if (k1.n_less + k1.n_eq <= B.sortcap) {
-                for (int base = 0; base < cnt; base += 32) {
-                    const int i = base + lane;
-                    const bool in = i < cnt && f2key(kj[i]) <= k1.K;
-                    const uint32_t row = in ? (uint32_t)ij[i] : 0u;
-                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in);
-                    if (in) sbuf[n1 + __popc(bal & ((1u << lane) - 1u))] = row;
-                    n1 += __popc(bal);
+                // the list read four rows of 32 at a time, their loads in flight together
+                constexpr int RA = 4;
+                for (int base = 0; base < cnt; base += 32 * RA) {
+                    float kv[RA];
+                    int32_t iv[RA];
+#pragma unroll
+                    for (int r = 0; r < RA; ++r) {
+                        const int i = base + 32 * r + lane;
+                        kv[r] = i < cnt ? kj[i] : __int_as_float(0x7F800000);
+                        iv[r] = i < cnt ? ij[i] : 0;
+                    }
+#pragma unroll
+                    for (int r = 0; r < RA; ++r) {
+                        const int i = base + 32 * r + lane;
+                        const bool in = i < cnt && f2key(kv[r]) <= k1.K;
+                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, in);
+                        if (in) sbuf[n1 + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)iv[r];
+                        n1 += __popc(bal);
+                    }
                 }
                 __syncwarp();
                 float d1 = 0.0f;
@@ -2039,15 +2057,28 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
                         const int i = i0 + r * R + grp;
                         xr[r] = P.xs + (int64_t)(uint32_t)sbuf[i < n1 ? i : 0] * P.ldxs;
                     }
-                    float d[NR];
-                    group_dist_n<NR>(yq, wq, xr, P.L, h, G, d);
-                    if (h == 0) {
+                    if (G >= 4) {
+                        // the reduce-scatter form (the same value per row as the full butterfly)
+                        int rr;
+                        const float dv = group_dist_scatter4(yq, wq, xr, P.L, h, G, rr);
+                        const int i = i0 + rr * R + grp;
+                        __syncwarp();
+                        if ((h & ((G >> 2) - 1)) == 0 && i < n1) {
+                            sbuf[i] = ((unsigned long long)__float_as_uint(dv) << 32) | (uint32_t)sbuf[i];
+                            d1 = fmaxf(d1, dv);
+                        }
+                    } else {
+                        float d[NR];
+                        group_dist_n<NR>(yq, wq, xr, P.L, h, G, d);
+                        __syncwarp();
+                        if (h == 0) {
 #pragma unroll
-                        for (int r = 0; r < NR; ++r) {
-                            const int i = i0 + r * R + grp;
-                            if (i < n1) {
-                                sbuf[i] = ((unsigned long long)__float_as_uint(d[r]) << 32) | (uint32_t)sbuf[i];
-                                d1 = fmaxf(d1, d[r]);
+                            for (int r = 0; r < NR; ++r) {
+                                const int i = i0 + r * R + grp;
+                                if (i < n1) {
+                                    sbuf[i] = ((unsigned long long)__float_as_uint(d[r]) << 32) | (uint32_t)sbuf[i];
+                                    d1 = fmaxf(d1, d[r]);
+                                }
                             }
                         }
                     }
@@ -2057,25 +2088,31 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
                 for (int o = 16; o > 0; o >>= 1) d1 = fmaxf(d1, __shfl_xor_sync(0xFFFFFFFFu, d1, o));
                 const float Tc = fminf(need_key(d1, P.ynorm[j], P.c0[j], P.dn[j],
                                                 SplitCoef{P.cacc, 4.0f * (float)P.L * 0x1p-24f}), T_out);
-                // keep K1 < key <= Tc (the first set is in sbuf), in place
+                // keep K1 < key <= Tc (the first set is in sbuf), in place: a batch of four rows is
+                // read before any of it is written, and writes stay below the next batch's reads
                 int out = 0;
-                for (int base = 0; base < cnt; base += 32) {
-                    const int i = base + lane;
-                    float kv = 0.0f;
-                    int32_t iv = 0;
-                    bool keep = false;
-                    if (i < cnt) {
-                        kv = kj[i];
-                        iv = ij[i];
-                        keep = f2key(kv) > k1.K && kv <= Tc;
+                for (int base = 0; base < cnt; base += 32 * RA) {
+                    float kv[RA];
+                    int32_t iv[RA];
+#pragma unroll
+                    for (int r = 0; r < RA; ++r) {
+                        const int i = base + 32 * r + lane;
+                        kv[r] = i < cnt ? kj[i] : __int_as_float(0x7F800000);
+                        iv[r] = i < cnt ? ij[i] : 0;
                     }
-                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
-                    if (keep) {
-                        const int pos = out + __popc(bal & ((1u << lane) - 1u));
-                        kj[pos] = kv;
-                        ij[pos] = iv;
+                    __syncwarp();
+#pragma unroll
+                    for (int r = 0; r < RA; ++r) {
+                        const int i = base + 32 * r + lane;
+                        const bool keep = i < cnt && f2key(kv[r]) > k1.K && kv[r] <= Tc;
+                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+                        if (keep) {
+                            const int pos = out + __popc(bal & ((1u << lane) - 1u));
+                            kj[pos] = kv[r];
+                            ij[pos] = iv[r];
+                        }
+                        out += __popc(bal);
                     }
-                    out += __popc(bal);
                 }
                 __syncwarp();
                 cnt = out;
