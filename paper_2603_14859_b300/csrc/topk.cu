@@ -285,8 +285,9 @@ Layout make_layout(int64_t J, int64_t N, int L, int k, int mode, const Tuning& t
     s.off_xs = o; o = align256(o + (size_t)s.Np * s.ldxs * sizeof(float));
     s.off_w = o; o = align256(o + MAXL * sizeof(float));
     s.off_tgroup = o; o = align256(o + (size_t)s.nvt * sizeof(int32_t));
-    // queue words: count, queued positions in use, then per group its count, cursor and first position
-    s.off_rq = o; o = align256(o + (size_t)(2 + 3 * s.G + 1) * sizeof(int32_t));
+    // queue words: count, queued positions in use, then per group its count, cursor and first position,
+    // then the rescue lists' capacity
+    s.off_rq = o; o = align256(o + (size_t)(2 + 3 * s.G + 2) * sizeof(int32_t));
     s.off_rrow = o; o = align256(o + (size_t)s.rcapa * sizeof(int32_t));
     s.off_rthr = o; o = align256(o + (size_t)s.rcapa * 2 * sizeof(float));   // thresholds, then first-net d_k
     s.off_rq2 = o; o = align256(o + (size_t)s.rcapa * 3 * sizeof(int32_t));   // the queue sorted by group
@@ -1086,6 +1087,7 @@ struct BatchTc {
     float* dump;                 // debug probe: raw keys, Jp x Np (null in production)
     int64_t ld_dump;
     const int32_t* dyn_count[MAX_ITEMS];   // rescue pass: voxels queued per item (null: all J)
+    const int32_t* dyn_C[MAX_ITEMS];       // rescue pass: list capacity per queue position (null: the item's C)
     const int32_t* tgroup[MAX_ITEMS];      // per item: centring group of each voxel tile (null: group 0)
     int64_t grows[MAX_ITEMS];              // per item: rows of one group's copy of the draw operand
     int nseg;                    // > 1 (rescue pass): work items per voxel tile, each an interleaved
@@ -1495,7 +1497,10 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
             if (w < 0) break;
             const WorkPos wp = decode_work(P, w);
             const ItemTc& I = P.item[wp.it];
-            const ItemRegs R{I.N, I.keys, I.idx, I.C, I.C2};
+            // list capacity (a rescue pass reads the one its layout kernel chose) and half-list size
+            const int Cl = P.dyn_C[wp.it] ? *P.dyn_C[wp.it] : I.C;
+            const int C2l = P.dyn_C[wp.it] ? (I.C2 == I.C ? Cl : Cl / 2) : I.C2;
+            const ItemRegs R{I.N, I.keys, I.idx, Cl, C2l};
             const int64_t vt = wp.vt;
             const int ntiles = I.ktile ? I.kcount[vt] : I.ntiles, lim = I.lim, lim0 = I.lim0;
             const int32_t* kt_list = I.ktile ? I.ktile + vt * I.kstride : nullptr;
@@ -1508,7 +1513,7 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
             const bool valid = j < I.J && jrow >= 0;
             float thr = valid ? (I.thr0 ? I.thr0[j] : 3.0e38f) : -3.0e38f;
             int cnt = 0;
-            const int64_t lbase = jrow * (int64_t)I.C + hh * I.C2;   // this thread's half-list
+            const int64_t lbase = jrow * (int64_t)Cl + hh * C2l;     // this thread's half-list
             // rescue pass: the voxel's threshold is fixed and its draw tiles are shared among
             // several CTAs, which reserve list entries atomically (no compaction)
             const bool shared_list = !TOPR && I.rows != nullptr;
@@ -1720,7 +1725,7 @@ __global__ void k_need_threshold(const __grid_constant__ BatchNeed B) {
 // voxel's packed operand row into the compact A operand.  The rescue pass lists by queue
 // position (counts and thresholds of its own, zeroed on the host).
 // Queue words: [0] voxels queued, [1] positions in use (runs padded), [2, 2+G) counts,
-// [2+G, 2+2G) cursors, [2+2G, 3+3G) first positions.
+// [2+G, 2+2G) cursors, [2+2G, 3+3G) first positions, [3+3G] the rescue lists' capacity.
 struct RescueItem {
     int32_t* words;
     const int32_t* qrows;
@@ -1734,6 +1739,8 @@ struct RescueItem {
     int G, Kp;
     const __nv_bfloat16* A;
     __nv_bfloat16* RA;
+    int64_t list_entries;        // the scan's candidate-list space (entries), shared by the rescue lists
+    int Cr;                      // the rescue lists' capacity with the whole queue in use
 };
 
 struct BatchRescue {
@@ -1773,6 +1780,12 @@ __global__ void k_rescue_layout(const __grid_constant__ BatchRescue B) {
         }
         first[I.G] = off;
         I.words[1] = off;
+        // the list space over the positions in use: a short queue gets long lists (at most 2^26
+        // entries, so that a list's count stays far below its overflow flag, bit 30)
+        int64_t cap = I.list_entries / (off > 0 ? off : 1);
+        cap = cap < (1 << 26) ? cap : (1 << 26);
+        cap &= ~(int64_t)1;
+        I.words[2 + 3 * I.G + 1] = (int32_t)(cap > I.Cr ? cap : I.Cr);
     }
     __syncthreads();
     const int32_t total = I.words[1];
@@ -1846,6 +1859,7 @@ struct FinItem {
     const float* w;              // frame weights (device copy in the workspace)
     const int32_t* rows;         // rescue pass: packed row of each queue position (lists by position), or null
     const int32_t* rcount;       // rescue pass: voxels queued
+    const int32_t* dyn_C;        // rescue pass: list capacity per queue position (null: C)
     int32_t* rq_rows;            // first pass of the split form: the rescue queue (null: no rescue)
     float* rq_thr;
     float* rq_dk;                // the queued net's exact k-th distance (first pass writes, rescue reads)
@@ -1982,14 +1996,16 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
     if (j < 0) return;                                          // rescue padding
     const int64_t lr = P.rows ? gpos : j;                       // list row (the rescue lists by position)
     const int64_t vox = P.perm ? (int64_t)P.perm[j] : j;        // voxel of that row
-    float* kj = P.keys + lr * P.C;
-    int32_t* ij = P.idx + lr * P.C;
+    const int Cf = P.dyn_C ? *P.dyn_C : P.C;                    // list capacity
+    const int C2f = P.dyn_C ? (P.C2 == P.C ? Cf : Cf / 2) : P.C2;
+    float* kj = P.keys + lr * Cf;
+    int32_t* ij = P.idx + lr * Cf;
     const int raw0 = P.cnt[lr], raw1 = P.cnt[lr + P.hstride];
     const int raw = raw0 | raw1;                          // an overflow flag from either half
     const int c0h = raw0 & 0x3FFFFFFF, c1h = raw1 & 0x3FFFFFFF;
     int cnt = c0h + c1h;
     // one contiguous list
-    if (!(raw & 0x40000000)) merge_halves(kj, ij, P.C2, c0h, c1h, lane);
+    if (!(raw & 0x40000000)) merge_halves(kj, ij, C2f, c0h, c1h, lane);
     for (int l = lane; l < P.L; l += 32) {
         ys[l] = P.y[vox * P.ldy + l];
         ws[l] = P.w[l];
@@ -2263,11 +2279,11 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
                 ij[pos] = gidx;
             }
             cnt += __popc(bal);
-            if (cnt > P.C - 32) {
+            if (cnt > Cf - 32) {
                 __syncwarp();
                 const uint32_t T = warp_select(kj, cnt, P.k - 1, 4, hist, lane);
-                const int q = warp_compact(kj, ij, cnt, T, P.C - 64, lane);
-                cnt = q < P.C - 64 ? q : P.C - 64;
+                const int q = warp_compact(kj, ij, cnt, T, Cf - 64, lane);
+                cnt = q < Cf - 64 ? q : Cf - 64;
                 thr = key2f(T);
             }
         };
@@ -2658,7 +2674,7 @@ bool layout_consistent(const Layout& L) {
                           (size_t)L.Np * 4, (size_t)3 * L.Np * 4 + 32, (size_t)(ORDER_BUCKETS + ORDER_BUCKETS / 1024) * 4,
                           (size_t)3 * L.Jp * 4, (size_t)3 * L.Np * 4, (size_t)6 * L.nt64 * 4,
                           (size_t)L.nvt * L.nt64 * 4, (size_t)L.nvt * 4, (size_t)L.Np * L.ldxs * 4, MAXL * 4,
-                          (size_t)L.nvt * 4, (size_t)(2 + 3 * L.G + 1) * 4, (size_t)L.rcapa * 4, (size_t)L.rcapa * 8,
+                          (size_t)L.nvt * 4, (size_t)(2 + 3 * L.G + 2) * 4, (size_t)L.rcapa * 4, (size_t)L.rcapa * 8,
                           (size_t)L.rcapa * 12, (size_t)(L.rcapa / BM + 1) * 4, (size_t)L.rcapa * 8,
                           (size_t)L.rcapa * 8, (size_t)L.rcapa * L.Kp * 2};
     const int n = (int)(sizeof off / sizeof off[0]);
@@ -2768,7 +2784,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             W.sw[l] = sqrtf(sc[i].w[l]);
         }
         VPET_CUDA(cudaMemsetAsync(p.cnt, 0, (size_t)2 * L.Jp * sizeof(int32_t), s));
-        VPET_CUDA(cudaMemsetAsync(p.rq, 0, (size_t)(2 + 3 * L.G + 1) * sizeof(int32_t), s));
+        VPET_CUDA(cudaMemsetAsync(p.rq, 0, (size_t)(2 + 3 * L.G + 2) * sizeof(int32_t), s));
         if (L.rcapa > 0) VPET_CUDA(cudaMemsetAsync(p.rcnt, 0, (size_t)2 * L.rcapa * sizeof(int32_t), s));
         const bool order = dump == nullptr && L.J > 1;   // the debug dump keeps voxel order
         if (order) {
@@ -3099,7 +3115,8 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         const Layout& L = BL.lay[i];
         const Ptrs& p = ptr[i];
         RB.item[i] = RescueItem{p.rq,   p.rrow, p.rthr, p.rthr + L.rcapa, p.rrow2, p.rthr2, p.rdk2,
-                                p.rtg,  queue_cap(L), L.Jg, L.J, L.G, L.Kp, p.A, p.RA};
+                                p.rtg,  queue_cap(L), L.Jg, L.J, L.G, L.Kp, p.A, p.RA,
+                                L.lrows * (int64_t)L.C, L.Cr};
     }
     RB.n_items = n;
     k_rescue_count<<<(unsigned)num_sms() * 2, 256, 0, s>>>(RB);
@@ -3156,6 +3173,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
             T.item[oi].kstride = L.nt64;
         }
         T.dyn_count[oi] = p.rq + 1;
+        T.dyn_C[oi] = p.rq + 2 + 3 * L.G + 1;
         T.vt_prefix[oi + 1] = T.vt_prefix[oi] + L.rcapa / BM * RESCUE_SEGMENTS;
     }
     T.nseg = RESCUE_SEGMENTS;
@@ -3175,6 +3193,7 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         f.cnt = ptr[i].rcnt;
         f.thr = ptr[i].rthrh;
         f.hstride = L.rcapa;
+        f.dyn_C = ptr[i].rq + 2 + 3 * L.G + 1;
         f.rq_rows = nullptr;
         f.rq_thr = nullptr;
         f.rq_dk = ptr[i].rdk2;   // read by the rescue finalize
