@@ -145,20 +145,28 @@ class ClockSampler:
 # ------------------------------------------------------------------ CPU oracle baseline
 def cpu_baseline(W, seconds_budget=20.0, distance="l2"):
     """The FP64 oracle as it stands, timed on this host on a bounded sample of the
-    workload and scaled to voxels/s of the full volume (with the step's distance)."""
+    workload and scaled to voxels/s of the full volume (with the step's distance).  The
+    sample is sized from a short probe so that about half of seconds_budget goes to
+    simulating draws (shared among the models by their draw counts) and half to ranking
+    sampled voxels against them."""
     import oracle
     from paper_2603_14859_b300 import synth as S
     oracle.build()
     cores = oracle.num_threads()
     L = W.L
-    # 1. simulation cost per draw, per model (sample of draws)
+    # 1. simulation cost per draw, per model
     t_sim = 0.0
     xs = []
     sim_desc = []
     for model, n in zip(W.models, W.n_per_model):
         lo, hi = W.priors(model)
-        ns = 2000 if model != S.LPNTPET else 2000
-        ns = min(ns, n)
+        probe = min(256, n)
+        th = oracle.sample_prior(W.prior_seed, model, lo, hi, probe)
+        t0 = time.perf_counter()
+        oracle.simulate(model, W.ts, W.te, W.inp, th)
+        per_draw = max((time.perf_counter() - t0) / probe, 1e-9)
+        share = 0.5 * seconds_budget * n / max(W.N, 1)
+        ns = int(min(n, 200_000, max(probe, share / per_draw)))
         th = oracle.sample_prior(W.prior_seed, model, lo, hi, ns)
         t0 = time.perf_counter()
         x = oracle.simulate(model, W.ts, W.te, W.inp, th)
@@ -167,18 +175,27 @@ def cpu_baseline(W, seconds_budget=20.0, distance="l2"):
         xs.append(x)
         sim_desc.append(f"{ns} {S.MODEL_NAMES[model]} draws")
     xs = np.concatenate(xs)
-    # 2. distance + full sort per voxel: sample of voxels against the sampled draws
+    # 2. distance + full sort per voxel: sampled voxels against the sampled draws
     rng = np.random.default_rng(0)
-    y = (xs[rng.integers(0, len(xs), 64)] * (1 + 0.1 * rng.standard_normal((64, L)))).astype(np.float32)
+    rank = oracle.topk_l1 if distance == "l1" else oracle.topk
     k = min(W.k, len(xs))
+
+    def voxels(nv):
+        return (xs[rng.integers(0, len(xs), nv)] * (1 + 0.1 * rng.standard_normal((nv, L)))).astype(np.float32)
+
     t0 = time.perf_counter()
-    (oracle.topk_l1 if distance == "l1" else oracle.topk)(y, xs, W.weights, k)
+    rank(voxels(16), xs, W.weights, k)
+    per_voxel = max((time.perf_counter() - t0) / 16, 1e-9)
+    nv = int(min(4096, max(16, 0.5 * seconds_budget / per_voxel)))
+    y = voxels(nv)
+    t0 = time.perf_counter()
+    rank(y, xs, W.weights, k)
     dt = time.perf_counter() - t0
-    per_pair = dt / (64 * len(xs))
+    per_pair = dt / (nv * len(xs))
     t_topk = per_pair * W.J * W.N * math.log(W.N) / math.log(len(xs))   # n log n sort
     total = t_sim + t_topk
     return {"value": W.J / total, "unit": "voxels/s", "cores": cores, "kind": "oracle",
-            "sample": (f"simulation timed on {', '.join(sim_desc)}; {distance} distance+sort timed on 64 voxels x "
+            "sample": (f"simulation timed on {', '.join(sim_desc)}; {distance} distance+sort timed on {nv} voxels x "
                        f"{len(xs)} draws; scaled to {W.J} voxels x {W.N} draws (sort as n log n)"),
             "pairs_per_s": W.J * W.N / total}
 
@@ -553,7 +570,7 @@ def main():
         vals = []
         cb = None
         for _ in range(args.warmup + args.steps):
-            cb = cpu_baseline(W, distance=args.distance)
+            cb = cpu_baseline(W, seconds_budget=10.0, distance=args.distance)
             vals.append(cb["value"])
         v = statistics.median(vals[args.warmup:]) if args.steps else vals[-1]
         cb["value"] = v
