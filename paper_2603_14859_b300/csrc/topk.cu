@@ -1178,12 +1178,21 @@ __device__ __forceinline__ float pick32(const float (&v)[32], int b) {
     return (b & 16) ? l1[1] : l1[0];
 }
 
+// Element b (0..7, any lane-varying value) of the 8-key group v[o .. o+7], by a select tree.
+__device__ __forceinline__ float pick8(const float (&v)[32], int o, int b) {
+    const bool b0 = b & 1;
+    const float a0 = b0 ? v[o + 1] : v[o], a1 = b0 ? v[o + 3] : v[o + 2];
+    const float a2 = b0 ? v[o + 5] : v[o + 4], a3 = b0 ? v[o + 7] : v[o + 6];
+    const float c0 = (b & 2) ? a1 : a0, c1 = (b & 2) ? a3 : a2;
+    return (b & 4) ? c1 : c0;
+}
+
 // One 32-column chunk of the epilogue, per thread (= voxel): the minima of
 // the four 8-key groups against the voxel's threshold; a thread with a passing
-// group builds the mask of passing keys (passing groups only), copies its 32
-// keys to its own row of shared memory (row_s) and appends each passing key,
-// read back by position, to its half-list (starting at entry lbase).  Threads
-// never wait for one another.
+// group copies its 32 keys to its own row of shared memory (row_s, if any) and, group
+// by passing group, appends each passing key to its half-list (starting at entry
+// lbase), read back by position from the row or picked from the group's eight
+// registers.  Threads never wait for one another.
 // acnt != null (rescue pass): several CTAs append to the voxel's half-list, each chunk
 // reserving its entries by an atomic add on the list's count; a list that would pass its
 // capacity is flagged (0x40000000) instead, and its voxel takes the exact scan.
@@ -1198,12 +1207,6 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
     float gm;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(gm) : "f"(g0), "f"(g1), "f"(g2));
     if (fminf(gm, g3) > thr) return;
-    // only the 8-key groups whose minimum passes are examined key by key
-    uint32_t m = 0;
-    if (g0 <= thr) m |= mask8(v, 0, thr);
-    if (g1 <= thr) m |= mask8(v, 8, thr) << 8;
-    if (g2 <= thr) m |= mask8(v, 16, thr) << 16;
-    if (g3 <= thr) m |= mask8(v, 24, thr) << 24;
     // the passing keys are read back by position from this thread's own row of shared memory,
     // or (row_s null: passing keys are rare) picked from the registers by a select tree
     if (row_s) {
@@ -1211,7 +1214,31 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
 #pragma unroll
         for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
-    if (acnt) {
+    if (!acnt) {
+        // only the 8-key groups whose minimum passes are examined key by key, in key order
+        float* kp = I.keys + lbase;
+        int32_t* ip = I.idx + lbase;
+        const float gmin[4] = {g0, g1, g2, g3};
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            if (gmin[g] > thr) continue;
+            uint32_t m = mask8(v, 8 * g, thr);
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                kp[cnt] = row_s ? row_s[8 * g + b] : pick8(v, 8 * g, b);
+                ip[cnt] = (int32_t)(n0 + 8 * g + b);
+                ++cnt;
+            }
+        }
+        return;
+    }
+    uint32_t m = 0;
+    if (g0 <= thr) m |= mask8(v, 0, thr);
+    if (g1 <= thr) m |= mask8(v, 8, thr) << 8;
+    if (g2 <= thr) m |= mask8(v, 16, thr) << 16;
+    if (g3 <= thr) m |= mask8(v, 24, thr) << 24;
+    {
         const int n = __popc(m);
         int pos = atomicAdd(acnt, n);
         if (pos + n > I.C2) {
@@ -1225,14 +1252,6 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
             I.idx[lbase + pos] = (int32_t)(n0 + b);
             ++pos;
         }
-        return;
-    }
-    while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        I.keys[lbase + cnt] = (row_s ? row_s[b] : pick32(v, b));
-        I.idx[lbase + cnt] = (int32_t)(n0 + b);
-        ++cnt;
     }
 }
 
@@ -1259,30 +1278,33 @@ __device__ __forceinline__ void topr_chunk(TopR& S, float (&v)[32], int64_t n0, 
     float gm;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(gm) : "f"(g0), "f"(g1), "f"(g2));
     if (fminf(gm, g3) > S.thr) return;
-    uint32_t m = 0;
-    if (g0 <= S.thr) m |= mask8(v, 0, S.thr);
-    if (g1 <= S.thr) m |= mask8(v, 8, S.thr) << 8;
-    if (g2 <= S.thr) m |= mask8(v, 16, S.thr) << 16;
-    if (g3 <= S.thr) m |= mask8(v, 24, S.thr) << 24;
-    while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        const float x = pick32(v, b);
-        if (S.n_in < S.r) {
-            S.A[S.n_in * 128] = x;
-            if (S.n_in == 0 || x > S.amax) { S.amax = x; S.imax = S.n_in; }
-            if (++S.n_in == S.r) S.thr = fminf(S.thr_in, S.amax);
-        } else if (x < S.amax) {
-            S.A[S.imax * 128] = x;
-            float mx = S.A[0];
-            int im = 0;
-            for (int i = 1; i < S.r; ++i) {
-                const float a = S.A[i * 128];
-                if (a > mx) { mx = a; im = i; }
+    // group by group (a later group's mask is taken against the threshold as it then stands,
+    // which keeps the same keys as one mask taken first)
+    const float gmin[4] = {g0, g1, g2, g3};
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        if (gmin[g] > S.thr) continue;
+        uint32_t m = mask8(v, 8 * g, S.thr);
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const float x = pick8(v, 8 * g, b);
+            if (S.n_in < S.r) {
+                S.A[S.n_in * 128] = x;
+                if (S.n_in == 0 || x > S.amax) { S.amax = x; S.imax = S.n_in; }
+                if (++S.n_in == S.r) S.thr = fminf(S.thr_in, S.amax);
+            } else if (x < S.amax) {
+                S.A[S.imax * 128] = x;
+                float mx = S.A[0];
+                int im = 0;
+                for (int i = 1; i < S.r; ++i) {
+                    const float a = S.A[i * 128];
+                    if (a > mx) { mx = a; im = i; }
+                }
+                S.amax = mx;
+                S.imax = im;
+                S.thr = fminf(S.thr_in, mx);
             }
-            S.amax = mx;
-            S.imax = im;
-            S.thr = fminf(S.thr_in, mx);
         }
     }
 }
@@ -1527,9 +1549,13 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                 if (kt_list && t + wp.nseg < ntiles) tnext = kt_list[t + wp.nseg];
                 const uint32_t acc = gt & 1u;
                 const uint32_t aph = (gt >> 1) & 1u;
-                if (__any_sync(0xFFFFFFFFu, *s_err != 0)) { stop = true; break; }
-                if (!ptx::mbar_wait(ptx::smem_u32(&tfull[acc]), aph, WAIT_NS)) { *s_err = 1; }
-                if (__any_sync(0xFFFFFFFFu, *s_err != 0)) { stop = true; break; }
+                // one vote per tile: this warp's wait ran out, or another role flagged an error
+                // (a role that stopped leaves this wait to run out at its bound)
+                {
+                    const bool ok = ptx::mbar_wait(ptx::smem_u32(&tfull[acc]), aph, WAIT_NS);
+                    if (!ok) *s_err = 1;
+                    if (__any_sync(0xFFFFFFFFu, !ok || *s_err != 0)) { stop = true; break; }
+                }
                 ptx::tc_fence_after();
                 const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
                 if (DUMP) {
@@ -1544,8 +1570,8 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
                     }
                 } else {
                     // one 32-column load at a time (fewer live registers than overlapping two
-                    // loads, which measured slower)
-#pragma unroll 1
+                    // loads, which measured slower); the chunk loop unrolled
+#pragma unroll
                     for (int c = hh; c < BN / 32; c += CSTEP) {
                         uint32_t r[32];
                         ptx::tmem_ld32_async(ta + c * 32, r);
