@@ -227,7 +227,8 @@ int abc_topk_status_noalloc(int32_t status_host[8], void* stream);
 /* Status of the last abc_discrepancy_topk that used this workspace.  Blocks
  * on `stream`.  Writes
  *   status[0] = ABC_OK or ABC_ERR_TIMEOUT (a bounded device wait ran out; the
- *               outputs are then not valid);
+ *               outputs are then not valid), or ABC_ERR_UNSUPPORTED (an internal
+ *               consistency check of the k-d row order failed; outputs not valid);
  *   status[1] = number of voxels resolved by an exact fp32 scan of all draws
  *               (ABC_FP32 voxels whose tensor-core result could not be
  *               certified, or whose candidate list overflowed; exact results);
@@ -280,6 +281,13 @@ int abc_debug_inject_stall(int64_t withheld_tile, uint64_t wait_ns);
  * scan's voxels.  0 turns the hook off.  Results do not change, only the path.
  * Process-wide; for tests only.  ABC_ERR_ARG for a mode outside 0..7. */
 int abc_debug_force_rescue(int32_t mode);
+
+/* Test hook for the row order of voxels and draws (which decides only how many draw
+ * tiles each pass can skip, never a result).  mode 0: k-d splits for scans of at least
+ * 2^36 voxel-draw pairs, the Morton key below; 1: the Morton key always; 2: k-d splits
+ * always (scans of at least 256 rows, when the scratch holds them).  Process-wide; for
+ * tests only.  ABC_ERR_ARG for a mode outside 0..2. */
+int abc_debug_order(int32_t mode);
 
 /* Diagnostics: grid size of the last fused-kernel launch of this process, the
  * CTAs per SM its variant can keep resident (shared memory, registers and TMEM

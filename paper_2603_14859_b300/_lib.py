@@ -31,7 +31,7 @@ EXPORTS = [
     "abc_mlp_loss_grad", "abc_adam_update", "abc_add_noise", "abc_local_abc_smem_bytes", "abc_local_abc",
     "abc_unit_box", "abc_topk_work", "abc_local_abc_table", "abc_response_cri",
     "abc_l1_workspace_size", "abc_discrepancy_topk_l1", "abc_l1_status", "abc_topk_status_noalloc",
-    "abc_debug_inject_stall", "abc_debug_force_rescue", "abc_fallback_scratch_size", "abc_fallback_rows",
+    "abc_debug_inject_stall", "abc_debug_force_rescue", "abc_debug_order", "abc_fallback_scratch_size", "abc_fallback_rows",
     "abc_gather_rows", "abc_scatter_rows", "abc_quantile_scratch_size", "abc_median_rel_quantile",
     "abc_mlp_status",
 ]
@@ -89,6 +89,7 @@ def lib():
     L.abc_topk_status_noalloc.argtypes = [P, P]
     L.abc_debug_inject_stall.argtypes = [i64, u64]
     L.abc_debug_force_rescue.argtypes = [i32]
+    L.abc_debug_order.argtypes = [i32]
     L.abc_default_tuning.argtypes = [i32, ctypes.POINTER(Tuning)]
     L.abc_set_default_tuning.argtypes = [ctypes.POINTER(Tuning)]
     L.abc_launch_info.argtypes = [P, P, P]
@@ -136,7 +137,7 @@ def lib():
                "abc_mlp_forward", "abc_mlp_loss_grad", "abc_adam_update", "abc_add_noise", "abc_local_abc", "abc_unit_box", "abc_topk_work",
                "abc_local_abc_table", "abc_response_cri", "abc_discrepancy_topk_l1", "abc_l1_status",
                "abc_fallback_rows", "abc_gather_rows", "abc_scatter_rows", "abc_median_rel_quantile", "abc_mlp_status",
-               "abc_topk_status_noalloc", "abc_debug_inject_stall", "abc_debug_force_rescue"]:
+               "abc_topk_status_noalloc", "abc_debug_inject_stall", "abc_debug_force_rescue", "abc_debug_order"]:
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L

@@ -557,6 +557,417 @@ __global__ void k_order_scatter(const float* __restrict__ feat, const uint32_t* 
 // delta = bf16(yh) - yh: c0 = -2 delta . yh and dn = ||delta|| (certificate).
 // Weighted sums of the three consecutive thirds of a TAC (the features of the
 // tile bound), computed by a warp; every lane gets them.
+// ------------------------------------------------------------------ k-d order
+// For a large scan the rows (the voxels; the draws of each pilot group) are ordered by a k-d
+// split of their bound coordinates u_c = F_c / sqrt(W_c) (F_c the weighted sum over third c of
+// the frames: the coordinates in which the tile bound measures gaps).  A run [a, b) of the
+// order that contains a 128-row tile boundary splits its widest coordinate at the boundary
+// nearest its middle, so every tile is one leaf, and its rows are those a median split put
+// together: tighter tile boxes than runs of a space-filling curve.  The split value comes from
+// a KD_BINS-bin histogram of the run's values on that coordinate; the rows of the bin holding
+// the boundary go to either side by ticket.  Levels run breadth first; node n of level l has
+// the children 2n and 2n + 1 (dense numbering; the roots are the pilot groups).
+constexpr int KD_BINS = 128;
+constexpr int KD_TILE = 128;
+constexpr int KD_MAX_GROUPS = MAX_PILOT_LEVELS + 1;
+constexpr double KD_MIN_PAIRS = 68719476736.0;   // 2^36 voxel-draw pairs: scans at least this large
+
+struct KdNode {
+    int32_t a, b;          // the run [a, b) of the order
+    int32_t m;             // split position (a multiple of KD_TILE), b for a leaf
+    int32_t dim;           // the widest coordinate
+    float lo, inv;         // bin of a value v: (v - lo) inv, clamped to [0, KD_BINS)
+    int32_t bstar, need;   // the bin holding the boundary, its rows that go left
+    int32_t lcur, rcur, tick;
+    uint32_t box[6];       // ordered-integer min, max per coordinate
+};
+
+struct KdGroups {
+    int32_t start[KD_MAX_GROUPS + 1];   // group q holds positions [start[q], start[q + 1])
+    int n;                              // groups
+    int frozen;                         // a group kept in arbitrary order (the coarsest pilot's), or -1
+    int nlev;                           // pilot levels (group q = nlev - pilot levels the row is in)
+    int64_t s1;                         // pilot stride
+    float isw[3];                       // 1 / sqrt(W_c)
+};
+
+__device__ __forceinline__ int kd_bin(float v, float lo, float inv) {
+    const float t = (v - lo) * inv;
+    return t >= 1.0f ? (int)fminf(t, (float)(KD_BINS - 1)) : 0;   // NaN and t < 1: bin 0
+}
+
+// an internal inconsistency (never expected): the outputs are flagged as not valid
+__device__ __forceinline__ void kd_fail(int32_t* status) { atomicCAS(status, 0, ABC_ERR_UNSUPPORTED); }
+
+// Bound coordinates of each row, its pilot group, and its place in the group's run (by ticket).
+__global__ void k_kd_seed(const float* __restrict__ x, int64_t N, int ldx, int L, Weights W, KdGroups G,
+                          int32_t* __restrict__ gcur, float4* __restrict__ kf, int32_t* __restrict__ krow,
+                          int32_t* __restrict__ knode, int32_t* __restrict__ status) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = j < N;
+    float F[3] = {0.0f, 0.0f, 0.0f};
+    int q = -1;
+    if (valid) {
+        const float* r = x + j * ldx;
+        for (int l = 0; l < L; ++l) {
+            const int c = (3 * l) / L;
+            const float v = W.w[l] * r[l];
+            F[0] += c == 0 ? v : 0.0f;
+            F[1] += c == 1 ? v : 0.0f;
+            F[2] += c == 2 ? v : 0.0f;
+        }
+        int g = 0;
+        int64_t sl = G.s1;
+        for (int l = 1; l <= G.nlev; ++l, sl *= G.s1) g += (j % sl) == 0;
+        q = G.nlev - g;
+    }
+    // tickets per group, one atomic per group present in the warp
+    const uint32_t same = __match_any_sync(0xFFFFFFFFu, q);
+    const int leader = __ffs(same) - 1;
+    int base = 0;
+    if (valid && lane == leader) base = atomicAdd(&gcur[q], __popc(same));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (!valid) return;
+    const int64_t pos = (int64_t)G.start[q] + base + __popc(same & ((1u << lane) - 1u));
+    if (pos >= G.start[q + 1]) {
+        kd_fail(status);
+        return;
+    }
+    kf[pos] = make_float4(F[0] * G.isw[0], F[1] * G.isw[1], F[2] * G.isw[2], 0.0f);
+    krow[pos] = (int32_t)j;
+    knode[pos] = q;
+}
+
+// Level roots: group q is node q of level 0.
+__global__ void k_kd_roots(KdGroups G, KdNode* __restrict__ nd) {
+    const int q = threadIdx.x;
+    if (q < G.n) {
+        nd[q].a = G.start[q];
+        nd[q].b = G.start[q + 1];
+    }
+}
+
+// Clears the boxes, cursors and histograms of the nn nodes of a level.
+__global__ void k_kd_level_init(KdNode* __restrict__ nd, uint32_t* __restrict__ hist, int64_t nn) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nn * KD_BINS) hist[i] = 0u;
+    if (i < nn) {
+        KdNode& n = nd[i];
+        for (int c = 0; c < 3; ++c) {
+            n.box[2 * c] = 0xFFFFFFFFu;
+            n.box[2 * c + 1] = 0u;
+        }
+        n.lcur = n.rcur = n.tick = 0;
+        n.m = n.b;
+    }
+}
+
+// Node boxes: one set of atomics per warp whose rows share a node (runs are contiguous).
+__global__ void k_kd_box(const float4* __restrict__ kf, const int32_t* __restrict__ knode, int64_t N,
+                         KdNode* __restrict__ nd) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = p < N;
+    const int node = valid ? knode[p] : -1;
+    float f[3] = {0.0f, 0.0f, 0.0f};
+    if (valid) {
+        const float4 v = kf[p];
+        f[0] = v.x;
+        f[1] = v.y;
+        f[2] = v.z;
+    }
+    const int n0 = __shfl_sync(0xFFFFFFFFu, node, 0);
+    if (__all_sync(0xFFFFFFFFu, valid && node == n0)) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t u = ord_f2u(f[c]);
+            const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, u), mx = __reduce_max_sync(0xFFFFFFFFu, u);
+            if (lane == 0) {
+                atomicMin(&nd[n0].box[2 * c], mn);
+                atomicMax(&nd[n0].box[2 * c + 1], mx);
+            }
+        }
+    } else if (valid) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            atomicMin(&nd[node].box[2 * c], ord_f2u(f[c]));
+            atomicMax(&nd[node].box[2 * c + 1], ord_f2u(f[c]));
+        }
+    }
+}
+
+// Per node of level `level`: whether it splits (it holds a tile boundary and is not in the
+// frozen group), where, and along which coordinate.
+__global__ void k_kd_dims(KdNode* __restrict__ nd, int64_t nn, int level, int frozen) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    KdNode& n = nd[i];
+    const int32_t a = n.a, b = n.b;
+    const int32_t first = (a / KD_TILE + 1) * KD_TILE;   // the first boundary past a
+    if (first >= b || (frozen >= 0 && (i >> level) == frozen)) {
+        n.m = b;
+        return;
+    }
+    int d = 0;
+    float best = -1.0f, lo = 0.0f;
+    for (int c = 0; c < 3; ++c) {
+        const float l = ord_u2f(n.box[2 * c]), h = ord_u2f(n.box[2 * c + 1]);
+        const float w = h - l;
+        if (w > best) {
+            best = w;
+            d = c;
+            lo = l;
+        }
+    }
+    n.dim = d;
+    n.lo = lo;
+    n.inv = (best > 0.0f && best < 3.0e38f) ? (float)KD_BINS / best : 0.0f;
+    const int32_t last = ((b - 1) / KD_TILE) * KD_TILE;   // the last boundary before b
+    int32_t m = (int32_t)((((int64_t)a + b) / 2 + KD_TILE / 2) / KD_TILE) * KD_TILE;
+    n.m = m < first ? first : (m > last ? last : m);
+}
+
+// Histogram of each splitting node's values on its coordinate: in shared memory for a block
+// whose rows share one node (the runs are contiguous), else in global memory.
+__global__ void __launch_bounds__(256) k_kd_hist(const float4* __restrict__ kf, const int32_t* __restrict__ knode,
+                                                 int64_t N, const KdNode* __restrict__ nd,
+                                                 uint32_t* __restrict__ hist) {
+    __shared__ uint32_t sh[KD_BINS];
+    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t p = p0 + threadIdx.x;
+    const int64_t plast = (p0 + blockDim.x <= N ? p0 + blockDim.x : N) - 1;
+    const bool uni = knode[p0] == knode[plast];
+    if (uni)
+        for (int i = threadIdx.x; i < KD_BINS; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+    if (p < N) {
+        const int node = knode[p];
+        const KdNode& n = nd[node];
+        if (n.m < n.b) {
+            const float4 v = kf[p];
+            const float u = n.dim == 0 ? v.x : (n.dim == 1 ? v.y : v.z);
+            const int bin = kd_bin(u, n.lo, n.inv);
+            if (uni) atomicAdd(&sh[bin], 1u);
+            else atomicAdd(&hist[(int64_t)node * KD_BINS + bin], 1u);
+        }
+    }
+    __syncthreads();
+    if (uni) {
+        const int node = knode[p0];
+        for (int i = threadIdx.x; i < KD_BINS; i += blockDim.x)
+            if (sh[i]) atomicAdd(&hist[(int64_t)node * KD_BINS + i], sh[i]);
+    }
+}
+
+// One warp per node: the bin holding the split position and the count of its rows that go
+// left; the children's runs for the next level (a leaf passes its run to child 2n).
+__global__ void k_kd_split(KdNode* __restrict__ nd, const uint32_t* __restrict__ hist, int64_t nn,
+                           KdNode* __restrict__ nx, int32_t* __restrict__ status) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= nn) return;
+    KdNode& n = nd[i];
+    const int32_t a = n.a, b = n.b, m = n.m;
+    if (lane == 0) {
+        nx[2 * i].a = a;
+        nx[2 * i].b = m;
+        nx[2 * i + 1].a = m;
+        nx[2 * i + 1].b = b;
+    }
+    if (m >= b) return;
+    const int target = m - a;
+    uint32_t h[KD_BINS / 32], sum = 0;
+#pragma unroll
+    for (int q = 0; q < KD_BINS / 32; ++q) {
+        h[q] = hist[i * KD_BINS + lane * (KD_BINS / 32) + q];
+        sum += h[q];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    uint32_t c = incl - sum;
+    int found = -1, below = 0;
+#pragma unroll
+    for (int q = 0; q < KD_BINS / 32; ++q) {
+        if (found < 0 && c + h[q] >= (uint32_t)target) {
+            found = lane * (KD_BINS / 32) + q;
+            below = (int)c;
+        }
+        c += h[q];
+    }
+    const uint32_t who = __ballot_sync(0xFFFFFFFFu, found >= 0);
+    if (total != (uint32_t)(b - a) || !who) {
+        if (lane == 0) kd_fail(status);
+        return;
+    }
+    const int src = __ffs(who) - 1;
+    if (lane == src) {
+        n.bstar = found;
+        n.need = target - below;
+    }
+}
+
+// Rows to their child runs: below the boundary's bin left, above it right, and in it by
+// ticket (the first `need` tickets left).  One set of atomics per warp whose rows share a
+// node; a leaf's rows keep their places.
+__global__ void k_kd_scatter(const float4* __restrict__ kf, const int32_t* __restrict__ krow,
+                             const int32_t* __restrict__ knode, int64_t N, KdNode* __restrict__ nd,
+                             float4* __restrict__ kf2, int32_t* __restrict__ krow2, int32_t* __restrict__ knode2,
+                             int32_t* __restrict__ status) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const bool valid = p < N;
+    const int node = valid ? knode[p] : -1;
+    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    int32_t a = 0, b = 0, m = 0;
+    int cls = -1;   // -1: stays (leaf), 0: left, 1: right, 2: the boundary's bin
+    if (valid) {
+        v = kf[p];
+        const KdNode& n = nd[node];
+        a = n.a;
+        b = n.b;
+        m = n.m;
+        if (m < b) {
+            const float u = n.dim == 0 ? v.x : (n.dim == 1 ? v.y : v.z);
+            const int bin = kd_bin(u, n.lo, n.inv);
+            cls = bin < n.bstar ? 0 : (bin > n.bstar ? 1 : 2);
+        }
+    }
+    const int n0 = __shfl_sync(0xFFFFFFFFu, node, 0);
+    const bool uni = __all_sync(0xFFFFFFFFu, valid && node == n0);
+    int64_t pos = p;
+    if (uni && cls >= 0) {   // the whole warp: one node that splits
+        KdNode& n = nd[n0];
+        const uint32_t tm = __ballot_sync(0xFFFFFFFFu, cls == 2);
+        int tb = 0;
+        if (lane == 0 && tm) tb = atomicAdd(&n.tick, __popc(tm));
+        tb = __shfl_sync(0xFFFFFFFFu, tb, 0);
+        if (cls == 2) cls = (tb + __popc(tm & lt)) < n.need ? 0 : 1;
+        const uint32_t lm = __ballot_sync(0xFFFFFFFFu, cls == 0), rm = ~lm;
+        int lb = 0, rb = 0;
+        if (lane == 0) {
+            if (lm) lb = atomicAdd(&n.lcur, __popc(lm));
+            if (rm) rb = atomicAdd(&n.rcur, __popc(rm));
+        }
+        lb = __shfl_sync(0xFFFFFFFFu, lb, 0);
+        rb = __shfl_sync(0xFFFFFFFFu, rb, 0);
+        pos = cls == 0 ? (int64_t)a + lb + __popc(lm & lt) : (int64_t)m + rb + __popc(rm & lt);
+    } else if (valid && cls >= 0) {
+        KdNode& n = nd[node];
+        if (cls == 2) cls = atomicAdd(&n.tick, 1) < n.need ? 0 : 1;
+        pos = cls == 0 ? (int64_t)a + atomicAdd(&n.lcur, 1) : (int64_t)m + atomicAdd(&n.rcur, 1);
+    }
+    if (!valid) return;
+    const int side = cls == 1 ? 1 : 0;
+    if (pos < (side ? m : a) || pos >= (cls < 0 ? b : (side ? b : m))) {
+        kd_fail(status);
+        return;
+    }
+    kf2[pos] = v;
+    krow2[pos] = krow[p];
+    knode2[pos] = 2 * node + side;
+}
+
+__global__ void k_kd_copy(const int32_t* __restrict__ src, int64_t N, int32_t* __restrict__ dst) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < N) dst[p] = src[p];
+}
+
+// Orders the N rows of x (row stride ldx) by the k-d split into perm (perm[p] = the row at
+// position p); with nlev > 0 the rows are first grouped by pilot level like the Morton
+// order (the coarsest pilot's group first and left in arbitrary order).  The work arrays
+// live in `scratch` (a buffer written only later in the call); done = false, nothing
+// launched, when it does not hold them.
+int kd_order(const float* x, int64_t N, int ldx, int L, const Weights& W, int nlev, int64_t s1, void* scratch,
+             size_t scratch_bytes, int32_t* perm, int32_t* status, cudaStream_t s, bool& done) {
+    done = false;
+    if (N < 2 * KD_TILE || N >= ((int64_t)1 << 30) || nlev + 1 > KD_MAX_GROUPS) return ABC_OK;
+    KdGroups G;
+    memset(&G, 0, sizeof G);
+    G.nlev = nlev;
+    G.s1 = s1 > 1 ? s1 : 2;
+    G.n = nlev + 1;
+    G.frozen = nlev > 0 ? 0 : -1;
+    // group q holds the rows in nlev - q pilot samples: ceil(N / s1^l) rows are in sample l
+    int64_t in_sample[KD_MAX_GROUPS + 1];
+    int64_t sl = 1;
+    for (int l = 0; l <= nlev; ++l, sl *= G.s1) in_sample[l] = (N + sl - 1) / sl;
+    in_sample[nlev + 1] = 0;
+    G.start[0] = 0;
+    for (int q = 0; q < G.n; ++q) {
+        const int g = nlev - q;   // pilot samples of the group's rows
+        const int64_t size = in_sample[g] - (g < nlev ? in_sample[g + 1] : 0);
+        G.start[q + 1] = (int32_t)(G.start[q] + size);
+    }
+    for (int c = 0; c < 3; ++c) {
+        double wc = 0.0;
+        for (int l = 0; l < L; ++l)
+            if ((3 * l) / L == c) wc += W.w[l];
+        G.isw[c] = wc > 0.0 ? (float)(1.0 / sqrt(wc)) : 0.0f;
+    }
+    // levels: every run of a group that holds a tile boundary halves its tiles per level
+    int levels = 0;
+    for (int q = 0; q < G.n; ++q) {
+        if (q == G.frozen || G.start[q + 1] <= G.start[q]) continue;
+        const int64_t pieces = (G.start[q + 1] - 1) / KD_TILE - G.start[q] / KD_TILE + 1;
+        int lv = 0;
+        while (((int64_t)1 << lv) < pieces) ++lv;
+        levels = lv > levels ? lv : levels;
+    }
+    if (levels == 0) return ABC_OK;
+    const int64_t nn_max = (int64_t)G.n << levels;   // nodes of the deepest table
+    // scratch: rows (two copies), node tables (two), histograms (a splitting level's)
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o = (o + bytes + 255) & ~(size_t)255; return at; };
+    const size_t o_kf0 = take((size_t)N * 16), o_kf1 = take((size_t)N * 16);
+    const size_t o_r0 = take((size_t)N * 4), o_r1 = take((size_t)N * 4);
+    const size_t o_n0 = take((size_t)N * 4), o_n1 = take((size_t)N * 4);
+    const size_t o_g = take(KD_MAX_GROUPS * 4);
+    const size_t o_d0 = take((size_t)nn_max * sizeof(KdNode)), o_d1 = take((size_t)nn_max * sizeof(KdNode));
+    const size_t o_h = take((size_t)(nn_max / 2) * KD_BINS * 4);
+    if (o > scratch_bytes) return ABC_OK;
+    uint8_t* sb = (uint8_t*)scratch;
+    float4* kf[2] = {(float4*)(sb + o_kf0), (float4*)(sb + o_kf1)};
+    int32_t* kr[2] = {(int32_t*)(sb + o_r0), (int32_t*)(sb + o_r1)};
+    int32_t* kn[2] = {(int32_t*)(sb + o_n0), (int32_t*)(sb + o_n1)};
+    int32_t* gcur = (int32_t*)(sb + o_g);
+    KdNode* nd[2] = {(KdNode*)(sb + o_d0), (KdNode*)(sb + o_d1)};
+    uint32_t* hist = (uint32_t*)(sb + o_h);
+    const unsigned gb = (unsigned)vpet_ceil_div(N, 256);
+    VPET_CUDA(cudaMemsetAsync(gcur, 0, KD_MAX_GROUPS * 4, s));
+    k_kd_seed<<<gb, 256, 0, s>>>(x, N, ldx, L, W, G, gcur, kf[0], kr[0], kn[0], status);
+    VPET_LAUNCH_CHECK();
+    k_kd_roots<<<1, 32, 0, s>>>(G, nd[0]);
+    VPET_LAUNCH_CHECK();
+    int c = 0;
+    for (int l = 0; l < levels; ++l) {
+        const int64_t nn = (int64_t)G.n << l;
+        k_kd_level_init<<<(unsigned)vpet_ceil_div(nn * KD_BINS, 256), 256, 0, s>>>(nd[c], hist, nn);
+        VPET_LAUNCH_CHECK();
+        k_kd_box<<<gb, 256, 0, s>>>(kf[c], kn[c], N, nd[c]);
+        VPET_LAUNCH_CHECK();
+        k_kd_dims<<<(unsigned)vpet_ceil_div(nn, 256), 256, 0, s>>>(nd[c], nn, l, G.frozen);
+        VPET_LAUNCH_CHECK();
+        k_kd_hist<<<gb, 256, 0, s>>>(kf[c], kn[c], N, nd[c], hist);
+        VPET_LAUNCH_CHECK();
+        k_kd_split<<<(unsigned)vpet_ceil_div(nn * 32, 256), 256, 0, s>>>(nd[c], hist, nn, nd[1 - c], status);
+        VPET_LAUNCH_CHECK();
+        k_kd_scatter<<<gb, 256, 0, s>>>(kf[c], kr[c], kn[c], N, nd[c], kf[1 - c], kr[1 - c], kn[1 - c], status);
+        VPET_LAUNCH_CHECK();
+        c = 1 - c;
+    }
+    k_kd_copy<<<gb, 256, 0, s>>>(kr[c], N, perm);
+    VPET_LAUNCH_CHECK();
+    done = true;
+    return ABC_OK;
+}
+
 __device__ __forceinline__ void seg_features(const float* r, int L, const float* w, int lane, float (&f)[3]) {
     f[0] = f[1] = f[2] = 0.0f;
     for (int l = lane; l < L; l += 32) {
@@ -2394,6 +2805,7 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 uint64_t g_wait_ns = WAIT_NS_DEFAULT;
 int64_t g_withhold = -1;
 int g_force_rescue = 0;        // test hook bits (abc_debug_force_rescue)
+int g_order_mode = 0;          // row order: 0 by scan size, 1 Morton, 2 k-d (abc_debug_order)
 cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
 int g_last_resident = 0;     // residency of the last configured fused-kernel variant
 int64_t g_last_grid = 0;     // grid of the last fused-kernel launch
@@ -2813,7 +3225,15 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         VPET_CUDA(cudaMemsetAsync(p.rq, 0, (size_t)(2 + 3 * L.G + 2) * sizeof(int32_t), s));
         if (L.rcapa > 0) VPET_CUDA(cudaMemsetAsync(p.rcnt, 0, (size_t)2 * L.rcapa * sizeof(int32_t), s));
         const bool order = dump == nullptr && L.J > 1;   // the debug dump keeps voxel order
-        if (order) {
+        // a large scan orders voxels and draws by k-d splits (tighter tile boxes, fewer tiles in
+        // every pass), a small one by the Morton key (fewer launches)
+        const bool kd = g_order_mode == 2 || (g_order_mode == 0 && (double)L.J * (double)L.N >= KD_MIN_PAIRS);
+        bool kd_done = false;
+        if (order && kd &&
+            (rc = kd_order(sc[i].y, L.J, sc[i].ldy, L.L, W, 0, 1, p.A, (size_t)L.Jp * L.Kp * 2, p.perm, status, s,
+                           kd_done)))
+            return rc;
+        if (order && !kd_done) {
             k_order_init<<<(unsigned)vpet_ceil_div(ORDER_BUCKETS, 256), 256, 0, s>>>(p.mm, p.hist);
             VPET_LAUNCH_CHECK();
             const unsigned gb = (unsigned)vpet_ceil_div(L.J, 256);
@@ -2842,7 +3262,12 @@ int run_batch(const ScanSpec* sc, int n, int mode, const Tuning& tu_in, void* ws
         VPET_LAUNCH_CHECK();
         // draws in the same kind of order (alike draws in the same tiles, so that tile boxes are tight)
         const bool xorder = dump == nullptr && L.N > 1;
-        if (xorder) {
+        bool xkd_done = false;
+        if (xorder && kd &&
+            (rc = kd_order(sc[i].x, L.N, sc[i].ldx, L.L, W, L.nlev, tu.pilot_stride, p.B,
+                           (size_t)L.G * L.Np * L.Kp * 2, p.xperm, status, s, xkd_done)))
+            return rc;
+        if (xorder && !xkd_done) {
             k_order_init<<<(unsigned)vpet_ceil_div(ORDER_BUCKETS, 256), 256, 0, s>>>(p.xmm, p.xhist);
             VPET_LAUNCH_CHECK();
             const unsigned gb = (unsigned)vpet_ceil_div(L.N, 256);
@@ -3367,6 +3792,13 @@ extern "C" int abc_debug_inject_stall(int64_t withheld_tile, uint64_t wait_ns) {
              "abc_debug_inject_stall: wait_ns must be 0 (default) or in [1 ms, 10 s]");
     g_withhold = withheld_tile < 0 ? -1 : withheld_tile;
     g_wait_ns = wait_ns == 0 ? WAIT_NS_DEFAULT : wait_ns;
+    return ABC_OK;
+}
+
+extern "C" int abc_debug_order(int32_t mode) {
+    vpet::clear_error();
+    VPET_ARG(mode >= 0 && mode <= 2, "abc_debug_order: mode must be 0, 1 or 2 (got %d)", mode);
+    g_order_mode = mode;
     return ABC_OK;
 }
 

@@ -241,6 +241,17 @@ def test_force_rescue_hook_mask_without_gpu(lib):
     assert lib.abc_debug_force_rescue(0) == _lib.ABC_OK
 
 
+def test_order_hook_modes_without_gpu(lib):
+    """The row-order test hook takes 0 (by scan size), 1 (Morton) or 2 (k-d); anything else
+    is refused."""
+    from paper_2603_14859_b300 import _lib
+    assert lib.abc_debug_order(3) == _lib.ABC_ERR_ARG
+    assert b"mode" in lib.abc_last_error()
+    assert lib.abc_debug_order(-1) == _lib.ABC_ERR_ARG
+    for m in (1, 2, 0):
+        assert lib.abc_debug_order(m) == _lib.ABC_OK
+
+
 def test_fallback_and_quantile_validation_without_gpu(lib):
     """Argument checks of the learned path's reliability calls, before any device work."""
     from paper_2603_14859_b300 import _lib

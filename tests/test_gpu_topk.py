@@ -196,3 +196,37 @@ def test_uncertified_voxels_match_oracle(orc, prec, k, mode):
     else:
         assert st[3] == W.J // 4 and st[1] >= W.J - W.J // 4, f"status {st}"
     assert swaps == 0
+
+
+@pytest.mark.parametrize("name,J,n,k,prec", [("raclopride_lpntpet", 700, 40000, 50, 2),
+                                             ("raclopride_lpntpet", 700, 40000, 50, 1),
+                                             ("brain_fdg_2tcm", 300, 5000, 100, 0),
+                                             ("brain_fdg_2tcm", 5, 100, 7, 2)])
+def test_kd_row_order_matches_oracle(orc, name, J, n, k, prec):
+    """The k-d row order (tile-aligned splits of the voxels' and of each pilot group's
+    draws) changes only which draw tiles a pass can skip: with the test hook
+    abc_debug_order forcing it (mode 2) on scans far below its size threshold, the accepted
+    sets match the oracle's and equal, index for index, those of the Morton order (mode 1).
+    The cases: 6 ragged voxel tiles against 625 draw tiles in three pilot groups whose runs
+    start off the tile grid; a single-group FP32 case; and a scan too small for the k-d
+    order (100 draws), which keeps the Morton order."""
+    from paper_2603_14859_b300 import _lib, api
+    W, y, x = _gpu_case(name, J, n, orc)
+    L, w = W.L, W.weights.astype(np.float32)
+    out = {}
+    try:
+        for mode in (1, 2):
+            _lib.check(_lib.lib().abc_debug_order(mode))
+            ws = api.alloc_workspace(W.J, x.shape[0], L, k, prec)
+            ws.fill_(0xFF)
+            if mode == 2:
+                swaps, worst, _ = _compare(orc, W, y, x, k, prec, ws=ws)
+                assert swaps <= 3
+            idx, dist = api.discrepancy_topk(y, x, L, w, k, prec, ws)
+            st = api.topk_status(ws)
+            assert st[0] == 0, f"status {st}"
+            out[mode] = (idx.cpu().numpy(), dist.cpu().numpy())
+    finally:
+        _lib.check(_lib.lib().abc_debug_order(0))
+    assert np.array_equal(out[1][0], out[2][0])
+    assert np.array_equal(out[1][1], out[2][1])
