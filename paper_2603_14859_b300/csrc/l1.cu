@@ -332,20 +332,24 @@ extern "C" int abc_discrepancy_topk_l1(const float* y_dev, int64_t J, int32_t ld
     const int warps = L1_BLOCK_VOXELS / L1_V;
     const size_t smem =
         ((size_t)2 * L * L1_TS + L1_MAXL + (size_t)warps * L1_V * L1_MAXL + (size_t)warps * 256) * 4;
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
+    // kernel attributes are per device: raised once for each device that launches
+    static size_t configured[64] = {};
+    int dev = 0;
+    VPET_CUDA(cudaGetDevice(&dev));
+    VPET_ARG(dev >= 0 && dev < 64, "device ordinal %d out of range", dev);
+    if (smem > 48 * 1024 && smem > configured[dev]) {
         VPET_CUDA(cudaFuncSetAttribute(k_l1_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = smem;
+        configured[dev] = smem;
     }
     k_l1_scan<<<dim3((unsigned)vpet_ceil_div(J, (int64_t)L1_BLOCK_VOXELS), (unsigned)A.S), warps * 32, smem, s>>>(A);
     VPET_LAUNCH_CHECK();
     int fw = 8;
     while (fw > 1 && (size_t)fw * (1024 + (size_t)sortcap * 8) > 96 * 1024) fw >>= 1;
     const size_t fsmem = (size_t)fw * (1024 + (size_t)sortcap * 8);
-    static size_t fconfigured = 0;
-    if (fsmem > 48 * 1024 && fsmem > fconfigured) {
+    static size_t fconfigured[64] = {};
+    if (fsmem > 48 * 1024 && fsmem > fconfigured[dev]) {
         VPET_CUDA(cudaFuncSetAttribute(k_l1_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
-        fconfigured = fsmem;
+        fconfigured[dev] = fsmem;
     }
     k_l1_final<<<(unsigned)vpet_ceil_div(J, fw), fw * 32, fsmem, s>>>(A);
     VPET_LAUNCH_CHECK();
