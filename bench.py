@@ -462,6 +462,27 @@ def run_learned_bench(args, world, rank, local):
     g2 = learned.GlobalIrr(model, N=n_glob, k=k, seed=4321)
     ref2 = g2.run(sub)["mean"].cpu().numpy()
     rel_l2 = lambda a, b: [float(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c])) for c in range(5)]
+    # the global path alone over the whole volume (no network), FP32 and fast exact forms, same
+    # draws: the comparators of the learned form (outside the timed region)
+    comparators = {}
+    if not args.no_fp32_comparator:
+        for name, prec in (("global_fp32", PRECISIONS["fp32"]), ("global_bf16r", PRECISIONS["bf16r"])):
+            gp = g if prec == g.precision else learned.GlobalIrr(model, N=n_glob, k=k, seed=1234, precision=prec)
+            gp.run(y)
+            torch.cuda.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nrep = 2
+            c0.record(stream)
+            for _ in range(nrep):
+                gp.run(y)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            gms = c0.elapsed_time(c1) / nrep
+            comparators[name] = {"ms_per_step": gms, "voxels_per_s": J / (gms / 1000.0), "draws": n_glob,
+                                 "steps": nrep}
+            if gp is not g:
+                del gp
+                torch.cuda.empty_cache()
     t = torch.tensor([ms, local_ms, e2e_ms], device="cuda", dtype=torch.float64)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -483,6 +504,8 @@ def run_learned_bench(args, world, rank, local):
            "accuracy_vs_global": {"columns": ["K1", "k2", "k3", "Vb", "Ki"], "sample_voxels": 4096,
                                   "rel_l2_learned": rel_l2(got, ref), "rel_l2_global_reseeded": rel_l2(ref2, ref)},
            "l2": "inputs larger than L2", "parallelism": f"voxel shards x{args.gpus}" if args.gpus > 1 else "single GPU"}
+    if comparators:
+        cfg["global_comparators"] = comparators
     line = {
         "metric": "voxels/s to posterior", "value": J * world / (ms / 1000.0), "unit": "voxels/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -606,47 +629,71 @@ def main():
         run.step(y)
     torch.cuda.synchronize()
     st = api.topk_status(run.ws) if not l1 else [0, 0, api.l1_status(run.ws, W.J, W.k), 0, 0, 0, 0, 0]
-    launches0 = api.launch_info()[2]
-    # timed region (device time on the launching stream)
     K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    # the squared-L2 step runs as one CUDA graph (its launches counted once, at capture); the
+    # fused main pass is bracketed by events recorded inside the graph, read after each replay.
+    # The L1 step runs eagerly, its launches counted by the library.
+    use_graph = not l1
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for a, b in ev:             # torch creates the CUDA event objects on first record
-        a.record(stream)
-        b.record(stream)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0.record(stream)
-    for i in range(K):
-        if not l1:
-            api.profile_events(*ev[i])
-        run.step(y)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    api.profile_events(None, None)
-    launches = api.launch_info()[2] - launches0
-    barrier()
-    ms = e0.elapsed_time(e1) / K
-    if l1:      # the L1 scan + final selection, timed alone on the same inputs
-        a, b = ev[0]
+    if use_graph:
+        prof = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        for e in prof:
+            e.record(stream)
+        torch.cuda.synchronize()
+        api.profile_events(*prof)
+        l0 = api.launch_info()[2]
+        run.capture(y)                     # one eager step, then the captured step
+        launches_per_step = (api.launch_info()[2] - l0) // 2
+        api.profile_events(None, None)
+        for _ in range(2):
+            run.replay()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+        barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        e0.record(stream)
+        tcs = []
+        for i in range(K):
+            run.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tcs.append(prof[0].elapsed_time(prof[1]))
+        launches = launches_per_step * K
+        barrier()
+        ms = e0.elapsed_time(e1) / K
+        tc_ms = statistics.mean(tcs)
+        cfg["step_launch"] = f"one CUDA graph replay per step ({launches_per_step} kernels)"
+    else:
+        launches0 = api.launch_info()[2]
+        # timed region (device time on the launching stream)
+        clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+        barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        e0.record(stream)
+        for i in range(K):
+            run.step(y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = api.launch_info()[2] - launches0
+        barrier()
+        ms = e0.elapsed_time(e1) / K
+        # the L1 scan + final selection, timed alone on the same inputs
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         api.discrepancy_topk_l1(y, run.x, W.L, run.weights, W.k, run.ws, run.idx, run.dist, stream=stream)
         b.record(stream)
         torch.cuda.synchronize()
         tc_ms = a.elapsed_time(b)
-    else:
-        tc_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     clk = clocks.stop()
     ms, tc_ms = sharding.max_over_ranks([ms, tc_ms], dist, device="cuda")
     voxels_all = int(round(sharding.sum_over_ranks(W.J, dist, device="cuda")))
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: pinned TACs into the step's input
+    # buffer, the step (graph replay, or the eager L1 step), model probabilities and summaries out
     y_host = y.cpu().pin_memory()
     outs_host = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in [run.prob, run.pref] + run.summ]
-    y_dev = torch.empty_like(y)
     h2d = y_host.numel() * y_host.element_size()
     d2h = sum(o.numel() * o.element_size() for o in outs_host)
     Ke = max(1, min(K, 3))
@@ -655,8 +702,8 @@ def main():
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(Ke):
-        y_dev.copy_(y_host, non_blocking=True)
-        out = run.step(y_dev)
+        y.copy_(y_host, non_blocking=True)
+        out = run.replay() if use_graph else run.step(y)
         for h, d in zip(outs_host, [out.prob, out.pref, out.mean, out.sd, out.lo, out.hi]):
             h.copy_(d, non_blocking=True)
     f1.record(stream)

@@ -663,11 +663,17 @@ __global__ void k_kd_level_init(KdNode* __restrict__ nd, uint32_t* __restrict__ 
     }
 }
 
-// Node boxes: one set of atomics per warp whose rows share a node (runs are contiguous).
-__global__ void k_kd_box(const float4* __restrict__ kf, const int32_t* __restrict__ knode, int64_t N,
-                         KdNode* __restrict__ nd) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+// Node boxes.  The runs are contiguous and sorted by node, so a block whose first and last
+// rows share a node holds that node alone: it reduces its rows in shared memory and issues one
+// set of atomics (the top levels, where every block of the level hits the same few nodes);
+// otherwise one set per warp whose rows share a node, else one per row.
+__global__ void __launch_bounds__(256) k_kd_box(const float4* __restrict__ kf, const int32_t* __restrict__ knode,
+                                                int64_t N, KdNode* __restrict__ nd) {
+    __shared__ uint32_t sred[8][6];
+    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t p = p0 + threadIdx.x;
+    const int64_t plast = (p0 + blockDim.x <= N ? p0 + blockDim.x : N) - 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const bool valid = p < N;
     const int node = valid ? knode[p] : -1;
     float f[3] = {0.0f, 0.0f, 0.0f};
@@ -676,6 +682,30 @@ __global__ void k_kd_box(const float4* __restrict__ kf, const int32_t* __restric
         f[0] = v.x;
         f[1] = v.y;
         f[2] = v.z;
+    }
+    const int nb = knode[p0];
+    if (nb == knode[plast]) {
+        // rows past N take the identities of min and max
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t u = ord_f2u(f[c]);
+            const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, valid ? u : 0xFFFFFFFFu);
+            const uint32_t mx = __reduce_max_sync(0xFFFFFFFFu, valid ? u : 0u);
+            if (lane == 0) {
+                sred[wid][2 * c] = mn;
+                sred[wid][2 * c + 1] = mx;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            const int e = threadIdx.x;
+            const int nw = blockDim.x >> 5;
+            uint32_t v = sred[0][e];
+            for (int w = 1; w < nw; ++w) v = (e & 1) ? max(v, sred[w][e]) : min(v, sred[w][e]);
+            if (e & 1) atomicMax(&nd[nb].box[e], v);
+            else atomicMin(&nd[nb].box[e], v);
+        }
+        return;
     }
     const int n0 = __shfl_sync(0xFFFFFFFFu, node, 0);
     if (__all_sync(0xFFFFFFFFu, valid && node == n0)) {
@@ -813,14 +843,20 @@ __global__ void k_kd_split(KdNode* __restrict__ nd, const uint32_t* __restrict__
 }
 
 // Rows to their child runs: below the boundary's bin left, above it right, and in it by
-// ticket (the first `need` tickets left).  One set of atomics per warp whose rows share a
-// node; a leaf's rows keep their places.
-__global__ void k_kd_scatter(const float4* __restrict__ kf, const int32_t* __restrict__ krow,
-                             const int32_t* __restrict__ knode, int64_t N, KdNode* __restrict__ nd,
-                             float4* __restrict__ kf2, int32_t* __restrict__ krow2, int32_t* __restrict__ knode2,
-                             int32_t* __restrict__ status) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+// ticket (the first `need` tickets left).  A block whose rows share one splitting node (the
+// runs are contiguous) reserves its tickets and places with one atomic per counter; otherwise
+// one set per warp whose rows share a node, else per row.  A leaf's rows keep their places.
+__global__ void __launch_bounds__(256) k_kd_scatter(const float4* __restrict__ kf, const int32_t* __restrict__ krow,
+                                                    const int32_t* __restrict__ knode, int64_t N,
+                                                    KdNode* __restrict__ nd, float4* __restrict__ kf2,
+                                                    int32_t* __restrict__ krow2, int32_t* __restrict__ knode2,
+                                                    int32_t* __restrict__ status) {
+    __shared__ int s_cnt[3][8];    // per warp: rows in the boundary's bin, rows going left, right
+    __shared__ int s_base[3][8];   // their first ticket / place
+    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t p = p0 + threadIdx.x;
+    const int64_t plast = (p0 + blockDim.x <= N ? p0 + blockDim.x : N) - 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const bool valid = p < N;
     const int node = valid ? knode[p] : -1;
@@ -839,29 +875,78 @@ __global__ void k_kd_scatter(const float4* __restrict__ kf, const int32_t* __res
             cls = bin < n.bstar ? 0 : (bin > n.bstar ? 1 : 2);
         }
     }
-    const int n0 = __shfl_sync(0xFFFFFFFFu, node, 0);
-    const bool uni = __all_sync(0xFFFFFFFFu, valid && node == n0);
     int64_t pos = p;
-    if (uni && cls >= 0) {   // the whole warp: one node that splits
-        KdNode& n = nd[n0];
-        const uint32_t tm = __ballot_sync(0xFFFFFFFFu, cls == 2);
-        int tb = 0;
-        if (lane == 0 && tm) tb = atomicAdd(&n.tick, __popc(tm));
-        tb = __shfl_sync(0xFFFFFFFFu, tb, 0);
-        if (cls == 2) cls = (tb + __popc(tm & lt)) < n.need ? 0 : 1;
-        const uint32_t lm = __ballot_sync(0xFFFFFFFFu, cls == 0), rm = ~lm;
-        int lb = 0, rb = 0;
-        if (lane == 0) {
-            if (lm) lb = atomicAdd(&n.lcur, __popc(lm));
-            if (rm) rb = atomicAdd(&n.rcur, __popc(rm));
+    const int nb = knode[p0];
+    if (nb == knode[plast]) {
+        // every row of the block is in node nb; a leaf's rows stay
+        KdNode& n = nd[nb];
+        if (n.m < n.b) {
+            const int nw = blockDim.x >> 5;
+            const uint32_t tm = __ballot_sync(0xFFFFFFFFu, valid && cls == 2);
+            if (lane == 0) s_cnt[0][wid] = __popc(tm);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int tot = 0;
+                for (int w = 0; w < nw; ++w) {
+                    s_base[0][w] = tot;
+                    tot += s_cnt[0][w];
+                }
+                const int tb = tot ? atomicAdd(&n.tick, tot) : 0;
+                for (int w = 0; w < nw; ++w) s_base[0][w] += tb;
+            }
+            __syncthreads();
+            if (cls == 2) cls = (s_base[0][wid] + __popc(tm & lt)) < n.need ? 0 : 1;
+            const uint32_t lm = __ballot_sync(0xFFFFFFFFu, valid && cls == 0);
+            const uint32_t rm = __ballot_sync(0xFFFFFFFFu, valid && cls == 1);
+            if (lane == 0) {
+                s_cnt[1][wid] = __popc(lm);
+                s_cnt[2][wid] = __popc(rm);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int tl = 0, tr = 0;
+                for (int w = 0; w < nw; ++w) {
+                    s_base[1][w] = tl;
+                    tl += s_cnt[1][w];
+                    s_base[2][w] = tr;
+                    tr += s_cnt[2][w];
+                }
+                const int lb = tl ? atomicAdd(&n.lcur, tl) : 0;
+                const int rb = tr ? atomicAdd(&n.rcur, tr) : 0;
+                for (int w = 0; w < nw; ++w) {
+                    s_base[1][w] += lb;
+                    s_base[2][w] += rb;
+                }
+            }
+            __syncthreads();
+            if (valid)
+                pos = cls == 0 ? (int64_t)a + s_base[1][wid] + __popc(lm & lt)
+                               : (int64_t)m + s_base[2][wid] + __popc(rm & lt);
         }
-        lb = __shfl_sync(0xFFFFFFFFu, lb, 0);
-        rb = __shfl_sync(0xFFFFFFFFu, rb, 0);
-        pos = cls == 0 ? (int64_t)a + lb + __popc(lm & lt) : (int64_t)m + rb + __popc(rm & lt);
-    } else if (valid && cls >= 0) {
-        KdNode& n = nd[node];
-        if (cls == 2) cls = atomicAdd(&n.tick, 1) < n.need ? 0 : 1;
-        pos = cls == 0 ? (int64_t)a + atomicAdd(&n.lcur, 1) : (int64_t)m + atomicAdd(&n.rcur, 1);
+    } else {
+        const int n0 = __shfl_sync(0xFFFFFFFFu, node, 0);
+        const bool uni = __all_sync(0xFFFFFFFFu, valid && node == n0);
+        if (uni && cls >= 0) {   // the whole warp: one node that splits
+            KdNode& n = nd[n0];
+            const uint32_t tm = __ballot_sync(0xFFFFFFFFu, cls == 2);
+            int tb = 0;
+            if (lane == 0 && tm) tb = atomicAdd(&n.tick, __popc(tm));
+            tb = __shfl_sync(0xFFFFFFFFu, tb, 0);
+            if (cls == 2) cls = (tb + __popc(tm & lt)) < n.need ? 0 : 1;
+            const uint32_t lm = __ballot_sync(0xFFFFFFFFu, cls == 0), rm = ~lm;
+            int lb = 0, rb = 0;
+            if (lane == 0) {
+                if (lm) lb = atomicAdd(&n.lcur, __popc(lm));
+                if (rm) rb = atomicAdd(&n.rcur, __popc(rm));
+            }
+            lb = __shfl_sync(0xFFFFFFFFu, lb, 0);
+            rb = __shfl_sync(0xFFFFFFFFu, rb, 0);
+            pos = cls == 0 ? (int64_t)a + lb + __popc(lm & lt) : (int64_t)m + rb + __popc(rm & lt);
+        } else if (valid && cls >= 0) {
+            KdNode& n = nd[node];
+            if (cls == 2) cls = atomicAdd(&n.tick, 1) < n.need ? 0 : 1;
+            pos = cls == 0 ? (int64_t)a + atomicAdd(&n.lcur, 1) : (int64_t)m + atomicAdd(&n.rcur, 1);
+        }
     }
     if (!valid) return;
     const int side = cls == 1 ? 1 : 0;

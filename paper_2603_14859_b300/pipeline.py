@@ -62,6 +62,7 @@ class AbcPipeline:
         nc = max(self.nparams) + 1
         self.summ = [torch.empty((self.J, nc), dtype=torch.float32, device=dev) for _ in range(4)]
         self.weights = W.weights.astype(np.float32)
+        self.graph = None
 
     def simulate_draws(self, stream=None):
         """Algorithm 1, steps 1-3: prior draws and their TACs for every model."""
@@ -87,7 +88,31 @@ class AbcPipeline:
     def step(self, y, stream=None) -> StepOutput:
         self.simulate_draws(stream)
         self.select(y, stream)
+        return self.outputs()
+
+    def outputs(self) -> StepOutput:
         return StepOutput(self.idx, self.dist, self.prob, self.pref, *self.summ)
+
+    def capture(self, y):
+        """Record one step on the voxel TACs in `y` into a CUDA graph, after one eager
+        warm-up step on a side stream.  The graph reads `y` in place: refill that buffer
+        between replays.  The squared-L2 path only (the L1 call reads a status word back)."""
+        if self.distance != "l2":
+            raise ValueError("capture: the L1 path is not captured")
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step(y)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step(y)
+        torch.cuda.synchronize()
+
+    def replay(self) -> StepOutput:
+        self.graph.replay()
+        return self.outputs()
 
 
 def truth_groups(W: S.Workload):

@@ -107,6 +107,38 @@ def test_batch_graph_replay(batch):
         assert torch.equal(torch.nan_to_num(r.summ[0], 7.0), torch.nan_to_num(m, 7.0))
 
 
+@pytest.mark.parametrize("order_mode", [0, 2])
+def test_single_scan_graph_replay(order_mode):
+    """One single-scan step (prior draws, simulation, discrepancy + top-k, model selection,
+    summaries) captured as a CUDA graph and replayed twice returns, bit for bit, what the eager
+    step returns; with the k-d row order forced (mode 2) its level-by-level kernels are in the
+    graph too."""
+    from paper_2603_14859_b300 import _lib, api, pipeline
+    W = S.workload("raclopride_lpntpet", J=700, N_per_model=40000)
+    W.k = 50
+    y = pipeline.make_y_gpu(W)
+    try:
+        _lib.check(_lib.lib().abc_debug_order(order_mode))
+        run = pipeline.AbcPipeline(W, _lib.ABC_BF16_RESCORE)
+        run.ws.fill_(0xFF)                                 # stale workspace contents must not matter
+        out = run.step(y)
+        torch.cuda.synchronize()
+        assert api.topk_status(run.ws)[0] == 0
+        fields = ("idx", "dist", "prob", "pref", "mean", "sd", "lo", "hi")
+        ref = [torch.nan_to_num(getattr(out, f).clone().float(), 7.0) for f in fields]
+        run.capture(y)
+        for t in (run.idx, run.dist, run.prob, *run.summ):   # scribble, then replay
+            t.fill_(-5)
+        run.replay()
+        got = run.replay()
+        torch.cuda.synchronize()
+        assert api.topk_status(run.ws)[0] == 0
+    finally:
+        _lib.check(_lib.lib().abc_debug_order(0))
+    for f, a in zip(fields, ref):
+        assert torch.equal(a, torch.nan_to_num(getattr(got, f).float(), 7.0)), f
+
+
 def test_autotune_choice_and_invariance(batch, tmp_path, monkeypatch):
     from paper_2603_14859_b300 import autotune, pipeline
     monkeypatch.setenv("VPETABC_TUNE_CACHE", str(tmp_path / "tune.json"))
