@@ -1752,14 +1752,57 @@ __device__ __forceinline__ void epilogue_chunk(const ItemRegs& I, float (&v)[32]
 }
 
 
-// Per-thread state of a top-r pilot: the voxel's kept keys A[i * 128] (i < n_in,
-// unordered), their maximum amax at position imax once n_in = r, and the
+// Per-thread state of a top-r pilot: the voxel's kept keys A[i * 128] (i < n_in), a
+// max-heap once filled (A[0] the largest), its maximum amax once n_in = r, and the
 // quick-reject threshold thr = min(thr_in, amax) (thr_in alone until r keys are in).
+// Each thread owns one column of the shared array, so heap moves of different lanes
+// never share a bank.
 struct TopR {
     float* A;
-    int r, n_in, imax;
+    int r, n_in;
     float amax, thr_in, thr;
 };
+
+// Adds key x to a top-r set: while filling, a sift-up insert; once full, x replaces the
+// root (the largest key) if it is smaller, and sifts down.  The kept multiset is the same
+// as any other exact top-r bookkeeping's.
+__device__ __forceinline__ void topr_add(TopR& S, float x) {
+    if (S.n_in < S.r) {
+        int i = S.n_in++;
+        while (i > 0) {
+            const int p = (i - 1) >> 1;
+            const float ap = S.A[p * 128];
+            if (ap >= x) break;
+            S.A[i * 128] = ap;
+            i = p;
+        }
+        S.A[i * 128] = x;
+        if (S.n_in == S.r) {
+            S.amax = S.A[0];
+            S.thr = fminf(S.thr_in, S.amax);
+        }
+    } else if (x < S.amax) {
+        int i = 0;
+        for (;;) {
+            int c = 2 * i + 1;
+            if (c >= S.r) break;
+            float ac = S.A[c * 128];
+            if (c + 1 < S.r) {
+                const float a2 = S.A[(c + 1) * 128];
+                if (a2 > ac) {
+                    ac = a2;
+                    ++c;
+                }
+            }
+            if (ac <= x) break;
+            S.A[i * 128] = ac;
+            i = c;
+        }
+        S.A[i * 128] = x;
+        S.amax = S.A[0];
+        S.thr = fminf(S.thr_in, S.amax);
+    }
+}
 
 // One 32-column chunk of a top-r pilot: keys <= thr join the kept set (the
 // largest kept key leaves once r are kept), so the set ends as the r smallest
@@ -1784,23 +1827,7 @@ __device__ __forceinline__ void topr_chunk(TopR& S, float (&v)[32], int64_t n0, 
         while (m) {
             const int b = __ffs(m) - 1;
             m &= m - 1;
-            const float x = pick8(v, 8 * g, b);
-            if (S.n_in < S.r) {
-                S.A[S.n_in * 128] = x;
-                if (S.n_in == 0 || x > S.amax) { S.amax = x; S.imax = S.n_in; }
-                if (++S.n_in == S.r) S.thr = fminf(S.thr_in, S.amax);
-            } else if (x < S.amax) {
-                S.A[S.imax * 128] = x;
-                float mx = S.A[0];
-                int im = 0;
-                for (int i = 1; i < S.r; ++i) {
-                    const float a = S.A[i * 128];
-                    if (a > mx) { mx = a; im = i; }
-                }
-                S.amax = mx;
-                S.imax = im;
-                S.thr = fminf(S.thr_in, mx);
-            }
+            topr_add(S, pick8(v, 8 * g, b));
         }
     }
 }
@@ -2036,7 +2063,7 @@ __global__ void __launch_bounds__(tc_threads(TOPR, BN), tc_epi_warps(TOPR, BN) =
             // several CTAs, which reserve list entries atomically (no compaction)
             const bool shared_list = !TOPR && I.rows != nullptr;
             int* acnt = (shared_list && valid) ? &I.cnt[jrow + hh * I.hstride] : nullptr;
-            TopR S{sRow + (threadIdx.x - 64), TOPR ? I.rsel : 0, 0, 0, -3.0e38f, thr, thr};
+            TopR S{sRow + (threadIdx.x - 64), TOPR ? I.rsel : 0, 0, -3.0e38f, thr, thr};
             // the next tile's draw offset is loaded a tile ahead, off the path from the
             // accumulator's arrival to its first use
             int tnext = kt_list && ntiles > wp.seg ? kt_list[wp.seg] : 0;

@@ -44,6 +44,29 @@ def test_select_and_summaries(orc, k):
         assert np.all(np.abs(a[m] - b[m]) <= 1e-5 * np.abs(b[m]) + 1e-7)
 
 
+@pytest.mark.parametrize("k,shift", [(64, 0), (64, 1), (2048, 0), (203, 0)])
+def test_model_select_many_models(orc, k, shift):
+    """Five models with uneven draw counts; k a multiple of 4 on a 16-byte aligned index
+    array (four indices per lane per load), the same rows one element off that alignment,
+    and k not a multiple of 4 (one index per lane per load): every count equals the
+    oracle's, ties going to the lower model."""
+    from paper_2603_14859_b300 import api
+    rng = np.random.default_rng(k + 7 * shift)
+    off = [0, 10, 400, 3000, 3001, 9000]
+    N = off[-1]
+    J = 257
+    idx = rng.integers(0, N, (J, k)).astype(np.int32)
+    idx[0] = 3000                                       # every draw from the one-draw model
+    idx[1, : k // 2], idx[1, k // 2:] = 5, 405          # a tie between models 0 and 2 (k even)
+    flat = torch.zeros(J * k + shift, dtype=torch.int32, device="cuda")
+    ti = flat[shift:].view(J, k)
+    ti.copy_(torch.from_numpy(idx))
+    prob, pref = api.model_select(ti, off)
+    op, opref = orc.model_select(idx, off)
+    assert np.array_equal(pref.cpu().numpy(), opref)
+    assert np.allclose(prob.cpu().numpy(), op, rtol=0, atol=1e-7)
+
+
 @pytest.mark.parametrize("k,P", [(2048, 30), (777, 12)])
 def test_summaries_wide_rows(orc, k, P):
     """Many parameters at the largest k (every column's values fill the shared-memory
