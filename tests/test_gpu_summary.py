@@ -46,10 +46,9 @@ def test_select_and_summaries(orc, k):
 
 @pytest.mark.parametrize("k,shift", [(64, 0), (64, 1), (2048, 0), (203, 0)])
 def test_model_select_many_models(orc, k, shift):
-    """Five models with uneven draw counts; k a multiple of 4 on a 16-byte aligned index
-    array (four indices per lane per load), the same rows one element off that alignment,
-    and k not a multiple of 4 (one index per lane per load): every count equals the
-    oracle's, ties going to the lower model."""
+    """Five models with uneven draw counts (one of them a single draw), index rows that
+    start on and off a 16-byte boundary, k from 64 to the largest (2048) and k not a
+    multiple of 4: every count equals the oracle's, ties going to the lower model."""
     from paper_2603_14859_b300 import api
     rng = np.random.default_rng(k + 7 * shift)
     off = [0, 10, 400, 3000, 3001, 9000]
