@@ -2490,19 +2490,22 @@ __device__ __forceinline__ void group_dist_n(const float (&yq)[4], const float (
     }
 }
 
+// The lane's four frames 4h..4h+3 of four draw rows (unloaded past L), issued together.
+__device__ __forceinline__ void load_rows4(const float* const (&xr)[4], int L, int h, float4 (&v)[4]) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        if (4 * h < L) v[r] = __ldg((const float4*)xr[r] + h);
+}
+
 // Four rows per group of G >= 4 lanes, as group_dist_n, but the butterfly is a
 // reduce-scatter: the first level keeps two of the four rows per lane, the second
 // one, the rest sum that one; each addition pairs the same operands as the full
 // butterfly, so every row's value is the same.  Lanes h with h % (G / 4) == 0
-// return row 2 [h & G/2] + [h & G/4].
-__device__ __forceinline__ float group_dist_scatter4(const float (&yq)[4], const float (&wq)[4],
-                                                     const float* const (&xr)[4], int L, int h, int G, int& row) {
+// return row 2 [h & G/2] + [h & G/4].  v: the rows' frames from load_rows4.
+__device__ __forceinline__ float group_dist_scatter4_v(const float (&yq)[4], const float (&wq)[4], const float4 (&v)[4],
+                                                       int L, int h, int G, int& row) {
     const int l = 4 * h;
     float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    float4 v[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-        if (l < L) v[r] = __ldg((const float4*)xr[r] + h);
     if (l < L) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -2526,7 +2529,14 @@ __device__ __forceinline__ float group_dist_scatter4(const float (&yq)[4], const
     return y;
 }
 
-__global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ BatchFin B) {
+__device__ __forceinline__ float group_dist_scatter4(const float (&yq)[4], const float (&wq)[4],
+                                                     const float* const (&xr)[4], int L, int h, int G, int& row) {
+    float4 v[4];
+    load_rows4(xr, L, h, v);
+    return group_dist_scatter4_v(yq, wq, v, L, h, G, row);
+}
+
+__global__ void __launch_bounds__(256, 3) k_finalize(const __grid_constant__ BatchFin B) {
     extern __shared__ __align__(16) uint8_t fsm[];
     const int warps = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2615,7 +2625,33 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
                 }
                 __syncwarp();
                 float d1 = 0.0f;
-                for (int i0 = 0; i0 < n1; i0 += NR * R) {
+                // G >= 8: two groups of four rows per lane per iteration, all eight loads in
+                // flight before either group's arithmetic (the same values as one group at a time)
+                const int n1_pair = G >= 8 ? n1 - n1 % (2 * NR * R) : 0;
+                for (int i0 = 0; i0 < n1_pair; i0 += 2 * NR * R) {
+                    const float* xa[NR];
+                    const float* xb[NR];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        xa[r] = P.xs + (int64_t)(uint32_t)sbuf[i0 + r * R + grp] * P.ldxs;
+                        xb[r] = P.xs + (int64_t)(uint32_t)sbuf[i0 + NR * R + r * R + grp] * P.ldxs;
+                    }
+                    float4 va[NR], vb[NR];
+                    load_rows4(xa, P.L, h, va);
+                    load_rows4(xb, P.L, h, vb);
+                    int ra, rb;
+                    const float da = group_dist_scatter4_v(yq, wq, va, P.L, h, G, ra);
+                    const float db = group_dist_scatter4_v(yq, wq, vb, P.L, h, G, rb);
+                    const int ia = i0 + ra * R + grp, ib = i0 + NR * R + rb * R + grp;
+                    __syncwarp();
+                    if ((h & ((G >> 2) - 1)) == 0) {
+                        sbuf[ia] = ((unsigned long long)__float_as_uint(da) << 32) | (uint32_t)sbuf[ia];
+                        sbuf[ib] = ((unsigned long long)__float_as_uint(db) << 32) | (uint32_t)sbuf[ib];
+                        d1 = fmaxf(d1, fmaxf(da, db));
+                    }
+                    __syncwarp();
+                }
+                for (int i0 = n1_pair; i0 < n1; i0 += NR * R) {
                     const float* xr[NR];
 #pragma unroll
                     for (int r = 0; r < NR; ++r) {
@@ -2694,7 +2730,39 @@ __global__ void __launch_bounds__(256, 4) k_finalize(const __grid_constant__ Bat
             int idx_cur = lane < cnt ? ij[lane] : 0;
             int idx_nxt = 32 + lane < cnt ? ij[32 + lane] : 0;
             int gx_cur = P.xperm ? P.xperm[idx_cur] : idx_cur;
-            for (int i0 = 0; i0 < cnt; i0 += NR * R) {
+            // G >= 8: two groups of four rows per lane per iteration (2 NR R <= 32 rows, inside
+            // one 32-row index chunk), all eight loads in flight before either group's arithmetic
+            const int cnt_pair = G >= 8 ? cnt - cnt % (2 * NR * R) : 0;
+            int i0 = 0;
+            for (; i0 < cnt_pair; i0 += 2 * NR * R) {
+                if (i0 - cb >= 32) {
+                    if (cb + lane < cnt) ij[cb + lane] = gx_cur;
+                    cb += 32;
+                    idx_cur = idx_nxt;
+                    idx_nxt = cb + 32 + lane < cnt ? ij[cb + 32 + lane] : 0;
+                    gx_cur = P.xperm ? P.xperm[idx_cur] : idx_cur;
+                }
+                const float* xa[NR];
+                const float* xb[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const int rowa = __shfl_sync(0xFFFFFFFFu, idx_cur, (i0 + r * R + grp - cb) & 31);
+                    const int rowb = __shfl_sync(0xFFFFFFFFu, idx_cur, (i0 + NR * R + r * R + grp - cb) & 31);
+                    xa[r] = P.xs + (int64_t)rowa * P.ldxs;
+                    xb[r] = P.xs + (int64_t)rowb * P.ldxs;
+                }
+                float4 va[NR], vb[NR];
+                load_rows4(xa, P.L, h, va);
+                load_rows4(xb, P.L, h, vb);
+                int ra, rb;
+                const float da = group_dist_scatter4_v(yq, wq, va, P.L, h, G, ra);
+                const float db = group_dist_scatter4_v(yq, wq, vb, P.L, h, G, rb);
+                if ((h & ((G >> 2) - 1)) == 0) {
+                    kj[i0 + ra * R + grp] = da;
+                    kj[i0 + NR * R + rb * R + grp] = db;
+                }
+            }
+            for (; i0 < cnt; i0 += NR * R) {
                 if (i0 - cb >= 32) {
                     if (cb + lane < cnt) ij[cb + lane] = gx_cur;
                     cb += 32;
