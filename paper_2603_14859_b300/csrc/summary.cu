@@ -140,6 +140,67 @@ __device__ float warp_kth_radix(const float* s, int n, int r, uint32_t* hist, in
     return o2f(prefix);
 }
 
+// Order statistics of ranks rk[0] <= rk[1] and rk[2] <= rk[3] (each in [0, n)) of
+// 32 < n <= 256 floats in s, exactly, for ranks near the two ends (the 95 % interval's):
+// each lane sorts its values s[lane + 32 i] (at most 8) in registers; the warp then takes
+// values in ascending order from the low end, rk[1] + 1 rounds, and in descending order
+// from the high end, n - rk[2] rounds, one value per round (the smallest, resp. largest,
+// of the lanes' next values; on equal values the lowest lane's), so the value taken in
+// round r is the order statistic of that rank, duplicates included.
+__device__ __forceinline__ void warp_tails4(const float* s, int n, const int (&rk)[4], int lane, float (&out)[4]) {
+    float v[8];
+    int c = 0;                                     // values this lane holds
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int idx = lane + 32 * i;
+        v[i] = idx < n ? s[idx] : __int_as_float(0x7F800000);
+        c += idx < n;
+    }
+    // odd-even transposition sort: eight phases order eight values (the +inf pads last)
+#pragma unroll
+    for (int ph = 0; ph < 8; ++ph)
+#pragma unroll
+        for (int i = ph & 1; i + 1 < 8; i += 2) {
+            const float a = fminf(v[i], v[i + 1]), b = fmaxf(v[i], v[i + 1]);
+            v[i] = a;
+            v[i + 1] = b;
+        }
+    auto pick = [&](int i) {
+        float h = v[0];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) h = i == q ? v[q] : h;
+        return h;
+    };
+    int lo = 0;
+    float head = c > 0 ? v[0] : __int_as_float(0x7F800000);
+    for (int r = 0; r <= rk[1]; ++r) {
+        float m = head;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+        const uint32_t who = __ballot_sync(0xFFFFFFFFu, lo < c && head == m);
+        if (lane == __ffs(who) - 1) {
+            ++lo;
+            head = lo < c ? pick(lo) : __int_as_float(0x7F800000);
+        }
+        if (r == rk[0]) out[0] = m;
+        if (r == rk[1]) out[1] = m;
+    }
+    int hi = c - 1;
+    head = c > 0 ? pick(hi) : __int_as_float(0xFF800000);
+    for (int r = n - 1; r >= rk[2]; --r) {
+        float m = head;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+        const uint32_t who = __ballot_sync(0xFFFFFFFFu, hi >= 0 && head == m);
+        if (lane == __ffs(who) - 1) {
+            --hi;
+            head = hi >= 0 ? pick(hi) : __int_as_float(0xFF800000);
+        }
+        if (r == rk[3]) out[3] = m;
+        if (r == rk[2]) out[2] = m;
+    }
+}
+
 // Order statistics of ranks rk[0..3] (each in [0, n)) of the n floats in s,
 // exactly, with one histogram: 256 equal-width bins over [min, max] locate the
 // bin of each rank; the members of those bins (at most 256 in all) are gathered
@@ -390,7 +451,8 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
                 rk[2 * t] = a;
                 rk[2 * t + 1] = a + 1 < n ? a + 1 : n - 1;
             }
-            warp_order4(vals, n, rk, hist, lane, mn, mx, os);
+            if (n > 32 && n <= 256) warp_tails4(vals, n, rk, lane, os);
+            else warp_order4(vals, n, rk, hist, lane, mn, mx, os);
             for (int t = 0; t < 2; ++t) qv[t] = fmaf(fr[t], os[2 * t + 1] - os[2 * t], os[2 * t]);
             o0 = mu;
             o1 = n > 1 ? sqrtf(sst / (float)(n - 1)) : 0.0f;

@@ -44,6 +44,34 @@ def test_select_and_summaries(orc, k):
         assert np.all(np.abs(a[m] - b[m]) <= 1e-5 * np.abs(b[m]) + 1e-7)
 
 
+@pytest.mark.parametrize("k", [40, 200, 256, 300])
+def test_summaries_with_many_ties(orc, k):
+    """Parameter values from five distinct levels, so every order statistic of the 95 %
+    interval falls inside a run of equal values; accepted counts per model on both sides of
+    256 (the register tournament of the interval's order statistics handles 33 to 256
+    values, the histogram selection the rest)."""
+    from paper_2603_14859_b300 import api
+    rng = np.random.default_rng(900 + k)
+    N = 5000
+    off = [0, 2000, 5000]
+    theta = (rng.integers(1, 6, (N, 8)) / 5.0).astype(np.float32)
+    J = 97
+    idx = np.stack([rng.choice(N, k, replace=False) for _ in range(J)]).astype(np.int32)
+    idx[0] = np.arange(k)                              # all from model 0
+    ti, tt = torch.from_numpy(idx).cuda(), torch.from_numpy(theta).cuda()
+    _, pref = api.model_select(ti, off)
+    _, opref = orc.model_select(idx, off)
+    nparams, has_ki = [4, 5], [1, 1]
+    for pr, opr in ((pref, opref), (None, None)):
+        g = api.summarize(tt, off, nparams, has_ki, [0, 1, 2], ti, pr)
+        o = orc.summarize(theta, off, nparams, has_ki, [0, 1, 2], idx, opr)
+        for a, b in zip(g, o):
+            a = a.cpu().numpy().astype(np.float64)
+            assert np.array_equal(np.isnan(a), np.isnan(b))
+            m = ~np.isnan(b)
+            assert np.all(np.abs(a[m] - b[m]) <= 1e-5 * np.abs(b[m]) + 1e-7)
+
+
 @pytest.mark.parametrize("k,shift", [(64, 0), (64, 1), (2048, 0), (203, 0)])
 def test_model_select_many_models(orc, k, shift):
     """Five models with uneven draw counts (one of them a single draw), index rows that
