@@ -394,6 +394,21 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
     }
     __syncwarp();
     const float qnan = __int_as_float(0x7FC00000);
+    // type-7 quantiles from the two order statistics around each level; the position
+    // h = (n - 1) q is formed in fp64 (exact floor at integer h), once per voxel: it
+    // depends on n alone, and fp64 issues slowly here
+    int rk[4];
+    float fr[2];
+    {
+        const double qs[2] = {0.025, 0.975};
+        for (int t = 0; t < 2; ++t) {
+            const double h = (n - 1) * qs[t];
+            const int a = (int)floor(h);
+            fr[t] = (float)(h - a);
+            rk[2 * t] = a;
+            rk[2 * t + 1] = a + 1 < n ? a + 1 : n - 1;
+        }
+    }
     for (int col = 0; col < Q.ncols; ++col) {
         const bool isk = col == Q.Pmax;
         float o0 = qnan, o1 = qnan, o2 = qnan, o3 = qnan;
@@ -438,19 +453,7 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
                 ss.add(e * e);
             }
             const float sst = warp_csum(ss);
-            // type-7 quantiles from the two order statistics around each level; the
-            // position h = (n - 1) q is formed in fp64 once (exact floor at integer h)
-            float qv[2];
-            const double qs[2] = {0.025, 0.975};
-            int rk[4];
-            float fr[2], os[4];
-            for (int t = 0; t < 2; ++t) {
-                const double h = (n - 1) * qs[t];
-                const int a = (int)floor(h);
-                fr[t] = (float)(h - a);
-                rk[2 * t] = a;
-                rk[2 * t + 1] = a + 1 < n ? a + 1 : n - 1;
-            }
+            float qv[2], os[4];
             if (n > 32 && n <= 256) warp_tails4(vals, n, rk, lane, os);
             else warp_order4(vals, n, rk, hist, lane, mn, mx, os);
             for (int t = 0; t < 2; ++t) qv[t] = fmaf(fr[t], os[2 * t + 1] - os[2 * t], os[2 * t]);
