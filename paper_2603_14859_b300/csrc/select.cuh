@@ -378,6 +378,47 @@ __device__ __forceinline__ int warp_compact(float* keys, int32_t* idx, int cnt, 
 }
 
 // Ascending bitonic sort of n (a power of two) 64-bit keys in this warp's shared memory.
+// Bitonic sort of 32 NE 64-bit keys held in registers, lane L holding elements
+// L NE .. L NE + NE - 1 in v[0 .. NE - 1]: ascending over the element index.  Strides below
+// NE compare within a lane (compile-time register indices), larger ones exchange with lane
+// L ^ (stride / NE) through shuffles, each lane keeping the minimum or the maximum.
+template <int S, int NE>
+__device__ __forceinline__ void bitonic_in_lane(unsigned long long (&v)[NE], int size, int lane) {
+#pragma unroll
+    for (int i = 0; i < NE; ++i) {
+        if (i & S) continue;
+        const int e = lane * NE + i;
+        const bool up = (e & size) == 0;
+        const unsigned long long a = v[i], b = v[i + S];
+        const bool sw = (a > b) == up;
+        v[i] = sw ? b : a;
+        v[i + S] = sw ? a : b;
+    }
+}
+
+template <int NE>
+__device__ __forceinline__ void warp_bitonic_sort_regs(unsigned long long (&v)[NE], int lane) {
+    constexpr int N = 32 * NE;
+    for (int size = 2; size <= N; size <<= 1) {
+        for (int stride = size >> 1; stride >= NE; stride >>= 1) {
+            const int lm = stride / NE;
+            const bool lower = (lane & lm) == 0;
+#pragma unroll
+            for (int i = 0; i < NE; ++i) {
+                const bool up = ((lane * NE + i) & size) == 0;
+                const unsigned long long p = __shfl_xor_sync(0xFFFFFFFFu, v[i], lm);
+                const bool take_min = lower == up;
+                v[i] = take_min ? (p < v[i] ? p : v[i]) : (p > v[i] ? p : v[i]);
+            }
+        }
+        const int s0 = (size >> 1) < NE ? (size >> 1) : NE / 2;   // the largest in-lane stride
+        if (NE >= 16 && s0 >= 8) bitonic_in_lane<(NE >= 16 ? 8 : 1), NE>(v, size, lane);
+        if (NE >= 8 && s0 >= 4) bitonic_in_lane<(NE >= 8 ? 4 : 1), NE>(v, size, lane);
+        if (NE >= 4 && s0 >= 2) bitonic_in_lane<(NE >= 4 ? 2 : 1), NE>(v, size, lane);
+        if (s0 >= 1) bitonic_in_lane<1, NE>(v, size, lane);
+    }
+}
+
 __device__ __forceinline__ void warp_bitonic_sort(unsigned long long* s, int n, int lane) {
     for (int size = 2; size <= n; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {

@@ -2536,6 +2536,25 @@ __device__ __forceinline__ float group_dist_scatter4(const float (&yq)[4], const
     return group_dist_scatter4_v(yq, wq, v, L, h, G, row);
 }
 
+// The cnt <= 32 NE survivors as (distance key, draw index) sorted in registers (lane L holds
+// sorted positions L NE .. L NE + NE - 1), then stored in order to the warp's sort buffer:
+// no shared-memory traffic in the sort's stages.
+template <int NE>
+__device__ __forceinline__ void sort_keys_to_buffer(const float* kj, const int32_t* ij, int cnt,
+                                                    unsigned long long* sbuf, int lane) {
+    __syncwarp();
+    unsigned long long v[NE];
+#pragma unroll
+    for (int i = 0; i < NE; ++i) {
+        const int e = lane * NE + i;
+        v[i] = e < cnt ? (((unsigned long long)f2key(kj[e]) << 32) | (uint32_t)ij[e]) : ~0ull;
+    }
+    warp_bitonic_sort_regs<NE>(v, lane);
+#pragma unroll
+    for (int i = 0; i < NE; ++i) sbuf[lane * NE + i] = v[i];
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(256, 3) k_finalize(const __grid_constant__ BatchFin B) {
     extern __shared__ __align__(16) uint8_t fsm[];
     const int warps = blockDim.x >> 5;
@@ -2963,9 +2982,15 @@ __global__ void __launch_bounds__(256, 3) k_finalize(const __grid_constant__ Bat
     }
     int n2 = 32;
     while (n2 < cnt) n2 <<= 1;
-    for (int i = lane; i < n2; i += 32)
-        sbuf[i] = i < cnt ? (((unsigned long long)f2key(kj[i]) << 32) | (uint32_t)ij[i]) : ~0ull;
-    warp_bitonic_sort(sbuf, n2, lane);
+    // 256 survivors (k up to 248) sort in registers; 512 in registers spilled and measured
+    // slower on the brain volume (k = 500), so larger sorts stay in shared memory
+    if (n2 == 256) {
+        sort_keys_to_buffer<8>(kj, ij, cnt, sbuf, lane);
+    } else {
+        for (int i = lane; i < n2; i += 32)
+            sbuf[i] = i < cnt ? (((unsigned long long)f2key(kj[i]) << 32) | (uint32_t)ij[i]) : ~0ull;
+        warp_bitonic_sort(sbuf, n2, lane);
+    }
     for (int r = lane; r < P.k; r += 32) {
         const unsigned long long e = r < cnt ? sbuf[r] : ~0ull;
         P.out_idx[vox * P.k + r] = r < cnt ? (int32_t)(uint32_t)e : -1;
