@@ -142,63 +142,65 @@ __device__ float warp_kth_radix(const float* s, int n, int r, uint32_t* hist, in
 
 // Order statistics of ranks rk[0] <= rk[1] and rk[2] <= rk[3] (each in [0, n)) of
 // 32 < n <= 256 floats in s, exactly, for ranks near the two ends (the 95 % interval's):
-// each lane sorts its values s[lane + 32 i] (at most 8) in registers; the warp then takes
-// values in ascending order from the low end, rk[1] + 1 rounds, and in descending order
-// from the high end, n - rk[2] rounds, one value per round (the smallest, resp. largest,
-// of the lanes' next values; on equal values the lowest lane's), so the value taken in
-// round r is the order statistic of that rank, duplicates included.
+// each lane sorts the order-preserving integer images of its values s[lane + 32 i] (at
+// most 8) in registers; the warp then takes values in ascending order from the low end,
+// rk[1] + 1 rounds, and in descending order from the high end, n - rk[2] rounds, both ends
+// in the same loop, one value per end and round (the smallest, resp. largest, of the lanes'
+// next values by one warp reduction; on equal values the lowest lane's), so the value taken
+// in round r is the order statistic of that rank, duplicates included.
 __device__ __forceinline__ void warp_tails4(const float* s, int n, const int (&rk)[4], int lane, float (&out)[4]) {
-    float v[8];
+    uint32_t v[8];
     int c = 0;                                     // values this lane holds
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int idx = lane + 32 * i;
-        v[i] = idx < n ? s[idx] : __int_as_float(0x7F800000);
+        v[i] = idx < n ? f2o(s[idx]) : 0xFFFFFFFFu;
         c += idx < n;
     }
-    // odd-even transposition sort: eight phases order eight values (the +inf pads last)
+    // odd-even transposition sort: eight phases order eight keys (the pads last)
 #pragma unroll
     for (int ph = 0; ph < 8; ++ph)
 #pragma unroll
         for (int i = ph & 1; i + 1 < 8; i += 2) {
-            const float a = fminf(v[i], v[i + 1]), b = fmaxf(v[i], v[i + 1]);
+            const uint32_t a = min(v[i], v[i + 1]), b = max(v[i], v[i + 1]);
             v[i] = a;
             v[i + 1] = b;
         }
     auto pick = [&](int i) {
-        float h = v[0];
+        uint32_t h = v[0];
 #pragma unroll
         for (int q = 1; q < 8; ++q) h = i == q ? v[q] : h;
         return h;
     };
-    int lo = 0;
-    float head = c > 0 ? v[0] : __int_as_float(0x7F800000);
-    for (int r = 0; r <= rk[1]; ++r) {
-        float m = head;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-        const uint32_t who = __ballot_sync(0xFFFFFFFFu, lo < c && head == m);
-        if (lane == __ffs(who) - 1) {
-            ++lo;
-            head = lo < c ? pick(lo) : __int_as_float(0x7F800000);
+    const int rl = rk[1] + 1, ru = n - rk[2];     // rounds at the low and the high end
+    const int rounds = rl > ru ? rl : ru;
+    int lo = 0, hi = c - 1;
+    uint32_t hl = c > 0 ? v[0] : 0xFFFFFFFFu, hh = c > 0 ? pick(hi) : 0u;
+    uint32_t o[4] = {0u, 0u, 0u, 0u};
+    for (int r = 0; r < rounds; ++r) {
+        const uint32_t ml = __reduce_min_sync(0xFFFFFFFFu, hl);
+        const uint32_t mh = __reduce_max_sync(0xFFFFFFFFu, hh);
+        if (r < rl) {
+            const uint32_t who = __ballot_sync(0xFFFFFFFFu, lo < c && hl == ml);
+            if (lane == __ffs(who) - 1) {
+                ++lo;
+                hl = lo < c ? pick(lo) : 0xFFFFFFFFu;
+            }
+            if (r == rk[0]) o[0] = ml;
+            if (r == rk[1]) o[1] = ml;
         }
-        if (r == rk[0]) out[0] = m;
-        if (r == rk[1]) out[1] = m;
-    }
-    int hi = c - 1;
-    head = c > 0 ? pick(hi) : __int_as_float(0xFF800000);
-    for (int r = n - 1; r >= rk[2]; --r) {
-        float m = head;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-        const uint32_t who = __ballot_sync(0xFFFFFFFFu, hi >= 0 && head == m);
-        if (lane == __ffs(who) - 1) {
-            --hi;
-            head = hi >= 0 ? pick(hi) : __int_as_float(0xFF800000);
+        if (r < ru) {
+            const uint32_t who = __ballot_sync(0xFFFFFFFFu, hi >= 0 && hh == mh);
+            if (lane == __ffs(who) - 1) {
+                --hi;
+                hh = hi >= 0 ? pick(hi) : 0u;
+            }
+            if (n - 1 - r == rk[3]) o[3] = mh;
+            if (n - 1 - r == rk[2]) o[2] = mh;
         }
-        if (r == rk[3]) out[3] = m;
-        if (r == rk[2]) out[2] = m;
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = o2f(o[q]);
 }
 
 // Order statistics of ranks rk[0..3] (each in [0, n)) of the n floats in s,
