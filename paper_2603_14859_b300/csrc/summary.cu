@@ -359,14 +359,22 @@ __device__ void warp_order4(const float* s, int n, const int (&rk)[4], uint32_t*
 }
 
 
+// ROWS (at most 8 parameters, and the warp's rows fit): each accepted draw's parameter row is
+// read once, with 16-byte loads where rows are 16-byte aligned (vec4), into the warp's
+// column-major table R (ncols columns of p2 floats, K_i computed as the row arrives), and the
+// column statistics read R; otherwise each column is gathered through the selected draw
+// indices into one column buffer.  The sums visit the values in the same order either way.
+template <bool ROWS>
 __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __restrict__ idx, int64_t J,
                             const int8_t* __restrict__ pref, SumParams Q, float* __restrict__ mean,
-                            float* __restrict__ sd, float* __restrict__ lo, float* __restrict__ hi) {
+                            float* __restrict__ sd, float* __restrict__ lo, float* __restrict__ hi, bool vec4) {
     extern __shared__ __align__(16) uint8_t sm[];
     const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t* sel = (int32_t*)sm + (size_t)wid * Q.p2;
     float* vals = (float*)(sm + (size_t)warps * Q.p2 * 4) + (size_t)wid * Q.p2;
     uint32_t* hist = (uint32_t*)(sm + (size_t)warps * Q.p2 * 8) + (size_t)wid * 256;
+    float* R = (float*)sm + (size_t)wid * Q.ncols * Q.p2;
+    if (ROWS) hist = (uint32_t*)(sm + (size_t)warps * Q.ncols * Q.p2 * 4) + (size_t)wid * 256;
     const int64_t j = (int64_t)blockIdx.x * warps + wid;
     if (j >= J) return;
     const int pm = pref ? (int)pref[j] : -1;
@@ -390,7 +398,31 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
         for (int u = 0; u < 4; ++u) {
             const bool take = id[u] >= 0 && (pm < 0 || model_of(id[u], Q.S) == pm);
             const uint32_t b = __ballot_sync(0xFFFFFFFFu, take);
-            if (take) sel[n + __popc(b & ((1u << lane) - 1u))] = id[u];
+            const int pos = n + __popc(b & ((1u << lane) - 1u));
+            if (ROWS) {
+                if (take) {
+                    const float* th = theta + (int64_t)id[u] * Q.ldt;
+                    float r8[8];
+                    if (vec4) {
+                        const float4 a = __ldg((const float4*)th);
+                        const float4 c = Q.Pmax > 4 ? __ldg((const float4*)th + 1) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        r8[0] = a.x; r8[1] = a.y; r8[2] = a.z; r8[3] = a.w;
+                        r8[4] = c.x; r8[5] = c.y; r8[6] = c.z; r8[7] = c.w;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) r8[q] = q < Q.Pmax ? th[q] : 0.0f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (q < Q.Pmax) R[(size_t)q * Q.p2 + pos] = r8[q];
+                    if (ki) {
+                        const float K1 = th[Q.ki[0]], k2 = th[Q.ki[1]], k3 = th[Q.ki[2]];
+                        R[(size_t)Q.Pmax * Q.p2 + pos] = K1 * k3 / (k2 + k3);
+                    }
+                }
+            } else if (take) {
+                sel[pos] = id[u];
+            }
             n += __popc(b);
         }
     }
@@ -418,6 +450,7 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
             // fp32 throughout (compensated sums): the values are fp32 and the sums'
             // relative error stays near 2^-24 for any k
             // eight 32-value rounds per gather, their loads in flight together
+            const float* cv = ROWS ? R + (size_t)col * Q.p2 : vals;   // the column's values
             CSum s;
             float mn = 3.0e38f, mx = -3.0e38f;
             for (int i0 = 0; i0 < n; i0 += 256) {
@@ -426,7 +459,9 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
                 for (int u = 0; u < 8; ++u) {
                     const int i = i0 + 32 * u + lane;
                     v[u] = 0.0f;
-                    if (i < n) {
+                    if (ROWS) {
+                        if (i < n) v[u] = cv[i];
+                    } else if (i < n) {
                         const float* th = theta + (int64_t)sel[i] * Q.ldt;
                         if (isk) {
                             const float K1 = th[Q.ki[0]], k2 = th[Q.ki[1]], k3 = th[Q.ki[2]];
@@ -440,7 +475,7 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
                 for (int u = 0; u < 8; ++u) {
                     const int i = i0 + 32 * u + lane;
                     if (i < n) {
-                        vals[i] = v[u];
+                        if (!ROWS) vals[i] = v[u];
                         s.add(v[u]);
                         mn = fminf(mn, v[u]);
                         mx = fmaxf(mx, v[u]);
@@ -451,13 +486,13 @@ __global__ void k_summarize(const float* __restrict__ theta, const int32_t* __re
             CSum ss;
             __syncwarp();
             for (int i = lane; i < n; i += 32) {
-                const float e = vals[i] - mu;
+                const float e = cv[i] - mu;
                 ss.add(e * e);
             }
             const float sst = warp_csum(ss);
             float qv[2], os[4];
-            if (n > 32 && n <= 256) warp_tails4(vals, n, rk, lane, os);
-            else warp_order4(vals, n, rk, hist, lane, mn, mx, os);
+            if (n > 32 && n <= 256) warp_tails4(cv, n, rk, lane, os);
+            else warp_order4(cv, n, rk, hist, lane, mn, mx, os);
             for (int t = 0; t < 2; ++t) qv[t] = fmaf(fr[t], os[2 * t + 1] - os[2 * t], os[2 * t]);
             o0 = mu;
             o1 = n > 1 ? sqrtf(sst / (float)(n - 1)) : 0.0f;
@@ -657,11 +692,22 @@ extern "C" int abc_summarize(const float* theta_dev, int32_t ldtheta, const int6
     Q.p2 = p2;
     if (J == 0) return ABC_OK;
     VPET_ARG(theta_dev && idx_dev && mean_dev && sd_dev && lo_dev && hi_dev, "abc_summarize: null pointer");
+    // row mode where a warp's table of accepted rows is small (at most 8 parameters, at most
+    // 9 KB with the histogram: a block of up to 6 such warps stays within 48 KB, and an SM still
+    // holds about 30 warps); otherwise the per-column gather
+    const size_t row_bytes = (size_t)ncols * p2 * 4 + 1024;
+    const bool rows = Q.Pmax <= 8 && row_bytes <= 9 * 1024;
+    const bool vec4 = ((uintptr_t)theta_dev & 15u) == 0 && (ldtheta & 3) == 0;
+    const size_t per_warp = rows ? row_bytes : (size_t)p2 * 8 + 1024;
     int warps = 8;
-    while (warps > 1 && (size_t)warps * (p2 * 8 + 1024) > 48 * 1024) warps >>= 1;
-    const size_t smem = (size_t)warps * (p2 * 8 + 1024);
-    k_summarize<<<(unsigned)vpet_ceil_div(J, warps), warps * 32, smem, (cudaStream_t)stream>>>(
-        theta_dev, idx_dev, J, preferred_dev, Q, mean_dev, sd_dev, lo_dev, hi_dev);
+    while (warps > 1 && (size_t)warps * per_warp > 48 * 1024) warps = rows ? warps - 1 : warps >> 1;
+    const size_t smem = (size_t)warps * per_warp;
+    if (rows)
+        k_summarize<true><<<(unsigned)vpet_ceil_div(J, warps), warps * 32, smem, (cudaStream_t)stream>>>(
+            theta_dev, idx_dev, J, preferred_dev, Q, mean_dev, sd_dev, lo_dev, hi_dev, vec4);
+    else
+        k_summarize<false><<<(unsigned)vpet_ceil_div(J, warps), warps * 32, smem, (cudaStream_t)stream>>>(
+            theta_dev, idx_dev, J, preferred_dev, Q, mean_dev, sd_dev, lo_dev, hi_dev, vec4);
     VPET_LAUNCH_CHECK();
     return ABC_OK;
 }

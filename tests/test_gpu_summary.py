@@ -44,6 +44,36 @@ def test_select_and_summaries(orc, k):
         assert np.all(np.abs(a[m] - b[m]) <= 1e-5 * np.abs(b[m]) + 1e-7)
 
 
+@pytest.mark.parametrize("shift", [0, 1])
+def test_summaries_rows_on_and_off_alignment(orc, shift):
+    """Parameter rows that start on a 16-byte boundary (read four values per load) and the
+    same rows one element off it (read one value per load): the same summaries as the oracle,
+    with and without a preferred model, for a k whose accepted rows fit the row table."""
+    from paper_2603_14859_b300 import api
+    rng = np.random.default_rng(4242 + shift)
+    N, k, J = 4000, 200, 129
+    off = [0, 1500, 4000]
+    theta = rng.uniform(0.001, 1.0, (N, 8)).astype(np.float32)
+    theta[:1500, 4:] = 0
+    theta[1500:, 5:] = 0
+    idx = np.stack([rng.choice(N, k, replace=False) for _ in range(J)]).astype(np.int32)
+    flat = torch.zeros(N * 8 + shift, dtype=torch.float32, device="cuda")
+    tt = flat[shift:].view(N, 8)
+    tt.copy_(torch.from_numpy(theta))
+    ti = torch.from_numpy(idx).cuda()
+    _, pref = api.model_select(ti, off)
+    _, opref = orc.model_select(idx, off)
+    nparams, has_ki = [4, 5], [1, 1]
+    for pr, opr in ((pref, opref), (None, None)):
+        g = api.summarize(tt, off, nparams, has_ki, [0, 1, 2], ti, pr)
+        o = orc.summarize(theta, off, nparams, has_ki, [0, 1, 2], idx, opr)
+        for a, b in zip(g, o):
+            a = a.cpu().numpy().astype(np.float64)
+            assert np.array_equal(np.isnan(a), np.isnan(b))
+            m = ~np.isnan(b)
+            assert np.all(np.abs(a[m] - b[m]) <= 1e-5 * np.abs(b[m]) + 1e-7)
+
+
 @pytest.mark.parametrize("k", [40, 200, 256, 300])
 def test_summaries_with_many_ties(orc, k):
     """Parameter values from five distinct levels, so every order statistic of the 95 %
